@@ -1,0 +1,419 @@
+"""Plain FP64 CPU oracle for the HICU hot path (test infrastructure only).
+
+This module is the correctness reference for the CUDA library.  It is slow on
+purpose: every operation is the paper's definition written out with numpy
+slicing, ``einsum``, ``matmul`` and LAPACK's ``eigh``, in float64/complex128,
+with no blocking, fusion or reordering beyond what the definition states.
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it.  It imports nothing from the CUDA package and the
+CUDA package imports nothing from here.
+
+Citations name the paper ("HICU", Zhao, Potter & Ahmad, MRM 2021) by section,
+equation and algorithm step.
+
+Conventions (fixed by this library, see the readings listed in the design notes):
+  * k-space array x has shape (C, Nz, Ny, Nx); 2D uses Nz = 1 and 2D+t puts
+    time in the Nz slot.
+  * Kernel support K is rectangular (kx, ky, kz) over all C coils, so
+    n = C*kz*ky*kx.  A filter vector v of length n is ordered (c, dz, dy, dx)
+    with dx fastest, i.e. ``v.reshape(C, kz, ky, kx)``.
+  * H(x) is the multi-level Hankel matrix whose row for output position p is
+    the patch [x_c[p + d]] over (c, d) in that order, so H(x) v is the valid
+    (correlation-form) convolution of x with v (Theory section).  A kernel
+    flip only relabels v and leaves every singular value unchanged.
+  * A region S is (off, ext) per axis (x, y, z).  Valid outputs are the
+    positions whose whole kernel footprint lies inside S; an axis flagged
+    circular wraps modulo its extent instead (2D+t time axis, Methods,
+    Study II).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+# --------------------------------------------------------------- geometry
+
+
+@dataclass(frozen=True)
+class Geom:
+    dims: Tuple[int, int, int]          # (Nx, Ny, Nz)
+    ncoil: int
+    kernel: Tuple[int, int, int]        # (kx, ky, kz)
+    circular: Tuple[int, int, int] = (0, 0, 0)
+
+    @property
+    def n(self) -> int:
+        kx, ky, kz = self.kernel
+        return self.ncoil * kx * ky * kz
+
+
+@dataclass(frozen=True)
+class Region:
+    off: Tuple[int, int, int]
+    ext: Tuple[int, int, int]
+
+
+def full_region(geom: Geom) -> Region:
+    return Region((0, 0, 0), tuple(geom.dims))
+
+
+def out_shape(geom: Geom, reg: Region) -> Tuple[int, int, int]:
+    """Valid-output grid (sz, sy, sx) inside region S (Theory: valid convolution)."""
+    out = []
+    for a in range(3):
+        if geom.circular[a]:
+            out.append(reg.ext[a])
+        else:
+            out.append(reg.ext[a] - geom.kernel[a] + 1)
+    sx, sy, sz = out
+    return (sz, sy, sx)
+
+
+def num_outputs(geom: Geom, reg: Region) -> int:
+    """s = |valid outputs in S| (Theory, complexity paragraph)."""
+    sz, sy, sx = out_shape(geom, reg)
+    return sz * sy * sx
+
+
+def _axis_index(geom: Geom, reg: Region, axis: int, d: int) -> np.ndarray:
+    """Absolute input index along ``axis`` (0=x,1=y,2=z) read by every output at kernel offset d."""
+    sz, sy, sx = out_shape(geom, reg)
+    nout = (sx, sy, sz)[axis]
+    o = np.arange(nout)
+    if geom.circular[axis]:
+        rel = (o + d) % reg.ext[axis]
+    else:
+        rel = o + d
+    return reg.off[axis] + rel
+
+
+def _shifted_block(x: np.ndarray, geom: Geom, reg: Region, dz: int, dy: int, dx: int) -> np.ndarray:
+    """x_c[p + d] for every coil c and every valid output p: shape (C, sz, sy, sx)."""
+    iz = _axis_index(geom, reg, 2, dz)
+    iy = _axis_index(geom, reg, 1, dy)
+    ix = _axis_index(geom, reg, 0, dx)
+    return x[:, iz[:, None, None], iy[None, :, None], ix[None, None, :]]
+
+
+def _offsets(geom: Geom):
+    kx, ky, kz = geom.kernel
+    for dz in range(kz):
+        for dy in range(ky):
+            for dx in range(kx):
+                yield dz, dy, dx
+
+
+def _check(x: np.ndarray, geom: Geom, reg: Region):
+    C, nz, ny, nx = x.shape
+    assert (nx, ny, nz) == tuple(geom.dims) and C == geom.ncoil, "array does not match geometry"
+    for a in range(3):
+        assert 0 <= reg.off[a] and reg.off[a] + reg.ext[a] <= geom.dims[a], "region outside array"
+        if not geom.circular[a]:
+            assert reg.ext[a] >= geom.kernel[a], "region smaller than kernel"
+
+
+# ----------------------------------------------- Hankel operator H(x) and adjoints
+
+
+def hankel_matrix(x: np.ndarray, geom: Geom, reg: Region) -> np.ndarray:
+    """Explicit m-by-n multi-level Hankel matrix H(x) on region S (Theory section).
+
+    Row order: valid outputs (z, y, x) with x fastest.  Column order: (c, dz, dy, dx).
+    Only for small inputs (it is the object HICU never forms).
+    """
+    _check(x, geom, reg)
+    s = num_outputs(geom, reg)
+    kx, ky, kz = geom.kernel
+    cols = np.empty((geom.ncoil, kz, ky, kx, s), dtype=np.complex128)
+    for dz, dy, dx in _offsets(geom):
+        cols[:, dz, dy, dx, :] = _shifted_block(x, geom, reg, dz, dy, dx).reshape(geom.ncoil, s)
+    return cols.reshape(geom.n, s).T.copy()
+
+
+def conv_null(x: np.ndarray, geom: Geom, reg: Region, filters: np.ndarray) -> np.ndarray:
+    """R[:, k] = H(x) q_k for each filter q_k (Theory: H(x)v is the valid convolution of x with v).
+
+    filters: (p, C, kz, ky, kx) complex.  Returns R with shape (sz, sy, sx, p),
+    i.e. R[p_out, k] = sum_{c,d} x_c[p_out + d] q_k[c, d].
+    """
+    _check(x, geom, reg)
+    x = np.asarray(x, dtype=np.complex128)
+    f = np.asarray(filters, dtype=np.complex128)
+    R = np.zeros(out_shape(geom, reg) + (f.shape[0],), dtype=np.complex128)
+    for dz, dy, dx in _offsets(geom):
+        blk = _shifted_block(x, geom, reg, dz, dy, dx)            # (C, sz, sy, sx)
+        R += np.einsum("czyx,kc->zyxk", blk, f[:, :, dz, dy, dx])
+    return R
+
+
+def conv_null_adjoint(R: np.ndarray, geom: Geom, reg: Region, filters: np.ndarray,
+                      mask: Optional[np.ndarray] = None) -> np.ndarray:
+    """Adjoint of x -> [H(x) q_k]_k, optionally projected onto unsampled entries.
+
+    g_c[u] = sum_k sum_d conj(q_k[c, d]) R[u - d, k]  (the conjugate transpose of a valid
+    convolution is itself a convolution, Theory section).  With ``mask`` the result is
+    multiplied by (1 - M): the gradient is zero at observed locations (hard data
+    consistency, end of the Theory section).  Output shape (C, Nz, Ny, Nx), zero outside S.
+    """
+    f = np.asarray(filters, dtype=np.complex128)
+    R = np.asarray(R, dtype=np.complex128)
+    nx, ny, nz = geom.dims
+    g = np.zeros((geom.ncoil, nz, ny, nx), dtype=np.complex128)
+    for dz, dy, dx in _offsets(geom):
+        iz = _axis_index(geom, reg, 2, dz)
+        iy = _axis_index(geom, reg, 1, dy)
+        ix = _axis_index(geom, reg, 0, dx)
+        contrib = np.einsum("zyxk,kc->czyx", R, np.conj(f[:, :, dz, dy, dx]))
+        # for a fixed offset d the map p -> p + d is injective, so plain fancy-index add is exact
+        g[:, iz[:, None, None], iy[None, :, None], ix[None, None, :]] += contrib
+    if mask is not None:
+        g *= (1 - _mask4(mask, g.shape))
+    return g
+
+
+def _mask4(mask: np.ndarray, shape) -> np.ndarray:
+    m = np.asarray(mask).astype(np.float64)
+    if m.ndim == 3:
+        m = m[None]
+    return np.broadcast_to(m, shape)
+
+
+# ------------------------------------------------------------ Gram and null space
+
+
+def gram(x: np.ndarray, geom: Geom, reg: Region, chunk: int = 1 << 15) -> np.ndarray:
+    """G = H(x)^H H(x), the n-by-n Gram matrix of the block-Hankel matrix on region S.
+
+    Entry (a, b) is sum over valid outputs p of conj(h_p[a]) h_p[b]; its eigenvalues are
+    the squared singular values of H(x) (Eq. 1), and the paper's Discussion names SVD of
+    this Gram matrix as the alternative to rSVD.  Built in row chunks of H.
+    """
+    _check(x, geom, reg)
+    x = np.asarray(x, dtype=np.complex128)
+    sz, sy, sx = out_shape(geom, reg)
+    G = np.zeros((geom.n, geom.n), dtype=np.complex128)
+    plane = sy * sx
+    zstep = max(1, chunk // max(plane, 1))
+    for z0 in range(0, sz, zstep):
+        z1 = min(sz, z0 + zstep)
+        sub = Region(reg.off, reg.ext)
+        Hc = _hankel_rows(x, geom, sub, z0, z1)
+        G += Hc.conj().T @ Hc
+    return G
+
+
+def _hankel_rows(x, geom, reg, z0, z1):
+    sz, sy, sx = out_shape(geom, reg)
+    kx, ky, kz = geom.kernel
+    rows = (z1 - z0) * sy * sx
+    cols = np.empty((geom.ncoil, kz, ky, kx, rows), dtype=np.complex128)
+    for dz, dy, dx in _offsets(geom):
+        blk = _shifted_block(x, geom, reg, dz, dy, dx)[:, z0:z1]
+        cols[:, dz, dy, dx, :] = blk.reshape(geom.ncoil, rows)
+    return cols.reshape(geom.n, rows).T
+
+
+def nullspace(G: np.ndarray, r: int) -> Tuple[np.ndarray, np.ndarray]:
+    """Null-space basis Q (n x (n-r)) and ascending eigenvalues of G (Algorithm 1 steps 2-3).
+
+    The r principal right singular vectors V of H are the top-r eigenvectors of G = H^H H;
+    Q spans their orthogonal complement, here taken directly as the eigenvectors of the
+    n - r smallest eigenvalues.  J(x) = sum of those eigenvalues (Eq. 1).
+    """
+    n = G.shape[0]
+    if not (0 < r < n):
+        raise ValueError("rank must satisfy 0 < r < n")
+    w, V = np.linalg.eigh(G)
+    return V[:, : n - r].copy(), w
+
+
+def tail_energy(eigvals: np.ndarray, r: int) -> float:
+    """J(x) = sum_{k>r} sigma_k^2 {H(x)} (Eq. 1) from ascending eigenvalues of H^H H."""
+    n = eigvals.shape[0]
+    return float(np.sum(eigvals[: n - r]))
+
+
+# --------------------------------------------------------------- JL compression
+
+_GAMMA = 0x9E3779B97F4A7C15
+_M64 = (1 << 64) - 1
+
+
+def splitmix64_mix(z: int) -> int:
+    """SplitMix64 output function (Steele, Lea & Flood, OOPSLA 2014)."""
+    z &= _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def splitmix64_output(seed: int, k: int) -> int:
+    """k-th output (k >= 1) of the SplitMix64 sequence started at state ``seed``."""
+    return splitmix64_mix((seed + k * _GAMMA) & _M64)
+
+
+def gaussian(seed: int, counter: int, e: int) -> float:
+    """Standard normal number e of draw ``counter``: Box-Muller on two SplitMix64 outputs.
+
+    Outputs k0+1 and k0+2 with k0 = 2*(counter*2^32 + e) give u1 in (0, 1] and u2 in [0, 1);
+    z = sqrt(-2 ln u1) cos(2 pi u2).
+    """
+    k0 = 2 * ((counter << 32) + e)
+    o1 = splitmix64_output(seed, k0 + 1)
+    o2 = splitmix64_output(seed, k0 + 2)
+    u1 = ((o1 >> 11) + 1) * 2.0 ** -53
+    u2 = (o2 >> 11) * 2.0 ** -53
+    return math.sqrt(-2.0 * math.log(u1)) * math.cos(2.0 * math.pi * u2)
+
+
+def jl_matrix(seed: int, counter: int, rows: int, p: int) -> np.ndarray:
+    """P^(i,j): rows x p i.i.d. zero-mean Gaussian entries of variance 1/p (Theory, JL paragraph).
+
+    Element (row, col) is gaussian(seed, counter, row * p + col) / sqrt(p).
+    """
+    out = np.empty((rows, p))
+    for a in range(rows):
+        for b in range(p):
+            out[a, b] = gaussian(seed, counter, a * p + b)
+    return out / math.sqrt(p)
+
+
+def jl_compress(Q: np.ndarray, P: np.ndarray, mode: str = "nullspace") -> np.ndarray:
+    """Q~ = Q P compressed to p filters (Algorithm 1 step 6).
+
+    mode "nullspace": P is (n-r) x p and Q~ = Q P, the formula of step 6.
+    mode "projector": P is n x p (the dimension the Theory text gives) and Q~ = Q (Q^H P),
+    i.e. the n x p Gaussian projected onto span(Q); Q~ then depends only on the null
+    subspace, not on the basis chosen for it.
+    Returns filters of shape (p, n).
+    """
+    if mode == "nullspace":
+        Qt = Q @ P
+    elif mode == "projector":
+        Qt = Q @ (Q.conj().T @ P)
+    else:
+        raise ValueError(mode)
+    return Qt.T.copy()
+
+
+def as_filters(Qt_pn: np.ndarray, geom: Geom) -> np.ndarray:
+    kx, ky, kz = geom.kernel
+    return Qt_pn.reshape(Qt_pn.shape[0], geom.ncoil, kz, ky, kx)
+
+
+# ------------------------------------------------------------ gradient step + ELS
+
+
+@dataclass
+class StepInfo:
+    eta: float
+    objective: float     # ||H(y) Q~||_F^2 before the step
+    gnorm2: float        # ||g||^2
+    denom: float         # ||H(g) Q~||_F^2
+
+
+def gradient(y, geom, reg, filters, mask):
+    """g = (1 - M) o sum_k H^H(H(y) q~_k)  (Algorithm 1 step 7 with hard data consistency).
+
+    The exact Wirtinger gradient of sum_k ||H(y) q~_k||^2 is 2 g; the factor 2 is absorbed
+    by the exact line search, which makes eta * g invariant to it.
+    """
+    R = conv_null(y, geom, reg, filters)
+    return conv_null_adjoint(R, geom, reg, filters, mask), R
+
+
+def gd_step(y: np.ndarray, mask: np.ndarray, geom: Geom, reg: Region, filters: np.ndarray
+            ) -> Tuple[np.ndarray, StepInfo]:
+    """One descent step with exact line search (Algorithm 1 steps 7-8).
+
+    phi(eta) = ||H(y - eta g) Q~||^2 is quadratic in eta; its minimiser is
+    eta = Re<H(y)Q~, H(g)Q~> / ||H(g)Q~||^2, obtained from one more convolution of g with
+    each of the p filters (Theory, ELS paragraph).  Because g is the masked adjoint of
+    H(y)Q~, the numerator equals ||g||^2.  A zero gradient or zero denominator gives eta = 0.
+    """
+    y = np.asarray(y, dtype=np.complex128)
+    g, R = gradient(y, geom, reg, filters, mask)
+    obj = float(np.vdot(R, R).real)
+    gn2 = float(np.vdot(g, g).real)
+    Rg = conv_null(g, geom, reg, filters)
+    D = float(np.vdot(Rg, Rg).real)
+    eta = gn2 / D if (D > 0.0 and gn2 > 0.0) else 0.0
+    return y - eta * g, StepInfo(eta, obj, gn2, D)
+
+
+# ----------------------------------------------------------- the HICU iteration
+
+
+@dataclass
+class StageSpec:
+    region: Region
+    iters: int
+    gd_steps: int
+    p: int
+
+
+@dataclass
+class ReconLog:
+    J: List[float]
+    objective: List[float]
+    eta: List[float]
+
+
+def initial_estimate(x0: np.ndarray, mask: np.ndarray, mode: str = "zero_filled") -> np.ndarray:
+    """x^(0) = vec{X0} (Algorithm 1); for 2D+t the time-averaged k-space (Methods, Study II):
+    each unsampled (k_x, k_y, t) takes the mean of its sampled frames, or zero if none."""
+    x = np.asarray(x0, dtype=np.complex128).copy()
+    if mode == "zero_filled":
+        return x
+    if mode != "time_average":
+        raise ValueError(mode)
+    m = _mask4(mask, x.shape)
+    cnt = m.sum(axis=1, keepdims=True)                       # frames sampled per (c, ky, kx)
+    tot = (x * m).sum(axis=1, keepdims=True)
+    avg = np.where(cnt > 0, tot / np.maximum(cnt, 1), 0.0)
+    return np.where(m > 0, x, np.broadcast_to(avg, x.shape))
+
+
+def reconstruct(x0: np.ndarray, mask: np.ndarray, geom: Geom, stages: Sequence[StageSpec], r: int,
+                seed: int, jl_mode: str = "projector", gram_on: str = "previous",
+                init: str = "zero_filled", log: Optional[ReconLog] = None) -> np.ndarray:
+    """Algorithm 1 (HICU) with the Gram route for steps 2-3 and centre-out stages.
+
+    For i = 1..I: null space of H^(i-1)(x^(i-1)) (step 2 names the previous region;
+    ``gram_on="current"`` uses S^(i) instead), then G^(i) descent steps on S^(i), each with a
+    fresh JL draw (counter = global step index, starting at 0).
+    """
+    x = initial_estimate(x0, mask, init)
+    counter = 0
+    prev = stages[0].region
+    for st in stages:
+        for _ in range(st.iters):
+            greg = prev if gram_on == "previous" else st.region
+            G = gram(x, geom, greg)
+            Q, w = nullspace(G, r)
+            if log is not None:
+                log.J.append(tail_energy(w, r))
+            y = x
+            rows = Q.shape[0] if jl_mode == "projector" else Q.shape[1]
+            for _ in range(st.gd_steps):
+                P = jl_matrix(seed, counter, rows, st.p)
+                counter += 1
+                f = as_filters(jl_compress(Q, P, jl_mode), geom)
+                y, info = gd_step(y, mask, geom, st.region, f)
+                if log is not None:
+                    log.objective.append(info.objective)
+                    log.eta.append(info.eta)
+            x = y
+            prev = st.region
+    return x
+
+
+def ser_db(x_ref: np.ndarray, x_hat: np.ndarray) -> float:
+    """SER = 20 log10(||X||_F / ||X_hat - X||_F) over all coils (Methods, Study I)."""
+    num = np.linalg.norm(np.asarray(x_ref, dtype=np.complex128).ravel())
+    den = np.linalg.norm((np.asarray(x_hat, dtype=np.complex128) - x_ref).ravel())
+    return float(20.0 * np.log10(num / den))

@@ -1,0 +1,425 @@
+"""Pins for the FP64 oracle: every check compares it with something other than itself.
+
+Hand-derived fixtures (tests/golden), brute-force pure-Python loops on tiny inputs,
+closed forms (adjoint identity, exact low rank, quadratic line search), invariants
+(data consistency, monotone decrease) and published generator outputs.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import hicu_oracle as O
+from synth.phantoms import lowrank_exponential_kspace, random_complex
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ helpers
+
+
+def read_hand_examples():
+    cases, cur, block = [], None, None
+    with open(os.path.join(GOLDEN, "hankel_hand_examples.txt")) as fh:
+        for raw in fh:
+            line = raw.split("#", 1)[0].strip()
+            if not line:
+                continue
+            tok = line.split()
+            if tok[0] == "dims":
+                cur = {"dims": tuple(map(int, tok[1:])), "null": []}
+                block = None
+            elif tok[0] in ("coils",):
+                cur["coils"] = int(tok[1])
+            elif tok[0] in ("kernel", "circular"):
+                cur[tok[0]] = tuple(map(int, tok[1:]))
+            elif tok[0] == "x":
+                cur["x"] = np.array(list(map(float, tok[1:])))
+            elif tok[0] in ("H", "G"):
+                block = tok[0]
+                cur[block] = []
+            elif tok[0] == "null":
+                cur["null"].append(np.array(list(map(float, tok[1:]))))
+                block = None
+            elif tok[0] == "end":
+                for k in ("H", "G"):
+                    if k in cur:
+                        cur[k] = np.array(cur[k])
+                cases.append(cur)
+                cur, block = None, None
+            else:
+                cur[block].append(list(map(float, tok)))
+    return cases
+
+
+def brute_hankel(x, geom, reg):
+    """Row-by-row construction of H(x) with explicit loops (independent of the oracle)."""
+    nx, ny, nz = geom.dims
+    kx, ky, kz = geom.kernel
+    C = geom.ncoil
+    ext = reg.ext
+    rng_ax = []
+    for a in range(3):
+        k = geom.kernel[a]
+        rng_ax.append(ext[a] if geom.circular[a] else ext[a] - k + 1)
+    rows = []
+    for pz in range(rng_ax[2]):
+        for py in range(rng_ax[1]):
+            for px in range(rng_ax[0]):
+                row = []
+                for c in range(C):
+                    for dz in range(kz):
+                        for dy in range(ky):
+                            for dx in range(kx):
+                                idx = []
+                                for a, (p, d) in enumerate(((px, dx), (py, dy), (pz, dz))):
+                                    rel = p + d
+                                    if geom.circular[a]:
+                                        rel %= ext[a]
+                                    idx.append(reg.off[a] + rel)
+                                row.append(x[c, idx[2], idx[1], idx[0]])
+                rows.append(row)
+    return np.array(rows, dtype=np.complex128)
+
+
+def brute_conv_operator(v, geom, reg):
+    """Matrix T_v with T_v @ vec(x) = H(x) v, built entry by entry (x in C-order)."""
+    nx, ny, nz = geom.dims
+    kx, ky, kz = geom.kernel
+    C = geom.ncoil
+    N = C * nz * ny * nx
+    H_rows = []
+    ext = reg.ext
+    out = [ext[a] if geom.circular[a] else ext[a] - geom.kernel[a] + 1 for a in range(3)]
+    vv = v.reshape(C, kz, ky, kx)
+    for pz in range(out[2]):
+        for py in range(out[1]):
+            for px in range(out[0]):
+                row = np.zeros(N, dtype=np.complex128)
+                for c, dz, dy, dx in itertools.product(range(C), range(kz), range(ky), range(kx)):
+                    idx = []
+                    for a, (p, d) in enumerate(((px, dx), (py, dy), (pz, dz))):
+                        rel = p + d
+                        if geom.circular[a]:
+                            rel %= ext[a]
+                        idx.append(reg.off[a] + rel)
+                    flat = ((c * nz + idx[2]) * ny + idx[1]) * nx + idx[0]
+                    row[flat] += vv[c, dz, dy, dx]
+                H_rows.append(row)
+    return np.array(H_rows)
+
+
+SMALL_CASES = [
+    # dims, C, kernel, circular, region(off, ext)
+    ((7, 6, 1), 2, (3, 2, 1), (0, 0, 0), ((1, 0, 0), (5, 6, 1))),
+    ((5, 4, 4), 2, (2, 2, 2), (0, 0, 0), ((0, 1, 1), (5, 3, 3))),
+    ((6, 5, 4), 2, (3, 2, 2), (0, 0, 1), ((1, 1, 0), (4, 4, 4))),
+]
+
+
+def make_case(i, seed=0):
+    dims, C, ker, circ, (off, ext) = SMALL_CASES[i]
+    geom = O.Geom(dims, C, ker, circ)
+    reg = O.Region(off, ext)
+    rng = np.random.default_rng(seed + i)
+    x = random_complex(rng, (C, dims[2], dims[1], dims[0]))
+    return geom, reg, x, rng
+
+
+def rand_filters(rng, geom, p):
+    kx, ky, kz = geom.kernel
+    return random_complex(rng, (p, geom.ncoil, kz, ky, kx))
+
+
+# --------------------------------------------------------------- golden pins
+
+
+def test_splitmix64_published_vectors():
+    with open(os.path.join(GOLDEN, "splitmix64_vectors.txt")) as fh:
+        for raw in fh:
+            line = raw.split("#", 1)[0].strip()
+            if not line:
+                continue
+            vals = [int(t) for t in line.split()]
+            seed, outs = vals[0], vals[1:]
+            got = [O.splitmix64_output(seed, k) for k in range(1, len(outs) + 1)]
+            assert got == outs
+
+
+def test_gaussian_draws_are_standard_normal():
+    from scipy import stats
+    z = np.array([O.gaussian(7, 3, e) for e in range(20000)])
+    assert abs(z.mean()) < 0.03
+    assert abs(z.var() - 1.0) < 0.04
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    # different counters give different draws
+    assert O.gaussian(7, 3, 0) != O.gaussian(7, 4, 0)
+
+
+@pytest.mark.parametrize("case", [0, 1])
+def test_hand_examples(case):
+    ex = read_hand_examples()[case]
+    nx, ny, nz = ex["dims"]
+    geom = O.Geom((nx, ny, nz), ex["coils"], ex["kernel"], ex["circular"])
+    reg = O.full_region(geom)
+    x = ex["x"].reshape(1, nz, ny, nx).astype(np.complex128)
+    H = O.hankel_matrix(x, geom, reg)
+    np.testing.assert_array_equal(H.real, ex["H"])
+    assert np.all(H.imag == 0)
+    # H v through the convolution routine, one unit vector at a time
+    eye = np.eye(geom.n).reshape(geom.n, 1, *geom.kernel[::-1])
+    R = O.conv_null(x, geom, reg, eye)
+    np.testing.assert_array_equal(R.reshape(-1, geom.n).real, ex["H"])
+    if "G" in ex:
+        G = O.gram(x, geom, reg)
+        np.testing.assert_array_equal(G.real, ex["G"])
+        for v in ex["null"]:
+            Rv = O.conv_null(x, geom, reg, v.reshape(1, 1, *geom.kernel[::-1]))
+            assert np.max(np.abs(Rv)) == 0.0
+        Q, w = O.nullspace(G, 2)
+        assert O.tail_energy(w, 2) < 1e-10 * np.trace(G).real
+        # the null space found must be the span of the hand-derived annihilators
+        Nv = np.array(ex["null"]).T
+        Pn = Nv @ np.linalg.pinv(Nv)
+        np.testing.assert_allclose(Q @ Q.conj().T, Pn, atol=1e-10)
+
+
+# ------------------------------------------------------------ brute force pins
+
+
+@pytest.mark.parametrize("i", range(len(SMALL_CASES)))
+def test_hankel_and_conv_match_brute_force(i):
+    geom, reg, x, rng = make_case(i)
+    Hb = brute_hankel(x, geom, reg)
+    np.testing.assert_allclose(O.hankel_matrix(x, geom, reg), Hb, rtol=0, atol=0)
+    f = rand_filters(rng, geom, 3)
+    R = O.conv_null(x, geom, reg, f)
+    ref = Hb @ f.reshape(3, -1).T
+    np.testing.assert_allclose(R.reshape(-1, 3), ref, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("i", range(len(SMALL_CASES)))
+def test_adjoint_matches_brute_force(i):
+    geom, reg, x, rng = make_case(i)
+    p = 2
+    f = rand_filters(rng, geom, p)
+    s = O.num_outputs(geom, reg)
+    R = random_complex(rng, O.out_shape(geom, reg) + (p,))
+    g = O.conv_null_adjoint(R, geom, reg, f)
+    ref = np.zeros(x.size, dtype=np.complex128)
+    for k in range(p):
+        T = brute_conv_operator(f[k].ravel(), geom, reg)
+        ref += T.conj().T @ R.reshape(s, p)[:, k]
+    np.testing.assert_allclose(g.ravel(), ref, rtol=1e-13, atol=1e-12)
+    # masked version zeroes exactly the observed entries
+    mask = (rng.random(x.shape[1:]) < 0.4).astype(np.uint8)
+    gm = O.conv_null_adjoint(R, geom, reg, f, mask)
+    np.testing.assert_array_equal(gm, g * (1 - mask[None]))
+
+
+@pytest.mark.parametrize("i", range(len(SMALL_CASES)))
+def test_adjoint_identity(i):
+    geom, reg, x, rng = make_case(i)
+    f = rand_filters(rng, geom, 4)
+    R = random_complex(rng, O.out_shape(geom, reg) + (4,))
+    lhs = np.vdot(R, O.conv_null(x, geom, reg, f))
+    rhs = np.vdot(O.conv_null_adjoint(R, geom, reg, f), x)
+    assert abs(lhs - rhs) < 1e-12 * (abs(lhs) + 1)
+
+
+@pytest.mark.parametrize("i", range(len(SMALL_CASES)))
+def test_gram_matches_explicit_hankel(i):
+    geom, reg, x, rng = make_case(i)
+    Hb = brute_hankel(x, geom, reg)
+    G = O.gram(x, geom, reg)
+    np.testing.assert_allclose(G, Hb.conj().T @ Hb, rtol=1e-13, atol=1e-12)
+    np.testing.assert_allclose(G, G.conj().T, atol=0)
+    assert np.linalg.eigvalsh(G).min() > -1e-10 * np.trace(G).real
+    np.testing.assert_allclose(np.trace(G).real, np.sum(np.abs(Hb) ** 2), rtol=1e-13)
+
+
+@pytest.mark.parametrize("i", range(len(SMALL_CASES)))
+def test_nullspace_tail_energy_is_eq1(i):
+    geom, reg, x, rng = make_case(i)
+    Hb = brute_hankel(x, geom, reg)
+    G = O.gram(x, geom, reg)
+    r = geom.n // 3
+    Q, w = O.nullspace(G, r)
+    sv = np.linalg.svd(Hb, compute_uv=False)          # descending
+    J_eq1 = np.sum(sv[r:] ** 2) if Hb.shape[0] >= geom.n else np.sum(sv[r:] ** 2)
+    J = O.tail_energy(w, r)
+    assert abs(J - J_eq1) < 1e-10 * sv[0] ** 2
+    # J = min_Q ||H Q||_F^2 with Q^H Q = I (Theory), attained at the oracle's Q
+    assert abs(np.linalg.norm(Hb @ Q) ** 2 - J) < 1e-10 * sv[0] ** 2
+    np.testing.assert_allclose(Q.conj().T @ Q, np.eye(Q.shape[1]), atol=1e-12)
+    np.testing.assert_allclose(G @ Q, Q * w[: Q.shape[1]], atol=1e-10 * sv[0] ** 2)
+    # any other orthonormal n x (n-r) basis does at least as badly
+    for t in range(5):
+        Z, _ = np.linalg.qr(random_complex(rng, (geom.n, geom.n - r)))
+        assert np.linalg.norm(Hb @ Z) ** 2 >= J - 1e-9 * sv[0] ** 2
+
+
+def test_exactly_low_rank_kspace_is_annihilated():
+    rng = np.random.default_rng(5)
+    L = 6
+    x = lowrank_exponential_kspace(rng, (1, 12, 11), 3, L)
+    geom = O.Geom((11, 12, 1), 3, (3, 3, 1))
+    reg = O.full_region(geom)
+    G = O.gram(x, geom, reg)
+    w = np.linalg.eigvalsh(G)
+    assert w[: geom.n - L].max() < 1e-11 * w[-1]
+    Q, _ = O.nullspace(G, L)
+    R = O.conv_null(x, geom, reg, Q.T.reshape(-1, 3, 1, 3, 3))
+    assert np.linalg.norm(R) < 1e-6 * np.linalg.norm(x)
+
+
+# --------------------------------------------------------------- JL and ELS
+
+
+def test_jl_identity_recovers_full_gradient():
+    geom, reg, x, rng = make_case(0)
+    G = O.gram(x, geom, reg)
+    r = 4
+    Q, _ = O.nullspace(G, r)
+    mask = (rng.random(x.shape[1:]) < 0.3).astype(np.uint8)
+    full = O.as_filters(Q.T.copy(), geom)                   # all n - r null filters
+    g_full, _ = O.gradient(x, geom, reg, full, mask)
+    # nullspace mode with P = I_(n-r): the compressed bank is Q itself
+    f_ns = O.as_filters(O.jl_compress(Q, np.eye(geom.n - r), "nullspace"), geom)
+    np.testing.assert_allclose(O.gradient(x, geom, reg, f_ns, mask)[0], g_full, atol=1e-12)
+    # projector mode with P = I_n: bank Q Q^H gives the same objective and gradient
+    f_pr = O.as_filters(O.jl_compress(Q, np.eye(geom.n), "projector"), geom)
+    g_pr, R_pr = O.gradient(x, geom, reg, f_pr, mask)
+    scale = np.abs(g_full).max()
+    np.testing.assert_allclose(g_pr, g_full, atol=1e-11 * scale)
+    # gradient by brute-force operator matrices: sum_j T_qj^H T_qj y
+    ref = np.zeros(x.size, dtype=np.complex128)
+    for j in range(Q.shape[1]):
+        T = brute_conv_operator(Q[:, j], geom, reg)
+        ref += T.conj().T @ (T @ x.ravel())
+    ref *= (1 - np.broadcast_to(mask[None], x.shape)).ravel()
+    np.testing.assert_allclose(g_full.ravel(), ref, atol=1e-11 * scale)
+
+
+@pytest.mark.parametrize("mode", ["nullspace", "projector"])
+def test_jl_mean_preserves_projector(mode):
+    rng = np.random.default_rng(11)
+    n, r, p = 12, 5, 3
+    Q, _ = np.linalg.qr(random_complex(rng, (n, n - r)))
+    rows = n if mode == "projector" else n - r
+    acc = np.zeros((n, n), dtype=np.complex128)
+    T = 3000
+    for t in range(T):
+        P = O.jl_matrix(99, t, rows, p)
+        Qt = O.jl_compress(Q, P, mode).T                    # n x p
+        acc += Qt @ Qt.conj().T
+    acc /= T
+    # E[Q~ Q~^H] = Q Q^H (Theory: JL keeps the mean gradient direction)
+    err = np.linalg.norm(acc - Q @ Q.conj().T) / np.linalg.norm(Q @ Q.conj().T)
+    assert err < 0.08
+
+
+def test_gradient_matches_finite_differences():
+    geom, reg, x, rng = make_case(1)
+    f = rand_filters(rng, geom, 3)
+
+    def obj(y):
+        R = O.conv_null(y, geom, reg, f)
+        return float(np.vdot(R, R).real)
+
+    g, _ = O.gradient(x, geom, reg, f, None)
+    h = 1e-6
+    for _ in range(6):
+        idx = tuple(int(rng.integers(0, s)) for s in x.shape)
+        e = np.zeros_like(x)
+        e[idx] = 1.0
+        d_re = (obj(x + h * e) - obj(x - h * e)) / (2 * h)
+        d_im = (obj(x + 1j * h * e) - obj(x - 1j * h * e)) / (2 * h)
+        # Wirtinger: d f = 2 Re<g, dy>  =>  df/da = 2 Re g, df/db = 2 Im g
+        assert abs(d_re - 2 * g[idx].real) < 1e-5 * (1 + abs(d_re))
+        assert abs(d_im - 2 * g[idx].imag) < 1e-5 * (1 + abs(d_im))
+
+
+def test_exact_line_search_is_the_quadratic_minimiser():
+    geom, reg, x, rng = make_case(2)
+    f = rand_filters(rng, geom, 3)
+    mask = (rng.random(x.shape[1:]) < 0.35).astype(np.uint8)
+    y1, info = O.gd_step(x, mask, geom, reg, f)
+    g, R = O.gradient(x, geom, reg, f, mask)
+    Rg = O.conv_null(g, geom, reg, f)
+    # numerator identity: Re<H(y)Q~, H(g)Q~> = ||g||^2 because g is the masked adjoint
+    assert abs(np.vdot(R, Rg).real - info.gnorm2) < 1e-11 * info.gnorm2
+
+    def phi(eta):
+        Ry = O.conv_null(x - eta * g, geom, reg, f)
+        return float(np.vdot(Ry, Ry).real)
+
+    e = info.eta
+    for eps in (1e-3 * e, 1e-2 * e, 0.5 * e):
+        assert phi(e) <= phi(e + eps) and phi(e) <= phi(e - eps)
+    # decrease in closed form: phi(0) - phi(eta*) = ||g||^4 / D
+    assert abs((phi(0) - phi(e)) - info.gnorm2 ** 2 / info.denom) < 1e-9 * phi(0)
+    assert abs(phi(0) - info.objective) < 1e-12 * phi(0)
+
+
+def test_zero_gradient_gives_zero_step():
+    geom, reg, x, rng = make_case(0)
+    f = rand_filters(rng, geom, 2)
+    mask = np.ones(x.shape[1:], dtype=np.uint8)               # everything observed
+    y1, info = O.gd_step(x, mask, geom, reg, f)
+    assert info.eta == 0.0 and info.gnorm2 == 0.0
+    np.testing.assert_array_equal(y1, x)
+
+
+def test_data_consistency_and_monotone_objective():
+    geom, reg, x, rng = make_case(0)
+    f = rand_filters(rng, geom, 3)
+    mask = (rng.random(x.shape[1:]) < 0.4).astype(np.uint8)
+    y = x.copy()
+    objs = []
+    for _ in range(8):
+        y, info = O.gd_step(y, mask, geom, reg, f)
+        objs.append(info.objective)
+    m4 = np.broadcast_to(mask[None], x.shape).astype(bool)
+    np.testing.assert_array_equal(y[m4], x[m4])                # sampled entries untouched
+    outside = np.ones(x.shape[1:], dtype=bool)
+    outside[reg.off[2]:reg.off[2] + reg.ext[2], reg.off[1]:reg.off[1] + reg.ext[1],
+            reg.off[0]:reg.off[0] + reg.ext[0]] = False
+    np.testing.assert_array_equal(y[:, outside], x[:, outside])  # nothing outside S moves
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(objs, objs[1:]))
+
+
+def test_time_average_initialisation_by_hand():
+    # one coil, 3 frames, 1x2 pixels; frame-sampling pattern chosen by hand
+    x0 = np.zeros((1, 3, 1, 2), dtype=np.complex128)
+    mask = np.zeros((3, 1, 2), dtype=np.uint8)
+    x0[0, 0, 0, 0], mask[0, 0, 0] = 2.0, 1
+    x0[0, 2, 0, 0], mask[2, 0, 0] = 4.0 + 2j, 1
+    x = O.initial_estimate(x0, mask, "time_average")
+    np.testing.assert_array_equal(x[0, :, 0, 0], [2.0, 3.0 + 1j, 4.0 + 2j])
+    np.testing.assert_array_equal(x[0, :, 0, 1], [0, 0, 0])   # never sampled -> zero
+
+
+def test_reconstruct_recovers_exactly_low_rank_data():
+    rng = np.random.default_rng(3)
+    L = 4
+    x_true = lowrank_exponential_kspace(rng, (1, 16, 16), 2, L)
+    mask = (rng.random((1, 16, 16)) < 0.55).astype(np.uint8)
+    x0 = x_true * mask[None]
+    geom = O.Geom((16, 16, 1), 2, (3, 3, 1))
+    st = [O.StageSpec(O.full_region(geom), iters=40, gd_steps=5, p=6)]
+    log = O.ReconLog([], [], [])
+    xr = O.reconstruct(x0, mask, geom, st, r=L, seed=1, log=log)
+    ser0 = O.ser_db(x_true, x0)
+    ser = O.ser_db(x_true, xr)
+    assert ser > ser0 + 30.0, (ser0, ser)
+    assert log.J[-1] < 1e-4 * log.J[0]
+    m4 = np.broadcast_to(mask[None], x0.shape).astype(bool)
+    np.testing.assert_array_equal(xr[m4], x0[m4])
+
+
+def test_ser_definition():
+    a = np.ones(4, dtype=np.complex128)
+    assert abs(O.ser_db(a, a * 1.1) - 20.0) < 1e-12              # ||X||/||0.1 X|| = 10
