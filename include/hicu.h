@@ -1,0 +1,249 @@
+/*
+ * hicu.h - C ABI of libhicu, a GB300 (sm_103a) library for the hot path of
+ * HICU, the calibrationless MRI reconstruction of Zhao, Potter & Ahmad
+ * ("High-dimensional fast convolutional framework (HICU) for calibrationless
+ * MRI", Magn. Reson. Med. 2021).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Complex numbers are interleaved (re, im) pairs: complex64 = 2 floats,
+ *    complex128 = 2 doubles.
+ *  - k-space x: complex64, shape [C][Nz][Ny][Nx] (x fastest, coil slowest).
+ *    2D uses Nz = 1; 2D+t puts time in the Nz slot.  k-space is centred.
+ *  - sampling mask M: uint8 (0 = unobserved, nonzero = observed), shape
+ *    [Nz][Ny][Nx] shared by all coils, or [C][Nz][Ny][Nx] when
+ *    geom.mask_per_coil = 1 (multi-shot channel stacks).
+ *  - kernel support K is rectangular over all C coils (Theory section: a
+ *    kernel of size Nc along the coil axis makes the convolution sum over
+ *    coils), so n = C*kz*ky*kx.  A filter is n complex64 values ordered
+ *    [C][kz][ky][kx]; a bank of p filters is [p][C][kz][ky][kx].
+ *  - H(x) is the multi-level Hankel matrix of the Theory section; row p of
+ *    H(x) is the patch x_c[p + d] over (c, d) in filter order, so H(x) v is
+ *    the valid convolution of x with v (correlation form).  It is never
+ *    formed.
+ *  - region S = (off, ext) per axis (x, y, z), the centre-out region of
+ *    Algorithm 1 step 4.  Valid outputs are the positions whose whole kernel
+ *    footprint lies inside S, s = prod(ext - k + 1); an axis flagged circular
+ *    wraps modulo ext and contributes ext outputs (2D+t time axis, Methods,
+ *    Study II).  Nothing outside S is read or written.
+ *  - R, the output of the convolution with a bank of p filters, is complex64
+ *    [sz][sy][sx][p] (valid outputs in (z, y, x) order, filter fastest).
+ *  - All data pointers are DEVICE pointers owned by the caller unless a call
+ *    says otherwise; the library never frees them.  Scratch memory belongs to
+ *    the handle, which grows it on demand with cudaMalloc.
+ *  - Calls are asynchronous on the given stream (a cudaStream_t passed as
+ *    void*, NULL = legacy default stream) unless documented otherwise.  They
+ *    return a hicu_status and never abort; hicu_last_error() gives the text.
+ *  - Errors found on the device (a bounded wait that gave up, a non-finite
+ *    value) are recorded in a device word of the handle and reported by
+ *    hicu_check(), which synchronises the stream.
+ *  - A handle belongs to the device that was current at hicu_create(); use
+ *    it from one host thread at a time.
+ */
+#ifndef HICU_H_
+#define HICU_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hicu_handle hicu_handle;
+
+typedef enum {
+  HICU_OK = 0,
+  HICU_ERR_ARG = 1,         /* null pointer, bad enum or flag */
+  HICU_ERR_SHAPE = 2,       /* geometry / region / layout inconsistent */
+  HICU_ERR_RANK = 3,        /* r outside (0, n), p outside [1, n-r] */
+  HICU_ERR_ALLOC = 4,       /* workspace allocation failed */
+  HICU_ERR_CUDA = 5,        /* a CUDA runtime call or launch failed */
+  HICU_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+  HICU_ERR_NUMERIC = 7,     /* non-finite value met on the device */
+  HICU_ERR_UNSUPPORTED = 8  /* valid request this build does not handle */
+} hicu_status;
+
+typedef enum {
+  HICU_FP32 = 0,        /* complex FP32 on CUDA cores (plain form) */
+  HICU_SPLIT_BF16 = 1   /* tcgen05 tensor cores, hi+lo bf16 split, FP32 accumulate */
+} hicu_prec;
+
+typedef enum {
+  HICU_JL_NULLSPACE = 0, /* Q~ = Q P, P is (n-r) x p  (Algorithm 1 step 6) */
+  HICU_JL_PROJECTOR = 1  /* Q~ = Q (Q^H P), P is n x p: depends only on span(Q) */
+} hicu_jl;
+
+typedef struct {
+  int64_t dim[3];        /* Nx, Ny, Nz */
+  int32_t ncoil;         /* C (channels; shots stacked as channels count here) */
+  int32_t k[3];          /* kernel extent kx, ky, kz (1 for an unused axis) */
+  uint8_t circular[3];   /* per axis: 0 = valid convolution, 1 = circular */
+  uint8_t mask_per_coil; /* 0: mask [Nz][Ny][Nx]; 1: mask [C][Nz][Ny][Nx] */
+} hicu_geom;
+
+typedef struct {
+  int64_t off[3];        /* first index of S along x, y, z */
+  int64_t ext[3];        /* extent of S along x, y, z */
+} hicu_region;
+
+/* One centre-out stage (Algorithm 1 steps 4-8 repeated `iters` times). */
+typedef struct {
+  hicu_region region;    /* S^(i) for the iterations of this stage */
+  int32_t iters;         /* outer iterations in this stage */
+  int32_t gd_steps;      /* G^(i): descent steps per outer iteration */
+  int32_t p;             /* JL compression dimension */
+} hicu_stage;
+
+typedef struct {
+  int64_t rank;              /* r */
+  int32_t nstages;
+  const hicu_stage* stages;  /* host array of nstages entries */
+  uint64_t seed;             /* JL generator seed */
+  int32_t jl;                /* hicu_jl */
+  int32_t prec;              /* hicu_prec for the convolutions */
+  int32_t gram_on_current;   /* 0: null space of H^(i-1) (Algorithm 1 step 2 as
+                                printed, S^(0) := S^(1)); 1: use S^(i) */
+  int32_t init;              /* 0: x^(0) = X0; 1: time-averaged along z (2D+t) */
+} hicu_params;
+
+/* Optional per-iteration log, HOST arrays (any may be NULL). */
+typedef struct {
+  double* J;          /* per outer iteration: sum of the n-r smallest eigenvalues (Eq. 1) */
+  double* objective;  /* per descent step: ||H(y) Q~||_F^2 before the step */
+  double* eta;        /* per descent step: exact line-search step size */
+} hicu_log;
+
+/* ---------------------------------------------------------------- handle */
+
+/* Create a handle on the current CUDA device.  *out receives the handle. */
+hicu_status hicu_create(hicu_handle** out);
+/* Release the handle and its workspace (synchronises the device). */
+hicu_status hicu_destroy(hicu_handle* h);
+/* Text of the last error on this handle ("" if none).  Owned by the handle. */
+const char* hicu_last_error(const hicu_handle* h);
+/* Static name of a status code. */
+const char* hicu_status_string(hicu_status s);
+/* Synchronise `stream`, then report (and clear) any device-side error word. */
+hicu_status hicu_check(hicu_handle* h, void* stream);
+
+/* Filter length n = C*kx*ky*kz, or -1 for an invalid geometry. */
+int64_t hicu_filter_length(const hicu_geom* geom);
+/* Number of valid outputs s of region S, or -1 if S does not fit the geometry. */
+int64_t hicu_num_outputs(const hicu_geom* geom, const hicu_region* region);
+
+/* ------------------------------------------------------------ hot path */
+
+/*
+ * hicu_gram - G = H(x)^H H(x) on region S (Eq. 1: the eigenvalues of G are the
+ * squared singular values of H; the Discussion names SVD of this Gram matrix
+ * as the alternative to rSVD for Algorithm 1 step 2).
+ *   x : complex64 k-space [C][Nz][Ny][Nx]
+ *   G : complex128 n x n, row-major: G[a*n + b] = sum_p conj(h_p[a]) h_p[b]
+ * Products of the FP32 inputs are formed exactly and accumulated in
+ * double-word arithmetic; entries are computed by multi-coil cross-correlation
+ * (one correlation per coil pair and lag), never from H itself.
+ */
+hicu_status hicu_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* region,
+                      const float* x, double* G, void* stream);
+
+/*
+ * hicu_nullspace - eigen-decomposition of the Hermitian n x n matrix G and the
+ * null-space basis Q spanned by the eigenvectors of its n-r smallest
+ * eigenvalues (Algorithm 1 steps 2-3: Q is the orthogonal complement of the r
+ * principal right singular vectors of H).  FP64 parallel Jacobi on the GPU.
+ *   G       : complex128 n x n row-major, Hermitian (only read)
+ *   Q       : complex128 [(n-r)][n]: null vector j is Q[j*n .. j*n+n-1],
+ *             ordered by ascending eigenvalue
+ *   eigvals : double [n], ascending (nullable)
+ * Eigenvectors are unique only up to a unit phase (and rotations inside
+ * repeated eigenvalues).  If `warm` is nonzero and the previous call on this
+ * handle had the same n, its eigenvectors seed the iteration.
+ */
+hicu_status hicu_nullspace(hicu_handle* h, int64_t n, int64_t r, const double* G, double* Q,
+                           double* eigvals, int32_t warm, void* stream);
+
+/*
+ * hicu_jl_compress - Q~ = Q P with P i.i.d. N(0, 1/p) (Algorithm 1 step 6;
+ * Theory, JL paragraph).
+ *   Q       : complex128 [(nr)][n] null basis as returned by hicu_nullspace
+ *   mode    : HICU_JL_NULLSPACE (P is nr x p) or HICU_JL_PROJECTOR (P is n x p,
+ *             Q~ = Q (Q^H P))
+ *   P       : optional float64 row-major P supplied by the caller (device);
+ *             if NULL, P is drawn on the device: element (row, col) is
+ *             z(seed, counter, row*p + col)/sqrt(p), z = Box-Muller on
+ *             SplitMix64 outputs 2m+1, 2m+2 with m = counter*2^32 + row*p + col
+ *   filters : complex64 [p][n] output bank
+ */
+hicu_status hicu_jl_compress(hicu_handle* h, int64_t n, int64_t nr, int32_t p, const double* Q,
+                             int32_t mode, const double* P, uint64_t seed, uint64_t counter,
+                             float* filters, void* stream);
+
+/*
+ * hicu_conv_null - R[:, k] = H(x) q~_k for the p filters (Theory: valid
+ * convolution of the k-space array with each annihilating filter; Algorithm 1
+ * step 7's inner term).
+ *   x       : complex64 k-space, filters: complex64 [p][n]
+ *   R       : complex64 [sz][sy][sx][p]
+ *   objective : optional device double, receives ||R||_F^2
+ */
+hicu_status hicu_conv_null(hicu_handle* h, const hicu_geom* geom, const hicu_region* region,
+                           const float* x, const float* filters, int32_t p, float* R,
+                           double* objective, int32_t prec, void* stream);
+
+/*
+ * hicu_conv_null_adjoint - g = (1 - M) o sum_k H^H(r_k) (Theory: the conjugate
+ * transpose of a valid convolution is itself a convolution; hard data
+ * consistency sets the gradient to zero at observed locations).
+ *   R     : complex64 [sz][sy][sx][p];  mask: nullable (NULL = no projection)
+ *   g     : complex64 [C][Nz][Ny][Nx]; every entry inside S is written,
+ *           entries outside S are left untouched
+ *   gnorm2: optional device double, receives ||g||^2
+ */
+hicu_status hicu_conv_null_adjoint(hicu_handle* h, const hicu_geom* geom,
+                                   const hicu_region* region, const float* R,
+                                   const float* filters, int32_t p, const uint8_t* mask,
+                                   float* g, double* gnorm2, int32_t prec, void* stream);
+
+/*
+ * hicu_gd_step_filters - one descent step for a fixed filter bank Q~ with
+ * exact line search (Algorithm 1 steps 7-8; Theory, ELS paragraph):
+ *   g = (1 - M) o sum_k H^H(H(y) q~_k),  D = sum_k ||H(g) q~_k||^2,
+ *   eta = ||g||^2 / D  (0 when g = 0 or D = 0),  y <- y - eta g.
+ *   y     : complex64 k-space, updated in place; entries with M != 0 and
+ *           entries outside S are never written
+ *   stats : optional device double[4] = {eta, ||H(y)Q~||^2 before the step,
+ *           ||g||^2, D}
+ */
+hicu_status hicu_gd_step_filters(hicu_handle* h, const hicu_geom* geom,
+                                 const hicu_region* region, float* y, const uint8_t* mask,
+                                 const float* filters, int32_t p, double* stats, int32_t prec,
+                                 void* stream);
+
+/*
+ * hicu_gd_step - JL compression (hicu_jl_compress) followed by
+ * hicu_gd_step_filters: Algorithm 1 steps 6-8 for one inner index j.
+ */
+hicu_status hicu_gd_step(hicu_handle* h, const hicu_geom* geom, const hicu_region* region,
+                         float* y, const uint8_t* mask, const double* Q, int64_t nr, int32_t p,
+                         int32_t jl_mode, uint64_t seed, uint64_t counter, const double* P,
+                         double* stats, int32_t prec, void* stream);
+
+/*
+ * hicu_reconstruct - Algorithm 1 with centre-out stages: for every outer
+ * iteration the Gram matrix and null space (hicu_gram, hicu_nullspace; region
+ * chosen by params->gram_on_current), then G^(i) calls of hicu_gd_step with
+ * JL counter = global step index (0, 1, 2, ...).
+ *   x0, mask, x_out may be HOST or DEVICE pointers (detected per pointer);
+ *   host buffers are staged through the handle's workspace with copies on
+ *   `stream`, and the call then returns after x_out is written.
+ *   log: optional host log; when given, the call synchronises the stream.
+ */
+hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, const float* x0,
+                             const uint8_t* mask, const hicu_params* params, float* x_out,
+                             hicu_log* log, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HICU_H_ */

@@ -1,0 +1,562 @@
+// C ABI of libhicu: handle, argument validation, workspace, and the drivers
+// that chain the kernels into the steps of Algorithm 1.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hicu_internal.cuh"
+
+namespace hicu {
+
+hicu_status set_error(hicu_handle* h, hicu_status s, const std::string& msg) {
+  if (h) h->last_error = msg;
+  return s;
+}
+
+hicu_status cuda_error(hicu_handle* h, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return HICU_OK;
+  return set_error(h, HICU_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+void* ws_get(hicu_handle* h, int slot, size_t bytes, hicu_status* st) {
+  Workspace& w = h->ws[slot];
+  if (bytes == 0) bytes = 16;
+  if (w.bytes >= bytes) return w.ptr;
+  if (w.ptr) {
+    cudaFree(w.ptr);  // synchronising; only happens while the workspace grows
+    w.ptr = nullptr;
+    w.bytes = 0;
+  }
+  void* p = nullptr;
+  const size_t want = (bytes + 255) / 256 * 256;
+  if (cudaMalloc(&p, want) != cudaSuccess) {
+    cudaGetLastError();
+    *st = set_error(h, HICU_ERR_ALLOC, "workspace allocation of " + std::to_string(want) + " bytes failed");
+    return nullptr;
+  }
+  w.ptr = p;
+  w.bytes = want;
+  return p;
+}
+
+static bool geom_ok(const hicu_geom* g) {
+  if (!g) return false;
+  if (g->ncoil < 1 || g->ncoil > 64) return false;
+  for (int a = 0; a < 3; ++a) {
+    if (g->dim[a] < 1 || g->dim[a] > (1 << 20)) return false;
+    if (g->k[a] < 1 || g->k[a] > 64) return false;
+    if (g->circular[a] > 1) return false;
+  }
+  if (g->mask_per_coil > 1) return false;
+  const long long N = g->dim[0] * g->dim[1] * g->dim[2] * (long long)g->ncoil;
+  return N < (1ll << 40);
+}
+
+hicu_status make_conv_geom(hicu_handle* h, const hicu_geom* geom, const hicu_region* r,
+                           ConvGeom* out) {
+  if (!geom || !r) return set_error(h, HICU_ERR_ARG, "null geometry or region");
+  if (!geom_ok(geom)) return set_error(h, HICU_ERR_SHAPE, "invalid geometry");
+  ConvGeom g;
+  g.C = geom->ncoil;
+  g.kx = geom->k[0];
+  g.ky = geom->k[1];
+  g.kz = geom->k[2];
+  g.K = g.kx * g.ky * g.kz;
+  g.n = g.C * g.K;
+  int ext[3], out_ext[3];
+  for (int a = 0; a < 3; ++a) {
+    if (r->off[a] < 0 || r->ext[a] < 1 || r->off[a] + r->ext[a] > geom->dim[a])
+      return set_error(h, HICU_ERR_SHAPE, "region does not fit inside the array");
+    ext[a] = (int)r->ext[a];
+    if (geom->circular[a]) {
+      out_ext[a] = ext[a];
+    } else {
+      if (ext[a] < geom->k[a]) return set_error(h, HICU_ERR_SHAPE, "region smaller than the kernel");
+      out_ext[a] = ext[a] - geom->k[a] + 1;
+    }
+  }
+  g.ex = ext[0];
+  g.ey = ext[1];
+  g.ez = ext[2];
+  g.sx = out_ext[0];
+  g.sy = out_ext[1];
+  g.sz = out_ext[2];
+  g.cx = geom->circular[0];
+  g.cy = geom->circular[1];
+  g.cz = geom->circular[2];
+  g.s = (long long)g.sx * g.sy * g.sz;
+  if (g.sy > 65535 * 4 || g.sz > 65535 || g.ez > 65535)
+    return set_error(h, HICU_ERR_UNSUPPORTED, "region extent above launch limits");
+  *out = g;
+  return HICU_OK;
+}
+
+KView full_view(const hicu_geom* g, const hicu_region* r, float* base) {
+  KView v;
+  v.p = reinterpret_cast<float2*>(base);
+  v.sy = g->dim[0];
+  v.sz = g->dim[0] * g->dim[1];
+  v.sc = v.sz * g->dim[2];
+  v.ox = (int)r->off[0];
+  v.oy = (int)r->off[1];
+  v.oz = (int)r->off[2];
+  return v;
+}
+
+static KView region_view(const ConvGeom& g, float2* base) {
+  KView v;
+  v.p = base;
+  v.sy = g.ex;
+  v.sz = (long long)g.ex * g.ey;
+  v.sc = v.sz * g.ez;
+  v.ox = v.oy = v.oz = 0;
+  return v;
+}
+
+MView mask_view(const hicu_geom* g, const hicu_region* r, const uint8_t* mask) {
+  MView m;
+  m.p = mask;
+  m.sy = g->dim[0];
+  m.sz = g->dim[0] * g->dim[1];
+  m.sc = g->mask_per_coil ? m.sz * g->dim[2] : 0;
+  m.ox = (int)r->off[0];
+  m.oy = (int)r->off[1];
+  m.oz = (int)r->off[2];
+  return m;
+}
+
+}  // namespace hicu
+
+using namespace hicu;
+
+// --------------------------------------------------------------- handle
+
+extern "C" hicu_status hicu_create(hicu_handle** out) {
+  if (!out) return HICU_ERR_ARG;
+  *out = nullptr;
+  hicu_handle* h = new (std::nothrow) hicu_handle();
+  if (!h) return HICU_ERR_ALLOC;
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return HICU_ERR_CUDA;
+  }
+  if (cudaMalloc(&h->dev_err, 64) != cudaSuccess || cudaMalloc(&h->dev_sync, 64) != cudaSuccess ||
+      cudaMemset(h->dev_err, 0, 64) != cudaSuccess || cudaMemset(h->dev_sync, 0, 64) != cudaSuccess) {
+    cudaGetLastError();
+    if (h->dev_err) cudaFree(h->dev_err);
+    if (h->dev_sync) cudaFree(h->dev_sync);
+    delete h;
+    return HICU_ERR_ALLOC;
+  }
+  *out = h;
+  return HICU_OK;
+}
+
+extern "C" hicu_status hicu_destroy(hicu_handle* h) {
+  if (!h) return HICU_ERR_ARG;
+  cudaDeviceSynchronize();
+  for (auto& w : h->ws)
+    if (w.ptr) cudaFree(w.ptr);
+  cudaFree(h->dev_err);
+  cudaFree(h->dev_sync);
+  delete h;
+  return HICU_OK;
+}
+
+extern "C" const char* hicu_last_error(const hicu_handle* h) { return h ? h->last_error.c_str() : ""; }
+
+extern "C" const char* hicu_status_string(hicu_status s) {
+  switch (s) {
+    case HICU_OK: return "HICU_OK";
+    case HICU_ERR_ARG: return "HICU_ERR_ARG";
+    case HICU_ERR_SHAPE: return "HICU_ERR_SHAPE";
+    case HICU_ERR_RANK: return "HICU_ERR_RANK";
+    case HICU_ERR_ALLOC: return "HICU_ERR_ALLOC";
+    case HICU_ERR_CUDA: return "HICU_ERR_CUDA";
+    case HICU_ERR_TIMEOUT: return "HICU_ERR_TIMEOUT";
+    case HICU_ERR_NUMERIC: return "HICU_ERR_NUMERIC";
+    case HICU_ERR_UNSUPPORTED: return "HICU_ERR_UNSUPPORTED";
+  }
+  return "HICU_ERR_UNKNOWN";
+}
+
+extern "C" hicu_status hicu_check(hicu_handle* h, void* stream) {
+  if (!h) return HICU_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(h, e, "stream");
+  int err = 0;
+  e = cudaMemcpy(&err, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_error(h, e, "error word");
+  if (err) {
+    cudaMemset(h->dev_err, 0, sizeof(int));
+    return set_error(h, (hicu_status)err, "device-side error recorded");
+  }
+  return HICU_OK;
+}
+
+extern "C" int64_t hicu_filter_length(const hicu_geom* geom) {
+  if (!geom_ok(geom)) return -1;
+  return (int64_t)geom->ncoil * geom->k[0] * geom->k[1] * geom->k[2];
+}
+
+extern "C" int64_t hicu_num_outputs(const hicu_geom* geom, const hicu_region* region) {
+  ConvGeom g;
+  if (make_conv_geom(nullptr, geom, region, &g) != HICU_OK) return -1;
+  return g.s;
+}
+
+// ------------------------------------------------------------ hot path
+
+extern "C" hicu_status hicu_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* region,
+                                 const float* x, double* G, void* stream) {
+  if (!h) return HICU_ERR_ARG;
+  if (!x || !G) return set_error(h, HICU_ERR_ARG, "gram: null pointer");
+  return run_gram(h, geom, region, x, G, (cudaStream_t)stream);
+}
+
+extern "C" hicu_status hicu_nullspace(hicu_handle* h, int64_t n, int64_t r, const double* G,
+                                      double* Q, double* eigvals, int32_t warm, void* stream) {
+  if (!h) return HICU_ERR_ARG;
+  if (!G || !Q) return set_error(h, HICU_ERR_ARG, "nullspace: null pointer");
+  return run_nullspace(h, n, r, G, Q, eigvals, warm, (cudaStream_t)stream);
+}
+
+extern "C" hicu_status hicu_jl_compress(hicu_handle* h, int64_t n, int64_t nr, int32_t p,
+                                        const double* Q, int32_t mode, const double* P,
+                                        uint64_t seed, uint64_t counter, float* filters,
+                                        void* stream) {
+  if (!h) return HICU_ERR_ARG;
+  if (!Q || !filters) return set_error(h, HICU_ERR_ARG, "jl_compress: null pointer");
+  if (mode != HICU_JL_NULLSPACE && mode != HICU_JL_PROJECTOR)
+    return set_error(h, HICU_ERR_ARG, "jl_compress: unknown mode");
+  if (n < 2 || nr < 1 || nr >= n) return set_error(h, HICU_ERR_RANK, "jl_compress: need 1 <= n-r < n");
+  if (p < 1 || p > 4096) return set_error(h, HICU_ERR_RANK, "jl_compress: p out of range");
+  return launch_jl(h, n, nr, p, Q, mode, P, seed, counter, filters, (cudaStream_t)stream);
+}
+
+namespace {
+
+struct StepBuffers {
+  float2* fT;
+  float2* fA;
+  int Ppad, Cpad;
+};
+
+hicu_status prep_filters(hicu_handle* h, const ConvGeom& g, const float* bank, int p, bool conv,
+                         bool adj, StepBuffers* b, cudaStream_t st) {
+  hicu_status s = HICU_OK;
+  b->Ppad = conv_ppad(p);
+  b->Cpad = adj_cpad(g.C);
+  b->fT = conv ? (float2*)ws_get(h, WS_FT, sizeof(float2) * (size_t)g.n * b->Ppad, &s) : nullptr;
+  if (s) return s;
+  b->fA = adj ? (float2*)ws_get(h, WS_FA, sizeof(float2) * (size_t)g.K * b->Ppad * b->Cpad, &s) : nullptr;
+  if (s) return s;
+  return launch_prep_filters(h, g, (const float2*)bank, p, b->fT, b->Ppad, b->fA, b->Cpad, st);
+}
+
+hicu_status check_prec(hicu_handle* h, int32_t prec) {
+  if (prec == HICU_FP32) return HICU_OK;
+  if (prec == HICU_SPLIT_BF16) return set_error(h, HICU_ERR_UNSUPPORTED, "split-bf16 path not built in");
+  return set_error(h, HICU_ERR_ARG, "unknown precision");
+}
+
+}  // namespace
+
+extern "C" hicu_status hicu_conv_null(hicu_handle* h, const hicu_geom* geom, const hicu_region* region,
+                                      const float* x, const float* filters, int32_t p, float* R,
+                                      double* objective, int32_t prec, void* stream) {
+  if (!h) return HICU_ERR_ARG;
+  if (!x || !filters || (!R && !objective)) return set_error(h, HICU_ERR_ARG, "conv_null: null pointer");
+  if (p < 1 || p > 4096) return set_error(h, HICU_ERR_RANK, "conv_null: p out of range");
+  hicu_status s = check_prec(h, prec);
+  if (s) return s;
+  ConvGeom g;
+  s = make_conv_geom(h, geom, region, &g);
+  if (s) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  StepBuffers b;
+  s = prep_filters(h, g, filters, p, true, false, &b, st);
+  if (s) return s;
+  int nb = 0;
+  launch_conv_fp32(h, g, full_view(geom, region, const_cast<float*>(x)), b.fT, p, b.Ppad, nullptr,
+                   nullptr, &nb, st);
+  double* part = (double*)ws_get(h, WS_PART, sizeof(double) * nb, &s);
+  if (s) return s;
+  s = launch_conv_fp32(h, g, full_view(geom, region, const_cast<float*>(x)), b.fT, p, b.Ppad,
+                       (float2*)R, part, &nb, st);
+  if (s) return s;
+  if (objective) return launch_sum_partials(part, nb, objective, st);
+  return HICU_OK;
+}
+
+extern "C" hicu_status hicu_conv_null_adjoint(hicu_handle* h, const hicu_geom* geom,
+                                              const hicu_region* region, const float* R,
+                                              const float* filters, int32_t p, const uint8_t* mask,
+                                              float* gout, double* gnorm2, int32_t prec,
+                                              void* stream) {
+  if (!h) return HICU_ERR_ARG;
+  if (!R || !filters || !gout) return set_error(h, HICU_ERR_ARG, "conv_null_adjoint: null pointer");
+  if (p < 1 || p > 4096) return set_error(h, HICU_ERR_RANK, "conv_null_adjoint: p out of range");
+  hicu_status s = check_prec(h, prec);
+  if (s) return s;
+  ConvGeom g;
+  s = make_conv_geom(h, geom, region, &g);
+  if (s) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  StepBuffers b;
+  s = prep_filters(h, g, filters, p, false, true, &b, st);
+  if (s) return s;
+  int nb = 0;
+  KView gv = full_view(geom, region, gout);
+  MView mv = mask_view(geom, region, mask);
+  launch_adjoint_fp32(h, g, (const float2*)R, b.fA, p, b.Ppad, b.Cpad, mv, gv, nullptr, &nb, st);
+  double* part = (double*)ws_get(h, WS_PART, sizeof(double) * nb, &s);
+  if (s) return s;
+  s = launch_adjoint_fp32(h, g, (const float2*)R, b.fA, p, b.Ppad, b.Cpad, mv, gv, part, &nb, st);
+  if (s) return s;
+  if (gnorm2) return launch_sum_partials(part, nb, gnorm2, st);
+  return HICU_OK;
+}
+
+namespace hicu {
+
+// One descent step for a fixed bank (Algorithm 1 steps 7-8).
+hicu_status gd_step_filters(hicu_handle* h, const hicu_geom* geom, const hicu_region* region, float* y,
+                            const uint8_t* mask, const float* filters, int32_t p, double* stats,
+                            int32_t prec, cudaStream_t st) {
+  hicu_status s = check_prec(h, prec);
+  if (s) return s;
+  ConvGeom g;
+  s = make_conv_geom(h, geom, region, &g);
+  if (s) return s;
+  StepBuffers b;
+  s = prep_filters(h, g, filters, p, true, true, &b, st);
+  if (s) return s;
+  float2* R = (float2*)ws_get(h, WS_R, sizeof(float2) * (size_t)g.s * p, &s);
+  if (s) return s;
+  float2* gb = (float2*)ws_get(h, WS_G, sizeof(float2) * (size_t)g.C * g.ex * g.ey * g.ez, &s);
+  if (s) return s;
+  double* st4 = stats;
+  if (!st4) {
+    st4 = (double*)ws_get(h, WS_STATS, sizeof(double) * 8, &s);
+    if (s) return s;
+  }
+  const KView yv = full_view(geom, region, y);
+  const KView gview = region_view(g, gb);
+  const MView mv = mask_view(geom, region, mask);
+  int n1 = 0, n2 = 0, n3 = 0;
+  launch_conv_fp32(h, g, yv, b.fT, p, b.Ppad, nullptr, nullptr, &n1, st);
+  launch_adjoint_fp32(h, g, R, b.fA, p, b.Ppad, b.Cpad, mv, gview, nullptr, &n2, st);
+  n3 = n1;
+  double* part = (double*)ws_get(h, WS_PART, sizeof(double) * (n1 + n2 + n3), &s);
+  if (s) return s;
+  s = launch_conv_fp32(h, g, yv, b.fT, p, b.Ppad, R, part, &n1, st);
+  if (s) return s;
+  s = launch_adjoint_fp32(h, g, R, b.fA, p, b.Ppad, b.Cpad, mv, gview, part + n1, &n2, st);
+  if (s) return s;
+  s = launch_conv_fp32(h, g, gview, b.fT, p, b.Ppad, nullptr, part + n1 + n2, &n3, st);
+  if (s) return s;
+  s = launch_finalize_step(part, n1, n2, n3, st4, st);
+  if (s) return cuda_error(h, cudaGetLastError(), "finalize");
+  s = launch_update(g, yv, gview, mv, st4, st);
+  if (s) return cuda_error(h, cudaGetLastError(), "update");
+  return HICU_OK;
+}
+
+}  // namespace hicu
+
+extern "C" hicu_status hicu_gd_step_filters(hicu_handle* h, const hicu_geom* geom,
+                                            const hicu_region* region, float* y, const uint8_t* mask,
+                                            const float* filters, int32_t p, double* stats,
+                                            int32_t prec, void* stream) {
+  if (!h) return HICU_ERR_ARG;
+  if (!y || !filters) return set_error(h, HICU_ERR_ARG, "gd_step_filters: null pointer");
+  if (p < 1 || p > 4096) return set_error(h, HICU_ERR_RANK, "gd_step_filters: p out of range");
+  return gd_step_filters(h, geom, region, y, mask, filters, p, stats, prec, (cudaStream_t)stream);
+}
+
+extern "C" hicu_status hicu_gd_step(hicu_handle* h, const hicu_geom* geom, const hicu_region* region,
+                                    float* y, const uint8_t* mask, const double* Q, int64_t nr,
+                                    int32_t p, int32_t jl_mode, uint64_t seed, uint64_t counter,
+                                    const double* P, double* stats, int32_t prec, void* stream) {
+  if (!h) return HICU_ERR_ARG;
+  if (!y || !Q) return set_error(h, HICU_ERR_ARG, "gd_step: null pointer");
+  const int64_t n = hicu_filter_length(geom);
+  if (n < 0) return set_error(h, HICU_ERR_SHAPE, "gd_step: invalid geometry");
+  if (nr < 1 || nr >= n) return set_error(h, HICU_ERR_RANK, "gd_step: need 1 <= n-r < n");
+  if (p < 1 || p > 4096) return set_error(h, HICU_ERR_RANK, "gd_step: p out of range");
+  if (jl_mode == HICU_JL_NULLSPACE && p > nr)
+    return set_error(h, HICU_ERR_RANK, "gd_step: p must not exceed n-r");
+  hicu_status s = HICU_OK;
+  float* bank = (float*)ws_get(h, WS_BANK, sizeof(float2) * (size_t)p * n, &s);
+  if (s) return s;
+  s = hicu_jl_compress(h, n, nr, p, Q, jl_mode, P, seed, counter, bank, stream);
+  if (s) return s;
+  return gd_step_filters(h, geom, region, y, mask, bank, p, stats, prec, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------- reconstruct
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// time-averaged start along z (2D+t): unsampled (c, y, x, t) take the mean of the
+// sampled frames at (c, y, x), or zero if none was sampled
+__global__ void time_average_kernel(int C, int nx, int ny, int nz, float2* x, const uint8_t* m,
+                                    long long msc) {
+  const long long tot = (long long)C * ny * nx;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(i % nx);
+    const int iy = (int)((i / nx) % ny);
+    const int c = (int)(i / ((long long)nx * ny));
+    const long long plane = (long long)nx * ny;
+    double sr = 0.0, si = 0.0;
+    int cnt = 0;
+    for (int z = 0; z < nz; ++z) {
+      const long long o = z * plane + (long long)iy * nx + ix;
+      if (m[c * msc + o]) {
+        const float2 v = x[c * plane * nz + o];
+        sr += v.x;
+        si += v.y;
+        ++cnt;
+      }
+    }
+    const float2 avg = cnt ? make_float2((float)(sr / cnt), (float)(si / cnt)) : make_float2(0.f, 0.f);
+    for (int z = 0; z < nz; ++z) {
+      const long long o = z * plane + (long long)iy * nx + ix;
+      if (!m[c * msc + o]) x[c * plane * nz + o] = avg;
+    }
+  }
+}
+
+__global__ void tail_sum_kernel(const double* eig, int nr, double* out) {
+  __shared__ double sh[8];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nr; i += 256) s += eig[i];
+  s = block_sum<256>(s, sh);
+  if (threadIdx.x == 0) *out = s;
+}
+
+}  // namespace
+
+extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, const float* x0,
+                                        const uint8_t* mask, const hicu_params* prm, float* x_out,
+                                        hicu_log* log, void* stream) {
+  if (!h) return HICU_ERR_ARG;
+  if (!geom || !x0 || !mask || !prm || !x_out) return set_error(h, HICU_ERR_ARG, "reconstruct: null pointer");
+  if (!geom_ok(geom)) return set_error(h, HICU_ERR_SHAPE, "reconstruct: invalid geometry");
+  if (prm->nstages < 1 || !prm->stages) return set_error(h, HICU_ERR_ARG, "reconstruct: no stages");
+  const int64_t n = hicu_filter_length(geom);
+  const int64_t r = prm->rank;
+  if (r < 1 || r >= n) return set_error(h, HICU_ERR_RANK, "reconstruct: rank must satisfy 0 < r < n");
+  const int64_t nr = n - r;
+  if (prm->jl != HICU_JL_NULLSPACE && prm->jl != HICU_JL_PROJECTOR)
+    return set_error(h, HICU_ERR_ARG, "reconstruct: unknown JL mode");
+  if (prm->init != 0 && prm->init != 1) return set_error(h, HICU_ERR_ARG, "reconstruct: unknown init");
+  hicu_status s = check_prec(h, prm->prec);
+  if (s) return s;
+  long long total_iters = 0, total_steps = 0;
+  for (int i = 0; i < prm->nstages; ++i) {
+    const hicu_stage& stg = prm->stages[i];
+    ConvGeom g;
+    s = make_conv_geom(h, geom, &stg.region, &g);
+    if (s) return s;
+    if (stg.iters < 0 || stg.gd_steps < 0) return set_error(h, HICU_ERR_ARG, "reconstruct: negative count");
+    if (stg.p < 1 || (prm->jl == HICU_JL_NULLSPACE && stg.p > nr))
+      return set_error(h, HICU_ERR_RANK, "reconstruct: p must be in [1, n-r]");
+    total_iters += stg.iters;
+    total_steps += (long long)stg.iters * stg.gd_steps;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long N = geom->dim[0] * geom->dim[1] * geom->dim[2] * (long long)geom->ncoil;
+  const long long NM = geom->dim[0] * geom->dim[1] * geom->dim[2] * (geom->mask_per_coil ? geom->ncoil : 1);
+  const bool out_dev = is_device_ptr(x_out);
+  const bool in_dev = is_device_ptr(x0);
+  const bool m_dev = is_device_ptr(mask);
+  float* y = x_out;
+  if (!out_dev) {
+    y = (float*)ws_get(h, WS_REC_X, sizeof(float2) * N, &s);
+    if (s) return s;
+  }
+  const uint8_t* m = mask;
+  if (!m_dev) {
+    uint8_t* mm = (uint8_t*)ws_get(h, WS_REC_M, NM, &s);
+    if (s) return s;
+    if (cudaMemcpyAsync(mm, mask, NM, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return cuda_error(h, cudaGetLastError(), "reconstruct: mask upload");
+    m = mm;
+  }
+  if (cudaMemcpyAsync(y, x0, sizeof(float2) * N, in_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                      st) != cudaSuccess)
+    return cuda_error(h, cudaGetLastError(), "reconstruct: input copy");
+  double* G = (double*)ws_get(h, WS_REC_G, sizeof(double2) * n * n, &s);
+  if (s) return s;
+  double* Q = (double*)ws_get(h, WS_REC_Q, sizeof(double2) * n * nr, &s);
+  if (s) return s;
+  double* eig = (double*)ws_get(h, WS_REC_EIG, sizeof(double) * n, &s);
+  if (s) return s;
+  double* dlog = (double*)ws_get(h, WS_REC_LOG, sizeof(double) * (total_iters + 1), &s);
+  if (s) return s;
+  double* dstats = (double*)ws_get(h, WS_REC_STATS, sizeof(double) * 4 * (total_steps + 1), &s);
+  if (s) return s;
+  if (prm->init == 1) {
+    time_average_kernel<<<1024, 256, 0, st>>>(geom->ncoil, (int)geom->dim[0], (int)geom->dim[1],
+                                             (int)geom->dim[2], (float2*)y, m,
+                                             geom->mask_per_coil ? geom->dim[0] * geom->dim[1] * geom->dim[2] : 0);
+  }
+  uint64_t counter = 0;
+  long long it = 0;
+  hicu_region prev = prm->stages[0].region;
+  for (int si = 0; si < prm->nstages; ++si) {
+    const hicu_stage& stg = prm->stages[si];
+    for (int i = 0; i < stg.iters; ++i) {
+      const hicu_region& greg = prm->gram_on_current ? stg.region : prev;
+      s = run_gram(h, geom, &greg, y, G, st);
+      if (s) return s;
+      s = run_nullspace(h, n, r, G, Q, eig, it > 0 ? 1 : 0, st);
+      if (s) return s;
+      tail_sum_kernel<<<1, 256, 0, st>>>(eig, (int)nr, dlog + it);
+      for (int j = 0; j < stg.gd_steps; ++j) {
+        s = hicu_gd_step(h, geom, &stg.region, y, m, Q, nr, stg.p, prm->jl, prm->seed, counter, nullptr,
+                         dstats + 4 * counter, prm->prec, stream);
+        if (s) return s;
+        ++counter;
+      }
+      ++it;
+      prev = stg.region;
+    }
+  }
+  if (!out_dev) {
+    if (cudaMemcpyAsync(x_out, y, sizeof(float2) * N, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      return cuda_error(h, cudaGetLastError(), "reconstruct: output copy");
+  }
+  if (log) {
+    std::vector<double> hs(4 * (total_steps + 1));
+    if (log->J &&
+        cudaMemcpyAsync(log->J, dlog, sizeof(double) * total_iters, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      return cuda_error(h, cudaGetLastError(), "reconstruct: log copy");
+    if (cudaMemcpyAsync(hs.data(), dstats, sizeof(double) * 4 * total_steps, cudaMemcpyDeviceToHost, st) !=
+        cudaSuccess)
+      return cuda_error(h, cudaGetLastError(), "reconstruct: log copy");
+    if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_error(h, cudaGetLastError(), "reconstruct: sync");
+    for (long long k = 0; k < total_steps; ++k) {
+      if (log->eta) log->eta[k] = hs[4 * k];
+      if (log->objective) log->objective[k] = hs[4 * k + 1];
+    }
+  }
+  if (!out_dev || log) return hicu_check(h, stream);
+  return cuda_error(h, cudaGetLastError(), "reconstruct");
+}

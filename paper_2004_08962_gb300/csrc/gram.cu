@@ -1,0 +1,294 @@
+// Gram matrix G = H(x)^H H(x) of the multi-level Hankel matrix (Eq. 1; the
+// Discussion names SVD of this Gram matrix as the alternative to rSVD),
+// computed as multi-coil cross-correlation without forming H.
+//
+// Entry ((c1,d1),(c2,d2)) = sum_{u in W(d1)} conj(x_c1[u]) x_c2[u + delta],
+// delta = d2 - d1, W(d) = {p + d : p a valid output}.  For one (c1, c2, delta)
+// all windows W(d) are unions of the same few "cells": along each valid axis
+// the cut points {0..k-1} and {L..L+k-1} (L = ext - k + 1) split the region
+// into at most 2k-1 intervals; a circular axis is one cell.  So
+//   1. gram_cells: one CTA per (task = (c1, c2, delta), row piece) forms the
+//      products once per region point and sums them per cell, and
+//   2. gram_assemble: each G entry adds the cells of its window.
+// Hermitian symmetry halves the tasks: (c1 < c2) or (c1 == c2, delta >= 0).
+//
+// Accuracy: products of FP32 inputs are formed exactly (fmaf error term) and
+// accumulated in double-word (float pair) arithmetic per thread, then summed
+// across threads and CTAs in FP64 in a fixed order (deterministic).
+#include <algorithm>
+#include <vector>
+
+#include "hicu_internal.cuh"
+
+namespace hicu {
+
+constexpr int GMAXCUT = 34;
+constexpr int GMAXPIECE = 64;
+constexpr int GXSLOT = 4;
+
+struct GramParams {
+  ConvGeom g;
+  KView x;
+  int ncx, ncy, ncz;
+  int cutx[GMAXCUT], cuty[GMAXCUT], cutz[GMAXCUT];
+  int npy, npz;
+  int py0[GMAXPIECE], py1[GMAXPIECE], pyc[GMAXPIECE];
+  int pz0[GMAXPIECE], pz1[GMAXPIECE], pzc[GMAXPIECE];
+  int lx, ly, lz, nl, nlh, center;
+};
+
+__device__ __forceinline__ void dd_acc(float a, float b, float& hi, float& lo) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);  // exact: a*b = p + e
+  const float s = __fadd_rn(hi, p);     // two-sum(hi, p) = s + err
+  const float bb = __fadd_rn(s, -hi);
+  const float err = __fadd_rn(__fadd_rn(hi, -__fadd_rn(s, -bb)), __fadd_rn(p, -bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ void dd_renorm(float& hi, float& lo) {
+  const float s = __fadd_rn(hi, lo);
+  lo = __fadd_rn(lo, -__fadd_rn(s, hi));
+  hi = s;
+}
+
+__host__ __device__ inline void decode_task(long long t, int C, int nl, int nlh, int center, int& c1,
+                                            int& c2, int& l) {
+  for (c1 = 0; c1 < C; ++c1) {
+    const long long sz = nlh + (long long)(C - 1 - c1) * nl;
+    if (t < sz) break;
+    t -= sz;
+  }
+  if (t < nlh) {
+    c2 = c1;
+    l = center + (int)t;
+  } else {
+    t -= nlh;
+    c2 = c1 + 1 + (int)(t / nl);
+    l = (int)(t % nl);
+  }
+}
+
+__host__ __device__ inline long long task_index(int c1, int c2, int l, int C, int nl, int nlh,
+                                                int center) {
+  const long long base =
+      (long long)c1 * nlh + (long long)nl * ((long long)c1 * (C - 1) - (long long)c1 * (c1 - 1) / 2);
+  if (c1 == c2) return base + (l - center);
+  return base + nlh + (long long)(c2 - c1 - 1) * nl + l;
+}
+
+__global__ void __launch_bounds__(256) gram_cells_kernel(GramParams P, double2* __restrict__ part) {
+  __shared__ double2 vals[256 * GXSLOT];
+  const ConvGeom& g = P.g;
+  const long long task = blockIdx.x;
+  const int piece = blockIdx.y;
+  const int pyi = piece % P.npy, pzi = piece / P.npy;
+  int c1, c2, l;
+  decode_task(task, g.C, P.nl, P.nlh, P.center, c1, c2, l);
+  const int ddx = l % P.lx - (g.kx - 1);
+  const int ddy = (l / P.lx) % P.ly - (g.ky - 1);
+  const int ddz = l / (P.lx * P.ly) - (g.kz - 1);
+  const float2* xa = P.x.p + (long long)c1 * P.x.sc;
+  const float2* xb = P.x.p + (long long)c2 * P.x.sc;
+  const int nt = blockDim.x;
+
+  float rh[GXSLOT], rl[GXSLOT], ih[GXSLOT], il[GXSLOT];
+  int bx[GXSLOT];
+  bool bok[GXSLOT];
+#pragma unroll
+  for (int j = 0; j < GXSLOT; ++j) {
+    rh[j] = rl[j] = ih[j] = il[j] = 0.f;
+    const int xx = threadIdx.x + j * nt;
+    int vx = xx + ddx;
+    bool ok = xx < g.ex;
+    if (g.cx) vx = wrap(vx, g.ex); else ok = ok && vx >= 0 && vx < g.ex;
+    bx[j] = vx;
+    bok[j] = ok;
+  }
+  for (int z = P.pz0[pzi]; z < P.pz1[pzi]; ++z) {
+    int vz = z + ddz;
+    if (g.cz) vz = wrap(vz, g.ez);
+    else if (vz < 0 || vz >= g.ez) continue;
+    for (int y = P.py0[pyi]; y < P.py1[pyi]; ++y) {
+      int vy = y + ddy;
+      if (g.cy) vy = wrap(vy, g.ey);
+      else if (vy < 0 || vy >= g.ey) continue;
+      const float2* arow = xa + (long long)(P.x.oz + z) * P.x.sz + (long long)(P.x.oy + y) * P.x.sy + P.x.ox;
+      const float2* brow = xb + (long long)(P.x.oz + vz) * P.x.sz + (long long)(P.x.oy + vy) * P.x.sy + P.x.ox;
+#pragma unroll
+      for (int j = 0; j < GXSLOT; ++j) {
+        if (bok[j]) {
+          const float2 a = arow[threadIdx.x + j * nt];
+          const float2 b = brow[bx[j]];
+          // conj(a) * b = (ar br + ai bi) + i (ar bi - ai br)
+          dd_acc(a.x, b.x, rh[j], rl[j]);
+          dd_acc(a.y, b.y, rh[j], rl[j]);
+          dd_acc(a.x, b.y, ih[j], il[j]);
+          dd_acc(-a.y, b.x, ih[j], il[j]);
+          dd_renorm(rh[j], rl[j]);
+          dd_renorm(ih[j], il[j]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < GXSLOT; ++j) {
+    const int xx = threadIdx.x + j * nt;
+    if (xx < g.ex)
+      vals[xx] = make_double2((double)rh[j] + (double)rl[j], (double)ih[j] + (double)il[j]);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = nt >> 5;
+  for (int ci = warp; ci < P.ncx; ci += nw) {
+    double sr = 0.0, si = 0.0;
+    for (int xx = P.cutx[ci] + lane; xx < P.cutx[ci + 1]; xx += 32) {
+      // zero-product cells (shifted sample outside S) were never written: skip them
+      const int vx = xx + ddx;
+      if (!g.cx && (vx < 0 || vx >= g.ex)) continue;
+      sr += vals[xx].x;
+      si += vals[xx].y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_down_sync(0xffffffffu, sr, o);
+      si += __shfl_down_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0)
+      part[(task * (P.npy * P.npz) + piece) * P.ncx + ci] = make_double2(sr, si);
+  }
+}
+
+__device__ __forceinline__ int cut_index(const int* cuts, int ncut, int v) {
+  for (int i = 0; i < ncut; ++i)
+    if (cuts[i] == v) return i;
+  return -1;
+}
+
+__global__ void gram_assemble_kernel(GramParams P, const double2* __restrict__ part,
+                                     double2* __restrict__ G) {
+  const ConvGeom& g = P.g;
+  const int n = g.n;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * n) return;
+  const int a = (int)(idx / n), b = (int)(idx % n);
+  const int K = g.K;
+  const int c1 = a / K, k1 = a % K, c2 = b / K, k2 = b % K;
+  const int d1x = k1 % g.kx, d1y = (k1 / g.kx) % g.ky, d1z = k1 / (g.kx * g.ky);
+  const int d2x = k2 % g.kx, d2y = (k2 / g.kx) % g.ky, d2z = k2 / (g.kx * g.ky);
+  const int l = ((d2z - d1z + g.kz - 1) * P.ly + (d2y - d1y + g.ky - 1)) * P.lx + (d2x - d1x + g.kx - 1);
+  const bool direct = (c1 < c2) || (c1 == c2 && l >= P.center);
+  int tc1, tc2, tl, wx, wy, wz;
+  if (direct) {
+    tc1 = c1; tc2 = c2; tl = l; wx = d1x; wy = d1y; wz = d1z;
+  } else {
+    tc1 = c2; tc2 = c1; tl = P.nl - 1 - l; wx = d2x; wy = d2y; wz = d2z;
+  }
+  const long long task = task_index(tc1, tc2, tl, g.C, P.nl, P.nlh, P.center);
+  int cx0 = 0, cx1 = 1, cy0 = 0, cy1 = 1, cz0 = 0, cz1 = 1;
+  if (!g.cx) {
+    cx0 = cut_index(P.cutx, P.ncx + 1, wx);
+    cx1 = cut_index(P.cutx, P.ncx + 1, wx + g.ex - g.kx + 1);
+  }
+  if (!g.cy) {
+    cy0 = cut_index(P.cuty, P.ncy + 1, wy);
+    cy1 = cut_index(P.cuty, P.ncy + 1, wy + g.ey - g.ky + 1);
+  }
+  if (!g.cz) {
+    cz0 = cut_index(P.cutz, P.ncz + 1, wz);
+    cz1 = cut_index(P.cutz, P.ncz + 1, wz + g.ez - g.kz + 1);
+  }
+  if (cx0 < 0 || cx1 < 0 || cy0 < 0 || cy1 < 0 || cz0 < 0 || cz1 < 0) {
+    G[idx] = make_double2(nan(""), nan(""));  // unreachable: window ends are always cut points
+    return;
+  }
+  double sr = 0.0, si = 0.0;
+  const int npieces = P.npy * P.npz;
+  for (int pz = 0; pz < P.npz; ++pz) {
+    if (P.pzc[pz] < cz0 || P.pzc[pz] >= cz1) continue;
+    for (int py = 0; py < P.npy; ++py) {
+      if (P.pyc[py] < cy0 || P.pyc[py] >= cy1) continue;
+      const double2* src = part + (task * npieces + (pz * P.npy + py)) * P.ncx;
+      for (int cx = cx0; cx < cx1; ++cx) {
+        sr += src[cx].x;
+        si += src[cx].y;
+      }
+    }
+  }
+  G[idx] = direct ? make_double2(sr, si) : make_double2(sr, -si);
+}
+
+// ------------------------------------------------------------------ host
+
+static int build_cuts(int ext, int k, bool circular, int* cuts) {
+  std::vector<int> v;
+  if (circular) {
+    v = {0, ext};
+  } else {
+    const int L = ext - k + 1;
+    for (int i = 0; i < k; ++i) v.push_back(i);
+    for (int i = 0; i < k; ++i) v.push_back(L + i);
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+  }
+  for (size_t i = 0; i < v.size(); ++i) cuts[i] = v[i];
+  return (int)v.size() - 1;  // number of cells
+}
+
+static int build_pieces(const int* cuts, int ncell, int* p0, int* p1, int* pc) {
+  int total = cuts[ncell] - cuts[0];
+  for (int len = std::max(8, (total + 31) / 32);; len *= 2) {
+    int np = 0;
+    bool fit = true;
+    for (int c = 0; c < ncell && fit; ++c) {
+      for (int s = cuts[c]; s < cuts[c + 1]; s += len) {
+        if (np >= GMAXPIECE) { fit = false; break; }
+        p0[np] = s;
+        p1[np] = std::min(s + len, cuts[c + 1]);
+        pc[np] = c;
+        ++np;
+      }
+    }
+    if (fit) return np;
+  }
+}
+
+hicu_status run_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* reg, const float* x,
+                     double* G, cudaStream_t st) {
+  ConvGeom g;
+  hicu_status s = make_conv_geom(h, geom, reg, &g);
+  if (s) return s;
+  if (g.kx > 16 || g.ky > 16 || g.kz > 16)
+    return set_error(h, HICU_ERR_UNSUPPORTED, "gram: kernel extent above 16");
+  if (g.ex > 256 * GXSLOT) return set_error(h, HICU_ERR_UNSUPPORTED, "gram: region x extent above 1024");
+  GramParams P;
+  P.g = g;
+  P.x = full_view(geom, reg, const_cast<float*>(x));
+  P.ncx = build_cuts(g.ex, g.kx, g.cx, P.cutx);
+  P.ncy = build_cuts(g.ey, g.ky, g.cy, P.cuty);
+  P.ncz = build_cuts(g.ez, g.kz, g.cz, P.cutz);
+  P.npy = build_pieces(P.cuty, P.ncy, P.py0, P.py1, P.pyc);
+  P.npz = build_pieces(P.cutz, P.ncz, P.pz0, P.pz1, P.pzc);
+  P.lx = 2 * g.kx - 1;
+  P.ly = 2 * g.ky - 1;
+  P.lz = 2 * g.kz - 1;
+  P.nl = P.lx * P.ly * P.lz;
+  P.nlh = (P.nl + 1) / 2;
+  P.center = (P.nl - 1) / 2;
+  const long long ntasks = (long long)g.C * P.nlh + (long long)P.nl * ((long long)g.C * (g.C - 1) / 2);
+  const int npieces = P.npy * P.npz;
+  double2* part =
+      (double2*)ws_get(h, WS_GRAM_PART, sizeof(double2) * ntasks * npieces * P.ncx, &s);
+  if (s) return s;
+  int nt = ((g.ex + GXSLOT - 1) / GXSLOT + 31) / 32 * 32;
+  if (nt < 64) nt = 64;
+  if (nt > 256) nt = 256;
+  dim3 grid((unsigned)ntasks, (unsigned)npieces);
+  gram_cells_kernel<<<grid, nt, 0, st>>>(P, part);
+  s = cuda_error(h, cudaGetLastError(), "gram_cells");
+  if (s) return s;
+  const long long nn = (long long)g.n * g.n;
+  gram_assemble_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(P, part, (double2*)G);
+  return cuda_error(h, cudaGetLastError(), "gram_assemble");
+}
+
+}  // namespace hicu

@@ -1,0 +1,211 @@
+// Internal declarations shared by the libhicu translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "hicu.h"
+
+namespace hicu {
+
+// ------------------------------------------------------------------ views
+
+// Read/write view of a complex64 k-space array.  Region coordinate (0,0,0)
+// maps to element (c, oz, oy, ox); strides are in complex elements, x stride 1.
+struct KView {
+  float2* p;
+  long long sc, sz, sy;
+  int ox, oy, oz;
+};
+
+// Mask view: uint8, same addressing as KView with a coil stride (0 if shared).
+struct MView {
+  const uint8_t* p;  // nullptr = no mask
+  long long sc, sz, sy;
+  int ox, oy, oz;
+};
+
+// Geometry of one convolution problem on a region.
+struct ConvGeom {
+  int C;
+  int kx, ky, kz, K;   // K = kx*ky*kz
+  int n;               // C*K
+  int ex, ey, ez;      // region extent
+  int sx, sy, sz;      // valid-output extent
+  int cx, cy, cz;      // circular flags
+  long long s;         // sx*sy*sz
+};
+
+__host__ __device__ inline int wrap(int v, int m) {
+  int r = v % m;
+  return r < 0 ? r + m : r;
+}
+
+// ------------------------------------------------------------ reductions
+
+template <int NT>
+__device__ inline double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = (threadIdx.x < NT / 32) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  __syncthreads();
+  return t;  // valid in thread 0
+}
+
+// ----------------------------------------------------- bounded grid barrier
+// Used only inside cooperative launches (all CTAs co-resident).  Each wait
+// gives up after `timeout_ns` and records HICU_ERR_TIMEOUT in *err.
+
+struct GridSync {
+  unsigned* count;
+  unsigned* gen;
+  int* err;
+  unsigned nblocks;
+  unsigned long long timeout_ns;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned atom_add_acqrel_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Returns false (in every thread of the CTA) if the barrier timed out or an
+// error was already recorded; the caller must then leave the kernel.
+__device__ inline bool grid_sync(const GridSync& gs) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g = ld_acquire_u32(gs.gen);
+    const unsigned old = atom_add_acqrel_u32(gs.count, 1u);
+    if (old == gs.nblocks - 1) {
+      *gs.count = 0u;
+      st_release_u32(gs.gen, g + 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (ld_acquire_u32(gs.gen) == g) {
+        if (global_ns() - t0 > gs.timeout_ns) {
+          atomicExch(gs.err, (int)HICU_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    if (*((volatile int*)gs.err) != 0) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ------------------------------------------------------------ host side
+
+struct Workspace {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace hicu
+
+// The handle (opaque in the public header).
+struct hicu_handle {
+  int device = 0;
+  int num_sms = 0;
+  std::string last_error;
+  static constexpr int kSlots = 24;
+  hicu::Workspace ws[kSlots];
+  int* dev_err = nullptr;          // device error word
+  unsigned* dev_sync = nullptr;    // grid-barrier words (count, gen)
+  // warm-start state of the eigen-solver
+  int64_t eig_n = 0;
+  bool eig_have_v = false;
+};
+
+namespace hicu {
+
+enum Slot {
+  WS_FT = 0,      // filters transposed for conv  [n][Ppad]
+  WS_FA,          // filters transposed for adjoint [K][Ppad][Cpad]
+  WS_PART,        // reduction partials (double)
+  WS_STATS,       // internal stats double[8]
+  WS_R,           // conv output R
+  WS_G,           // gradient on the region
+  WS_P,           // JL matrix
+  WS_QF,          // Q in complex64
+  WS_T,           // projector intermediate
+  WS_BANK,        // filter bank [p][n]
+  WS_GRAM_PART,   // Gram cell partial sums
+  WS_EIG_A0,      // Jacobi ping
+  WS_EIG_A1,      // Jacobi pong
+  WS_EIG_V,       // eigenvectors
+  WS_EIG_VPREV,   // previous eigenvectors (warm start)
+  WS_EIG_PART,    // off-norm partials
+  WS_EIG_TMP,     // GEMM temp for warm start
+  WS_REC_G,       // reconstruct: Gram matrix
+  WS_REC_Q,       // reconstruct: null basis
+  WS_REC_EIG,     // reconstruct: eigenvalues
+  WS_REC_X,       // reconstruct: staged x (host input)
+  WS_REC_M,       // reconstruct: staged mask
+  WS_REC_LOG,     // reconstruct: device log
+  WS_REC_STATS,   // reconstruct: per-step stats
+};
+
+hicu_status set_error(hicu_handle* h, hicu_status s, const std::string& msg);
+hicu_status cuda_error(hicu_handle* h, cudaError_t e, const char* where);
+void* ws_get(hicu_handle* h, int slot, size_t bytes, hicu_status* st);
+
+// Validation + device geometry.
+hicu_status make_conv_geom(hicu_handle* h, const hicu_geom* g, const hicu_region* r,
+                           ConvGeom* out);
+KView full_view(const hicu_geom* g, const hicu_region* r, float* base);
+MView mask_view(const hicu_geom* g, const hicu_region* r, const uint8_t* mask);
+
+// Kernel launchers (stream = cudaStream_t).
+hicu_status launch_prep_filters(hicu_handle* h, const ConvGeom& g, const float2* bank, int p,
+                                float2* fT, int Ppad, float2* fA, int Cpad, cudaStream_t st);
+int conv_ppad(int p);
+int adj_cpad(int C);
+hicu_status launch_conv_fp32(hicu_handle* h, const ConvGeom& g, KView x, const float2* fT, int p,
+                             int Ppad, float2* R, double* partial, int* nblocks, cudaStream_t st);
+hicu_status launch_adjoint_fp32(hicu_handle* h, const ConvGeom& g, const float2* R,
+                                const float2* fA, int p, int Ppad, int Cpad, MView m, KView gout,
+                                double* partial, int* nblocks, cudaStream_t st);
+hicu_status launch_sum_partials(const double* partial, int n, double* out, cudaStream_t st);
+hicu_status launch_finalize_step(const double* part, int n_obj, int n_g, int n_d, double* stats,
+                                 cudaStream_t st);
+hicu_status launch_update(const ConvGeom& g, KView y, KView gbuf, MView m, const double* stats,
+                          cudaStream_t st);
+
+hicu_status launch_jl(hicu_handle* h, int64_t n, int64_t nr, int p, const double* Q, int mode,
+                      const double* P, uint64_t seed, uint64_t counter, float* bank,
+                      cudaStream_t st);
+
+hicu_status run_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* reg, const float* x,
+                     double* G, cudaStream_t st);
+hicu_status run_nullspace(hicu_handle* h, int64_t n, int64_t r, const double* G, double* Q,
+                          double* eigvals, int warm, cudaStream_t st);
+
+}  // namespace hicu

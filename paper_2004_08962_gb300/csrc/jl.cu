@@ -1,0 +1,139 @@
+// JL compression of the null space (Algorithm 1 step 6; Theory, JL paragraph):
+// Q~ = Q P with P i.i.d. zero-mean Gaussian of variance 1/p, drawn afresh for
+// every descent step.
+//
+// Random numbers: counter-based.  Element e of draw `counter` is Box-Muller on
+// SplitMix64 outputs 2m+1 and 2m+2 of the stream started at `seed`, with
+// m = counter*2^32 + e.  SplitMix64 is the generator of Steele, Lea & Flood
+// (OOPSLA 2014): state advances by 0x9E3779B97F4A7C15 and each state is passed
+// through the published 64-bit output mix.
+#include "hicu_internal.cuh"
+
+namespace hicu {
+
+__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double jl_gauss(uint64_t seed, uint64_t counter, uint64_t e) {
+  const uint64_t gamma = 0x9E3779B97F4A7C15ull;
+  const uint64_t k0 = 2ull * ((counter << 32) + e);
+  const uint64_t o1 = splitmix_mix(seed + (k0 + 1ull) * gamma);
+  const uint64_t o2 = splitmix_mix(seed + (k0 + 2ull) * gamma);
+  const double u1 = (double)((o1 >> 11) + 1ull) * 0x1.0p-53;  // (0, 1]
+  const double u2 = (double)(o2 >> 11) * 0x1.0p-53;           // [0, 1)
+  return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+// P (rows x p, row-major) in float; from the caller's double matrix or drawn here.
+__global__ void jl_make_p_kernel(int rows, int p, const double* __restrict__ Pin, uint64_t seed,
+                                 uint64_t counter, float* __restrict__ Pout) {
+  const long long tot = (long long)rows * p;
+  const double scale = 1.0 / sqrt((double)p);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = Pin ? Pin[i] : jl_gauss(seed, counter, (uint64_t)i) * scale;
+    Pout[i] = (float)v;
+  }
+}
+
+// complex128 -> complex64
+__global__ void to_c64_kernel(const double2* __restrict__ in, float2* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = in[i];
+    out[i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+// bank[k][a] = sum_j B[j][a] * W[j][k], B complex [m][n], W real [m][p] (nullspace mode)
+__global__ void jl_combine_real_kernel(int n, int m, int p, const float2* __restrict__ B,
+                                       const float* __restrict__ W, float2* __restrict__ bank) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (a >= n) return;
+  float re = 0.f, im = 0.f;
+  for (int j = 0; j < m; ++j) {
+    const float2 b = B[(long long)j * n + a];
+    const float w = __ldg(W + (long long)j * p + k);
+    re = fmaf(b.x, w, re);
+    im = fmaf(b.y, w, im);
+  }
+  bank[(long long)k * n + a] = make_float2(re, im);
+}
+
+// T[j][k] = sum_a conj(Q[j][a]) P[a][k]   (one warp per (j, k))
+__global__ void jl_project_kernel(int n, int m, int p, const float2* __restrict__ Q,
+                                  const float* __restrict__ P, float2* __restrict__ T) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= m * p) return;
+  const int j = warp / p, k = warp % p;
+  float re = 0.f, im = 0.f;
+  for (int a = lane; a < n; a += 32) {
+    const float2 q = Q[(long long)j * n + a];
+    const float w = P[(long long)a * p + k];
+    re = fmaf(q.x, w, re);
+    im = fmaf(-q.y, w, im);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_down_sync(0xffffffffu, re, o);
+    im += __shfl_down_sync(0xffffffffu, im, o);
+  }
+  if (lane == 0) T[(long long)j * p + k] = make_float2(re, im);
+}
+
+// bank[k][a] = sum_j Q[j][a] T[j][k] (complex x complex)
+__global__ void jl_combine_cplx_kernel(int n, int m, int p, const float2* __restrict__ Q,
+                                       const float2* __restrict__ T, float2* __restrict__ bank) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (a >= n) return;
+  float re = 0.f, im = 0.f;
+  for (int j = 0; j < m; ++j) {
+    const float2 q = Q[(long long)j * n + a];
+    const float2 t = T[(long long)j * p + k];
+    re = fmaf(q.x, t.x, fmaf(-q.y, t.y, re));
+    im = fmaf(q.x, t.y, fmaf(q.y, t.x, im));
+  }
+  bank[(long long)k * n + a] = make_float2(re, im);
+}
+
+hicu_status launch_jl(hicu_handle* h, int64_t n, int64_t nr, int p, const double* Q, int mode,
+                      const double* P, uint64_t seed, uint64_t counter, float* bank,
+                      cudaStream_t st) {
+  hicu_status s = HICU_OK;
+  const int rows = (mode == HICU_JL_PROJECTOR) ? (int)n : (int)nr;
+  float* Pf = (float*)ws_get(h, WS_P, sizeof(float) * rows * p, &s);
+  if (s) return s;
+  float2* Qf = (float2*)ws_get(h, WS_QF, sizeof(float2) * nr * n, &s);
+  if (s) return s;
+  {
+    const long long tot = (long long)rows * p;
+    int blocks = (int)((tot + 255) / 256);
+    if (blocks > 1024) blocks = 1024;
+    jl_make_p_kernel<<<blocks, 256, 0, st>>>(rows, p, P, seed, counter, Pf);
+  }
+  {
+    const long long tot = nr * n;
+    int blocks = (int)((tot + 255) / 256);
+    if (blocks > 2048) blocks = 2048;
+    to_c64_kernel<<<blocks, 256, 0, st>>>((const double2*)Q, Qf, tot);
+  }
+  dim3 grid((unsigned)((n + 127) / 128), (unsigned)p);
+  if (mode == HICU_JL_NULLSPACE) {
+    jl_combine_real_kernel<<<grid, 128, 0, st>>>((int)n, (int)nr, p, Qf, Pf, (float2*)bank);
+  } else {
+    float2* T = (float2*)ws_get(h, WS_T, sizeof(float2) * nr * p, &s);
+    if (s) return s;
+    const long long warps = nr * p;
+    jl_project_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>((int)n, (int)nr, p, Qf,
+                                                                            Pf, T);
+    jl_combine_cplx_kernel<<<grid, 128, 0, st>>>((int)n, (int)nr, p, Qf, T, (float2*)bank);
+  }
+  return cuda_error(h, cudaGetLastError(), "jl_compress");
+}
+
+}  // namespace hicu

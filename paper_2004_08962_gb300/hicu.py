@@ -1,0 +1,294 @@
+"""Thin ctypes binding of libhicu (include/hicu.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Tensors are torch CUDA tensors (device memory and streams come from
+PyTorch); complex64 k-space has shape (C, Nz, Ny, Nx).  Function names match
+the C entry points.  If the shared library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int32, c_int64, c_uint8, c_uint64, c_void_p
+from typing import Optional, Sequence
+
+import torch
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libhicu.so")
+
+HICU_FP32, HICU_SPLIT_BF16 = 0, 1
+HICU_JL_NULLSPACE, HICU_JL_PROJECTOR = 0, 1
+
+EXPORTED = (
+    "hicu_create", "hicu_destroy", "hicu_last_error", "hicu_status_string", "hicu_check",
+    "hicu_filter_length", "hicu_num_outputs", "hicu_gram", "hicu_nullspace", "hicu_jl_compress",
+    "hicu_conv_null", "hicu_conv_null_adjoint", "hicu_gd_step_filters", "hicu_gd_step",
+    "hicu_reconstruct",
+)
+
+
+class hicu_geom(ctypes.Structure):
+    _fields_ = [("dim", c_int64 * 3), ("ncoil", c_int32), ("k", c_int32 * 3),
+                ("circular", c_uint8 * 3), ("mask_per_coil", c_uint8)]
+
+
+class hicu_region(ctypes.Structure):
+    _fields_ = [("off", c_int64 * 3), ("ext", c_int64 * 3)]
+
+
+class hicu_stage(ctypes.Structure):
+    _fields_ = [("region", hicu_region), ("iters", c_int32), ("gd_steps", c_int32), ("p", c_int32)]
+
+
+class hicu_params(ctypes.Structure):
+    _fields_ = [("rank", c_int64), ("nstages", c_int32), ("stages", POINTER(hicu_stage)),
+                ("seed", c_uint64), ("jl", c_int32), ("prec", c_int32),
+                ("gram_on_current", c_int32), ("init", c_int32)]
+
+
+class hicu_log(ctypes.Structure):
+    _fields_ = [("J", POINTER(c_double)), ("objective", POINTER(c_double)), ("eta", POINTER(c_double))]
+
+
+class HicuError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libhicu.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing; build it with "
+                               "`python -m paper_2004_08962_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        P = c_void_p
+        G, R = POINTER(hicu_geom), POINTER(hicu_region)
+        sig = {
+            "hicu_create": ([POINTER(P)], c_int32),
+            "hicu_destroy": ([P], c_int32),
+            "hicu_last_error": ([P], ctypes.c_char_p),
+            "hicu_status_string": ([c_int32], ctypes.c_char_p),
+            "hicu_check": ([P, P], c_int32),
+            "hicu_filter_length": ([G], c_int64),
+            "hicu_num_outputs": ([G, R], c_int64),
+            "hicu_gram": ([P, G, R, P, P, P], c_int32),
+            "hicu_nullspace": ([P, c_int64, c_int64, P, P, P, c_int32, P], c_int32),
+            "hicu_jl_compress": ([P, c_int64, c_int64, c_int32, P, c_int32, P, c_uint64, c_uint64, P, P],
+                                 c_int32),
+            "hicu_conv_null": ([P, G, R, P, P, c_int32, P, P, c_int32, P], c_int32),
+            "hicu_conv_null_adjoint": ([P, G, R, P, P, c_int32, P, P, P, c_int32, P], c_int32),
+            "hicu_gd_step_filters": ([P, G, R, P, P, P, c_int32, P, c_int32, P], c_int32),
+            "hicu_gd_step": ([P, G, R, P, P, P, c_int64, c_int32, c_int32, c_uint64, c_uint64, P, P,
+                              c_int32, P], c_int32),
+            "hicu_reconstruct": ([P, G, P, P, POINTER(hicu_params), P, POINTER(hicu_log), P], c_int32),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _LIB = L
+    return _LIB
+
+
+# ----------------------------------------------------------------- helpers
+
+def make_geom(dims: Sequence[int], ncoil: int, kernel: Sequence[int], circular=(0, 0, 0),
+              mask_per_coil: bool = False) -> hicu_geom:
+    g = hicu_geom()
+    for a in range(3):
+        g.dim[a] = int(dims[a])
+        g.k[a] = int(kernel[a])
+        g.circular[a] = int(circular[a])
+    g.ncoil = int(ncoil)
+    g.mask_per_coil = 1 if mask_per_coil else 0
+    return g
+
+
+def make_region(off: Sequence[int], ext: Sequence[int]) -> hicu_region:
+    r = hicu_region()
+    for a in range(3):
+        r.off[a] = int(off[a])
+        r.ext[a] = int(ext[a])
+    return r
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return c_void_p(s.cuda_stream)
+
+
+class Handle:
+    """Owns a hicu_handle (workspace, warm-start state) on the current device."""
+
+    def __init__(self):
+        self.ptr = c_void_p()
+        self._check(lib().hicu_create(ctypes.byref(self.ptr)))
+
+    def _check(self, status: int):
+        if status != 0:
+            name = lib().hicu_status_string(status).decode()
+            msg = lib().hicu_last_error(self.ptr).decode() if self.ptr else ""
+            raise HicuError(status, f"{name}: {msg}")
+
+    def close(self):
+        if self.ptr:
+            lib().hicu_destroy(self.ptr)
+            self.ptr = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hicu_filter_length(geom: hicu_geom) -> int:
+    return int(lib().hicu_filter_length(ctypes.byref(geom)))
+
+
+def hicu_num_outputs(geom: hicu_geom, region: hicu_region) -> int:
+    return int(lib().hicu_num_outputs(ctypes.byref(geom), ctypes.byref(region)))
+
+
+def out_shape(geom: hicu_geom, region: hicu_region):
+    out = []
+    for a in range(3):
+        out.append(region.ext[a] if geom.circular[a] else region.ext[a] - geom.k[a] + 1)
+    return (out[2], out[1], out[0])
+
+
+def hicu_check(h: Handle, stream=None):
+    h._check(lib().hicu_check(h.ptr, _stream(stream)))
+
+
+def hicu_gram(h: Handle, geom, region, x: torch.Tensor, G: Optional[torch.Tensor] = None, stream=None):
+    n = hicu_filter_length(geom)
+    if G is None:
+        G = torch.empty((n, n), dtype=torch.complex128, device=x.device)
+    h._check(lib().hicu_gram(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(x), _ptr(G),
+                             _stream(stream)))
+    return G
+
+
+def hicu_nullspace(h: Handle, G: torch.Tensor, r: int, warm: bool = False, stream=None):
+    n = G.shape[0]
+    Q = torch.empty((n - r, n), dtype=torch.complex128, device=G.device)
+    eig = torch.empty((n,), dtype=torch.float64, device=G.device)
+    h._check(lib().hicu_nullspace(h.ptr, n, r, _ptr(G), _ptr(Q), _ptr(eig), 1 if warm else 0,
+                                  _stream(stream)))
+    return Q, eig
+
+
+def hicu_jl_compress(h: Handle, Q: torch.Tensor, p: int, mode: int = HICU_JL_NULLSPACE,
+                     P: Optional[torch.Tensor] = None, seed: int = 0, counter: int = 0, stream=None):
+    nr, n = Q.shape
+    bank = torch.empty((p, n), dtype=torch.complex64, device=Q.device)
+    h._check(lib().hicu_jl_compress(h.ptr, n, nr, p, _ptr(Q), mode, _ptr(P), seed, counter,
+                                    _ptr(bank), _stream(stream)))
+    return bank
+
+
+def hicu_conv_null(h: Handle, geom, region, x: torch.Tensor, filters: torch.Tensor,
+                   prec: int = HICU_FP32, want_objective: bool = False, stream=None):
+    p = filters.shape[0]
+    R = torch.empty(out_shape(geom, region) + (p,), dtype=torch.complex64, device=x.device)
+    obj = torch.zeros((1,), dtype=torch.float64, device=x.device) if want_objective else None
+    h._check(lib().hicu_conv_null(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(x),
+                                  _ptr(filters), p, _ptr(R), _ptr(obj), prec, _stream(stream)))
+    return (R, obj) if want_objective else R
+
+
+def hicu_conv_null_adjoint(h: Handle, geom, region, R: torch.Tensor, filters: torch.Tensor,
+                           mask: Optional[torch.Tensor] = None, g: Optional[torch.Tensor] = None,
+                           prec: int = HICU_FP32, want_gnorm2: bool = False, stream=None):
+    p = filters.shape[0]
+    if g is None:
+        g = torch.zeros((geom.ncoil, geom.dim[2], geom.dim[1], geom.dim[0]), dtype=torch.complex64,
+                        device=R.device)
+    gn = torch.zeros((1,), dtype=torch.float64, device=R.device) if want_gnorm2 else None
+    h._check(lib().hicu_conv_null_adjoint(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(R),
+                                          _ptr(filters), p, _ptr(mask), _ptr(g), _ptr(gn), prec,
+                                          _stream(stream)))
+    return (g, gn) if want_gnorm2 else g
+
+
+def hicu_gd_step_filters(h: Handle, geom, region, y: torch.Tensor, mask: Optional[torch.Tensor],
+                         filters: torch.Tensor, prec: int = HICU_FP32, stats=None, stream=None):
+    p = filters.shape[0]
+    if stats is None:
+        stats = torch.zeros((4,), dtype=torch.float64, device=y.device)
+    h._check(lib().hicu_gd_step_filters(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(y),
+                                        _ptr(mask), _ptr(filters), p, _ptr(stats), prec,
+                                        _stream(stream)))
+    return stats
+
+
+def hicu_gd_step(h: Handle, geom, region, y: torch.Tensor, mask: Optional[torch.Tensor],
+                 Q: torch.Tensor, p: int, jl_mode: int = HICU_JL_NULLSPACE, seed: int = 0,
+                 counter: int = 0, P: Optional[torch.Tensor] = None, prec: int = HICU_FP32,
+                 stats=None, stream=None):
+    nr = Q.shape[0]
+    if stats is None:
+        stats = torch.zeros((4,), dtype=torch.float64, device=y.device)
+    h._check(lib().hicu_gd_step(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(y), _ptr(mask),
+                                _ptr(Q), nr, p, jl_mode, seed, counter, _ptr(P), _ptr(stats), prec,
+                                _stream(stream)))
+    return stats
+
+
+def make_params(rank: int, stages, seed: int = 0, jl: int = HICU_JL_PROJECTOR, prec: int = HICU_FP32,
+                gram_on_current: bool = False, init: int = 0):
+    """stages: sequence of (off, ext, iters, gd_steps, p)."""
+    arr = (hicu_stage * len(stages))()
+    for i, (off, ext, iters, gd, p) in enumerate(stages):
+        arr[i].region = make_region(off, ext)
+        arr[i].iters = int(iters)
+        arr[i].gd_steps = int(gd)
+        arr[i].p = int(p)
+    prm = hicu_params()
+    prm.rank = int(rank)
+    prm.nstages = len(stages)
+    prm.stages = ctypes.cast(arr, POINTER(hicu_stage))
+    prm.seed = int(seed)
+    prm.jl = int(jl)
+    prm.prec = int(prec)
+    prm.gram_on_current = 1 if gram_on_current else 0
+    prm.init = int(init)
+    prm._keep = arr  # keep the stage array alive with the struct
+    return prm
+
+
+def hicu_reconstruct(h: Handle, geom, x0: torch.Tensor, mask: torch.Tensor, params: hicu_params,
+                     x_out: Optional[torch.Tensor] = None, want_log: bool = False, stream=None):
+    """x0 / mask / x_out may live on the GPU or (pinned) on the host."""
+    if x_out is None:
+        x_out = torch.empty_like(x0)
+    log_struct, logs = None, None
+    if want_log:
+        iters = sum(params.stages[i].iters for i in range(params.nstages))
+        steps = sum(params.stages[i].iters * params.stages[i].gd_steps for i in range(params.nstages))
+        logs = {"J": (c_double * max(iters, 1))(), "objective": (c_double * max(steps, 1))(),
+                "eta": (c_double * max(steps, 1))()}
+        log_struct = hicu_log(ctypes.cast(logs["J"], POINTER(c_double)),
+                              ctypes.cast(logs["objective"], POINTER(c_double)),
+                              ctypes.cast(logs["eta"], POINTER(c_double)))
+        logs["_n"] = (iters, steps)
+    h._check(lib().hicu_reconstruct(h.ptr, ctypes.byref(geom), _ptr(x0), _ptr(mask),
+                                    ctypes.byref(params), _ptr(x_out),
+                                    ctypes.byref(log_struct) if log_struct is not None else None,
+                                    _stream(stream)))
+    if want_log:
+        it, st = logs["_n"]
+        return x_out, {"J": list(logs["J"])[:it], "objective": list(logs["objective"])[:st],
+                       "eta": list(logs["eta"])[:st]}
+    return x_out
