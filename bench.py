@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Benchmark of the HICU hot path on GB300.
+
+One step = one call of hicu_reconstruct on the 2D brain-slice workload
+(256 x 256 k-space, 8 coils, 5 x 5 kernel, n = 200, rank 75; centre-out stage
+on the central 64 x 64 region: 50 outer iterations x 5 descent steps, p = 8;
+then full k-space: 10 outer iterations x 10 descent steps, p = 32), i.e. 60
+Gram + null-space updates and 350 JL-compressed descent steps with exact line
+search.  The metric is descent steps (GD iterations) per second.
+
+  value   device time of K steps (CUDA events on the launch stream), inputs
+          resident in HBM, L2 flushed between steps, max over ranks
+  e2e     the same call with pinned HOST input/output buffers: the library
+          copies x0 and the mask in and the result out inside the timed call
+  roofline  the kernel class with the largest live device time, timed with CUDA
+          events around each of its launches during the timed region
+  cpu_baseline  the FP64 oracle on a bounded sample of the same workload
+
+Multi-GPU: replicas only (each rank reconstructs its own slice), no collective
+on the data path; launched by torchrun with one process per GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "2d_brain_256"
+METRIC = "HICU GD-iters/s (full hicu_reconstruct of one 256x256x8-coil slice)"
+UNIT = "GD-iters/s"
+KERNEL_NAMES = {0: "gram", 1: "jacobi_eig", 2: "conv_fp32", 3: "adjoint_fp32", 4: "jl", 5: "misc",
+                6: "conv_tc", 7: "adjoint_tc"}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+def schedule(pb):
+    return [(s.off, s.ext, s.iters, s.gd_steps, s.p) for s in pb.stages]
+
+
+def gd_steps_per_recon(pb):
+    return sum(s.iters * s.gd_steps for s in pb.stages)
+
+
+def algorithmic_flops(pb, cls):
+    """Algorithmic real flops per reconstruction for a kernel class (see design notes)."""
+    C = pb.ncoil
+    kx, ky, kz = pb.kernel
+    n = C * kx * ky * kz
+    tot = 0.0
+    prev = pb.stages[0]
+    for st in pb.stages:
+        sx, sy, sz = (st.ext[0] - kx + 1, st.ext[1] - ky + 1, st.ext[2] - kz + 1)
+        s = sx * sy * sz
+        if cls == 2:    # two convolutions per step (H(y)Q~ and H(g)Q~), 8 n p s flops each
+            tot += st.iters * st.gd_steps * 2 * 8.0 * n * st.p * s
+        elif cls == 3:  # one adjoint per step, same count
+            tot += st.iters * st.gd_steps * 8.0 * n * st.p * s
+        elif cls == 0:  # lag-form correlation: C^2 (2k-1)^d / 2 complex MACs per region point
+            region = prev.ext[0] * prev.ext[1] * prev.ext[2]
+            lags = (2 * kx - 1) * (2 * ky - 1) * (2 * kz - 1)
+            tot += st.iters * 8.0 * (C * C * lags / 2.0) * region
+        prev = st
+    return tot
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r.split(",") for r in self.tmp.read().strip().splitlines() if r.strip()]
+        self.tmp.close()
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle arm
+
+def oracle_sample(pb, seed=11):
+    """Time the FP64 oracle on a bounded sample of one reconstruction and extrapolate.
+
+    Sample: one centre-out outer iteration (Gram, eigh, 5 descent steps), one
+    full-k-space Gram + eigh, one full-k-space descent step (p = 32).
+    """
+    from oracle import hicu_oracle as O
+    og = O.Geom(pb.dims, pb.ncoil, pb.kernel, pb.circular)
+    co, full = pb.stages[0], pb.stages[1]
+    rco, rfull = O.Region(co.off, co.ext), O.Region(full.off, full.ext)
+    x = pb.x0.astype(np.complex128)
+    t0 = time.perf_counter()
+    G = O.gram(x, og, rco)
+    Q, _ = O.nullspace(G, pb.rank)
+    y = x
+    for j in range(co.gd_steps):
+        f = O.as_filters(O.jl_compress(Q, O.jl_matrix(seed, j, og.n, co.p), "projector"), og)
+        y, _ = O.gd_step(y, pb.mask, og, rco, f)
+    t_co_iter = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    G = O.gram(y, og, rfull)
+    Q, _ = O.nullspace(G, pb.rank)
+    t_full_null = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    f = O.as_filters(O.jl_compress(Q, O.jl_matrix(seed, 99, og.n, full.p), "projector"), og)
+    y, _ = O.gd_step(y, pb.mask, og, rfull, f)
+    t_full_gd = time.perf_counter() - t0
+    t_recon = co.iters * t_co_iter + full.iters * t_full_null + full.iters * full.gd_steps * t_full_gd
+    sample_s = t_co_iter + t_full_null + t_full_gd
+    return gd_steps_per_recon(pb) / t_recon, sample_s
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [d.get("num_threads", 0) for d in threadpool_info() if d.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from synth.phantoms import make_problem
+    pb = make_problem(WORKLOAD)
+    vals, samples = [], []
+    for i in range(args.warmup + args.steps):
+        v, s = oracle_sample(pb)
+        if i >= args.warmup:
+            vals.append(v)
+            samples.append(s)
+    value = statistics.median(vals)
+    cores = blas_threads()
+    sample = (f"per step: 1 centre-out outer iteration (Gram, eigh, 5 steps p=8) + 1 full-k-space "
+              f"Gram/eigh + 1 full-k-space step (p=32), {statistics.mean(samples):.1f} s of CPU, "
+              f"extrapolated to the 350-step schedule")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * gd_steps_per_recon(pb) / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "image": "256x256", "coils": 8, "kernel": "5x5",
+                       "rank": 75, "schedule": "CO 64x64 50x5 p=8 + full 10x10 p=32"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------------- GPU arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hicu", choices=["hicu", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2004_08962_gb300 import build, hicu
+    from synth.phantoms import make_problem
+
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    pb = make_problem(WORKLOAD, seed=1000 + rank)
+    prec = hicu.HICU_FP32 if args.prec == "fp32" else hicu.HICU_SPLIT_BF16
+    h = hicu.Handle()
+    geom = hicu.make_geom(pb.dims, pb.ncoil, pb.kernel)
+    params = hicu.make_params(pb.rank, schedule(pb), seed=11, jl=hicu.HICU_JL_PROJECTOR, prec=prec)
+    x0 = torch.from_numpy(pb.x0).cuda()
+    mask = torch.from_numpy(pb.mask).cuda()
+    xout = torch.empty_like(x0)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    stream = torch.cuda.current_stream()
+    steps_per = gd_steps_per_recon(pb)
+
+    def one():
+        hicu.hicu_reconstruct(h, geom, x0, mask, params, x_out=xout)
+
+    # warm-up; the last warm-up steps find the kernel class with the most device time
+    classes = [0, 1, 2, 3, 4, 5]
+    per_class = {}
+    for i in range(args.warmup):
+        one()
+    for c in classes:
+        hicu.hicu_profile_select(h, c)
+        one()
+        ms, nl, _ = hicu.hicu_profile_read(h)
+        per_class[c] = ms
+    dominant = max(per_class, key=per_class.get)
+
+    # timed region
+    sampler = ClockSampler(local)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler.start()
+    hicu.hicu_profile_select(h, dominant)
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    dom_ms, dom_launches, all_launches = hicu.hicu_profile_read(h)
+    hicu.hicu_profile_select(h, -1)
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax_s = t.item() / 1e3
+    value = steps_per * args.steps * world / tmax_s
+
+    # end-to-end through the C ABI with pinned host buffers (copies inside the call)
+    x0h = torch.from_numpy(pb.x0).pin_memory()
+    mh = torch.from_numpy(pb.mask).pin_memory()
+    outh = torch.empty_like(x0h).pin_memory()
+    hicu.hicu_reconstruct(h, geom, x0h, mh, params, x_out=outh)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e2e_s = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hicu.hicu_reconstruct(h, geom, x0h, mh, params, x_out=outh)
+        e2e_s += time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = steps_per * args.steps * world / te.item()
+    h2d = pb.x0.nbytes + pb.mask.nbytes
+    d2h = pb.x0.nbytes
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    peaks, peak_src = load_peaks()
+    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # TFLOP/s
+    avg_launch_s = dom_ms / 1e3 / max(dom_launches, 1)
+    flops_recon = algorithmic_flops(pb, dominant)
+    if flops_recon > 0:
+        per_launch = flops_recon * args.steps / max(dom_launches, 1)
+        achieved = per_launch / avg_launch_s / 1e12
+        roof = {"kernel": KERNEL_NAMES[dominant], "bound": "alu", "achieved": achieved,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                "peak_source": "FP32 CUDA-core peak derived from 152 SMs x 128 lanes x 2 x max SM clock",
+                "avg_launch_us": avg_launch_s * 1e6, "launches": dom_launches}
+    else:
+        fp64_peak = 1.25
+        roof = {"kernel": KERNEL_NAMES[dominant], "bound": "alu", "achieved": None, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": None, "traffic": None,
+                "peak_source": "nominal FP64 rate of GB300",
+                "avg_launch_us": avg_launch_s * 1e6, "launches": dom_launches}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tmax_s * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "bf16x2",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "image": "256x256", "coils": 8, "kernel": "5x5",
+                       "rank": 75, "schedule": "CO 64x64 50x5 p=8 + full 10x10 p=32",
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": all_launches,
+            "roofline": roof,
+            "class_ms_per_step": {KERNEL_NAMES[c]: round(v, 3) for c, v in per_class.items()},
+            "clocks": clocks,
+            "peaks_source": peak_src}
+    if world == 1 and not args.no_cpu_baseline:
+        v, s = oracle_sample(pb)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                                "sample": f"1 CO outer iteration + 1 full Gram/eigh + 1 full step "
+                                          f"({s:.1f} s CPU), extrapolated to the 350-step schedule"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    h.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -74,6 +74,18 @@ typedef enum {
   HICU_JL_PROJECTOR = 1  /* Q~ = Q (Q^H P), P is n x p: depends only on span(Q) */
 } hicu_jl;
 
+/* Kernel classes for launch accounting and event timing (hicu_profile_*). */
+typedef enum {
+  HICU_K_GRAM = 0,       /* Gram cross-correlation kernels */
+  HICU_K_EIG = 1,        /* Jacobi eigen-solver */
+  HICU_K_CONV = 2,       /* FP32 valid convolution */
+  HICU_K_ADJOINT = 3,    /* FP32 masked adjoint */
+  HICU_K_JL = 4,         /* JL draw and compression */
+  HICU_K_MISC = 5,       /* layout, reductions, update, sorting */
+  HICU_K_CONV_TC = 6,    /* tensor-core convolution */
+  HICU_K_ADJOINT_TC = 7  /* tensor-core adjoint */
+} hicu_kernel_class;
+
 typedef struct {
   int64_t dim[3];        /* Nx, Ny, Nz */
   int32_t ncoil;         /* C (channels; shots stacked as channels count here) */
@@ -127,6 +139,18 @@ const char* hicu_status_string(hicu_status s);
 /* Synchronise `stream`, then report (and clear) any device-side error word. */
 hicu_status hicu_check(hicu_handle* h, void* stream);
 
+/*
+ * Tracing: every kernel the library launches is counted; launches of one
+ * selected class (hicu_kernel_class, -1 = none) are also bracketed by CUDA
+ * events recorded on the launch stream.  hicu_profile_select() resets the
+ * counters; hicu_profile_read() synchronises on the last event and returns the
+ * summed device time (ms) of the timed launches, their number, and the number
+ * of launches of every class since the last select/read, then resets.
+ */
+hicu_status hicu_profile_select(hicu_handle* h, int32_t kernel_class);
+hicu_status hicu_profile_read(hicu_handle* h, double* total_ms, int64_t* class_launches,
+                              int64_t* all_launches);
+
 /* Filter length n = C*kx*ky*kz, or -1 for an invalid geometry. */
 int64_t hicu_filter_length(const hicu_geom* geom);
 /* Number of valid outputs s of region S, or -1 if S does not fit the geometry. */
@@ -162,6 +186,12 @@ hicu_status hicu_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* 
  */
 hicu_status hicu_nullspace(hicu_handle* h, int64_t n, int64_t r, const double* G, double* Q,
                            double* eigvals, int32_t warm, void* stream);
+
+/*
+ * hicu_nullspace_info - sweeps used and convergence flag of the last
+ * hicu_nullspace call on this handle (synchronises the device).
+ */
+hicu_status hicu_nullspace_info(hicu_handle* h, int32_t* sweeps, int32_t* converged);
 
 /*
  * hicu_jl_compress - Q~ = Q P with P i.i.d. N(0, 1/p) (Algorithm 1 step 6;

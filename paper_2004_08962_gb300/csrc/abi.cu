@@ -20,6 +20,25 @@ hicu_status cuda_error(hicu_handle* h, cudaError_t e, const char* where) {
   return set_error(h, HICU_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+void prof_begin(hicu_handle* h, int cls, cudaStream_t st) {
+  ++h->launches_all;
+  if (h->prof_class != cls) return;
+  ++h->launches_class;
+  if (h->prof_used + 2 > (size_t)(1 << 16)) return;  // cap the number of timed launches
+  while (h->prof_events.size() < h->prof_used + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    h->prof_events.push_back(e);
+  }
+  cudaEventRecord(h->prof_events[h->prof_used], st);
+}
+
+void prof_end(hicu_handle* h, int cls, cudaStream_t st) {
+  if (h->prof_class != cls || h->prof_used + 2 > h->prof_events.size()) return;
+  cudaEventRecord(h->prof_events[h->prof_used + 1], st);
+  h->prof_used += 2;
+}
+
 void* ws_get(hicu_handle* h, int slot, size_t bytes, hicu_status* st) {
   Workspace& w = h->ws[slot];
   if (bytes == 0) bytes = 16;
@@ -161,6 +180,7 @@ extern "C" hicu_status hicu_destroy(hicu_handle* h) {
   cudaDeviceSynchronize();
   for (auto& w : h->ws)
     if (w.ptr) cudaFree(w.ptr);
+  for (auto e : h->prof_events) cudaEventDestroy(e);
   cudaFree(h->dev_err);
   cudaFree(h->dev_sync);
   delete h;
@@ -198,6 +218,38 @@ extern "C" hicu_status hicu_check(hicu_handle* h, void* stream) {
   return HICU_OK;
 }
 
+extern "C" hicu_status hicu_profile_select(hicu_handle* h, int32_t kernel_class) {
+  if (!h) return HICU_ERR_ARG;
+  if (kernel_class < -1 || kernel_class > K_ADJOINT_TC)
+    return set_error(h, HICU_ERR_ARG, "profile_select: unknown kernel class");
+  h->prof_class = kernel_class;
+  h->prof_used = 0;
+  h->launches_class = 0;
+  h->launches_all = 0;
+  return HICU_OK;
+}
+
+extern "C" hicu_status hicu_profile_read(hicu_handle* h, double* total_ms, int64_t* class_launches,
+                                         int64_t* all_launches) {
+  if (!h) return HICU_ERR_ARG;
+  double ms = 0.0;
+  if (h->prof_used > 0) {
+    cudaError_t e = cudaEventSynchronize(h->prof_events[h->prof_used - 1]);
+    if (e != cudaSuccess) return cuda_error(h, e, "profile_read");
+    for (size_t i = 0; i + 1 < h->prof_used; i += 2) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, h->prof_events[i], h->prof_events[i + 1]) == cudaSuccess) ms += t;
+    }
+  }
+  if (total_ms) *total_ms = ms;
+  if (class_launches) *class_launches = h->launches_class;
+  if (all_launches) *all_launches = h->launches_all;
+  h->prof_used = 0;
+  h->launches_class = 0;
+  h->launches_all = 0;
+  return HICU_OK;
+}
+
 extern "C" int64_t hicu_filter_length(const hicu_geom* geom) {
   if (!geom_ok(geom)) return -1;
   return (int64_t)geom->ncoil * geom->k[0] * geom->k[1] * geom->k[2];
@@ -223,6 +275,18 @@ extern "C" hicu_status hicu_nullspace(hicu_handle* h, int64_t n, int64_t r, cons
   if (!h) return HICU_ERR_ARG;
   if (!G || !Q) return set_error(h, HICU_ERR_ARG, "nullspace: null pointer");
   return run_nullspace(h, n, r, G, Q, eigvals, warm, (cudaStream_t)stream);
+}
+
+extern "C" hicu_status hicu_nullspace_info(hicu_handle* h, int32_t* sweeps, int32_t* converged) {
+  if (!h || !sweeps || !converged) return HICU_ERR_ARG;
+  if (!h->eig_info) return set_error(h, HICU_ERR_ARG, "nullspace_info: no eigen-decomposition yet");
+  int info[3] = {0, 0, 0};
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(info, h->eig_info, sizeof(info), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_error(h, e, "nullspace_info");
+  *sweeps = info[0];
+  *converged = info[1];
+  return HICU_OK;
 }
 
 extern "C" hicu_status hicu_jl_compress(hicu_handle* h, int64_t n, int64_t nr, int32_t p,
@@ -289,7 +353,7 @@ extern "C" hicu_status hicu_conv_null(hicu_handle* h, const hicu_geom* geom, con
   s = launch_conv_fp32(h, g, full_view(geom, region, const_cast<float*>(x)), b.fT, p, b.Ppad,
                        (float2*)R, part, &nb, st);
   if (s) return s;
-  if (objective) return launch_sum_partials(part, nb, objective, st);
+  if (objective) return launch_sum_partials(h, part, nb, objective, st);
   return HICU_OK;
 }
 
@@ -318,7 +382,7 @@ extern "C" hicu_status hicu_conv_null_adjoint(hicu_handle* h, const hicu_geom* g
   if (s) return s;
   s = launch_adjoint_fp32(h, g, (const float2*)R, b.fA, p, b.Ppad, b.Cpad, mv, gv, part, &nb, st);
   if (s) return s;
-  if (gnorm2) return launch_sum_partials(part, nb, gnorm2, st);
+  if (gnorm2) return launch_sum_partials(h, part, nb, gnorm2, st);
   return HICU_OK;
 }
 
@@ -360,9 +424,9 @@ hicu_status gd_step_filters(hicu_handle* h, const hicu_geom* geom, const hicu_re
   if (s) return s;
   s = launch_conv_fp32(h, g, gview, b.fT, p, b.Ppad, nullptr, part + n1 + n2, &n3, st);
   if (s) return s;
-  s = launch_finalize_step(part, n1, n2, n3, st4, st);
+  s = launch_finalize_step(h, part, n1, n2, n3, st4, st);
   if (s) return cuda_error(h, cudaGetLastError(), "finalize");
-  s = launch_update(g, yv, gview, mv, st4, st);
+  s = launch_update(h, g, yv, gview, mv, st4, st);
   if (s) return cuda_error(h, cudaGetLastError(), "update");
   return HICU_OK;
 }
@@ -513,9 +577,10 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
   double* dstats = (double*)ws_get(h, WS_REC_STATS, sizeof(double) * 4 * (total_steps + 1), &s);
   if (s) return s;
   if (prm->init == 1) {
-    time_average_kernel<<<1024, 256, 0, st>>>(geom->ncoil, (int)geom->dim[0], (int)geom->dim[1],
-                                             (int)geom->dim[2], (float2*)y, m,
-                                             geom->mask_per_coil ? geom->dim[0] * geom->dim[1] * geom->dim[2] : 0);
+    HICU_LAUNCH(h, K_MISC, st,
+                time_average_kernel<<<1024, 256, 0, st>>>(
+                    geom->ncoil, (int)geom->dim[0], (int)geom->dim[1], (int)geom->dim[2], (float2*)y, m,
+                    geom->mask_per_coil ? geom->dim[0] * geom->dim[1] * geom->dim[2] : 0));
   }
   uint64_t counter = 0;
   long long it = 0;
@@ -528,7 +593,7 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
       if (s) return s;
       s = run_nullspace(h, n, r, G, Q, eig, it > 0 ? 1 : 0, st);
       if (s) return s;
-      tail_sum_kernel<<<1, 256, 0, st>>>(eig, (int)nr, dlog + it);
+      HICU_LAUNCH(h, K_MISC, st, tail_sum_kernel<<<1, 256, 0, st>>>(eig, (int)nr, dlog + it));
       for (int j = 0; j < stg.gd_steps; ++j) {
         s = hicu_gd_step(h, geom, &stg.region, y, m, Q, nr, stg.p, prm->jl, prm->seed, counter, nullptr,
                          dstats + 4 * counter, prm->prec, stream);

@@ -59,7 +59,7 @@ hicu_status launch_prep_filters(hicu_handle* h, const ConvGeom& g, const float2*
   if (totA > tot) tot = totA;
   int blocks = (int)((tot + 255) / 256);
   if (blocks > 4096) blocks = 4096;
-  prep_filters_kernel<<<blocks, 256, 0, st>>>(g, bank, p, fT, Ppad, fA, Cpad);
+  HICU_LAUNCH(h, K_MISC, st, prep_filters_kernel<<<blocks, 256, 0, st>>>(g, bank, p, fT, Ppad, fA, Cpad));
   return cuda_error(h, cudaGetLastError(), "prep_filters");
 }
 
@@ -148,7 +148,7 @@ hicu_status launch_conv_fp32(hicu_handle* h, const ConvGeom& g, KView x, const f
   if (smem > 48 * 1024) {
     cudaFuncSetAttribute(conv_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
-  conv_fp32_kernel<<<grid, CNT, smem, st>>>(g, x, fT, p, Ppad, R, partial);
+  HICU_LAUNCH(h, K_CONV, st, conv_fp32_kernel<<<grid, CNT, smem, st>>>(g, x, fT, p, Ppad, R, partial));
   return cuda_error(h, cudaGetLastError(), "conv_fp32");
 }
 
@@ -247,11 +247,11 @@ hicu_status launch_adjoint_fp32(hicu_handle* h, const ConvGeom& g, const float2*
   if (partial == nullptr) return HICU_OK;
   const size_t smem = sizeof(float2) * APK * (ATY + g.ky - 1) * (ATX + g.kx - 1);
   switch (Cpad) {
-    case 4: adjoint_fp32_kernel<4><<<grid, ANT, smem, st>>>(g, R, fA, p, Ppad, m, gout, partial); break;
-    case 8: adjoint_fp32_kernel<8><<<grid, ANT, smem, st>>>(g, R, fA, p, Ppad, m, gout, partial); break;
-    case 16: adjoint_fp32_kernel<16><<<grid, ANT, smem, st>>>(g, R, fA, p, Ppad, m, gout, partial); break;
-    case 32: adjoint_fp32_kernel<32><<<grid, ANT, smem, st>>>(g, R, fA, p, Ppad, m, gout, partial); break;
-    case 64: adjoint_fp32_kernel<64><<<grid, ANT, smem, st>>>(g, R, fA, p, Ppad, m, gout, partial); break;
+    case 4: HICU_LAUNCH(h, K_ADJOINT, st, adjoint_fp32_kernel<4><<<grid, ANT, smem, st>>>(g, R, fA, p, Ppad, m, gout, partial)); break;
+    case 8: HICU_LAUNCH(h, K_ADJOINT, st, adjoint_fp32_kernel<8><<<grid, ANT, smem, st>>>(g, R, fA, p, Ppad, m, gout, partial)); break;
+    case 16: HICU_LAUNCH(h, K_ADJOINT, st, adjoint_fp32_kernel<16><<<grid, ANT, smem, st>>>(g, R, fA, p, Ppad, m, gout, partial)); break;
+    case 32: HICU_LAUNCH(h, K_ADJOINT, st, adjoint_fp32_kernel<32><<<grid, ANT, smem, st>>>(g, R, fA, p, Ppad, m, gout, partial)); break;
+    case 64: HICU_LAUNCH(h, K_ADJOINT, st, adjoint_fp32_kernel<64><<<grid, ANT, smem, st>>>(g, R, fA, p, Ppad, m, gout, partial)); break;
     default: return set_error(h, HICU_ERR_UNSUPPORTED, "adjoint: coil count above 64");
   }
   return cuda_error(h, cudaGetLastError(), "adjoint_fp32");
@@ -271,8 +271,9 @@ __global__ void sum_partials_kernel(const double* __restrict__ part, int n, doub
   if (threadIdx.x == 0) *out = s;
 }
 
-hicu_status launch_sum_partials(const double* partial, int n, double* out, cudaStream_t st) {
-  sum_partials_kernel<<<1, 256, 0, st>>>(partial, n, out);
+hicu_status launch_sum_partials(hicu_handle* h, const double* partial, int n, double* out,
+                                cudaStream_t st) {
+  HICU_LAUNCH(h, K_MISC, st, sum_partials_kernel<<<1, 256, 0, st>>>(partial, n, out));
   return cudaGetLastError() == cudaSuccess ? HICU_OK : HICU_ERR_CUDA;
 }
 
@@ -293,9 +294,9 @@ __global__ void finalize_step_kernel(const double* __restrict__ part, int n_obj,
   }
 }
 
-hicu_status launch_finalize_step(const double* part, int n_obj, int n_g, int n_d, double* stats,
-                                 cudaStream_t st) {
-  finalize_step_kernel<<<1, 256, 0, st>>>(part, n_obj, n_g, n_d, stats);
+hicu_status launch_finalize_step(hicu_handle* h, const double* part, int n_obj, int n_g, int n_d,
+                                 double* stats, cudaStream_t st) {
+  HICU_LAUNCH(h, K_MISC, st, finalize_step_kernel<<<1, 256, 0, st>>>(part, n_obj, n_g, n_d, stats));
   return cudaGetLastError() == cudaSuccess ? HICU_OK : HICU_ERR_CUDA;
 }
 
@@ -329,12 +330,12 @@ __global__ void update_kernel(ConvGeom g, KView y, KView gb, MView m, const doub
   }
 }
 
-hicu_status launch_update(const ConvGeom& g, KView y, KView gb, MView m, const double* stats,
-                          cudaStream_t st) {
+hicu_status launch_update(hicu_handle* h, const ConvGeom& g, KView y, KView gb, MView m,
+                          const double* stats, cudaStream_t st) {
   const long long total = (long long)g.C * g.ez * g.ey * g.ex;
   int blocks = (int)((total + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
-  update_kernel<<<blocks, 256, 0, st>>>(g, y, gb, m, stats);
+  HICU_LAUNCH(h, K_MISC, st, update_kernel<<<blocks, 256, 0, st>>>(g, y, gb, m, stats));
   return cudaGetLastError() == cudaSuccess ? HICU_OK : HICU_ERR_CUDA;
 }
 

@@ -26,24 +26,42 @@ namespace hicu {
 
 struct Rot {
   double cs, sn, ex, ey;  // W = [[cs, sn], [-sn e, cs e]], e = ex + i ey
+  int ident;              // 1: W = I (pair already decoupled)
 };
 
+// The rotation angle is computed in FP32 from the FP64 entries (an angle accurate to
+// ~1e-7 leaves |A_pq| ~ 1e-7 |b|, so Jacobi still converges, with at worst a 1e-7
+// linear rate near the end) and then made unitary to FP64 precision with two Newton
+// steps for 1/sqrt(cs^2 + sn^2) and 1/|e|.  This keeps long FP64 sqrt/divide chains
+// off the critical path of every round.  Pairs with |b| <= 1e-17 sqrt(|a c|) are left
+// alone (the usual relative threshold, which protects tiny eigenvalues).
 __device__ __forceinline__ Rot make_rot(double a, double c, double2 b) {
   Rot R;
-  const double ab = hypot(b.x, b.y);
-  if (!(ab > 0.0)) {
-    R.cs = 1.0; R.sn = 0.0; R.ex = 1.0; R.ey = 0.0;
+  const float bx = (float)b.x, by = (float)b.y;
+  const float ab = hypotf(bx, by);
+  const float thr = 1e-17f * sqrtf(fabsf((float)a)) * sqrtf(fabsf((float)c));
+  if (!(ab > thr) || !(ab > 0.f)) {
+    R.cs = 1.0; R.sn = 0.0; R.ex = 1.0; R.ey = 0.0; R.ident = 1;
     return R;
   }
-  const double tau = (c - a) / (2.0 * ab);
-  double t;
-  if (fabs(tau) > 1e150) t = 0.5 / tau;
-  else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-  const double cs = 1.0 / sqrt(1.0 + t * t);
-  R.cs = cs;
-  R.sn = t * cs;
-  R.ex = b.x / ab;
-  R.ey = -b.y / ab;
+  const float tau = (float)(c - a) / (2.f * ab);
+  float t;
+  if (fabsf(tau) > 1e18f) t = 0.5f / tau;
+  else t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+  const float cs = rsqrtf(1.f + t * t);
+  double c64 = cs, s64 = (double)t * cs;
+  double q = c64 * c64 + s64 * s64;
+  double f = 1.5 - 0.5 * q;
+  f = f * (1.5 - 0.5 * q * f * f);
+  R.cs = c64 * f;
+  R.sn = s64 * f;
+  double x64 = bx / ab, y64 = -by / ab;
+  q = x64 * x64 + y64 * y64;
+  f = 1.5 - 0.5 * q;
+  f = f * (1.5 - 0.5 * q * f * f);
+  R.ex = x64 * f;
+  R.ey = y64 * f;
+  R.ident = 0;
   return R;
 }
 
@@ -83,7 +101,6 @@ struct JacArgs {
   int* info;     // [0] sweeps, [1] converged, [2] buffer holding the result
   int max_sweeps;
   double tol2;
-  int T;  // tile side in pairs, blockDim.x == T*T
   GridSync gs;
 };
 
@@ -99,71 +116,99 @@ __device__ double dyn_block_sum(double v, double* sh) {
   return t;
 }
 
-__global__ void __launch_bounds__(256) jacobi_kernel(JacArgs J) {
-  __shared__ Rot rp[16], rq[16];
-  __shared__ int ip[16], iq[16], jp[16], jq[16];
+// One warp owns one tile of JT x JT pair-blocks per round.  Pass 1: lane (b, c)
+// writes column c of block b of W_P^H A_blk W_Q (all four inputs are loaded, so no
+// lane diverges); pass 2: lane (b, r) updates row r of V on the block's column pair.
+constexpr int JT = 4;
+constexpr int JWARPS = 8;
+
+__device__ __forceinline__ double2 cmul_e(double2 a, double ex, double ey) {  // a * e
+  return make_double2(a.x * ex - a.y * ey, a.x * ey + a.y * ex);
+}
+__device__ __forceinline__ double2 cmul_ce(double2 a, double ex, double ey) {  // conj(e) * a
+  return make_double2(a.x * ex + a.y * ey, a.y * ex - a.x * ey);
+}
+__device__ __forceinline__ double2 lin(double s, double2 a, double t, double2 b) {  // s a + t b
+  return make_double2(fma(s, a.x, t * b.x), fma(s, a.y, t * b.y));
+}
+
+__global__ void __launch_bounds__(JWARPS * 32) jacobi_kernel(JacArgs J) {
+  __shared__ Rot rp[JWARPS][JT], rq[JWARPS][JT];
+  __shared__ int ip[JWARPS][JT], iq[JWARPS][JT], jp[JWARPS][JT], jq[JWARPS][JT];
   __shared__ double red[8];
   __shared__ int s_done;
-  const int n = J.n, np = n / 2, T = J.T;
-  const int ntile = (np + T - 1) / T;
+  const int n = J.n, np = n / 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntile = (np + JT - 1) / JT;
   const long long ntiles = (long long)ntile * ntile;
+  const long long gw = (long long)blockIdx.x * JWARPS + warp;
+  const long long nw = (long long)gridDim.x * JWARPS;
   int cur = 0;
   for (int sweep = 0; sweep < J.max_sweeps; ++sweep) {
     for (int t = 0; t < n - 1; ++t) {
       const double2* A = cur ? J.A1 : J.A0;
       double2* B = cur ? J.A0 : J.A1;
-      for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      for (long long tile = gw; tile < ntiles; tile += nw) {
         const int tp = (int)(tile / ntile), tq = (int)(tile % ntile);
-        __syncthreads();
-        if (threadIdx.x < 2 * T) {
-          const int side = threadIdx.x / T, i = threadIdx.x % T;
-          const int P = (side == 0 ? tp : tq) * T + i;
+        __syncwarp();
+        if (lane < 2 * JT) {
+          const int side = lane / JT, i = lane % JT;
+          const int P = (side == 0 ? tp : tq) * JT + i;
           if (P < np) {
             int p, q;
             pair_of(n, t, P, p, q);
             const Rot R = make_rot(A[(long long)p * n + p].x, A[(long long)q * n + q].x,
                                    A[(long long)p * n + q]);
-            if (side == 0) { rp[i] = R; ip[i] = p; iq[i] = q; }
-            else { rq[i] = R; jp[i] = p; jq[i] = q; }
+            if (side == 0) { rp[warp][i] = R; ip[warp][i] = p; iq[warp][i] = q; }
+            else { rq[warp][i] = R; jp[warp][i] = p; jq[warp][i] = q; }
           }
         }
-        __syncthreads();
-        const int i = threadIdx.x / T, j = threadIdx.x % T;
-        const int P = tp * T + i, Q = tq * T + j;
+        __syncwarp();
+        const int blk = lane >> 1, sub = lane & 1;
+        const int i = blk / JT, j = blk % JT;
+        const int P = tp * JT + i, Q = tq * JT + j;
         if (P < np && Q < np) {
-          const int p1 = ip[i], q1 = iq[i], p2 = jp[j], q2 = jq[j];
-          double2 u00, u01, u10, u11, w00, w01, w10, w11;
-          rot_entries(rp[i], u00, u01, u10, u11);
-          rot_entries(rq[j], w00, w01, w10, w11);
-          const double2 a00 = A[(long long)p1 * n + p2], a01 = A[(long long)p1 * n + q2];
-          const double2 a10 = A[(long long)q1 * n + p2], a11 = A[(long long)q1 * n + q2];
-          // M = A_blk W_Q
-          const double2 m00 = cadd(cmul(a00, w00), cmul(a01, w10));
-          const double2 m01 = cadd(cmul(a00, w01), cmul(a01, w11));
-          const double2 m10 = cadd(cmul(a10, w00), cmul(a11, w10));
-          const double2 m11 = cadd(cmul(a10, w01), cmul(a11, w11));
-          // B_blk = W_P^H M
-          double2 b00 = cadd(cmulc(u00, m00), cmulc(u10, m10));
-          double2 b01 = cadd(cmulc(u00, m01), cmulc(u10, m11));
-          double2 b10 = cadd(cmulc(u01, m00), cmulc(u11, m10));
-          double2 b11 = cadd(cmulc(u01, m01), cmulc(u11, m11));
-          if (P == Q) {
-            b01 = make_double2(0.0, 0.0);
-            b10 = make_double2(0.0, 0.0);
-            b00.y = 0.0;
-            b11.y = 0.0;
+          const int p1 = ip[warp][i], q1 = iq[warp][i], p2 = jp[warp][j], q2 = jq[warp][j];
+          const Rot wq = rq[warp][j];
+          const Rot wp = rp[warp][i];
+          // pass 1: column `sub` of the new block
+          {
+            const double2 a00 = A[(long long)p1 * n + p2], a01 = A[(long long)p1 * n + q2];
+            const double2 a10 = A[(long long)q1 * n + p2], a11 = A[(long long)q1 * n + q2];
+            double2 b0, b1;
+            if (wp.ident && wq.ident) {
+              b0 = sub ? a01 : a00;
+              b1 = sub ? a11 : a10;
+            } else {
+              // M = A_blk W_Q: m_r0 = cs a_r0 - sn (a_r1 e), m_r1 = sn a_r0 + cs (a_r1 e)
+              const double2 u0 = cmul_e(a01, wq.ex, wq.ey), u1 = cmul_e(a11, wq.ex, wq.ey);
+              double2 m0, m1;
+              if (sub == 0) {
+                m0 = lin(wq.cs, a00, -wq.sn, u0);
+                m1 = lin(wq.cs, a10, -wq.sn, u1);
+              } else {
+                m0 = lin(wq.sn, a00, wq.cs, u0);
+                m1 = lin(wq.sn, a10, wq.cs, u1);
+              }
+              // B = W_P^H M: b_0 = cs m0 - sn conj(e) m1, b_1 = sn m0 + cs conj(e) m1
+              const double2 v = cmul_ce(m1, wp.ex, wp.ey);
+              b0 = lin(wp.cs, m0, -wp.sn, v);
+              b1 = lin(wp.sn, m0, wp.cs, v);
+            }
+            if (P == Q) {  // diagonal entries of a Hermitian matrix are real
+              if (sub == 0) b0.y = 0.0; else b1.y = 0.0;
+            }
+            const int col = sub ? q2 : p2;
+            B[(long long)p1 * n + col] = b0;
+            B[(long long)q1 * n + col] = b1;
           }
-          B[(long long)p1 * n + p2] = b00;
-          B[(long long)p1 * n + q2] = b01;
-          B[(long long)q1 * n + p2] = b10;
-          B[(long long)q1 * n + q2] = b11;
-          // V <- V W on columns (p2, q2), rows p1 and q1
-#pragma unroll
-          for (int rr = 0; rr < 2; ++rr) {
-            const long long row = (long long)(rr ? q1 : p1) * n;
+          // pass 2: row `sub` (p1 or q1) of V on columns (p2, q2): V <- V W_Q
+          if (!wq.ident) {
+            const long long row = (long long)(sub ? q1 : p1) * n;
             const double2 v0 = J.V[row + p2], v1 = J.V[row + q2];
-            J.V[row + p2] = cadd(cmul(v0, w00), cmul(v1, w10));
-            J.V[row + q2] = cadd(cmul(v0, w01), cmul(v1, w11));
+            const double2 u = cmul_e(v1, wq.ex, wq.ey);
+            J.V[row + p2] = lin(wq.cs, v0, -wq.sn, u);
+            J.V[row + q2] = lin(wq.sn, v0, wq.cs, u);
           }
         }
       }
@@ -174,12 +219,12 @@ __global__ void __launch_bounds__(256) jacobi_kernel(JacArgs J) {
     {
       const double2* A = cur ? J.A1 : J.A0;
       double off = 0.0, dia = 0.0;
-      const long long nn = (long long)n * n;
-      for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn;
-           e += (long long)gridDim.x * blockDim.x) {
-        const double2 v = A[e];
-        const double m2 = v.x * v.x + v.y * v.y;
-        if (e / n == e % n) dia += m2; else off += m2;
+      for (int row = blockIdx.x; row < n; row += gridDim.x) {
+        for (int col = threadIdx.x; col < n; col += blockDim.x) {
+          const double2 v = A[(long long)row * n + col];
+          const double m2 = v.x * v.x + v.y * v.y;
+          if (row == col) dia += m2; else off += m2;
+        }
       }
       const double so = dyn_block_sum(off, red);
       const double sd = dyn_block_sum(dia, red);
@@ -312,16 +357,16 @@ hicu_status run_nullspace(hicu_handle* h, int64_t n64, int64_t r, const double* 
   double2* Vprev = (double2*)ws_get(h, WS_EIG_VPREV, sizeof(double2) * nn, &s);
   if (s) return s;
   int grid_blocks = 0;
-  int T = (npad / 2 >= 12 * 16) ? 16 : 8;
-  const int threads = T * T;
+  const int threads = JWARPS * 32;
   {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, threads, 0) != cudaSuccess ||
         per_sm < 1)
       return set_error(h, HICU_ERR_CUDA, "nullspace: occupancy query failed");
-    const int ntile = (npad / 2 + T - 1) / T;
+    const int ntile = (npad / 2 + JT - 1) / JT;
     const long long ntiles = (long long)ntile * ntile;
-    grid_blocks = (int)std::min<long long>(ntiles, (long long)h->num_sms * std::min(per_sm, 1));
+    const long long ctas = (ntiles + JWARPS - 1) / JWARPS;
+    grid_blocks = (int)std::min<long long>(ctas, (long long)h->num_sms * std::min(per_sm, 1));
     if (grid_blocks < 1) grid_blocks = 1;
   }
   double* part = (double*)ws_get(h, WS_EIG_PART, sizeof(double) * 2 * grid_blocks + 64, &s);
@@ -333,15 +378,15 @@ hicu_status run_nullspace(hicu_handle* h, int64_t n64, int64_t r, const double* 
   const bool use_warm = warm && h->eig_have_v && h->eig_n == n;
   int blocks = (int)std::min<long long>((nn + 255) / 256, 4096);
   if (!use_warm) {
-    eig_pad_kernel<<<blocks, 256, 0, st>>>(n, npad, (const double2*)G, A0, V, 1);
+    HICU_LAUNCH(h, K_MISC, st, eig_pad_kernel<<<blocks, 256, 0, st>>>(n, npad, (const double2*)G, A0, V, 1));
   } else {
     // A0 = Vprev^H (G Vprev); V = Vprev
-    eig_pad_kernel<<<blocks, 256, 0, st>>>(n, npad, (const double2*)G, A1, V, 0);
+    HICU_LAUNCH(h, K_MISC, st, eig_pad_kernel<<<blocks, 256, 0, st>>>(n, npad, (const double2*)G, A1, V, 0));
     dim3 gg((npad + 15) / 16, (npad + 15) / 16), bb(16, 16);
     // the pad column of Vprev is the pad unit vector, so the product keeps the pad row zero
-    zgemm_kernel<<<gg, bb, 0, st>>>(npad, 0, A1, Vprev, A0);       // A0 = A Vprev
-    zgemm_kernel<<<gg, bb, 0, st>>>(npad, 1, Vprev, A0, A1);       // A1 = Vprev^H A0
-    hermitize_kernel<<<blocks, 256, 0, st>>>(npad, A1);
+    HICU_LAUNCH(h, K_MISC, st, zgemm_kernel<<<gg, bb, 0, st>>>(npad, 0, A1, Vprev, A0));  // A0 = A Vprev
+    HICU_LAUNCH(h, K_MISC, st, zgemm_kernel<<<gg, bb, 0, st>>>(npad, 1, Vprev, A0, A1));  // A1 = Vprev^H A0
+    HICU_LAUNCH(h, K_MISC, st, hermitize_kernel<<<blocks, 256, 0, st>>>(npad, A1));
     cudaMemcpyAsync(A0, A1, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(V, Vprev, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st);
   }
@@ -358,23 +403,25 @@ hicu_status run_nullspace(hicu_handle* h, int64_t n64, int64_t r, const double* 
   J.info = info;
   J.max_sweeps = 40;
   J.tol2 = 1e-26;
-  J.T = T;
   J.gs.count = h->dev_sync;
   J.gs.gen = h->dev_sync + 1;
   J.gs.err = h->dev_err;
   J.gs.nblocks = (unsigned)grid_blocks;
   J.gs.timeout_ns = 2000000000ull;  // 2 s per wait
   void* args[] = {&J};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(grid_blocks),
-                                              dim3(threads), args, 0, st);
+  cudaError_t e;
+  HICU_LAUNCH(h, K_EIG, st,
+              e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(grid_blocks), dim3(threads),
+                                              args, 0, st));
   if (e != cudaSuccess) return cuda_error(h, e, "nullspace jacobi launch");
-  eig_rank_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, npad, A0, A1, info, rank, eigvals);
-  eig_gather_q_kernel<<<blocks, 256, 0, st>>>(n, npad, n - (int)r, V, rank, (double2*)Q);
+  HICU_LAUNCH(h, K_MISC, st, eig_rank_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, npad, A0, A1, info, rank, eigvals));
+  HICU_LAUNCH(h, K_MISC, st, eig_gather_q_kernel<<<blocks, 256, 0, st>>>(n, npad, n - (int)r, V, rank, (double2*)Q));
   cudaMemcpyAsync(Vprev, V, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st);
   s = cuda_error(h, cudaGetLastError(), "nullspace output");
   if (s) return s;
   h->eig_have_v = true;
   h->eig_n = n;
+  h->eig_info = info;
   return HICU_OK;
 }
 

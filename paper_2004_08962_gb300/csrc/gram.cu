@@ -49,7 +49,7 @@ __device__ __forceinline__ void dd_acc(float a, float b, float& hi, float& lo) {
 
 __device__ __forceinline__ void dd_renorm(float& hi, float& lo) {
   const float s = __fadd_rn(hi, lo);
-  lo = __fadd_rn(lo, -__fadd_rn(s, hi));
+  lo = __fadd_rn(lo, -__fadd_rn(s, -hi));
   hi = s;
 }
 
@@ -283,11 +283,11 @@ hicu_status run_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* r
   if (nt < 64) nt = 64;
   if (nt > 256) nt = 256;
   dim3 grid((unsigned)ntasks, (unsigned)npieces);
-  gram_cells_kernel<<<grid, nt, 0, st>>>(P, part);
+  HICU_LAUNCH(h, K_GRAM, st, gram_cells_kernel<<<grid, nt, 0, st>>>(P, part));
   s = cuda_error(h, cudaGetLastError(), "gram_cells");
   if (s) return s;
   const long long nn = (long long)g.n * g.n;
-  gram_assemble_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(P, part, (double2*)G);
+  HICU_LAUNCH(h, K_GRAM, st, gram_assemble_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(P, part, (double2*)G));
   return cuda_error(h, cudaGetLastError(), "gram_assemble");
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "hicu.h"
 
@@ -130,6 +131,14 @@ struct Workspace {
 
 }  // namespace hicu
 
+// Launch a kernel through the handle's accounting (and event timing when its class is selected).
+#define HICU_LAUNCH(h, cls, st, ...)  \
+  do {                                 \
+    hicu::prof_begin((h), (cls), (st)); \
+    __VA_ARGS__;                       \
+    hicu::prof_end((h), (cls), (st));   \
+  } while (0)
+
 // The handle (opaque in the public header).
 struct hicu_handle {
   int device = 0;
@@ -142,6 +151,13 @@ struct hicu_handle {
   // warm-start state of the eigen-solver
   int64_t eig_n = 0;
   bool eig_have_v = false;
+  int* eig_info = nullptr;  // device words of the last Jacobi run (sweeps, converged, buffer)
+  // launch accounting and optional event timing of one kernel class
+  int prof_class = -1;
+  long long launches_all = 0;
+  long long launches_class = 0;
+  std::vector<cudaEvent_t> prof_events;
+  size_t prof_used = 0;
 };
 
 namespace hicu {
@@ -173,6 +189,12 @@ enum Slot {
   WS_REC_STATS,   // reconstruct: per-step stats
 };
 
+// Kernel classes for launch accounting / event timing (hicu_kernel_class in hicu.h).
+enum KClass { K_GRAM = 0, K_EIG = 1, K_CONV = 2, K_ADJOINT = 3, K_JL = 4, K_MISC = 5, K_CONV_TC = 6,
+              K_ADJOINT_TC = 7 };
+void prof_begin(hicu_handle* h, int cls, cudaStream_t st);
+void prof_end(hicu_handle* h, int cls, cudaStream_t st);
+
 hicu_status set_error(hicu_handle* h, hicu_status s, const std::string& msg);
 hicu_status cuda_error(hicu_handle* h, cudaError_t e, const char* where);
 void* ws_get(hicu_handle* h, int slot, size_t bytes, hicu_status* st);
@@ -193,11 +215,12 @@ hicu_status launch_conv_fp32(hicu_handle* h, const ConvGeom& g, KView x, const f
 hicu_status launch_adjoint_fp32(hicu_handle* h, const ConvGeom& g, const float2* R,
                                 const float2* fA, int p, int Ppad, int Cpad, MView m, KView gout,
                                 double* partial, int* nblocks, cudaStream_t st);
-hicu_status launch_sum_partials(const double* partial, int n, double* out, cudaStream_t st);
-hicu_status launch_finalize_step(const double* part, int n_obj, int n_g, int n_d, double* stats,
-                                 cudaStream_t st);
-hicu_status launch_update(const ConvGeom& g, KView y, KView gbuf, MView m, const double* stats,
-                          cudaStream_t st);
+hicu_status launch_sum_partials(hicu_handle* h, const double* partial, int n, double* out,
+                                cudaStream_t st);
+hicu_status launch_finalize_step(hicu_handle* h, const double* part, int n_obj, int n_g, int n_d,
+                                 double* stats, cudaStream_t st);
+hicu_status launch_update(hicu_handle* h, const ConvGeom& g, KView y, KView gbuf, MView m,
+                          const double* stats, cudaStream_t st);
 
 hicu_status launch_jl(hicu_handle* h, int64_t n, int64_t nr, int p, const double* Q, int mode,
                       const double* P, uint64_t seed, uint64_t counter, float* bank,
@@ -209,3 +232,11 @@ hicu_status run_nullspace(hicu_handle* h, int64_t n, int64_t r, const double* G,
                           double* eigvals, int warm, cudaStream_t st);
 
 }  // namespace hicu
+
+// Launch a kernel through the handle's accounting (and event timing when its class is selected).
+#define HICU_LAUNCH(h, cls, st, ...)  \
+  do {                                 \
+    hicu::prof_begin((h), (cls), (st)); \
+    __VA_ARGS__;                       \
+    hicu::prof_end((h), (cls), (st));   \
+  } while (0)

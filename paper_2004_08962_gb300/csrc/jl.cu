@@ -114,24 +114,25 @@ hicu_status launch_jl(hicu_handle* h, int64_t n, int64_t nr, int p, const double
     const long long tot = (long long)rows * p;
     int blocks = (int)((tot + 255) / 256);
     if (blocks > 1024) blocks = 1024;
-    jl_make_p_kernel<<<blocks, 256, 0, st>>>(rows, p, P, seed, counter, Pf);
+    HICU_LAUNCH(h, K_JL, st, jl_make_p_kernel<<<blocks, 256, 0, st>>>(rows, p, P, seed, counter, Pf));
   }
   {
     const long long tot = nr * n;
     int blocks = (int)((tot + 255) / 256);
     if (blocks > 2048) blocks = 2048;
-    to_c64_kernel<<<blocks, 256, 0, st>>>((const double2*)Q, Qf, tot);
+    HICU_LAUNCH(h, K_JL, st, to_c64_kernel<<<blocks, 256, 0, st>>>((const double2*)Q, Qf, tot));
   }
   dim3 grid((unsigned)((n + 127) / 128), (unsigned)p);
   if (mode == HICU_JL_NULLSPACE) {
-    jl_combine_real_kernel<<<grid, 128, 0, st>>>((int)n, (int)nr, p, Qf, Pf, (float2*)bank);
+    HICU_LAUNCH(h, K_JL, st, jl_combine_real_kernel<<<grid, 128, 0, st>>>((int)n, (int)nr, p, Qf, Pf, (float2*)bank));
   } else {
     float2* T = (float2*)ws_get(h, WS_T, sizeof(float2) * nr * p, &s);
     if (s) return s;
     const long long warps = nr * p;
-    jl_project_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>((int)n, (int)nr, p, Qf,
-                                                                            Pf, T);
-    jl_combine_cplx_kernel<<<grid, 128, 0, st>>>((int)n, (int)nr, p, Qf, T, (float2*)bank);
+    HICU_LAUNCH(h, K_JL, st,
+                jl_project_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>((int)n, (int)nr, p,
+                                                                                        Qf, Pf, T));
+    HICU_LAUNCH(h, K_JL, st, jl_combine_cplx_kernel<<<grid, 128, 0, st>>>((int)n, (int)nr, p, Qf, T, (float2*)bank));
   }
   return cuda_error(h, cudaGetLastError(), "jl_compress");
 }

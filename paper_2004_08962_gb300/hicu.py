@@ -21,10 +21,14 @@ HICU_JL_NULLSPACE, HICU_JL_PROJECTOR = 0, 1
 
 EXPORTED = (
     "hicu_create", "hicu_destroy", "hicu_last_error", "hicu_status_string", "hicu_check",
-    "hicu_filter_length", "hicu_num_outputs", "hicu_gram", "hicu_nullspace", "hicu_jl_compress",
+    "hicu_filter_length", "hicu_num_outputs", "hicu_gram", "hicu_nullspace", "hicu_nullspace_info",
+    "hicu_jl_compress",
     "hicu_conv_null", "hicu_conv_null_adjoint", "hicu_gd_step_filters", "hicu_gd_step",
-    "hicu_reconstruct",
+    "hicu_reconstruct", "hicu_profile_select", "hicu_profile_read",
 )
+
+HICU_K_GRAM, HICU_K_EIG, HICU_K_CONV, HICU_K_ADJOINT, HICU_K_JL, HICU_K_MISC = 0, 1, 2, 3, 4, 5
+HICU_K_CONV_TC, HICU_K_ADJOINT_TC = 6, 7
 
 
 class hicu_geom(ctypes.Structure):
@@ -79,6 +83,7 @@ def lib() -> ctypes.CDLL:
             "hicu_num_outputs": ([G, R], c_int64),
             "hicu_gram": ([P, G, R, P, P, P], c_int32),
             "hicu_nullspace": ([P, c_int64, c_int64, P, P, P, c_int32, P], c_int32),
+            "hicu_nullspace_info": ([P, POINTER(c_int32), POINTER(c_int32)], c_int32),
             "hicu_jl_compress": ([P, c_int64, c_int64, c_int32, P, c_int32, P, c_uint64, c_uint64, P, P],
                                  c_int32),
             "hicu_conv_null": ([P, G, R, P, P, c_int32, P, P, c_int32, P], c_int32),
@@ -87,6 +92,8 @@ def lib() -> ctypes.CDLL:
             "hicu_gd_step": ([P, G, R, P, P, P, c_int64, c_int32, c_int32, c_uint64, c_uint64, P, P,
                               c_int32, P], c_int32),
             "hicu_reconstruct": ([P, G, P, P, POINTER(hicu_params), P, POINTER(hicu_log), P], c_int32),
+            "hicu_profile_select": ([P, c_int32], c_int32),
+            "hicu_profile_read": ([P, POINTER(c_double), POINTER(c_int64), POINTER(c_int64)], c_int32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -171,6 +178,17 @@ def hicu_check(h: Handle, stream=None):
     h._check(lib().hicu_check(h.ptr, _stream(stream)))
 
 
+def hicu_profile_select(h: Handle, kernel_class: int = -1):
+    h._check(lib().hicu_profile_select(h.ptr, kernel_class))
+
+
+def hicu_profile_read(h: Handle):
+    """-> (ms of timed launches, timed launches, all launches) since the last select/read."""
+    ms, nc, na = c_double(), c_int64(), c_int64()
+    h._check(lib().hicu_profile_read(h.ptr, ctypes.byref(ms), ctypes.byref(nc), ctypes.byref(na)))
+    return ms.value, nc.value, na.value
+
+
 def hicu_gram(h: Handle, geom, region, x: torch.Tensor, G: Optional[torch.Tensor] = None, stream=None):
     n = hicu_filter_length(geom)
     if G is None:
@@ -187,6 +205,12 @@ def hicu_nullspace(h: Handle, G: torch.Tensor, r: int, warm: bool = False, strea
     h._check(lib().hicu_nullspace(h.ptr, n, r, _ptr(G), _ptr(Q), _ptr(eig), 1 if warm else 0,
                                   _stream(stream)))
     return Q, eig
+
+
+def hicu_nullspace_info(h: Handle):
+    sweeps, conv = c_int32(), c_int32()
+    h._check(lib().hicu_nullspace_info(h.ptr, ctypes.byref(sweeps), ctypes.byref(conv)))
+    return sweeps.value, bool(conv.value)
 
 
 def hicu_jl_compress(h: Handle, Q: torch.Tensor, p: int, mode: int = HICU_JL_NULLSPACE,

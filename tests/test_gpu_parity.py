@@ -326,7 +326,7 @@ def test_argument_errors(H):
     assert e.value.status == 2
     G = torch.zeros((100, 100), dtype=torch.complex128, device="cuda")
     with pytest.raises(hicu.HicuError) as e:
-        hicu.hicu_nullspace(H, G, 100)
+        hicu.hicu_nullspace(H, G, 0)
     assert e.value.status == 3
     with pytest.raises(hicu.HicuError) as e:
         hicu.hicu_conv_null(H, hg, hr, cuda(x), cuda(f), prec=7)
