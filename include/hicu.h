@@ -273,6 +273,37 @@ hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, const float*
                              const uint8_t* mask, const hicu_params* params, float* x_out,
                              hicu_log* log, void* stream);
 
+/* ------------------------------------------------------ allocation-free */
+
+#define HICU_NOALLOC_MAX_FILTER_WORDS 131072 /* n * (p rounded up to 16), complex64 words */
+#define HICU_NOALLOC_MAX_PARTIALS 65536      /* CTAs of the convolution grid:
+                                                ceil(sx/32) * ceil(sy/4) * sz */
+#define HICU_NOALLOC_SCRATCH_BYTES (8 * 131072 + 8 * 65536) /* 1.5 MiB static device array */
+
+/*
+ * hicu_conv_null_noalloc - the same convolution and ||R||^2 as hicu_conv_null
+ * (FP32 form), for callers that cannot allocate device memory when they call
+ * it: a host framework that already holds all free device memory in its own
+ * pool, or a latency-critical stage that cannot afford the device-wide
+ * synchronisation cudaMalloc/cudaFree may cause.  The paper has no counterpart.
+ *   No handle, no cudaMalloc/cudaFree, no allocating library call.  Scratch is
+ *   one static device array of HICU_NOALLOC_SCRATCH_BYTES that every GPU
+ *   loading the library keeps until the process exits.
+ *   Limits: n * roundup(p, 16) <= HICU_NOALLOC_MAX_FILTER_WORDS and
+ *   ceil(sx/32) * ceil(sy/4) * sz <= HICU_NOALLOC_MAX_PARTIALS; larger requests
+ *   return HICU_ERR_UNSUPPORTED (use hicu_conv_null).  Other errors: HICU_ERR_ARG,
+ *   HICU_ERR_RANK, HICU_ERR_SHAPE, HICU_ERR_CUDA (no error text without a handle).
+ *   The first call on each device (with that device current) looks up the
+ *   array's device address; make that first call before any stream capture.
+ *   All calls share the array and it keeps the previous call's contents; each
+ *   call writes every word it reads, so nothing needs clearing.  Calls that
+ *   overlap on the GPU (other streams or host threads) race on the array.
+ *   Arguments as hicu_conv_null (device pointers; R and/or objective).
+ */
+hicu_status hicu_conv_null_noalloc(const hicu_geom* geom, const hicu_region* region, const float* x,
+                                   const float* filters, int32_t p, float* R, double* objective,
+                                   void* stream);
+
 #ifdef __cplusplus
 }
 #endif

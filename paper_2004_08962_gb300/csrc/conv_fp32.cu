@@ -139,6 +139,12 @@ __global__ void __launch_bounds__(CNT) conv_fp32_kernel(ConvGeom g, KView x,
     partial[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
 }
 
+void conv_fp32_launch_shape(const ConvGeom& g, dim3* grid, dim3* block, size_t* smem) {
+  *grid = dim3((g.sx + CTX - 1) / CTX, (g.sy + CTY - 1) / CTY, g.sz);
+  *block = dim3(CNT);
+  *smem = sizeof(float2) * g.kz * (CTY + g.ky - 1) * (CTX + g.kx - 1);
+}
+
 hicu_status launch_conv_fp32(hicu_handle* h, const ConvGeom& g, KView x, const float2* fT, int p,
                              int Ppad, float2* R, double* partial, int* nblocks, cudaStream_t st) {
   dim3 grid((g.sx + CTX - 1) / CTX, (g.sy + CTY - 1) / CTY, g.sz);

@@ -212,6 +212,14 @@ int conv_ppad(int p);
 int adj_cpad(int C);
 hicu_status launch_conv_fp32(hicu_handle* h, const ConvGeom& g, KView x, const float2* fT, int p,
                              int Ppad, float2* R, double* partial, int* nblocks, cudaStream_t st);
+// Launch shape of conv_fp32_kernel (grid, block, dynamic shared memory) for a geometry.
+void conv_fp32_launch_shape(const ConvGeom& g, dim3* grid, dim3* block, size_t* smem);
+__global__ void prep_filters_kernel(ConvGeom g, const float2* __restrict__ bank, int p,
+                                    float2* __restrict__ fT, int Ppad, float2* __restrict__ fA,
+                                    int Cpad);
+__global__ void conv_fp32_kernel(ConvGeom g, KView x, const float2* __restrict__ fT, int p, int Ppad,
+                                 float2* __restrict__ R, double* __restrict__ partial);
+__global__ void sum_partials_kernel(const double* __restrict__ part, int n, double* out);
 hicu_status launch_adjoint_fp32(hicu_handle* h, const ConvGeom& g, const float2* R,
                                 const float2* fA, int p, int Ppad, int Cpad, MView m, KView gout,
                                 double* partial, int* nblocks, cudaStream_t st);

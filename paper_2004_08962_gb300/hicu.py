@@ -24,7 +24,7 @@ EXPORTED = (
     "hicu_filter_length", "hicu_num_outputs", "hicu_gram", "hicu_nullspace", "hicu_nullspace_info",
     "hicu_jl_compress",
     "hicu_conv_null", "hicu_conv_null_adjoint", "hicu_gd_step_filters", "hicu_gd_step",
-    "hicu_reconstruct", "hicu_profile_select", "hicu_profile_read",
+    "hicu_reconstruct", "hicu_profile_select", "hicu_profile_read", "hicu_conv_null_noalloc",
 )
 
 HICU_K_GRAM, HICU_K_EIG, HICU_K_CONV, HICU_K_ADJOINT, HICU_K_JL, HICU_K_MISC = 0, 1, 2, 3, 4, 5
@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
                               c_int32, P], c_int32),
             "hicu_reconstruct": ([P, G, P, P, POINTER(hicu_params), P, POINTER(hicu_log), P], c_int32),
             "hicu_profile_select": ([P, c_int32], c_int32),
+            "hicu_conv_null_noalloc": ([G, R, P, P, c_int32, P, P, P], c_int32),
             "hicu_profile_read": ([P, POINTER(c_double), POINTER(c_int64), POINTER(c_int64)], c_int32),
         }
         for name, (args, res) in sig.items():
@@ -229,6 +230,19 @@ def hicu_conv_null(h: Handle, geom, region, x: torch.Tensor, filters: torch.Tens
     obj = torch.zeros((1,), dtype=torch.float64, device=x.device) if want_objective else None
     h._check(lib().hicu_conv_null(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(x),
                                   _ptr(filters), p, _ptr(R), _ptr(obj), prec, _stream(stream)))
+    return (R, obj) if want_objective else R
+
+
+def hicu_conv_null_noalloc(geom, region, x: torch.Tensor, filters: torch.Tensor,
+                           want_objective: bool = False, stream=None):
+    """hicu_conv_null without a handle or any device allocation (static scratch)."""
+    p = filters.shape[0]
+    R = torch.empty(out_shape(geom, region) + (p,), dtype=torch.complex64, device=x.device)
+    obj = torch.zeros((1,), dtype=torch.float64, device=x.device) if want_objective else None
+    st = lib().hicu_conv_null_noalloc(ctypes.byref(geom), ctypes.byref(region), _ptr(x),
+                                      _ptr(filters), p, _ptr(R), _ptr(obj), _stream(stream))
+    if st != 0:
+        raise HicuError(st, lib().hicu_status_string(st).decode())
     return (R, obj) if want_objective else R
 
 
