@@ -150,6 +150,8 @@ hicu_status hicu_check(hicu_handle* h, void* stream);
 hicu_status hicu_profile_select(hicu_handle* h, int32_t kernel_class);
 hicu_status hicu_profile_read(hicu_handle* h, double* total_ms, int64_t* class_launches,
                               int64_t* all_launches);
+/* Jacobi sweeps run by all hicu_nullspace calls since the last read (synchronises, resets). */
+hicu_status hicu_profile_eig_sweeps(hicu_handle* h, int64_t* sweeps);
 
 /* Filter length n = C*kx*ky*kz, or -1 for an invalid geometry. */
 int64_t hicu_filter_length(const hicu_geom* geom);
@@ -171,25 +173,40 @@ int64_t hicu_num_outputs(const hicu_geom* geom, const hicu_region* region);
 hicu_status hicu_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* region,
                       const float* x, double* G, void* stream);
 
+/* flags of hicu_nullspace */
+#define HICU_NULLSPACE_WARM 1   /* start from the previous call's eigenvectors (same n) */
+#define HICU_NULLSPACE_SPLIT 2  /* stop once the top-r / bottom n-r split has converged */
+
 /*
  * hicu_nullspace - eigen-decomposition of the Hermitian n x n matrix G and the
  * null-space basis Q spanned by the eigenvectors of its n-r smallest
- * eigenvalues (Algorithm 1 steps 2-3: Q is the orthogonal complement of the r
- * principal right singular vectors of H).  FP64 parallel Jacobi on the GPU.
+ * eigenvalues (Algorithm 1 steps 2-3: Q is an orthonormal basis of the
+ * orthogonal complement of the r principal right singular vectors of H).
+ * FP64 parallel cyclic Jacobi on the GPU (one cooperative kernel, bounded grid
+ * barriers; a barrier that times out sets the handle's device error word).
  *   G       : complex128 n x n row-major, Hermitian (only read)
  *   Q       : complex128 [(n-r)][n]: null vector j is Q[j*n .. j*n+n-1],
  *             ordered by ascending eigenvalue
  *   eigvals : double [n], ascending (nullable)
+ *   flags   : HICU_NULLSPACE_WARM: start from V^H G V with V the previous
+ *             call's eigenvectors (ignored if there is none of the same n).
+ *             HICU_NULLSPACE_SPLIT: stop as soon as the coupling between the
+ *             r largest diagonal entries and the others is below 1e-11 ||G||_F
+ *             instead of waiting for every off-diagonal entry.  Q then spans
+ *             the null space to FP64 accuracy, but its vectors need not be
+ *             individual eigenvectors and the n-r smallest eigvals are diagonal
+ *             entries of a not fully diagonalised block (their sum, J of
+ *             Eq. 1, is still exact).  Algorithm 1 step 3 needs only the span.
  * Eigenvectors are unique only up to a unit phase (and rotations inside
- * repeated eigenvalues).  If `warm` is nonzero and the previous call on this
- * handle had the same n, its eigenvectors seed the iteration.
+ * repeated eigenvalues).
  */
 hicu_status hicu_nullspace(hicu_handle* h, int64_t n, int64_t r, const double* G, double* Q,
-                           double* eigvals, int32_t warm, void* stream);
+                           double* eigvals, int32_t flags, void* stream);
 
 /*
- * hicu_nullspace_info - sweeps used and convergence flag of the last
- * hicu_nullspace call on this handle (synchronises the device).
+ * hicu_nullspace_info - sweeps used by the last hicu_nullspace call on this
+ * handle and how it converged: 0 = not within the sweep limit, 1 = full
+ * decomposition, 2 = split criterion (synchronises the device).
  */
 hicu_status hicu_nullspace_info(hicu_handle* h, int32_t* sweeps, int32_t* converged);
 

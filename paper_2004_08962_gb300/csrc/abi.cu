@@ -250,6 +250,17 @@ extern "C" hicu_status hicu_profile_read(hicu_handle* h, double* total_ms, int64
   return HICU_OK;
 }
 
+extern "C" hicu_status hicu_profile_eig_sweeps(hicu_handle* h, int64_t* sweeps) {
+  if (!h || !sweeps) return HICU_ERR_ARG;
+  unsigned long long v = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&v, h->dev_err + 8, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(h->dev_err + 8, 0, sizeof(v));
+  if (e != cudaSuccess) return cuda_error(h, e, "profile_eig_sweeps");
+  *sweeps = (int64_t)v;
+  return HICU_OK;
+}
+
 extern "C" int64_t hicu_filter_length(const hicu_geom* geom) {
   if (!geom_ok(geom)) return -1;
   return (int64_t)geom->ncoil * geom->k[0] * geom->k[1] * geom->k[2];
@@ -271,21 +282,22 @@ extern "C" hicu_status hicu_gram(hicu_handle* h, const hicu_geom* geom, const hi
 }
 
 extern "C" hicu_status hicu_nullspace(hicu_handle* h, int64_t n, int64_t r, const double* G,
-                                      double* Q, double* eigvals, int32_t warm, void* stream) {
+                                      double* Q, double* eigvals, int32_t flags, void* stream) {
   if (!h) return HICU_ERR_ARG;
   if (!G || !Q) return set_error(h, HICU_ERR_ARG, "nullspace: null pointer");
-  return run_nullspace(h, n, r, G, Q, eigvals, warm, (cudaStream_t)stream);
+  if (flags & ~3) return set_error(h, HICU_ERR_ARG, "nullspace: unknown flags");
+  return run_nullspace(h, n, r, G, Q, eigvals, flags, (cudaStream_t)stream);
 }
 
 extern "C" hicu_status hicu_nullspace_info(hicu_handle* h, int32_t* sweeps, int32_t* converged) {
   if (!h || !sweeps || !converged) return HICU_ERR_ARG;
   if (!h->eig_info) return set_error(h, HICU_ERR_ARG, "nullspace_info: no eigen-decomposition yet");
-  int info[3] = {0, 0, 0};
+  int info[4] = {0, 0, 0, 0};
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(info, h->eig_info, sizeof(info), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_error(h, e, "nullspace_info");
   *sweeps = info[0];
-  *converged = info[1];
+  *converged = info[1] ? (info[3] == 1 ? 2 : 1) : 0;
   return HICU_OK;
 }
 
@@ -591,7 +603,9 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
       const hicu_region& greg = prm->gram_on_current ? stg.region : prev;
       s = run_gram(h, geom, &greg, y, G, st);
       if (s) return s;
-      s = run_nullspace(h, n, r, G, Q, eig, it > 0 ? 1 : 0, st);
+      // after the first outer iteration: warm start, and stop at the top-r / rest split (step 3
+      // needs an orthonormal basis of the complement of the r principal vectors, nothing more)
+      s = run_nullspace(h, n, r, G, Q, eig, it > 0 ? (HICU_NULLSPACE_WARM | HICU_NULLSPACE_SPLIT) : 0, st);
       if (s) return s;
       HICU_LAUNCH(h, K_MISC, st, tail_sum_kernel<<<1, 256, 0, st>>>(eig, (int)nr, dlog + it));
       for (int j = 0; j < stg.gd_steps; ++j) {

@@ -98,9 +98,15 @@ struct JacArgs {
   double2* A1;
   double2* V;
   double* part;  // 2 doubles per CTA
-  int* info;     // [0] sweeps, [1] converged, [2] buffer holding the result
+  int* info;     // [0] sweeps, [1] converged, [2] buffer holding the result, [3] final mode
   int max_sweeps;
   double tol2;
+  int mode;     // 0: stop when all off-diagonal mass is small; 1: stop when the coupling
+                // between the r largest diagonal entries and the rest is small
+  int nreal;    // n without the pad index
+  int r;
+  int* rankd;   // mode 1: descending rank of each diagonal entry (nreal ints)
+  unsigned long long* sweep_total;  // running count of sweeps over all calls (tracing)
   GridSync gs;
 };
 
@@ -134,7 +140,6 @@ __device__ __forceinline__ double2 lin(double s, double2 a, double t, double2 b)
 
 __global__ void __launch_bounds__(JWARPS * 32) jacobi_kernel(JacArgs J) {
   __shared__ Rot rp[JWARPS][JT], rq[JWARPS][JT];
-  __shared__ int ip[JWARPS][JT], iq[JWARPS][JT], jp[JWARPS][JT], jq[JWARPS][JT];
   __shared__ double red[8];
   __shared__ int s_done;
   const int n = J.n, np = n / 2;
@@ -144,68 +149,76 @@ __global__ void __launch_bounds__(JWARPS * 32) jacobi_kernel(JacArgs J) {
   const long long gw = (long long)blockIdx.x * JWARPS + warp;
   const long long nw = (long long)gridDim.x * JWARPS;
   int cur = 0;
+  const int mode = J.mode;
   for (int sweep = 0; sweep < J.max_sweeps; ++sweep) {
     for (int t = 0; t < n - 1; ++t) {
       const double2* A = cur ? J.A1 : J.A0;
       double2* B = cur ? J.A0 : J.A1;
       for (long long tile = gw; tile < ntiles; tile += nw) {
         const int tp = (int)(tile / ntile), tq = (int)(tile % ntile);
-        __syncwarp();
-        if (lane < 2 * JT) {
-          const int side = lane / JT, i = lane % JT;
-          const int P = (side == 0 ? tp : tq) * JT + i;
-          if (P < np) {
-            int p, q;
-            pair_of(n, t, P, p, q);
-            const Rot R = make_rot(A[(long long)p * n + p].x, A[(long long)q * n + q].x,
-                                   A[(long long)p * n + q]);
-            if (side == 0) { rp[warp][i] = R; ip[warp][i] = p; iq[warp][i] = q; }
-            else { rq[warp][i] = R; jp[warp][i] = p; jq[warp][i] = q; }
-          }
-        }
-        __syncwarp();
+        // this lane's block (i, j) and column/row `sub`; issue its loads before the rotations
         const int blk = lane >> 1, sub = lane & 1;
         const int i = blk / JT, j = blk % JT;
         const int P = tp * JT + i, Q = tq * JT + j;
-        if (P < np && Q < np) {
-          const int p1 = ip[warp][i], q1 = iq[warp][i], p2 = jp[warp][j], q2 = jq[warp][j];
+        const bool valid = P < np && Q < np;
+        int p1 = 0, q1 = 0, p2 = 0, q2 = 0;
+        double2 a00, a01, a10, a11, v0, v1;
+        if (valid) {
+          pair_of(n, t, P, p1, q1);
+          pair_of(n, t, Q, p2, q2);
+          a00 = A[(long long)p1 * n + p2];
+          a01 = A[(long long)p1 * n + q2];
+          a10 = A[(long long)q1 * n + p2];
+          a11 = A[(long long)q1 * n + q2];
+          const long long row = (long long)(sub ? q1 : p1) * n;
+          v0 = J.V[row + p2];
+          v1 = J.V[row + q2];
+        }
+        __syncwarp();
+        if (lane < 2 * JT) {
+          const int side = lane / JT, ii = lane % JT;
+          const int PP = (side == 0 ? tp : tq) * JT + ii;
+          if (PP < np) {
+            int p, q;
+            pair_of(n, t, PP, p, q);
+            const Rot R = make_rot(A[(long long)p * n + p].x, A[(long long)q * n + q].x,
+                                   A[(long long)p * n + q]);
+            if (side == 0) rp[warp][ii] = R; else rq[warp][ii] = R;
+          }
+        }
+        __syncwarp();
+        if (valid) {
           const Rot wq = rq[warp][j];
           const Rot wp = rp[warp][i];
-          // pass 1: column `sub` of the new block
-          {
-            const double2 a00 = A[(long long)p1 * n + p2], a01 = A[(long long)p1 * n + q2];
-            const double2 a10 = A[(long long)q1 * n + p2], a11 = A[(long long)q1 * n + q2];
-            double2 b0, b1;
-            if (wp.ident && wq.ident) {
-              b0 = sub ? a01 : a00;
-              b1 = sub ? a11 : a10;
+          double2 b0, b1;
+          if (wp.ident && wq.ident) {
+            b0 = sub ? a01 : a00;
+            b1 = sub ? a11 : a10;
+          } else {
+            // M = A_blk W_Q: m_r0 = cs a_r0 - sn (a_r1 e), m_r1 = sn a_r0 + cs (a_r1 e)
+            const double2 u0 = cmul_e(a01, wq.ex, wq.ey), u1 = cmul_e(a11, wq.ex, wq.ey);
+            double2 m0, m1;
+            if (sub == 0) {
+              m0 = lin(wq.cs, a00, -wq.sn, u0);
+              m1 = lin(wq.cs, a10, -wq.sn, u1);
             } else {
-              // M = A_blk W_Q: m_r0 = cs a_r0 - sn (a_r1 e), m_r1 = sn a_r0 + cs (a_r1 e)
-              const double2 u0 = cmul_e(a01, wq.ex, wq.ey), u1 = cmul_e(a11, wq.ex, wq.ey);
-              double2 m0, m1;
-              if (sub == 0) {
-                m0 = lin(wq.cs, a00, -wq.sn, u0);
-                m1 = lin(wq.cs, a10, -wq.sn, u1);
-              } else {
-                m0 = lin(wq.sn, a00, wq.cs, u0);
-                m1 = lin(wq.sn, a10, wq.cs, u1);
-              }
-              // B = W_P^H M: b_0 = cs m0 - sn conj(e) m1, b_1 = sn m0 + cs conj(e) m1
-              const double2 v = cmul_ce(m1, wp.ex, wp.ey);
-              b0 = lin(wp.cs, m0, -wp.sn, v);
-              b1 = lin(wp.sn, m0, wp.cs, v);
+              m0 = lin(wq.sn, a00, wq.cs, u0);
+              m1 = lin(wq.sn, a10, wq.cs, u1);
             }
-            if (P == Q) {  // diagonal entries of a Hermitian matrix are real
-              if (sub == 0) b0.y = 0.0; else b1.y = 0.0;
-            }
-            const int col = sub ? q2 : p2;
-            B[(long long)p1 * n + col] = b0;
-            B[(long long)q1 * n + col] = b1;
+            // B = W_P^H M: b_0 = cs m0 - sn conj(e) m1, b_1 = sn m0 + cs conj(e) m1
+            const double2 v = cmul_ce(m1, wp.ex, wp.ey);
+            b0 = lin(wp.cs, m0, -wp.sn, v);
+            b1 = lin(wp.sn, m0, wp.cs, v);
           }
-          // pass 2: row `sub` (p1 or q1) of V on columns (p2, q2): V <- V W_Q
+          if (P == Q) {  // diagonal entries of a Hermitian matrix are real
+            if (sub == 0) b0.y = 0.0; else b1.y = 0.0;
+          }
+          const int col = sub ? q2 : p2;
+          B[(long long)p1 * n + col] = b0;
+          B[(long long)q1 * n + col] = b1;
+          // row `sub` (p1 or q1) of V on columns (p2, q2): V <- V W_Q
           if (!wq.ident) {
             const long long row = (long long)(sub ? q1 : p1) * n;
-            const double2 v0 = J.V[row + p2], v1 = J.V[row + q2];
             const double2 u = cmul_e(v1, wq.ex, wq.ey);
             J.V[row + p2] = lin(wq.cs, v0, -wq.sn, u);
             J.V[row + q2] = lin(wq.sn, v0, wq.cs, u);
@@ -215,22 +228,41 @@ __global__ void __launch_bounds__(JWARPS * 32) jacobi_kernel(JacArgs J) {
       if (!grid_sync(J.gs)) return;
       cur ^= 1;
     }
-    // convergence test on the current matrix
+    // convergence test: all off-diagonal mass (mode 0) or the coupling between the r
+    // largest diagonal entries and the others (mode 1)
     {
       const double2* A = cur ? J.A1 : J.A0;
-      double off = 0.0, dia = 0.0;
+      if (mode == 1) {
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < J.nreal; i += gridDim.x * blockDim.x) {
+          const double di = A[(long long)i * n + i].x;
+          int rk = 0;
+          for (int j = 0; j < J.nreal; ++j) {
+            const double dj = A[(long long)j * n + j].x;
+            rk += (dj > di) || (dj == di && j < i);
+          }
+          J.rankd[i] = rk;
+        }
+        if (!grid_sync(J.gs)) return;
+      }
+      double off = 0.0, tot = 0.0;
       for (int row = blockIdx.x; row < n; row += gridDim.x) {
+        const bool top_row = (mode == 1 && row < J.nreal) ? (J.rankd[row] < J.r) : false;
         for (int col = threadIdx.x; col < n; col += blockDim.x) {
           const double2 v = A[(long long)row * n + col];
           const double m2 = v.x * v.x + v.y * v.y;
-          if (row == col) dia += m2; else off += m2;
+          tot += m2;
+          if (mode == 0) {
+            if (row != col) off += m2;
+          } else if (row < J.nreal && col < J.nreal && top_row != (J.rankd[col] < J.r)) {
+            off += m2;
+          }
         }
       }
       const double so = dyn_block_sum(off, red);
-      const double sd = dyn_block_sum(dia, red);
+      const double st = dyn_block_sum(tot, red);
       if (threadIdx.x == 0) {
         J.part[2 * blockIdx.x] = so;
-        J.part[2 * blockIdx.x + 1] = sd;
+        J.part[2 * blockIdx.x + 1] = st;
       }
       if (!grid_sync(J.gs)) return;
       if (threadIdx.x == 0) {
@@ -239,18 +271,23 @@ __global__ void __launch_bounds__(JWARPS * 32) jacobi_kernel(JacArgs J) {
           o += J.part[2 * b];
           d += J.part[2 * b + 1];
         }
-        const int done = (o <= J.tol2 * (o + d)) ? 1 : 0;
+        const int done = (o <= J.tol2 * d) ? 1 : 0;
         s_done = done || !(o == o);
         if (blockIdx.x == 0) {
           J.info[0] = sweep + 1;
           J.info[1] = done;
           J.info[2] = cur;
+          J.info[3] = mode;
         }
       }
       __syncthreads();
-      if (s_done) return;
+      if (s_done) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(J.sweep_total, (unsigned long long)(sweep + 1));
+        return;
+      }
     }
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(J.sweep_total, (unsigned long long)J.max_sweeps);
 }
 
 // A (npad x npad) <- G (n x n, row-major) padded with a zero row and column when n
@@ -341,7 +378,7 @@ __global__ void eig_gather_q_kernel(int n, int npad, int nr, const double2* __re
 }
 
 hicu_status run_nullspace(hicu_handle* h, int64_t n64, int64_t r, const double* G, double* Q,
-                          double* eigvals, int warm, cudaStream_t st) {
+                          double* eigvals, int flags, cudaStream_t st) {
   if (n64 < 2 || n64 > 4096) return set_error(h, HICU_ERR_SHAPE, "nullspace: n must be in [2, 4096]");
   if (r <= 0 || r >= n64) return set_error(h, HICU_ERR_RANK, "nullspace: rank must satisfy 0 < r < n");
   const int n = (int)n64;
@@ -372,10 +409,11 @@ hicu_status run_nullspace(hicu_handle* h, int64_t n64, int64_t r, const double* 
   double* part = (double*)ws_get(h, WS_EIG_PART, sizeof(double) * 2 * grid_blocks + 64, &s);
   if (s) return s;
   int* info = (int*)(part + 2 * grid_blocks);
-  int* rank = (int*)ws_get(h, WS_EIG_TMP, sizeof(int) * npad, &s);
+  int* rank = (int*)ws_get(h, WS_EIG_TMP, sizeof(int) * 2 * npad, &s);
   if (s) return s;
+  int* rankd = rank + npad;
 
-  const bool use_warm = warm && h->eig_have_v && h->eig_n == n;
+  const bool use_warm = (flags & 1) && h->eig_have_v && h->eig_n == n;
   int blocks = (int)std::min<long long>((nn + 255) / 256, 4096);
   if (!use_warm) {
     HICU_LAUNCH(h, K_MISC, st, eig_pad_kernel<<<blocks, 256, 0, st>>>(n, npad, (const double2*)G, A0, V, 1));
@@ -393,7 +431,7 @@ hicu_status run_nullspace(hicu_handle* h, int64_t n64, int64_t r, const double* 
   s = cuda_error(h, cudaGetLastError(), "nullspace prep");
   if (s) return s;
   cudaMemsetAsync(h->dev_sync, 0, 2 * sizeof(unsigned), st);
-  cudaMemsetAsync(info, 0, 4 * sizeof(int), st);
+  cudaMemsetAsync(info, 0, 8 * sizeof(int), st);
   JacArgs J;
   J.n = npad;
   J.A0 = A0;
@@ -402,7 +440,12 @@ hicu_status run_nullspace(hicu_handle* h, int64_t n64, int64_t r, const double* 
   J.part = part;
   J.info = info;
   J.max_sweeps = 40;
-  J.tol2 = 1e-26;
+  J.tol2 = 1e-22;  // off-diagonal (or coupling) mass <= (1e-11 ||A||_F)^2
+  J.mode = (flags & 2) ? 1 : 0;
+  J.nreal = n;
+  J.r = (int)r;
+  J.rankd = rankd;
+  J.sweep_total = reinterpret_cast<unsigned long long*>(h->dev_err + 8);
   J.gs.count = h->dev_sync;
   J.gs.gen = h->dev_sync + 1;
   J.gs.err = h->dev_err;

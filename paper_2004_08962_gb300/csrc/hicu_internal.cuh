@@ -237,7 +237,7 @@ hicu_status launch_jl(hicu_handle* h, int64_t n, int64_t nr, int p, const double
 hicu_status run_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* reg, const float* x,
                      double* G, cudaStream_t st);
 hicu_status run_nullspace(hicu_handle* h, int64_t n, int64_t r, const double* G, double* Q,
-                          double* eigvals, int warm, cudaStream_t st);
+                          double* eigvals, int flags, cudaStream_t st);
 
 }  // namespace hicu
 

@@ -25,6 +25,7 @@ EXPORTED = (
     "hicu_jl_compress",
     "hicu_conv_null", "hicu_conv_null_adjoint", "hicu_gd_step_filters", "hicu_gd_step",
     "hicu_reconstruct", "hicu_profile_select", "hicu_profile_read", "hicu_conv_null_noalloc",
+    "hicu_profile_eig_sweeps",
 )
 
 HICU_K_GRAM, HICU_K_EIG, HICU_K_CONV, HICU_K_ADJOINT, HICU_K_JL, HICU_K_MISC = 0, 1, 2, 3, 4, 5
@@ -94,6 +95,7 @@ def lib() -> ctypes.CDLL:
             "hicu_reconstruct": ([P, G, P, P, POINTER(hicu_params), P, POINTER(hicu_log), P], c_int32),
             "hicu_profile_select": ([P, c_int32], c_int32),
             "hicu_conv_null_noalloc": ([G, R, P, P, c_int32, P, P, P], c_int32),
+            "hicu_profile_eig_sweeps": ([P, POINTER(c_int64)], c_int32),
             "hicu_profile_read": ([P, POINTER(c_double), POINTER(c_int64), POINTER(c_int64)], c_int32),
         }
         for name, (args, res) in sig.items():
@@ -190,6 +192,12 @@ def hicu_profile_read(h: Handle):
     return ms.value, nc.value, na.value
 
 
+def hicu_profile_eig_sweeps(h: Handle) -> int:
+    v = c_int64()
+    h._check(lib().hicu_profile_eig_sweeps(h.ptr, ctypes.byref(v)))
+    return v.value
+
+
 def hicu_gram(h: Handle, geom, region, x: torch.Tensor, G: Optional[torch.Tensor] = None, stream=None):
     n = hicu_filter_length(geom)
     if G is None:
@@ -199,19 +207,24 @@ def hicu_gram(h: Handle, geom, region, x: torch.Tensor, G: Optional[torch.Tensor
     return G
 
 
-def hicu_nullspace(h: Handle, G: torch.Tensor, r: int, warm: bool = False, stream=None):
+HICU_NULLSPACE_WARM, HICU_NULLSPACE_SPLIT = 1, 2
+
+
+def hicu_nullspace(h: Handle, G: torch.Tensor, r: int, warm: bool = False, split: bool = False,
+                   stream=None):
     n = G.shape[0]
     Q = torch.empty((n - r, n), dtype=torch.complex128, device=G.device)
     eig = torch.empty((n,), dtype=torch.float64, device=G.device)
-    h._check(lib().hicu_nullspace(h.ptr, n, r, _ptr(G), _ptr(Q), _ptr(eig), 1 if warm else 0,
-                                  _stream(stream)))
+    flags = (HICU_NULLSPACE_WARM if warm else 0) | (HICU_NULLSPACE_SPLIT if split else 0)
+    h._check(lib().hicu_nullspace(h.ptr, n, r, _ptr(G), _ptr(Q), _ptr(eig), flags, _stream(stream)))
     return Q, eig
 
 
 def hicu_nullspace_info(h: Handle):
+    """-> (sweeps, how): how = 0 not converged, 1 full decomposition, 2 split criterion."""
     sweeps, conv = c_int32(), c_int32()
     h._check(lib().hicu_nullspace_info(h.ptr, ctypes.byref(sweeps), ctypes.byref(conv)))
-    return sweeps.value, bool(conv.value)
+    return sweeps.value, conv.value
 
 
 def hicu_jl_compress(h: Handle, Q: torch.Tensor, p: int, mode: int = HICU_JL_NULLSPACE,

@@ -173,6 +173,31 @@ def test_nullspace_parity_phantom(H):
     _nullspace_check(Q2.cpu().numpy(), eig2.cpu().numpy(), G2, pb.rank)
 
 
+def test_nullspace_split_mode_matches_oracle_subspace(H):
+    """Warm split mode: same null space and the same J (Eq. 1) as LAPACK, not eigenvectors."""
+    from paper_2004_08962_gb300 import hicu
+    pb = make_problem("2d_small_64")
+    og = O.Geom(pb.dims, pb.ncoil, pb.kernel)
+    G = O.gram(pb.x0.astype(np.complex128), og, O.full_region(og))
+    hicu.hicu_nullspace(H, cuda(G), pb.rank)                     # cold: seeds the warm start
+    rng = np.random.default_rng(12)
+    E = random_complex(rng, G.shape)
+    G2 = G + (E + E.conj().T) * 1e-4 * np.abs(G).max()
+    Q, eig = hicu.hicu_nullspace(H, cuda(G2), pb.rank, warm=True, split=True)
+    sweeps, how = hicu.hicu_nullspace_info(H)
+    assert how == 2, (sweeps, how)
+    Q = Q.cpu().numpy().T
+    n, r = G.shape[0], pb.rank
+    w, V = np.linalg.eigh(G2)
+    np.testing.assert_allclose(Q.conj().T @ Q, np.eye(n - r), atol=1e-12)
+    Qo = V[:, : n - r]
+    gap = w[n - r] - w[n - r - 1]
+    dist = np.linalg.norm(Q @ Q.conj().T - Qo @ Qo.conj().T)
+    assert dist < 1e-11 * w[-1] / gap * np.sqrt(n) + 1e-10
+    J = eig.cpu().numpy()[: n - r].sum()
+    assert abs(J - w[: n - r].sum()) < 1e-11 * w[-1] * n
+
+
 def test_nullspace_odd_n_lowrank(H):
     from paper_2004_08962_gb300 import hicu
     rng = np.random.default_rng(4)
