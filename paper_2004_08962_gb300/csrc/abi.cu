@@ -335,9 +335,14 @@ hicu_status prep_filters(hicu_handle* h, const ConvGeom& g, const float* bank, i
 }
 
 hicu_status check_prec(hicu_handle* h, int32_t prec) {
-  if (prec == HICU_FP32) return HICU_OK;
-  if (prec == HICU_SPLIT_BF16) return set_error(h, HICU_ERR_UNSUPPORTED, "split-bf16 path not built in");
+  if (prec == HICU_FP32 || prec == HICU_SPLIT_BF16) return HICU_OK;
   return set_error(h, HICU_ERR_ARG, "unknown precision");
+}
+
+hicu_status check_tc(hicu_handle* h, const ConvGeom& g) {
+  if (tc_supported(g)) return HICU_OK;
+  return set_error(h, HICU_ERR_UNSUPPORTED,
+                   "split-bf16 path needs a 2D valid geometry (kz = 1, no circular axis) with C % 4 == 0");
 }
 
 }  // namespace
@@ -354,6 +359,27 @@ extern "C" hicu_status hicu_conv_null(hicu_handle* h, const hicu_geom* geom, con
   s = make_conv_geom(h, geom, region, &g);
   if (s) return s;
   cudaStream_t st = (cudaStream_t)stream;
+  if (prec == HICU_SPLIT_BF16) {
+    s = check_tc(h, g);
+    if (s) return s;
+    uint4* xpl = (uint4*)ws_get(h, WS_TC_X, sizeof(uint4) * 2 * (size_t)(g.C / 4) * g.ex * g.ey, &s);
+    if (s) return s;
+    void* bw = ws_get(h, WS_TC_BC, tc_b_bytes(g, p, 0), &s);
+    if (s) return s;
+    int nb = 0;
+    s = launch_conv_tc(h, g, nullptr, nullptr, p, nullptr, nullptr, nullptr, &nb, st);
+    if (s) return s;
+    double* part = (double*)ws_get(h, WS_PART, sizeof(double) * nb, &s);
+    if (s) return s;
+    s = tc_prepare_weights(h, g, (const float2*)filters, p, 0, bw, st);
+    if (s) return s;
+    s = tc_prepare_input(h, g, full_view(geom, region, const_cast<float*>(x)), xpl, st);
+    if (s) return s;
+    s = launch_conv_tc(h, g, xpl, bw, p, (float2*)R, nullptr, part, &nb, st);
+    if (s) return s;
+    if (objective) return launch_sum_partials(h, part, nb, objective, st);
+    return HICU_OK;
+  }
   StepBuffers b;
   s = prep_filters(h, g, filters, p, true, false, &b, st);
   if (s) return s;
@@ -383,12 +409,33 @@ extern "C" hicu_status hicu_conv_null_adjoint(hicu_handle* h, const hicu_geom* g
   s = make_conv_geom(h, geom, region, &g);
   if (s) return s;
   cudaStream_t st = (cudaStream_t)stream;
+  KView gv = full_view(geom, region, gout);
+  MView mv = mask_view(geom, region, mask);
+  if (prec == HICU_SPLIT_BF16) {
+    s = check_tc(h, g);
+    if (s) return s;
+    uint4* rpl = (uint4*)ws_get(h, WS_TC_R, sizeof(uint4) * 2 * (size_t)((p + 3) / 4) * g.s, &s);
+    if (s) return s;
+    void* bw = ws_get(h, WS_TC_BA, tc_b_bytes(g, p, 1), &s);
+    if (s) return s;
+    int nb = 0;
+    s = launch_adjoint_tc(h, g, nullptr, nullptr, p, mv, gv, nullptr, &nb, st);
+    if (s) return s;
+    double* part = (double*)ws_get(h, WS_PART, sizeof(double) * nb, &s);
+    if (s) return s;
+    s = tc_prepare_weights(h, g, (const float2*)filters, p, 1, bw, st);
+    if (s) return s;
+    s = tc_prepare_r(h, g, (const float2*)R, p, rpl, st);
+    if (s) return s;
+    s = launch_adjoint_tc(h, g, rpl, bw, p, mv, gv, part, &nb, st);
+    if (s) return s;
+    if (gnorm2) return launch_sum_partials(h, part, nb, gnorm2, st);
+    return HICU_OK;
+  }
   StepBuffers b;
   s = prep_filters(h, g, filters, p, false, true, &b, st);
   if (s) return s;
   int nb = 0;
-  KView gv = full_view(geom, region, gout);
-  MView mv = mask_view(geom, region, mask);
   launch_adjoint_fp32(h, g, (const float2*)R, b.fA, p, b.Ppad, b.Cpad, mv, gv, nullptr, &nb, st);
   double* part = (double*)ws_get(h, WS_PART, sizeof(double) * nb, &s);
   if (s) return s;
@@ -400,6 +447,54 @@ extern "C" hicu_status hicu_conv_null_adjoint(hicu_handle* h, const hicu_geom* g
 
 namespace hicu {
 
+// Split-bf16 tensor-core descent step: conv of y (R kept only as split bf16 planes), masked adjoint,
+// conv of g reduced to D, then the same line search and update as the FP32 form.
+static hicu_status gd_step_filters_tc(hicu_handle* h, const hicu_geom* geom, const hicu_region* region,
+                                      const ConvGeom& g, float* y, const uint8_t* mask, const float* filters,
+                                      int p, double* stats, cudaStream_t st) {
+  hicu_status s = check_tc(h, g);
+  if (s) return s;
+  const size_t xbytes = sizeof(uint4) * 2 * (size_t)(g.C / 4) * g.ex * g.ey;
+  uint4* xpl = (uint4*)ws_get(h, WS_TC_X, xbytes, &s);
+  if (s) return s;
+  uint4* gpl = (uint4*)ws_get(h, WS_TC_G, xbytes, &s);
+  if (s) return s;
+  uint4* rpl = (uint4*)ws_get(h, WS_TC_R, sizeof(uint4) * 2 * (size_t)((p + 3) / 4) * g.s, &s);
+  if (s) return s;
+  void* bwc = ws_get(h, WS_TC_BC, tc_b_bytes(g, p, 0), &s);
+  if (s) return s;
+  void* bwa = ws_get(h, WS_TC_BA, tc_b_bytes(g, p, 1), &s);
+  if (s) return s;
+  float2* gb = (float2*)ws_get(h, WS_G, sizeof(float2) * (size_t)g.C * g.ex * g.ey * g.ez, &s);
+  if (s) return s;
+  double* st4 = stats;
+  if (!st4) {
+    st4 = (double*)ws_get(h, WS_STATS, sizeof(double) * 8, &s);
+    if (s) return s;
+  }
+  const KView yv = full_view(geom, region, y);
+  const KView gview = region_view(g, gb);
+  const MView mv = mask_view(geom, region, mask);
+  int n1 = 0, n2 = 0, n3 = 0;
+  s = launch_conv_tc(h, g, nullptr, nullptr, p, nullptr, nullptr, nullptr, &n1, st);
+  if (s) return s;
+  s = launch_adjoint_tc(h, g, nullptr, nullptr, p, mv, gview, nullptr, &n2, st);
+  if (s) return s;
+  n3 = n1;
+  double* part = (double*)ws_get(h, WS_PART, sizeof(double) * (n1 + n2 + n3), &s);
+  if (s) return s;
+  if ((s = tc_prepare_weights(h, g, (const float2*)filters, p, 0, bwc, st))) return s;
+  if ((s = tc_prepare_weights(h, g, (const float2*)filters, p, 1, bwa, st))) return s;
+  if ((s = tc_prepare_input(h, g, yv, xpl, st))) return s;
+  if ((s = launch_conv_tc(h, g, xpl, bwc, p, nullptr, rpl, part, &n1, st))) return s;
+  if ((s = launch_adjoint_tc(h, g, rpl, bwa, p, mv, gview, part + n1, &n2, st))) return s;
+  if ((s = tc_prepare_input(h, g, gview, gpl, st))) return s;
+  if ((s = launch_conv_tc(h, g, gpl, bwc, p, nullptr, nullptr, part + n1 + n2, &n3, st))) return s;
+  if ((s = launch_finalize_step(h, part, n1, n2, n3, st4, st))) return cuda_error(h, cudaGetLastError(), "finalize");
+  if ((s = launch_update(h, g, yv, gview, mv, st4, st))) return cuda_error(h, cudaGetLastError(), "update");
+  return HICU_OK;
+}
+
 // One descent step for a fixed bank (Algorithm 1 steps 7-8).
 hicu_status gd_step_filters(hicu_handle* h, const hicu_geom* geom, const hicu_region* region, float* y,
                             const uint8_t* mask, const float* filters, int32_t p, double* stats,
@@ -409,6 +504,7 @@ hicu_status gd_step_filters(hicu_handle* h, const hicu_geom* geom, const hicu_re
   ConvGeom g;
   s = make_conv_geom(h, geom, region, &g);
   if (s) return s;
+  if (prec == HICU_SPLIT_BF16) return gd_step_filters_tc(h, geom, region, g, y, mask, filters, p, stats, st);
   StepBuffers b;
   s = prep_filters(h, g, filters, p, true, true, &b, st);
   if (s) return s;

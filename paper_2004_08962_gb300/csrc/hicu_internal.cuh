@@ -144,7 +144,7 @@ struct hicu_handle {
   int device = 0;
   int num_sms = 0;
   std::string last_error;
-  static constexpr int kSlots = 24;
+  static constexpr int kSlots = 32;
   hicu::Workspace ws[kSlots];
   int* dev_err = nullptr;          // device error word
   unsigned* dev_sync = nullptr;    // grid-barrier words (count, gen)
@@ -187,6 +187,11 @@ enum Slot {
   WS_REC_M,       // reconstruct: staged mask
   WS_REC_LOG,     // reconstruct: device log
   WS_REC_STATS,   // reconstruct: per-step stats
+  WS_TC_X,        // split bf16 planes of the region input
+  WS_TC_G,        // split bf16 planes of the gradient
+  WS_TC_R,        // split bf16 planes of R
+  WS_TC_BC,       // tensor-core B planes, conv
+  WS_TC_BA,       // tensor-core B planes, adjoint
 };
 
 // Kernel classes for launch accounting / event timing (hicu_kernel_class in hicu.h).
@@ -229,6 +234,19 @@ hicu_status launch_finalize_step(hicu_handle* h, const double* part, int n_obj, 
                                  double* stats, cudaStream_t st);
 hicu_status launch_update(hicu_handle* h, const ConvGeom& g, KView y, KView gbuf, MView m,
                           const double* stats, cudaStream_t st);
+
+// tensor-core (split-bf16) path, 2D valid convolutions with C % 4 == 0
+bool tc_supported(const ConvGeom& g);
+size_t tc_b_bytes(const ConvGeom& g, int p, int mode);
+hicu_status tc_prepare_weights(hicu_handle* h, const ConvGeom& g, const float2* bank, int p, int mode,
+                               void* out, cudaStream_t st);
+hicu_status tc_prepare_input(hicu_handle* h, const ConvGeom& g, KView x, uint4* planar, cudaStream_t st);
+hicu_status tc_prepare_r(hicu_handle* h, const ConvGeom& g, const float2* R, int p, uint4* planar,
+                         cudaStream_t st);
+hicu_status launch_conv_tc(hicu_handle* h, const ConvGeom& g, const uint4* xplanar, const void* bw, int p,
+                           float2* R, uint4* Rs, double* partial, int* nblocks, cudaStream_t st);
+hicu_status launch_adjoint_tc(hicu_handle* h, const ConvGeom& g, const uint4* Rs, const void* bw, int p,
+                              MView m, KView gout, double* partial, int* nblocks, cudaStream_t st);
 
 hicu_status launch_jl(hicu_handle* h, int64_t n, int64_t nr, int p, const double* Q, int mode,
                       const double* P, uint64_t seed, uint64_t counter, float* bank,

@@ -357,3 +357,102 @@ def test_argument_errors(H):
         hicu.hicu_conv_null(H, hg, hr, cuda(x), cuda(f), prec=7)
     assert e.value.status == 1
     hicu.hicu_check(H)
+
+
+# ------------------------------------------------------------ split-bf16 tensor cores
+
+TC_CASES = ["2d_64_c4_p4", "2d_c16_p20", "2d_c32_permask", "tiny_one_output_c4", "2d_c8_p32_region"]
+CASES["tiny_one_output_c4"] = ((9, 9, 1), 4, (5, 5, 1), (0, 0, 0), ((2, 3, 0), (5, 5, 1)), 3)
+CASES["2d_c8_p32_region"] = ((100, 90, 1), 8, (5, 5, 1), (0, 0, 0), ((7, 11, 0), (83, 70, 1)), 32)
+
+
+@pytest.mark.parametrize("name", TC_CASES)
+def test_conv_null_split_bf16(H, name):
+    from paper_2004_08962_gb300 import hicu
+    og, oreg, hg, hr, x, f, mask, p, _ = setup(name)
+    R, obj = hicu.hicu_conv_null(H, hg, hr, cuda(x), cuda(f), prec=hicu.HICU_SPLIT_BF16,
+                                 want_objective=True)
+    ref = O.conv_null(x.astype(np.complex128), og, oreg, ofilters(f, og))
+    assert rel(R.cpu().numpy(), ref) < 2e-5
+    assert abs(obj.item() - np.vdot(ref, ref).real) < 4e-5 * np.vdot(ref, ref).real
+
+
+@pytest.mark.parametrize("name", TC_CASES)
+def test_adjoint_split_bf16(H, name):
+    from paper_2004_08962_gb300 import hicu
+    og, oreg, hg, hr, x, f, mask, p, rng = setup(name, seed=1)
+    R = random_complex(rng, O.out_shape(og, oreg) + (p,)).astype(np.complex64)
+    sentinel = np.full(x.shape, 7.0 + 3.0j, dtype=np.complex64)
+    g, gn = hicu.hicu_conv_null_adjoint(H, hg, hr, cuda(R), cuda(f), mask=cuda(mask), g=cuda(sentinel),
+                                        prec=hicu.HICU_SPLIT_BF16, want_gnorm2=True)
+    ref = O.conv_null_adjoint(R.astype(np.complex128), og, oreg, ofilters(f, og), mask)
+    g = g.cpu().numpy()
+    inside = np.zeros(x.shape[1:], dtype=bool)
+    (ox, oy, oz), (ex, ey, ez) = CASES[name][4]
+    inside[oz:oz + ez, oy:oy + ey, ox:ox + ex] = True
+    assert rel(g[:, inside], ref[:, inside]) < 2e-5
+    np.testing.assert_array_equal(g[:, ~inside], sentinel[:, ~inside])
+    m4 = np.broadcast_to(mask if mask.ndim == 4 else mask[None], x.shape).astype(bool)
+    assert np.all(g[m4 & inside[None]] == 0)
+    assert abs(gn.item() - np.vdot(ref, ref).real) < 4e-5 * np.vdot(ref, ref).real
+
+
+@pytest.mark.parametrize("name", TC_CASES)
+def test_gd_step_split_bf16(H, name):
+    from paper_2004_08962_gb300 import hicu
+    og, oreg, hg, hr, x, f, mask, p, _ = setup(name, seed=2)
+    y = cuda(x)
+    stats = hicu.hicu_gd_step_filters(H, hg, hr, y, cuda(mask), cuda(f),
+                                      prec=hicu.HICU_SPLIT_BF16).cpu().numpy()
+    y1_ref, info = O.gd_step(x, mask, og, oreg, ofilters(f, og))
+    for got, want in zip(stats, (info.eta, info.objective, info.gnorm2, info.denom)):
+        assert abs(got - want) <= 1e-4 * abs(want)
+    y1 = y.cpu().numpy()
+    assert rel(y1 - x, y1_ref - x) < 1e-4
+    m4 = np.broadcast_to(mask if mask.ndim == 4 else mask[None], x.shape).astype(bool)
+    np.testing.assert_array_equal(y1[m4], x[m4])
+
+
+def test_split_bf16_full_size_brain_slice(H):
+    """256x256, C=8, p=32 step of the 2D brain workload with null-space filters (spec bound
+    for split-bf16: gradient error <= 1e-3)."""
+    from paper_2004_08962_gb300 import hicu
+    pb = make_problem("2d_brain_256")
+    og = O.Geom(pb.dims, pb.ncoil, pb.kernel)
+    reg = O.full_region(og)
+    hg = hicu.make_geom(pb.dims, pb.ncoil, pb.kernel)
+    hr = hicu.make_region((0, 0, 0), pb.dims)
+    G = O.gram(pb.x0.astype(np.complex128), og, reg)
+    Qo, _ = O.nullspace(G, pb.rank)
+    f = O.as_filters(O.jl_compress(Qo, O.jl_matrix(3, 1, og.n, 32), "projector"), og)
+    fb = cuda(f.reshape(32, -1).astype(np.complex64))
+    g_gpu = hicu.hicu_conv_null_adjoint(
+        H, hg, hr, hicu.hicu_conv_null(H, hg, hr, cuda(pb.x0), fb, prec=hicu.HICU_SPLIT_BF16), fb,
+        mask=cuda(pb.mask), prec=hicu.HICU_SPLIT_BF16).cpu().numpy()
+    g_ref, _ = O.gradient(pb.x0.astype(np.complex128), og, reg, f, pb.mask)
+    assert rel(g_gpu, g_ref) < 1e-3
+    y = cuda(pb.x0)
+    stats = hicu.hicu_gd_step_filters(H, hg, hr, y, cuda(pb.mask), fb, prec=hicu.HICU_SPLIT_BF16).cpu().numpy()
+    y_ref, info = O.gd_step(pb.x0, pb.mask, og, reg, f)
+    assert abs(stats[0] - info.eta) < 1e-3 * info.eta
+    assert rel(y.cpu().numpy() - pb.x0, y_ref - pb.x0) < 1e-3
+
+
+def test_reconstruct_config1_split_bf16(H):
+    from paper_2004_08962_gb300 import hicu
+    pb = make_problem("2d_small_64")
+    hg = hicu.make_geom(pb.dims, pb.ncoil, pb.kernel)
+    prm = hicu.make_params(pb.rank, [(s.off, s.ext, s.iters, s.gd_steps, s.p) for s in pb.stages],
+                           seed=11, jl=1, prec=hicu.HICU_SPLIT_BF16)
+    x_gpu = hicu.hicu_reconstruct(H, hg, cuda(pb.x0), cuda(pb.mask), prm).cpu().numpy()
+    x_ref, _ = _oracle_recon(pb)
+    assert rel(x_gpu, x_ref) <= 1e-3
+    assert abs(O.ser_db(pb.x_full, x_gpu) - O.ser_db(pb.x_full, x_ref)) <= 0.05
+
+
+def test_split_bf16_unsupported_geometry(H):
+    from paper_2004_08962_gb300 import hicu
+    og, oreg, hg, hr, x, f, mask, p, _ = setup("2d_odd_region")   # C = 3
+    with pytest.raises(hicu.HicuError) as e:
+        hicu.hicu_conv_null(H, hg, hr, cuda(x), cuda(f), prec=hicu.HICU_SPLIT_BF16)
+    assert e.value.status == 8
