@@ -228,6 +228,42 @@ def run_reference(args, rank, world):
     return 0
 
 
+# ----------------------------------------------------------- profiling cases
+
+def run_profile_case(kind: str, size: int) -> int:
+    """Small fixed workloads for ncu captures of one kernel (no timing, no JSON line)."""
+    import torch
+    from paper_2004_08962_gb300 import build, hicu
+    from synth.phantoms import _slice_2d, make_problem
+    build.build()
+    h = hicu.Handle()
+    if kind == "eig":
+        pb = make_problem(WORKLOAD)
+        geom = hicu.make_geom(pb.dims, pb.ncoil, pb.kernel)
+        reg = hicu.make_region((0, 0, 0), pb.dims)
+        G = hicu.hicu_gram(h, geom, reg, torch.from_numpy(pb.x0).cuda())
+        for _ in range(2):
+            hicu.hicu_nullspace(h, G, pb.rank)
+    elif kind == "tc_step":
+        rng = np.random.default_rng(7)
+        k, mask = _slice_2d(rng, size, 8, 4.0, n_ellipses=20)
+        x = torch.from_numpy(k).cuda()
+        m = torch.from_numpy(mask).cuda()
+        geom = hicu.make_geom((size, size, 1), 8, (5, 5, 1))
+        reg = hicu.make_region((0, 0, 0), (size, size, 1))
+        f = torch.from_numpy((rng.standard_normal((32, 200)) + 1j * rng.standard_normal((32, 200)))
+                             .astype(np.complex64) * 0.05).cuda()
+        for _ in range(2):
+            hicu.hicu_gd_step_filters(h, geom, reg, x, m, f, prec=hicu.HICU_SPLIT_BF16)
+    else:
+        raise SystemExit(f"unknown profile case {kind}")
+    torch.cuda.synchronize()
+    hicu.hicu_check(h)
+    h.close()
+    print(f"profile case {kind} done")
+    return 0
+
+
 # -------------------------------------------------------------------- GPU arm
 
 def main():
@@ -238,7 +274,12 @@ def main():
     ap.add_argument("--impl", default="hicu", choices=["hicu", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", default=None, choices=["eig", "tc_step"],
+                    help="run one small fixed case for an ncu capture and exit")
+    ap.add_argument("--size", type=int, default=2048, help="image size of the tc_step profile case")
     args = ap.parse_args()
+    if args.profile:
+        return run_profile_case(args.profile, args.size)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -192,8 +192,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_corr_kernel(const TcParams P
     tc::tc_fence_after();
   }
 
-  // epilogue: thread (warp, lane) owns accumulator row 32*warp + lane of every M tile
-  double nrm = 0.0;
+  // epilogue: thread (warp, lane) owns accumulator row 32*warp + lane of every M tile.  Squared
+  // norms are summed in FP32 per thread (at most a few hundred terms) and in FP64 across threads:
+  // FP64 arithmetic runs at 1/58 of the FP32 rate on this part.
+  float nrm = 0.f;
   if (ok) {
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
     for (int mt = 0; mt < P.nM; ++mt) {
@@ -213,7 +215,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_corr_kernel(const TcParams P
             const int k = c0 / 2 + q;
             if (k < P.p) {
               const float2 v = make_float2(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
-              nrm += (double)v.x * v.x + (double)v.y * v.y;
+              nrm = fmaf(v.x, v.x, fmaf(v.y, v.y, nrm));
               if (P.R) P.R[o * P.p + k] = v;
             }
           }
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_corr_kernel(const TcParams P
               float2 v = make_float2(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
               if (P.m.p && P.m.p[(long long)c * P.m.sc + mo]) v = make_float2(0.f, 0.f);
               P.gout.p[(long long)c * P.gout.sc + go] = v;
-              nrm += (double)v.x * v.x + (double)v.y * v.y;
+              nrm = fmaf(v.x, v.x, fmaf(v.y, v.y, nrm));
             }
           }
         }
@@ -258,8 +260,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_corr_kernel(const TcParams P
   tc::tc_fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(taddr, (uint32_t)P.tmem_cols);
-  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
-  if (lane == 0) red[warp] = nrm;
+  double dn = (double)nrm;
+  for (int o = 16; o > 0; o >>= 1) dn += __shfl_down_sync(0xffffffffu, dn, o);
+  if (lane == 0) red[warp] = dn;
   __syncthreads();
   if (tid == 0) P.partial[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
 }

@@ -146,7 +146,8 @@ __global__ void __launch_bounds__(JWARPS * 32) jacobi_kernel(JacArgs J) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntile = (np + JT - 1) / JT;
   const long long ntiles = (long long)ntile * ntile;
-  const long long gw = (long long)blockIdx.x * JWARPS + warp;
+  // tiles interleaved CTA-fastest so that every SM gets work even when tiles < warps
+  const long long gw = (long long)warp * gridDim.x + blockIdx.x;
   const long long nw = (long long)gridDim.x * JWARPS;
   int cur = 0;
   const int mode = J.mode;
@@ -402,8 +403,7 @@ hicu_status run_nullspace(hicu_handle* h, int64_t n64, int64_t r, const double* 
       return set_error(h, HICU_ERR_CUDA, "nullspace: occupancy query failed");
     const int ntile = (npad / 2 + JT - 1) / JT;
     const long long ntiles = (long long)ntile * ntile;
-    const long long ctas = (ntiles + JWARPS - 1) / JWARPS;
-    grid_blocks = (int)std::min<long long>(ctas, (long long)h->num_sms * std::min(per_sm, 1));
+    grid_blocks = (int)std::min<long long>(ntiles, (long long)h->num_sms * std::min(per_sm, 1));
     if (grid_blocks < 1) grid_blocks = 1;
   }
   double* part = (double*)ws_get(h, WS_EIG_PART, sizeof(double) * 2 * grid_blocks + 64, &s);
