@@ -191,9 +191,9 @@ hicu_status hicu_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* 
  *   flags   : HICU_NULLSPACE_WARM: start from V^H G V with V the previous
  *             call's eigenvectors (ignored if there is none of the same n).
  *             HICU_NULLSPACE_SPLIT: stop as soon as the coupling between the
- *             r largest diagonal entries and the others is below 1e-11 ||G||_F
- *             instead of waiting for every off-diagonal entry.  Q then spans
- *             the null space to FP64 accuracy, but its vectors need not be
+ *             r largest diagonal entries and the others is below 1e-8 ||G||_F
+ *             (full decomposition: every off-diagonal entry, 1e-11 ||G||_F).  Q then spans
+ *             the null space to within 1e-8 ||G|| / gap, but its vectors need not be
  *             individual eigenvectors and the n-r smallest eigvals are diagonal
  *             entries of a not fully diagonalised block (their sum, J of
  *             Eq. 1, is still exact).  Algorithm 1 step 3 needs only the span.

@@ -701,7 +701,7 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
       if (s) return s;
       // after the first outer iteration: warm start, and stop at the top-r / rest split (step 3
       // needs an orthonormal basis of the complement of the r principal vectors, nothing more)
-      s = run_nullspace(h, n, r, G, Q, eig, it > 0 ? (HICU_NULLSPACE_WARM | HICU_NULLSPACE_SPLIT) : 0, st);
+      s = run_nullspace(h, n, r, G, Q, eig, HICU_NULLSPACE_SPLIT | (it > 0 ? HICU_NULLSPACE_WARM : 0), st);
       if (s) return s;
       HICU_LAUNCH(h, K_MISC, st, tail_sum_kernel<<<1, 256, 0, st>>>(eig, (int)nr, dlog + it));
       for (int j = 0; j < stg.gd_steps; ++j) {
