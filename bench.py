@@ -242,8 +242,8 @@ def run_profile_case(kind: str, size: int) -> int:
         geom = hicu.make_geom(pb.dims, pb.ncoil, pb.kernel)
         reg = hicu.make_region((0, 0, 0), pb.dims)
         G = hicu.hicu_gram(h, geom, reg, torch.from_numpy(pb.x0).cuda())
-        for _ in range(2):
-            hicu.hicu_nullspace(h, G, pb.rank)
+        for solver in ("cluster", "cluster", "grid", "grid"):
+            hicu.hicu_nullspace(h, G, pb.rank, solver=solver)
     elif kind == "tc_step":
         rng = np.random.default_rng(7)
         k, mask = _slice_2d(rng, size, 8, 4.0, n_ellipses=20)

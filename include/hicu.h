@@ -176,20 +176,35 @@ hicu_status hicu_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* 
 /* flags of hicu_nullspace */
 #define HICU_NULLSPACE_WARM 1   /* start from the previous call's eigenvectors (same n) */
 #define HICU_NULLSPACE_SPLIT 2  /* stop once the top-r / bottom n-r split has converged */
+#define HICU_NULLSPACE_GRID 4    /* grid-wide FP64 solver */
+#define HICU_NULLSPACE_CLUSTER 8 /* one-cluster double-float solver (n <= 256) */
+/* without either flag: the cluster solver for n <= HICU_NULLSPACE_CLUSTER_AUTO_MAX, else the grid one */
+#define HICU_NULLSPACE_CLUSTER_AUTO_MAX 128
 
 /*
  * hicu_nullspace - eigen-decomposition of the Hermitian n x n matrix G and the
  * null-space basis Q spanned by the eigenvectors of its n-r smallest
  * eigenvalues (Algorithm 1 steps 2-3: Q is an orthonormal basis of the
  * orthogonal complement of the r principal right singular vectors of H).
- * FP64 parallel cyclic Jacobi on the GPU (one cooperative kernel, bounded grid
- * barriers; a barrier that times out sets the handle's device error word).
+ * Parallel cyclic Jacobi on the GPU, by one of two solvers:
+ *   cluster: one thread-block cluster (16 or 8 SMs) holds the matrix in
+ *     distributed shared memory and computes in double-float (FP32 pairs,
+ *     ~2^-48 relative precision; inputs and outputs FP64).  n <= 256.  It
+ *     leaves the other SMs free, so independent solves on separate streams run
+ *     side by side.
+ *   grid: one cooperative FP64 kernel over the whole GPU (bounded grid
+ *     barriers; a barrier that times out sets the handle's device error word).
+ * HICU_NULLSPACE_CLUSTER / HICU_NULLSPACE_GRID choose one (both: HICU_ERR_ARG;
+ * CLUSTER for n > 256 or on a device that cannot run the cluster:
+ * HICU_ERR_UNSUPPORTED); without either, n <= HICU_NULLSPACE_CLUSTER_AUTO_MAX
+ * uses the cluster solver.
  *   G       : complex128 n x n row-major, Hermitian (only read)
  *   Q       : complex128 [(n-r)][n]: null vector j is Q[j*n .. j*n+n-1],
  *             ordered by ascending eigenvalue
  *   eigvals : double [n], ascending (nullable)
  *   flags   : HICU_NULLSPACE_WARM: start from V^H G V with V the previous
- *             call's eigenvectors (ignored if there is none of the same n).
+ *             call's eigenvectors (ignored if there is none of the same n
+ *             and solver).
  *             HICU_NULLSPACE_SPLIT: stop as soon as the coupling between the
  *             r largest diagonal entries and the others is below 1e-8 ||G||_F
  *             (full decomposition: every off-diagonal entry, 1e-11 ||G||_F).  Q then spans

@@ -285,7 +285,8 @@ extern "C" hicu_status hicu_nullspace(hicu_handle* h, int64_t n, int64_t r, cons
                                       double* Q, double* eigvals, int32_t flags, void* stream) {
   if (!h) return HICU_ERR_ARG;
   if (!G || !Q) return set_error(h, HICU_ERR_ARG, "nullspace: null pointer");
-  if (flags & ~3) return set_error(h, HICU_ERR_ARG, "nullspace: unknown flags");
+  if (flags & ~(HICU_NULLSPACE_WARM | HICU_NULLSPACE_SPLIT | HICU_NULLSPACE_GRID | HICU_NULLSPACE_CLUSTER))
+    return set_error(h, HICU_ERR_ARG, "nullspace: unknown flags");
   return run_nullspace(h, n, r, G, Q, eigvals, flags, (cudaStream_t)stream);
 }
 

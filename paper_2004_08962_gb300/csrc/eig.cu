@@ -37,14 +37,18 @@ struct Rot {
 // alone (the usual relative threshold, which protects tiny eigenvalues).
 __device__ __forceinline__ Rot make_rot(double a, double c, double2 b) {
   Rot R;
-  const float bx = (float)b.x, by = (float)b.y;
+  // the angle and phase depend only on ratios: bring the entries into FP32 range first
+  // (exact power-of-two scale)
+  const double big = fmax(fmax(fabs(a), fabs(c)), fmax(fabs(b.x), fabs(b.y)));
+  const double sc = (big > 0.0 && big <= 1.7e308) ? ldexp(1.0, -ilogb(big)) : 1.0;
+  const float bx = (float)(b.x * sc), by = (float)(b.y * sc);
   const float ab = hypotf(bx, by);
-  const float thr = 1e-17f * sqrtf(fabsf((float)a)) * sqrtf(fabsf((float)c));
+  const float thr = 1e-17f * sqrtf(fabsf((float)(a * sc))) * sqrtf(fabsf((float)(c * sc)));
   if (!(ab > thr) || !(ab > 0.f)) {
     R.cs = 1.0; R.sn = 0.0; R.ex = 1.0; R.ey = 0.0; R.ident = 1;
     return R;
   }
-  const float tau = (float)(c - a) / (2.f * ab);
+  const float tau = (float)((c - a) * sc) / (2.f * ab);
   float t;
   if (fabsf(tau) > 1e18f) t = 0.5f / tau;
   else t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
@@ -301,9 +305,9 @@ __global__ void __launch_bounds__(JWARPS * 32) jacobi_kernel(JacArgs J) {
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(J.sweep_total, (unsigned long long)J.max_sweeps);
 }
 
-// A (npad x npad) <- G (n x n, row-major) padded with a zero row and column when n
-// is odd.  A zero pad row never couples (its rotations are the identity) and the
-// pad index is excluded from the output ranking.
+// A (npad x npad) <- G (n x n, row-major) padded with zero rows and columns.  A zero
+// pad row never couples (its rotations are the identity) and pad indices are excluded
+// from the output ranking.
 __global__ void eig_pad_kernel(int n, int npad, const double2* __restrict__ G, double2* __restrict__ A,
                                double2* __restrict__ V, int set_identity) {
   const long long nn = (long long)npad * npad;
@@ -359,10 +363,38 @@ __global__ void hermitize_kernel(int n, double2* A) {
   }
 }
 
-// rank of each eigenvalue (ascending, ties by index), eigenvalue output
+// largest |Re|, |Im| of A (non-negative doubles order like their bit patterns)
+__global__ void eig_absmax_kernel(long long nn, const double2* __restrict__ A, unsigned long long* amax_bits) {
+  double m = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double2 a = A[e];
+    m = fmax(m, fmax(fabs(a.x), fabs(a.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(amax_bits, (unsigned long long)__double_as_longlong(m));
+}
+
+// A <- 2^-e A with 2^(e-1) <= max entry < 2^e: the Jacobi sums of squared entries then stay
+// far from overflow and underflow whatever the scale of G (rotations are scale-invariant)
+__global__ void eig_scale_kernel(long long nn, double2* __restrict__ A, const unsigned long long* amax_bits,
+                                 double* scale_out) {
+  const double amax = __longlong_as_double((long long)*amax_bits);
+  int ex2 = 0;
+  if (amax > 0.0 && amax <= 1.7e308) frexp(amax, &ex2);
+  const double sc = ldexp(1.0, -ex2);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *scale_out = sc;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double2 a = A[e];
+    A[e] = make_double2(a.x * sc, a.y * sc);
+  }
+}
+
+// rank of each eigenvalue (ascending, ties by index), eigenvalue output (undoing the scale)
 __global__ void eig_rank_kernel(int n, int npad, const double2* A0, const double2* A1,
-                                const int* __restrict__ info, int* __restrict__ rank,
-                                double* __restrict__ eig_out) {
+                                const int* __restrict__ info, const double* __restrict__ scale,
+                                int* __restrict__ rank, double* __restrict__ eig_out) {
   const double2* A = info[2] ? A1 : A0;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -373,7 +405,7 @@ __global__ void eig_rank_kernel(int n, int npad, const double2* A0, const double
     r += (lj < li) || (lj == li && j < i);
   }
   rank[i] = r;
-  if (eig_out) eig_out[r] = li;
+  if (eig_out) eig_out[r] = li / *scale;
 }
 
 // Q[rank_i][a] = V[a][i] for the nr smallest eigenvalues
@@ -393,7 +425,18 @@ hicu_status run_nullspace(hicu_handle* h, int64_t n64, int64_t r, const double* 
   if (n64 < 2 || n64 > 4096) return set_error(h, HICU_ERR_SHAPE, "nullspace: n must be in [2, 4096]");
   if (r <= 0 || r >= n64) return set_error(h, HICU_ERR_RANK, "nullspace: rank must satisfy 0 < r < n");
   const int n = (int)n64;
-  const int npad = (n + 1) / 2 * 2;
+  // one-cluster solver (shared-memory resident, double-float arithmetic, eig_cluster.cu) or the
+  // grid-wide FP64 solver below
+  if ((flags & HICU_NULLSPACE_GRID) && (flags & HICU_NULLSPACE_CLUSTER))
+    return set_error(h, HICU_ERR_ARG, "nullspace: GRID and CLUSTER both requested");
+  int nct = 0;
+  if (flags & HICU_NULLSPACE_CLUSTER) {
+    nct = cluster_eig_ctas(n);
+    if (!nct) return set_error(h, HICU_ERR_UNSUPPORTED, "nullspace: no cluster solver for this n on this device");
+  } else if (!(flags & HICU_NULLSPACE_GRID) && n <= HICU_NULLSPACE_CLUSTER_AUTO_MAX) {
+    nct = cluster_eig_ctas(n);
+  }
+  const int npad = nct ? cluster_eig_npad(n, nct) : (n + 1) / 2 * 2;
   const long long nn = (long long)npad * npad;
   hicu_status s = HICU_OK;
   double2* A0 = (double2*)ws_get(h, WS_EIG_A0, sizeof(double2) * nn, &s);
@@ -416,14 +459,16 @@ hicu_status run_nullspace(hicu_handle* h, int64_t n64, int64_t r, const double* 
     grid_blocks = (int)std::min<long long>(ntiles, (long long)h->num_sms * std::min(per_sm, 1));
     if (grid_blocks < 1) grid_blocks = 1;
   }
-  double* part = (double*)ws_get(h, WS_EIG_PART, sizeof(double) * 2 * grid_blocks + 64, &s);
+  double* part = (double*)ws_get(h, WS_EIG_PART, sizeof(double) * 2 * grid_blocks + 128, &s);
   if (s) return s;
-  int* info = (int*)(part + 2 * grid_blocks);
+  int* info = (int*)(part + 2 * grid_blocks);                                  // 8 ints
+  unsigned long long* amax_bits = (unsigned long long*)(part + 2 * grid_blocks + 4);
+  double* scale = part + 2 * grid_blocks + 5;
   int* rank = (int*)ws_get(h, WS_EIG_TMP, sizeof(int) * 2 * npad, &s);
   if (s) return s;
   int* rankd = rank + npad;
 
-  const bool use_warm = (flags & 1) && h->eig_have_v && h->eig_n == n;
+  const bool use_warm = (flags & 1) && h->eig_have_v && h->eig_n == n && h->eig_npad == npad;
   int blocks = (int)std::min<long long>((nn + 255) / 256, 4096);
   if (!use_warm) {
     HICU_LAUNCH(h, K_MISC, st, eig_pad_kernel<<<blocks, 256, 0, st>>>(n, npad, (const double2*)G, A0, V, 1));
@@ -431,7 +476,7 @@ hicu_status run_nullspace(hicu_handle* h, int64_t n64, int64_t r, const double* 
     // A0 = Vprev^H (G Vprev); V = Vprev
     HICU_LAUNCH(h, K_MISC, st, eig_pad_kernel<<<blocks, 256, 0, st>>>(n, npad, (const double2*)G, A1, V, 0));
     dim3 gg((npad + 15) / 16, (npad + 15) / 16), bb(16, 16);
-    // the pad column of Vprev is the pad unit vector, so the product keeps the pad row zero
+    // the pad columns of Vprev are pad unit vectors, so the product keeps the pad rows zero
     HICU_LAUNCH(h, K_MISC, st, zgemm_kernel<<<gg, bb, 0, st>>>(npad, 0, A1, Vprev, A0));  // A0 = A Vprev
     HICU_LAUNCH(h, K_MISC, st, zgemm_kernel<<<gg, bb, 0, st>>>(npad, 1, Vprev, A0, A1));  // A1 = Vprev^H A0
     HICU_LAUNCH(h, K_MISC, st, hermitize_kernel<<<blocks, 256, 0, st>>>(npad, A1));
@@ -440,8 +485,24 @@ hicu_status run_nullspace(hicu_handle* h, int64_t n64, int64_t r, const double* 
   }
   s = cuda_error(h, cudaGetLastError(), "nullspace prep");
   if (s) return s;
+  if (nct) {
+    s = run_nullspace_cluster(h, n, npad, nct, r, A0, V, V, Q, eigvals, flags, st);
+    if (s) return s;
+    cudaMemcpyAsync(Vprev, V, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st);
+    s = cuda_error(h, cudaGetLastError(), "nullspace output");
+    if (s) return s;
+    h->eig_have_v = true;
+    h->eig_n = n;
+    h->eig_npad = npad;
+    return HICU_OK;
+  }
   cudaMemsetAsync(h->dev_sync, 0, 2 * sizeof(unsigned), st);
-  cudaMemsetAsync(info, 0, 8 * sizeof(int), st);
+  cudaMemsetAsync(info, 0, 8 * sizeof(int) + 16, st);  // info, amax bits
+  {
+    const int sb = (int)std::min<long long>((nn + 255) / 256, (long long)h->num_sms * 8);
+    HICU_LAUNCH(h, K_MISC, st, eig_absmax_kernel<<<sb, 256, 0, st>>>(nn, A0, amax_bits));
+    HICU_LAUNCH(h, K_MISC, st, eig_scale_kernel<<<sb, 256, 0, st>>>(nn, A0, amax_bits, scale));
+  }
   JacArgs J;
   J.n = npad;
   J.A0 = A0;
@@ -470,13 +531,14 @@ hicu_status run_nullspace(hicu_handle* h, int64_t n64, int64_t r, const double* 
               e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(grid_blocks), dim3(threads),
                                               args, 0, st));
   if (e != cudaSuccess) return cuda_error(h, e, "nullspace jacobi launch");
-  HICU_LAUNCH(h, K_MISC, st, eig_rank_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, npad, A0, A1, info, rank, eigvals));
+  HICU_LAUNCH(h, K_MISC, st, eig_rank_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, npad, A0, A1, info, scale, rank, eigvals));
   HICU_LAUNCH(h, K_MISC, st, eig_gather_q_kernel<<<blocks, 256, 0, st>>>(n, npad, n - (int)r, V, rank, (double2*)Q));
   cudaMemcpyAsync(Vprev, V, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st);
   s = cuda_error(h, cudaGetLastError(), "nullspace output");
   if (s) return s;
   h->eig_have_v = true;
   h->eig_n = n;
+  h->eig_npad = npad;
   h->eig_info = info;
   return HICU_OK;
 }

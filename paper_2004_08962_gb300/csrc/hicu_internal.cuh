@@ -150,6 +150,7 @@ struct hicu_handle {
   unsigned* dev_sync = nullptr;    // grid-barrier words (count, gen)
   // warm-start state of the eigen-solver
   int64_t eig_n = 0;
+  int eig_npad = 0;  // padded size of the stored eigenvectors (grid and cluster solvers pad differently)
   bool eig_have_v = false;
   int* eig_info = nullptr;  // device words of the last Jacobi run (sweeps, converged, buffer)
   // launch accounting and optional event timing of one kernel class
@@ -254,6 +255,15 @@ hicu_status launch_jl(hicu_handle* h, int64_t n, int64_t nr, int p, const double
 
 hicu_status run_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* reg, const float* x,
                      double* G, cudaStream_t st);
+// cluster Jacobi (eig_cluster.cu): cluster size for an n x n solve (0: use the grid solver),
+// its padded size, and the solve itself on a prepared A0 / V0
+int cluster_eig_ctas(int64_t n);
+int cluster_eig_npad(int64_t n, int nct);
+hicu_status run_nullspace_cluster(hicu_handle* h, int n, int npad, int nct, int64_t r, const double2* A0,
+                                  const double2* V0, double2* Vout, double* Q, double* eigvals, int flags,
+                                  cudaStream_t st);
+__global__ void eig_gather_q_kernel(int n, int npad, int nr, const double2* __restrict__ V,
+                                    const int* __restrict__ rank, double2* __restrict__ Q);
 hicu_status run_nullspace(hicu_handle* h, int64_t n, int64_t r, const double* G, double* Q,
                           double* eigvals, int flags, cudaStream_t st);
 

@@ -207,15 +207,20 @@ def hicu_gram(h: Handle, geom, region, x: torch.Tensor, G: Optional[torch.Tensor
     return G
 
 
-HICU_NULLSPACE_WARM, HICU_NULLSPACE_SPLIT = 1, 2
+HICU_NULLSPACE_WARM, HICU_NULLSPACE_SPLIT, HICU_NULLSPACE_GRID, HICU_NULLSPACE_CLUSTER = 1, 2, 4, 8
 
 
 def hicu_nullspace(h: Handle, G: torch.Tensor, r: int, warm: bool = False, split: bool = False,
-                   stream=None):
+                   solver: Optional[str] = None, stream=None):
+    """solver: None (by size), "grid" or "cluster"."""
     n = G.shape[0]
     Q = torch.empty((n - r, n), dtype=torch.complex128, device=G.device)
     eig = torch.empty((n,), dtype=torch.float64, device=G.device)
-    flags = (HICU_NULLSPACE_WARM if warm else 0) | (HICU_NULLSPACE_SPLIT if split else 0)
+    if solver not in (None, "grid", "cluster"):
+        raise ValueError(f"unknown solver {solver!r}")
+    flags = ((HICU_NULLSPACE_WARM if warm else 0) | (HICU_NULLSPACE_SPLIT if split else 0)
+             | (HICU_NULLSPACE_GRID if solver == "grid" else 0)
+             | (HICU_NULLSPACE_CLUSTER if solver == "cluster" else 0))
     h._check(lib().hicu_nullspace(h.ptr, n, r, _ptr(G), _ptr(Q), _ptr(eig), flags, _stream(stream)))
     return Q, eig
 

@@ -143,13 +143,32 @@ def test_gram_phantom_config1(H):
     assert rel(G, ref) < 1e-12
 
 
-def _nullspace_check(Q, eig, ref_G, r):
+DF_U = 2.0**-48   # unit roundoff of double-float (FP32 pair) arithmetic
+
+
+def _uses_cluster(n, solver):
+    return solver == "cluster" or (solver is None and n <= 128)
+
+
+def _orth_tol(H, n, solver):
+    """Orthonormality bound of the returned basis.  Grid solver (FP64): 1e-12.  Cluster solver
+    (double-float, n <= 256): each rotation is unitary to a few u and each V update rounds to a
+    few u, so the error is a random walk over the K = sweeps x (n_pad - 1) rotations a column
+    goes through; 40 u sqrt(K) covers the largest of the n^2 entries of Q^H Q."""
+    from paper_2004_08962_gb300 import hicu
+    if not _uses_cluster(n, solver):
+        return 1e-12
+    sweeps, _ = hicu.hicu_nullspace_info(H)
+    return max(1e-12, 40 * DF_U * np.sqrt(sweeps * (n + 32)))
+
+
+def _nullspace_check(Q, eig, ref_G, r, orth_atol=1e-12):
     w, V = np.linalg.eigh(ref_G)
     n = ref_G.shape[0]
     lmax = abs(w).max()
     assert np.max(np.abs(eig - w)) < 1e-11 * lmax
     Qh = Q.T  # (n, n-r)
-    np.testing.assert_allclose(Qh.conj().T @ Qh, np.eye(n - r), atol=1e-12)
+    np.testing.assert_allclose(Qh.conj().T @ Qh, np.eye(n - r), atol=orth_atol)
     res = ref_G @ Qh - Qh * eig[: n - r]
     assert np.linalg.norm(res) < 1e-11 * lmax * np.sqrt(n)
     Qo = V[:, : n - r]
@@ -158,42 +177,53 @@ def _nullspace_check(Q, eig, ref_G, r):
     assert dist < 1e-12 * lmax / gap * np.sqrt(n) + 1e-10
 
 
-def test_nullspace_parity_phantom(H):
+# both solvers (one-cluster double-float and grid-wide FP64) are held to the same bounds,
+# except the orthonormality bound that each one's arithmetic sets
+@pytest.mark.parametrize("solver", ["cluster", "grid"])
+def test_nullspace_parity_phantom(H, solver):
     from paper_2004_08962_gb300 import hicu
     pb = make_problem("2d_small_64")
     og = O.Geom(pb.dims, pb.ncoil, pb.kernel)
     G = O.gram(pb.x0.astype(np.complex128), og, O.full_region(og))
-    Q, eig = hicu.hicu_nullspace(H, cuda(G), pb.rank)
-    _nullspace_check(Q.cpu().numpy(), eig.cpu().numpy(), G, pb.rank)
+    Q, eig = hicu.hicu_nullspace(H, cuda(G), pb.rank, solver=solver)
+    tol = _orth_tol(H, G.shape[0], solver)
+    _nullspace_check(Q.cpu().numpy(), eig.cpu().numpy(), G, pb.rank, tol)
     # warm start from the previous eigenvectors on a perturbed matrix
     rng = np.random.default_rng(9)
     E = random_complex(rng, G.shape) * 1e-3 * np.abs(G).max()
     G2 = G + (E + E.conj().T) / 2 * 1e-3
-    Q2, eig2 = hicu.hicu_nullspace(H, cuda(G2), pb.rank, warm=True)
-    _nullspace_check(Q2.cpu().numpy(), eig2.cpu().numpy(), G2, pb.rank)
+    Q2, eig2 = hicu.hicu_nullspace(H, cuda(G2), pb.rank, warm=True, solver=solver)
+    # the warm start inherits the first basis' error
+    tol += _orth_tol(H, G.shape[0], solver)
+    _nullspace_check(Q2.cpu().numpy(), eig2.cpu().numpy(), G2, pb.rank, tol)
 
 
-def test_nullspace_split_mode_matches_oracle_subspace(H):
+@pytest.mark.parametrize("solver", ["cluster", "grid"])
+def test_nullspace_split_mode_matches_oracle_subspace(H, solver):
     """Warm split mode: same null space and the same J (Eq. 1) as LAPACK, not eigenvectors."""
     from paper_2004_08962_gb300 import hicu
     pb = make_problem("2d_small_64")
     og = O.Geom(pb.dims, pb.ncoil, pb.kernel)
     G = O.gram(pb.x0.astype(np.complex128), og, O.full_region(og))
-    hicu.hicu_nullspace(H, cuda(G), pb.rank)                     # cold: seeds the warm start
+    hicu.hicu_nullspace(H, cuda(G), pb.rank, solver=solver)          # cold: seeds the warm start
     rng = np.random.default_rng(12)
     E = random_complex(rng, G.shape)
     G2 = G + (E + E.conj().T) * 1e-4 * np.abs(G).max()
-    Q, eig = hicu.hicu_nullspace(H, cuda(G2), pb.rank, warm=True, split=True)
+    tol = _orth_tol(H, G.shape[0], solver)
+    Q, eig = hicu.hicu_nullspace(H, cuda(G2), pb.rank, warm=True, split=True, solver=solver)
     sweeps, how = hicu.hicu_nullspace_info(H)
     assert how == 2, (sweeps, how)
+    tol += _orth_tol(H, G.shape[0], solver)
     Q = Q.cpu().numpy().T
     n, r = G.shape[0], pb.rank
     w, V = np.linalg.eigh(G2)
-    np.testing.assert_allclose(Q.conj().T @ Q, np.eye(n - r), atol=1e-12)
+    np.testing.assert_allclose(Q.conj().T @ Q, np.eye(n - r), atol=tol)
     Qo = V[:, : n - r]
     gap = w[n - r] - w[n - r - 1]
     dist = np.linalg.norm(Q @ Q.conj().T - Qo @ Qo.conj().T)
-    assert dist < 1e-11 * w[-1] / gap * np.sqrt(n) + 1e-10
+    # the split stop guarantees a top-r / rest coupling block of Frobenius norm <= 1e-8 ||G||_F;
+    # by the Davis-Kahan sin-theta theorem the projector distance is then <= sqrt(2) x that / gap
+    assert dist < np.sqrt(2) * 1e-8 * np.linalg.norm(G2) / gap
     J = eig.cpu().numpy()[: n - r].sum()
     assert abs(J - w[: n - r].sum()) < 1e-11 * w[-1] * n
 
@@ -205,8 +235,44 @@ def test_nullspace_odd_n_lowrank(H):
     og = O.Geom((13, 14, 1), 1, (3, 3, 1))
     G = O.gram(x, og, O.full_region(og))
     Q, eig = hicu.hicu_nullspace(H, cuda(G), 3)
-    _nullspace_check(Q.cpu().numpy(), eig.cpu().numpy(), G, 3)
+    _nullspace_check(Q.cpu().numpy(), eig.cpu().numpy(), G, 3, _orth_tol(H, 9, None))
     assert eig.cpu().numpy()[:6].max() < 1e-10 * eig.cpu().numpy().max()
+
+
+@pytest.mark.parametrize("n,solver", [(256, "cluster"), (257, None), (200, "grid"), (200, "cluster"),
+                                      (2, "cluster"), (2, "grid"), (128, None), (129, None)])
+def test_nullspace_sizes(H, n, solver):
+    """The cluster solver's largest size (n = 256), sizes above it (grid), the brain-slice size
+    on both solvers, the smallest problem (n = 2, padded to 32) and both sides of the size at
+    which the default switches from the cluster to the grid solver (128 / 129)."""
+    from paper_2004_08962_gb300 import hicu
+    rng = np.random.default_rng(n)
+    r = max(1, n // 3)
+    X = random_complex(rng, (n, n + 7))
+    sv = np.exp(-np.arange(n) / 10.0)        # decaying spectrum, like a Gram of a low-rank Hankel
+    U, _ = np.linalg.qr(X[:, :n])
+    G = (U * sv**2) @ U.conj().T * 1e4
+    G = (G + G.conj().T) / 2
+    Q, eig = hicu.hicu_nullspace(H, cuda(G), r, solver=solver)
+    _nullspace_check(Q.cpu().numpy(), eig.cpu().numpy(), G, r, _orth_tol(H, n, solver))
+
+
+@pytest.mark.parametrize("solver", ["cluster", "grid"])
+def test_nullspace_scale_invariance(H, solver):
+    """Entries far outside the FP32 range (~1e270) or tiny (~1e-271): both solvers work on a
+    power-of-two scaled copy, so eigenvalues scale exactly and the basis is bit-identical."""
+    from paper_2004_08962_gb300 import hicu
+    pb = make_problem("2d_small_64")
+    og = O.Geom(pb.dims, pb.ncoil, pb.kernel)
+    G = O.gram(pb.x0.astype(np.complex128), og, O.full_region(og))
+    G = G / np.abs(G).max()
+    Q1, e1 = hicu.hicu_nullspace(H, cuda(G), pb.rank, solver=solver)
+    Q1, e1 = Q1.cpu().numpy(), e1.cpu().numpy()
+    for s in (2.0**900, 2.0**-900):
+        Qs, es = hicu.hicu_nullspace(H, cuda(G * s), pb.rank, solver=solver)
+        Qs, es = Qs.cpu().numpy(), es.cpu().numpy()
+        np.testing.assert_array_equal(es, e1 * s)
+        np.testing.assert_array_equal(Qs, Q1)
 
 
 @pytest.mark.parametrize("mode", [0, 1])
@@ -353,6 +419,10 @@ def test_argument_errors(H):
     with pytest.raises(hicu.HicuError) as e:
         hicu.hicu_nullspace(H, G, 0)
     assert e.value.status == 3
+    G300 = torch.zeros((300, 300), dtype=torch.complex128, device="cuda")
+    with pytest.raises(hicu.HicuError) as e:                 # cluster solver is for n <= 256
+        hicu.hicu_nullspace(H, G300, 10, solver="cluster")
+    assert e.value.status == 8
     with pytest.raises(hicu.HicuError) as e:
         hicu.hicu_conv_null(H, hg, hr, cuda(x), cuda(f), prec=7)
     assert e.value.status == 1
