@@ -117,6 +117,8 @@ typedef struct {
   int32_t gram_on_current;   /* 0: null space of H^(i-1) (Algorithm 1 step 2 as
                                 printed, S^(0) := S^(1)); 1: use S^(i) */
   int32_t init;              /* 0: x^(0) = X0; 1: time-averaged along z (2D+t) */
+  int32_t eig_solver;        /* null-space solver: 0 by size, HICU_NULLSPACE_GRID or
+                                HICU_NULLSPACE_CLUSTER (see hicu_nullspace) */
 } hicu_params;
 
 /* Optional per-iteration log, HOST arrays (any may be NULL). */
@@ -304,6 +306,58 @@ hicu_status hicu_gd_step(hicu_handle* h, const hicu_geom* geom, const hicu_regio
 hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, const float* x0,
                              const uint8_t* mask, const hicu_params* params, float* x_out,
                              hicu_log* log, void* stream);
+
+/* ------------------------------------------------------------- batches */
+
+/* One independent reconstruction of a batch (arguments of hicu_reconstruct). */
+typedef struct {
+  hicu_geom geom;
+  const float* x0;      /* host or device, as hicu_reconstruct */
+  const uint8_t* mask;  /* host or device */
+  hicu_params params;   /* params.stages must stay valid for the call */
+  float* x_out;         /* host or device */
+  hicu_log* log;        /* nullable */
+} hicu_problem;
+
+/* Per-problem outcome of hicu_reconstruct_batched. */
+typedef struct {
+  double start_ms;   /* GPU time from the start of the batch to the problem's first kernel */
+  double end_ms;     /* ... to the completion of its last kernel (completion latency) */
+  int32_t lane;      /* worker lane that ran it */
+  int32_t status;    /* hicu_status of the problem */
+  int64_t gd_steps;  /* descent steps it ran (sum of iters x gd_steps over its stages) */
+} hicu_slice_report;
+
+/*
+ * hicu_batch_order - the order in which hicu_reconstruct_batched starts the
+ * problems: descending estimated cost (longest first, so that the large
+ * problems do not finish last), ties by index.  Host only; no GPU needed.
+ *   order : int32 [nslices], a permutation of 0 .. nslices-1
+ *   cost  : optional double [nslices], the estimate in floating-point
+ *           operations (Gram, eigen-solver sweeps and convolutions of every
+ *           stage)
+ */
+hicu_status hicu_batch_order(int32_t nslices, const hicu_problem* problems, int32_t* order, double* cost);
+
+/*
+ * hicu_reconstruct_batched - hicu_reconstruct for many independent problems of
+ * uneven size (matrix size, coils, kernel, rank, schedule), run side by side.
+ * There is no counterpart in the paper, which reconstructs slices one at a time.
+ *   `lanes` worker lanes (0: min(nslices, 8)), each with its own stream,
+ *   workspace and host thread, take problems from one queue in hicu_batch_order
+ *   order.  Problems with n <= 256 whose params.eig_solver is 0 use the cluster
+ *   eigen-solver, which occupies 16 SMs and leaves the others to the other lanes;
+ *   grid-solver launches are limited to num_SMs / lanes CTAs for the same reason.
+ *   Every problem gives the same result as hicu_reconstruct with the same
+ *   params (and that eig_solver): lanes share no mutable state.
+ *   The lanes start after the work already queued on `stream`; the call returns
+ *   when every problem has finished (it synchronises the lanes, not `stream`).
+ *   report : optional host array [nslices], indexed like `problems`
+ * Returns HICU_OK or the first failing problem's status (in `problems` order);
+ * the other problems still run.  hicu_last_error names the failing problem.
+ */
+hicu_status hicu_reconstruct_batched(hicu_handle* h, int32_t nslices, const hicu_problem* problems,
+                                     int32_t lanes, hicu_slice_report* report, void* stream);
 
 /* ------------------------------------------------------ allocation-free */
 

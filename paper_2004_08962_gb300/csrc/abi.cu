@@ -2,8 +2,11 @@
 // that chain the kernels into the steps of Algorithm 1.
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "hicu_internal.cuh"
@@ -13,6 +16,26 @@ namespace hicu {
 hicu_status set_error(hicu_handle* h, hicu_status s, const std::string& msg) {
   if (h) h->last_error = msg;
   return s;
+}
+
+cudaError_t allow_max_dynamic_smem(const void* kernel) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, cudaError_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = done.find({kernel, dev});
+  if (it != done.end()) return it->second;
+  int optin = 0;
+  cudaFuncAttributes fa;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  if (e != cudaSuccess) cudaGetLastError();
+  done[{kernel, dev}] = e;
+  return e;
 }
 
 hicu_status cuda_error(hicu_handle* h, cudaError_t e, const char* where) {
@@ -178,6 +201,9 @@ extern "C" hicu_status hicu_create(hicu_handle** out) {
 extern "C" hicu_status hicu_destroy(hicu_handle* h) {
   if (!h) return HICU_ERR_ARG;
   cudaDeviceSynchronize();
+  for (auto* c : h->lane_h) hicu_destroy(c);
+  for (auto st : h->lane_st) cudaStreamDestroy(st);
+  for (auto e : h->batch_ev) cudaEventDestroy(e);
   for (auto& w : h->ws)
     if (w.ptr) cudaFree(w.ptr);
   for (auto e : h->prof_events) cudaEventDestroy(e);
@@ -639,6 +665,8 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
   if (prm->jl != HICU_JL_NULLSPACE && prm->jl != HICU_JL_PROJECTOR)
     return set_error(h, HICU_ERR_ARG, "reconstruct: unknown JL mode");
   if (prm->init != 0 && prm->init != 1) return set_error(h, HICU_ERR_ARG, "reconstruct: unknown init");
+  if (prm->eig_solver != 0 && prm->eig_solver != HICU_NULLSPACE_GRID && prm->eig_solver != HICU_NULLSPACE_CLUSTER)
+    return set_error(h, HICU_ERR_ARG, "reconstruct: unknown eig_solver");
   hicu_status s = check_prec(h, prm->prec);
   if (s) return s;
   long long total_iters = 0, total_steps = 0;
@@ -702,7 +730,8 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
       if (s) return s;
       // after the first outer iteration: warm start, and stop at the top-r / rest split (step 3
       // needs an orthonormal basis of the complement of the r principal vectors, nothing more)
-      s = run_nullspace(h, n, r, G, Q, eig, HICU_NULLSPACE_SPLIT | (it > 0 ? HICU_NULLSPACE_WARM : 0), st);
+      s = run_nullspace(h, n, r, G, Q, eig,
+                        HICU_NULLSPACE_SPLIT | (it > 0 ? HICU_NULLSPACE_WARM : 0) | prm->eig_solver, st);
       if (s) return s;
       HICU_LAUNCH(h, K_MISC, st, tail_sum_kernel<<<1, 256, 0, st>>>(eig, (int)nr, dlog + it));
       for (int j = 0; j < stg.gd_steps; ++j) {

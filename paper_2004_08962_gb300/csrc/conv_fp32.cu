@@ -152,7 +152,8 @@ hicu_status launch_conv_fp32(hicu_handle* h, const ConvGeom& g, KView x, const f
   *nblocks = grid.x * grid.y * grid.z;
   if (partial == nullptr) return HICU_OK;  // sizing query
   if (smem > 48 * 1024) {
-    cudaFuncSetAttribute(conv_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = allow_max_dynamic_smem((const void*)conv_fp32_kernel);
+    if (e != cudaSuccess) return cuda_error(h, e, "conv_fp32 smem");
   }
   HICU_LAUNCH(h, K_CONV, st, conv_fp32_kernel<<<grid, CNT, smem, st>>>(g, x, fT, p, Ppad, R, partial));
   return cuda_error(h, cudaGetLastError(), "conv_fp32");

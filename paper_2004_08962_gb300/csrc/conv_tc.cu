@@ -468,7 +468,8 @@ hicu_status tc_prepare_weights(hicu_handle* h, const ConvGeom& g, const float2* 
 }
 
 static hicu_status launch_plan(hicu_handle* h, TcPlan& pl, int cls, cudaStream_t st) {
-  cudaFuncSetAttribute(tc_corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+  const cudaError_t e = allow_max_dynamic_smem((const void*)tc_corr_kernel);
+  if (e != cudaSuccess) return cuda_error(h, e, "tc_corr smem");
   HICU_LAUNCH(h, cls, st, tc_corr_kernel<<<pl.grid, TC_THREADS, pl.smem, st>>>(pl.P));
   return cuda_error(h, cudaGetLastError(), "tc_corr");
 }

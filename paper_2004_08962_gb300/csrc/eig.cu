@@ -433,7 +433,7 @@ hicu_status run_nullspace(hicu_handle* h, int64_t n64, int64_t r, const double* 
   if (flags & HICU_NULLSPACE_CLUSTER) {
     nct = cluster_eig_ctas(n);
     if (!nct) return set_error(h, HICU_ERR_UNSUPPORTED, "nullspace: no cluster solver for this n on this device");
-  } else if (!(flags & HICU_NULLSPACE_GRID) && n <= HICU_NULLSPACE_CLUSTER_AUTO_MAX) {
+  } else if (!(flags & HICU_NULLSPACE_GRID) && n <= h->auto_cluster_max) {
     nct = cluster_eig_ctas(n);
   }
   const int npad = nct ? cluster_eig_npad(n, nct) : (n + 1) / 2 * 2;
@@ -457,6 +457,7 @@ hicu_status run_nullspace(hicu_handle* h, int64_t n64, int64_t r, const double* 
     const int ntile = (npad / 2 + JT - 1) / JT;
     const long long ntiles = (long long)ntile * ntile;
     grid_blocks = (int)std::min<long long>(ntiles, (long long)h->num_sms * std::min(per_sm, 1));
+    if (h->max_coop_blocks > 0) grid_blocks = std::min(grid_blocks, h->max_coop_blocks);
     if (grid_blocks < 1) grid_blocks = 1;
   }
   double* part = (double*)ws_get(h, WS_EIG_PART, sizeof(double) * 2 * grid_blocks + 128, &s);

@@ -23,6 +23,8 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 
 #include "hicu_internal.cuh"
 
@@ -421,8 +423,12 @@ int cluster_eig_npad(int64_t n, int nct) { return (int)((n + 2 * nct - 1) / (2 *
 
 int cluster_eig_ctas(int64_t n) {
   if (n < 2 || n > CL_MAX_N) return 0;
-  static int cached[CL_MAX_N + 1] = {0};  // per n: 0 unknown, -1 unavailable, else cluster size
-  if (cached[n]) return cached[n] > 0 ? cached[n] : 0;
+  // per n: 0 unknown, -1 unavailable, else the cluster size (host threads of a batch share it)
+  static std::atomic<int> cached[CL_MAX_N + 1];
+  static std::mutex mu;
+  const int known = cached[n].load();
+  if (known) return known > 0 ? known : 0;
+  std::lock_guard<std::mutex> lock(mu);
   int found = -1;
   for (int nct : {16, 8}) {
     const int npad = cluster_eig_npad(n, nct);
@@ -434,11 +440,7 @@ int cluster_eig_ctas(int64_t n) {
       cudaGetLastError();
       continue;
     }
-    if (cudaFuncSetAttribute(jacobi_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
-      cudaGetLastError();
-      continue;
-    }
+    if (allow_max_dynamic_smem((const void*)jacobi_cluster_kernel) != cudaSuccess) continue;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cluster_cfg(nct, smem, 0, attr);
     int clusters = 0;
@@ -448,7 +450,7 @@ int cluster_eig_ctas(int64_t n) {
     }
     cudaGetLastError();
   }
-  cached[n] = found;
+  cached[n].store(found);
   return found > 0 ? found : 0;
 }
 
@@ -480,7 +482,7 @@ hicu_status run_nullspace_cluster(hicu_handle* h, int n, int npad, int nct, int6
   J.tol2 = (flags & 2) ? 1e-16 : 1e-22;
   cudaLaunchAttribute attr[1];
   const size_t smem = cluster_smem(npad, nct);
-  cudaError_t e = cudaFuncSetAttribute(jacobi_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_dynamic_smem((const void*)jacobi_cluster_kernel);
   if (e != cudaSuccess) return cuda_error(h, e, "nullspace cluster smem");
   cudaLaunchConfig_t cfg = cluster_cfg(nct, smem, st, attr);
   HICU_LAUNCH(h, K_EIG, st, e = cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel, J));

@@ -153,12 +153,20 @@ struct hicu_handle {
   int eig_npad = 0;  // padded size of the stored eigenvectors (grid and cluster solvers pad differently)
   bool eig_have_v = false;
   int* eig_info = nullptr;  // device words of the last Jacobi run (sweeps, converged, buffer)
+  // eigen-solver choice: largest n the size rule gives to the cluster solver, and a cap on
+  // the grid solver's CTAs (0: one per SM) so that concurrent lanes can co-reside
+  int auto_cluster_max = HICU_NULLSPACE_CLUSTER_AUTO_MAX;
+  int max_coop_blocks = 0;
   // launch accounting and optional event timing of one kernel class
   int prof_class = -1;
   long long launches_all = 0;
   long long launches_class = 0;
   std::vector<cudaEvent_t> prof_events;
   size_t prof_used = 0;
+  // batch lanes (hicu_reconstruct_batched): one sub-handle and stream each, created on demand
+  std::vector<hicu_handle*> lane_h;
+  std::vector<cudaStream_t> lane_st;
+  std::vector<cudaEvent_t> batch_ev;
 };
 
 namespace hicu {
@@ -201,6 +209,10 @@ enum KClass { K_GRAM = 0, K_EIG = 1, K_CONV = 2, K_ADJOINT = 3, K_JL = 4, K_MISC
 void prof_begin(hicu_handle* h, int cls, cudaStream_t st);
 void prof_end(hicu_handle* h, int cls, cudaStream_t st);
 
+// Raise a kernel's dynamic shared-memory cap to the device's opt-in maximum, once per
+// kernel and device (thread-safe).  Never set per launch: host threads launching the same
+// kernel with different sizes would race on the attribute.
+cudaError_t allow_max_dynamic_smem(const void* kernel);
 hicu_status set_error(hicu_handle* h, hicu_status s, const std::string& msg);
 hicu_status cuda_error(hicu_handle* h, cudaError_t e, const char* where);
 void* ws_get(hicu_handle* h, int slot, size_t bytes, hicu_status* st);

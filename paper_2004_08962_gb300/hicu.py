@@ -25,7 +25,7 @@ EXPORTED = (
     "hicu_jl_compress",
     "hicu_conv_null", "hicu_conv_null_adjoint", "hicu_gd_step_filters", "hicu_gd_step",
     "hicu_reconstruct", "hicu_profile_select", "hicu_profile_read", "hicu_conv_null_noalloc",
-    "hicu_profile_eig_sweeps",
+    "hicu_profile_eig_sweeps", "hicu_batch_order", "hicu_reconstruct_batched",
 )
 
 HICU_K_GRAM, HICU_K_EIG, HICU_K_CONV, HICU_K_ADJOINT, HICU_K_JL, HICU_K_MISC = 0, 1, 2, 3, 4, 5
@@ -48,11 +48,21 @@ class hicu_stage(ctypes.Structure):
 class hicu_params(ctypes.Structure):
     _fields_ = [("rank", c_int64), ("nstages", c_int32), ("stages", POINTER(hicu_stage)),
                 ("seed", c_uint64), ("jl", c_int32), ("prec", c_int32),
-                ("gram_on_current", c_int32), ("init", c_int32)]
+                ("gram_on_current", c_int32), ("init", c_int32), ("eig_solver", c_int32)]
 
 
 class hicu_log(ctypes.Structure):
     _fields_ = [("J", POINTER(c_double)), ("objective", POINTER(c_double)), ("eta", POINTER(c_double))]
+
+
+class hicu_problem(ctypes.Structure):
+    _fields_ = [("geom", hicu_geom), ("x0", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("params", hicu_params), ("x_out", ctypes.c_void_p), ("log", POINTER(hicu_log))]
+
+
+class hicu_slice_report(ctypes.Structure):
+    _fields_ = [("start_ms", c_double), ("end_ms", c_double), ("lane", c_int32), ("status", c_int32),
+                ("gd_steps", c_int64)]
 
 
 class HicuError(RuntimeError):
@@ -97,6 +107,8 @@ def lib() -> ctypes.CDLL:
             "hicu_conv_null_noalloc": ([G, R, P, P, c_int32, P, P, P], c_int32),
             "hicu_profile_eig_sweeps": ([P, POINTER(c_int64)], c_int32),
             "hicu_profile_read": ([P, POINTER(c_double), POINTER(c_int64), POINTER(c_int64)], c_int32),
+            "hicu_batch_order": ([c_int32, P, POINTER(c_int32), POINTER(c_double)], c_int32),
+            "hicu_reconstruct_batched": ([P, c_int32, P, c_int32, P, P], c_int32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -303,7 +315,8 @@ def hicu_gd_step(h: Handle, geom, region, y: torch.Tensor, mask: Optional[torch.
 
 
 def make_params(rank: int, stages, seed: int = 0, jl: int = HICU_JL_PROJECTOR, prec: int = HICU_FP32,
-                gram_on_current: bool = False, init: int = 0):
+                gram_on_current: bool = False, init: int = 0, eig_solver: Optional[str] = None):
+    """eig_solver: None (by size), "grid" or "cluster"."""
     """stages: sequence of (off, ext, iters, gd_steps, p)."""
     arr = (hicu_stage * len(stages))()
     for i, (off, ext, iters, gd, p) in enumerate(stages):
@@ -320,6 +333,7 @@ def make_params(rank: int, stages, seed: int = 0, jl: int = HICU_JL_PROJECTOR, p
     prm.prec = int(prec)
     prm.gram_on_current = 1 if gram_on_current else 0
     prm.init = int(init)
+    prm.eig_solver = {None: 0, "grid": HICU_NULLSPACE_GRID, "cluster": HICU_NULLSPACE_CLUSTER}[eig_solver]
     prm._keep = arr  # keep the stage array alive with the struct
     return prm
 
@@ -348,3 +362,45 @@ def hicu_reconstruct(h: Handle, geom, x0: torch.Tensor, mask: torch.Tensor, para
         return x_out, {"J": list(logs["J"])[:it], "objective": list(logs["objective"])[:st],
                        "eta": list(logs["eta"])[:st]}
     return x_out
+
+
+# ------------------------------------------------------------------ batches
+
+def make_problem_struct(geom, x0: torch.Tensor, mask: torch.Tensor, params: hicu_params,
+                        x_out: torch.Tensor) -> hicu_problem:
+    pr = hicu_problem()
+    pr.geom = geom
+    pr.x0 = x0.data_ptr()
+    pr.mask = mask.data_ptr()
+    pr.params = params
+    pr.x_out = x_out.data_ptr()
+    pr.log = None
+    pr._keep = (params, x0, mask, x_out)
+    return pr
+
+
+def hicu_batch_order(problems: Sequence[hicu_problem]):
+    """-> (order, cost): start order of hicu_reconstruct_batched and the cost estimates."""
+    n = len(problems)
+    arr = (hicu_problem * max(n, 1))(*problems)
+    order = (c_int32 * max(n, 1))()
+    cost = (c_double * max(n, 1))()
+    st = lib().hicu_batch_order(n, ctypes.cast(arr, ctypes.c_void_p), order, cost)
+    if st != 0:
+        raise HicuError(st, lib().hicu_status_string(st).decode())
+    return list(order)[:n], list(cost)[:n]
+
+
+def hicu_reconstruct_batched(h: Handle, problems: Sequence[hicu_problem], lanes: int = 0, stream=None,
+                             check: bool = True):
+    """Runs every problem (hicu_reconstruct semantics); returns one report dict per problem.
+    With check=False a failing problem does not raise; its report carries the status."""
+    n = len(problems)
+    arr = (hicu_problem * max(n, 1))(*problems)
+    rep = (hicu_slice_report * max(n, 1))()
+    st = lib().hicu_reconstruct_batched(h.ptr, n, ctypes.cast(arr, ctypes.c_void_p), int(lanes),
+                                        ctypes.cast(rep, ctypes.c_void_p), _stream(stream))
+    if check:
+        h._check(st)
+    return [{"start_ms": r.start_ms, "end_ms": r.end_ms, "lane": r.lane, "status": r.status,
+             "gd_steps": r.gd_steps} for r in list(rep)[:n]], st
