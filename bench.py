@@ -264,6 +264,97 @@ def run_profile_case(kind: str, size: int) -> int:
     return 0
 
 
+# ------------------------------------------------------------ batched workload
+
+BATCH_METRIC = "HICU GD-iters/s (batched: 48 uneven 2D slices + 4 multi-shot 32-channel slices)"
+
+
+def run_batch(args, rank, world):
+    """The uneven batch (48 slices of 128^2..320^2 x 4..16 coils at R 3..5, plus 4 multi-shot
+    256^2 slices stacked as 32 channels) through hicu_reconstruct_batched: aggregate descent
+    steps per second, per-slice steps per second and completion latency percentiles, and the
+    FP64 oracle's reconstruction of the cheapest slice for the NRMSE / SER check."""
+    import torch
+    from paper_2004_08962_gb300 import build, hicu
+    from synth.phantoms import make_batch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if rank == 0:
+        build.build()
+    batch = make_batch(seed=4000 + 97 * rank)
+    prec = hicu.HICU_FP32 if args.prec == "fp32" else hicu.HICU_SPLIT_BF16
+    h = hicu.Handle()
+    probs, outs, x0s, masks = [], [], [], []
+    for pb in batch:
+        per_coil = pb.mask.ndim == 4
+        geom = hicu.make_geom(pb.dims, pb.ncoil, pb.kernel, mask_per_coil=per_coil)
+        prm = hicu.make_params(pb.rank, schedule(pb), seed=pb.seed, jl=hicu.HICU_JL_PROJECTOR, prec=prec)
+        x0 = torch.from_numpy(pb.x0).cuda()
+        m = torch.from_numpy(pb.mask).cuda()
+        out = torch.empty_like(x0)
+        probs.append(hicu.make_problem_struct(geom, x0, m, prm, out))
+        outs.append(out)
+    steps_total = sum(gd_steps_per_recon(pb) for pb in batch)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        hicu.hicu_reconstruct_batched(h, probs, lanes=args.lanes)
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.synchronize()
+    sampler.start()
+    hicu.hicu_profile_select(h, -1)
+    _, _, launches0 = hicu.hicu_profile_read(h)
+    stream = torch.cuda.current_stream()
+    total_ms, reports = 0.0, []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep, _ = hicu.hicu_reconstruct_batched(h, probs, lanes=args.lanes)
+        e1.record(stream)    # the call returns after every lane finished
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        reports.append(rep)
+    _, _, launches1 = hicu.hicu_profile_read(h)
+    clocks = sampler.stop()
+    value = steps_total * args.steps / (total_ms / 1e3)
+    lat = [r["end_ms"] for rep in reports for r in rep]
+    per_slice = [r["gd_steps"] / ((r["end_ms"] - r["start_ms"]) / 1e3) for rep in reports for r in rep]
+    pct = lambda v, q: float(np.percentile(np.asarray(v), q))
+    line = {"metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "bf16x2",
+            "data": "synthetic",
+            "config": {"workload": "batch_uneven_52", "slices": len(batch), "lanes": args.lanes,
+                       "gd_steps_per_batch": steps_total,
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+            "per_slice_gd_iters_per_s": {"p50": pct(per_slice, 50), "min": min(per_slice),
+                                         "max": max(per_slice)},
+            "completion_latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": max(lat)},
+            "gpu_launches": (launches1 - launches0) // max(args.steps, 1),
+            "clocks": clocks}
+    if not args.no_cpu_baseline:
+        # FP64 oracle on the cheapest slice of the batch: NRMSE / SER of the GPU result, and its time
+        from oracle import hicu_oracle as O
+        order, cost = hicu.hicu_batch_order(probs)
+        i = order[-1]
+        pb = batch[i]
+        og = O.Geom(pb.dims, pb.ncoil, pb.kernel, pb.circular)
+        st = [O.StageSpec(O.Region(s.off, s.ext), s.iters, s.gd_steps, s.p) for s in pb.stages]
+        t0 = time.perf_counter()
+        ref = O.reconstruct(pb.x0, pb.mask, og, st, pb.rank, seed=pb.seed, jl_mode="projector")
+        t_or = time.perf_counter() - t0
+        x = outs[i].cpu().numpy()
+        line["oracle_check"] = {"slice": pb.name, "nrmse": float(np.linalg.norm(x - ref) / np.linalg.norm(ref)),
+                                "ser_db_gpu": O.ser_db(pb.x_full, x), "ser_db_oracle": O.ser_db(pb.x_full, ref)}
+        line["cpu_baseline"] = {"value": gd_steps_per_recon(pb) / t_or, "unit": UNIT, "cores": blas_threads(),
+                                "kind": "oracle", "sample": f"full reconstruction of the cheapest slice "
+                                                            f"({pb.name}, {t_or:.1f} s of CPU)"}
+    print(json.dumps(line), flush=True)
+    h.close()
+    return 0
+
+
 # -------------------------------------------------------------------- GPU arm
 
 def main():
@@ -277,6 +368,9 @@ def main():
     ap.add_argument("--profile", default=None, choices=["eig", "tc_step"],
                     help="run one small fixed case for an ncu capture and exit")
     ap.add_argument("--size", type=int, default=2048, help="image size of the tc_step profile case")
+    ap.add_argument("--workload", default="brain", choices=["brain", "batch"],
+                    help="brain: the 256x256x8 slice (default line); batch: the uneven 52-slice batch")
+    ap.add_argument("--lanes", type=int, default=8, help="worker lanes of the batched workload")
     args = ap.parse_args()
     if args.profile:
         return run_profile_case(args.profile, args.size)
@@ -287,6 +381,8 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batch":
+        return run_batch(args, rank, world)
 
     import torch
     import torch.distributed as dist

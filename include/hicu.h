@@ -346,8 +346,10 @@ hicu_status hicu_batch_order(int32_t nslices, const hicu_problem* problems, int3
  *   `lanes` worker lanes (0: min(nslices, 8)), each with its own stream,
  *   workspace and host thread, take problems from one queue in hicu_batch_order
  *   order.  Problems with n <= 256 whose params.eig_solver is 0 use the cluster
- *   eigen-solver, which occupies 16 SMs and leaves the others to the other lanes;
- *   grid-solver launches are limited to num_SMs / lanes CTAs for the same reason.
+ *   eigen-solver, which occupies 16 SMs and leaves the others to the other lanes.
+ *   Grid-solver launches (n > 256) of all lanes go, in order, to one shared
+ *   high-priority stream: two grid-barrier kernels never wait for each other's
+ *   SMs, and a pending one gets SMs first as they free up.
  *   Every problem gives the same result as hicu_reconstruct with the same
  *   params (and that eig_solver): lanes share no mutable state.
  *   The lanes start after the work already queued on `stream`; the call returns

@@ -204,6 +204,9 @@ extern "C" hicu_status hicu_destroy(hicu_handle* h) {
   for (auto* c : h->lane_h) hicu_destroy(c);
   for (auto st : h->lane_st) cudaStreamDestroy(st);
   for (auto e : h->batch_ev) cudaEventDestroy(e);
+  if (h->coop_st_own) cudaStreamDestroy(h->coop_st_own);
+  if (h->coop_in) cudaEventDestroy(h->coop_in);
+  if (h->coop_out) cudaEventDestroy(h->coop_out);
   for (auto& w : h->ws)
     if (w.ptr) cudaFree(w.ptr);
   for (auto e : h->prof_events) cudaEventDestroy(e);

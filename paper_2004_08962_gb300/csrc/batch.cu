@@ -95,9 +95,21 @@ extern "C" hicu_status hicu_reconstruct_batched(hicu_handle* h, int32_t nslices,
     h->lane_h.push_back(c);
     h->lane_st.push_back(ls);
   }
+  if (!h->coop_st_own) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    e = cudaStreamCreateWithPriority(&h->coop_st_own, cudaStreamNonBlocking, hi);
+    if (e != cudaSuccess) return cuda_error(h, e, "batched: priority stream");
+  }
   for (int i = 0; i < L; ++i) {
-    h->lane_h[i]->auto_cluster_max = 256;  // cluster solver wherever it applies
-    h->lane_h[i]->max_coop_blocks = std::max(8, h->num_sms / L);
+    hicu_handle* c = h->lane_h[i];
+    c->auto_cluster_max = 256;  // cluster solver wherever it applies
+    c->coop_mu = &h->coop_mu_own;
+    c->coop_st = h->coop_st_own;
+    if (!c->coop_in && cudaEventCreateWithFlags(&c->coop_in, cudaEventDisableTiming) != cudaSuccess)
+      return cuda_error(h, cudaGetLastError(), "batched: event");
+    if (!c->coop_out && cudaEventCreateWithFlags(&c->coop_out, cudaEventDisableTiming) != cudaSuccess)
+      return cuda_error(h, cudaGetLastError(), "batched: event");
   }
   while ((int)h->batch_ev.size() < 2 * nslices + 1) {
     cudaEvent_t ev;

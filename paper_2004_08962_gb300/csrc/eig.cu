@@ -457,7 +457,6 @@ hicu_status run_nullspace(hicu_handle* h, int64_t n64, int64_t r, const double* 
     const int ntile = (npad / 2 + JT - 1) / JT;
     const long long ntiles = (long long)ntile * ntile;
     grid_blocks = (int)std::min<long long>(ntiles, (long long)h->num_sms * std::min(per_sm, 1));
-    if (h->max_coop_blocks > 0) grid_blocks = std::min(grid_blocks, h->max_coop_blocks);
     if (grid_blocks < 1) grid_blocks = 1;
   }
   double* part = (double*)ws_get(h, WS_EIG_PART, sizeof(double) * 2 * grid_blocks + 128, &s);
@@ -528,9 +527,21 @@ hicu_status run_nullspace(hicu_handle* h, int64_t n64, int64_t r, const double* 
   J.gs.timeout_ns = 2000000000ull;  // 2 s per wait
   void* args[] = {&J};
   cudaError_t e;
-  HICU_LAUNCH(h, K_EIG, st,
-              e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(grid_blocks), dim3(threads),
-                                              args, 0, st));
+  if (h->coop_mu) {  // batch lane: on the shared high-priority stream, in order
+    std::lock_guard<std::mutex> lock(*h->coop_mu);
+    e = cudaEventRecord(h->coop_in, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->coop_st, h->coop_in, 0);
+    if (e == cudaSuccess)
+      HICU_LAUNCH(h, K_EIG, h->coop_st,
+                  e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(grid_blocks), dim3(threads),
+                                                  args, 0, h->coop_st));
+    if (e == cudaSuccess) e = cudaEventRecord(h->coop_out, h->coop_st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->coop_out, 0);
+  } else {
+    HICU_LAUNCH(h, K_EIG, st,
+                e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(grid_blocks), dim3(threads),
+                                                args, 0, st));
+  }
   if (e != cudaSuccess) return cuda_error(h, e, "nullspace jacobi launch");
   HICU_LAUNCH(h, K_MISC, st, eig_rank_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, npad, A0, A1, info, scale, rank, eigvals));
   HICU_LAUNCH(h, K_MISC, st, eig_gather_q_kernel<<<blocks, 256, 0, st>>>(n, npad, n - (int)r, V, rank, (double2*)Q));

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -153,10 +154,17 @@ struct hicu_handle {
   int eig_npad = 0;  // padded size of the stored eigenvectors (grid and cluster solvers pad differently)
   bool eig_have_v = false;
   int* eig_info = nullptr;  // device words of the last Jacobi run (sweeps, converged, buffer)
-  // eigen-solver choice: largest n the size rule gives to the cluster solver, and a cap on
-  // the grid solver's CTAs (0: one per SM) so that concurrent lanes can co-reside
+  // eigen-solver choice: largest n the size rule gives to the cluster solver
   int auto_cluster_max = HICU_NULLSPACE_CLUSTER_AUTO_MAX;
-  int max_coop_blocks = 0;
+  // batch lanes: the cooperative (grid-barrier) launches of all lanes go to one shared
+  // high-priority stream, in order, so that two of them never wait for each other's SMs and
+  // their pending CTAs come first when SMs free up
+  std::mutex* coop_mu = nullptr;     // guards the shared stream (owned by the batch parent)
+  cudaStream_t coop_st = nullptr;    // shared stream (owned by the batch parent)
+  cudaEvent_t coop_in = nullptr;     // this lane's work up to the launch
+  cudaEvent_t coop_out = nullptr;    // the launch's completion
+  std::mutex coop_mu_own;
+  cudaStream_t coop_st_own = nullptr;
   // launch accounting and optional event timing of one kernel class
   int prof_class = -1;
   long long launches_all = 0;
