@@ -175,6 +175,37 @@ def conv_null_adjoint(R: np.ndarray, geom: Geom, reg: Region, filters: np.ndarra
     return g
 
 
+def filter_gradient(x: np.ndarray, geom: Geom, reg: Region, Rbar: np.ndarray) -> np.ndarray:
+    """Adjoint of v -> H(x) v: F[k] = H(x)^H Rbar[:, k], returned as filters (p, C, kz, ky, kx).
+
+    F_k[c, d] = sum_{p_out} conj(x_c[p_out + d]) Rbar[p_out, k].  The filters are the
+    unknowns of the annihilation relation H(x) v = 0 (Theory section), so this is the
+    gradient of Re<Rbar, H(x) v> with respect to v; with Rbar = H(x) v it equals the Gram
+    product (H^H H) v.  Rbar has the shape of conv_null's output, (sz, sy, sx, p).
+    """
+    _check(x, geom, reg)
+    x = np.asarray(x, dtype=np.complex128)
+    Rb = np.asarray(Rbar, dtype=np.complex128)
+    kx, ky, kz = geom.kernel
+    F = np.zeros((Rb.shape[-1], geom.ncoil, kz, ky, kx), dtype=np.complex128)
+    for dz, dy, dx in _offsets(geom):
+        blk = _shifted_block(x, geom, reg, dz, dy, dx)            # (C, sz, sy, sx)
+        F[:, :, dz, dy, dx] = np.einsum("czyx,zyxk->kc", np.conj(blk), Rb)
+    return F
+
+
+def project_unobserved(x: np.ndarray, geom: Geom, reg: Region, mask: Optional[np.ndarray]) -> np.ndarray:
+    """(1 - M) o x on the region S and 0 outside it (hard data consistency, Theory section)."""
+    x = np.asarray(x, dtype=np.complex128)
+    out = np.zeros_like(x)
+    z0, y0, x0 = reg.off[2], reg.off[1], reg.off[0]
+    z1, y1, x1 = z0 + reg.ext[2], y0 + reg.ext[1], x0 + reg.ext[0]
+    out[:, z0:z1, y0:y1, x0:x1] = x[:, z0:z1, y0:y1, x0:x1]
+    if mask is not None:
+        out *= (1 - _mask4(mask, out.shape))
+    return out
+
+
 def _mask4(mask: np.ndarray, shape) -> np.ndarray:
     m = np.asarray(mask).astype(np.float64)
     if m.ndim == 3:

@@ -230,6 +230,37 @@ def test_adjoint_identity(i):
 
 
 @pytest.mark.parametrize("i", range(len(SMALL_CASES)))
+def test_filter_gradient_matches_brute_force_and_gram(i):
+    """F = H(x)^H Rbar against the brute-force Hankel matrix; the adjoint identity in the filter
+    variable; and F(x, H(x) v) = (H^H H) v, the Gram product."""
+    geom, reg, x, rng = make_case(i)
+    p = 3
+    Hb = brute_hankel(x, geom, reg)
+    Rb = random_complex(rng, O.out_shape(geom, reg) + (p,))
+    F = O.filter_gradient(x, geom, reg, Rb)
+    ref = (Hb.conj().T @ Rb.reshape(-1, p)).T                     # (p, n)
+    np.testing.assert_allclose(F.reshape(p, -1), ref, rtol=1e-13, atol=1e-12)
+    f = rand_filters(rng, geom, p)
+    lhs = np.vdot(Rb, O.conv_null(x, geom, reg, f))
+    rhs = np.vdot(F, f)
+    assert abs(lhs - rhs) < 1e-12 * (abs(lhs) + 1)
+    FG = O.filter_gradient(x, geom, reg, O.conv_null(x, geom, reg, f))
+    G = Hb.conj().T @ Hb
+    np.testing.assert_allclose(FG.reshape(p, -1), (G @ f.reshape(p, -1).T).T, rtol=1e-12, atol=1e-11)
+
+
+@pytest.mark.parametrize("i", range(len(SMALL_CASES)))
+def test_project_unobserved_by_hand(i):
+    geom, reg, x, rng = make_case(i)
+    mask = (rng.random(x.shape[1:]) < 0.4).astype(np.uint8)
+    out = O.project_unobserved(x, geom, reg, mask)
+    for c, z, y, xx in itertools.product(*(range(d) for d in x.shape)):
+        inside = all(reg.off[a] <= v < reg.off[a] + reg.ext[a] for a, v in enumerate((xx, y, z)))
+        want = x[c, z, y, xx] if (inside and not mask[z, y, xx]) else 0.0
+        assert out[c, z, y, xx] == want
+
+
+@pytest.mark.parametrize("i", range(len(SMALL_CASES)))
 def test_gram_matches_explicit_hankel(i):
     geom, reg, x, rng = make_case(i)
     Hb = brute_hankel(x, geom, reg)
