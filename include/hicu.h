@@ -270,6 +270,32 @@ hicu_status hicu_conv_null_adjoint(hicu_handle* h, const hicu_geom* geom,
                                    float* g, double* gnorm2, int32_t prec, void* stream);
 
 /*
+ * hicu_conv_null_filter_grad - F_k[c, d] = sum_{o in V(S)} conj(x_c[o + d]) Rbar[o, k],
+ * i.e. F = H(x)^H Rbar: the adjoint of the convolution v -> H(x) v in the filter
+ * variable (the annihilating filters of the Theory section are its unknowns), so
+ * <H(x) v, Rbar> = <v, F>; with Rbar = H(x) v it is the Gram product (H^H H) v.
+ * Used for gradients with respect to the filters.
+ *   x     : complex64 k-space [C][Nz][Ny][Nx] (device), read on S as hicu_conv_null
+ *   Rbar  : complex64 [sz][sy][sx][p] (device), hicu_conv_null's output layout
+ *   fbar  : complex64 [p][n] (device), filter layout [p][C][kz][ky][kx]; fully written
+ * Complex FP32 products, FP32 partial sums per CTA, FP64 sum over CTAs in a fixed
+ * order (deterministic).  HICU_ERR_UNSUPPORTED if one filter's coefficients (n
+ * complex values) and the staging tiles exceed a CTA's shared memory.
+ */
+hicu_status hicu_conv_null_filter_grad(hicu_handle* h, const hicu_geom* geom, const hicu_region* region,
+                                       const float* x, const float* Rbar, int32_t p, float* fbar,
+                                       void* stream);
+
+/*
+ * hicu_project_unobserved - out = (1 - M) o x on S and 0 outside S (the projection
+ * of hard data consistency: only unobserved entries of the region move).
+ *   mask : nullable (NULL = keep every entry of S); layout as the hicu_geom mask
+ *   x, out : complex64 [C][Nz][Ny][Nx] (device); out may be x (in place)
+ */
+hicu_status hicu_project_unobserved(hicu_handle* h, const hicu_geom* geom, const hicu_region* region,
+                                    const uint8_t* mask, const float* x, float* out, void* stream);
+
+/*
  * hicu_gd_step_filters - one descent step for a fixed filter bank Q~ with
  * exact line search (Algorithm 1 steps 7-8; Theory, ELS paragraph):
  *   g = (1 - M) o sum_k H^H(H(y) q~_k),  D = sum_k ||H(g) q~_k||^2,

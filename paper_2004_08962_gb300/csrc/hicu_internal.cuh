@@ -209,7 +209,10 @@ enum Slot {
   WS_TC_R,        // split bf16 planes of R
   WS_TC_BC,       // tensor-core B planes, conv
   WS_TC_BA,       // tensor-core B planes, adjoint
+  WS_FGRAD,       // filter-gradient partials per CTA
+  WS_COUNT
 };
+static_assert(WS_COUNT <= hicu_handle::kSlots, "workspace slots");
 
 // Kernel classes for launch accounting / event timing (hicu_kernel_class in hicu.h).
 enum KClass { K_GRAM = 0, K_EIG = 1, K_CONV = 2, K_ADJOINT = 3, K_JL = 4, K_MISC = 5, K_CONV_TC = 6,

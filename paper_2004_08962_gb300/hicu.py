@@ -26,6 +26,7 @@ EXPORTED = (
     "hicu_conv_null", "hicu_conv_null_adjoint", "hicu_gd_step_filters", "hicu_gd_step",
     "hicu_reconstruct", "hicu_profile_select", "hicu_profile_read", "hicu_conv_null_noalloc",
     "hicu_profile_eig_sweeps", "hicu_batch_order", "hicu_reconstruct_batched",
+    "hicu_conv_null_filter_grad", "hicu_project_unobserved",
 )
 
 HICU_K_GRAM, HICU_K_EIG, HICU_K_CONV, HICU_K_ADJOINT, HICU_K_JL, HICU_K_MISC = 0, 1, 2, 3, 4, 5
@@ -108,6 +109,8 @@ def lib() -> ctypes.CDLL:
             "hicu_profile_eig_sweeps": ([P, POINTER(c_int64)], c_int32),
             "hicu_profile_read": ([P, POINTER(c_double), POINTER(c_int64), POINTER(c_int64)], c_int32),
             "hicu_batch_order": ([c_int32, P, POINTER(c_int32), POINTER(c_double)], c_int32),
+            "hicu_conv_null_filter_grad": ([P, G, R, P, P, c_int32, P, P], c_int32),
+            "hicu_project_unobserved": ([P, G, R, P, P, P, P], c_int32),
             "hicu_reconstruct_batched": ([P, c_int32, P, c_int32, P, P], c_int32),
         }
         for name, (args, res) in sig.items():
@@ -253,10 +256,34 @@ def hicu_jl_compress(h: Handle, Q: torch.Tensor, p: int, mode: int = HICU_JL_NUL
     return bank
 
 
+def hicu_conv_null_filter_grad(h: Handle, geom, region, x: torch.Tensor, Rbar: torch.Tensor, stream=None):
+    """F = H(x)^H Rbar as a (p, n) complex64 filter bank."""
+    p = Rbar.shape[-1]
+    n = geom.ncoil * geom.k[0] * geom.k[1] * geom.k[2]
+    F = torch.empty((p, n), dtype=torch.complex64, device=x.device)
+    h._check(lib().hicu_conv_null_filter_grad(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(x),
+                                              _ptr(Rbar), p, _ptr(F), _stream(stream)))
+    return F
+
+
+def hicu_project_unobserved(h: Handle, geom, region, x: torch.Tensor, mask: Optional[torch.Tensor],
+                            out: Optional[torch.Tensor] = None, stream=None):
+    """(1 - M) o x on the region, 0 elsewhere."""
+    if out is None:
+        out = torch.empty_like(x)
+    h._check(lib().hicu_project_unobserved(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(mask),
+                                           _ptr(x), _ptr(out), _stream(stream)))
+    return out
+
+
 def hicu_conv_null(h: Handle, geom, region, x: torch.Tensor, filters: torch.Tensor,
-                   prec: int = HICU_FP32, want_objective: bool = False, stream=None):
+                   prec: int = HICU_FP32, want_objective: bool = False, stream=None, store_R: bool = True):
+    """store_R=False (with want_objective) only reduces ||R||^2 and returns (None, objective)."""
     p = filters.shape[0]
-    R = torch.empty(out_shape(geom, region) + (p,), dtype=torch.complex64, device=x.device)
+    if not store_R and not want_objective:
+        raise ValueError("store_R=False needs want_objective=True")
+    R = (torch.empty(out_shape(geom, region) + (p,), dtype=torch.complex64, device=x.device)
+         if store_R else None)
     obj = torch.zeros((1,), dtype=torch.float64, device=x.device) if want_objective else None
     h._check(lib().hicu_conv_null(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(x),
                                   _ptr(filters), p, _ptr(R), _ptr(obj), prec, _stream(stream)))
