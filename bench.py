@@ -134,6 +134,29 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ----------------------------------------------------------- rank aggregation
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def max_over_ranks(x: float, device) -> float:
+    """The largest value over the ranks of the process group (the value itself without one)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank_step: float, steps: int, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_rank_step * steps * world / seconds
+
+
 # ------------------------------------------------------------------ oracle arm
 
 def oracle_sample(pb, seed=11):
@@ -195,26 +218,6 @@ def run_reference(args, rank, world):
     sample = (f"per step: 1 centre-out outer iteration (Gram, eigh, 5 steps p=8) + 1 full-k-space "
               f"Gram/eigh + 1 full-k-space step (p=32), {statistics.mean(samples):.1f} s of CPU, "
               f"extrapolated to the 350-step schedule")
-    bf16_peak = peaks.get("bf16_tflops", 1855.5)
-    extra_roofs = {}
-    for c in (6, 7, 2, 3):
-        ms_c, nl_c = launches_per_class.get(c, (0.0, 0))
-        if nl_c == 0:
-            continue
-        fl = algorithmic_flops(pb, c)
-        ach = fl / (ms_c / 1e3) / 1e12
-        if c in (6, 7):
-            extra_roofs[KERNEL_NAMES[c]] = {
-                "bound": "tensor", "achieved": ach, "peak": bf16_peak, "unit": "TFLOP/s",
-                "frac": ach / bf16_peak, "traffic": None,
-                "note": "algorithmic 8 n p s flops; the split-bf16 form issues 3x that on the tensor "
-                        "pipe (hi*hi + hi*lo + lo*hi); timed with events over one warm-up reconstruction",
-                "avg_launch_us": ms_c * 1e3 / nl_c, "launches": nl_c}
-        else:
-            extra_roofs[KERNEL_NAMES[c]] = {
-                "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": None, "avg_launch_us": ms_c * 1e3 / nl_c,
-                "launches": nl_c}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * gd_steps_per_recon(pb) / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -278,10 +281,15 @@ def run_batch(args, rank, world):
     from paper_2004_08962_gb300 import build, hicu
     from synth.phantoms import make_batch
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import torch.distributed as dist
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     if rank == 0:
         build.build()
-    batch = make_batch(seed=4000 + 97 * rank)
+    barrier()
+    batch = make_batch(seed=4000 + 97 * rank)   # replicas: each rank reconstructs its own batch
     prec = hicu.HICU_FP32 if args.prec == "fp32" else hicu.HICU_SPLIT_BF16
     h = hicu.Handle()
     probs, outs, x0s, masks = [], [], [], []
@@ -298,8 +306,9 @@ def run_batch(args, rank, world):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
         hicu.hicu_reconstruct_batched(h, probs, lanes=args.lanes)
-    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler = ClockSampler(local)
     torch.cuda.synchronize()
+    barrier()
     sampler.start()
     hicu.hicu_profile_select(h, -1)
     _, _, launches0 = hicu.hicu_profile_read(h)
@@ -316,8 +325,15 @@ def run_batch(args, rank, world):
         total_ms += e0.elapsed_time(e1)
         reports.append(rep)
     _, _, launches1 = hicu.hicu_profile_read(h)
+    barrier()
     clocks = sampler.stop()
-    value = steps_total * args.steps / (total_ms / 1e3)
+    value = job_rate(steps_total, args.steps, world, max_over_ranks(total_ms, "cuda") / 1e3)
+    if rank != 0:
+        barrier()
+        if world > 1:
+            dist.destroy_process_group()
+        h.close()
+        return 0
     lat = [r["end_ms"] for rep in reports for r in rep]
     per_slice = [r["gd_steps"] / ((r["end_ms"] - r["start_ms"]) / 1e3) for rep in reports for r in rep]
     pct = lambda v, q: float(np.percentile(np.asarray(v), q))
@@ -333,7 +349,7 @@ def run_batch(args, rank, world):
             "completion_latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": max(lat)},
             "gpu_launches": (launches1 - launches0) // max(args.steps, 1),
             "clocks": clocks}
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:
         # FP64 oracle on the cheapest slice of the batch: NRMSE / SER of the GPU result, and its time
         from oracle import hicu_oracle as O
         order, cost = hicu.hicu_batch_order(probs)
@@ -351,6 +367,9 @@ def run_batch(args, rank, world):
                                 "kind": "oracle", "sample": f"full reconstruction of the cheapest slice "
                                                             f"({pb.name}, {t_or:.1f} s of CPU)"}
     print(json.dumps(line), flush=True)
+    barrier()
+    if world > 1:
+        dist.destroy_process_group()
     h.close()
     return 0
 
@@ -457,11 +476,8 @@ def main():
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tmax_s = t.item() / 1e3
-    value = steps_per * args.steps * world / tmax_s
+    tmax_s = max_over_ranks(total_ms, "cuda") / 1e3
+    value = job_rate(steps_per, args.steps, world, tmax_s)
 
     # the plain complex-FP32 form of the same reconstruction, same timing rules
     fp32_ms = None
@@ -480,6 +496,9 @@ def main():
             e1.synchronize()
             fp32_ms += e0.elapsed_time(e1)
 
+    fp32_value = None if fp32_ms is None else job_rate(steps_per, args.steps, world,
+                                                        max_over_ranks(fp32_ms, "cuda") / 1e3)
+
     # end-to-end through the C ABI with pinned host buffers (copies inside the call)
     x0h = torch.from_numpy(pb.x0).pin_memory()
     mh = torch.from_numpy(pb.mask).pin_memory()
@@ -495,10 +514,7 @@ def main():
         t0 = time.perf_counter()
         hicu.hicu_reconstruct(h, geom, x0h, mh, params, x_out=outh)
         e2e_s += time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = steps_per * args.steps * world / te.item()
+    e2e_value = job_rate(steps_per, args.steps, world, max_over_ranks(e2e_s, "cuda"))
     h2d = pb.x0.nbytes + pb.mask.nbytes
     d2h = pb.x0.nbytes
 
@@ -571,7 +587,7 @@ def main():
             "class_ms_per_step": {KERNEL_NAMES[c]: round(v, 3) for c, v in per_class.items()},
             "kernel_rooflines": extra_roofs,
             "plain_fp32": None if fp32_ms is None else {
-                "value": steps_per * args.steps * world / (fp32_ms / 1e3), "unit": UNIT,
+                "value": fp32_value, "unit": UNIT,
                 "ms_per_step": fp32_ms / args.steps},
             "clocks": clocks,
             "peaks_source": peak_src}

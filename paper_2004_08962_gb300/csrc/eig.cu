@@ -37,18 +37,16 @@ struct Rot {
 // alone (the usual relative threshold, which protects tiny eigenvalues).
 __device__ __forceinline__ Rot make_rot(double a, double c, double2 b) {
   Rot R;
-  // the angle and phase depend only on ratios: bring the entries into FP32 range first
-  // (exact power-of-two scale)
-  const double big = fmax(fmax(fabs(a), fabs(c)), fmax(fabs(b.x), fabs(b.y)));
-  const double sc = (big > 0.0 && big <= 1.7e308) ? ldexp(1.0, -ilogb(big)) : 1.0;
-  const float bx = (float)(b.x * sc), by = (float)(b.y * sc);
+  // the solver pre-scales A by a power of two to max |A_ij| < 1, so the FP32 conversions
+  // below cannot overflow (entries below the FP32 range only ever mean |b| ~ 0)
+  const float bx = (float)b.x, by = (float)b.y;
   const float ab = hypotf(bx, by);
-  const float thr = 1e-17f * sqrtf(fabsf((float)(a * sc))) * sqrtf(fabsf((float)(c * sc)));
+  const float thr = 1e-17f * sqrtf(fabsf((float)a)) * sqrtf(fabsf((float)c));
   if (!(ab > thr) || !(ab > 0.f)) {
     R.cs = 1.0; R.sn = 0.0; R.ex = 1.0; R.ey = 0.0; R.ident = 1;
     return R;
   }
-  const float tau = (float)((c - a) * sc) / (2.f * ab);
+  const float tau = (float)(c - a) / (2.f * ab);
   float t;
   if (fabsf(tau) > 1e18f) t = 0.5f / tau;
   else t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));

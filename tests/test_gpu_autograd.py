@@ -172,3 +172,38 @@ def test_gradient_step_on_filters_reduces_objective(H):
         t = (torch.vdot(g.reshape(-1), g.reshape(-1)).real / (2 * op.null_objective(xt, g))).item()
         F1 = op.null_objective(xt, ft - t * g)
     assert F1.item() < F0.item()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_autograd_full_size_brain_slice(H, prec):
+    """The 256 x 256 x 8-coil slice (n = 200, p = 32): gradients of ||H(x) f||^2 with respect to
+    x and the filters against the FP64 oracle and finite differences, in the plain FP32 form
+    (bound 1e-5) and the split-BF16 tensor-core form (bound 1e-3)."""
+    from paper_2004_08962_gb300 import hicu
+    from paper_2004_08962_gb300.autograd import HicuConv
+    from synth.phantoms import make_problem
+    pb = make_problem("2d_brain_256")
+    og = O.Geom(pb.dims, pb.ncoil, pb.kernel)
+    reg = O.full_region(og)
+    op = HicuConv(H, pb.dims, pb.ncoil, pb.kernel,
+                  prec=hicu.HICU_FP32 if prec == "fp32" else hicu.HICU_SPLIT_BF16)
+    rng = np.random.default_rng(21)
+    p = 32
+    f = (random_complex(rng, (p, og.n)) * 0.05).astype(np.complex64)
+    x = pb.x0
+    xt = torch.from_numpy(x).cuda().requires_grad_(True)
+    ft = torch.from_numpy(f).cuda().requires_grad_(True)
+    F = op.null_objective(xt, ft)
+    F.backward()
+    R = O.conv_null(x, og, reg, filt(f, og))
+    tol = 1e-5 if prec == "fp32" else 1e-3
+    assert abs(F.item() - np.sum(np.abs(R) ** 2)) < tol * F.item()
+    assert rel(xt.grad.cpu().numpy(), 2 * O.conv_null_adjoint(R, og, reg, filt(f, og))) < tol
+    assert rel(ft.grad.cpu().numpy(), 2 * O.filter_gradient(x, og, reg, R).reshape(p, -1)) < tol
+    vx = torch.from_numpy((random_complex(rng, x.shape) * 0.02 * np.abs(x).max()).astype(np.complex64)).cuda()
+    vf = torch.from_numpy((random_complex(rng, f.shape) * 0.002).astype(np.complex64)).cuda()
+    lx = lambda t: op.null_objective(t, ft.detach())
+    lf = lambda t: op.null_objective(xt.detach(), t)
+    for l, t, v, g in ((lx, xt, vx, xt.grad), (lf, ft, vf, ft.grad)):
+        fd, an = _fd(l, t.detach(), v), _dir(g, v)
+        assert abs(fd - an) <= 10 * tol * abs(an) + tol * F.item(), (fd, an)
