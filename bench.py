@@ -234,30 +234,54 @@ def run_reference(args, rank, world):
 # ----------------------------------------------------------- profiling cases
 
 def run_profile_case(kind: str, size: int) -> int:
-    """Small fixed workloads for ncu captures of one kernel (no timing, no JSON line)."""
+    """Small fixed workloads for ncu captures of one kernel (no timing, no JSON line).
+
+    eig / eig_cluster: the brain slice's Gram (n = 200), one cold solve then one warm
+        split-criterion solve of a perturbed Gram on the grid / cluster solver (the warm one
+        is the launch a reconstruction repeats: capture with -s 1 -c 1)
+    tc_step: one split-BF16 descent step on a size x size x 8-coil slice, p = 32
+    fgrad: the filter gradient H(x)^H R on the brain slice, p = 32
+    recon: one full reconstruction of the brain slice (for the launch list)
+    """
     import torch
     from paper_2004_08962_gb300 import build, hicu
     from synth.phantoms import _slice_2d, make_problem
     build.build()
     h = hicu.Handle()
-    if kind == "eig":
-        pb = make_problem(WORKLOAD)
-        geom = hicu.make_geom(pb.dims, pb.ncoil, pb.kernel)
-        reg = hicu.make_region((0, 0, 0), pb.dims)
+    pb = make_problem(WORKLOAD)
+    geom = hicu.make_geom(pb.dims, pb.ncoil, pb.kernel)
+    reg = hicu.make_region((0, 0, 0), pb.dims)
+    if kind in ("eig", "eig_cluster"):
+        solver = "grid" if kind == "eig" else "cluster"
         G = hicu.hicu_gram(h, geom, reg, torch.from_numpy(pb.x0).cuda())
-        for solver in ("cluster", "cluster", "grid", "grid"):
-            hicu.hicu_nullspace(h, G, pb.rank, solver=solver)
+        hicu.hicu_nullspace(h, G, pb.rank, split=True, solver=solver)
+        rng = np.random.default_rng(3)
+        E = torch.from_numpy(rng.standard_normal(G.shape) + 1j * rng.standard_normal(G.shape)).cuda()
+        G2 = G + (E + E.conj().T) * (1e-4 * G.abs().max())
+        hicu.hicu_nullspace(h, G2, pb.rank, warm=True, split=True, solver=solver)
     elif kind == "tc_step":
         rng = np.random.default_rng(7)
         k, mask = _slice_2d(rng, size, 8, 4.0, n_ellipses=20)
         x = torch.from_numpy(k).cuda()
         m = torch.from_numpy(mask).cuda()
-        geom = hicu.make_geom((size, size, 1), 8, (5, 5, 1))
-        reg = hicu.make_region((0, 0, 0), (size, size, 1))
+        g2 = hicu.make_geom((size, size, 1), 8, (5, 5, 1))
+        r2 = hicu.make_region((0, 0, 0), (size, size, 1))
         f = torch.from_numpy((rng.standard_normal((32, 200)) + 1j * rng.standard_normal((32, 200)))
                              .astype(np.complex64) * 0.05).cuda()
         for _ in range(2):
-            hicu.hicu_gd_step_filters(h, geom, reg, x, m, f, prec=hicu.HICU_SPLIT_BF16)
+            hicu.hicu_gd_step_filters(h, g2, r2, x, m, f, prec=hicu.HICU_SPLIT_BF16)
+    elif kind == "fgrad":
+        rng = np.random.default_rng(8)
+        x = torch.from_numpy(pb.x0).cuda()
+        Rb = torch.from_numpy((rng.standard_normal(hicu.out_shape(geom, reg) + (32,)) + 0j)
+                              .astype(np.complex64)).cuda()
+        for _ in range(2):
+            hicu.hicu_conv_null_filter_grad(h, geom, reg, x, Rb)
+    elif kind == "recon":
+        params = hicu.make_params(pb.rank, schedule(pb), seed=11, jl=hicu.HICU_JL_PROJECTOR,
+                                  prec=hicu.HICU_SPLIT_BF16)
+        hicu.hicu_reconstruct(h, geom, torch.from_numpy(pb.x0).cuda(), torch.from_numpy(pb.mask).cuda(),
+                              params)
     else:
         raise SystemExit(f"unknown profile case {kind}")
     torch.cuda.synchronize()
@@ -384,7 +408,7 @@ def main():
     ap.add_argument("--impl", default="hicu", choices=["hicu", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", default=None, choices=["eig", "tc_step"],
+    ap.add_argument("--profile", default=None, choices=["eig", "eig_cluster", "tc_step", "fgrad", "recon"],
                     help="run one small fixed case for an ncu capture and exit")
     ap.add_argument("--size", type=int, default=2048, help="image size of the tc_step profile case")
     ap.add_argument("--workload", default="brain", choices=["brain", "batch"],
