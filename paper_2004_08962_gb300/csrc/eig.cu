@@ -152,6 +152,7 @@ __global__ void __launch_bounds__(JWARPS * 32) jacobi_kernel(JacArgs J) {
   const long long gw = (long long)warp * gridDim.x + blockIdx.x;
   const long long nw = (long long)gridDim.x * JWARPS;
   int cur = 0;
+  unsigned epoch = 0;  // grid barriers passed
   const int mode = J.mode;
   for (int sweep = 0; sweep < J.max_sweeps; ++sweep) {
     for (int t = 0; t < n - 1; ++t) {
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(JWARPS * 32) jacobi_kernel(JacArgs J) {
           }
         }
       }
-      if (!grid_sync(J.gs)) return;
+      if (!grid_sync(J.gs, epoch)) return;
       cur ^= 1;
     }
     // convergence test: all off-diagonal mass (mode 0) or the coupling between the r
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(JWARPS * 32) jacobi_kernel(JacArgs J) {
           }
           J.rankd[i] = rk;
         }
-        if (!grid_sync(J.gs)) return;
+        if (!grid_sync(J.gs, epoch)) return;
       }
       double off = 0.0, tot = 0.0;
       for (int row = blockIdx.x; row < n; row += gridDim.x) {
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(JWARPS * 32) jacobi_kernel(JacArgs J) {
         J.part[2 * blockIdx.x] = so;
         J.part[2 * blockIdx.x + 1] = st;
       }
-      if (!grid_sync(J.gs)) return;
+      if (!grid_sync(J.gs, epoch)) return;
       if (threadIdx.x == 0) {
         double o = 0.0, d = 0.0;
         for (unsigned b = 0; b < gridDim.x; ++b) {

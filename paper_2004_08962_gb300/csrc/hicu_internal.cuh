@@ -93,33 +93,40 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Returns false (in every thread of the CTA) if the barrier timed out or an
-// error was already recorded; the caller must then leave the kernel.
-__device__ inline bool grid_sync(const GridSync& gs) {
+// Grid-wide barrier for cooperative kernels.  The count and generation words are zero at
+// launch, so the k-th barrier (epoch k, counted by each CTA) completes when the generation
+// reaches k + 1: arriving costs one atomic and waiting one acquire load per poll, with no
+// extra round trip on the critical path.  The wait gives up after timeout_ns (or when
+// another CTA recorded an error), records HICU_ERR_TIMEOUT and returns false in every thread
+// of the CTA; the caller must then leave the kernel.
+__device__ inline bool grid_sync(const GridSync& gs, unsigned& epoch) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned g = ld_acquire_u32(gs.gen);
+    const unsigned target = epoch + 1u;
     const unsigned old = atom_add_acqrel_u32(gs.count, 1u);
     if (old == gs.nblocks - 1) {
       *gs.count = 0u;
-      st_release_u32(gs.gen, g + 1u);
+      st_release_u32(gs.gen, target);
     } else {
-      const unsigned long long t0 = global_ns();
-      while (ld_acquire_u32(gs.gen) == g) {
-        if (global_ns() - t0 > gs.timeout_ns) {
-          atomicExch(gs.err, (int)HICU_ERR_TIMEOUT);
-          ok = 0;
-          break;
+      unsigned long long t0 = 0;
+      for (unsigned it = 0; ld_acquire_u32(gs.gen) != target; ++it) {
+        if ((it & 255u) == 255u) {  // occasional checks keep them off the fast path
+          const unsigned long long t = global_ns();
+          if (t0 == 0) t0 = t;
+          if (t - t0 > gs.timeout_ns || *((volatile int*)gs.err) != 0) {
+            atomicExch(gs.err, (int)HICU_ERR_TIMEOUT);
+            ok = 0;
+            break;
+          }
         }
-        __nanosleep(64);
       }
     }
-    if (*((volatile int*)gs.err) != 0) ok = 0;
     s_ok = ok;
   }
   __syncthreads();
+  ++epoch;
   return s_ok != 0;
 }
 
