@@ -372,7 +372,8 @@ hicu_status check_prec(hicu_handle* h, int32_t prec) {
 hicu_status check_tc(hicu_handle* h, const ConvGeom& g) {
   if (tc_supported(g)) return HICU_OK;
   return set_error(h, HICU_ERR_UNSUPPORTED,
-                   "split-bf16 path needs a 2D valid geometry (kz = 1, no circular axis) with C % 4 == 0");
+                   "split-bf16 path: a circular axis other than the outermost one, or a kernel the "
+                   "tensor-core tiling does not fit");
 }
 
 }  // namespace
@@ -392,7 +393,7 @@ extern "C" hicu_status hicu_conv_null(hicu_handle* h, const hicu_geom* geom, con
   if (prec == HICU_SPLIT_BF16) {
     s = check_tc(h, g);
     if (s) return s;
-    uint4* xpl = (uint4*)ws_get(h, WS_TC_X, sizeof(uint4) * 2 * (size_t)(g.C / 4) * g.ex * g.ey, &s);
+    uint4* xpl = (uint4*)ws_get(h, WS_TC_X, tc_x_bytes(g), &s);
     if (s) return s;
     void* bw = ws_get(h, WS_TC_BC, tc_b_bytes(g, p, 0), &s);
     if (s) return s;
@@ -444,7 +445,7 @@ extern "C" hicu_status hicu_conv_null_adjoint(hicu_handle* h, const hicu_geom* g
   if (prec == HICU_SPLIT_BF16) {
     s = check_tc(h, g);
     if (s) return s;
-    uint4* rpl = (uint4*)ws_get(h, WS_TC_R, sizeof(uint4) * 2 * (size_t)((p + 3) / 4) * g.s, &s);
+    uint4* rpl = (uint4*)ws_get(h, WS_TC_R, tc_r_bytes(g, p), &s);
     if (s) return s;
     void* bw = ws_get(h, WS_TC_BA, tc_b_bytes(g, p, 1), &s);
     if (s) return s;
@@ -484,12 +485,12 @@ static hicu_status gd_step_filters_tc(hicu_handle* h, const hicu_geom* geom, con
                                       int p, double* stats, cudaStream_t st) {
   hicu_status s = check_tc(h, g);
   if (s) return s;
-  const size_t xbytes = sizeof(uint4) * 2 * (size_t)(g.C / 4) * g.ex * g.ey;
+  const size_t xbytes = tc_x_bytes(g);
   uint4* xpl = (uint4*)ws_get(h, WS_TC_X, xbytes, &s);
   if (s) return s;
   uint4* gpl = (uint4*)ws_get(h, WS_TC_G, xbytes, &s);
   if (s) return s;
-  uint4* rpl = (uint4*)ws_get(h, WS_TC_R, sizeof(uint4) * 2 * (size_t)((p + 3) / 4) * g.s, &s);
+  uint4* rpl = (uint4*)ws_get(h, WS_TC_R, tc_r_bytes(g, p), &s);
   if (s) return s;
   void* bwc = ws_get(h, WS_TC_BC, tc_b_bytes(g, p, 0), &s);
   if (s) return s;

@@ -1,67 +1,79 @@
-// Tensor-core (tcgen05, TMEM) split-BF16 forms of the HICU convolutions, 2D.
+// Tensor-core (tcgen05, TMEM) split-BF16 forms of the HICU convolutions, 2D and 3D.
 //
 // Both operators are implicit GEMMs over the kernel offsets d (Theory: H(x) v is
 // the valid convolution; its conjugate transpose is again a convolution):
-//   conv    : R[o, k]   = sum_d sum_c  x_c[o + d] q_k[c, d]          K = 2C, N = 2p
-//   adjoint : g_c[u]    = sum_d sum_k  conj(q_k[c, d]) R[u - d, k]   K = 2p, N = 2C
-// Complex products run as real MMAs: the A row of a position is (re, im) of every
-// channel, and B embeds each complex weight w as [[w.re, w.im], [-w.im, w.re]]
-// (conv) or the conjugate embedding (adjoint).  Each FP32 value is split into
-// bf16 hi + lo; the MMAs accumulate hi*hi + hi*lo + lo*hi in FP32 (the lo*lo
-// term is below the FP32 accumulation error).
+//   conv    : R[o, k]   = sum_d sum_c  x_c[o + d] q_k[c, d]
+//   adjoint : g_c[u]    = sum_d sum_k  conj(q_k[c, d]) R[u - d, k]
+// The adjoint is run as a correlation of R (origin shifted by -(k-1) per axis)
+// with the flipped conjugate filters, so one kernel serves both.  Complex
+// products run as real MMAs: an A row holds (re, im) of 8 input channels (one
+// K = 16 step), and B embeds each complex weight w as [[w.re, w.im], [-w.im,
+// w.re]].  Each FP32 value is split into bf16 hi + lo; B is stored as [B_hi |
+// B_lo] along N, so two MMAs (A_hi and A_lo against [B_hi | B_lo]) form all
+// four products in FP32 accumulators, summed in the epilogue.
 //
-// Data path per CTA (128 threads, one M-tile = 128 consecutive positions):
-//  * the input tile (rows of W positions plus the kernel halo) of every
-//    (split, 4-channel chunk) plane is copied from a planar bf16 buffer
-//    [split][chunk][Y][X][8] into shared memory with 1D bulk async copies, one
-//    per row and plane, completing on an mbarrier;
-//  * an offset d shifts the whole M-tile by dy*W + dx positions, i.e. the A
-//    descriptor start moves by 16 bytes per position (no-swizzle K-major core
-//    matrices are 8 positions x 16 bytes), so no im2col copy is ever made;
-//  * one thread issues all MMAs of a K group into per-M-tile TMEM accumulators
-//    and commits them to an mbarrier; K groups (pairs of chunks) stream through
-//    one shared-memory buffer;
-//  * epilogue: tcgen05.ld of each thread's accumulator row, then either R
-//    (complex64 and/or split bf16 planes for the adjoint) with ||R||^2, or the
-//    masked gradient g with ||g||^2.
-// Every mbarrier wait is bounded (tc_ptx.cuh); a timeout skips the remaining
-// work, records HICU_ERR_TIMEOUT and still releases TMEM.
+// Streaming along the outer axis.  A problem is seen as planes (z) of rows (y)
+// of positions (x); a 2D problem runs with its rows as planes.  One work unit
+// is (8 output channels, a run of L output planes, Ty rows, one x tile).  The
+// CTA walks the input planes v of the run once: input plane v contributes to
+// output planes v - dz for every kernel offset dz, so one MMA multiplies the A
+// tile of plane v with the weights of all kz offsets at once (N = 32 kz) and
+// writes the kz output planes' accumulators, which sit side by side in a ring
+// of TMEM slots.  This keeps N wide for small filter banks (p = 8 gives N =
+// 160 for kz = 5) instead of re-reading the A tile once per z offset.
+//
+// Roles (192 threads): warp 0 lane 0 issues TMA tensor loads (5D tensor map,
+// out-of-range boxes are zero-filled, which supplies the adjoint's halo) into a
+// ring of shared-memory stages; warp 1 lane 0 issues the MMAs and commits each
+// stage back to the producer and each finished output plane to the epilogue;
+// warps 2-5 drain finished planes from TMEM (tcgen05.ld), write R / the masked
+// gradient and accumulate squared norms, then free the slot.  The filter bank of
+// the unit's output-channel group stays resident in shared memory.  The grid is
+// persistent (one CTA per SM, static unit schedule), so results are
+// deterministic.  Every mbarrier wait is bounded (tc_ptx.cuh): on a timeout the
+// role records HICU_ERR_TIMEOUT and stops, and TMEM is still released.
+#include <cuda.h>
+
 #include <algorithm>
+#include <mutex>
 
 #include "hicu_internal.cuh"
 #include "tc_ptx.cuh"
 
 namespace hicu {
 
-constexpr int TC_THREADS = 128;
-constexpr int TC_SMEM_LIMIT = 220 * 1024;
+constexpr int TC_THREADS = 192;
+constexpr int TC_MAX_STAGES = 8;
+constexpr int TC_SLOT_COLS = 32;               // 8 complex outputs x (re, im) x (hi, lo)
+constexpr size_t TC_SMEM_LIMIT = 225 * 1024;   // dynamic shared memory used at most
+constexpr size_t TC_BAR_BYTES = 1024;          // mbarriers at the start of dynamic smem
 
 struct TcParams {
-  int kx, ky, K;       // kernel extent and offsets (2D)
-  int X, Y;            // planar input extent (positions)
-  int W;               // tile width in positions (<= 256)
-  int Tx, Ty;          // outputs per tile row, output rows per CTA
-  int ntx;             // tiles along x
-  int org_x, org_y;    // input coordinate of the tile origin = output origin + (org_x, org_y)
-  int chunks;          // 4-channel chunks of the A operand per split
-  int groups;          // K groups (each = 2 chunks)
-  int Npad;            // MMA N (multiple of 16)
-  int Hpos;            // positions per shared-memory plane
-  int nM;              // M tiles per CTA
-  int tmem_cols;       // allocated TMEM columns (power of two >= nM * Npad)
-  int conj_shift;      // 0: conv shift (dy*W + dx); 1: adjoint shift ((ky-1-dy)*W + (kx-1-dx))
-  const uint4* ain;    // planar bf16 input, 16 bytes per (plane, position)
-  const uint4* bw;     // B planes [group][d][split][2][Npad][8] bf16
-  uint32_t bgroup_bytes;
-  // outputs
-  int mode;            // 0: conv (R and/or ||R||^2), 1: adjoint (masked g and ||g||^2)
-  int ox_lim, oy_lim;  // valid output extent
-  int p;               // conv: filters; adjoint: coils written
-  float2* R;           // conv: complex64 [oy][ox][p] (nullable)
-  uint4* Rs;           // conv: split planes of R [split][chunkR][oy_lim][ox_lim] (nullable)
-  int chunksR;
-  KView gout;          // adjoint: output view (region coordinates)
-  MView m;             // adjoint: mask view
+  // pseudo-3D geometry (a 2D problem has its rows as planes and one row per plane)
+  int kx, ky, kz;
+  int W, Tx, Ty, nM;        // row pitch (positions), outputs per row, rows per tile, M tiles
+  int Wb, nbx;              // TMA box width and boxes per row (2 when a row exceeds 256 positions)
+  int PA;                   // positions per shared-memory plane of a stage
+  int ntx, nty, nzr, L;     // x tiles, y tiles, runs of L output planes
+  int ogs, kgroups;         // output-channel groups of 8, K groups of 8 input channels
+  int org_x, org_y, org_z;  // input coordinate = output coordinate + offset + org
+  int Zin, circ_z;          // input planes; wrap modulo Zin when circ_z
+  int ox_lim, oy_lim, oz_lim;
+  int chunks_even;          // 4-channel planes per split in the input tensor
+  int stages, rs;           // stage ring depth, accumulator slots per M tile
+  int tmem_cols;
+  uint32_t stage_bytes, b_bytes;
+  long long units;
+  const unsigned char* bw;  // B per output-channel group, b_bytes each
+  int mode;                 // 0: conv (R, split R planes, norms); 1: adjoint (masked g, norm)
+  int cout;                 // output channels: p (conv) or C (adjoint)
+  float2* R;                // conv: complex64 [o][cout]
+  uint4* Rs;                // conv: split planes [split][2 ogs][o][8]
+  long long r_plane;        // positions per R plane (= valid outputs)
+  float2* g;                // adjoint output, element c*g_sc + base + z*g_sz + y*g_sy + x
+  long long g_sc, g_sz, g_sy, g_base;
+  const uint8_t* m;         // adjoint mask (nullable), same addressing with its strides
+  long long m_sc, m_sz, m_sy, m_base;
   double* partial;
   int* err;
 };
@@ -85,219 +97,330 @@ __device__ __forceinline__ void split8(const float (&v)[8], uint4& hi, uint4& lo
                   pack_bf16x2(l[6], l[7]));
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1) tc_corr_kernel(const TcParams P) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ uint64_t bar_load, bar_mma;
-  __shared__ uint32_t tslot;
-  __shared__ double red[4];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tile_x = blockIdx.x % P.ntx, tile_y = blockIdx.x / P.ntx;
-  const int x0 = tile_x * P.Tx, y0 = tile_y * P.Ty;  // output origin of the tile
-  const int ix0 = x0 + P.org_x, iy0 = y0 + P.org_y;  // input origin (may be negative)
-  const int rows = P.Ty + P.ky - 1;
-  const uint32_t plane_bytes = (uint32_t)P.Hpos * 16u;
-  unsigned char* sA = smem;                          // 4 planes: [split][2 chunks]
-  unsigned char* sB = smem + 4 * plane_bytes;        // B of one K group
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            int c4, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(tc::smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4),
+      "r"(tc::smem_u32(bar))
+      : "memory");
+}
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+struct Unit {
+  int og, zr, ty, tx;
+};
+
+__device__ __forceinline__ Unit unit_of(const TcParams& P, long long u) {
+  Unit U;
+  U.tx = (int)(u % P.ntx);
+  u /= P.ntx;
+  U.ty = (int)(u % P.nty);
+  u /= P.nty;
+  U.zr = (int)(u % P.nzr);
+  U.og = (int)(u / P.nzr);
+  return U;
+}
+
+// MMAs of one A tile into the accumulators of `cnt` consecutive output planes whose slots
+// start at `slot` (wrapping around the ring of rs slots); B block j of the window sits
+// 512 bytes after block j - 1.
+__device__ __forceinline__ void mma_window(uint32_t dcol0, int slot, int cnt, int rs, uint64_t adesc,
+                                           uint32_t baddr, uint32_t lbo_b, uint32_t acc) {
+  const int first = min(cnt, rs - slot);
+  tc::mma_bf16(dcol0 + (uint32_t)(slot * TC_SLOT_COLS), adesc, tc::smem_desc(baddr, lbo_b, 128),
+               tc::idesc_bf16_f32(128, TC_SLOT_COLS * first), acc);
+  if (cnt > first)
+    tc::mma_bf16(dcol0, adesc, tc::smem_desc(baddr + (uint32_t)first * 512u, lbo_b, 128),
+                 tc::idesc_bf16_f32(128, TC_SLOT_COLS * (cnt - first)), acc);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_corr_kernel(const __grid_constant__ CUtensorMap amap, const TcParams P) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // 128-byte aligned base (TMA destinations); the launch adds 128 bytes of slack
+  unsigned char* smem = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* full = bars;                        // [stages]
+  uint64_t* empty = bars + TC_MAX_STAGES;       // [stages]
+  uint64_t* acc_full = bars + 2 * TC_MAX_STAGES;         // [rs]
+  uint64_t* acc_empty = acc_full + 16;                   // [rs]
+  uint64_t* bfull = acc_empty + 16;
+  uint64_t* bfree = bfull + 1;
+  uint64_t* done = bfree + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  double* red = reinterpret_cast<double*>(smem + 512);  // per-warp norm sums
+  unsigned char* sB = smem + TC_BAR_BYTES;
+  unsigned char* sA = sB + P.b_bytes;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    tc::mbar_init(&bar_load, 1);
-    tc::mbar_init(&bar_mma, 1);
+    for (int i = 0; i < P.stages; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < P.rs; ++i) {
+      tc::mbar_init(&acc_full[i], 1);
+      tc::mbar_init(&acc_empty[i], 4);  // one arrival per epilogue warp
+    }
+    tc::mbar_init(bfull, 1);
+    tc::mbar_init(bfree, 1);
+    tc::mbar_init(done, 1);
     tc::fence_mbar_init();
   }
-  if (warp == 0) tc::tmem_alloc(&tslot, (uint32_t)P.tmem_cols);
+  if (warp == 0) tc::tmem_alloc(tslot, (uint32_t)P.tmem_cols);
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  const uint32_t taddr = tslot;
+  const uint32_t taddr = *tslot;
+  const int zspan = P.kz - 1;  // input planes beyond the last output plane of a run
 
-  // rows / columns of the input tile that exist in the planar buffer
-  const int ry0 = max(0, -iy0), ry1 = min(rows, P.Y - iy0);
-  const int cx0 = max(0, -ix0), cx1 = min(P.W, P.X - ix0);
-  const bool full_tile = ry0 == 0 && ry1 == rows && cx0 == 0 && cx1 == P.W;
-
-  bool ok = true;
-  for (int grp = 0; grp < P.groups && ok; ++grp) {
-    if (grp > 0) {
-      tc::tc_fence_before();
-      __syncthreads();  // previous group's MMAs are complete (bar_mma waited); buffer is free
-    }
-    // zero what the copies will not overwrite: missing rows/columns (adjoint halo) and the
-    // padding chunk of an odd chunk count
-    const bool pad_chunk = (2 * grp + 1 >= P.chunks);
-    if (!full_tile || pad_chunk) {
-      const int n16 = (int)(4 * plane_bytes / 16);
-      uint4* z = reinterpret_cast<uint4*>(sA);
-      for (int i = tid; i < n16; i += TC_THREADS) z[i] = make_uint4(0, 0, 0, 0);
-      tc::fence_proxy_async_smem();
-    }
-    __syncthreads();
-    if (tid == 0) {
-      uint32_t bytes = P.bgroup_bytes;
-      const int ncopy = cx1 - cx0;
-      int nplanes = 0;
-      for (int cc = 0; cc < 2; ++cc)
-        if (2 * grp + cc < P.chunks) ++nplanes;
-      if (ry1 > ry0 && ncopy > 0) bytes += (uint32_t)(2 * nplanes * (ry1 - ry0) * ncopy * 16);
-      tc::mbar_arrive_expect_tx(&bar_load, bytes);
-      tc::bulk_g2s(sB, reinterpret_cast<const unsigned char*>(P.bw) + (size_t)grp * P.bgroup_bytes,
-                   P.bgroup_bytes, &bar_load);
-      if (ncopy > 0) {
-        for (int s = 0; s < 2; ++s) {
-          for (int cc = 0; cc < 2; ++cc) {
-            const int j = 2 * grp + cc;
-            if (j >= P.chunks) continue;
-            const uint4* src_plane = P.ain + (size_t)(s * P.chunks + j) * P.Y * P.X;
-            unsigned char* dst_plane = sA + (s * 2 + cc) * plane_bytes;
-            for (int hy = ry0; hy < ry1; ++hy) {
-              const uint4* src = src_plane + (size_t)(iy0 + hy) * P.X + (ix0 + cx0);
-              tc::bulk_g2s(dst_plane + ((size_t)hy * P.W + cx0) * 16, src, (uint32_t)(ncopy * 16), &bar_load);
+  if (warp == 0) {
+    // ------------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      bool ok = true;
+      long long it = 0;
+      int prev_og = -1, j = 0;
+      const uint32_t plane_b = (uint32_t)P.PA * 16u;
+      const uint32_t a_tx = 4u * (uint32_t)P.nbx * (uint32_t)P.Ty * (uint32_t)P.Wb * 16u;
+      for (long long u = blockIdx.x; u < P.units && ok; u += gridDim.x, ++j) {
+        const Unit U = unit_of(P, u);
+        if (U.og != prev_og) {
+          if (j > 0) ok = tc::mbar_wait(bfree, (uint32_t)((j - 1) & 1), P.err);
+          if (!ok) break;
+          tc::mbar_arrive_expect_tx(bfull, P.b_bytes);
+          tc::bulk_g2s(sB, P.bw + (size_t)U.og * P.b_bytes, P.b_bytes, bfull);
+          prev_og = U.og;
+        }
+        const int zo_lo = U.zr * P.L, zo_hi = min(zo_lo + P.L, P.oz_lim);
+        const int xin = U.tx * P.Tx + P.org_x;
+        for (int v = zo_lo; v <= zo_hi - 1 + zspan && ok; ++v) {
+          int zin = v + P.org_z;
+          if (P.circ_z) zin = wrap(zin, P.Zin);
+          for (int dy = 0; dy < P.ky && ok; ++dy) {
+            const int yin = U.ty * P.Ty + dy + P.org_y;
+            for (int kg = 0; kg < P.kgroups; ++kg, ++it) {
+              const int s = (int)(it % P.stages);
+              const long long round = it / P.stages;
+              if (round > 0) ok = tc::mbar_wait(&empty[s], (uint32_t)((round - 1) & 1), P.err);
+              if (!ok) break;
+              unsigned char* st = sA + (size_t)s * P.stage_bytes;
+              tc::mbar_arrive_expect_tx(&full[s], a_tx);
+#pragma unroll
+              for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc)
+                  for (int bx = 0; bx < P.nbx; ++bx)  // nbx > 1 only with one row per tile
+                    tma_load_5d(st + (sp * 2 + cc) * plane_b + bx * P.Wb * 16, &amap, 0, xin + bx * P.Wb, yin,
+                                zin, sp * P.chunks_even + 2 * kg + cc, &full[s]);
             }
           }
         }
       }
     }
-    ok = tc::mbar_wait(&bar_load, grp & 1, P.err);
-    ok = __syncthreads_and(ok);
-    if (!ok) break;
-    // one thread issues the group's MMAs for every M tile
-    if (tid == 0) {
-      tc::tc_fence_after();
-      const uint32_t idesc = tc::idesc_bf16_f32(128, P.Npad);
-      const uint32_t a_base = tc::smem_u32(sA), b_base = tc::smem_u32(sB);
-      const uint32_t bsplit = 2u * P.Npad * 16u;  // one (d, split) B block: 2 chunk planes
-      for (int mt = 0; mt < P.nM; ++mt) {
-        const uint32_t dcol = taddr + (uint32_t)(mt * P.Npad);
-        int first = (grp == 0);
-        for (int dy = 0; dy < P.ky; ++dy) {
-          for (int dx = 0; dx < P.kx; ++dx) {
-            const int d = dy * P.kx + dx;
-            const int shift = P.conj_shift ? (P.ky - 1 - dy) * P.W + (P.kx - 1 - dx) : dy * P.W + dx;
-            const uint32_t apos = (uint32_t)(mt * 128 + shift) * 16u;
-            const uint64_t a_hi = tc::smem_desc(a_base + apos, plane_bytes, 128);
-            const uint64_t a_lo = tc::smem_desc(a_base + 2 * plane_bytes + apos, plane_bytes, 128);
-            const uint32_t bd = b_base + (uint32_t)(d * 2) * bsplit;
-            const uint64_t b_hi = tc::smem_desc(bd, P.Npad * 16u, 128);
-            const uint64_t b_lo = tc::smem_desc(bd + bsplit, P.Npad * 16u, 128);
-            tc::mma_bf16(dcol, a_hi, b_hi, idesc, first ? 0u : 1u);
-            tc::mma_bf16(dcol, a_hi, b_lo, idesc, 1u);
-            tc::mma_bf16(dcol, a_lo, b_hi, idesc, 1u);
-            first = 0;
-          }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      bool ok = true;
+      long long it = 0, q0 = 0;
+      int prev_og = -1, nb = 0;
+      const uint32_t plane_b = (uint32_t)P.PA * 16u;
+      const uint32_t lbo_b = 512u * (uint32_t)P.kz;   // cc0 -> cc1 core matrices of B
+      const uint32_t boff = 1024u * (uint32_t)P.kz;   // B bytes per (kg, dy, dx)
+      const uint32_t b_base = tc::smem_u32(sB);
+      for (long long u = blockIdx.x; u < P.units && ok; u += gridDim.x) {
+        const Unit U = unit_of(P, u);
+        if (U.og != prev_og) {
+          ok = tc::mbar_wait(bfull, (uint32_t)(nb & 1), P.err);
+          ++nb;
+          prev_og = U.og;
+          if (!ok) break;
         }
-      }
-      tc::mma_commit(&bar_mma);
-    }
-    ok = tc::mbar_wait(&bar_mma, grp & 1, P.err);
-    ok = __syncthreads_and(ok);
-    tc::tc_fence_after();
-  }
-
-  // epilogue: thread (warp, lane) owns accumulator row 32*warp + lane of every M tile.  Squared
-  // norms are summed in FP32 per thread (at most a few hundred terms) and in FP64 across threads:
-  // FP64 arithmetic runs at 1/58 of the FP32 rate on this part.
-  float nrm = 0.f;
-  if (ok) {
-    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-    for (int mt = 0; mt < P.nM; ++mt) {
-      const int mrow = mt * 128 + 32 * warp + lane;
-      const int ly = mrow / P.W, lx = mrow - (mrow / P.W) * P.W;
-      const int ox = x0 + lx, oy = y0 + ly;
-      const bool valid = ly < P.Ty && lx < P.Tx && ox < P.ox_lim && oy < P.oy_lim;
-      for (int c0 = 0; c0 < P.Npad; c0 += 16) {
-        uint32_t r[16];
-        tc::tmem_ld16(taddr + lane_base + (uint32_t)(mt * P.Npad + c0), r);
-        tc::tmem_ld_wait();
-        if (!valid) continue;
-        if (P.mode == 0) {
-          const long long o = (long long)oy * P.ox_lim + ox;
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int k = c0 / 2 + q;
-            if (k < P.p) {
-              const float2 v = make_float2(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
-              nrm = fmaf(v.x, v.x, fmaf(v.y, v.y, nrm));
-              if (P.R) P.R[o * P.p + k] = v;
-            }
+        const int zo_lo = U.zr * P.L, zo_hi = min(zo_lo + P.L, P.oz_lim);
+        for (int v = zo_lo; v <= zo_hi - 1 + zspan && ok; ++v) {
+          const int za = max(zo_lo, v - zspan), zb = min(zo_hi - 1, v);
+          const int cnt = zb - za + 1;
+          const bool fresh = v <= zo_hi - 1;  // output plane v starts here
+          const long long qa = q0 + (za - zo_lo);
+          const int sa = (int)(qa % P.rs);
+          if (fresh) {
+            const long long qn = q0 + (v - zo_lo);
+            if (qn >= P.rs) ok = tc::mbar_wait(&acc_empty[qn % P.rs], (uint32_t)(((qn / P.rs) - 1) & 1), P.err);
+            if (!ok) break;
           }
-          if (P.Rs) {
-            // two 4-filter chunks per 16 columns: split into bf16 planes for the adjoint
-#pragma unroll
-            for (int hc = 0; hc < 2; ++hc) {
-              const int jr = c0 / 8 + hc;
-              if (jr < P.chunksR) {
-                float v[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                  const int k = jr * 4 + e / 2;
-                  v[e] = (k < P.p) ? __uint_as_float(r[hc * 8 + e]) : 0.f;
+          const int ba = P.kz - 1 - (v - za);  // B block of output plane za (blocks hold dz = kz-1-b)
+          const int sb = (sa + cnt - 1) % P.rs;
+          for (int dy = 0; dy < P.ky && ok; ++dy) {
+            for (int kg = 0; kg < P.kgroups; ++kg, ++it) {
+              const int s = (int)(it % P.stages);
+              ok = tc::mbar_wait(&full[s], (uint32_t)((it / P.stages) & 1), P.err);
+              if (!ok) break;
+              tc::tc_fence_after();
+              const uint32_t a_st = tc::smem_u32(sA) + (uint32_t)s * P.stage_bytes;
+              for (int mt = 0; mt < P.nM; ++mt) {
+                const uint32_t dcol0 = taddr + (uint32_t)(mt * P.rs * TC_SLOT_COLS);
+                for (int dx = 0; dx < P.kx; ++dx) {
+                  const uint32_t apos = (uint32_t)(mt * 128 + dx) * 16u;
+                  const uint64_t a_hi = tc::smem_desc(a_st + apos, plane_b, 128);
+                  const uint64_t a_lo = tc::smem_desc(a_st + 2u * plane_b + apos, plane_b, 128);
+                  const uint32_t baddr = b_base + (uint32_t)((kg * P.ky + dy) * P.kx + dx) * boff + (uint32_t)ba * 512u;
+                  if (fresh && dy == 0 && kg == 0 && dx == 0) {
+                    if (cnt > 1) mma_window(dcol0, sa, cnt - 1, P.rs, a_hi, baddr, lbo_b, 1u);
+                    mma_window(dcol0, sb, 1, P.rs, a_hi, baddr + (uint32_t)(cnt - 1) * 512u, lbo_b, 0u);
+                  } else {
+                    mma_window(dcol0, sa, cnt, P.rs, a_hi, baddr, lbo_b, 1u);
+                  }
+                  mma_window(dcol0, sa, cnt, P.rs, a_lo, baddr, lbo_b, 1u);
                 }
-                uint4 hi, lo;
-                split8(v, hi, lo);
-                const size_t plane = (size_t)P.oy_lim * P.ox_lim;
-                P.Rs[(size_t)jr * plane + o] = hi;
-                P.Rs[(size_t)(P.chunksR + jr) * plane + o] = lo;
+              }
+              tc::mma_commit(&empty[s]);
+            }
+          }
+          if (ok && v - zspan >= zo_lo) {
+            const long long qc = q0 + (v - zspan - zo_lo);  // output plane complete
+            tc::mma_commit(&acc_full[qc % P.rs]);
+          }
+        }
+        q0 += zo_hi - zo_lo;
+        if (ok) tc::mma_commit(bfree);
+      }
+      tc::mma_commit(done);
+      tc::mbar_wait(done, 0, P.err);
+    }
+  } else {
+    // --------------------------------------------------------------------- epilogue
+    const int quad = warp & 3;  // TMEM lanes 32*quad .. 32*quad + 31
+    const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+    double nrm_d = 0.0;
+    bool ok = true;
+    long long q = 0;
+    for (long long u = blockIdx.x; u < P.units && ok; u += gridDim.x) {
+      const Unit U = unit_of(P, u);
+      const int zo_lo = U.zr * P.L, zo_hi = min(zo_lo + P.L, P.oz_lim);
+      for (int z = zo_lo; z < zo_hi; ++z, ++q) {
+        const int slot = (int)(q % P.rs);
+        ok = tc::mbar_wait(&acc_full[slot], (uint32_t)((q / P.rs) & 1), P.err);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        tc::tc_fence_after();
+        uint32_t hi[2][16], lo[2][16];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          if (mt < P.nM) {
+            const uint32_t col = taddr + lane_base + (uint32_t)((mt * P.rs + slot) * TC_SLOT_COLS);
+            tc::tmem_ld16(col, hi[mt]);
+            tc::tmem_ld16(col + 16u, lo[mt]);
+          }
+        }
+        tc::tmem_ld_wait();
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[slot]);
+        float nrm = 0.f;
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          if (mt >= P.nM) continue;
+          const int pos = mt * 128 + 32 * quad + lane;
+          const int ly = pos / P.W, lx = pos - (pos / P.W) * P.W;
+          const int ox = U.tx * P.Tx + lx, oy = U.ty * P.Ty + ly;
+          if (!(ly < P.Ty && lx < P.Tx && ox < P.ox_lim && oy < P.oy_lim)) continue;
+          float v[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(hi[mt][e]) + __uint_as_float(lo[mt][e]);
+          if (P.mode == 0) {
+            const long long o = ((long long)z * P.oy_lim + oy) * P.ox_lim + ox;
+#pragma unroll
+            for (int q2 = 0; q2 < 8; ++q2) {
+              const int k = U.og * 8 + q2;
+              if (k < P.cout) {
+                nrm = fmaf(v[2 * q2], v[2 * q2], fmaf(v[2 * q2 + 1], v[2 * q2 + 1], nrm));
+                if (P.R) P.R[o * P.cout + k] = make_float2(v[2 * q2], v[2 * q2 + 1]);
+              } else {
+                v[2 * q2] = 0.f;
+                v[2 * q2 + 1] = 0.f;
+              }
+            }
+            if (P.Rs) {
+              const int nplanes = 2 * P.ogs;
+#pragma unroll
+              for (int hc = 0; hc < 2; ++hc) {
+                float w8[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) w8[e] = v[8 * hc + e];
+                uint4 h4, l4;
+                split8(w8, h4, l4);
+                const int jr = 2 * U.og + hc;
+                P.Rs[(size_t)jr * P.r_plane + o] = h4;
+                P.Rs[(size_t)(nplanes + jr) * P.r_plane + o] = l4;
+              }
+            }
+          } else {
+            const long long go = P.g_base + (long long)z * P.g_sz + (long long)oy * P.g_sy + ox;
+            const long long mo = P.m_base + (long long)z * P.m_sz + (long long)oy * P.m_sy + ox;
+#pragma unroll
+            for (int q2 = 0; q2 < 8; ++q2) {
+              const int c = U.og * 8 + q2;
+              if (c < P.cout) {
+                float2 w = make_float2(v[2 * q2], v[2 * q2 + 1]);
+                if (P.m && P.m[(long long)c * P.m_sc + mo]) w = make_float2(0.f, 0.f);
+                P.g[(long long)c * P.g_sc + go] = w;
+                nrm = fmaf(w.x, w.x, fmaf(w.y, w.y, nrm));
               }
             }
           }
-        } else {
-          const long long mo = (long long)(P.m.oz) * P.m.sz + (long long)(P.m.oy + oy) * P.m.sy + (P.m.ox + ox);
-          const long long go = (long long)(P.gout.oz) * P.gout.sz + (long long)(P.gout.oy + oy) * P.gout.sy +
-                               (P.gout.ox + ox);
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int c = c0 / 2 + q;
-            if (c < P.p) {
-              float2 v = make_float2(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
-              if (P.m.p && P.m.p[(long long)c * P.m.sc + mo]) v = make_float2(0.f, 0.f);
-              P.gout.p[(long long)c * P.gout.sc + go] = v;
-              nrm = fmaf(v.x, v.x, fmaf(v.y, v.y, nrm));
-            }
-          }
         }
+        nrm_d += (double)nrm;
       }
     }
+    for (int o = 16; o > 0; o >>= 1) nrm_d += __shfl_down_sync(0xffffffffu, nrm_d, o);
+    if (lane == 0) red[warp] = nrm_d;
   }
   tc::tc_fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(taddr, (uint32_t)P.tmem_cols);
-  double dn = (double)nrm;
-  for (int o = 16; o > 0; o >>= 1) dn += __shfl_down_sync(0xffffffffu, dn, o);
-  if (lane == 0) red[warp] = dn;
-  __syncthreads();
-  if (tid == 0) P.partial[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
+  if (tid == 0) P.partial[blockIdx.x] = red[2] + red[3] + red[4] + red[5];
 }
 
 // ------------------------------------------------------------- layout kernels
 
-// region of a complex64 array -> planar split bf16 [split][chunk][ey][ex][8], chunk = 4 channels
-__global__ void tc_split_input_kernel(int C, int ex, int ey, KView x, uint4* __restrict__ out) {
-  const int chunks = C / 4;
-  const long long plane = (long long)ex * ey;
-  const long long tot = plane * chunks;
+// Region of a complex64 array -> planar split bf16 [split][chunk_even][ez][ey][ex][8],
+// chunk = 4 channels; channels >= C (padding) are zero.
+__global__ void tc_split_input_kernel(int C, int chunks_even, int ex, int ey, int ez, KView x,
+                                      uint4* __restrict__ out) {
+  const long long plane = (long long)ex * ey * ez;
+  const long long tot = plane * chunks_even;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
        i += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(i / plane);
     const long long pos = i - (long long)j * plane;
-    const int ux = (int)(pos % ex), uy = (int)(pos / ex);
+    const int ux = (int)(pos % ex);
+    const long long r = pos / ex;
+    const int uy = (int)(r % ey), uz = (int)(r / ey);
     float v[8];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const float2 a = x.p[(long long)(4 * j + e) * x.sc + (long long)(x.oz) * x.sz + (long long)(x.oy + uy) * x.sy +
-                           (x.ox + ux)];
+      const int c = 4 * j + e;
+      float2 a = make_float2(0.f, 0.f);
+      if (c < C)
+        a = x.p[(long long)c * x.sc + (long long)(x.oz + uz) * x.sz + (long long)(x.oy + uy) * x.sy + (x.ox + ux)];
       v[2 * e] = a.x;
       v[2 * e + 1] = a.y;
     }
     uint4 hi, lo;
     split8(v, hi, lo);
     out[(long long)j * plane + pos] = hi;
-    out[(long long)(chunks + j) * plane + pos] = lo;
+    out[(long long)(chunks_even + j) * plane + pos] = lo;
   }
 }
 
-// R complex64 [s][p] -> planar split bf16 [split][chunkR][s][8], chunk = 4 filters (zero padded)
-__global__ void tc_split_r_kernel(long long npos, int p, const float2* __restrict__ R, uint4* __restrict__ out) {
-  const int chunks = (p + 3) / 4;
-  const long long tot = npos * chunks;
+// R complex64 [s][p] -> planar split bf16 [split][chunk_even][s][8], chunk = 4 filters (zero padded)
+__global__ void tc_split_r_kernel(long long npos, int p, int chunks_even, const float2* __restrict__ R,
+                                  uint4* __restrict__ out) {
+  const long long tot = npos * chunks_even;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
        i += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(i / npos);
@@ -313,38 +436,50 @@ __global__ void tc_split_r_kernel(long long npos, int p, const float2* __restric
     uint4 hi, lo;
     split8(v, hi, lo);
     out[(long long)j * npos + pos] = hi;
-    out[(long long)(chunks + j) * npos + pos] = lo;
+    out[(long long)(chunks_even + j) * npos + pos] = lo;
   }
 }
 
-// B planes [group][d][split][cc][Npad][8] from a bank [p][n] (n = C*K, filter order [c][ky][kx]).
-// conv:    K index kk = 2c + t (t: re/im of x), N index = 2k + u:  [[f.re, f.im], [-f.im, f.re]]
-// adjoint: K index kk = 2k + t (t: re/im of R), N index = 2c + u:  [[f.re, -f.im], [f.im, f.re]]
-__global__ void tc_prep_b_kernel(int mode, int C, int K, int p, int groups, int Npad,
+// B for the streamed correlation, per output-channel group og (8 outputs):
+//   [og][kg][dy][dx][cc][blk][row][e]   (bf16), pseudo-3D offsets (dz, dy, dx)
+// K index within the MMA step: cc*8 + e -> input channel 8 kg + 4 cc + e/2, t = e%2 (re/im);
+// N row: blk b holds dz = kz-1-b, row = split*16 + 2 o + u (output channel 8 og + o, u = re/im).
+// conv    (mode 0): weight of offset d = (dz, dy, dx) is f = bank[co][ci*K + d], embedding
+//                   [[f.re, f.im], [-f.im, f.re]] (rows t, columns u);
+// adjoint (mode 1): weight of shift d' is conj(bank[ci][co*K + (k-1-d')]), embedding
+//                   [[f.re, -f.im], [f.im, f.re]].
+// The pseudo-3D offset index is (dz*ky + dy)*kx + dx, which is the bank's [kz][ky][kx] order in
+// 3D and its [ky][kx] order for a 2D problem run with rows as planes (ky = 1, kz = k_y).
+__global__ void tc_prep_b_kernel(int mode, int Cin, int Cout, int n, int kx, int ky, int kz, int kgroups, int ogs,
                                  const float2* __restrict__ bank, __nv_bfloat16* __restrict__ out) {
-  const long long per_group = (long long)K * 2 * 2 * Npad * 8;
-  const long long tot = per_group * groups;
-  const int n = C * K;
+  const long long per_og = (long long)kgroups * ky * kx * 2 * kz * 32 * 8;
+  const long long tot = per_og * ogs;
+  const int K = kx * ky * kz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
        i += (long long)gridDim.x * blockDim.x) {
     long long t = i;
     const int e = (int)(t % 8); t /= 8;
-    const int col = (int)(t % Npad); t /= Npad;
+    const int row = (int)(t % 32); t /= 32;
+    const int blk = (int)(t % kz); t /= kz;
     const int cc = (int)(t % 2); t /= 2;
-    const int split = (int)(t % 2); t /= 2;
-    const int d = (int)(t % K); t /= K;
-    const int grp = (int)t;
-    const int kk = (grp * 2 + cc) * 8 + e;  // K index within the offset
-    const int kin = kk >> 1, tin = kk & 1;  // input channel (coil or filter) and re/im
-    const int kout = col >> 1, uout = col & 1;
+    const int dx = (int)(t % kx); t /= kx;
+    const int dy = (int)(t % ky); t /= ky;
+    const int kg = (int)(t % kgroups); t /= kgroups;
+    const int og = (int)t;
+    const int dz = kz - 1 - blk;
+    const int ci = 8 * kg + 4 * cc + e / 2, tin = e & 1;
+    const int split = row >> 4, rr = row & 15;
+    const int co = 8 * og + rr / 2, uout = rr & 1;
     float w = 0.f;
-    int coil, filt;
-    if (mode == 0) { coil = kin; filt = kout; }
-    else { coil = kout; filt = kin; }
-    if (coil < C && filt < p && kout < (mode == 0 ? p : C)) {
-      const float2 f = bank[(long long)filt * n + (long long)coil * K + d];
-      if (mode == 0) w = (tin == 0) ? (uout == 0 ? f.x : f.y) : (uout == 0 ? -f.y : f.x);
-      else w = (tin == 0) ? (uout == 0 ? f.x : -f.y) : (uout == 0 ? f.y : f.x);
+    if (ci < Cin && co < Cout) {
+      if (mode == 0) {
+        const float2 f = bank[(long long)co * n + (long long)ci * K + (dz * ky + dy) * kx + dx];
+        w = (tin == 0) ? (uout == 0 ? f.x : f.y) : (uout == 0 ? -f.y : f.x);
+      } else {
+        const int d = ((kz - 1 - dz) * ky + (ky - 1 - dy)) * kx + (kx - 1 - dx);
+        const float2 f = bank[(long long)ci * n + (long long)co * K + d];
+        w = (tin == 0) ? (uout == 0 ? f.x : -f.y) : (uout == 0 ? f.y : f.x);
+      }
     }
     const float hi = __bfloat162float(__float2bfloat16_rn(w));
     out[i] = __float2bfloat16_rn(split == 0 ? hi : w - hi);
@@ -353,124 +488,229 @@ __global__ void tc_prep_b_kernel(int mode, int C, int K, int p, int groups, int 
 
 // ---------------------------------------------------------------- host side
 
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// Pseudo-3D view of a problem: a 2D problem (kz = 1, one plane) runs with its rows as planes.
+struct Pseudo {
+  int kx, ky, kz;
+  int circ;            // circular along the pseudo-z axis
+  bool ok;             // a circular axis the kernel cannot wrap (x, or y of a 3D problem)
+};
+
+Pseudo pseudo_of(const ConvGeom& g) {
+  Pseudo q;
+  q.kx = g.kx;
+  if (g.kz == 1 && g.ez == 1) {
+    q.ky = 1;
+    q.kz = g.ky;
+    q.circ = g.cy;
+    q.ok = !g.cx && !g.cz;
+  } else {
+    q.ky = g.ky;
+    q.kz = g.kz;
+    q.circ = g.cz;
+    q.ok = !g.cx && !g.cy;
+  }
+  return q;
+}
+
+// extents of an array in pseudo-3D (x, y, z)
+void pseudo_ext(const ConvGeom& g, int ax, int ay, int az, int* px, int* py, int* pz) {
+  *px = ax;
+  if (g.kz == 1 && g.ez == 1) {
+    *py = 1;
+    *pz = ay;
+  } else {
+    *py = ay;
+    *pz = az;
+  }
+}
+
+int chunks_even_of(int channels) { return 2 * ((channels + 7) / 8); }
+
 struct TcPlan {
   TcParams P;
   size_t smem;
   int grid;
+  int Xin, Yin;  // input extents (pseudo x, y)
 };
 
-static int pow2_at_least(int v) {
-  int p = 32;
-  while (p < v) p <<= 1;
-  return p;
-}
-
-// Tile plan for a valid correlation: output columns are split into the fewest tiles whose halo
-// (Tx + kx - 1 positions) fits a 256-position row; the number of output rows per CTA (Ty) is the
-// largest that still gives >= 148 CTAs, else the smallest that fills whole M tiles (most CTAs).
-static bool tile_fits(const TcParams& P, int Ty, size_t b_bytes, int* Hpos_out, size_t* smem_out) {
-  const int nM = (Ty * P.W + 127) / 128;
-  if (nM * P.Npad > 512) return false;
-  int Hpos = std::max((Ty + P.ky - 1) * P.W, nM * 128 + (P.ky - 1) * P.W + (P.kx - 1));
-  Hpos = (Hpos + 7) / 8 * 8;
-  const size_t smem = 4 * (size_t)Hpos * 16 + b_bytes;
-  if (smem > (size_t)TC_SMEM_LIMIT) return false;
-  *Hpos_out = Hpos;
-  *smem_out = smem;
+// Tile plan.  x: the fewest tiles whose halo (Tx + kx - 1) fits 256 positions; y: as many rows
+// as fill 256 positions (one row for a 2D problem); z: the run length L that minimises
+// (units per CTA) x (planes each unit reads) over a persistent grid of num_sms CTAs.
+bool plan_tc(TcPlan* pl, const ConvGeom& g, int mode, int p, int num_sms) {
+  const Pseudo q = pseudo_of(g);
+  if (!q.ok || q.kz > 8 || q.kx > 16) return false;
+  TcParams& P = pl->P;
+  P = TcParams{};
+  P.kx = q.kx;
+  P.ky = q.ky;
+  P.kz = q.kz;
+  P.circ_z = q.circ;
+  P.mode = mode;
+  const int Cin = mode == 0 ? g.C : p;
+  P.cout = mode == 0 ? p : g.C;
+  P.kgroups = (Cin + 7) / 8;
+  P.ogs = (P.cout + 7) / 8;
+  P.chunks_even = chunks_even_of(Cin);
+  int ox, oy, oz, ix, iy, iz;
+  if (mode == 0) {
+    pseudo_ext(g, g.sx, g.sy, g.sz, &ox, &oy, &oz);
+    pseudo_ext(g, g.ex, g.ey, g.ez, &ix, &iy, &iz);
+    P.org_x = P.org_y = P.org_z = 0;
+  } else {
+    pseudo_ext(g, g.ex, g.ey, g.ez, &ox, &oy, &oz);
+    pseudo_ext(g, g.sx, g.sy, g.sz, &ix, &iy, &iz);
+    P.org_x = -(P.kx - 1);
+    P.org_y = -(P.ky - 1);
+    P.org_z = -(P.kz - 1);
+  }
+  P.ox_lim = ox;
+  P.oy_lim = oy;
+  P.oz_lim = oz;
+  P.Zin = iz;
+  pl->Xin = ix;
+  pl->Yin = iy;
+  // M rows are tile positions ly * W + lx; the valid ones (lx < Tx, ly < Ty) must fit 2 M tiles
+  P.ntx = (ox + 255) / 256;
+  P.Tx = (ox + P.ntx - 1) / P.ntx;
+  P.W = P.Tx + P.kx - 1;
+  P.Ty = 1;
+  if (P.W <= 256) P.Ty = std::max(1, std::min(oy, (256 - P.Tx) / P.W + 1));
+  P.nty = (oy + P.Ty - 1) / P.Ty;
+  P.nM = ((P.Ty - 1) * P.W + P.Tx + 127) / 128;
+  if (P.nM > 2) return false;
+  P.nbx = P.W <= 256 ? 1 : 2;
+  P.Wb = (P.W + P.nbx - 1) / P.nbx;
+  P.PA = (std::max(P.nbx * P.Wb * P.Ty, P.nM * 128 + P.kx - 1) + 7) / 8 * 8;
+  P.stage_bytes = (uint32_t)(4 * P.PA * 16);
+  P.b_bytes = (uint32_t)((size_t)P.kgroups * P.kx * P.ky * P.kz * 1024);
+  const size_t fixed = TC_BAR_BYTES + P.b_bytes + 128;
+  if (fixed + 2 * (size_t)P.stage_bytes > TC_SMEM_LIMIT) return false;
+  P.stages = (int)std::min<size_t>(TC_MAX_STAGES, (TC_SMEM_LIMIT - fixed) / P.stage_bytes);
+  P.rs = std::min(P.kz + 1, 512 / (TC_SLOT_COLS * P.nM));
+  if (P.rs < P.kz || P.rs > 16) return false;
+  int cols = 32;
+  while (cols < P.nM * P.rs * TC_SLOT_COLS) cols <<= 1;
+  P.tmem_cols = cols;
+  // run length along z
+  const long long per_z = (long long)P.ogs * P.nty * P.ntx;
+  long long best_cost = -1;
+  int bestL = 1;
+  for (int L = 1; L <= oz; ++L) {
+    const long long units = per_z * ((oz + L - 1) / L);
+    const long long waves = (units + num_sms - 1) / num_sms;
+    const long long cost = waves * (L + P.kz - 1);
+    if (best_cost < 0 || cost <= best_cost) {
+      best_cost = cost;
+      bestL = L;
+    }
+  }
+  P.L = bestL;
+  P.nzr = (oz + P.L - 1) / P.L;
+  P.units = per_z * P.nzr;
+  pl->grid = (int)std::min<long long>(P.units, num_sms);
+  // at least half the SM's shared memory, so that one CTA (and its TMEM ring) owns each SM
+  pl->smem = std::max<size_t>(fixed + (size_t)P.stages * P.stage_bytes, 120 * 1024);
   return true;
 }
 
-static bool plan_tc(TcPlan* pl, int kx, int ky, int X, int Y, int ox_lim, int oy_lim, int org_x, int org_y,
-                    int chunks, int Npad) {
-  TcParams& P = pl->P;
-  P.kx = kx;
-  P.ky = ky;
-  P.K = kx * ky;
-  P.X = X;
-  P.Y = Y;
-  P.org_x = org_x;
-  P.org_y = org_y;
-  P.chunks = chunks;
-  P.groups = (chunks + 1) / 2;
-  P.Npad = Npad;
-  const int maxTx = 256 - (kx - 1);
-  P.ntx = (ox_lim + maxTx - 1) / maxTx;
-  P.Tx = (ox_lim + P.ntx - 1) / P.ntx;
-  P.W = P.Tx + kx - 1;
-  const size_t b_bytes = (size_t)P.K * 2 * 2 * Npad * 16;
-  P.bgroup_bytes = (uint32_t)b_bytes;
-  const int tymax = std::min(oy_lim, 64);
-  int chosen = 0, Hpos = 0;
-  size_t smem = 0;
-  for (int Ty = tymax; Ty >= 1; --Ty) {
-    int hp;
-    size_t sm;
-    if (!tile_fits(P, Ty, b_bytes, &hp, &sm)) continue;
-    if (P.ntx * ((oy_lim + Ty - 1) / Ty) >= 148) { chosen = Ty; Hpos = hp; smem = sm; break; }
-  }
-  if (chosen == 0) {
-    const int ty_fill = std::max(1, std::min(tymax, (128 + P.W - 1) / P.W));
-    for (int Ty = ty_fill; Ty >= 1; --Ty) {
-      int hp;
-      size_t sm;
-      if (tile_fits(P, Ty, b_bytes, &hp, &sm)) { chosen = Ty; Hpos = hp; smem = sm; break; }
-    }
-  }
-  if (chosen == 0) return false;
-  P.Ty = chosen;
-  P.nM = (P.Ty * P.W + 127) / 128;
-  P.Hpos = Hpos;
-  P.tmem_cols = pow2_at_least(P.nM * Npad);
-  pl->smem = smem;
-  pl->grid = P.ntx * ((oy_lim + P.Ty - 1) / P.Ty);
-  P.ox_lim = ox_lim;
-  P.oy_lim = oy_lim;
-  return P.tmem_cols <= 512;
+bool encode_input_map(CUtensorMap* map, const void* base, int X, int Y, int Z, int planes, int W, int Ty) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[5] = {8, (cuuint64_t)X, (cuuint64_t)Y, (cuuint64_t)Z, (cuuint64_t)planes};
+  const cuuint64_t strides[4] = {16, (cuuint64_t)16 * X, (cuuint64_t)16 * X * Y, (cuuint64_t)16 * X * Y * Z};
+  const cuuint32_t box[5] = {8, (cuuint32_t)W, (cuuint32_t)Ty, 1, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+int device_sms(hicu_handle* h) { return h->num_sms > 0 ? h->num_sms : 148; }
+
+}  // namespace
+
 bool tc_supported(const ConvGeom& g) {
-  return g.kz == 1 && g.ez == 1 && !g.cx && !g.cy && !g.cz && (g.C % 4) == 0 && g.kx <= 16 && g.ky <= 16;
+  TcPlan a, b;
+  return plan_tc(&a, g, 0, 8, 152) && plan_tc(&b, g, 1, 8, 152) && encode_fn() != nullptr;
+}
+
+bool tc_supported_p(const ConvGeom& g, int p) {
+  TcPlan a, b;
+  return plan_tc(&a, g, 0, p, 152) && plan_tc(&b, g, 1, p, 152) && encode_fn() != nullptr;
+}
+
+size_t tc_x_bytes(const ConvGeom& g) {
+  return (size_t)16 * 2 * chunks_even_of(g.C) * g.ex * g.ey * g.ez;
+}
+
+size_t tc_r_bytes(const ConvGeom& g, int p) { return (size_t)16 * 2 * chunks_even_of(p) * g.s; }
+
+size_t tc_b_bytes(const ConvGeom& g, int p, int mode) {
+  const Pseudo q = pseudo_of(g);
+  const int Cin = mode == 0 ? g.C : p, Cout = mode == 0 ? p : g.C;
+  return (size_t)((Cout + 7) / 8) * ((Cin + 7) / 8) * q.kx * q.ky * q.kz * 1024;
 }
 
 hicu_status tc_prepare_input(hicu_handle* h, const ConvGeom& g, KView x, uint4* planar, cudaStream_t st) {
-  const long long tot = (long long)g.ex * g.ey * (g.C / 4);
-  int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
-  HICU_LAUNCH(h, K_MISC, st, tc_split_input_kernel<<<blocks, 256, 0, st>>>(g.C, g.ex, g.ey, x, planar));
+  const int ce = chunks_even_of(g.C);
+  const long long tot = (long long)g.ex * g.ey * g.ez * ce;
+  int blocks = (int)std::min<long long>((tot + 255) / 256, 8192);
+  HICU_LAUNCH(h, K_MISC, st,
+              tc_split_input_kernel<<<blocks, 256, 0, st>>>(g.C, ce, g.ex, g.ey, g.ez, x, planar));
   return cuda_error(h, cudaGetLastError(), "tc_split_input");
 }
 
 hicu_status tc_prepare_r(hicu_handle* h, const ConvGeom& g, const float2* R, int p, uint4* planar,
                          cudaStream_t st) {
-  const long long tot = g.s * ((p + 3) / 4);
-  int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
-  HICU_LAUNCH(h, K_MISC, st, tc_split_r_kernel<<<blocks, 256, 0, st>>>(g.s, p, R, planar));
+  const int ce = chunks_even_of(p);
+  const long long tot = g.s * ce;
+  int blocks = (int)std::min<long long>((tot + 255) / 256, 8192);
+  HICU_LAUNCH(h, K_MISC, st, tc_split_r_kernel<<<blocks, 256, 0, st>>>(g.s, p, ce, R, planar));
   return cuda_error(h, cudaGetLastError(), "tc_split_r");
-}
-
-size_t tc_b_bytes(const ConvGeom& g, int p, int mode) {
-  const int chunks = mode == 0 ? g.C / 4 : (p + 3) / 4;
-  const int groups = (chunks + 1) / 2;
-  const int Npad = mode == 0 ? (2 * p + 15) / 16 * 16 : (2 * g.C + 15) / 16 * 16;
-  return (size_t)groups * g.K * 2 * 2 * Npad * 16;
 }
 
 hicu_status tc_prepare_weights(hicu_handle* h, const ConvGeom& g, const float2* bank, int p, int mode,
                                void* out, cudaStream_t st) {
-  const int chunks = mode == 0 ? g.C / 4 : (p + 3) / 4;
-  const int groups = (chunks + 1) / 2;
-  const int Npad = mode == 0 ? (2 * p + 15) / 16 * 16 : (2 * g.C + 15) / 16 * 16;
-  const long long tot = (long long)groups * g.K * 2 * 2 * Npad * 8;
+  const Pseudo q = pseudo_of(g);
+  const int Cin = mode == 0 ? g.C : p, Cout = mode == 0 ? p : g.C;
+  const int kgroups = (Cin + 7) / 8, ogs = (Cout + 7) / 8;
+  const long long tot = (long long)tc_b_bytes(g, p, mode) / 2;
   int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
   HICU_LAUNCH(h, K_MISC, st,
-              tc_prep_b_kernel<<<blocks, 256, 0, st>>>(mode, g.C, g.K, p, groups, Npad, bank,
-                                                       (__nv_bfloat16*)out));
+              tc_prep_b_kernel<<<blocks, 256, 0, st>>>(mode, Cin, Cout, g.n, q.kx, q.ky, q.kz, kgroups, ogs,
+                                                       bank, (__nv_bfloat16*)out));
   return cuda_error(h, cudaGetLastError(), "tc_prep_b");
 }
 
-static hicu_status launch_plan(hicu_handle* h, TcPlan& pl, int cls, cudaStream_t st) {
+static hicu_status launch_plan(hicu_handle* h, TcPlan& pl, const void* in, int cls, cudaStream_t st) {
+  CUtensorMap map;
+  if (!encode_input_map(&map, in, pl.Xin, pl.Yin, pl.P.Zin, 2 * pl.P.chunks_even, pl.P.Wb, pl.P.Ty))
+    return set_error(h, HICU_ERR_CUDA, "split-bf16: tensor map encoding failed");
   const cudaError_t e = allow_max_dynamic_smem((const void*)tc_corr_kernel);
   if (e != cudaSuccess) return cuda_error(h, e, "tc_corr smem");
-  HICU_LAUNCH(h, cls, st, tc_corr_kernel<<<pl.grid, TC_THREADS, pl.smem, st>>>(pl.P));
+  HICU_LAUNCH(h, cls, st, tc_corr_kernel<<<pl.grid, TC_THREADS, pl.smem, st>>>(map, pl.P));
   return cuda_error(h, cudaGetLastError(), "tc_corr");
 }
 
@@ -478,49 +718,50 @@ static hicu_status launch_plan(hicu_handle* h, TcPlan& pl, int cls, cudaStream_t
 hicu_status launch_conv_tc(hicu_handle* h, const ConvGeom& g, const uint4* xplanar, const void* bw, int p,
                            float2* R, uint4* Rs, double* partial, int* nblocks, cudaStream_t st) {
   TcPlan pl;
-  const int Npad = (2 * p + 15) / 16 * 16;
-  if (Npad > 256 || !plan_tc(&pl, g.kx, g.ky, g.ex, g.ey, g.sx, g.sy, 0, 0, g.C / 4, Npad))
-    return set_error(h, HICU_ERR_UNSUPPORTED, "split-bf16 conv: tile does not fit shared memory");
+  if (!plan_tc(&pl, g, 0, p, device_sms(h)))
+    return set_error(h, HICU_ERR_UNSUPPORTED, "split-bf16 conv: geometry or filter bank does not fit the kernel");
   *nblocks = pl.grid;
   if (!partial) return HICU_OK;
-  pl.P.conj_shift = 0;
-  pl.P.ain = xplanar;
-  pl.P.bw = (const uint4*)bw;
-  pl.P.mode = 0;
-  pl.P.p = p;
-  pl.P.R = R;
-  pl.P.Rs = Rs;
-  pl.P.chunksR = (p + 3) / 4;
-  pl.P.partial = partial;
-  pl.P.err = h->dev_err;
-  pl.P.m.p = nullptr;
-  pl.P.gout.p = nullptr;
-  return launch_plan(h, pl, K_CONV_TC, st);
+  TcParams& P = pl.P;
+  P.bw = (const unsigned char*)bw;
+  P.R = R;
+  P.Rs = Rs;
+  P.r_plane = g.s;
+  P.g = nullptr;
+  P.m = nullptr;
+  P.partial = partial;
+  P.err = h->dev_err;
+  return launch_plan(h, pl, xplanar, K_CONV_TC, st);
 }
 
 // adjoint: split planes of R -> masked g (region view), partial norms per CTA
 hicu_status launch_adjoint_tc(hicu_handle* h, const ConvGeom& g, const uint4* Rs, const void* bw, int p,
                               MView m, KView gout, double* partial, int* nblocks, cudaStream_t st) {
   TcPlan pl;
-  const int Npad = (2 * g.C + 15) / 16 * 16;
-  if (Npad > 256 ||
-      !plan_tc(&pl, g.kx, g.ky, g.sx, g.sy, g.ex, g.ey, -(g.kx - 1), -(g.ky - 1), (p + 3) / 4, Npad))
-    return set_error(h, HICU_ERR_UNSUPPORTED, "split-bf16 adjoint: tile does not fit shared memory");
+  if (!plan_tc(&pl, g, 1, p, device_sms(h)))
+    return set_error(h, HICU_ERR_UNSUPPORTED,
+                     "split-bf16 adjoint: geometry or filter bank does not fit the kernel");
   *nblocks = pl.grid;
   if (!partial) return HICU_OK;
-  pl.P.conj_shift = 1;
-  pl.P.ain = Rs;
-  pl.P.bw = (const uint4*)bw;
-  pl.P.mode = 1;
-  pl.P.p = g.C;
-  pl.P.R = nullptr;
-  pl.P.Rs = nullptr;
-  pl.P.chunksR = 0;
-  pl.P.gout = gout;
-  pl.P.m = m;
-  pl.P.partial = partial;
-  pl.P.err = h->dev_err;
-  return launch_plan(h, pl, K_ADJOINT_TC, st);
+  TcParams& P = pl.P;
+  P.bw = (const unsigned char*)bw;
+  P.R = nullptr;
+  P.Rs = nullptr;
+  P.g = gout.p;
+  P.g_sc = gout.sc;
+  P.m = m.p;
+  P.m_sc = m.sc;
+  const bool as2d = g.kz == 1 && g.ez == 1;
+  // pseudo (z, y) strides: a 2D problem's rows are its planes
+  P.g_sz = as2d ? gout.sy : gout.sz;
+  P.g_sy = as2d ? 0 : gout.sy;
+  P.g_base = (long long)gout.oz * gout.sz + (long long)gout.oy * gout.sy + gout.ox;
+  P.m_sz = as2d ? m.sy : m.sz;
+  P.m_sy = as2d ? 0 : m.sy;
+  P.m_base = (long long)m.oz * m.sz + (long long)m.oy * m.sy + m.ox;
+  P.partial = partial;
+  P.err = h->dev_err;
+  return launch_plan(h, pl, Rs, K_ADJOINT_TC, st);
 }
 
 }  // namespace hicu

@@ -266,9 +266,11 @@ hicu_status launch_finalize_step(hicu_handle* h, const double* part, int n_obj, 
 hicu_status launch_update(hicu_handle* h, const ConvGeom& g, KView y, KView gbuf, MView m,
                           const double* stats, cudaStream_t st);
 
-// tensor-core (split-bf16) path, 2D valid convolutions with C % 4 == 0
+// tensor-core (split-bf16) path: 2D and 3D, valid or circular along the outer axis
 bool tc_supported(const ConvGeom& g);
 size_t tc_b_bytes(const ConvGeom& g, int p, int mode);
+size_t tc_x_bytes(const ConvGeom& g);          // split planes of a region input
+size_t tc_r_bytes(const ConvGeom& g, int p);   // split planes of R
 hicu_status tc_prepare_weights(hicu_handle* h, const ConvGeom& g, const float2* bank, int p, int mode,
                                void* out, cudaStream_t st);
 hicu_status tc_prepare_input(hicu_handle* h, const ConvGeom& g, KView x, uint4* planar, cudaStream_t st);

@@ -431,9 +431,18 @@ def test_argument_errors(H):
 
 # ------------------------------------------------------------ split-bf16 tensor cores
 
-TC_CASES = ["2d_64_c4_p4", "2d_c16_p20", "2d_c32_permask", "tiny_one_output_c4", "2d_c8_p32_region"]
 CASES["tiny_one_output_c4"] = ((9, 9, 1), 4, (5, 5, 1), (0, 0, 0), ((2, 3, 0), (5, 5, 1)), 3)
 CASES["2d_c8_p32_region"] = ((100, 90, 1), 8, (5, 5, 1), (0, 0, 0), ((7, 11, 0), (83, 70, 1)), 32)
+# wider than one 256-position tile row, so the x axis splits into tiles
+CASES["2d_wide_two_x_tiles"] = ((300, 24, 1), 4, (5, 5, 1), (0, 0, 0), ((0, 0, 0), (300, 24, 1)), 8)
+# 2D with the row axis circular (streamed axis wraps)
+CASES["2d_circular_rows"] = ((40, 30, 1), 8, (5, 5, 1), (0, 1, 0), ((0, 0, 0), (40, 30, 1)), 8)
+# 3D shapes of the cine / knee workloads in miniature: 5x5x5 kernel, C = 8, p = 8
+CASES["3d_c8_k5_region"] = ((44, 38, 18), 8, (5, 5, 5), (0, 0, 0), ((2, 1, 1), (40, 36, 16)), 8)
+CASES["cine_c8_k5_circular_t"] = ((48, 36, 12), 8, (5, 5, 5), (0, 0, 1), ((0, 0, 0), (48, 36, 12)), 8)
+TC_CASES = ["2d_64_c4_p4", "2d_c16_p20", "2d_c32_permask", "tiny_one_output_c4", "2d_c8_p32_region",
+            "2d_odd_region", "tiny_one_output", "3d_region", "cine_circular_t", "2d_wide_two_x_tiles",
+            "2d_circular_rows", "3d_c8_k5_region", "cine_c8_k5_circular_t"]
 
 
 @pytest.mark.parametrize("name", TC_CASES)
@@ -520,9 +529,20 @@ def test_reconstruct_config1_split_bf16(H):
     assert abs(O.ser_db(pb.x_full, x_gpu) - O.ser_db(pb.x_full, x_ref)) <= 0.05
 
 
-def test_split_bf16_unsupported_geometry(H):
+@pytest.mark.parametrize("dims,ker,circ", [((24, 20, 1), (3, 3, 1), (1, 0, 0)),
+                                           ((24, 20, 8), (3, 3, 3), (0, 1, 0)),
+                                           ((24, 20, 8), (3, 3, 9), (0, 0, 1))])
+def test_split_bf16_unsupported_geometry(H, dims, ker, circ):
+    """The tensor-core tiling wraps only the streamed (outermost) axis and takes up to 8 offsets
+    along it; anything else is refused with HICU_ERR_UNSUPPORTED before any launch."""
     from paper_2004_08962_gb300 import hicu
-    og, oreg, hg, hr, x, f, mask, p, _ = setup("2d_odd_region")   # C = 3
+    rng = np.random.default_rng(3)
+    hg = hicu.make_geom(dims, 4, ker, circ)
+    hr = hicu.make_region((0, 0, 0), dims)
+    n = 4 * ker[0] * ker[1] * ker[2]
+    x = random_complex(rng, (4, dims[2], dims[1], dims[0])).astype(np.complex64)
+    f = random_complex(rng, (2, n)).astype(np.complex64)
     with pytest.raises(hicu.HicuError) as e:
         hicu.hicu_conv_null(H, hg, hr, cuda(x), cuda(f), prec=hicu.HICU_SPLIT_BF16)
     assert e.value.status == 8
+    hicu.hicu_check(H)
