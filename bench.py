@@ -240,7 +240,12 @@ def run_profile_case(kind: str, size: int) -> int:
         split-criterion solve of a perturbed Gram on the grid / cluster solver (the warm one
         is the launch a reconstruction repeats: capture with -s 1 -c 1)
     tc_step: one split-BF16 descent step on a size x size x 8-coil slice, p = 32
+    tc_step3d: one split-BF16 descent step on the knee-shaped 256 x 256 x 160 x 8-coil volume
+        (5 x 5 x 5 kernel, p = 8); each step launches conv, adjoint, conv
     fgrad: the filter gradient H(x)^H R on the brain slice, p = 32
+    principal: the principal subspace (tridiagonalisation path) of the brain slice's centre-region
+        Gram (n = 200, r = 75) and of the cine workload's centre-region Gram (n = 1000, r = 300),
+        twice each
     recon: one full reconstruction of the brain slice (for the launch list)
     """
     import torch
@@ -270,6 +275,23 @@ def run_profile_case(kind: str, size: int) -> int:
                              .astype(np.complex64) * 0.05).cuda()
         for _ in range(2):
             hicu.hicu_gd_step_filters(h, g2, r2, x, m, f, prec=hicu.HICU_SPLIT_BF16)
+    elif kind == "tc_step3d":
+        g3 = hicu.make_geom((256, 256, 160), 8, (5, 5, 5))
+        r3 = hicu.make_region((0, 0, 0), (256, 256, 160))
+        gen = torch.Generator(device="cuda").manual_seed(7)
+        x = torch.randn((8, 160, 256, 256), dtype=torch.complex64, device="cuda", generator=gen)
+        m = (torch.rand((160, 256, 256), device="cuda", generator=gen) < 0.2).to(torch.uint8)
+        f = torch.randn((8, 1000), dtype=torch.complex64, device="cuda", generator=gen) * 0.03
+        for _ in range(2):
+            hicu.hicu_gd_step_filters(h, g3, r3, x, m, f, prec=hicu.HICU_SPLIT_BF16)
+    elif kind == "principal":
+        for name in (WORKLOAD, "cine_192x144x24"):
+            pq = make_problem(name)
+            gq = hicu.make_geom(pq.dims, pq.ncoil, pq.kernel, pq.circular)
+            st = pq.stages[0]
+            G = hicu.hicu_gram(h, gq, hicu.make_region(st.off, st.ext), torch.from_numpy(pq.x0).cuda())
+            for _ in range(2):
+                hicu.hicu_principal_subspace(h, G, pq.rank)
     elif kind == "fgrad":
         rng = np.random.default_rng(8)
         x = torch.from_numpy(pb.x0).cuda()
@@ -408,7 +430,7 @@ def main():
     ap.add_argument("--impl", default="hicu", choices=["hicu", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", default=None, choices=["eig", "eig_cluster", "tc_step", "fgrad", "recon"],
+    ap.add_argument("--profile", default=None, choices=["eig", "eig_cluster", "tc_step", "tc_step3d", "principal", "fgrad", "recon"],
                     help="run one small fixed case for an ncu capture and exit")
     ap.add_argument("--size", type=int, default=2048, help="image size of the tc_step profile case")
     ap.add_argument("--workload", default="brain", choices=["brain", "batch"],

@@ -70,8 +70,10 @@ typedef enum {
 } hicu_prec;
 
 typedef enum {
-  HICU_JL_NULLSPACE = 0, /* Q~ = Q P, P is (n-r) x p  (Algorithm 1 step 6) */
-  HICU_JL_PROJECTOR = 1  /* Q~ = Q (Q^H P), P is n x p: depends only on span(Q) */
+  HICU_JL_NULLSPACE = 0,  /* Q~ = Q P, P is (n-r) x p  (Algorithm 1 step 6) */
+  HICU_JL_PROJECTOR = 1,  /* Q~ = Q (Q^H P), P is n x p: depends only on span(Q) */
+  HICU_JL_COMPLEMENT = 2  /* Q~ = P - V (V^H P) from the r principal vectors V: the same
+                             filters as HICU_JL_PROJECTOR (I - V V^H = Q Q^H), same draws of P */
 } hicu_jl;
 
 /* Kernel classes for launch accounting and event timing (hicu_profile_*). */
@@ -117,8 +119,12 @@ typedef struct {
   int32_t gram_on_current;   /* 0: null space of H^(i-1) (Algorithm 1 step 2 as
                                 printed, S^(0) := S^(1)); 1: use S^(i) */
   int32_t init;              /* 0: x^(0) = X0; 1: time-averaged along z (2D+t) */
-  int32_t eig_solver;        /* null-space solver: 0 by size, HICU_NULLSPACE_GRID or
-                                HICU_NULLSPACE_CLUSTER (see hicu_nullspace) */
+  int32_t eig_solver;        /* null-space solver: 0 = HICU_NULLSPACE_TRIDIAG when jl is
+                                HICU_JL_PROJECTOR (the principal vectors V, then
+                                HICU_JL_COMPLEMENT filters), else Jacobi by size;
+                                HICU_NULLSPACE_GRID or HICU_NULLSPACE_CLUSTER force
+                                Jacobi (see hicu_nullspace); HICU_NULLSPACE_TRIDIAG
+                                needs jl = HICU_JL_PROJECTOR */
 } hicu_params;
 
 /* Optional per-iteration log, HOST arrays (any may be NULL). */
@@ -182,6 +188,8 @@ hicu_status hicu_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* 
 #define HICU_NULLSPACE_CLUSTER 8 /* one-cluster double-float solver (n <= 256) */
 /* without either flag: the cluster solver for n <= HICU_NULLSPACE_CLUSTER_AUTO_MAX, else the grid one */
 #define HICU_NULLSPACE_CLUSTER_AUTO_MAX 128
+/* hicu_params.eig_solver only: principal subspace by tridiagonalisation (hicu_principal_subspace) */
+#define HICU_NULLSPACE_TRIDIAG 16
 
 /*
  * hicu_nullspace - eigen-decomposition of the Hermitian n x n matrix G and the
@@ -221,6 +229,34 @@ hicu_status hicu_nullspace(hicu_handle* h, int64_t n, int64_t r, const double* G
                            double* eigvals, int32_t flags, void* stream);
 
 /*
+ * hicu_principal_subspace - the r principal eigenvectors V of the Hermitian n x n
+ * matrix G (Algorithm 1 step 2 in Gram form: the r principal right singular
+ * vectors of H are the eigenvectors of G = H^H H for its r largest
+ * eigenvalues; the null space of step 3 is their orthogonal complement, which
+ * HICU_JL_COMPLEMENT uses without forming it).
+ * Householder tridiagonalisation G = Q_H T Q_H^H (one cooperative FP64 kernel,
+ * two bounded grid barriers per reflector), bisection on Sturm counts for the
+ * eigenvalues of T, inverse iteration for its r top eigenvectors (eigenvalues
+ * closer than 1e-10 ||G|| are orthogonalised against each other) and the
+ * reflectors applied to them.  FP64 throughout; the input is pre-scaled by a
+ * power of two.  Eigenvalues are accurate to ~1e-16 ||G|| (absolute) and
+ * span(V) to ~1e-16 ||G|| / (lambda_r - lambda_{r+1}).
+ *   n       : 2 .. 4096;  r : 1 .. n-1  (else HICU_ERR_SHAPE / HICU_ERR_RANK)
+ *   G       : complex128 n x n row-major, Hermitian (only read)
+ *   V       : complex128 [r][n]: row j is the eigenvector of eig_top[j]
+ *   eig_top : double [r], the r largest eigenvalues, ascending
+ *   eig_all : double [n], all eigenvalues ascending (nullable; costs one more
+ *             bisection pass)
+ *   tail    : device double, J = trace(G) - sum(eig_top), the tail energy of
+ *             Eq. 1 (nullable)
+ * All pointers are device pointers owned by the caller.  Scratch lives in the
+ * handle.  Eigenvectors are unique only up to a unit phase (and rotations
+ * inside repeated eigenvalues).
+ */
+hicu_status hicu_principal_subspace(hicu_handle* h, int64_t n, int64_t r, const double* G, double* V,
+                                    double* eig_top, double* eig_all, double* tail, void* stream);
+
+/*
  * hicu_nullspace_info - sweeps used by the last hicu_nullspace call on this
  * handle and how it converged: 0 = not within the sweep limit, 1 = full
  * decomposition, 2 = split criterion (synchronises the device).
@@ -230,9 +266,11 @@ hicu_status hicu_nullspace_info(hicu_handle* h, int32_t* sweeps, int32_t* conver
 /*
  * hicu_jl_compress - Q~ = Q P with P i.i.d. N(0, 1/p) (Algorithm 1 step 6;
  * Theory, JL paragraph).
- *   Q       : complex128 [(nr)][n] null basis as returned by hicu_nullspace
- *   mode    : HICU_JL_NULLSPACE (P is nr x p) or HICU_JL_PROJECTOR (P is n x p,
- *             Q~ = Q (Q^H P))
+ *   Q       : complex128 [(nr)][n] null basis as returned by hicu_nullspace, or,
+ *             with HICU_JL_COMPLEMENT, the nr = r principal vectors of
+ *             hicu_principal_subspace
+ *   mode    : HICU_JL_NULLSPACE (P is nr x p), HICU_JL_PROJECTOR (P is n x p,
+ *             Q~ = Q (Q^H P)) or HICU_JL_COMPLEMENT (P is n x p, Q~ = P - V (V^H P))
  *   P       : optional float64 row-major P supplied by the caller (device);
  *             if NULL, P is drawn on the device: element (row, col) is
  *             z(seed, counter, row*p + col)/sqrt(p), z = Box-Muller on
@@ -371,9 +409,10 @@ hicu_status hicu_batch_order(int32_t nslices, const hicu_problem* problems, int3
  * There is no counterpart in the paper, which reconstructs slices one at a time.
  *   `lanes` worker lanes (0: min(nslices, 8)), each with its own stream,
  *   workspace and host thread, take problems from one queue in hicu_batch_order
- *   order.  Problems with n <= 256 whose params.eig_solver is 0 use the cluster
- *   eigen-solver, which occupies 16 SMs and leaves the others to the other lanes.
- *   Grid-solver launches (n > 256) of all lanes go, in order, to one shared
+ *   order.  Problems that take a Jacobi solver by size (eig_solver 0 with
+ *   HICU_JL_NULLSPACE) use the cluster eigen-solver for n <= 256, which occupies
+ *   16 SMs and leaves the others to the other lanes.  Cooperative launches
+ *   (tridiagonalisation, grid Jacobi) of all lanes go, in order, to one shared
  *   high-priority stream: two grid-barrier kernels never wait for each other's
  *   SMs, and a pending one gets SMs first as they free up.
  *   Every problem gives the same result as hicu_reconstruct with the same

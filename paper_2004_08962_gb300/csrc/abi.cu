@@ -319,6 +319,15 @@ extern "C" hicu_status hicu_nullspace(hicu_handle* h, int64_t n, int64_t r, cons
   return run_nullspace(h, n, r, G, Q, eigvals, flags, (cudaStream_t)stream);
 }
 
+extern "C" hicu_status hicu_principal_subspace(hicu_handle* h, int64_t n, int64_t r, const double* G, double* V,
+                                               double* eig_top, double* eig_all, double* tail, void* stream) {
+  if (!h) return HICU_ERR_ARG;
+  if (n < 2 || n > 4096) return set_error(h, HICU_ERR_SHAPE, "principal_subspace: n must be in [2, 4096]");
+  if (r <= 0 || r >= n) return set_error(h, HICU_ERR_RANK, "principal_subspace: rank must satisfy 0 < r < n");
+  if (!G || !V || !eig_top) return set_error(h, HICU_ERR_ARG, "principal_subspace: null pointer");
+  return run_principal(h, n, r, G, V, eig_top, eig_all, tail, (cudaStream_t)stream);
+}
+
 extern "C" hicu_status hicu_nullspace_info(hicu_handle* h, int32_t* sweeps, int32_t* converged) {
   if (!h || !sweeps || !converged) return HICU_ERR_ARG;
   if (!h->eig_info) return set_error(h, HICU_ERR_ARG, "nullspace_info: no eigen-decomposition yet");
@@ -337,7 +346,7 @@ extern "C" hicu_status hicu_jl_compress(hicu_handle* h, int64_t n, int64_t nr, i
                                         void* stream) {
   if (!h) return HICU_ERR_ARG;
   if (!Q || !filters) return set_error(h, HICU_ERR_ARG, "jl_compress: null pointer");
-  if (mode != HICU_JL_NULLSPACE && mode != HICU_JL_PROJECTOR)
+  if (mode != HICU_JL_NULLSPACE && mode != HICU_JL_PROJECTOR && mode != HICU_JL_COMPLEMENT)
     return set_error(h, HICU_ERR_ARG, "jl_compress: unknown mode");
   if (n < 2 || nr < 1 || nr >= n) return set_error(h, HICU_ERR_RANK, "jl_compress: need 1 <= n-r < n");
   if (p < 1 || p > 4096) return set_error(h, HICU_ERR_RANK, "jl_compress: p out of range");
@@ -669,8 +678,14 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
   if (prm->jl != HICU_JL_NULLSPACE && prm->jl != HICU_JL_PROJECTOR)
     return set_error(h, HICU_ERR_ARG, "reconstruct: unknown JL mode");
   if (prm->init != 0 && prm->init != 1) return set_error(h, HICU_ERR_ARG, "reconstruct: unknown init");
-  if (prm->eig_solver != 0 && prm->eig_solver != HICU_NULLSPACE_GRID && prm->eig_solver != HICU_NULLSPACE_CLUSTER)
+  if (prm->eig_solver != 0 && prm->eig_solver != HICU_NULLSPACE_GRID && prm->eig_solver != HICU_NULLSPACE_CLUSTER &&
+      prm->eig_solver != HICU_NULLSPACE_TRIDIAG)
     return set_error(h, HICU_ERR_ARG, "reconstruct: unknown eig_solver");
+  if (prm->eig_solver == HICU_NULLSPACE_TRIDIAG && prm->jl != HICU_JL_PROJECTOR)
+    return set_error(h, HICU_ERR_ARG, "reconstruct: the tridiagonal solver needs jl = HICU_JL_PROJECTOR");
+  // principal vectors V and complement filters (I - V V^H) P: the projector-mode filters
+  const bool principal = prm->jl == HICU_JL_PROJECTOR &&
+                         (prm->eig_solver == 0 || prm->eig_solver == HICU_NULLSPACE_TRIDIAG);
   hicu_status s = check_prec(h, prm->prec);
   if (s) return s;
   long long total_iters = 0, total_steps = 0;
@@ -709,7 +724,7 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
     return cuda_error(h, cudaGetLastError(), "reconstruct: input copy");
   double* G = (double*)ws_get(h, WS_REC_G, sizeof(double2) * n * n, &s);
   if (s) return s;
-  double* Q = (double*)ws_get(h, WS_REC_Q, sizeof(double2) * n * nr, &s);
+  double* Q = (double*)ws_get(h, WS_REC_Q, sizeof(double2) * n * (principal ? r : nr), &s);
   if (s) return s;
   double* eig = (double*)ws_get(h, WS_REC_EIG, sizeof(double) * n, &s);
   if (s) return s;
@@ -734,12 +749,19 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
       if (s) return s;
       // after the first outer iteration: warm start, and stop at the top-r / rest split (step 3
       // needs an orthonormal basis of the complement of the r principal vectors, nothing more)
-      s = run_nullspace(h, n, r, G, Q, eig,
-                        HICU_NULLSPACE_SPLIT | (it > 0 ? HICU_NULLSPACE_WARM : 0) | prm->eig_solver, st);
-      if (s) return s;
-      HICU_LAUNCH(h, K_MISC, st, tail_sum_kernel<<<1, 256, 0, st>>>(eig, (int)nr, dlog + it));
+      if (principal) {
+        // Q (here: the r principal vectors) and J of Eq. 1 directly
+        s = run_principal(h, n, r, G, Q, eig, nullptr, dlog + it, st);
+        if (s) return s;
+      } else {
+        s = run_nullspace(h, n, r, G, Q, eig,
+                          HICU_NULLSPACE_SPLIT | (it > 0 ? HICU_NULLSPACE_WARM : 0) | prm->eig_solver, st);
+        if (s) return s;
+        HICU_LAUNCH(h, K_MISC, st, tail_sum_kernel<<<1, 256, 0, st>>>(eig, (int)nr, dlog + it));
+      }
       for (int j = 0; j < stg.gd_steps; ++j) {
-        s = hicu_gd_step(h, geom, &stg.region, y, m, Q, nr, stg.p, prm->jl, prm->seed, counter, nullptr,
+        s = hicu_gd_step(h, geom, &stg.region, y, m, Q, principal ? r : nr, stg.p,
+                         principal ? HICU_JL_COMPLEMENT : prm->jl, prm->seed, counter, nullptr,
                          dstats + 4 * counter, prm->prec, stream);
         if (s) return s;
         ++counter;

@@ -601,7 +601,10 @@ bool plan_tc(TcPlan* pl, const ConvGeom& g, int mode, int p, int num_sms) {
   P.nM = ((P.Ty - 1) * P.W + P.Tx + 127) / 128;
   if (P.nM > 2) return false;
   P.nbx = P.W <= 256 ? 1 : 2;
-  P.Wb = (P.W + P.nbx - 1) / P.nbx;
+  // One box keeps the row pitch W (a box of Ty rows lands as [Ty][W]).  A split row (Ty = 1):
+  // TMA writes to shared memory start 128-byte aligned and the second box starts Wb positions
+  // (16 bytes each) in, so Wb is a multiple of 8.
+  P.Wb = P.nbx == 1 ? P.W : ((P.W + 1) / 2 + 7) / 8 * 8;
   P.PA = (std::max(P.nbx * P.Wb * P.Ty, P.nM * 128 + P.kx - 1) + 7) / 8 * 8;
   P.stage_bytes = (uint32_t)(4 * P.PA * 16);
   P.b_bytes = (uint32_t)((size_t)P.kgroups * P.kx * P.ky * P.kz * 1024);

@@ -298,6 +298,14 @@ __global__ void eig_gather_q_kernel(int n, int npad, int nr, const double2* __re
                                     const int* __restrict__ rank, double2* __restrict__ Q);
 hicu_status run_nullspace(hicu_handle* h, int64_t n, int64_t r, const double* G, double* Q,
                           double* eigvals, int flags, cudaStream_t st);
+// principal subspace by tridiagonalisation (eig_tridiag.cu): V [r][n], eig_top [r] ascending,
+// eig_all [n] (nullable), J = trace(G) - sum(eig_top) (nullable)
+hicu_status run_principal(hicu_handle* h, int64_t n, int64_t r, const double* G, double* V, double* eig_top,
+                          double* eig_all, double* J, cudaStream_t st);
+// shared with the Jacobi solver (eig.cu): largest |Re|, |Im| and the exact power-of-two pre-scale
+__global__ void eig_absmax_kernel(long long nn, const double2* __restrict__ A, unsigned long long* amax_bits);
+__global__ void eig_scale_kernel(long long nn, double2* __restrict__ A, const unsigned long long* amax_bits,
+                                 double* scale_out);
 
 }  // namespace hicu
 

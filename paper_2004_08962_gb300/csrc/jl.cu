@@ -1,6 +1,7 @@
 // JL compression of the null space (Algorithm 1 step 6; Theory, JL paragraph):
 // Q~ = Q P with P i.i.d. zero-mean Gaussian of variance 1/p, drawn afresh for
-// every descent step.
+// every descent step.  Projector form Q~ = Q Q^H P, and the same filters from the
+// principal vectors V as Q~ = (I - V V^H) P.
 //
 // Random numbers: counter-based.  Element e of draw `counter` is Box-Muller on
 // SplitMix64 outputs 2m+1 and 2m+2 of the stream started at `seed`, with
@@ -101,11 +102,28 @@ __global__ void jl_combine_cplx_kernel(int n, int m, int p, const float2* __rest
   bank[(long long)k * n + a] = make_float2(re, im);
 }
 
+// bank[k][a] = P[a][k] - sum_j V[j][a] T[j][k]   (complement of the principal vectors V)
+__global__ void jl_combine_compl_kernel(int n, int m, int p, const float2* __restrict__ V,
+                                        const float2* __restrict__ T, const float* __restrict__ P,
+                                        float2* __restrict__ bank) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (a >= n) return;
+  float re = 0.f, im = 0.f;
+  for (int j = 0; j < m; ++j) {
+    const float2 q = V[(long long)j * n + a];
+    const float2 t = T[(long long)j * p + k];
+    re = fmaf(q.x, t.x, fmaf(-q.y, t.y, re));
+    im = fmaf(q.x, t.y, fmaf(q.y, t.x, im));
+  }
+  bank[(long long)k * n + a] = make_float2(P[(long long)a * p + k] - re, -im);
+}
+
 hicu_status launch_jl(hicu_handle* h, int64_t n, int64_t nr, int p, const double* Q, int mode,
                       const double* P, uint64_t seed, uint64_t counter, float* bank,
                       cudaStream_t st) {
   hicu_status s = HICU_OK;
-  const int rows = (mode == HICU_JL_PROJECTOR) ? (int)n : (int)nr;
+  const int rows = (mode == HICU_JL_NULLSPACE) ? (int)nr : (int)n;
   float* Pf = (float*)ws_get(h, WS_P, sizeof(float) * rows * p, &s);
   if (s) return s;
   float2* Qf = (float2*)ws_get(h, WS_QF, sizeof(float2) * nr * n, &s);
@@ -132,7 +150,12 @@ hicu_status launch_jl(hicu_handle* h, int64_t n, int64_t nr, int p, const double
     HICU_LAUNCH(h, K_JL, st,
                 jl_project_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>((int)n, (int)nr, p,
                                                                                         Qf, Pf, T));
-    HICU_LAUNCH(h, K_JL, st, jl_combine_cplx_kernel<<<grid, 128, 0, st>>>((int)n, (int)nr, p, Qf, T, (float2*)bank));
+    if (mode == HICU_JL_PROJECTOR)
+      HICU_LAUNCH(h, K_JL, st,
+                  jl_combine_cplx_kernel<<<grid, 128, 0, st>>>((int)n, (int)nr, p, Qf, T, (float2*)bank));
+    else
+      HICU_LAUNCH(h, K_JL, st,
+                  jl_combine_compl_kernel<<<grid, 128, 0, st>>>((int)n, (int)nr, p, Qf, T, Pf, (float2*)bank));
   }
   return cuda_error(h, cudaGetLastError(), "jl_compress");
 }

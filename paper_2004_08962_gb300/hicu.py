@@ -17,11 +17,12 @@ import torch
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libhicu.so")
 
 HICU_FP32, HICU_SPLIT_BF16 = 0, 1
-HICU_JL_NULLSPACE, HICU_JL_PROJECTOR = 0, 1
+HICU_JL_NULLSPACE, HICU_JL_PROJECTOR, HICU_JL_COMPLEMENT = 0, 1, 2
 
 EXPORTED = (
     "hicu_create", "hicu_destroy", "hicu_last_error", "hicu_status_string", "hicu_check",
     "hicu_filter_length", "hicu_num_outputs", "hicu_gram", "hicu_nullspace", "hicu_nullspace_info",
+    "hicu_principal_subspace",
     "hicu_jl_compress",
     "hicu_conv_null", "hicu_conv_null_adjoint", "hicu_gd_step_filters", "hicu_gd_step",
     "hicu_reconstruct", "hicu_profile_select", "hicu_profile_read", "hicu_conv_null_noalloc",
@@ -96,6 +97,7 @@ def lib() -> ctypes.CDLL:
             "hicu_gram": ([P, G, R, P, P, P], c_int32),
             "hicu_nullspace": ([P, c_int64, c_int64, P, P, P, c_int32, P], c_int32),
             "hicu_nullspace_info": ([P, POINTER(c_int32), POINTER(c_int32)], c_int32),
+            "hicu_principal_subspace": ([P, c_int64, c_int64, P, P, P, P, P, P], c_int32),
             "hicu_jl_compress": ([P, c_int64, c_int64, c_int32, P, c_int32, P, c_uint64, c_uint64, P, P],
                                  c_int32),
             "hicu_conv_null": ([P, G, R, P, P, c_int32, P, P, c_int32, P], c_int32),
@@ -223,6 +225,7 @@ def hicu_gram(h: Handle, geom, region, x: torch.Tensor, G: Optional[torch.Tensor
 
 
 HICU_NULLSPACE_WARM, HICU_NULLSPACE_SPLIT, HICU_NULLSPACE_GRID, HICU_NULLSPACE_CLUSTER = 1, 2, 4, 8
+HICU_NULLSPACE_TRIDIAG = 16
 
 
 def hicu_nullspace(h: Handle, G: torch.Tensor, r: int, warm: bool = False, split: bool = False,
@@ -238,6 +241,24 @@ def hicu_nullspace(h: Handle, G: torch.Tensor, r: int, warm: bool = False, split
              | (HICU_NULLSPACE_CLUSTER if solver == "cluster" else 0))
     h._check(lib().hicu_nullspace(h.ptr, n, r, _ptr(G), _ptr(Q), _ptr(eig), flags, _stream(stream)))
     return Q, eig
+
+
+def hicu_principal_subspace(h: Handle, G: torch.Tensor, r: int, want_all: bool = False,
+                            want_tail: bool = False, stream=None):
+    """-> (V [r][n] complex128 rows, eig_top [r] ascending[, eig_all [n]][, tail J])."""
+    n = G.shape[0]
+    V = torch.empty((r, n), dtype=torch.complex128, device=G.device)
+    top = torch.empty((r,), dtype=torch.float64, device=G.device)
+    allv = torch.empty((n,), dtype=torch.float64, device=G.device) if want_all else None
+    tail = torch.zeros((1,), dtype=torch.float64, device=G.device) if want_tail else None
+    h._check(lib().hicu_principal_subspace(h.ptr, n, r, _ptr(G), _ptr(V), _ptr(top), _ptr(allv), _ptr(tail),
+                                           _stream(stream)))
+    out = (V, top)
+    if want_all:
+        out += (allv,)
+    if want_tail:
+        out += (tail,)
+    return out
 
 
 def hicu_nullspace_info(h: Handle):
@@ -343,8 +364,9 @@ def hicu_gd_step(h: Handle, geom, region, y: torch.Tensor, mask: Optional[torch.
 
 def make_params(rank: int, stages, seed: int = 0, jl: int = HICU_JL_PROJECTOR, prec: int = HICU_FP32,
                 gram_on_current: bool = False, init: int = 0, eig_solver: Optional[str] = None):
-    """eig_solver: None (by size), "grid" or "cluster"."""
-    """stages: sequence of (off, ext, iters, gd_steps, p)."""
+    """stages: sequence of (off, ext, iters, gd_steps, p).  eig_solver: None (the library's
+    default: tridiagonal principal subspace in projector mode, else Jacobi by size), "grid",
+    "cluster" (Jacobi) or "tridiag"."""
     arr = (hicu_stage * len(stages))()
     for i, (off, ext, iters, gd, p) in enumerate(stages):
         arr[i].region = make_region(off, ext)
@@ -360,7 +382,8 @@ def make_params(rank: int, stages, seed: int = 0, jl: int = HICU_JL_PROJECTOR, p
     prm.prec = int(prec)
     prm.gram_on_current = 1 if gram_on_current else 0
     prm.init = int(init)
-    prm.eig_solver = {None: 0, "grid": HICU_NULLSPACE_GRID, "cluster": HICU_NULLSPACE_CLUSTER}[eig_solver]
+    prm.eig_solver = {None: 0, "grid": HICU_NULLSPACE_GRID, "cluster": HICU_NULLSPACE_CLUSTER,
+                      "tridiag": HICU_NULLSPACE_TRIDIAG}[eig_solver]
     prm._keep = arr  # keep the stage array alive with the struct
     return prm
 

@@ -67,13 +67,21 @@ def _geom(c):
     return hicu.make_geom((c["n"], c["n"], 1), c["C"], (c["k"], c["k"], 1), mask_per_coil=c["per_coil"])
 
 
-def test_batch_matches_single_problem_runs(H):
+def _jacobi_by_size(c):
+    return "cluster" if c["C"] * c["k"] ** 2 <= 256 else "grid"
+
+
+@pytest.mark.parametrize("solver", ["default", "jacobi"])
+def test_batch_matches_single_problem_runs(H, solver):
+    """default: the tridiagonal principal-subspace path (eig_solver 0, projector JL); jacobi: the
+    one-cluster solver for n <= 256 and the grid solver above, requested explicitly."""
     from paper_2004_08962_gb300 import hicu
     cases = _cases()
+    pick = (lambda c: None) if solver == "default" else _jacobi_by_size
     probs, outs = [], []
     for c in cases:
         x0, m, out = _tensors(c)
-        probs.append(hicu.make_problem_struct(_geom(c), x0, m, _params(c), out))
+        probs.append(hicu.make_problem_struct(_geom(c), x0, m, _params(c, pick(c)), out))
         outs.append(out)
     reports, st = hicu.hicu_reconstruct_batched(H, probs, lanes=3)
     assert st == 0
@@ -86,10 +94,8 @@ def test_batch_matches_single_problem_runs(H):
     assert lanes_used <= {0, 1, 2} and len(lanes_used) >= 2
     torch.cuda.synchronize()
     for c, out in zip(cases, outs):
-        n = c["C"] * c["k"] ** 2
-        solver = "cluster" if n <= 256 else "grid"
         x0, m, ref = _tensors(c)
-        hicu.hicu_reconstruct(H, _geom(c), x0, m, _params(c, solver), x_out=ref)
+        hicu.hicu_reconstruct(H, _geom(c), x0, m, _params(c, pick(c)), x_out=ref)
         torch.cuda.synchronize()
         np.testing.assert_array_equal(out.cpu().numpy(), ref.cpu().numpy())
         # observed entries untouched
@@ -136,7 +142,7 @@ def test_batch_failing_problem_does_not_stop_the_others(H):
     assert st == 3 and [r["status"] for r in reports] == [0, 3, 0]
     for c, out in ((cases[0], outs[0]), (cases[1], outs[2])):
         x0, m, ref = _tensors(c)
-        hicu.hicu_reconstruct(H, _geom(c), x0, m, _params(c, "cluster"), x_out=ref)
+        hicu.hicu_reconstruct(H, _geom(c), x0, m, _params(c), x_out=ref)
         torch.cuda.synchronize()
         np.testing.assert_array_equal(out.cpu().numpy(), ref.cpu().numpy())
     assert "problem 1" in hicu.lib().hicu_last_error(H.ptr).decode()

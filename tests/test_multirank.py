@@ -37,12 +37,14 @@ def test_rank_aggregation_gloo(tmp_path):
         "import bench\n"
         "r, w = dist.get_rank(), dist.get_world_size()\n"
         "t = bench.max_over_ranks(1.0 + r, 'cpu')\n"
-        "print(json.dumps({'rank': r, 't': t, 'rate': bench.job_rate(350, 3, w, t)}), flush=True)\n"
+        f"out = {str(tmp_path)!r} + f'/rank{{r}}.json'\n"
+        "open(out, 'w').write(json.dumps({'rank': r, 't': t, 'rate': bench.job_rate(350, 3, w, t)}))\n"
         "bench.barrier()\n"
         "dist.destroy_process_group()\n")
     res = _torchrun([str(script)], timeout=300)
     assert res.returncode == 0, res.stderr[-2000:]
-    rows = [json.loads(l) for l in res.stdout.splitlines() if l.startswith("{")]
+    # one file per rank: two ranks printing to one pipe may interleave their lines
+    rows = [json.loads((tmp_path / f"rank{r}.json").read_text()) for r in (0, 1)]
     assert sorted(r["rank"] for r in rows) == [0, 1]
     for r in rows:
         assert r["t"] == 2.0                       # the slowest rank's time on every rank
