@@ -85,7 +85,8 @@ typedef enum {
   HICU_K_JL = 4,         /* JL draw and compression */
   HICU_K_MISC = 5,       /* layout, reductions, update, sorting */
   HICU_K_CONV_TC = 6,    /* tensor-core convolution */
-  HICU_K_ADJOINT_TC = 7  /* tensor-core adjoint */
+  HICU_K_ADJOINT_TC = 7, /* tensor-core adjoint */
+  HICU_K_TRIDIAG = 8     /* Householder tridiagonalisation (principal subspace) */
 } hicu_kernel_class;
 
 typedef struct {

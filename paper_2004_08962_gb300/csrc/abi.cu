@@ -249,7 +249,7 @@ extern "C" hicu_status hicu_check(hicu_handle* h, void* stream) {
 
 extern "C" hicu_status hicu_profile_select(hicu_handle* h, int32_t kernel_class) {
   if (!h) return HICU_ERR_ARG;
-  if (kernel_class < -1 || kernel_class > K_ADJOINT_TC)
+  if (kernel_class < -1 || kernel_class > K_TRIDIAG)
     return set_error(h, HICU_ERR_ARG, "profile_select: unknown kernel class");
   h->prof_class = kernel_class;
   h->prof_used = 0;

@@ -1,0 +1,105 @@
+// Double-float arithmetic: a real number is the unevaluated sum hi + lo of two FP32
+// numbers (|lo| <= ulp(hi) / 2), added with Knuth's two-sum and multiplied with an
+// FMA-based two-product (Dekker), following the double-double formulas of Hida, Li and
+// Bailey's QD library with float in place of double.  ~2^-48 relative precision on the
+// FP32 pipes, which on this GPU run ~58x the FP64 rate at a fraction of its latency.
+// Used by the eigen-solvers (null-space step) for their serial and reduction-heavy
+// parts.  Operands must stay inside the FP32 range (the callers pre-scale by a power of
+// two so that the largest entry is O(1)).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace hicu {
+
+struct dfl {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fadd_rn(s, -a);
+  const float e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
+  return {s, e};
+}
+__device__ __forceinline__ dfl df_fast(float a, float b) {  // requires |a| >= |b| (or a == 0)
+  const float s = __fadd_rn(a, b);
+  return {s, __fadd_rn(b, -__fadd_rn(s, -a))};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  const dfl s = df_two_sum(a.hi, b.hi);
+  return df_fast(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  return df_fast(p, e);
+}
+__device__ __forceinline__ dfl df_mul_f(dfl a, float b) {  // double-float times float
+  const float p = __fmul_rn(a.hi, b);
+  const float e = __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p));
+  return df_fast(p, e);
+}
+__device__ __forceinline__ dfl df_from(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ dfl df_f(float x) { return {x, 0.f}; }
+
+// a / b: three quotient digits, each from the FP32 reciprocal of b.hi and the exact remainder
+__device__ __forceinline__ dfl df_div(dfl a, dfl b) {
+  const float r = __frcp_rn(b.hi);
+  const float q1 = __fmul_rn(a.hi, r);
+  dfl s = df_sub(a, df_mul_f(b, q1));
+  const float q2 = __fmul_rn(s.hi, r);
+  s = df_sub(s, df_mul_f(b, q2));
+  const float q3 = __fmul_rn(s.hi, r);
+  return df_add(df_fast(q1, q2), df_f(q3));
+}
+
+// sqrt(a), a >= 0: one Newton correction of the FP32 root with the exact residual a - x^2
+__device__ __forceinline__ dfl df_sqrt(dfl a) {
+  if (!(a.hi > 0.f)) return {0.f, 0.f};
+  const float x = __fsqrt_rn(a.hi);
+  const float p = __fmul_rn(x, x);
+  const float e = __fmaf_rn(x, x, -p);
+  const dfl res = df_sub(a, df_fast(p, e));
+  return df_fast(x, __fdiv_rn(res.hi, __fmul_rn(2.f, x)));
+}
+
+__device__ __forceinline__ dfl df_shfl_xor(dfl a, int o) {
+  return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+__device__ __forceinline__ dfl df_warp_sum(dfl a) {
+  for (int o = 16; o > 0; o >>= 1) a = df_add(a, df_shfl_xor(a, o));
+  return a;
+}
+
+// complex double-float
+struct cdf {
+  dfl re, im;
+};
+__device__ __forceinline__ cdf ld4(const float4* p) {
+  const float4 v = *p;
+  return {{v.x, v.y}, {v.z, v.w}};
+}
+__device__ __forceinline__ void st4(float4* p, cdf a) { *p = make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }
+__device__ __forceinline__ cdf c_conj(cdf a) { return {a.re, df_neg(a.im)}; }
+__device__ __forceinline__ cdf c_add(cdf a, cdf b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ cdf c_sub(cdf a, cdf b) { return {df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
+__device__ __forceinline__ cdf c_mul(cdf a, cdf b) {
+  return {df_sub(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+__device__ __forceinline__ cdf c_mulc(cdf a, cdf b) {  // conj(a) * b
+  return {df_add(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_sub(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+__device__ __forceinline__ cdf c_zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
+__device__ __forceinline__ cdf c_from(double2 z) { return {df_from(z.x), df_from(z.y)}; }
+__device__ __forceinline__ double2 c_to(cdf a) { return make_double2(df_to(a.re), df_to(a.im)); }
+__device__ __forceinline__ cdf c_warp_sum(cdf a) { return {df_warp_sum(a.re), df_warp_sum(a.im)}; }
+
+}  // namespace hicu

@@ -26,6 +26,7 @@
 #include <atomic>
 #include <mutex>
 
+#include "df.cuh"
 #include "hicu_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -37,46 +38,6 @@ constexpr int CL_MAX_N = 256;
 constexpr int CL_MAX_NP = CL_MAX_N / 2;
 constexpr size_t CL_MAX_SMEM = 200 * 1024;
 
-struct dfl {
-  float hi, lo;
-};
-
-__device__ __forceinline__ dfl df_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fadd_rn(s, -a);
-  const float e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
-  return {s, e};
-}
-__device__ __forceinline__ dfl df_fast(float a, float b) {  // requires |a| >= |b| (or a == 0)
-  const float s = __fadd_rn(a, b);
-  return {s, __fadd_rn(b, -__fadd_rn(s, -a))};
-}
-__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
-  const dfl s = df_two_sum(a.hi, b.hi);
-  return df_fast(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
-}
-__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
-  return df_fast(p, e);
-}
-__device__ __forceinline__ dfl df_from(double x) {
-  const float h = __double2float_rn(x);
-  return {h, __double2float_rn(x - (double)h)};
-}
-__device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
-
-struct cdf {
-  dfl re, im;
-};
-__device__ __forceinline__ cdf ld4(const float4* p) {
-  const float4 v = *p;
-  return {{v.x, v.y}, {v.z, v.w}};
-}
-__device__ __forceinline__ void st4(float4* p, cdf a) { *p = make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }
-__device__ __forceinline__ cdf c_conj(cdf a) { return {a.re, df_neg(a.im)}; }
 __device__ __forceinline__ cdf c_mul_e(cdf a, dfl ex, dfl ey) {  // a * e
   return {df_add(df_mul(a.re, ex), df_neg(df_mul(a.im, ey))), df_add(df_mul(a.re, ey), df_mul(a.im, ex))};
 }

@@ -6,183 +6,200 @@
 // Method (Golub & Van Loan, 4th ed., sections 8.3.1, 8.4.1 and 8.4.2):
 //  1. G = Q_H T Q_H^H with T real symmetric tridiagonal: n - 1 Householder steps
 //     H_k = I - tau_k v_k v_k^H, each making the part of column k below the
-//     subdiagonal vanish with a real subdiagonal entry.  One cooperative kernel;
-//     every CTA forms v_k itself from row k (G is Hermitian and kept in full), then
-//     w = tau A v on its own rows, one grid barrier, the symmetric rank-2 update
-//     A <- A - v w^H - w v^H of its own rows (w corrected by -tau/2 (w^H v) v), and a
-//     second barrier.
+//     subdiagonal vanish with a real subdiagonal entry.  One cooperative kernel over
+//     all SMs: every CTA forms v_k itself from the pivot row k (G is Hermitian and kept
+//     in full), w = tau A v on its own rows, one grid barrier, then the symmetric
+//     rank-2 update A <- A - v w^H - w v^H (w corrected by -tau/2 (w^H v) v) of its own
+//     rows and, in every CTA, of the next pivot row.
 //  2. Eigenvalues of T by bisection on Sturm counts (the LDL^T pivot recurrence,
-//     Kahan's form, which is backward stable), eight points per eigenvalue and round.
+//     Kahan's form, which is backward stable): one warp per eigenvalue, 32 points a round.
 //  3. Eigenvectors of T for the r largest eigenvalues by inverse iteration with a
 //     pivoted tridiagonal LU; eigenvalues closer than 1e-10 ||T|| are solved one after
 //     the other and orthogonalised against each other (modified Gram-Schmidt).
 //  4. V = Q_H Z: the reflectors applied to each eigenvector, last one first.
-// The input is pre-scaled by an exact power of two, so no intermediate overflows or
-// underflows whatever the scale of G.  Accuracy: eigenvalues to ~eps ||G|| (absolute),
-// span(V) to ~eps ||G|| / gap (the Davis-Kahan bound of any backward-stable method).
+// Arithmetic: double-float (df.cuh, ~2^-48), because FP64 on this GPU is both slow and of
+// long latency, and every stage here is a chain of dependent operations.  The input is
+// pre-scaled by an exact power of two (largest entry O(1)); inputs and outputs are FP64.
+// Accuracy: eigenvalues to ~1e-14 ||G|| (absolute), span(V) to ~1e-14 ||G|| / gap (the
+// Davis-Kahan bound of a backward-stable method at this precision).
 #include <algorithm>
 
+#include "df.cuh"
 #include "hicu_internal.cuh"
 
 namespace hicu {
 
 constexpr int TD_THREADS = 256;
-constexpr int BS_LANES = 8;  // bisection points per eigenvalue and round
-
-__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
 
 struct TdArgs {
   int n;
-  double2* A;      // n x n row-major, scaled copy of G (overwritten)
-  double* d;       // n   diagonal of T
-  double* e;       // n-1 subdiagonal of T
-  double2* refl;   // n x n: row k holds v_k (v_k[0] = 1, length n-k-1)
-  double2* tau;    // n-1
-  double2* w;      // n   scratch (w0 = tau A v)
-  double2* part;   // gridDim.x partial sums w0^H v
+  float4* A;      // n x n row-major complex double-float (rows of the trailing block updated in place)
+  float2* d;      // n   diagonal of T
+  float2* e;      // n-1 subdiagonal of T
+  float4* refl;   // n x n: row k holds v_k (v_k[0] = 1, length n-k-1)
+  float4* tau;    // n-1
+  float4* w;      // 2 n scratch (w0 = tau A v), by step parity
+  float4* part;   // 2 gridDim.x partial sums w0^H v, by step parity
   GridSync gs;
 };
 
-__device__ inline double block_sum_bcast(double v, double* sh) {
-  // sum over the CTA, result in every thread (two __syncthreads)
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) sh[w] = v;
+__device__ __forceinline__ float2 dpack(dfl a) { return make_float2(a.hi, a.lo); }
+__device__ __forceinline__ dfl dload(float2 a) { return {a.x, a.y}; }
+
+// sum of a complex double-float over the CTA, result in every thread (two __syncthreads)
+__device__ inline cdf block_sum_c(cdf a, float4* sh) {
+  a = c_warp_sum(a);
+  const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) st4(&sh[wi], a);
   __syncthreads();
-  double t = 0.0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+  cdf t = c_zero();
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = c_add(t, ld4(&sh[i]));
   __syncthreads();
   return t;
 }
 
+// One barrier per reflector.  Global row g is owned by CTA g mod G for the whole run (so a
+// CTA only ever reads back rows it wrote itself, ordered by __syncthreads) and updated in
+// place, except row k+1, the next pivot row: nobody writes it during step k, and every CTA
+// forms its updated values itself from v and w (all of which it holds), so the next
+// Householder vector needs no second barrier.  w0 and the partial sums alternate between
+// two buffers: a CTA can start step k+1 while others still read step k's, but cannot reach
+// step k+2 before every CTA has passed step k+1's barrier.
 __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
-  extern __shared__ double2 tsm[];
-  double2* v = tsm;          // [n]
-  double2* w = tsm + a.n;    // [n]
-  __shared__ double red[TD_THREADS / 32];
-  __shared__ double2 hh[2];  // tau, alpha
-  __shared__ double hbeta;
-  const int n = a.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = TD_THREADS / 32;
+  extern __shared__ float4 tsm[];
+  const int n = a.n;
+  float4* x = tsm;          // [n] current pivot row k: x[j] = A[k][k + j]
+  float4* v = tsm + n;      // [n]
+  float4* w = tsm + 2 * n;  // [n]
+  __shared__ float4 red[TD_THREADS / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = TD_THREADS / 32;
   const int G = gridDim.x, c = blockIdx.x;
   unsigned epoch = 0;
+  for (int j = tid; j < n; j += TD_THREADS) x[j] = a.A[j];
+  __syncthreads();
   for (int k = 0; k < n - 1; ++k) {
     const int m = n - k - 1;
-    const double2* rowk = a.A + (long long)k * n + (k + 1);
-    // --- the Householder vector of column k (every CTA, from row k)
-    double s2 = 0.0;
-    for (int j = tid; j < m; j += TD_THREADS) {
-      const double2 x = zconj(rowk[j]);
-      v[j] = x;
-      if (j > 0) s2 += x.x * x.x + x.y * x.y;
+    // --- Householder vector of column k = conj(row k right of the diagonal), in every CTA
+    cdf s2 = c_zero();
+    for (int j = 1 + tid; j < m; j += TD_THREADS) {
+      const cdf xj = ld4(&x[1 + j]);
+      s2.re = df_add(s2.re, df_add(df_mul(xj.re, xj.re), df_mul(xj.im, xj.im)));
     }
-    const double xn2 = block_sum_bcast(s2, red);
-    if (tid == 0) {
-      const double2 x0 = v[0];
-      double2 t = make_double2(0.0, 0.0), scale = make_double2(0.0, 0.0);
-      double beta = x0.x;
-      if (!(xn2 == 0.0 && x0.y == 0.0)) {
-        beta = -copysign(sqrt(x0.x * x0.x + x0.y * x0.y + xn2), x0.x);
-        t = make_double2((beta - x0.x) / beta, -x0.y / beta);
-        const double2 den = make_double2(x0.x - beta, x0.y);  // v = x / (x0 - beta)
-        const double dd = den.x * den.x + den.y * den.y;
-        scale = make_double2(den.x / dd, -den.y / dd);
-      }
-      hh[0] = t;
-      hh[1] = scale;
-      hbeta = beta;
-      if (c == 0) {
-        a.d[k] = a.A[(long long)k * n + k].x;
-        a.e[k] = beta;
-        a.tau[k] = t;
-      }
+    const dfl xn2 = block_sum_c(s2, red).re;
+    const cdf x0 = c_conj(ld4(&x[1]));
+    cdf tau = c_zero(), scale = c_zero();
+    dfl beta = x0.re;
+    if (!(xn2.hi == 0.f && x0.im.hi == 0.f)) {
+      const dfl nrm = df_sqrt(df_add(df_add(df_mul(x0.re, x0.re), df_mul(x0.im, x0.im)), xn2));
+      beta = x0.re.hi >= 0.f ? df_neg(nrm) : nrm;
+      tau.re = df_div(df_sub(beta, x0.re), beta);
+      tau.im = df_div(df_neg(x0.im), beta);
+      const cdf den = {df_sub(x0.re, beta), x0.im};  // v = x / (x0 - beta)
+      const dfl dd = df_add(df_mul(den.re, den.re), df_mul(den.im, den.im));
+      scale.re = df_div(den.re, dd);
+      scale.im = df_div(df_neg(den.im), dd);
+    }
+    const bool active = !(tau.re.hi == 0.f && tau.im.hi == 0.f);
+    if (c == 0 && tid == 0) {
+      a.d[k] = dpack(ld4(&x[0]).re);
+      a.e[k] = dpack(beta);
+      st4(&a.tau[k], tau);
+    }
+    for (int j = tid; j < m; j += TD_THREADS) {
+      cdf vj;
+      if (j == 0) vj = {{1.f, 0.f}, {0.f, 0.f}};
+      else vj = active ? c_mul(c_conj(ld4(&x[1 + j])), scale) : c_zero();
+      st4(&v[j], vj);
+      if (c == 0) st4(&a.refl[(long long)k * n + j], vj);
     }
     __syncthreads();
-    const double2 tau = hh[0], scale = hh[1];
-    const bool active = !(tau.x == 0.0 && tau.y == 0.0);
-    for (int j = tid; j < m; j += TD_THREADS) {
-      const double2 vj = j == 0 ? make_double2(1.0, 0.0) : (active ? zmul(v[j], scale) : make_double2(0.0, 0.0));
-      v[j] = vj;
-      if (c == 0) a.refl[(long long)k * n + j] = vj;
-    }
-    __syncthreads();
-    // --- w0 = tau A v on this CTA's rows (row i of the trailing block is owned by CTA i mod G)
-    double2 pp = make_double2(0.0, 0.0);
+    // --- w0 = tau A v on this CTA's rows (relative row i is global row k+1+i)
+    float4* wg = a.w + (k & 1) * n;
+    float4* pg = a.part + (k & 1) * G;
+    const int i0 = ((c - (k + 1)) % G + G) % G;  // first relative row owned by this CTA
+    cdf pp = c_zero();
     if (active) {
-      for (int i = c + G * warp; i < m; i += G * nw) {
-        const double2* row = a.A + (long long)(k + 1 + i) * n + (k + 1);
-        double2 y = make_double2(0.0, 0.0);
-        for (int j = lane; j < m; j += 32) {
-          const double2 aij = row[j], vj = v[j];
-          y.x += aij.x * vj.x - aij.y * vj.y;
-          y.y += aij.x * vj.y + aij.y * vj.x;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          y.x += __shfl_down_sync(0xffffffffu, y.x, o);
-          y.y += __shfl_down_sync(0xffffffffu, y.y, o);
-        }
+      for (int i = i0 + G * warp; i < m; i += G * nw) {
+        const float4* row = a.A + (long long)(k + 1 + i) * n + (k + 1);
+        cdf y = c_zero();
+        for (int j = lane; j < m; j += 32) y = c_add(y, c_mul(ld4(&row[j]), ld4(&v[j])));
+        y = c_warp_sum(y);
         if (lane == 0) {
-          const double2 w0 = zmul(tau, y);
-          a.w[i] = w0;
-          const double2 cv = zmul(zconj(w0), v[i]);
-          pp.x += cv.x;
-          pp.y += cv.y;
+          const cdf w0 = c_mul(tau, y);
+          st4(&wg[i], w0);
+          pp = c_add(pp, c_mulc(w0, ld4(&v[i])));
         }
       }
     }
     {
-      const double px = block_sum_bcast(pp.x, red);
-      const double py = block_sum_bcast(pp.y, red);
-      if (tid == 0) a.part[c] = make_double2(px, py);
+      const cdf ps = block_sum_c(pp, red);
+      if (tid == 0) st4(&pg[c], ps);
     }
     if (!grid_sync(a.gs, epoch)) return;
-    // --- alpha = -tau/2 (w0^H v); w = w0 + alpha v; rank-2 update of this CTA's rows
+    // --- alpha = -tau/2 (w0^H v); w = w0 + alpha v; rank-2 update of this CTA's rows but row k+1
     if (active) {
-      double sx = 0.0, sy = 0.0;
-      for (int q = tid; q < G; q += TD_THREADS) {
-        const double2 pq = a.part[q];
-        sx += pq.x;
-        sy += pq.y;
-      }
-      sx = block_sum_bcast(sx, red);
-      sy = block_sum_bcast(sy, red);
-      const double2 alpha = zmul(make_double2(-0.5 * tau.x, -0.5 * tau.y), make_double2(sx, sy));
-      for (int j = tid; j < m; j += TD_THREADS) {
-        const double2 w0 = a.w[j], vj = v[j];
-        w[j] = make_double2(w0.x + alpha.x * vj.x - alpha.y * vj.y, w0.y + alpha.x * vj.y + alpha.y * vj.x);
-      }
+      cdf sp = c_zero();
+      for (int q = tid; q < G; q += TD_THREADS) sp = c_add(sp, ld4(&pg[q]));
+      const cdf ssum = block_sum_c(sp, red);
+      const cdf htau = {df_mul_f(tau.re, -0.5f), df_mul_f(tau.im, -0.5f)};
+      const cdf alpha = c_mul(htau, ssum);
+      for (int j = tid; j < m; j += TD_THREADS) st4(&w[j], c_add(ld4(&wg[j]), c_mul(alpha, ld4(&v[j]))));
       __syncthreads();
-      for (int i = c + G * warp; i < m; i += G * nw) {
-        double2* row = a.A + (long long)(k + 1 + i) * n + (k + 1);
-        const double2 vi = v[i], wi = w[i];
+      for (int i = i0 + G * warp; i < m; i += G * nw) {
+        if (i == 0) continue;
+        float4* row = a.A + (long long)(k + 1 + i) * n + (k + 1);
+        const cdf vi = ld4(&v[i]), wi = ld4(&w[i]);
         for (int j = lane; j < m; j += 32) {
-          const double2 vj = v[j], wj = w[j];
           // A_ij -= v_i conj(w_j) + w_i conj(v_j)
-          const double2 t1 = zmul(vi, zconj(wj)), t2 = zmul(wi, zconj(vj));
-          double2 aij = row[j];
-          aij.x -= t1.x + t2.x;
-          aij.y -= t1.y + t2.y;
-          row[j] = aij;
+          const cdf t = c_add(c_mul(vi, c_conj(ld4(&w[j]))), c_mul(wi, c_conj(ld4(&v[j]))));
+          st4(&row[j], c_sub(ld4(&row[j]), t));
         }
       }
     }
-    if (!grid_sync(a.gs, epoch)) return;
+    // --- the next pivot row k+1 (relative row 0: v_0 = 1), formed by every CTA
+    {
+      const float4* row = a.A + (long long)(k + 1) * n + (k + 1);
+      const cdf w0c = active ? ld4(&w[0]) : c_zero();
+      for (int j = tid; j < m; j += TD_THREADS) {
+        cdf aij = ld4(&row[j]);
+        if (active) aij = c_sub(aij, c_add(c_conj(ld4(&w[j])), c_mul(w0c, c_conj(ld4(&v[j])))));
+        st4(&x[j], aij);
+      }
+    }
+    __syncthreads();
   }
-  if (c == 0 && tid == 0) a.d[n - 1] = a.A[(long long)(n - 1) * n + (n - 1)].x;
+  if (c == 0 && tid == 0) a.d[n - 1] = dpack(ld4(&x[0]).re);
 }
 
-// Gershgorin interval of T, its norm bound and the pivot floor: info[0..3] = lo, hi, tnorm, pivmin
-__global__ void td_bounds_kernel(int n, const double* __restrict__ d, const double* __restrict__ e,
-                                 double* __restrict__ info) {
-  __shared__ double s_lo[256], s_hi[256], s_e2[256];
-  double lo = 1e308, hi = -1e308, e2m = 0.0;
+// A = 2^-e G in double-float (the largest |Re|, |Im| of G in [2^(e-1), 2^e)); scale = 2^-e
+__global__ void td_prep_kernel(long long nn, const double2* __restrict__ G, const unsigned long long* amax_bits,
+                               double* scale_out, float4* __restrict__ A) {
+  const double amax = __longlong_as_double((long long)*amax_bits);
+  int ex2 = 0;
+  if (amax > 0.0 && amax <= 1.7e308) frexp(amax, &ex2);
+  const double sc = ldexp(1.0, -ex2);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *scale_out = sc;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x) {
+    const double2 g = G[i];
+    st4(&A[i], c_from(make_double2(g.x * sc, g.y * sc)));
+  }
+}
+
+// Gershgorin interval of T, its norm bound and the pivot floor; e2[i] = e[i]^2.
+// info: [0] lo, [1] hi (double-float), [2] tnorm, [3] pivmin (float in .x)
+__global__ void td_bounds_kernel(int n, const float2* __restrict__ d, const float2* __restrict__ e,
+                                 float2* __restrict__ e2, float2* __restrict__ info) {
+  __shared__ float s_lo[256], s_hi[256], s_e2[256];
+  float lo = 3e38f, hi = -3e38f, e2m = 0.f;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double el = i > 0 ? fabs(e[i - 1]) : 0.0, er = i < n - 1 ? fabs(e[i]) : 0.0;
-    lo = fmin(lo, d[i] - el - er);
-    hi = fmax(hi, d[i] + el + er);
-    if (i < n - 1) e2m = fmax(e2m, e[i] * e[i]);
+    const float el = i > 0 ? fabsf(e[i - 1].x) : 0.f, er = i < n - 1 ? fabsf(e[i].x) : 0.f;
+    lo = fminf(lo, d[i].x - el - er);
+    hi = fmaxf(hi, d[i].x + el + er);
+    if (i < n - 1) {
+      const dfl ei = dload(e[i]);
+      e2[i] = dpack(df_mul(ei, ei));
+      e2m = fmaxf(e2m, ei.hi * ei.hi);
+    }
   }
   s_lo[threadIdx.x] = lo;
   s_hi[threadIdx.x] = hi;
@@ -190,210 +207,222 @@ __global__ void td_bounds_kernel(int n, const double* __restrict__ d, const doub
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o) {
-      s_lo[threadIdx.x] = fmin(s_lo[threadIdx.x], s_lo[threadIdx.x + o]);
-      s_hi[threadIdx.x] = fmax(s_hi[threadIdx.x], s_hi[threadIdx.x + o]);
-      s_e2[threadIdx.x] = fmax(s_e2[threadIdx.x], s_e2[threadIdx.x + o]);
+      s_lo[threadIdx.x] = fminf(s_lo[threadIdx.x], s_lo[threadIdx.x + o]);
+      s_hi[threadIdx.x] = fmaxf(s_hi[threadIdx.x], s_hi[threadIdx.x + o]);
+      s_e2[threadIdx.x] = fmaxf(s_e2[threadIdx.x], s_e2[threadIdx.x + o]);
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const double tn = fmax(fabs(s_lo[0]), fabs(s_hi[0]));
-    const double pivmin = 1e-290 * fmax(1.0, s_e2[0]);
-    const double eps = 0x1.0p-52;
-    info[0] = s_lo[0] - 4.0 * eps * tn - 2.0 * pivmin;
-    info[1] = s_hi[0] + 4.0 * eps * tn + 2.0 * pivmin;
-    info[2] = tn;
-    info[3] = pivmin;
+    // the bounds use the hi parts only: widen them by a relative 2^-20
+    const float tn = fmaxf(fabsf(s_lo[0]), fabsf(s_hi[0]));
+    const float pad = 0x1.0p-20f * tn + 1e-30f;
+    const float pivmin = 1e-33f * fmaxf(1.f, s_e2[0]);
+    info[0] = make_float2(s_lo[0] - pad, 0.f);
+    info[1] = make_float2(s_hi[0] + pad, 0.f);
+    info[2] = make_float2(tn, 0.f);
+    info[3] = make_float2(pivmin, 0.f);
   }
 }
 
 // number of eigenvalues of T below x (Sturm count on the LDL^T pivots)
-__device__ __forceinline__ int sturm_count(int n, const double* __restrict__ d, const double* __restrict__ e,
-                                           double x, double pivmin) {
-  double q = d[0] - x;
-  if (fabs(q) <= pivmin) q = -pivmin;
-  int cnt = q < 0.0;
+__device__ __forceinline__ int sturm_count(int n, const float2* __restrict__ d, const float2* __restrict__ e2,
+                                           dfl x, float pivmin) {
+  dfl q = df_sub(dload(d[0]), x);
+  if (fabsf(q.hi) <= pivmin) q = {-pivmin, 0.f};
+  int cnt = q.hi < 0.f;
   for (int i = 1; i < n; ++i) {
-    const double ei = e[i - 1];
-    q = (d[i] - x) - ei * ei / q;
-    if (fabs(q) <= pivmin) q = -pivmin;
-    cnt += q < 0.0;
+    q = df_sub(df_sub(dload(d[i]), x), df_div(dload(e2[i - 1]), q));
+    if (fabsf(q.hi) <= pivmin) q = {-pivmin, 0.f};
+    cnt += q.hi < 0.f;
   }
   return cnt;
 }
 
-// Eigenvalue t0 + g (ascending order) for every group g of BS_LANES lanes: multisection to an
-// absolute width of 2 eps ||T||.  lam_out[g] = eigenvalue / scale.
-__global__ void td_bisect_kernel(int n, int t0, int count, const double* __restrict__ d, const double* __restrict__ e,
-                                 const double* __restrict__ info, const double* __restrict__ scale,
-                                 double* __restrict__ lam_scaled, double* __restrict__ lam_out) {
-  const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / BS_LANES;
-  const int sub = threadIdx.x % BS_LANES;
-  const unsigned gmask = ((1u << BS_LANES) - 1u) << ((threadIdx.x & 31) / BS_LANES * BS_LANES);
-  if (gid >= count) return;  // whole groups leave together (count is per group)
-  const int t = t0 + gid;
-  double lo = info[0], hi = info[1];
-  const double tol = 2.0 * 0x1.0p-52 * info[2] + info[3];
-  const double pivmin = info[3];
-  for (int it = 0; it < 64 && hi - lo > tol; ++it) {
-    const double step = (hi - lo) / (BS_LANES + 1);
-    const double x = lo + step * (sub + 1);
-    const int cnt = sturm_count(n, d, e, x, pivmin);
+// Eigenvalue t0 + blockIdx.x (ascending order), one warp each: multisection with 32 points a
+// round (5 bits) to an absolute width of 2^-46 ||T||.
+__global__ void __launch_bounds__(32) td_bisect_kernel(int n, int t0, const float2* __restrict__ d,
+                                                       const float2* __restrict__ e2,
+                                                       const float2* __restrict__ info,
+                                                       const double* __restrict__ scale,
+                                                       float2* __restrict__ lam_scaled,
+                                                       double* __restrict__ lam_out) {
+  const int g = blockIdx.x, lane = threadIdx.x;
+  const int t = t0 + g;
+  dfl lo = dload(info[0]), hi = dload(info[1]);
+  const float tol = 0x1.0p-46f * info[2].x + info[3].x;
+  const float pivmin = info[3].x;
+  const dfl inv33 = df_div(df_f(1.f), df_f(33.f));
+  for (int it = 0; it < 24 && df_sub(hi, lo).hi > tol; ++it) {
+    const dfl step = df_mul(df_sub(hi, lo), inv33);
+    const int cnt = sturm_count(n, d, e2, df_add(lo, df_mul_f(step, (float)(lane + 1))), pivmin);
     // the first point whose count exceeds t bounds the eigenvalue from above
-    const unsigned above = __ballot_sync(gmask, cnt > t) & gmask;
-    const int first = above ? (__ffs(above) - 1) % BS_LANES : BS_LANES;
-    const double nlo = first == 0 ? lo : lo + step * first;
-    const double nhi = first == BS_LANES ? hi : lo + step * (first + 1);
+    const unsigned above = __ballot_sync(0xffffffffu, cnt > t);
+    const int first = above ? __ffs(above) - 1 : 32;
+    const dfl nlo = first == 0 ? lo : df_add(lo, df_mul_f(step, (float)first));
+    const dfl nhi = first == 32 ? hi : df_add(lo, df_mul_f(step, (float)(first + 1)));
     lo = nlo;
     hi = nhi;
   }
-  if (sub == 0) {
-    const double l = 0.5 * (lo + hi);
-    if (lam_scaled) lam_scaled[gid] = l;
-    if (lam_out) lam_out[gid] = l / *scale;
+  if (lane == 0) {
+    const dfl l = df_mul_f(df_add(lo, hi), 0.5f);
+    if (lam_scaled) lam_scaled[g] = dpack(l);
+    if (lam_out) lam_out[g] = df_to(l) / *scale;
   }
 }
 
-__device__ __forceinline__ double hash_unit(uint64_t t, uint64_t i) {
+__device__ __forceinline__ float hash_unit(uint64_t t, uint64_t i) {
   uint64_t z = t * 0x9E3779B97F4A7C15ull + i * 0xBF58476D1CE4E5B9ull + 1ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   z ^= z >> 31;
-  return (double)(z >> 11) * 0x1.0p-53 * 2.0 - 1.0;
+  return (float)(z >> 40) * 0x1.0p-24f * 2.f - 1.f;
 }
 
 // Eigenvectors of T for lam[0..r) (ascending) by inverse iteration; Z[j] (length n, real, unit).
-// A thread owns a run of eigenvalues closer than 1e-10 ||T|| (the first of the run does the work)
-// and orthogonalises each new vector against the earlier ones of its run.  work: 5 n doubles per
-// thread (the pivoted LU of T - lam I).
-__global__ void td_inviter_kernel(int n, int r, const double* __restrict__ d, const double* __restrict__ e,
-                                  const double* __restrict__ lam, const double* __restrict__ info,
-                                  double* __restrict__ work, double* __restrict__ Z) {
-  const int j0 = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j0 >= r) return;
-  const double tnorm = info[2];
-  const double ctol = 1e-10 * tnorm;
-  if (j0 > 0 && lam[j0] - lam[j0 - 1] < ctol) return;  // not the first of its run
+// One warp per run of eigenvalues closer than 1e-10 ||T|| (the block of the run's first index
+// does the work; the others leave): lane 0 runs the serial pivoted LU and the triangular
+// solves in shared memory, the warp normalises and orthogonalises each new vector against the
+// run's earlier ones (modified Gram-Schmidt).  Shared memory: 6 n float2.
+__global__ void __launch_bounds__(32) td_inviter_kernel(int n, int r, const float2* __restrict__ d,
+                                                        const float2* __restrict__ e,
+                                                        const float2* __restrict__ lam,
+                                                        const float2* __restrict__ info, float2* __restrict__ Z) {
+  extern __shared__ float2 ism[];
+  float2* u1i = ism;  // 1 / pivot
+  float2* u2 = u1i + n;
+  float2* u3 = u2 + n;
+  float2* lm = u3 + n;
+  float2* sw = lm + n;  // .x = 1: rows i, i+1 swapped at step i
+  float2* z = sw + n;
+  const int j0 = blockIdx.x, lane = threadIdx.x;
+  const float tnorm = info[2].x;
+  const float ctol = 1e-10f * tnorm;
+  if (j0 > 0 && df_sub(dload(lam[j0]), dload(lam[j0 - 1])).hi < ctol) return;  // not the first of its run
   int j1 = j0 + 1;
-  while (j1 < r && lam[j1] - lam[j1 - 1] < ctol) ++j1;
-  double* u1 = work + (size_t)j0 * 5 * n;
-  double* u2 = u1 + n;
-  double* u3 = u2 + n;
-  double* lm = u3 + n;
-  double* sw = lm + n;  // 1.0: rows i, i+1 swapped at step i
-  const double tiny = 0x1.0p-52 * tnorm + info[3];
+  while (j1 < r && df_sub(dload(lam[j1]), dload(lam[j1 - 1])).hi < ctol) ++j1;
+  const float tiny = 0x1.0p-46f * tnorm + info[3].x;
   for (int j = j0; j < j1; ++j) {
-    const double lj = lam[j];
-    // pivoted LU of T - lj I
-    double ca = d[0] - lj, cc = n > 1 ? e[0] : 0.0;
-    for (int i = 0; i < n - 1; ++i) {
-      const double b = e[i];
-      const double na = d[i + 1] - lj, nc = (i + 1 < n - 1) ? e[i + 1] : 0.0;
-      if (fabs(ca) >= fabs(b)) {
-        const double piv = fabs(ca) > tiny ? ca : (ca >= 0.0 ? tiny : -tiny);
-        const double l = b / piv;
-        lm[i] = l;
-        sw[i] = 0.0;
-        u1[i] = piv;
-        u2[i] = cc;
-        u3[i] = 0.0;
-        ca = na - l * cc;
-        cc = nc;
-      } else {
-        const double l = ca / b;
-        lm[i] = l;
-        sw[i] = 1.0;
-        u1[i] = b;
-        u2[i] = na;
-        u3[i] = nc;
-        ca = cc - l * na;
-        cc = -l * nc;
-      }
-    }
-    u1[n - 1] = fabs(ca) > tiny ? ca : (ca >= 0.0 ? tiny : -tiny);
-    double* z = Z + (size_t)j * n;
-    for (int i = 0; i < n; ++i) z[i] = hash_unit((uint64_t)(j + 1), (uint64_t)i);
-    for (int iter = 0; iter < 3; ++iter) {
-      // forward: row swaps and L
+    const dfl lj = dload(lam[j]);
+    if (lane == 0) {
+      // pivoted LU of T - lj I
+      dfl ca = df_sub(dload(d[0]), lj), cc = n > 1 ? dload(e[0]) : df_f(0.f);
       for (int i = 0; i < n - 1; ++i) {
-        double zi = z[i], zn = z[i + 1];
-        if (sw[i] != 0.0) {
-          const double t = zi;
-          zi = zn;
-          zn = t;
+        const dfl b = dload(e[i]);
+        const dfl na = df_sub(dload(d[i + 1]), lj), nc = (i + 1 < n - 1) ? dload(e[i + 1]) : df_f(0.f);
+        if (fabsf(ca.hi) >= fabsf(b.hi)) {
+          const dfl piv = fabsf(ca.hi) > tiny ? ca : df_f(ca.hi >= 0.f ? tiny : -tiny);
+          const dfl pinv = df_div(df_f(1.f), piv);
+          const dfl l = df_mul(b, pinv);
+          lm[i] = dpack(l);
+          sw[i] = make_float2(0.f, 0.f);
+          u1i[i] = dpack(pinv);
+          u2[i] = dpack(cc);
+          u3[i] = make_float2(0.f, 0.f);
+          ca = df_sub(na, df_mul(l, cc));
+          cc = nc;
+        } else {
+          const dfl binv = df_div(df_f(1.f), b);
+          const dfl l = df_mul(ca, binv);
+          lm[i] = dpack(l);
+          sw[i] = make_float2(1.f, 0.f);
+          u1i[i] = dpack(binv);
+          u2[i] = dpack(na);
+          u3[i] = dpack(nc);
+          ca = df_sub(cc, df_mul(l, na));
+          cc = df_neg(df_mul(l, nc));
         }
-        z[i] = zi;
-        z[i + 1] = zn - lm[i] * zi;
       }
-      // back substitution with U (diagonals u1, u2, u3)
-      double x1 = 0.0, x2 = 0.0;  // x[i+1], x[i+2]
-      double nrm = 0.0;
-      for (int i = n - 1; i >= 0; --i) {
-        double s = z[i];
-        if (i + 1 < n) s -= u2[i] * x1;
-        if (i + 2 < n) s -= u3[i] * x2;
-        const double xi = s / u1[i];
-        z[i] = xi;
-        x2 = x1;
-        x1 = xi;
-      }
-      for (int q = j0; q < j; ++q) {  // modified Gram-Schmidt against the run's earlier vectors
-        const double* p = Z + (size_t)q * n;
-        double dp = 0.0;
-        for (int i = 0; i < n; ++i) dp += p[i] * z[i];
-        for (int i = 0; i < n; ++i) z[i] -= dp * p[i];
-      }
-      for (int i = 0; i < n; ++i) nrm += z[i] * z[i];
-      // scale by a power of two first (the solve can grow by ~1 / tiny), then normalise
-      int ex = 0;
-      frexp(sqrt(nrm), &ex);
-      const double p2 = ldexp(1.0, -ex);
-      nrm = 0.0;
-      for (int i = 0; i < n; ++i) {
-        z[i] *= p2;
-        nrm += z[i] * z[i];
-      }
-      const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
-      for (int i = 0; i < n; ++i) z[i] *= inv;
+      const dfl last = fabsf(ca.hi) > tiny ? ca : df_f(ca.hi >= 0.f ? tiny : -tiny);
+      u1i[n - 1] = dpack(df_div(df_f(1.f), last));
     }
+    for (int i = lane; i < n; i += 32) z[i] = make_float2(hash_unit((uint64_t)(j + 1), (uint64_t)i), 0.f);
+    __syncwarp();
+    for (int iter = 0; iter < 3; ++iter) {
+      if (lane == 0) {
+        // forward: row swaps and L
+        dfl zi = dload(z[0]);
+        for (int i = 0; i < n - 1; ++i) {
+          dfl zn = dload(z[i + 1]);
+          if (sw[i].x != 0.f) {
+            const dfl t = zi;
+            zi = zn;
+            zn = t;
+          }
+          z[i] = dpack(zi);
+          zi = df_sub(zn, df_mul(dload(lm[i]), zi));
+        }
+        z[n - 1] = dpack(zi);
+        // back substitution with U (diagonals 1/u1, u2, u3)
+        dfl x1 = df_f(0.f), x2 = df_f(0.f);  // x[i+1], x[i+2]
+        for (int i = n - 1; i >= 0; --i) {
+          dfl sacc = dload(z[i]);
+          if (i + 1 < n) sacc = df_sub(sacc, df_mul(dload(u2[i]), x1));
+          if (i + 2 < n) sacc = df_sub(sacc, df_mul(dload(u3[i]), x2));
+          const dfl xi = df_mul(sacc, dload(u1i[i]));
+          z[i] = dpack(xi);
+          x2 = x1;
+          x1 = xi;
+        }
+      }
+      __syncwarp();
+      for (int q = j0; q < j; ++q) {  // modified Gram-Schmidt against the run's earlier vectors
+        const float2* p = Z + (size_t)q * n;
+        dfl dp = df_f(0.f);
+        for (int i = lane; i < n; i += 32) dp = df_add(dp, df_mul(dload(p[i]), dload(z[i])));
+        dp = df_warp_sum(dp);
+        for (int i = lane; i < n; i += 32) z[i] = dpack(df_sub(dload(z[i]), df_mul(dp, dload(p[i]))));
+        __syncwarp();
+      }
+      // scale by a power of two first (the solve can grow by ~1 / tiny), then normalise
+      float mx = 0.f;
+      for (int i = lane; i < n; i += 32) mx = fmaxf(mx, fabsf(z[i].x));
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      int ex = 0;
+      frexpf(mx, &ex);
+      const float p2 = ldexpf(1.f, -ex);
+      dfl nrm = df_f(0.f);
+      for (int i = lane; i < n; i += 32) {
+        const dfl zi = df_mul_f(dload(z[i]), p2);
+        z[i] = dpack(zi);
+        nrm = df_add(nrm, df_mul(zi, zi));
+      }
+      nrm = df_warp_sum(nrm);
+      const dfl inv = nrm.hi > 0.f ? df_div(df_f(1.f), df_sqrt(nrm)) : df_f(0.f);
+      for (int i = lane; i < n; i += 32) z[i] = dpack(df_mul(dload(z[i]), inv));
+      __syncwarp();
+    }
+    for (int i = lane; i < n; i += 32) Z[(size_t)j * n + i] = z[i];
+    __syncwarp();
   }
 }
 
-// V[j] = Q_H z_j = H_0 (H_1 (... H_{n-2} z_j)), one CTA per eigenvector, complex128 rows of length n
-__global__ void __launch_bounds__(TD_THREADS) td_backxform_kernel(int n, int r, const double2* __restrict__ refl,
-                                                                 const double2* __restrict__ tau,
-                                                                 const double* __restrict__ Z,
-                                                                 double2* __restrict__ V) {
-  extern __shared__ double2 u[];
-  __shared__ double red[TD_THREADS / 32];
-  const int j = blockIdx.x;
-  if (j >= r) return;
-  for (int i = threadIdx.x; i < n; i += TD_THREADS) u[i] = make_double2(Z[(size_t)j * n + i], 0.0);
-  __syncthreads();
+// V[j] = Q_H z_j = H_0 (H_1 (... H_{n-2} z_j)), one warp per eigenvector (shuffle reductions,
+// no block barriers), the vector in shared memory; written as complex128 rows of length n.
+__global__ void td_backxform_kernel(int n, int r, const float4* __restrict__ refl, const float4* __restrict__ tau,
+                                    const float2* __restrict__ Z, double2* __restrict__ V) {
+  extern __shared__ float4 usm[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (j >= r) return;  // whole warps leave
+  float4* u = usm + (size_t)wib * n;
+  for (int i = lane; i < n; i += 32) {
+    const float2 zi = Z[(size_t)j * n + i];
+    u[i] = make_float4(zi.x, zi.y, 0.f, 0.f);
+  }
+  __syncwarp();
   for (int k = n - 2; k >= 0; --k) {
     const int m = n - k - 1;
-    const double2 tk = tau[k];
-    if (tk.x == 0.0 && tk.y == 0.0) continue;
-    const double2* vk = refl + (size_t)k * n;
-    double sx = 0.0, sy = 0.0;
-    for (int i = threadIdx.x; i < m; i += TD_THREADS) {
-      const double2 vi = vk[i], ui = u[k + 1 + i];
-      sx += vi.x * ui.x + vi.y * ui.y;  // conj(v) u
-      sy += vi.x * ui.y - vi.y * ui.x;
-    }
-    sx = block_sum_bcast(sx, red);
-    sy = block_sum_bcast(sy, red);
-    const double2 ts = zmul(tk, make_double2(sx, sy));
-    for (int i = threadIdx.x; i < m; i += TD_THREADS) {
-      const double2 vi = vk[i];
-      double2 ui = u[k + 1 + i];
-      ui.x -= ts.x * vi.x - ts.y * vi.y;
-      ui.y -= ts.x * vi.y + ts.y * vi.x;
-      u[k + 1 + i] = ui;
-    }
-    __syncthreads();
+    const cdf tk = ld4(&tau[k]);
+    if (tk.re.hi == 0.f && tk.im.hi == 0.f) continue;
+    const float4* vk = refl + (size_t)k * n;
+    cdf s = c_zero();
+    for (int i = lane; i < m; i += 32) s = c_add(s, c_mulc(ld4(&vk[i]), ld4(&u[k + 1 + i])));
+    const cdf ts = c_mul(tk, c_warp_sum(s));
+    for (int i = lane; i < m; i += 32) st4(&u[k + 1 + i], c_sub(ld4(&u[k + 1 + i]), c_mul(ts, ld4(&vk[i]))));
+    __syncwarp();
   }
-  for (int i = threadIdx.x; i < n; i += TD_THREADS) V[(size_t)j * n + i] = u[i];
+  for (int i = lane; i < n; i += 32) V[(size_t)j * n + i] = c_to(ld4(&u[i]));
 }
 
 // J = trace(G) - sum of the top r eigenvalues (the tail energy of Eq. 1); trace in FP64
@@ -412,11 +441,6 @@ __global__ void td_tail_kernel(int n, int r, const double2* __restrict__ G, cons
   if (threadIdx.x == 0) *J = fmax(red[0], 0.0);
 }
 
-__global__ void td_copy_kernel(long long nn, const double2* __restrict__ in, double2* __restrict__ out) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x)
-    out[i] = in[i];
-}
-
 hicu_status run_principal(hicu_handle* h, int64_t n64, int64_t r64, const double* Gd, double* Vout,
                           double* eig_top, double* eig_all, double* J, cudaStream_t st) {
   if (n64 < 2 || n64 > 4096) return set_error(h, HICU_ERR_SHAPE, "principal subspace: n must be in [2, 4096]");
@@ -425,35 +449,36 @@ hicu_status run_principal(hicu_handle* h, int64_t n64, int64_t r64, const double
   const long long nn = (long long)n * n;
   const double2* G = (const double2*)Gd;
   hicu_status s = HICU_OK;
-  double2* A = (double2*)ws_get(h, WS_EIG_A0, sizeof(double2) * nn, &s);
+  float4* A = (float4*)ws_get(h, WS_EIG_A0, sizeof(float4) * nn, &s);
   if (s) return s;
-  double2* refl = (double2*)ws_get(h, WS_EIG_A1, sizeof(double2) * nn, &s);
+  float4* refl = (float4*)ws_get(h, WS_EIG_A1, sizeof(float4) * nn, &s);
   if (s) return s;
-  // small vectors: d, e, info(8), scale/amax(2), tau, w, part, lam (n), Z (r n), LU work (5 r n)
+  // float4 units: tau (n), w (2n), part (2 nsm); float2 units: d, e, e2, lam (n each), info (4),
+  // Z (r n); then amax bits and the scale (8 bytes each)
   const size_t nsm = (size_t)std::max(1, h->num_sms);
-  const size_t small = (size_t)n * 2 + 16 + 2 * (size_t)n * 2 + nsm * 2 + (size_t)n;
-  double* buf = (double*)ws_get(h, WS_EIG_V, sizeof(double) * (small + 6 * (size_t)r * n), &s);
+  const size_t f4 = (size_t)n + 2 * (size_t)n + 2 * nsm;
+  const size_t f2 = 4 * (size_t)n + 4 + (size_t)r * n;
+  unsigned char* buf = (unsigned char*)ws_get(h, WS_EIG_V, 16 * f4 + 8 * f2 + 16, &s);
   if (s) return s;
-  double* d = buf;
-  double* e = d + n;
-  double* info = e + n;          // 8
-  unsigned long long* amax_bits = (unsigned long long*)(info + 8);
-  double* scale = info + 9;
-  double2* tau = (double2*)(info + 16);
-  double2* w = tau + n;
-  double2* part = w + n;
-  double* lam = (double*)(part + nsm);
-  double* Z = lam + n;
-  double* work = Z + (size_t)r * n;
+  float4* tau = (float4*)buf;
+  float4* w = tau + n;
+  float4* part = w + 2 * n;
+  float2* d = (float2*)(part + 2 * nsm);
+  float2* e = d + n;
+  float2* e2 = e + n;
+  float2* lam = e2 + n;
+  float2* info = lam + n;
+  float2* Z = info + 4;
+  unsigned long long* amax_bits = (unsigned long long*)(Z + (size_t)r * n);
+  double* scale = (double*)(amax_bits + 1);
 
-  // scaled copy of G
+  // scaled double-float copy of G
   const int eb = (int)std::min<long long>((nn + 255) / 256, (long long)h->num_sms * 8);
   cudaMemsetAsync(amax_bits, 0, sizeof(unsigned long long), st);
-  HICU_LAUNCH(h, K_EIG, st, td_copy_kernel<<<eb, 256, 0, st>>>(nn, G, A));
-  HICU_LAUNCH(h, K_EIG, st, eig_absmax_kernel<<<eb, 256, 0, st>>>(nn, A, amax_bits));
-  HICU_LAUNCH(h, K_EIG, st, eig_scale_kernel<<<eb, 256, 0, st>>>(nn, A, amax_bits, scale));
+  HICU_LAUNCH(h, K_EIG, st, eig_absmax_kernel<<<eb, 256, 0, st>>>(nn, G, amax_bits));
+  HICU_LAUNCH(h, K_EIG, st, td_prep_kernel<<<eb, 256, 0, st>>>(nn, G, amax_bits, scale, A));
 
-  // 1. tridiagonalisation (cooperative)
+  // 1. tridiagonalisation (cooperative, one CTA per SM)
   TdArgs a;
   a.n = n;
   a.A = A;
@@ -463,17 +488,16 @@ hicu_status run_principal(hicu_handle* h, int64_t n64, int64_t r64, const double
   a.tau = tau;
   a.w = w;
   a.part = part;
-  const size_t smem = sizeof(double2) * 2 * (size_t)n;
-  int grid = std::min(h->num_sms, std::max(1, (n + 3) / 4));
+  const size_t smem = sizeof(float4) * 3 * (size_t)n;
+  int grid = h->num_sms;
   {
-    static_assert(TD_THREADS == 256, "");
     cudaError_t e0 = allow_max_dynamic_smem((const void*)tridiag_kernel);
     if (e0 != cudaSuccess) return cuda_error(h, e0, "tridiag smem");
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_kernel, TD_THREADS, smem) != cudaSuccess ||
         per_sm < 1)
       return set_error(h, HICU_ERR_CUDA, "principal subspace: occupancy query failed");
-    grid = std::min(grid, h->num_sms * per_sm);
+    grid = std::max(1, std::min(grid, h->num_sms * per_sm));
   }
   a.gs.count = h->dev_sync;
   a.gs.gen = h->dev_sync + 1;
@@ -489,39 +513,37 @@ hicu_status run_principal(hicu_handle* h, int64_t n64, int64_t r64, const double
     if (ce == cudaSuccess) ce = cudaStreamWaitEvent(h->coop_st, h->coop_in, 0);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(h->dev_sync, 0, 2 * sizeof(unsigned), h->coop_st);
     if (ce == cudaSuccess)
-      HICU_LAUNCH(h, K_EIG, h->coop_st,
+      HICU_LAUNCH(h, K_TRIDIAG, h->coop_st,
                   ce = cudaLaunchCooperativeKernel((const void*)tridiag_kernel, dim3(grid), dim3(TD_THREADS), args,
                                                    smem, h->coop_st));
     if (ce == cudaSuccess) ce = cudaEventRecord(h->coop_out, h->coop_st);
     if (ce == cudaSuccess) ce = cudaStreamWaitEvent(st, h->coop_out, 0);
   } else {
-    HICU_LAUNCH(h, K_EIG, st,
+    HICU_LAUNCH(h, K_TRIDIAG, st,
                 ce = cudaLaunchCooperativeKernel((const void*)tridiag_kernel, dim3(grid), dim3(TD_THREADS), args,
                                                  smem, st));
   }
   if (ce != cudaSuccess) return cuda_error(h, ce, "principal subspace: tridiagonalisation launch");
 
   // 2. eigenvalues (top r; all n when requested)
-  HICU_LAUNCH(h, K_EIG, st, td_bounds_kernel<<<1, 256, 0, st>>>(n, d, e, info));
-  {
-    const int thr = 64;
-    const int blocks = (r * BS_LANES + thr - 1) / thr;
-    HICU_LAUNCH(h, K_EIG, st,
-                td_bisect_kernel<<<blocks, thr, 0, st>>>(n, n - r, r, d, e, info, scale, lam, eig_top));
-    if (eig_all) {
-      const int ball = (n * BS_LANES + thr - 1) / thr;
-      HICU_LAUNCH(h, K_EIG, st,
-                  td_bisect_kernel<<<ball, thr, 0, st>>>(n, 0, n, d, e, info, scale, nullptr, eig_all));
-    }
-  }
+  HICU_LAUNCH(h, K_EIG, st, td_bounds_kernel<<<1, 256, 0, st>>>(n, d, e, e2, info));
+  HICU_LAUNCH(h, K_EIG, st, td_bisect_kernel<<<r, 32, 0, st>>>(n, n - r, d, e2, info, scale, lam, eig_top));
+  if (eig_all)
+    HICU_LAUNCH(h, K_EIG, st, td_bisect_kernel<<<n, 32, 0, st>>>(n, 0, d, e2, info, scale, nullptr, eig_all));
   // 3. eigenvectors of T, 4. back-transformation
-  HICU_LAUNCH(h, K_EIG, st, td_inviter_kernel<<<(r + 31) / 32, 32, 0, st>>>(n, r, d, e, lam, info, work, Z));
   {
-    const size_t usm = sizeof(double2) * (size_t)n;
+    const size_t ism = sizeof(float2) * 6 * (size_t)n;
+    cudaError_t e0 = allow_max_dynamic_smem((const void*)td_inviter_kernel);
+    if (e0 != cudaSuccess) return cuda_error(h, e0, "inverse iteration smem");
+    HICU_LAUNCH(h, K_EIG, st, td_inviter_kernel<<<r, 32, ism, st>>>(n, r, d, e, lam, info, Z));
+  }
+  {
+    const int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (200 * 1024) / (sizeof(float4) * (size_t)n)));
+    const size_t usm = sizeof(float4) * (size_t)n * wpb;
     cudaError_t e0 = allow_max_dynamic_smem((const void*)td_backxform_kernel);
     if (e0 != cudaSuccess) return cuda_error(h, e0, "backxform smem");
     HICU_LAUNCH(h, K_EIG, st,
-                td_backxform_kernel<<<r, TD_THREADS, usm, st>>>(n, r, refl, tau, Z, (double2*)Vout));
+                td_backxform_kernel<<<(r + wpb - 1) / wpb, 32 * wpb, usm, st>>>(n, r, refl, tau, Z, (double2*)Vout));
   }
   if (J) HICU_LAUNCH(h, K_MISC, st, td_tail_kernel<<<1, 256, 0, st>>>(n, r, G, eig_top, J));
   return cuda_error(h, cudaGetLastError(), "principal subspace");

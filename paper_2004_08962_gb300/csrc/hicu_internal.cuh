@@ -223,7 +223,7 @@ static_assert(WS_COUNT <= hicu_handle::kSlots, "workspace slots");
 
 // Kernel classes for launch accounting / event timing (hicu_kernel_class in hicu.h).
 enum KClass { K_GRAM = 0, K_EIG = 1, K_CONV = 2, K_ADJOINT = 3, K_JL = 4, K_MISC = 5, K_CONV_TC = 6,
-              K_ADJOINT_TC = 7 };
+              K_ADJOINT_TC = 7, K_TRIDIAG = 8 };
 void prof_begin(hicu_handle* h, int cls, cudaStream_t st);
 void prof_end(hicu_handle* h, int cls, cudaStream_t st);
 

@@ -31,7 +31,7 @@ EXPORTED = (
 )
 
 HICU_K_GRAM, HICU_K_EIG, HICU_K_CONV, HICU_K_ADJOINT, HICU_K_JL, HICU_K_MISC = 0, 1, 2, 3, 4, 5
-HICU_K_CONV_TC, HICU_K_ADJOINT_TC = 6, 7
+HICU_K_CONV_TC, HICU_K_ADJOINT_TC, HICU_K_TRIDIAG = 6, 7, 8
 
 
 class hicu_geom(ctypes.Structure):

@@ -1,10 +1,11 @@
 """Principal subspace by Householder tridiagonalisation (hicu_principal_subspace) and the
 complement form of the JL filters, against LAPACK's eigh in the FP64 oracle.
 
-Bounds: eigenvalues to 1e-13 lambda_max (bisection to 2 eps ||T|| on a backward-stable
-tridiagonal form); span of the r principal vectors to 1e-13 lambda_max / gap (Davis-Kahan
-with a backward error of a few hundred eps ||G||); orthonormality 1e-11; J of Eq. 1 (tail
-energy) to 1e-12 lambda_max n.
+The solver computes in double-float (FP32 pairs, unit roundoff u = 2^-48 ~ 3.6e-15, a few u per
+operation).  Bounds: eigenvalues to 2e-12 lambda_max (bisection to 2^-46 ||T|| on a
+backward-stable tridiagonal form whose backward error grows like sqrt(n) u ||G||); span of the r
+principal vectors to 2e-12 lambda_max / gap (Davis-Kahan with that backward error);
+orthonormality 1e-11; J of Eq. 1 (tail energy) to 1e-11 lambda_max n.
 """
 import numpy as np
 import pytest
@@ -29,7 +30,7 @@ def cuda(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def _check(H, G, r, span_tol=1e-13):
+def _check(H, G, r, span_tol=2e-12):
     from paper_2004_08962_gb300 import hicu
     n = G.shape[0]
     V, top, allv, tail = hicu.hicu_principal_subspace(H, cuda(G), r, want_all=True, want_tail=True)
@@ -38,15 +39,15 @@ def _check(H, G, r, span_tol=1e-13):
     top, allv, tail = top.cpu().numpy(), allv.cpu().numpy(), tail.item()
     w, U = np.linalg.eigh(G)
     lmax = max(abs(w[0]), abs(w[-1]))
-    assert np.max(np.abs(allv - w)) < 1e-13 * lmax
-    assert np.max(np.abs(top - w[n - r:])) < 1e-13 * lmax
+    assert np.max(np.abs(allv - w)) < 2e-12 * lmax
+    assert np.max(np.abs(top - w[n - r:])) < 2e-12 * lmax
     np.testing.assert_allclose(V.conj().T @ V, np.eye(r), atol=1e-11)
     gap = w[n - r] - w[n - r - 1]
     Uo = U[:, n - r:]
     dist = np.linalg.norm(V @ V.conj().T - Uo @ Uo.conj().T, 2)
     assert dist < span_tol * lmax / max(gap, 1e-300) + 1e-12, (dist, gap / lmax)
     J = w[: n - r].sum()
-    assert abs(tail - max(J, 0.0)) < 1e-12 * lmax * n
+    assert abs(tail - max(J, 0.0)) < 1e-11 * lmax * n
     return V
 
 
