@@ -194,6 +194,64 @@ def filter_gradient(x: np.ndarray, geom: Geom, reg: Region, Rbar: np.ndarray) ->
     return F
 
 
+def conv_null_at(x: np.ndarray, geom: Geom, reg: Region, filters: np.ndarray, outs: np.ndarray) -> np.ndarray:
+    """R[o, k] = H(x) q_k at chosen valid outputs only (Theory: row o of H(x) is the patch
+    [x_c[o + d]] over (c, d)); for sampled checks of volumes too large to convolve here.
+
+    outs: int array (m, 3) of (oz, oy, ox) indices into the valid-output grid out_shape(geom, reg).
+    Returns (m, p).
+    """
+    _check(x, geom, reg)
+    x = np.asarray(x, dtype=np.complex128)
+    f = np.asarray(filters, dtype=np.complex128)
+    outs = np.asarray(outs, dtype=np.int64).reshape(-1, 3)
+    kx, ky, kz = geom.kernel
+    idx = []
+    for a, (col, k) in enumerate(((2, kx), (1, ky), (0, kz))):   # axis a = x, y, z
+        rel = outs[:, col][:, None] + np.arange(k)[None, :]
+        if geom.circular[a]:
+            rel = rel % reg.ext[a]
+        idx.append(reg.off[a] + rel)                               # (m, k_a)
+    ix, iy, iz = idx
+    patch = x[:, iz[:, :, None, None], iy[:, None, :, None], ix[:, None, None, :]]   # (C, m, kz, ky, kx)
+    return np.einsum("cmzyx,kczyx->mk", patch, f)
+
+
+def gradient_at(x: np.ndarray, geom: Geom, reg: Region, filters: np.ndarray, us: np.ndarray,
+                mask: Optional[np.ndarray] = None) -> np.ndarray:
+    """The descent direction g = (1 - M) o sum_k H^H(H(x) q_k) at chosen positions u of region S.
+
+    g_c[u] = sum_k sum_d conj(q_k[c, d]) R[u - d, k] over the offsets d for which u - d is a
+    valid output (taken modulo the extent on a circular axis), R = H(x) q from conv_null_at;
+    times (1 - M[u]) (hard data consistency, end of the Theory section).
+    us: int array (m, 3) of (uz, uy, ux) in region coordinates.  Returns (C, m).
+    """
+    f = np.asarray(filters, dtype=np.complex128)
+    us = np.asarray(us, dtype=np.int64).reshape(-1, 3)
+    kx, ky, kz = geom.kernel
+    sz, sy, sx = out_shape(geom, reg)
+    lim = (sz, sy, sx)
+    g = np.zeros((geom.ncoil, len(us)), dtype=np.complex128)
+    for dz, dy, dx in _offsets(geom):
+        o = us - np.array([dz, dy, dx])[None, :]
+        ok = np.ones(len(us), dtype=bool)
+        for col, a in ((0, 2), (1, 1), (2, 0)):
+            if geom.circular[a]:
+                o[:, col] %= reg.ext[a]
+            else:
+                ok &= (o[:, col] >= 0) & (o[:, col] < lim[col])
+        if not ok.any():
+            continue
+        R = conv_null_at(x, geom, reg, f, o[ok])                   # (m_ok, p)
+        g[:, ok] += np.einsum("mk,kc->cm", R, np.conj(f[:, :, dz, dy, dx]))
+    if mask is not None:
+        m = np.asarray(mask)
+        m4 = m if m.ndim == 4 else m[None]
+        mv = m4[:, reg.off[2] + us[:, 0], reg.off[1] + us[:, 1], reg.off[0] + us[:, 2]]
+        g = g * (1 - mv.astype(np.float64))
+    return g
+
+
 def project_unobserved(x: np.ndarray, geom: Geom, reg: Region, mask: Optional[np.ndarray]) -> np.ndarray:
     """(1 - M) o x on the region S and 0 outside it (hard data consistency, Theory section)."""
     x = np.asarray(x, dtype=np.complex128)

@@ -220,6 +220,33 @@ def test_adjoint_matches_brute_force(i):
 
 
 @pytest.mark.parametrize("i", range(len(SMALL_CASES)))
+def test_sampled_conv_and_gradient_match_brute_force(i):
+    """conv_null_at / gradient_at (the sampled forms used at full workload sizes) against the
+    brute-force Hankel rows and the brute-force adjoint operators, at every position."""
+    geom, reg, x, rng = make_case(i)
+    p = 3
+    f = rand_filters(rng, geom, p)
+    Hb = brute_hankel(x, geom, reg)
+    sz, sy, sx = O.out_shape(geom, reg)
+    outs = np.stack(np.meshgrid(np.arange(sz), np.arange(sy), np.arange(sx), indexing="ij"), -1).reshape(-1, 3)
+    np.testing.assert_allclose(O.conv_null_at(x, geom, reg, f, outs), Hb @ f.reshape(p, -1).T,
+                               rtol=1e-13, atol=1e-13)
+    s = O.num_outputs(geom, reg)
+    mask = (rng.random(x.shape[1:]) < 0.4).astype(np.uint8)
+    ref = np.zeros(x.size, dtype=np.complex128)
+    for k in range(p):
+        T = brute_conv_operator(f[k].ravel(), geom, reg)
+        ref += T.conj().T @ (Hb @ f[k].ravel())
+    ref = (ref.reshape(x.shape) * (1 - mask[None]))
+    ez, ey, ex = reg.ext[2], reg.ext[1], reg.ext[0]
+    us = np.stack(np.meshgrid(np.arange(ez), np.arange(ey), np.arange(ex), indexing="ij"), -1).reshape(-1, 3)
+    g = O.gradient_at(x, geom, reg, f, us, mask)
+    want = ref[:, reg.off[2] + us[:, 0], reg.off[1] + us[:, 1], reg.off[0] + us[:, 2]]
+    np.testing.assert_allclose(g, want, rtol=1e-12, atol=1e-12)
+    assert s == len(outs)
+
+
+@pytest.mark.parametrize("i", range(len(SMALL_CASES)))
 def test_adjoint_identity(i):
     geom, reg, x, rng = make_case(i)
     f = rand_filters(rng, geom, 4)
