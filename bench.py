@@ -47,6 +47,9 @@ UNIT = "GD-iters/s"
 KERNEL_NAMES = {0: "gram", 1: "eig", 2: "conv_fp32", 3: "adjoint_fp32", 4: "jl", 5: "misc",
                 6: "conv_tc", 7: "adjoint_tc", 8: "tridiag"}
 FP64_PEAK_TFLOPS = 1.25  # FP64 FMA-chain probe on this GB300, equal to the nominal rate
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of the same
+# kernel on the same workload (profiles/); a kernel changed since its capture has no entry.
+NCU_TRAFFIC = {("2d_brain_256", "tridiag_kernel"): 696064 + 53504}
 
 
 def load_peaks():
@@ -670,9 +673,11 @@ def main():
     elif dominant in (1, 8) and flops_recon > 0:
         per_launch = flops_recon * args.steps / max(dom_launches, 1)
         achieved = per_launch / avg_launch_s / 1e12
-        roof = {"kernel": "tridiag_kernel" if dominant == 8 else KERNEL_NAMES[dominant], "bound": "alu",
+        kname = "tridiag_kernel" if dominant == 8 else KERNEL_NAMES[dominant]
+        roof = {"kernel": kname, "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get((wname, kname)),
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "work": "16 n^3 / 3 real FP64 flops per n x n Hermitian tridiagonalisation" if dominant == 8
                         else "8 n^2 r FP64 flops per back-transformation",
                 "peak_source": "FP64 FMA-chain probe on this GB300 (1.25 TFLOP/s, equal to the nominal rate)",
