@@ -22,10 +22,16 @@
 // pre-scaled by an exact power of two (largest entry O(1)); inputs and outputs are FP64.
 // Accuracy: eigenvalues to ~1e-14 ||G|| (absolute), span(V) to ~1e-14 ||G|| / gap (the
 // Davis-Kahan bound of a backward-stable method at this precision).
+#include <cooperative_groups.h>
+
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 
 #include "df.cuh"
 #include "hicu_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace hicu {
 
@@ -169,6 +175,212 @@ __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
     __syncthreads();
   }
   if (c == 0 && tid == 0) a.d[n - 1] = dpack(ld4(&x[0]).re);
+}
+
+// ---------------------------------------------------------------- one-cluster form (n <= 440)
+//
+// The same steps inside one thread-block cluster of TDC_CTAS CTAs: global row g lives in the
+// shared memory of CTA g mod TDC_CTAS (local row g / TDC_CTAS) for the whole run, w0 and the
+// partial sums stay in their producers' shared memory and are read through distributed shared
+// memory, and a step ends at the hardware cluster barrier (~0.5 us) instead of a grid barrier
+// and L2 round trips.  As in the grid form, the pivot row k+1 is never written during step k:
+// every CTA forms it from the owner's stored row (read remotely) and v, w.
+
+constexpr int TDC_CTAS = 16;
+constexpr int TDC_THREADS = 512;
+constexpr int TDC_MAX_N = 440;
+
+struct TdcArgs {
+  int n;
+  const float4* A;  // n x n scaled double-float copy of G
+  float2* d;
+  float2* e;
+  float4* refl;
+  float4* tau;
+};
+
+// CTA sum of a complex double-float: warp shuffles, then warp 0 over the warp partials
+__device__ inline cdf block_sum_c2(cdf a, float4* sh, float4* out) {
+  a = c_warp_sum(a);
+  const int wi = threadIdx.x >> 5, l = threadIdx.x & 31, nwp = blockDim.x >> 5;
+  if (l == 0) st4(&sh[wi], a);
+  __syncthreads();
+  if (wi == 0) {
+    cdf t = l < nwp ? ld4(&sh[l]) : c_zero();
+    t = c_warp_sum(t);
+    if (l == 0) st4(out, t);
+  }
+  __syncthreads();
+  return ld4(out);
+}
+
+__global__ void __launch_bounds__(TDC_THREADS, 1) tridiag_cluster_kernel(const TdcArgs a) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int crank = (int)cl.block_rank(), nct = (int)cl.num_blocks();
+  const int n = a.n;
+  const int R = (n + nct - 1) / nct;
+  extern __shared__ float4 csm[];
+  float4* rows = csm;             // [R][n]
+  float4* x = rows + (size_t)R * n;  // [n] pivot row
+  float4* v = x + n;              // [n]
+  float4* w = v + n;              // [n]
+  float4* w0loc = w + n;          // [2][R] w0 of own rows, by step parity
+  float4* partloc = w0loc + 2 * R;  // [2] partial sums w0^H v, by step parity
+  float4* bsum = partloc + 2;     // [1] block-sum result
+  __shared__ float4 red[TDC_THREADS / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = TDC_THREADS / 32;
+  for (int idx = tid; idx < R * n; idx += TDC_THREADS) {
+    const int lr = idx / n, j = idx - lr * n;
+    const int g = lr * nct + crank;
+    if (g < n) rows[idx] = a.A[(size_t)g * n + j];
+  }
+  cl.sync();
+  {
+    const float4* r0 = cl.map_shared_rank(rows, 0);
+    for (int j = tid; j < n; j += TDC_THREADS) x[j] = r0[j];
+  }
+  __syncthreads();
+  for (int k = 0; k < n - 1; ++k) {
+    const int m = n - k - 1;
+    const int par = k & 1;
+    // --- Householder vector of column k (every CTA)
+    cdf s2 = c_zero();
+    for (int j = 1 + tid; j < m; j += TDC_THREADS) {
+      const cdf xj = ld4(&x[1 + j]);
+      s2.re = df_add(s2.re, df_add(df_mul(xj.re, xj.re), df_mul(xj.im, xj.im)));
+    }
+    const dfl xn2 = block_sum_c2(s2, red, bsum).re;
+    const cdf x0 = c_conj(ld4(&x[1]));
+    cdf tau = c_zero(), scale = c_zero();
+    dfl beta = x0.re;
+    if (!(xn2.hi == 0.f && x0.im.hi == 0.f)) {
+      const dfl nrm = df_sqrt(df_add(df_add(df_mul(x0.re, x0.re), df_mul(x0.im, x0.im)), xn2));
+      beta = x0.re.hi >= 0.f ? df_neg(nrm) : nrm;
+      tau.re = df_div(df_sub(beta, x0.re), beta);
+      tau.im = df_div(df_neg(x0.im), beta);
+      const cdf den = {df_sub(x0.re, beta), x0.im};
+      const dfl dd = df_add(df_mul(den.re, den.re), df_mul(den.im, den.im));
+      scale.re = df_div(den.re, dd);
+      scale.im = df_div(df_neg(den.im), dd);
+    }
+    const bool active = !(tau.re.hi == 0.f && tau.im.hi == 0.f);
+    if (crank == 0 && tid == 0) {
+      a.d[k] = dpack(ld4(&x[0]).re);
+      a.e[k] = dpack(beta);
+      st4(&a.tau[k], tau);
+    }
+    for (int j = tid; j < m; j += TDC_THREADS) {
+      cdf vj;
+      if (j == 0) vj = {{1.f, 0.f}, {0.f, 0.f}};
+      else vj = active ? c_mul(c_conj(ld4(&x[1 + j])), scale) : c_zero();
+      st4(&v[j], vj);
+      if (crank == 0) st4(&a.refl[(long long)k * n + j], vj);
+    }
+    __syncthreads();
+    // --- own trailing rows: global g = k+1 .. n-1 with g % nct == crank, local lr = g / nct
+    const int lr0 = (k + 1 - crank + nct - 1) / nct;  // first own local row with g >= k+1
+    const int nown = lr0 < R ? R - lr0 - ((R - 1) * nct + crank >= n ? 1 : 0) : 0;
+    cdf pp = c_zero();
+    if (active) {
+      for (int q = warp; q < nown; q += nw) {
+        const int lr = lr0 + q, g = lr * nct + crank, i = g - (k + 1);
+        const float4* row = rows + (size_t)lr * n + (k + 1);
+        cdf y = c_zero();
+        for (int j = lane; j < m; j += 32) y = c_add(y, c_mul(ld4(&row[j]), ld4(&v[j])));
+        y = c_warp_sum(y);
+        if (lane == 0) {
+          const cdf w0 = c_mul(tau, y);
+          st4(&w0loc[par * R + lr], w0);
+          pp = c_add(pp, c_mulc(w0, ld4(&v[i])));
+        }
+      }
+    }
+    {
+      const cdf ps = block_sum_c2(pp, red, bsum);
+      if (tid == 0) st4(&partloc[par], ps);
+    }
+    cl.sync();
+    // --- alpha, w (all m), rank-2 update of the own rows but row k+1, next pivot row
+    const int owner1 = (k + 1) % nct;
+    const float4* prow = cl.map_shared_rank(rows, owner1) + (size_t)((k + 1) / nct) * n + (k + 1);
+    if (active) {
+      cdf sp = c_zero();
+      if (tid < nct) sp = ld4(cl.map_shared_rank(partloc, tid) + par);
+      const cdf ssum = block_sum_c2(sp, red, bsum);
+      const cdf htau = {df_mul_f(tau.re, -0.5f), df_mul_f(tau.im, -0.5f)};
+      const cdf alpha = c_mul(htau, ssum);
+      for (int j = tid; j < m; j += TDC_THREADS) {
+        const int g = k + 1 + j;
+        const cdf w0 = ld4(cl.map_shared_rank(w0loc, g % nct) + par * R + g / nct);
+        st4(&w[j], c_add(w0, c_mul(alpha, ld4(&v[j]))));
+      }
+      __syncthreads();
+      for (int idx = tid; idx < nown * m; idx += TDC_THREADS) {
+        const int q = idx / m, j = idx - q * m;
+        const int lr = lr0 + q, g = lr * nct + crank, i = g - (k + 1);
+        if (i == 0) continue;
+        float4* aij = rows + (size_t)lr * n + (k + 1) + j;
+        const cdf t = c_add(c_mul(ld4(&v[i]), c_conj(ld4(&w[j]))), c_mul(ld4(&w[i]), c_conj(ld4(&v[j]))));
+        st4(aij, c_sub(ld4(aij), t));
+      }
+    }
+    {
+      const cdf w0c = active ? ld4(&w[0]) : c_zero();
+      for (int j = tid; j < m; j += TDC_THREADS) {
+        cdf aij = ld4(&prow[j]);
+        if (active) aij = c_sub(aij, c_add(c_conj(ld4(&w[j])), c_mul(w0c, c_conj(ld4(&v[j])))));
+        st4(&x[j], aij);
+      }
+    }
+    __syncthreads();
+  }
+  if (crank == 0 && tid == 0) a.d[n - 1] = dpack(ld4(&x[0]).re);
+  cl.sync();  // no CTA leaves while others may still read its shared memory
+}
+
+static size_t tdc_smem(int n) {
+  const int R = (n + TDC_CTAS - 1) / TDC_CTAS;
+  return sizeof(float4) * ((size_t)R * n + 3 * (size_t)n + 2 * (size_t)R + 3);
+}
+
+static cudaLaunchConfig_t tdc_cfg(size_t smem, cudaStream_t st, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = TDC_CTAS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(TDC_CTAS);
+  cfg.blockDim = dim3(TDC_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// whether this device runs the one-cluster form for n (cached per n; host threads of a batch
+// share it)
+static bool tdc_available(int n) {
+  if (n < 2 || n > TDC_MAX_N) return false;
+  static std::atomic<int> cached[TDC_MAX_N + 1];
+  static std::mutex mu;
+  const int known = cached[n].load();
+  if (known) return known > 0;
+  std::lock_guard<std::mutex> lock(mu);
+  int ok = -1;
+  const size_t smem = tdc_smem(n);
+  if (cudaFuncSetAttribute(tridiag_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+          cudaSuccess &&
+      allow_max_dynamic_smem((const void*)tridiag_cluster_kernel) == cudaSuccess) {
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = tdc_cfg(smem, 0, attr);
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, tridiag_cluster_kernel, &cfg) == cudaSuccess && clusters >= 1)
+      ok = 1;
+  }
+  cudaGetLastError();
+  cached[n].store(ok);
+  return ok > 0;
 }
 
 // A = 2^-e G in double-float (the largest |Re|, |Im| of G in [2^(e-1), 2^e)); scale = 2^-e
@@ -441,44 +653,8 @@ __global__ void td_tail_kernel(int n, int r, const double2* __restrict__ G, cons
   if (threadIdx.x == 0) *J = fmax(red[0], 0.0);
 }
 
-hicu_status run_principal(hicu_handle* h, int64_t n64, int64_t r64, const double* Gd, double* Vout,
-                          double* eig_top, double* eig_all, double* J, cudaStream_t st) {
-  if (n64 < 2 || n64 > 4096) return set_error(h, HICU_ERR_SHAPE, "principal subspace: n must be in [2, 4096]");
-  if (r64 <= 0 || r64 >= n64) return set_error(h, HICU_ERR_RANK, "principal subspace: rank must satisfy 0 < r < n");
-  const int n = (int)n64, r = (int)r64;
-  const long long nn = (long long)n * n;
-  const double2* G = (const double2*)Gd;
-  hicu_status s = HICU_OK;
-  float4* A = (float4*)ws_get(h, WS_EIG_A0, sizeof(float4) * nn, &s);
-  if (s) return s;
-  float4* refl = (float4*)ws_get(h, WS_EIG_A1, sizeof(float4) * nn, &s);
-  if (s) return s;
-  // float4 units: tau (n), w (2n), part (2 nsm); float2 units: d, e, e2, lam (n each), info (4),
-  // Z (r n); then amax bits and the scale (8 bytes each)
-  const size_t nsm = (size_t)std::max(1, h->num_sms);
-  const size_t f4 = (size_t)n + 2 * (size_t)n + 2 * nsm;
-  const size_t f2 = 4 * (size_t)n + 4 + (size_t)r * n;
-  unsigned char* buf = (unsigned char*)ws_get(h, WS_EIG_V, 16 * f4 + 8 * f2 + 16, &s);
-  if (s) return s;
-  float4* tau = (float4*)buf;
-  float4* w = tau + n;
-  float4* part = w + 2 * n;
-  float2* d = (float2*)(part + 2 * nsm);
-  float2* e = d + n;
-  float2* e2 = e + n;
-  float2* lam = e2 + n;
-  float2* info = lam + n;
-  float2* Z = info + 4;
-  unsigned long long* amax_bits = (unsigned long long*)(Z + (size_t)r * n);
-  double* scale = (double*)(amax_bits + 1);
-
-  // scaled double-float copy of G
-  const int eb = (int)std::min<long long>((nn + 255) / 256, (long long)h->num_sms * 8);
-  cudaMemsetAsync(amax_bits, 0, sizeof(unsigned long long), st);
-  HICU_LAUNCH(h, K_EIG, st, eig_absmax_kernel<<<eb, 256, 0, st>>>(nn, G, amax_bits));
-  HICU_LAUNCH(h, K_EIG, st, td_prep_kernel<<<eb, 256, 0, st>>>(nn, G, amax_bits, scale, A));
-
-  // 1. tridiagonalisation (cooperative, one CTA per SM)
+static hicu_status launch_tridiag_grid(hicu_handle* h, int n, float4* A, float2* d, float2* e, float4* refl,
+                                       float4* tau, float4* w, float4* part, cudaStream_t st) {
   TdArgs a;
   a.n = n;
   a.A = A;
@@ -524,7 +700,14 @@ hicu_status run_principal(hicu_handle* h, int64_t n64, int64_t r64, const double
                                                  smem, st));
   }
   if (ce != cudaSuccess) return cuda_error(h, ce, "principal subspace: tridiagonalisation launch");
+  return HICU_OK;
+}
 
+// steps 2-4 and J, after the tridiagonalisation
+static hicu_status finish_principal(hicu_handle* h, int n, int r, const double2* G, double* Vout, double* eig_top,
+                                    double* eig_all, double* J, float2* d, float2* e, float2* e2, float2* lam,
+                                    float2* info, float2* Z, float4* refl, float4* tau, double* scale,
+                                    cudaStream_t st) {
   // 2. eigenvalues (top r; all n when requested)
   HICU_LAUNCH(h, K_EIG, st, td_bounds_kernel<<<1, 256, 0, st>>>(n, d, e, e2, info));
   HICU_LAUNCH(h, K_EIG, st, td_bisect_kernel<<<r, 32, 0, st>>>(n, n - r, d, e2, info, scale, lam, eig_top));
@@ -538,7 +721,10 @@ hicu_status run_principal(hicu_handle* h, int64_t n64, int64_t r64, const double
     HICU_LAUNCH(h, K_EIG, st, td_inviter_kernel<<<r, 32, ism, st>>>(n, r, d, e, lam, info, Z));
   }
   {
-    const int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (200 * 1024) / (sizeof(float4) * (size_t)n)));
+    // one warp per eigenvector; several per CTA only when there are more vectors than SMs
+    const int wpb = (int)std::max<size_t>(
+        1, std::min<size_t>({(size_t)4, (size_t)r / (size_t)std::max(1, h->num_sms),
+                             (200 * 1024) / (sizeof(float4) * (size_t)n)}));
     const size_t usm = sizeof(float4) * (size_t)n * wpb;
     cudaError_t e0 = allow_max_dynamic_smem((const void*)td_backxform_kernel);
     if (e0 != cudaSuccess) return cuda_error(h, e0, "backxform smem");
@@ -547,6 +733,64 @@ hicu_status run_principal(hicu_handle* h, int64_t n64, int64_t r64, const double
   }
   if (J) HICU_LAUNCH(h, K_MISC, st, td_tail_kernel<<<1, 256, 0, st>>>(n, r, G, eig_top, J));
   return cuda_error(h, cudaGetLastError(), "principal subspace");
+}
+
+hicu_status run_principal(hicu_handle* h, int64_t n64, int64_t r64, const double* Gd, double* Vout,
+                          double* eig_top, double* eig_all, double* J, cudaStream_t st) {
+  if (n64 < 2 || n64 > 4096) return set_error(h, HICU_ERR_SHAPE, "principal subspace: n must be in [2, 4096]");
+  if (r64 <= 0 || r64 >= n64) return set_error(h, HICU_ERR_RANK, "principal subspace: rank must satisfy 0 < r < n");
+  const int n = (int)n64, r = (int)r64;
+  const long long nn = (long long)n * n;
+  const double2* G = (const double2*)Gd;
+  hicu_status s = HICU_OK;
+  float4* A = (float4*)ws_get(h, WS_EIG_A0, sizeof(float4) * nn, &s);
+  if (s) return s;
+  float4* refl = (float4*)ws_get(h, WS_EIG_A1, sizeof(float4) * nn, &s);
+  if (s) return s;
+  // float4 units: tau (n), w (2n), part (2 nsm); float2 units: d, e, e2, lam (n each), info (4),
+  // Z (r n); then amax bits and the scale (8 bytes each)
+  const size_t nsm = (size_t)std::max(1, h->num_sms);
+  const size_t f4 = (size_t)n + 2 * (size_t)n + 2 * nsm;
+  const size_t f2 = 4 * (size_t)n + 4 + (size_t)r * n;
+  unsigned char* buf = (unsigned char*)ws_get(h, WS_EIG_V, 16 * f4 + 8 * f2 + 16, &s);
+  if (s) return s;
+  float4* tau = (float4*)buf;
+  float4* w = tau + n;
+  float4* part = w + 2 * n;
+  float2* d = (float2*)(part + 2 * nsm);
+  float2* e = d + n;
+  float2* e2 = e + n;
+  float2* lam = e2 + n;
+  float2* info = lam + n;
+  float2* Z = info + 4;
+  unsigned long long* amax_bits = (unsigned long long*)(Z + (size_t)r * n);
+  double* scale = (double*)(amax_bits + 1);
+
+  // scaled double-float copy of G
+  const int eb = (int)std::min<long long>((nn + 255) / 256, (long long)h->num_sms * 8);
+  cudaMemsetAsync(amax_bits, 0, sizeof(unsigned long long), st);
+  HICU_LAUNCH(h, K_EIG, st, eig_absmax_kernel<<<eb, 256, 0, st>>>(nn, G, amax_bits));
+  HICU_LAUNCH(h, K_EIG, st, td_prep_kernel<<<eb, 256, 0, st>>>(nn, G, amax_bits, scale, A));
+
+  // 1. tridiagonalisation: one cluster for n <= 440, else cooperative over all SMs
+  if (tdc_available(n)) {
+    TdcArgs ca;
+    ca.n = n;
+    ca.A = A;
+    ca.d = d;
+    ca.e = e;
+    ca.refl = refl;
+    ca.tau = tau;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = tdc_cfg(tdc_smem(n), st, attr);
+    cudaError_t ce;
+    HICU_LAUNCH(h, K_TRIDIAG, st, ce = cudaLaunchKernelEx(&cfg, tridiag_cluster_kernel, ca));
+    if (ce != cudaSuccess) return cuda_error(h, ce, "principal subspace: cluster tridiagonalisation launch");
+  } else {
+    hicu_status s2 = launch_tridiag_grid(h, n, A, d, e, refl, tau, w, part, st);
+    if (s2) return s2;
+  }
+  return finish_principal(h, n, r, G, Vout, eig_top, eig_all, J, d, e, e2, lam, info, Z, refl, tau, scale, st);
 }
 
 }  // namespace hicu
