@@ -49,7 +49,7 @@ KERNEL_NAMES = {0: "gram", 1: "eig", 2: "conv_fp32", 3: "adjoint_fp32", 4: "jl",
 FP64_PEAK_TFLOPS = 1.25  # FP64 FMA-chain probe on this GB300, equal to the nominal rate
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of the same
 # kernel on the same workload (profiles/); a kernel changed since its capture has no entry.
-NCU_TRAFFIC = {("2d_brain_256", "tridiag_kernel"): 696064 + 53504}
+NCU_TRAFFIC = {}
 
 
 def load_peaks():
@@ -673,7 +673,10 @@ def main():
     elif dominant in (1, 8) and flops_recon > 0:
         per_launch = flops_recon * args.steps / max(dom_launches, 1)
         achieved = per_launch / avg_launch_s / 1e12
-        kname = "tridiag_kernel" if dominant == 8 else KERNEL_NAMES[dominant]
+        n_pb = pb.ncoil * pb.kernel[0] * pb.kernel[1] * pb.kernel[2]
+        # n <= 440 runs the one-cluster form of the tridiagonalisation, larger n the grid form
+        kname = (("tridiag_cluster_kernel" if n_pb <= 440 else "tridiag_kernel") if dominant == 8
+                 else KERNEL_NAMES[dominant])
         roof = {"kernel": kname, "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get((wname, kname)),

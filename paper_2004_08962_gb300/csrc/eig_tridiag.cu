@@ -16,7 +16,8 @@
 //  3. Eigenvectors of T for the r largest eigenvalues by inverse iteration with a
 //     pivoted tridiagonal LU; eigenvalues closer than 1e-10 ||T|| are solved one after
 //     the other and orthogonalised against each other (modified Gram-Schmidt).
-//  4. V = Q_H Z: the reflectors applied to each eigenvector, last one first.
+//  4. V = Q_H Z: the reflectors applied to each eigenvector in compact WY blocks of 32
+//     (I - Y T Y^H per block, Schreiber & Van Loan), last block first.
 // Arithmetic: double-float (df.cuh, ~2^-48), because FP64 on this GPU is both slow and of
 // long latency, and every stage here is a chain of dependent operations.  The input is
 // pre-scaled by an exact power of two (largest entry O(1)); inputs and outputs are FP64.
@@ -98,12 +99,14 @@ __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
     if (!(xn2.hi == 0.f && x0.im.hi == 0.f)) {
       const dfl nrm = df_sqrt(df_add(df_add(df_mul(x0.re, x0.re), df_mul(x0.im, x0.im)), xn2));
       beta = x0.re.hi >= 0.f ? df_neg(nrm) : nrm;
-      tau.re = df_div(df_sub(beta, x0.re), beta);
-      tau.im = df_div(df_neg(x0.im), beta);
+      const dfl rb = df_div(df_f(1.f), beta);
+      tau.re = df_sub(df_f(1.f), df_mul(x0.re, rb));  // (beta - x0.re) / beta
+      tau.im = df_neg(df_mul(x0.im, rb));
       const cdf den = {df_sub(x0.re, beta), x0.im};  // v = x / (x0 - beta)
       const dfl dd = df_add(df_mul(den.re, den.re), df_mul(den.im, den.im));
-      scale.re = df_div(den.re, dd);
-      scale.im = df_div(df_neg(den.im), dd);
+      const dfl rd = df_div(df_f(1.f), dd);
+      scale.re = df_mul(den.re, rd);
+      scale.im = df_neg(df_mul(den.im, rd));
     }
     const bool active = !(tau.re.hi == 0.f && tau.im.hi == 0.f);
     if (c == 0 && tid == 0) {
@@ -256,12 +259,14 @@ __global__ void __launch_bounds__(TDC_THREADS, 1) tridiag_cluster_kernel(const T
     if (!(xn2.hi == 0.f && x0.im.hi == 0.f)) {
       const dfl nrm = df_sqrt(df_add(df_add(df_mul(x0.re, x0.re), df_mul(x0.im, x0.im)), xn2));
       beta = x0.re.hi >= 0.f ? df_neg(nrm) : nrm;
-      tau.re = df_div(df_sub(beta, x0.re), beta);
-      tau.im = df_div(df_neg(x0.im), beta);
+      const dfl rb = df_div(df_f(1.f), beta);
+      tau.re = df_sub(df_f(1.f), df_mul(x0.re, rb));  // (beta - x0.re) / beta
+      tau.im = df_neg(df_mul(x0.im, rb));
       const cdf den = {df_sub(x0.re, beta), x0.im};
       const dfl dd = df_add(df_mul(den.re, den.re), df_mul(den.im, den.im));
-      scale.re = df_div(den.re, dd);
-      scale.im = df_div(df_neg(den.im), dd);
+      const dfl rd = df_div(df_f(1.f), dd);
+      scale.re = df_mul(den.re, rd);
+      scale.im = df_neg(df_mul(den.im, rd));
     }
     const bool active = !(tau.re.hi == 0.f && tau.im.hi == 0.f);
     if (crank == 0 && tid == 0) {
@@ -609,32 +614,124 @@ __global__ void __launch_bounds__(32) td_inviter_kernel(int n, int r, const floa
   }
 }
 
-// V[j] = Q_H z_j = H_0 (H_1 (... H_{n-2} z_j)), one warp per eigenvector (shuffle reductions,
-// no block barriers), the vector in shared memory; written as complex128 rows of length n.
-__global__ void td_backxform_kernel(int n, int r, const float4* __restrict__ refl, const float4* __restrict__ tau,
-                                    const float2* __restrict__ Z, double2* __restrict__ V) {
-  extern __shared__ float4 usm[];
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j = blockIdx.x * (blockDim.x >> 5) + wib;
-  if (j >= r) return;  // whole warps leave
-  float4* u = usm + (size_t)wib * n;
-  for (int i = lane; i < n; i += 32) {
+// Compact WY form of the back-transformation (Schreiber & Van Loan 1989): for a block of WY_B
+// consecutive reflectors H_k0 ... H_k1-1 = I - Y T Y^H, with Y = [v_k0 .. v_k1-1] (v_k supported
+// on the rows k+1 .. n-1) and T upper triangular: T_ii = tau_i, T[0:i, i] = -tau_i T[0:i, 0:i]
+// (Y[:, 0:i]^H v_i).  One CTA per block builds T (into Tb) and a row-major copy of the block's
+// reflectors Yt[block][g][j] (g = global row), used by the update u -= Y t.
+constexpr int WY_B = 32;
+
+__global__ void __launch_bounds__(256) td_wy_t_kernel(int n, const float4* __restrict__ refl,
+                                                      const float4* __restrict__ tau, float4* __restrict__ Tb,
+                                                      float4* __restrict__ Yt) {
+  __shared__ float4 S[WY_B][WY_B];  // S[i][j] = v_i^H v_j (i < j)
+  __shared__ float4 T[WY_B][WY_B];
+  const int blk = blockIdx.x, k0 = blk * WY_B, nb = min(WY_B, n - 1 - k0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  // row-major copy: Yt[blk][g][j] = v_{k0+j}[g], zero where g <= k0 + j
+  float4* Y = Yt + (size_t)blk * n * WY_B;
+  for (int idx = threadIdx.x; idx < n * WY_B; idx += blockDim.x) {
+    const int g = idx / WY_B, j = idx - g * WY_B;
+    const int k = k0 + j;
+    float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (j < nb && g > k) val = refl[(size_t)k * n + (g - k - 1)];
+    Y[idx] = val;
+  }
+  __syncthreads();  // Y complete (global writes of this CTA are visible to it after the barrier)
+  // S[i][j], i < j, one thread per pair over the rows g >= k0 + j + 1 of the row-major copy: for
+  // a given g the threads read within one 512-byte row
+  for (int pair = threadIdx.x; pair < WY_B * WY_B; pair += blockDim.x) {
+    const int i = pair / WY_B, j = pair - i * WY_B;
+    if (!(i < j && j < nb)) continue;
+    cdf a0 = c_zero(), a1 = c_zero();
+    int g = k0 + j + 1;
+    for (; g + 1 < n; g += 2) {
+      const float4* y0 = Y + (size_t)g * WY_B;
+      a0 = c_add(a0, c_mulc(ld4(&y0[i]), ld4(&y0[j])));
+      a1 = c_add(a1, c_mulc(ld4(&y0[WY_B + i]), ld4(&y0[WY_B + j])));
+    }
+    if (g < n) a0 = c_add(a0, c_mulc(ld4(&Y[(size_t)g * WY_B + i]), ld4(&Y[(size_t)g * WY_B + j])));
+    st4(&S[i][j], c_add(a0, a1));
+  }
+  for (int idx = threadIdx.x; idx < WY_B * WY_B; idx += blockDim.x) T[idx / WY_B][idx % WY_B] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  // column recurrence, warp 0: column i from columns 0..i-1
+  if (warp == 0) {
+    for (int i = 0; i < nb; ++i) {
+      const cdf ti = ld4(&tau[k0 + i]);
+      // lane a < i: T[a][i] = -tau_i sum_{c=a}^{i-1} T[a][c] S[c][i]
+      if (lane < i) {
+        cdf acc = c_zero();
+        for (int c = lane; c < i; ++c) acc = c_add(acc, c_mul(ld4(&T[lane][c]), ld4(&S[c][i])));
+        const cdf nt = {df_neg(ti.re), df_neg(ti.im)};
+        st4(&T[lane][i], c_mul(nt, acc));
+      }
+      if (lane == 0) st4(&T[i][i], ti);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < WY_B * WY_B; idx += blockDim.x)
+    Tb[(size_t)blk * WY_B * WY_B + idx] = T[idx / WY_B][idx % WY_B];
+}
+
+// V[j] = Q_H z_j applying the WY blocks last to first: u <- u - Y (T (Y^H u)).  One CTA per
+// eigenvector, the vector in shared memory; written as complex128 rows of length n.
+__global__ void __launch_bounds__(256, 2) td_backxform_wy_kernel(int n, int r, const float4* __restrict__ refl,
+                                                             const float4* __restrict__ Tb,
+                                                             const float4* __restrict__ Yt,
+                                                             const float2* __restrict__ Z, double2* __restrict__ V) {
+  extern __shared__ float4 usm2[];
+  __shared__ float4 sv[WY_B], tv[WY_B];
+  const int j = blockIdx.x;
+  if (j >= r) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  float4* u = usm2;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const float2 zi = Z[(size_t)j * n + i];
     u[i] = make_float4(zi.x, zi.y, 0.f, 0.f);
   }
-  __syncwarp();
-  for (int k = n - 2; k >= 0; --k) {
-    const int m = n - k - 1;
-    const cdf tk = ld4(&tau[k]);
-    if (tk.re.hi == 0.f && tk.im.hi == 0.f) continue;
-    const float4* vk = refl + (size_t)k * n;
-    cdf s = c_zero();
-    for (int i = lane; i < m; i += 32) s = c_add(s, c_mulc(ld4(&vk[i]), ld4(&u[k + 1 + i])));
-    const cdf ts = c_mul(tk, c_warp_sum(s));
-    for (int i = lane; i < m; i += 32) st4(&u[k + 1 + i], c_sub(ld4(&u[k + 1 + i]), c_mul(ts, ld4(&vk[i]))));
-    __syncwarp();
+  __syncthreads();
+  const int nblk = (n - 1 + WY_B - 1) / WY_B;
+  for (int blk = nblk - 1; blk >= 0; --blk) {
+    const int k0 = blk * WY_B, nb = min(WY_B, n - 1 - k0);
+    // s = Y^H u (warp per reflector, lanes over rows)
+    for (int q = warp; q < WY_B; q += nwarps) {
+      cdf acc = c_zero();
+      if (q < nb) {
+        const int k = k0 + q;
+        for (int g = k + 1 + lane; g < n; g += 32) acc = c_add(acc, c_mulc(ld4(&refl[(size_t)k * n + (g - k - 1)]), ld4(&u[g])));
+        acc = c_warp_sum(acc);
+      }
+      if (lane == 0) st4(&sv[q], acc);
+    }
+    __syncthreads();
+    // t = T s (upper triangular)
+    if (warp == 0) {
+      cdf acc = c_zero();
+      const float4* Trow = Tb + (size_t)blk * WY_B * WY_B + (size_t)lane * WY_B;
+      for (int c = lane; c < nb; ++c) acc = c_add(acc, c_mul(ld4(&Trow[c]), ld4(&sv[c])));
+      st4(&tv[lane], acc);
+    }
+    __syncthreads();
+    // u[g] -= sum_j Y[g][j] t_j for the rows the block touches
+    const float4* Y = Yt + (size_t)blk * n * WY_B;
+    for (int g = k0 + 1 + threadIdx.x; g < n; g += blockDim.x) {
+      // four independent partial sums (the rows of Y are zero past nb)
+      cdf a0 = c_zero(), a1 = c_zero(), a2 = c_zero(), a3 = c_zero();
+      const float4* yg = Y + (size_t)g * WY_B;
+#pragma unroll 2
+      for (int c = 0; c < WY_B; c += 4) {
+        a0 = c_add(a0, c_mul(ld4(&yg[c]), ld4(&tv[c])));
+        a1 = c_add(a1, c_mul(ld4(&yg[c + 1]), ld4(&tv[c + 1])));
+        a2 = c_add(a2, c_mul(ld4(&yg[c + 2]), ld4(&tv[c + 2])));
+        a3 = c_add(a3, c_mul(ld4(&yg[c + 3]), ld4(&tv[c + 3])));
+      }
+      st4(&u[g], c_sub(ld4(&u[g]), c_add(c_add(a0, a1), c_add(a2, a3))));
+    }
+    __syncthreads();
   }
-  for (int i = lane; i < n; i += 32) V[(size_t)j * n + i] = c_to(ld4(&u[i]));
+  for (int i = threadIdx.x; i < n; i += blockDim.x) V[(size_t)j * n + i] = c_to(ld4(&u[i]));
 }
 
 // J = trace(G) - sum of the top r eigenvalues (the tail energy of Eq. 1); trace in FP64
@@ -721,15 +818,19 @@ static hicu_status finish_principal(hicu_handle* h, int n, int r, const double2*
     HICU_LAUNCH(h, K_EIG, st, td_inviter_kernel<<<r, 32, ism, st>>>(n, r, d, e, lam, info, Z));
   }
   {
-    // one warp per eigenvector; several per CTA only when there are more vectors than SMs
-    const int wpb = (int)std::max<size_t>(
-        1, std::min<size_t>({(size_t)4, (size_t)r / (size_t)std::max(1, h->num_sms),
-                             (200 * 1024) / (sizeof(float4) * (size_t)n)}));
-    const size_t usm = sizeof(float4) * (size_t)n * wpb;
-    cudaError_t e0 = allow_max_dynamic_smem((const void*)td_backxform_kernel);
+    // compact WY blocks of WY_B reflectors: T and the row-major reflector copy, then one CTA per
+    // eigenvector
+    const int nblk = (n - 1 + WY_B - 1) / WY_B;
+    hicu_status s = HICU_OK;
+    float4* Tb = (float4*)ws_get(h, WS_EIG_WY, sizeof(float4) * (size_t)nblk * WY_B * (WY_B + (size_t)n), &s);
+    if (s) return s;
+    float4* Yt = Tb + (size_t)nblk * WY_B * WY_B;
+    HICU_LAUNCH(h, K_EIG, st, td_wy_t_kernel<<<nblk, 256, 0, st>>>(n, refl, tau, Tb, Yt));
+    const size_t usm = sizeof(float4) * (size_t)n;
+    cudaError_t e0 = allow_max_dynamic_smem((const void*)td_backxform_wy_kernel);
     if (e0 != cudaSuccess) return cuda_error(h, e0, "backxform smem");
     HICU_LAUNCH(h, K_EIG, st,
-                td_backxform_kernel<<<(r + wpb - 1) / wpb, 32 * wpb, usm, st>>>(n, r, refl, tau, Z, (double2*)Vout));
+                td_backxform_wy_kernel<<<r, 256, usm, st>>>(n, r, refl, Tb, Yt, Z, (double2*)Vout));
   }
   if (J) HICU_LAUNCH(h, K_MISC, st, td_tail_kernel<<<1, 256, 0, st>>>(n, r, G, eig_top, J));
   return cuda_error(h, cudaGetLastError(), "principal subspace");

@@ -14,10 +14,13 @@
 //
 // Accuracy: products of FP32 inputs are formed exactly (fmaf error term) and
 // accumulated in double-word (float pair) arithmetic per thread, then summed
-// across threads and CTAs in FP64 in a fixed order (deterministic).
+// across threads, cells and CTAs in double-float (df.cuh) in a fixed order
+// (deterministic); only the finished entries are converted to FP64 (FP64
+// arithmetic on this GPU is 1/58 of the FP32 rate).
 #include <algorithm>
 #include <vector>
 
+#include "df.cuh"
 #include "hicu_internal.cuh"
 
 namespace hicu {
@@ -78,8 +81,8 @@ __host__ __device__ inline long long task_index(int c1, int c2, int l, int C, in
   return base + nlh + (long long)(c2 - c1 - 1) * nl + l;
 }
 
-__global__ void __launch_bounds__(256) gram_cells_kernel(GramParams P, double2* __restrict__ part) {
-  __shared__ double2 vals[256 * GXSLOT];
+__global__ void __launch_bounds__(256) gram_cells_kernel(GramParams P, float4* __restrict__ part) {
+  __shared__ float4 vals[256 * GXSLOT];
   const ConvGeom& g = P.g;
   const long long task = blockIdx.x;
   const int piece = blockIdx.y;
@@ -135,26 +138,20 @@ __global__ void __launch_bounds__(256) gram_cells_kernel(GramParams P, double2* 
 #pragma unroll
   for (int j = 0; j < GXSLOT; ++j) {
     const int xx = threadIdx.x + j * nt;
-    if (xx < g.ex)
-      vals[xx] = make_double2((double)rh[j] + (double)rl[j], (double)ih[j] + (double)il[j]);
+    if (xx < g.ex) vals[xx] = make_float4(rh[j], rl[j], ih[j], il[j]);
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = nt >> 5;
   for (int ci = warp; ci < P.ncx; ci += nw) {
-    double sr = 0.0, si = 0.0;
+    cdf acc = c_zero();
     for (int xx = P.cutx[ci] + lane; xx < P.cutx[ci + 1]; xx += 32) {
       // zero-product cells (shifted sample outside S) were never written: skip them
       const int vx = xx + ddx;
       if (!g.cx && (vx < 0 || vx >= g.ex)) continue;
-      sr += vals[xx].x;
-      si += vals[xx].y;
+      acc = c_add(acc, ld4(&vals[xx]));
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      sr += __shfl_down_sync(0xffffffffu, sr, o);
-      si += __shfl_down_sync(0xffffffffu, si, o);
-    }
-    if (lane == 0)
-      part[(task * (P.npy * P.npz) + piece) * P.ncx + ci] = make_double2(sr, si);
+    acc = c_warp_sum(acc);
+    if (lane == 0) st4(&part[(task * (P.npy * P.npz) + piece) * P.ncx + ci], acc);
   }
 }
 
@@ -164,7 +161,7 @@ __device__ __forceinline__ int cut_index(const int* cuts, int ncut, int v) {
   return -1;
 }
 
-__global__ void gram_assemble_kernel(GramParams P, const double2* __restrict__ part,
+__global__ void gram_assemble_kernel(GramParams P, const float4* __restrict__ part,
                                      double2* __restrict__ G) {
   const ConvGeom& g = P.g;
   const int n = g.n;
@@ -201,19 +198,17 @@ __global__ void gram_assemble_kernel(GramParams P, const double2* __restrict__ p
     G[idx] = make_double2(nan(""), nan(""));  // unreachable: window ends are always cut points
     return;
   }
-  double sr = 0.0, si = 0.0;
+  cdf acc = c_zero();
   const int npieces = P.npy * P.npz;
   for (int pz = 0; pz < P.npz; ++pz) {
     if (P.pzc[pz] < cz0 || P.pzc[pz] >= cz1) continue;
     for (int py = 0; py < P.npy; ++py) {
       if (P.pyc[py] < cy0 || P.pyc[py] >= cy1) continue;
-      const double2* src = part + (task * npieces + (pz * P.npy + py)) * P.ncx;
-      for (int cx = cx0; cx < cx1; ++cx) {
-        sr += src[cx].x;
-        si += src[cx].y;
-      }
+      const float4* src = part + (task * npieces + (pz * P.npy + py)) * P.ncx;
+      for (int cx = cx0; cx < cx1; ++cx) acc = c_add(acc, ld4(&src[cx]));
     }
   }
+  const double sr = df_to(acc.re), si = df_to(acc.im);
   G[idx] = direct ? make_double2(sr, si) : make_double2(sr, -si);
 }
 
@@ -276,8 +271,7 @@ hicu_status run_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* r
   P.center = (P.nl - 1) / 2;
   const long long ntasks = (long long)g.C * P.nlh + (long long)P.nl * ((long long)g.C * (g.C - 1) / 2);
   const int npieces = P.npy * P.npz;
-  double2* part =
-      (double2*)ws_get(h, WS_GRAM_PART, sizeof(double2) * ntasks * npieces * P.ncx, &s);
+  float4* part = (float4*)ws_get(h, WS_GRAM_PART, sizeof(float4) * ntasks * npieces * P.ncx, &s);
   if (s) return s;
   int nt = ((g.ex + GXSLOT - 1) / GXSLOT + 31) / 32 * 32;
   if (nt < 64) nt = 64;

@@ -217,6 +217,7 @@ enum Slot {
   WS_TC_BC,       // tensor-core B planes, conv
   WS_TC_BA,       // tensor-core B planes, adjoint
   WS_FGRAD,       // filter-gradient partials per CTA
+  WS_EIG_WY,      // principal subspace: compact WY blocks of the back-transformation
   WS_COUNT
 };
 static_assert(WS_COUNT <= hicu_handle::kSlots, "workspace slots");
