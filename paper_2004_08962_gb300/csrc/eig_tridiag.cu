@@ -40,59 +40,83 @@ constexpr int TD_THREADS = 256;
 
 struct TdArgs {
   int n;
-  float4* A;      // n x n row-major complex double-float (rows of the trailing block updated in place)
+  float4* A;      // n x n row-major complex double-float (scaled G); rows updated in place when not
+                  // held in shared memory
   float2* d;      // n   diagonal of T
   float2* e;      // n-1 subdiagonal of T
   float4* refl;   // n x n: row k holds v_k (v_k[0] = 1, length n-k-1)
   float4* tau;    // n-1
   float4* w;      // 2 n scratch (w0 = tau A v), by step parity
   float4* part;   // 2 gridDim.x partial sums w0^H v, by step parity
+  float4* prow;   // 2 n: the next pivot row as stored, published by its owner, by step parity
   GridSync gs;
 };
 
 __device__ __forceinline__ float2 dpack(dfl a) { return make_float2(a.hi, a.lo); }
 __device__ __forceinline__ dfl dload(float2 a) { return {a.x, a.y}; }
 
-// sum of a complex double-float over the CTA, result in every thread (two __syncthreads)
-__device__ inline cdf block_sum_c(cdf a, float4* sh) {
+// CTA sum of a complex double-float, result in every thread: warp shuffles, then warp 0 over
+// the warp partials (two __syncthreads)
+__device__ inline cdf block_sum_c2(cdf a, float4* sh, float4* out) {
   a = c_warp_sum(a);
-  const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int wi = threadIdx.x >> 5, l = threadIdx.x & 31, nwp = blockDim.x >> 5;
   if (l == 0) st4(&sh[wi], a);
   __syncthreads();
-  cdf t = c_zero();
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = c_add(t, ld4(&sh[i]));
+  if (wi == 0) {
+    cdf t = l < nwp ? ld4(&sh[l]) : c_zero();
+    t = c_warp_sum(t);
+    if (l == 0) st4(out, t);
+  }
   __syncthreads();
-  return t;
+  return ld4(out);
 }
 
-// One barrier per reflector.  Global row g is owned by CTA g mod G for the whole run (so a
-// CTA only ever reads back rows it wrote itself, ordered by __syncthreads) and updated in
-// place, except row k+1, the next pivot row: nobody writes it during step k, and every CTA
-// forms its updated values itself from v and w (all of which it holds), so the next
-// Householder vector needs no second barrier.  w0 and the partial sums alternate between
-// two buffers: a CTA can start step k+1 while others still read step k's, but cannot reach
-// step k+2 before every CTA has passed step k+1's barrier.
+// One barrier per reflector.  Global row g is owned by CTA g mod G for the whole run and, with
+// ROWS_IN_SMEM, held in that CTA's shared memory (local row g / G); it is updated in place by its
+// owner only, except row k+1, the next pivot row: nobody writes it during step k, its owner
+// publishes the stored values before the barrier, and every CTA forms its updated values from
+// them and v, w, so the next Householder vector needs no second barrier.  w0, the partial sums
+// and the published row alternate between two buffers: a CTA can start step k+1 while others
+// still read step k's, but cannot reach step k+2 before every CTA has passed step k+1's barrier.
+template <bool ROWS_IN_SMEM>
 __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
   extern __shared__ float4 tsm[];
   const int n = a.n;
+  const int G = gridDim.x, c = blockIdx.x;
+  const int R = (n + G - 1) / G;  // rows per CTA
   float4* x = tsm;          // [n] current pivot row k: x[j] = A[k][k + j]
   float4* v = tsm + n;      // [n]
   float4* w = tsm + 2 * n;  // [n]
+  float4* rows = tsm + 3 * n;  // [R][n] own rows (ROWS_IN_SMEM)
   __shared__ float4 red[TD_THREADS / 32];
+  __shared__ float4 bsum;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = TD_THREADS / 32;
-  const int G = gridDim.x, c = blockIdx.x;
+  auto row_of = [&](int g) -> float4* {
+    return ROWS_IN_SMEM ? rows + (size_t)(g / G) * n : a.A + (size_t)g * n;
+  };
   unsigned epoch = 0;
+  if (ROWS_IN_SMEM)
+    for (int idx = tid; idx < R * n; idx += TD_THREADS) {
+      const int lr = idx / n, g = lr * G + c;
+      if (g < n) rows[idx] = a.A[(size_t)g * n + (idx - lr * n)];
+    }
   for (int j = tid; j < n; j += TD_THREADS) x[j] = a.A[j];
   __syncthreads();
   for (int k = 0; k < n - 1; ++k) {
     const int m = n - k - 1;
+    // --- the owner of row k+1 publishes it (stored values, columns k+1 ..)
+    float4* pub = a.prow + (k & 1) * n;
+    if ((k + 1) % G == c) {
+      const float4* src = row_of(k + 1) + (k + 1);
+      for (int j = tid; j < m; j += TD_THREADS) pub[j] = src[j];
+    }
     // --- Householder vector of column k = conj(row k right of the diagonal), in every CTA
     cdf s2 = c_zero();
     for (int j = 1 + tid; j < m; j += TD_THREADS) {
       const cdf xj = ld4(&x[1 + j]);
       s2.re = df_add(s2.re, df_add(df_mul(xj.re, xj.re), df_mul(xj.im, xj.im)));
     }
-    const dfl xn2 = block_sum_c(s2, red).re;
+    const dfl xn2 = block_sum_c2(s2, red, &bsum).re;
     const cdf x0 = c_conj(ld4(&x[1]));
     cdf tau = c_zero(), scale = c_zero();
     dfl beta = x0.re;
@@ -129,10 +153,15 @@ __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
     cdf pp = c_zero();
     if (active) {
       for (int i = i0 + G * warp; i < m; i += G * nw) {
-        const float4* row = a.A + (long long)(k + 1 + i) * n + (k + 1);
-        cdf y = c_zero();
-        for (int j = lane; j < m; j += 32) y = c_add(y, c_mul(ld4(&row[j]), ld4(&v[j])));
-        y = c_warp_sum(y);
+        const float4* row = row_of(k + 1 + i) + (k + 1);
+        cdf y0 = c_zero(), y1 = c_zero();
+        int j = lane;
+        for (; j + 32 < m; j += 64) {
+          y0 = c_add(y0, c_mul(ld4(&row[j]), ld4(&v[j])));
+          y1 = c_add(y1, c_mul(ld4(&row[j + 32]), ld4(&v[j + 32])));
+        }
+        if (j < m) y0 = c_add(y0, c_mul(ld4(&row[j]), ld4(&v[j])));
+        const cdf y = c_warp_sum(c_add(y0, y1));
         if (lane == 0) {
           const cdf w0 = c_mul(tau, y);
           st4(&wg[i], w0);
@@ -141,7 +170,7 @@ __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
       }
     }
     {
-      const cdf ps = block_sum_c(pp, red);
+      const cdf ps = block_sum_c2(pp, red, &bsum);
       if (tid == 0) st4(&pg[c], ps);
     }
     if (!grid_sync(a.gs, epoch)) return;
@@ -149,14 +178,14 @@ __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
     if (active) {
       cdf sp = c_zero();
       for (int q = tid; q < G; q += TD_THREADS) sp = c_add(sp, ld4(&pg[q]));
-      const cdf ssum = block_sum_c(sp, red);
+      const cdf ssum = block_sum_c2(sp, red, &bsum);
       const cdf htau = {df_mul_f(tau.re, -0.5f), df_mul_f(tau.im, -0.5f)};
       const cdf alpha = c_mul(htau, ssum);
       for (int j = tid; j < m; j += TD_THREADS) st4(&w[j], c_add(ld4(&wg[j]), c_mul(alpha, ld4(&v[j]))));
       __syncthreads();
       for (int i = i0 + G * warp; i < m; i += G * nw) {
         if (i == 0) continue;
-        float4* row = a.A + (long long)(k + 1 + i) * n + (k + 1);
+        float4* row = row_of(k + 1 + i) + (k + 1);
         const cdf vi = ld4(&v[i]), wi = ld4(&w[i]);
         for (int j = lane; j < m; j += 32) {
           // A_ij -= v_i conj(w_j) + w_i conj(v_j)
@@ -167,10 +196,9 @@ __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
     }
     // --- the next pivot row k+1 (relative row 0: v_0 = 1), formed by every CTA
     {
-      const float4* row = a.A + (long long)(k + 1) * n + (k + 1);
       const cdf w0c = active ? ld4(&w[0]) : c_zero();
       for (int j = tid; j < m; j += TD_THREADS) {
-        cdf aij = ld4(&row[j]);
+        cdf aij = ld4(&pub[j]);
         if (active) aij = c_sub(aij, c_add(c_conj(ld4(&w[j])), c_mul(w0c, c_conj(ld4(&v[j])))));
         st4(&x[j], aij);
       }
@@ -201,21 +229,6 @@ struct TdcArgs {
   float4* refl;
   float4* tau;
 };
-
-// CTA sum of a complex double-float: warp shuffles, then warp 0 over the warp partials
-__device__ inline cdf block_sum_c2(cdf a, float4* sh, float4* out) {
-  a = c_warp_sum(a);
-  const int wi = threadIdx.x >> 5, l = threadIdx.x & 31, nwp = blockDim.x >> 5;
-  if (l == 0) st4(&sh[wi], a);
-  __syncthreads();
-  if (wi == 0) {
-    cdf t = l < nwp ? ld4(&sh[l]) : c_zero();
-    t = c_warp_sum(t);
-    if (l == 0) st4(out, t);
-  }
-  __syncthreads();
-  return ld4(out);
-}
 
 __global__ void __launch_bounds__(TDC_THREADS, 1) tridiag_cluster_kernel(const TdcArgs a) {
   cg::cluster_group cl = cg::this_cluster();
@@ -751,7 +764,7 @@ __global__ void td_tail_kernel(int n, int r, const double2* __restrict__ G, cons
 }
 
 static hicu_status launch_tridiag_grid(hicu_handle* h, int n, float4* A, float2* d, float2* e, float4* refl,
-                                       float4* tau, float4* w, float4* part, cudaStream_t st) {
+                                       float4* tau, float4* w, float4* part, float4* prow, cudaStream_t st) {
   TdArgs a;
   a.n = n;
   a.A = A;
@@ -761,14 +774,20 @@ static hicu_status launch_tridiag_grid(hicu_handle* h, int n, float4* A, float2*
   a.tau = tau;
   a.w = w;
   a.part = part;
-  const size_t smem = sizeof(float4) * 3 * (size_t)n;
+  a.prow = prow;
   int grid = h->num_sms;
+  // own rows in shared memory when they fit next to the three vectors
+  const int R = (n + grid - 1) / grid;
+  const size_t smem_vec = sizeof(float4) * 3 * (size_t)n;
+  const size_t smem_rows = smem_vec + sizeof(float4) * (size_t)R * n;
+  const bool in_smem = smem_rows <= 200 * 1024;
+  const void* kern = in_smem ? (const void*)tridiag_kernel<true> : (const void*)tridiag_kernel<false>;
+  const size_t smem = in_smem ? smem_rows : smem_vec;
   {
-    cudaError_t e0 = allow_max_dynamic_smem((const void*)tridiag_kernel);
+    cudaError_t e0 = allow_max_dynamic_smem(kern);
     if (e0 != cudaSuccess) return cuda_error(h, e0, "tridiag smem");
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_kernel, TD_THREADS, smem) != cudaSuccess ||
-        per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TD_THREADS, smem) != cudaSuccess || per_sm < 1)
       return set_error(h, HICU_ERR_CUDA, "principal subspace: occupancy query failed");
     grid = std::max(1, std::min(grid, h->num_sms * per_sm));
   }
@@ -787,14 +806,11 @@ static hicu_status launch_tridiag_grid(hicu_handle* h, int n, float4* A, float2*
     if (ce == cudaSuccess) ce = cudaMemsetAsync(h->dev_sync, 0, 2 * sizeof(unsigned), h->coop_st);
     if (ce == cudaSuccess)
       HICU_LAUNCH(h, K_TRIDIAG, h->coop_st,
-                  ce = cudaLaunchCooperativeKernel((const void*)tridiag_kernel, dim3(grid), dim3(TD_THREADS), args,
-                                                   smem, h->coop_st));
+                  ce = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(TD_THREADS), args, smem, h->coop_st));
     if (ce == cudaSuccess) ce = cudaEventRecord(h->coop_out, h->coop_st);
     if (ce == cudaSuccess) ce = cudaStreamWaitEvent(st, h->coop_out, 0);
   } else {
-    HICU_LAUNCH(h, K_TRIDIAG, st,
-                ce = cudaLaunchCooperativeKernel((const void*)tridiag_kernel, dim3(grid), dim3(TD_THREADS), args,
-                                                 smem, st));
+    HICU_LAUNCH(h, K_TRIDIAG, st, ce = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(TD_THREADS), args, smem, st));
   }
   if (ce != cudaSuccess) return cuda_error(h, ce, "principal subspace: tridiagonalisation launch");
   return HICU_OK;
@@ -848,17 +864,18 @@ hicu_status run_principal(hicu_handle* h, int64_t n64, int64_t r64, const double
   if (s) return s;
   float4* refl = (float4*)ws_get(h, WS_EIG_A1, sizeof(float4) * nn, &s);
   if (s) return s;
-  // float4 units: tau (n), w (2n), part (2 nsm); float2 units: d, e, e2, lam (n each), info (4),
+  // float4 units: tau (n), w (2n), part (2 nsm), prow (2n); float2 units: d, e, e2, lam (n each), info (4),
   // Z (r n); then amax bits and the scale (8 bytes each)
   const size_t nsm = (size_t)std::max(1, h->num_sms);
-  const size_t f4 = (size_t)n + 2 * (size_t)n + 2 * nsm;
+  const size_t f4 = (size_t)n + 2 * (size_t)n + 2 * nsm + 2 * (size_t)n;
   const size_t f2 = 4 * (size_t)n + 4 + (size_t)r * n;
   unsigned char* buf = (unsigned char*)ws_get(h, WS_EIG_V, 16 * f4 + 8 * f2 + 16, &s);
   if (s) return s;
   float4* tau = (float4*)buf;
   float4* w = tau + n;
   float4* part = w + 2 * n;
-  float2* d = (float2*)(part + 2 * nsm);
+  float4* prow = part + 2 * nsm;
+  float2* d = (float2*)(prow + 2 * n);
   float2* e = d + n;
   float2* e2 = e + n;
   float2* lam = e2 + n;
@@ -888,7 +905,7 @@ hicu_status run_principal(hicu_handle* h, int64_t n64, int64_t r64, const double
     HICU_LAUNCH(h, K_TRIDIAG, st, ce = cudaLaunchKernelEx(&cfg, tridiag_cluster_kernel, ca));
     if (ce != cudaSuccess) return cuda_error(h, ce, "principal subspace: cluster tridiagonalisation launch");
   } else {
-    hicu_status s2 = launch_tridiag_grid(h, n, A, d, e, refl, tau, w, part, st);
+    hicu_status s2 = launch_tridiag_grid(h, n, A, d, e, refl, tau, w, part, prow, st);
     if (s2) return s2;
   }
   return finish_principal(h, n, r, G, Vout, eig_top, eig_all, J, d, e, e2, lam, info, Z, refl, tau, scale, st);
