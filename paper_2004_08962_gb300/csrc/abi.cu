@@ -1,5 +1,6 @@
 // C ABI of libhicu: handle, argument validation, workspace, and the drivers
 // that chain the kernels into the steps of Algorithm 1.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -205,6 +206,9 @@ extern "C" hicu_status hicu_destroy(hicu_handle* h) {
   for (auto st : h->lane_st) cudaStreamDestroy(st);
   for (auto e : h->batch_ev) cudaEventDestroy(e);
   if (h->coop_st_own) cudaStreamDestroy(h->coop_st_own);
+  if (h->side_st) cudaStreamDestroy(h->side_st);
+  if (h->side_fork) cudaEventDestroy(h->side_fork);
+  if (h->side_join) cudaEventDestroy(h->side_join);
   if (h->coop_in) cudaEventDestroy(h->coop_in);
   if (h->coop_out) cudaEventDestroy(h->coop_out);
   for (auto& w : h->ws)
@@ -732,6 +736,10 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
   if (s) return s;
   double* dstats = (double*)ws_get(h, WS_REC_STATS, sizeof(double) * 4 * (total_steps + 1), &s);
   if (s) return s;
+  int pmax = 1;
+  for (int i = 0; i < prm->nstages; ++i) pmax = std::max(pmax, (int)prm->stages[i].p);
+  float* bank = (float*)ws_get(h, WS_BANK, sizeof(float2) * (size_t)pmax * n, &s);
+  if (s) return s;
   if (prm->init == 1) {
     HICU_LAUNCH(h, K_MISC, st,
                 time_average_kernel<<<1024, 256, 0, st>>>(
@@ -759,10 +767,15 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
         if (s) return s;
         HICU_LAUNCH(h, K_MISC, st, tail_sum_kernel<<<1, 256, 0, st>>>(eig, (int)nr, dlog + it));
       }
+      // Algorithm 1 steps 6-8: the basis is converted to complex64 once per outer iteration
+      const int64_t nq = principal ? r : nr;
+      const int jmode = principal ? HICU_JL_COMPLEMENT : prm->jl;
+      float2* Qf = nullptr;
+      if (stg.gd_steps > 0 && (s = jl_convert_q(h, n, nq, Q, &Qf, st))) return s;
       for (int j = 0; j < stg.gd_steps; ++j) {
-        s = hicu_gd_step(h, geom, &stg.region, y, m, Q, principal ? r : nr, stg.p,
-                         principal ? HICU_JL_COMPLEMENT : prm->jl, prm->seed, counter, nullptr,
-                         dstats + 4 * counter, prm->prec, stream);
+        s = launch_jl_converted(h, n, nq, stg.p, Qf, jmode, nullptr, prm->seed, counter, bank, st);
+        if (s) return s;
+        s = gd_step_filters(h, geom, &stg.region, y, m, bank, stg.p, dstats + 4 * counter, prm->prec, st);
         if (s) return s;
         ++counter;
       }

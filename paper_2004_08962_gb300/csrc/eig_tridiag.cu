@@ -821,6 +821,27 @@ static hicu_status finish_principal(hicu_handle* h, int n, int r, const double2*
                                     double* eig_all, double* J, float2* d, float2* e, float2* e2, float2* lam,
                                     float2* info, float2* Z, float4* refl, float4* tau, double* scale,
                                     cudaStream_t st) {
+  // the compact WY factors of the back-transformation need only the reflectors: build them on
+  // the side stream while the eigenvalues and eigenvectors of T are computed
+  const int nblk = (n - 1 + WY_B - 1) / WY_B;
+  hicu_status sw = HICU_OK;
+  float4* Tb = (float4*)ws_get(h, WS_EIG_WY, sizeof(float4) * (size_t)nblk * WY_B * (WY_B + (size_t)n), &sw);
+  if (sw) return sw;
+  float4* Yt = Tb + (size_t)nblk * WY_B * WY_B;
+  if (!h->side_st) {
+    if (cudaStreamCreateWithFlags(&h->side_st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->side_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->side_join, cudaEventDisableTiming) != cudaSuccess)
+      return cuda_error(h, cudaGetLastError(), "principal subspace: side stream");
+  }
+  {
+    cudaError_t ce = cudaEventRecord(h->side_fork, st);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(h->side_st, h->side_fork, 0);
+    if (ce != cudaSuccess) return cuda_error(h, ce, "principal subspace: fork");
+    HICU_LAUNCH(h, K_EIG, h->side_st, td_wy_t_kernel<<<nblk, 256, 0, h->side_st>>>(n, refl, tau, Tb, Yt));
+    ce = cudaEventRecord(h->side_join, h->side_st);
+    if (ce != cudaSuccess) return cuda_error(h, ce, "principal subspace: join");
+  }
   // 2. eigenvalues (top r; all n when requested)
   HICU_LAUNCH(h, K_EIG, st, td_bounds_kernel<<<1, 256, 0, st>>>(n, d, e, e2, info));
   HICU_LAUNCH(h, K_EIG, st, td_bisect_kernel<<<r, 32, 0, st>>>(n, n - r, d, e2, info, scale, lam, eig_top));
@@ -834,14 +855,9 @@ static hicu_status finish_principal(hicu_handle* h, int n, int r, const double2*
     HICU_LAUNCH(h, K_EIG, st, td_inviter_kernel<<<r, 32, ism, st>>>(n, r, d, e, lam, info, Z));
   }
   {
-    // compact WY blocks of WY_B reflectors: T and the row-major reflector copy, then one CTA per
-    // eigenvector
-    const int nblk = (n - 1 + WY_B - 1) / WY_B;
-    hicu_status s = HICU_OK;
-    float4* Tb = (float4*)ws_get(h, WS_EIG_WY, sizeof(float4) * (size_t)nblk * WY_B * (WY_B + (size_t)n), &s);
-    if (s) return s;
-    float4* Yt = Tb + (size_t)nblk * WY_B * WY_B;
-    HICU_LAUNCH(h, K_EIG, st, td_wy_t_kernel<<<nblk, 256, 0, st>>>(n, refl, tau, Tb, Yt));
+    // apply the compact WY blocks, one CTA per eigenvector, once the factors are ready
+    cudaError_t ce = cudaStreamWaitEvent(st, h->side_join, 0);
+    if (ce != cudaSuccess) return cuda_error(h, ce, "principal subspace: wait");
     const size_t usm = sizeof(float4) * (size_t)n;
     cudaError_t e0 = allow_max_dynamic_smem((const void*)td_backxform_wy_kernel);
     if (e0 != cudaSuccess) return cuda_error(h, e0, "backxform smem");

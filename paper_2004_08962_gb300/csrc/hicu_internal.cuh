@@ -178,6 +178,11 @@ struct hicu_handle {
   long long launches_class = 0;
   std::vector<cudaEvent_t> prof_events;
   size_t prof_used = 0;
+  // side stream for work independent of the main chain inside one call (created on demand):
+  // forked from and joined back to the caller's stream with events
+  cudaStream_t side_st = nullptr;
+  cudaEvent_t side_fork = nullptr;
+  cudaEvent_t side_join = nullptr;
   // batch lanes (hicu_reconstruct_batched): one sub-handle and stream each, created on demand
   std::vector<hicu_handle*> lane_h;
   std::vector<cudaStream_t> lane_st;
@@ -285,6 +290,14 @@ hicu_status launch_adjoint_tc(hicu_handle* h, const ConvGeom& g, const uint4* Rs
 hicu_status launch_jl(hicu_handle* h, int64_t n, int64_t nr, int p, const double* Q, int mode,
                       const double* P, uint64_t seed, uint64_t counter, float* bank,
                       cudaStream_t st);
+// the same in two parts: Q (complex128 [nr][n]) to complex64 in the handle's workspace, then the
+// compression from that copy (the reconstruction driver converts once per outer iteration)
+hicu_status jl_convert_q(hicu_handle* h, int64_t n, int64_t nr, const double* Q, float2** Qf, cudaStream_t st);
+hicu_status launch_jl_converted(hicu_handle* h, int64_t n, int64_t nr, int p, const float2* Qf, int mode,
+                                const double* P, uint64_t seed, uint64_t counter, float* bank, cudaStream_t st);
+hicu_status gd_step_filters(hicu_handle* h, const hicu_geom* geom, const hicu_region* region, float* y,
+                            const uint8_t* mask, const float* filters, int32_t p, double* stats,
+                            int32_t prec, cudaStream_t st);
 
 hicu_status run_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* reg, const float* x,
                      double* G, cudaStream_t st);

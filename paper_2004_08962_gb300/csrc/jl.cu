@@ -119,26 +119,28 @@ __global__ void jl_combine_compl_kernel(int n, int m, int p, const float2* __res
   bank[(long long)k * n + a] = make_float2(P[(long long)a * p + k] - re, -im);
 }
 
-hicu_status launch_jl(hicu_handle* h, int64_t n, int64_t nr, int p, const double* Q, int mode,
-                      const double* P, uint64_t seed, uint64_t counter, float* bank,
-                      cudaStream_t st) {
+hicu_status jl_convert_q(hicu_handle* h, int64_t n, int64_t nr, const double* Q, float2** Qf, cudaStream_t st) {
+  hicu_status s = HICU_OK;
+  *Qf = (float2*)ws_get(h, WS_QF, sizeof(float2) * nr * n, &s);
+  if (s) return s;
+  const long long tot = nr * n;
+  int blocks = (int)((tot + 255) / 256);
+  if (blocks > 2048) blocks = 2048;
+  HICU_LAUNCH(h, K_JL, st, to_c64_kernel<<<blocks, 256, 0, st>>>((const double2*)Q, *Qf, tot));
+  return cuda_error(h, cudaGetLastError(), "jl convert");
+}
+
+hicu_status launch_jl_converted(hicu_handle* h, int64_t n, int64_t nr, int p, const float2* Qf, int mode,
+                                const double* P, uint64_t seed, uint64_t counter, float* bank, cudaStream_t st) {
   hicu_status s = HICU_OK;
   const int rows = (mode == HICU_JL_NULLSPACE) ? (int)nr : (int)n;
   float* Pf = (float*)ws_get(h, WS_P, sizeof(float) * rows * p, &s);
-  if (s) return s;
-  float2* Qf = (float2*)ws_get(h, WS_QF, sizeof(float2) * nr * n, &s);
   if (s) return s;
   {
     const long long tot = (long long)rows * p;
     int blocks = (int)((tot + 255) / 256);
     if (blocks > 1024) blocks = 1024;
     HICU_LAUNCH(h, K_JL, st, jl_make_p_kernel<<<blocks, 256, 0, st>>>(rows, p, P, seed, counter, Pf));
-  }
-  {
-    const long long tot = nr * n;
-    int blocks = (int)((tot + 255) / 256);
-    if (blocks > 2048) blocks = 2048;
-    HICU_LAUNCH(h, K_JL, st, to_c64_kernel<<<blocks, 256, 0, st>>>((const double2*)Q, Qf, tot));
   }
   dim3 grid((unsigned)((n + 127) / 128), (unsigned)p);
   if (mode == HICU_JL_NULLSPACE) {
@@ -158,6 +160,15 @@ hicu_status launch_jl(hicu_handle* h, int64_t n, int64_t nr, int p, const double
                   jl_combine_compl_kernel<<<grid, 128, 0, st>>>((int)n, (int)nr, p, Qf, T, Pf, (float2*)bank));
   }
   return cuda_error(h, cudaGetLastError(), "jl_compress");
+}
+
+hicu_status launch_jl(hicu_handle* h, int64_t n, int64_t nr, int p, const double* Q, int mode,
+                      const double* P, uint64_t seed, uint64_t counter, float* bank,
+                      cudaStream_t st) {
+  float2* Qf = nullptr;
+  hicu_status s = jl_convert_q(h, n, nr, Q, &Qf, st);
+  if (s) return s;
+  return launch_jl_converted(h, n, nr, p, Qf, mode, P, seed, counter, bank, st);
 }
 
 }  // namespace hicu
