@@ -71,6 +71,17 @@ __device__ inline cdf block_sum_c2(cdf a, float4* sh, float4* out) {
   return ld4(out);
 }
 
+// CTA sum of a complex double-float, result in every thread with one __syncthreads: every warp
+// reduces the warp partials itself (the butterfly gives bitwise the same sum in every lane, as
+// df_add is commutative).  sh (one slot per warp) may be reused after the next __syncthreads.
+__device__ inline cdf block_sum_all(cdf a, float4* sh) {
+  a = c_warp_sum(a);
+  const int wi = threadIdx.x >> 5, l = threadIdx.x & 31, nwp = blockDim.x >> 5;
+  if (l == 0) st4(&sh[wi], a);
+  __syncthreads();
+  return c_warp_sum(l < nwp ? ld4(&sh[l]) : c_zero());
+}
+
 // One barrier per reflector.  Global row g is owned by CTA g mod G for the whole run and, with
 // ROWS_IN_SMEM, held in that CTA's shared memory (local row g / G); it is updated in place by its
 // owner only, except row k+1, the next pivot row: nobody writes it during step k, its owner
@@ -123,12 +134,12 @@ __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
     if (!(xn2.hi == 0.f && x0.im.hi == 0.f)) {
       const dfl nrm = df_sqrt(df_add(df_add(df_mul(x0.re, x0.re), df_mul(x0.im, x0.im)), xn2));
       beta = x0.re.hi >= 0.f ? df_neg(nrm) : nrm;
-      const dfl rb = df_div(df_f(1.f), beta);
+      const dfl rb = df_rcp(beta);
       tau.re = df_sub(df_f(1.f), df_mul(x0.re, rb));  // (beta - x0.re) / beta
       tau.im = df_neg(df_mul(x0.im, rb));
       const cdf den = {df_sub(x0.re, beta), x0.im};  // v = x / (x0 - beta)
       const dfl dd = df_add(df_mul(den.re, den.re), df_mul(den.im, den.im));
-      const dfl rd = df_div(df_f(1.f), dd);
+      const dfl rd = df_rcp(dd);
       scale.re = df_mul(den.re, rd);
       scale.im = df_neg(df_mul(den.im, rd));
     }
@@ -236,14 +247,12 @@ __global__ void __launch_bounds__(TDC_THREADS, 1) tridiag_cluster_kernel(const T
   const int n = a.n;
   const int R = (n + nct - 1) / nct;
   extern __shared__ float4 csm[];
-  float4* rows = csm;             // [R][n]
+  float4* rows = csm;                // [R][n]
   float4* x = rows + (size_t)R * n;  // [n] pivot row
-  float4* v = x + n;              // [n]
-  float4* w = v + n;              // [n]
-  float4* w0loc = w + n;          // [2][R] w0 of own rows, by step parity
-  float4* partloc = w0loc + 2 * R;  // [2] partial sums w0^H v, by step parity
-  float4* bsum = partloc + 2;     // [1] block-sum result
-  __shared__ float4 red[TDC_THREADS / 32];
+  float4* v = x + n;                 // [n]
+  float4* w = v + n;                 // [n]
+  float4* w0loc = w + n;             // [2][R] w0 of own rows, by step parity
+  __shared__ float4 red_n[TDC_THREADS / 32], red_s[TDC_THREADS / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = TDC_THREADS / 32;
   for (int idx = tid; idx < R * n; idx += TDC_THREADS) {
     const int lr = idx / n, j = idx - lr * n;
@@ -251,33 +260,33 @@ __global__ void __launch_bounds__(TDC_THREADS, 1) tridiag_cluster_kernel(const T
     if (g < n) rows[idx] = a.A[(size_t)g * n + j];
   }
   cl.sync();
+  // pivot row 0 and the squared norm of its entries 2.. (the Householder vector's tail)
+  cdf s2 = c_zero();
   {
     const float4* r0 = cl.map_shared_rank(rows, 0);
-    for (int j = tid; j < n; j += TDC_THREADS) x[j] = r0[j];
+    for (int j = tid; j < n; j += TDC_THREADS) {
+      const float4 xj = r0[j];
+      x[j] = xj;
+      if (j >= 2) s2.re = df_add(s2.re, df_add(df_mul({xj.x, xj.y}, {xj.x, xj.y}), df_mul({xj.z, xj.w}, {xj.z, xj.w})));
+    }
   }
-  __syncthreads();
+  dfl xn2 = block_sum_all(s2, red_n).re;
   for (int k = 0; k < n - 1; ++k) {
     const int m = n - k - 1;
     const int par = k & 1;
-    // --- Householder vector of column k (every CTA)
-    cdf s2 = c_zero();
-    for (int j = 1 + tid; j < m; j += TDC_THREADS) {
-      const cdf xj = ld4(&x[1 + j]);
-      s2.re = df_add(s2.re, df_add(df_mul(xj.re, xj.re), df_mul(xj.im, xj.im)));
-    }
-    const dfl xn2 = block_sum_c2(s2, red, bsum).re;
+    // --- Householder vector of column k (every CTA, from its copy of the pivot row)
     const cdf x0 = c_conj(ld4(&x[1]));
     cdf tau = c_zero(), scale = c_zero();
     dfl beta = x0.re;
     if (!(xn2.hi == 0.f && x0.im.hi == 0.f)) {
       const dfl nrm = df_sqrt(df_add(df_add(df_mul(x0.re, x0.re), df_mul(x0.im, x0.im)), xn2));
       beta = x0.re.hi >= 0.f ? df_neg(nrm) : nrm;
-      const dfl rb = df_div(df_f(1.f), beta);
+      const dfl rb = df_rcp(beta);
       tau.re = df_sub(df_f(1.f), df_mul(x0.re, rb));  // (beta - x0.re) / beta
       tau.im = df_neg(df_mul(x0.im, rb));
       const cdf den = {df_sub(x0.re, beta), x0.im};
       const dfl dd = df_add(df_mul(den.re, den.re), df_mul(den.im, den.im));
-      const dfl rd = df_div(df_f(1.f), dd);
+      const dfl rd = df_rcp(dd);
       scale.re = df_mul(den.re, rd);
       scale.im = df_neg(df_mul(den.im, rd));
     }
@@ -287,70 +296,79 @@ __global__ void __launch_bounds__(TDC_THREADS, 1) tridiag_cluster_kernel(const T
       a.e[k] = dpack(beta);
       st4(&a.tau[k], tau);
     }
-    for (int j = tid; j < m; j += TDC_THREADS) {
+    // m <= TDC_MAX_N - 1 < TDC_THREADS: one entry per thread
+    if (tid < m) {
       cdf vj;
-      if (j == 0) vj = {{1.f, 0.f}, {0.f, 0.f}};
-      else vj = active ? c_mul(c_conj(ld4(&x[1 + j])), scale) : c_zero();
-      st4(&v[j], vj);
-      if (crank == 0) st4(&a.refl[(long long)k * n + j], vj);
+      if (tid == 0) vj = {{1.f, 0.f}, {0.f, 0.f}};
+      else vj = active ? c_mul(c_conj(ld4(&x[1 + tid])), scale) : c_zero();
+      st4(&v[tid], vj);
+      if (crank == 0) st4(&a.refl[(long long)k * n + tid], vj);
     }
     __syncthreads();
-    // --- own trailing rows: global g = k+1 .. n-1 with g % nct == crank, local lr = g / nct
+    // --- w0 = tau A v for the own trailing rows: global g = k+1 .. n-1 with g % nct == crank
     const int lr0 = (k + 1 - crank + nct - 1) / nct;  // first own local row with g >= k+1
     const int nown = lr0 < R ? R - lr0 - ((R - 1) * nct + crank >= n ? 1 : 0) : 0;
-    cdf pp = c_zero();
     if (active) {
       for (int q = warp; q < nown; q += nw) {
-        const int lr = lr0 + q, g = lr * nct + crank, i = g - (k + 1);
+        const int lr = lr0 + q;
         const float4* row = rows + (size_t)lr * n + (k + 1);
         cdf y = c_zero();
-        for (int j = lane; j < m; j += 32) y = c_add(y, c_mul(ld4(&row[j]), ld4(&v[j])));
+        for (int j = lane; j < m; j += 32) c_acc_mul(y, ld4(&row[j]), ld4(&v[j]));
         y = c_warp_sum(y);
-        if (lane == 0) {
-          const cdf w0 = c_mul(tau, y);
-          st4(&w0loc[par * R + lr], w0);
-          pp = c_add(pp, c_mulc(w0, ld4(&v[i])));
-        }
+        if (lane == 0) st4(&w0loc[par * R + lr], c_mul(tau, y));
       }
     }
-    {
-      const cdf ps = block_sum_c2(pp, red, bsum);
-      if (tid == 0) st4(&partloc[par], ps);
-    }
     cl.sync();
-    // --- alpha, w (all m), rank-2 update of the own rows but row k+1, next pivot row
+    // --- alpha = -tau/2 (w0^H v), w = w0 + alpha v (every CTA, w0 read from the row owners)
     const int owner1 = (k + 1) % nct;
     const float4* prow = cl.map_shared_rank(rows, owner1) + (size_t)((k + 1) / nct) * n + (k + 1);
     if (active) {
-      cdf sp = c_zero();
-      if (tid < nct) sp = ld4(cl.map_shared_rank(partloc, tid) + par);
-      const cdf ssum = block_sum_c2(sp, red, bsum);
+      cdf w0 = c_zero(), vj = c_zero();
+      if (tid < m) {
+        const int g = k + 1 + tid;
+        w0 = ld4(cl.map_shared_rank(w0loc, g % nct) + par * R + g / nct);
+        vj = ld4(&v[tid]);
+      }
+      const cdf ssum = block_sum_all(c_mulc(w0, vj), red_s);
       const cdf htau = {df_mul_f(tau.re, -0.5f), df_mul_f(tau.im, -0.5f)};
       const cdf alpha = c_mul(htau, ssum);
-      for (int j = tid; j < m; j += TDC_THREADS) {
-        const int g = k + 1 + j;
-        const cdf w0 = ld4(cl.map_shared_rank(w0loc, g % nct) + par * R + g / nct);
-        st4(&w[j], c_add(w0, c_mul(alpha, ld4(&v[j]))));
-      }
+      if (tid < m) st4(&w[tid], c_add(w0, c_mul(alpha, vj)));
       __syncthreads();
-      for (int idx = tid; idx < nown * m; idx += TDC_THREADS) {
-        const int q = idx / m, j = idx - q * m;
-        const int lr = lr0 + q, g = lr * nct + crank, i = g - (k + 1);
+      // rank-2 update of the own rows but row k+1: A_ij -= v_i conj(w_j) + w_i conj(v_j)
+      const int tot = nown * m;
+      const float rm = 1.f / (float)m;
+      for (int idx = tid; idx < tot; idx += TDC_THREADS) {
+        const int q = (int)__fmul_rn((float)idx + 0.5f, rm);  // idx / m (exact: idx < 2^14, m <= 439)
+        const int j = idx - q * m;
+        const int lr = lr0 + q, i = lr * nct + crank - (k + 1);
         if (i == 0) continue;
         float4* aij = rows + (size_t)lr * n + (k + 1) + j;
-        const cdf t = c_add(c_mul(ld4(&v[i]), c_conj(ld4(&w[j]))), c_mul(ld4(&w[i]), c_conj(ld4(&v[j]))));
-        st4(aij, c_sub(ld4(aij), t));
+        const cdf vi = ld4(&v[i]), wi = ld4(&w[i]), wj = ld4(&w[j]), vjj = ld4(&v[j]);
+        cdf acc = ld4(aij);
+        df_acc_mul(acc.re, df_neg(vi.re), wj.re);
+        df_acc_mul(acc.re, df_neg(vi.im), wj.im);
+        df_acc_mul(acc.re, df_neg(wi.re), vjj.re);
+        df_acc_mul(acc.re, df_neg(wi.im), vjj.im);
+        df_acc_mul(acc.im, df_neg(vi.im), wj.re);
+        df_acc_mul(acc.im, vi.re, wj.im);
+        df_acc_mul(acc.im, df_neg(wi.im), vjj.re);
+        df_acc_mul(acc.im, wi.re, vjj.im);
+        st4(aij, c_renorm(acc));
       }
     }
-    {
-      const cdf w0c = active ? ld4(&w[0]) : c_zero();
-      for (int j = tid; j < m; j += TDC_THREADS) {
-        cdf aij = ld4(&prow[j]);
-        if (active) aij = c_sub(aij, c_add(c_conj(ld4(&w[j])), c_mul(w0c, c_conj(ld4(&v[j])))));
-        st4(&x[j], aij);
+    // --- the next pivot row k+1 (relative row 0: v_0 = 1), formed by every CTA, and the squared
+    // norm of its entries 2.. for the next step
+    cdf s2n = c_zero();
+    if (tid < m) {
+      cdf aij = ld4(&prow[tid]);
+      if (active) {
+        const cdf w0c = ld4(&w[0]);
+        aij = c_sub(aij, c_add(c_conj(ld4(&w[tid])), c_mul(w0c, c_conj(ld4(&v[tid])))));
       }
+      st4(&x[tid], aij);
+      if (tid >= 2) s2n.re = df_add(df_mul(aij.re, aij.re), df_mul(aij.im, aij.im));
     }
-    __syncthreads();
+    xn2 = block_sum_all(s2n, red_n).re;
   }
   if (crank == 0 && tid == 0) a.d[n - 1] = dpack(ld4(&x[0]).re);
   cl.sync();  // no CTA leaves while others may still read its shared memory
@@ -358,7 +376,7 @@ __global__ void __launch_bounds__(TDC_THREADS, 1) tridiag_cluster_kernel(const T
 
 static size_t tdc_smem(int n) {
   const int R = (n + TDC_CTAS - 1) / TDC_CTAS;
-  return sizeof(float4) * ((size_t)R * n + 3 * (size_t)n + 2 * (size_t)R + 3);
+  return sizeof(float4) * ((size_t)R * n + 3 * (size_t)n + 2 * (size_t)R);
 }
 
 static cudaLaunchConfig_t tdc_cfg(size_t smem, cudaStream_t st, cudaLaunchAttribute* attr) {
@@ -455,46 +473,61 @@ __global__ void td_bounds_kernel(int n, const float2* __restrict__ d, const floa
   }
 }
 
-// number of eigenvalues of T below x (Sturm count on the LDL^T pivots)
-__device__ __forceinline__ int sturm_count(int n, const float2* __restrict__ d, const float2* __restrict__ e2,
-                                           dfl x, float pivmin) {
+// number of eigenvalues of T below x (Sturm count on the LDL^T pivots); d, e2 in shared memory
+__device__ __forceinline__ int sturm_count(int n, const float2* d, const float2* e2, dfl x, float pivmin) {
   dfl q = df_sub(dload(d[0]), x);
   if (fabsf(q.hi) <= pivmin) q = {-pivmin, 0.f};
   int cnt = q.hi < 0.f;
   for (int i = 1; i < n; ++i) {
-    q = df_sub(df_sub(dload(d[i]), x), df_div(dload(e2[i - 1]), q));
+    q = df_sub(df_sub(dload(d[i]), x), df_mul(dload(e2[i - 1]), df_rcp(q)));
     if (fabsf(q.hi) <= pivmin) q = {-pivmin, 0.f};
     cnt += q.hi < 0.f;
   }
   return cnt;
 }
 
-// Eigenvalue t0 + blockIdx.x (ascending order), one warp each: multisection with 32 points a
-// round (5 bits) to an absolute width of 2^-46 ||T||.
-__global__ void __launch_bounds__(32) td_bisect_kernel(int n, int t0, const float2* __restrict__ d,
-                                                       const float2* __restrict__ e2,
-                                                       const float2* __restrict__ info,
-                                                       const double* __restrict__ scale,
-                                                       float2* __restrict__ lam_scaled,
-                                                       double* __restrict__ lam_out) {
-  const int g = blockIdx.x, lane = threadIdx.x;
+// Eigenvalue t0 + blockIdx.x (ascending order), one CTA of TB_THREADS each: multisection with
+// TB_THREADS points a round (8 bits) to an absolute width of 2^-46 ||T||, six rounds from the
+// Gershgorin interval.  Dynamic shared memory: d and e2 (2 n float2).
+constexpr int TB_THREADS = 256;
+
+__global__ void __launch_bounds__(TB_THREADS) td_bisect_kernel(int n, int t0, const float2* __restrict__ d,
+                                                               const float2* __restrict__ e2,
+                                                               const float2* __restrict__ info,
+                                                               const double* __restrict__ scale,
+                                                               float2* __restrict__ lam_scaled,
+                                                               double* __restrict__ lam_out) {
+  extern __shared__ float2 bsm[];
+  float2* sd = bsm;
+  float2* se2 = bsm + n;
+  __shared__ int wfirst[2][TB_THREADS / 32];
+  const int g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int t = t0 + g;
+  for (int i = tid; i < n; i += TB_THREADS) {
+    sd[i] = d[i];
+    if (i < n - 1) se2[i] = e2[i];
+  }
+  __syncthreads();
   dfl lo = dload(info[0]), hi = dload(info[1]);
   const float tol = 0x1.0p-46f * info[2].x + info[3].x;
   const float pivmin = info[3].x;
-  const dfl inv33 = df_div(df_f(1.f), df_f(33.f));
+  const dfl inv = df_div(df_f(1.f), df_f((float)(TB_THREADS + 1)));
   for (int it = 0; it < 24 && df_sub(hi, lo).hi > tol; ++it) {
-    const dfl step = df_mul(df_sub(hi, lo), inv33);
-    const int cnt = sturm_count(n, d, e2, df_add(lo, df_mul_f(step, (float)(lane + 1))), pivmin);
+    const dfl step = df_mul(df_sub(hi, lo), inv);
+    const int cnt = sturm_count(n, sd, se2, df_add(lo, df_mul_f(step, (float)(tid + 1))), pivmin);
     // the first point whose count exceeds t bounds the eigenvalue from above
     const unsigned above = __ballot_sync(0xffffffffu, cnt > t);
-    const int first = above ? __ffs(above) - 1 : 32;
+    if (lane == 0) wfirst[it & 1][warp] = above ? warp * 32 + __ffs(above) - 1 : TB_THREADS;
+    __syncthreads();
+    int first = TB_THREADS;
+#pragma unroll
+    for (int w = 0; w < TB_THREADS / 32; ++w) first = min(first, wfirst[it & 1][w]);
     const dfl nlo = first == 0 ? lo : df_add(lo, df_mul_f(step, (float)first));
-    const dfl nhi = first == 32 ? hi : df_add(lo, df_mul_f(step, (float)(first + 1)));
+    const dfl nhi = first == TB_THREADS ? hi : df_add(lo, df_mul_f(step, (float)(first + 1)));
     lo = nlo;
     hi = nhi;
   }
-  if (lane == 0) {
+  if (tid == 0) {
     const dfl l = df_mul_f(df_add(lo, hi), 0.5f);
     if (lam_scaled) lam_scaled[g] = dpack(l);
     if (lam_out) lam_out[g] = df_to(l) / *scale;
@@ -513,11 +546,13 @@ __device__ __forceinline__ float hash_unit(uint64_t t, uint64_t i) {
 // One warp per run of eigenvalues closer than 1e-10 ||T|| (the block of the run's first index
 // does the work; the others leave): lane 0 runs the serial pivoted LU and the triangular
 // solves in shared memory, the warp normalises and orthogonalises each new vector against the
-// run's earlier ones (modified Gram-Schmidt).  Shared memory: 6 n float2.
+// run's earlier ones (modified Gram-Schmidt).  Shared memory: 6 n float2, plus 2 n for copies
+// of d and e when they fit (stage != 0).
 __global__ void __launch_bounds__(32) td_inviter_kernel(int n, int r, const float2* __restrict__ d,
                                                         const float2* __restrict__ e,
                                                         const float2* __restrict__ lam,
-                                                        const float2* __restrict__ info, float2* __restrict__ Z) {
+                                                        const float2* __restrict__ info, float2* __restrict__ Z,
+                                                        int stage) {
   extern __shared__ float2 ism[];
   float2* u1i = ism;  // 1 / pivot
   float2* u2 = u1i + n;
@@ -525,6 +560,8 @@ __global__ void __launch_bounds__(32) td_inviter_kernel(int n, int r, const floa
   float2* lm = u3 + n;
   float2* sw = lm + n;  // .x = 1: rows i, i+1 swapped at step i
   float2* z = sw + n;
+  float2* sd = stage ? z + n : nullptr;
+  float2* se = stage ? sd + n : nullptr;
   const int j0 = blockIdx.x, lane = threadIdx.x;
   const float tnorm = info[2].x;
   const float ctol = 1e-10f * tnorm;
@@ -532,17 +569,26 @@ __global__ void __launch_bounds__(32) td_inviter_kernel(int n, int r, const floa
   int j1 = j0 + 1;
   while (j1 < r && df_sub(dload(lam[j1]), dload(lam[j1 - 1])).hi < ctol) ++j1;
   const float tiny = 0x1.0p-46f * tnorm + info[3].x;
+  if (stage) {
+    for (int i = lane; i < n; i += 32) {
+      sd[i] = d[i];
+      se[i] = i < n - 1 ? e[i] : make_float2(0.f, 0.f);
+    }
+    __syncwarp();
+  }
+  const float2* dd = stage ? sd : d;
+  const float2* ee = stage ? se : e;
   for (int j = j0; j < j1; ++j) {
     const dfl lj = dload(lam[j]);
     if (lane == 0) {
       // pivoted LU of T - lj I
-      dfl ca = df_sub(dload(d[0]), lj), cc = n > 1 ? dload(e[0]) : df_f(0.f);
+      dfl ca = df_sub(dload(dd[0]), lj), cc = dload(ee[0]);
       for (int i = 0; i < n - 1; ++i) {
-        const dfl b = dload(e[i]);
-        const dfl na = df_sub(dload(d[i + 1]), lj), nc = (i + 1 < n - 1) ? dload(e[i + 1]) : df_f(0.f);
+        const dfl b = dload(ee[i]);
+        const dfl na = df_sub(dload(dd[i + 1]), lj), nc = (i + 1 < n - 1) ? dload(ee[i + 1]) : df_f(0.f);
         if (fabsf(ca.hi) >= fabsf(b.hi)) {
           const dfl piv = fabsf(ca.hi) > tiny ? ca : df_f(ca.hi >= 0.f ? tiny : -tiny);
-          const dfl pinv = df_div(df_f(1.f), piv);
+          const dfl pinv = df_rcp(piv);
           const dfl l = df_mul(b, pinv);
           lm[i] = dpack(l);
           sw[i] = make_float2(0.f, 0.f);
@@ -552,7 +598,7 @@ __global__ void __launch_bounds__(32) td_inviter_kernel(int n, int r, const floa
           ca = df_sub(na, df_mul(l, cc));
           cc = nc;
         } else {
-          const dfl binv = df_div(df_f(1.f), b);
+          const dfl binv = df_rcp(b);
           const dfl l = df_mul(ca, binv);
           lm[i] = dpack(l);
           sw[i] = make_float2(1.f, 0.f);
@@ -564,7 +610,7 @@ __global__ void __launch_bounds__(32) td_inviter_kernel(int n, int r, const floa
         }
       }
       const dfl last = fabsf(ca.hi) > tiny ? ca : df_f(ca.hi >= 0.f ? tiny : -tiny);
-      u1i[n - 1] = dpack(df_div(df_f(1.f), last));
+      u1i[n - 1] = dpack(df_rcp(last));
     }
     for (int i = lane; i < n; i += 32) z[i] = make_float2(hash_unit((uint64_t)(j + 1), (uint64_t)i), 0.f);
     __syncwarp();
@@ -689,18 +735,26 @@ __global__ void __launch_bounds__(256) td_wy_t_kernel(int n, const float4* __res
 }
 
 // V[j] = Q_H z_j applying the WY blocks last to first: u <- u - Y (T (Y^H u)).  One CTA per
-// eigenvector, the vector in shared memory; written as complex128 rows of length n.
-__global__ void __launch_bounds__(256, 2) td_backxform_wy_kernel(int n, int r, const float4* __restrict__ refl,
-                                                             const float4* __restrict__ Tb,
-                                                             const float4* __restrict__ Yt,
-                                                             const float2* __restrict__ Z, double2* __restrict__ V) {
+// eigenvector, the vector in shared memory; written as complex128 rows of length n.  s = Y^H u
+// with lane = reflector and the warps over rows (each row of the row-major copy is one 512-byte
+// read), t = T s with a warp per row of T, and the update with a thread per row reading the
+// reflectors column-major (consecutive rows are consecutive addresses).
+constexpr int BX_THREADS = 256;
+
+__global__ void __launch_bounds__(BX_THREADS, 2) td_backxform_wy_kernel(int n, int r, const float4* __restrict__ refl,
+                                                                    const float4* __restrict__ Tb,
+                                                                    const float4* __restrict__ Yt,
+                                                                    const float2* __restrict__ Z,
+                                                                    double2* __restrict__ V) {
+  constexpr int NW = BX_THREADS / 32;
   extern __shared__ float4 usm2[];
+  __shared__ float4 part[NW][WY_B];
   __shared__ float4 sv[WY_B], tv[WY_B];
   const int j = blockIdx.x;
   if (j >= r) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   float4* u = usm2;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int i = tid; i < n; i += BX_THREADS) {
     const float2 zi = Z[(size_t)j * n + i];
     u[i] = make_float4(zi.x, zi.y, 0.f, 0.f);
   }
@@ -708,43 +762,63 @@ __global__ void __launch_bounds__(256, 2) td_backxform_wy_kernel(int n, int r, c
   const int nblk = (n - 1 + WY_B - 1) / WY_B;
   for (int blk = nblk - 1; blk >= 0; --blk) {
     const int k0 = blk * WY_B, nb = min(WY_B, n - 1 - k0);
-    // s = Y^H u (warp per reflector, lanes over rows)
-    for (int q = warp; q < WY_B; q += nwarps) {
+    const float4* Y = Yt + (size_t)blk * n * WY_B;  // zero where g <= k0 + lane
+    // s = Y^H u
+    {
       cdf acc = c_zero();
-      if (q < nb) {
-        const int k = k0 + q;
-        for (int g = k + 1 + lane; g < n; g += 32) acc = c_add(acc, c_mulc(ld4(&refl[(size_t)k * n + (g - k - 1)]), ld4(&u[g])));
-        acc = c_warp_sum(acc);
+      int g = k0 + 1 + warp;
+#pragma unroll 1
+      for (; g + 3 * NW < n; g += 4 * NW) {
+        const float4 y0 = Y[(size_t)g * WY_B + lane], y1 = Y[(size_t)(g + NW) * WY_B + lane];
+        const float4 y2 = Y[(size_t)(g + 2 * NW) * WY_B + lane], y3 = Y[(size_t)(g + 3 * NW) * WY_B + lane];
+        c_acc_mulc(acc, {{y0.x, y0.y}, {y0.z, y0.w}}, ld4(&u[g]));
+        c_acc_mulc(acc, {{y1.x, y1.y}, {y1.z, y1.w}}, ld4(&u[g + NW]));
+        c_acc_mulc(acc, {{y2.x, y2.y}, {y2.z, y2.w}}, ld4(&u[g + 2 * NW]));
+        c_acc_mulc(acc, {{y3.x, y3.y}, {y3.z, y3.w}}, ld4(&u[g + 3 * NW]));
       }
-      if (lane == 0) st4(&sv[q], acc);
+      for (; g < n; g += NW) c_acc_mulc(acc, ld4(&Y[(size_t)g * WY_B + lane]), ld4(&u[g]));
+      st4(&part[warp][lane], acc);
     }
     __syncthreads();
-    // t = T s (upper triangular)
     if (warp == 0) {
-      cdf acc = c_zero();
-      const float4* Trow = Tb + (size_t)blk * WY_B * WY_B + (size_t)lane * WY_B;
-      for (int c = lane; c < nb; ++c) acc = c_add(acc, c_mul(ld4(&Trow[c]), ld4(&sv[c])));
-      st4(&tv[lane], acc);
+      cdf sacc = ld4(&part[0][lane]);
+#pragma unroll
+      for (int w = 1; w < NW; ++w) sacc = c_add(sacc, ld4(&part[w][lane]));
+      st4(&sv[lane], sacc);
     }
     __syncthreads();
-    // u[g] -= sum_j Y[g][j] t_j for the rows the block touches
-    const float4* Y = Yt + (size_t)blk * n * WY_B;
-    for (int g = k0 + 1 + threadIdx.x; g < n; g += blockDim.x) {
-      // four independent partial sums (the rows of Y are zero past nb)
-      cdf a0 = c_zero(), a1 = c_zero(), a2 = c_zero(), a3 = c_zero();
-      const float4* yg = Y + (size_t)g * WY_B;
-#pragma unroll 2
-      for (int c = 0; c < WY_B; c += 4) {
-        a0 = c_add(a0, c_mul(ld4(&yg[c]), ld4(&tv[c])));
-        a1 = c_add(a1, c_mul(ld4(&yg[c + 1]), ld4(&tv[c + 1])));
-        a2 = c_add(a2, c_mul(ld4(&yg[c + 2]), ld4(&tv[c + 2])));
-        a3 = c_add(a3, c_mul(ld4(&yg[c + 3]), ld4(&tv[c + 3])));
+    // t = T s (T upper triangular): warp per row, lanes over columns
+    {
+      const float4* Tblk = Tb + (size_t)blk * WY_B * WY_B;
+      for (int i = warp; i < WY_B; i += NW) {
+        cdf pr = c_zero();
+        if (i < nb && lane >= i && lane < nb) pr = c_mul(ld4(&Tblk[i * WY_B + lane]), ld4(&sv[lane]));
+        pr = c_warp_sum(pr);
+        if (lane == 0) st4(&tv[i], pr);
       }
-      st4(&u[g], c_sub(ld4(&u[g]), c_add(c_add(a0, a1), c_add(a2, a3))));
+    }
+    __syncthreads();
+    // u[g] -= sum_c Y[g][c] t_c for the rows the block touches (Y[g][c] = v_{k0+c}[g], g > k0 + c)
+    for (int g = k0 + 1 + tid; g < n; g += BX_THREADS) {
+      const int cmax = min(nb, g - k0);
+      cdf acc = c_zero();
+      const float4* col = refl + (size_t)k0 * n + (g - k0 - 1);  // v_{k0+c}[g] = col[c (n - 1)]
+      int c = 0;
+#pragma unroll 1
+      for (; c + 3 < cmax; c += 4) {
+        const float4 y0 = col[(size_t)c * (n - 1)], y1 = col[(size_t)(c + 1) * (n - 1)];
+        const float4 y2 = col[(size_t)(c + 2) * (n - 1)], y3 = col[(size_t)(c + 3) * (n - 1)];
+        c_acc_mul(acc, {{y0.x, y0.y}, {y0.z, y0.w}}, ld4(&tv[c]));
+        c_acc_mul(acc, {{y1.x, y1.y}, {y1.z, y1.w}}, ld4(&tv[c + 1]));
+        c_acc_mul(acc, {{y2.x, y2.y}, {y2.z, y2.w}}, ld4(&tv[c + 2]));
+        c_acc_mul(acc, {{y3.x, y3.y}, {y3.z, y3.w}}, ld4(&tv[c + 3]));
+      }
+      for (; c < cmax; ++c) c_acc_mul(acc, ld4(&col[(size_t)c * (n - 1)]), ld4(&tv[c]));
+      st4(&u[g], c_sub(ld4(&u[g]), acc));
     }
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) V[(size_t)j * n + i] = c_to(ld4(&u[i]));
+  for (int i = tid; i < n; i += BX_THREADS) V[(size_t)j * n + i] = c_to(ld4(&u[i]));
 }
 
 // J = trace(G) - sum of the top r eigenvalues (the tail energy of Eq. 1); trace in FP64
@@ -844,15 +918,21 @@ static hicu_status finish_principal(hicu_handle* h, int n, int r, const double2*
   }
   // 2. eigenvalues (top r; all n when requested)
   HICU_LAUNCH(h, K_EIG, st, td_bounds_kernel<<<1, 256, 0, st>>>(n, d, e, e2, info));
-  HICU_LAUNCH(h, K_EIG, st, td_bisect_kernel<<<r, 32, 0, st>>>(n, n - r, d, e2, info, scale, lam, eig_top));
+  const size_t bsm_bytes = sizeof(float2) * 2 * (size_t)n;
+  {
+    cudaError_t e0 = allow_max_dynamic_smem((const void*)td_bisect_kernel);
+    if (e0 != cudaSuccess) return cuda_error(h, e0, "bisection smem");
+  }
+  HICU_LAUNCH(h, K_EIG, st, td_bisect_kernel<<<r, TB_THREADS, bsm_bytes, st>>>(n, n - r, d, e2, info, scale, lam, eig_top));
   if (eig_all)
-    HICU_LAUNCH(h, K_EIG, st, td_bisect_kernel<<<n, 32, 0, st>>>(n, 0, d, e2, info, scale, nullptr, eig_all));
+    HICU_LAUNCH(h, K_EIG, st, td_bisect_kernel<<<n, TB_THREADS, bsm_bytes, st>>>(n, 0, d, e2, info, scale, nullptr, eig_all));
   // 3. eigenvectors of T, 4. back-transformation
   {
-    const size_t ism = sizeof(float2) * 6 * (size_t)n;
+    const int stage = 8 * (size_t)n * sizeof(float2) <= 200 * 1024;
+    const size_t ism = sizeof(float2) * (stage ? 8 : 6) * (size_t)n;
     cudaError_t e0 = allow_max_dynamic_smem((const void*)td_inviter_kernel);
     if (e0 != cudaSuccess) return cuda_error(h, e0, "inverse iteration smem");
-    HICU_LAUNCH(h, K_EIG, st, td_inviter_kernel<<<r, 32, ism, st>>>(n, r, d, e, lam, info, Z));
+    HICU_LAUNCH(h, K_EIG, st, td_inviter_kernel<<<r, 32, ism, st>>>(n, r, d, e, lam, info, Z, stage));
   }
   {
     // apply the compact WY blocks, one CTA per eigenvector, once the factors are ready
@@ -862,7 +942,7 @@ static hicu_status finish_principal(hicu_handle* h, int n, int r, const double2*
     cudaError_t e0 = allow_max_dynamic_smem((const void*)td_backxform_wy_kernel);
     if (e0 != cudaSuccess) return cuda_error(h, e0, "backxform smem");
     HICU_LAUNCH(h, K_EIG, st,
-                td_backxform_wy_kernel<<<r, 256, usm, st>>>(n, r, refl, Tb, Yt, Z, (double2*)Vout));
+                td_backxform_wy_kernel<<<r, BX_THREADS, usm, st>>>(n, r, refl, Tb, Yt, Z, (double2*)Vout));
   }
   if (J) HICU_LAUNCH(h, K_MISC, st, td_tail_kernel<<<1, 256, 0, st>>>(n, r, G, eig_top, J));
   return cuda_error(h, cudaGetLastError(), "principal subspace");
