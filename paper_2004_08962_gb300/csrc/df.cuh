@@ -90,7 +90,7 @@ __device__ __forceinline__ dfl df_sqrt(dfl a) {
   const float p = __fmul_rn(x, x);
   const float e = __fmaf_rn(x, x, -p);
   const dfl res = df_sub(a, df_fast(p, e));
-  return df_fast(x, __fdiv_rn(res.hi, __fmul_rn(2.f, x)));
+  return df_fast(x, __fmul_rn(res.hi, rcp_approx(__fmul_rn(2.f, x))));  // the correction needs ~20 bits
 }
 
 __device__ __forceinline__ dfl df_shfl_xor(dfl a, int o) {

@@ -55,33 +55,6 @@ struct TdArgs {
 __device__ __forceinline__ float2 dpack(dfl a) { return make_float2(a.hi, a.lo); }
 __device__ __forceinline__ dfl dload(float2 a) { return {a.x, a.y}; }
 
-// CTA sum of a complex double-float, result in every thread: warp shuffles, then warp 0 over
-// the warp partials (two __syncthreads)
-__device__ inline cdf block_sum_c2(cdf a, float4* sh, float4* out) {
-  a = c_warp_sum(a);
-  const int wi = threadIdx.x >> 5, l = threadIdx.x & 31, nwp = blockDim.x >> 5;
-  if (l == 0) st4(&sh[wi], a);
-  __syncthreads();
-  if (wi == 0) {
-    cdf t = l < nwp ? ld4(&sh[l]) : c_zero();
-    t = c_warp_sum(t);
-    if (l == 0) st4(out, t);
-  }
-  __syncthreads();
-  return ld4(out);
-}
-
-// CTA sum of a complex double-float, result in every thread with one __syncthreads: every warp
-// reduces the warp partials itself (the butterfly gives bitwise the same sum in every lane, as
-// df_add is commutative).  sh (one slot per warp) may be reused after the next __syncthreads.
-__device__ inline cdf block_sum_all(cdf a, float4* sh) {
-  a = c_warp_sum(a);
-  const int wi = threadIdx.x >> 5, l = threadIdx.x & 31, nwp = blockDim.x >> 5;
-  if (l == 0) st4(&sh[wi], a);
-  __syncthreads();
-  return c_warp_sum(l < nwp ? ld4(&sh[l]) : c_zero());
-}
-
 // One barrier per reflector.  Global row g is owned by CTA g mod G for the whole run and, with
 // ROWS_IN_SMEM, held in that CTA's shared memory (local row g / G); it is updated in place by its
 // owner only, except row k+1, the next pivot row: nobody writes it during step k, its owner
@@ -89,18 +62,22 @@ __device__ inline cdf block_sum_all(cdf a, float4* sh) {
 // them and v, w, so the next Householder vector needs no second barrier.  w0, the partial sums
 // and the published row alternate between two buffers: a CTA can start step k+1 while others
 // still read step k's, but cannot reach step k+2 before every CTA has passed step k+1's barrier.
+// Within a step (as in the one-cluster form below): the own rows' sums against conj(x) run on
+// warps 0..nw-2 while warp nw-1 forms the Householder scalars; v, w0 and the CTA's partial sum
+// follow; after the grid barrier every warp sums the G partials itself.
 template <bool ROWS_IN_SMEM>
 __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
   extern __shared__ float4 tsm[];
   const int n = a.n;
   const int G = gridDim.x, c = blockIdx.x;
   const int R = (n + G - 1) / G;  // rows per CTA
-  float4* x = tsm;          // [n] current pivot row k: x[j] = A[k][k + j]
-  float4* v = tsm + n;      // [n]
-  float4* w = tsm + 2 * n;  // [n]
-  float4* rows = tsm + 3 * n;  // [R][n] own rows (ROWS_IN_SMEM)
-  __shared__ float4 red[TD_THREADS / 32];
-  __shared__ float4 bsum;
+  float4* x = tsm;             // [n] current pivot row k: x[j] = A[k][k + j]
+  float4* v = x + n;           // [n]
+  float4* w = v + n;           // [n]
+  float4* srow = w + n;        // [2R] s_i of the own rows, then their entries A_i0
+  float4* rows = srow + 2 * R;  // [R][n] own rows (ROWS_IN_SMEM)
+  float2* xsq = (float2*)(rows + (ROWS_IN_SMEM ? (size_t)R * n : 0));  // [n] squares of x
+  __shared__ float4 hs[2];     // tau, 1 / (x0 - beta)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = TD_THREADS / 32;
   auto row_of = [&](int g) -> float4* {
     return ROWS_IN_SMEM ? rows + (size_t)(g / G) * n : a.A + (size_t)g * n;
@@ -111,107 +88,131 @@ __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
       const int lr = idx / n, g = lr * G + c;
       if (g < n) rows[idx] = a.A[(size_t)g * n + (idx - lr * n)];
     }
-  for (int j = tid; j < n; j += TD_THREADS) x[j] = a.A[j];
+  for (int j = tid; j < n; j += TD_THREADS) {
+    const float4 xj = a.A[j];
+    x[j] = xj;
+    xsq[j] = dpack(df_add(df_mul({xj.x, xj.y}, {xj.x, xj.y}), df_mul({xj.z, xj.w}, {xj.z, xj.w})));
+  }
   __syncthreads();
   for (int k = 0; k < n - 1; ++k) {
     const int m = n - k - 1;
+    const int par = k & 1;
     // --- the owner of row k+1 publishes it (stored values, columns k+1 ..)
-    float4* pub = a.prow + (k & 1) * n;
+    float4* pub = a.prow + par * n;
     if ((k + 1) % G == c) {
       const float4* src = row_of(k + 1) + (k + 1);
       for (int j = tid; j < m; j += TD_THREADS) pub[j] = src[j];
     }
-    // --- Householder vector of column k = conj(row k right of the diagonal), in every CTA
-    cdf s2 = c_zero();
-    for (int j = 1 + tid; j < m; j += TD_THREADS) {
-      const cdf xj = ld4(&x[1 + j]);
-      s2.re = df_add(s2.re, df_add(df_mul(xj.re, xj.re), df_mul(xj.im, xj.im)));
+    const int i0 = ((c - (k + 1)) % G + G) % G;  // first relative row owned by this CTA
+    const int nown = i0 < m ? (m - 1 - i0) / G + 1 : 0;
+    // --- 1. row sums against conj(x) / Householder scalars
+    if (warp < nw - 1) {
+      for (int q = warp; q < nown; q += nw - 1) {
+        const float4* row = row_of(k + 1 + i0 + q * G) + (k + 1);
+        cdf y = c_zero();
+        for (int j = 1 + lane; j < m; j += 32) c_acc_mul(y, ld4(&row[j]), c_conj(ld4(&x[1 + j])));
+        y = c_warp_sum(y);
+        if (lane == 0) {
+          st4(&srow[q], y);
+          srow[R + q] = row[0];
+        }
+      }
+    } else {
+      dfl t2 = df_f(0.f);
+      for (int j = 2 + lane; j <= m; j += 32) t2 = df_add(t2, dload(xsq[j]));
+      const dfl xn2 = df_warp_sum(t2);
+      const cdf x0 = c_conj(ld4(&x[1]));
+      cdf tau = c_zero(), scale = c_zero();
+      dfl beta = x0.re;
+      if (!(xn2.hi == 0.f && x0.im.hi == 0.f)) {
+        const dfl nrm = df_sqrt(df_add(df_add(df_mul(x0.re, x0.re), df_mul(x0.im, x0.im)), xn2));
+        beta = x0.re.hi >= 0.f ? df_neg(nrm) : nrm;
+        const dfl rb = df_rcp(beta);
+        tau.re = df_sub(df_f(1.f), df_mul(x0.re, rb));  // (beta - x0.re) / beta
+        tau.im = df_neg(df_mul(x0.im, rb));
+        const cdf den = {df_sub(x0.re, beta), x0.im};  // v = x / (x0 - beta)
+        const dfl dd = df_add(df_mul(den.re, den.re), df_mul(den.im, den.im));
+        const dfl rd = df_rcp(dd);
+        scale.re = df_mul(den.re, rd);
+        scale.im = df_neg(df_mul(den.im, rd));
+      }
+      if (lane == 0) {
+        st4(&hs[0], tau);
+        st4(&hs[1], scale);
+        if (c == 0) {
+          a.d[k] = dpack(ld4(&x[0]).re);
+          a.e[k] = dpack(beta);
+          st4(&a.tau[k], tau);
+        }
+      }
     }
-    const dfl xn2 = block_sum_c2(s2, red, &bsum).re;
-    const cdf x0 = c_conj(ld4(&x[1]));
-    cdf tau = c_zero(), scale = c_zero();
-    dfl beta = x0.re;
-    if (!(xn2.hi == 0.f && x0.im.hi == 0.f)) {
-      const dfl nrm = df_sqrt(df_add(df_add(df_mul(x0.re, x0.re), df_mul(x0.im, x0.im)), xn2));
-      beta = x0.re.hi >= 0.f ? df_neg(nrm) : nrm;
-      const dfl rb = df_rcp(beta);
-      tau.re = df_sub(df_f(1.f), df_mul(x0.re, rb));  // (beta - x0.re) / beta
-      tau.im = df_neg(df_mul(x0.im, rb));
-      const cdf den = {df_sub(x0.re, beta), x0.im};  // v = x / (x0 - beta)
-      const dfl dd = df_add(df_mul(den.re, den.re), df_mul(den.im, den.im));
-      const dfl rd = df_rcp(dd);
-      scale.re = df_mul(den.re, rd);
-      scale.im = df_neg(df_mul(den.im, rd));
-    }
+    __syncthreads();
+    // --- 2. v; w0 = tau (A_i0 + s_i / (x0 - beta)) of the own rows and the CTA's partial sum
+    const cdf tau = ld4(&hs[0]), scale = ld4(&hs[1]);
     const bool active = !(tau.re.hi == 0.f && tau.im.hi == 0.f);
-    if (c == 0 && tid == 0) {
-      a.d[k] = dpack(ld4(&x[0]).re);
-      a.e[k] = dpack(beta);
-      st4(&a.tau[k], tau);
-    }
     for (int j = tid; j < m; j += TD_THREADS) {
-      cdf vj;
-      if (j == 0) vj = {{1.f, 0.f}, {0.f, 0.f}};
-      else vj = active ? c_mul(c_conj(ld4(&x[1 + j])), scale) : c_zero();
+      const cdf vj = j == 0 ? cdf{{1.f, 0.f}, {0.f, 0.f}} : c_mul(c_conj(ld4(&x[1 + j])), scale);
       st4(&v[j], vj);
       if (c == 0) st4(&a.refl[(long long)k * n + j], vj);
     }
-    __syncthreads();
-    // --- w0 = tau A v on this CTA's rows (relative row i is global row k+1+i)
-    float4* wg = a.w + (k & 1) * n;
-    float4* pg = a.part + (k & 1) * G;
-    const int i0 = ((c - (k + 1)) % G + G) % G;  // first relative row owned by this CTA
-    cdf pp = c_zero();
-    if (active) {
-      for (int i = i0 + G * warp; i < m; i += G * nw) {
-        const float4* row = row_of(k + 1 + i) + (k + 1);
-        cdf y0 = c_zero(), y1 = c_zero();
-        int j = lane;
-        for (; j + 32 < m; j += 64) {
-          y0 = c_add(y0, c_mul(ld4(&row[j]), ld4(&v[j])));
-          y1 = c_add(y1, c_mul(ld4(&row[j + 32]), ld4(&v[j + 32])));
-        }
-        if (j < m) y0 = c_add(y0, c_mul(ld4(&row[j]), ld4(&v[j])));
-        const cdf y = c_warp_sum(c_add(y0, y1));
-        if (lane == 0) {
-          const cdf w0 = c_mul(tau, y);
-          st4(&wg[i], w0);
-          pp = c_add(pp, c_mulc(w0, ld4(&v[i])));
-        }
+    float4* wg = a.w + par * n;
+    float4* pg = a.part + par * G;
+    if (warp == 0) {
+      cdf pc = c_zero();
+      for (int q = lane; q < nown; q += 32) {
+        const int i = i0 + q * G;
+        const cdf w0 = c_mul(tau, c_add(ld4(&srow[R + q]), c_mul(scale, ld4(&srow[q]))));
+        st4(&wg[i], w0);
+        const cdf vi = i == 0 ? cdf{{1.f, 0.f}, {0.f, 0.f}} : c_mul(c_conj(ld4(&x[1 + i])), scale);
+        pc = c_add(pc, c_mulc(w0, vi));
       }
-    }
-    {
-      const cdf ps = block_sum_c2(pp, red, &bsum);
-      if (tid == 0) st4(&pg[c], ps);
+      pc = c_warp_sum(pc);
+      if (lane == 0) st4(&pg[c], pc);
     }
     if (!grid_sync(a.gs, epoch)) return;
-    // --- alpha = -tau/2 (w0^H v); w = w0 + alpha v; rank-2 update of this CTA's rows but row k+1
-    if (active) {
+    // --- 3. alpha = -tau/2 sum conj(w0) v (every warp sums the G partials); w = w0 + alpha v
+    {
       cdf sp = c_zero();
-      for (int q = tid; q < G; q += TD_THREADS) sp = c_add(sp, ld4(&pg[q]));
-      const cdf ssum = block_sum_c2(sp, red, &bsum);
+      for (int q = lane; q < G; q += 32) sp = c_add(sp, ld4(&pg[q]));
+      const cdf ssum = c_warp_sum(sp);
       const cdf htau = {df_mul_f(tau.re, -0.5f), df_mul_f(tau.im, -0.5f)};
       const cdf alpha = c_mul(htau, ssum);
       for (int j = tid; j < m; j += TD_THREADS) st4(&w[j], c_add(ld4(&wg[j]), c_mul(alpha, ld4(&v[j]))));
-      __syncthreads();
-      for (int i = i0 + G * warp; i < m; i += G * nw) {
+    }
+    __syncthreads();
+    // --- 4. rank-2 update of the own rows but row k+1: A_ij -= v_i conj(w_j) + w_i conj(v_j)
+    if (active) {
+      const int tot = nown * m;
+      const float rm = 1.f / (float)m;
+      for (int idx = tid; idx < tot; idx += TD_THREADS) {
+        // idx / m: exact while nown m < 2^21 (the rounding error of the product stays below the
+        // distance 0.5 / m of (idx + 0.5) / m from an integer)
+        const int q = (int)__fmul_rn((float)idx + 0.5f, rm);
+        const int j = idx - q * m;
+        const int i = i0 + q * G;
         if (i == 0) continue;
-        float4* row = row_of(k + 1 + i) + (k + 1);
-        const cdf vi = ld4(&v[i]), wi = ld4(&w[i]);
-        for (int j = lane; j < m; j += 32) {
-          // A_ij -= v_i conj(w_j) + w_i conj(v_j)
-          const cdf t = c_add(c_mul(vi, c_conj(ld4(&w[j]))), c_mul(wi, c_conj(ld4(&v[j]))));
-          st4(&row[j], c_sub(ld4(&row[j]), t));
-        }
+        float4* aij = row_of(k + 1 + i) + (k + 1) + j;
+        const cdf vi = ld4(&v[i]), wi = ld4(&w[i]), wj = ld4(&w[j]), vjj = ld4(&v[j]);
+        cdf acc = ld4(aij);
+        df_acc_mul(acc.re, df_neg(vi.re), wj.re);
+        df_acc_mul(acc.re, df_neg(vi.im), wj.im);
+        df_acc_mul(acc.re, df_neg(wi.re), vjj.re);
+        df_acc_mul(acc.re, df_neg(wi.im), vjj.im);
+        df_acc_mul(acc.im, df_neg(vi.im), wj.re);
+        df_acc_mul(acc.im, vi.re, wj.im);
+        df_acc_mul(acc.im, df_neg(wi.im), vjj.re);
+        df_acc_mul(acc.im, wi.re, vjj.im);
+        st4(aij, c_renorm(acc));
       }
     }
-    // --- the next pivot row k+1 (relative row 0: v_0 = 1), formed by every CTA
+    // the next pivot row k+1 (relative row 0: v_0 = 1), formed by every CTA, and its squares
     {
-      const cdf w0c = active ? ld4(&w[0]) : c_zero();
+      const cdf w0c = ld4(&w[0]);
       for (int j = tid; j < m; j += TD_THREADS) {
         cdf aij = ld4(&pub[j]);
         if (active) aij = c_sub(aij, c_add(c_conj(ld4(&w[j])), c_mul(w0c, c_conj(ld4(&v[j])))));
         st4(&x[j], aij);
+        xsq[j] = dpack(df_add(df_mul(aij.re, aij.re), df_mul(aij.im, aij.im)));
       }
     }
     __syncthreads();
@@ -224,10 +225,20 @@ __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
 // The same steps inside one thread-block cluster of TDC_CTAS CTAs: global row g lives in the
 // shared memory of CTA g mod TDC_CTAS (local row g / TDC_CTAS) for the whole run, w0 and the
 // partial sums stay in their producers' shared memory and are read through distributed shared
-// memory, and a step ends at the hardware cluster barrier (~0.5 us) instead of a grid barrier
-// and L2 round trips.  As in the grid form, the pivot row k+1 is never written during step k:
-// every CTA forms it from the owner's stored row (read remotely) and v, w.
-
+// memory, and a step ends at the hardware cluster barrier instead of a grid barrier and L2
+// round trips.  As in the grid form, the pivot row k+1 is never written during step k: every CTA
+// forms it from the owner's stored row (read remotely) and v, w.
+//
+// Per step, with v = conj(x_{1..m}) / (x0 - beta) (x the pivot row, v_0 = 1):
+//   1. warps 0..nw-2: s_i = sum_{j>=1} A_ij conj(x_{1+j}) for the own rows; warp nw-1 in the
+//      meantime the norm of the pivot row's tail (squares left by the previous step) and the
+//      Householder scalars tau, beta, 1 / (x0 - beta).  CTA barrier.
+//   2. v; w0_i = tau (A_i0 + s_i / (x0 - beta)) and the CTA's partial sum of conj(w0_i) v_i
+//      (warp 0).  Cluster barrier.
+//   3. every warp: the 16 partial sums (remote) -> alpha; w = w0 + alpha v with w0 read from the
+//      row owners, the next pivot row's stored values fetched at the same time.  CTA barrier.
+//   4. rank-2 update of the own rows but row k+1; the next pivot row and its squares.  CTA
+//      barrier.
 constexpr int TDC_CTAS = 16;
 constexpr int TDC_THREADS = 512;
 constexpr int TDC_MAX_N = 440;
@@ -252,7 +263,10 @@ __global__ void __launch_bounds__(TDC_THREADS, 1) tridiag_cluster_kernel(const T
   float4* v = x + n;                 // [n]
   float4* w = v + n;                 // [n]
   float4* w0loc = w + n;             // [2][R] w0 of own rows, by step parity
-  __shared__ float4 red_n[TDC_THREADS / 32], red_s[TDC_THREADS / 32];
+  float4* srow = w0loc + 2 * R;      // [R] s_i of own rows, then A_i0 in [R..2R)
+  float2* xsq = (float2*)(srow + 2 * R);  // [n] squares of the pivot row's entries (double-float)
+  __shared__ float4 partloc[2];      // the CTA's partial sum of conj(w0_i) v_i, by step parity
+  __shared__ float4 hs[3];           // tau, 1 / (x0 - beta), (beta, active)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = TDC_THREADS / 32;
   for (int idx = tid; idx < R * n; idx += TDC_THREADS) {
     const int lr = idx / n, j = idx - lr * n;
@@ -260,81 +274,102 @@ __global__ void __launch_bounds__(TDC_THREADS, 1) tridiag_cluster_kernel(const T
     if (g < n) rows[idx] = a.A[(size_t)g * n + j];
   }
   cl.sync();
-  // pivot row 0 and the squared norm of its entries 2.. (the Householder vector's tail)
-  cdf s2 = c_zero();
   {
     const float4* r0 = cl.map_shared_rank(rows, 0);
     for (int j = tid; j < n; j += TDC_THREADS) {
       const float4 xj = r0[j];
       x[j] = xj;
-      if (j >= 2) s2.re = df_add(s2.re, df_add(df_mul({xj.x, xj.y}, {xj.x, xj.y}), df_mul({xj.z, xj.w}, {xj.z, xj.w})));
+      xsq[j] = dpack(df_add(df_mul({xj.x, xj.y}, {xj.x, xj.y}), df_mul({xj.z, xj.w}, {xj.z, xj.w})));
     }
   }
-  dfl xn2 = block_sum_all(s2, red_n).re;
+  __syncthreads();
   for (int k = 0; k < n - 1; ++k) {
-    const int m = n - k - 1;
+    const int m = n - k - 1;  // m <= TDC_MAX_N - 1 < TDC_THREADS: one entry per thread below
     const int par = k & 1;
-    // --- Householder vector of column k (every CTA, from its copy of the pivot row)
-    const cdf x0 = c_conj(ld4(&x[1]));
-    cdf tau = c_zero(), scale = c_zero();
-    dfl beta = x0.re;
-    if (!(xn2.hi == 0.f && x0.im.hi == 0.f)) {
-      const dfl nrm = df_sqrt(df_add(df_add(df_mul(x0.re, x0.re), df_mul(x0.im, x0.im)), xn2));
-      beta = x0.re.hi >= 0.f ? df_neg(nrm) : nrm;
-      const dfl rb = df_rcp(beta);
-      tau.re = df_sub(df_f(1.f), df_mul(x0.re, rb));  // (beta - x0.re) / beta
-      tau.im = df_neg(df_mul(x0.im, rb));
-      const cdf den = {df_sub(x0.re, beta), x0.im};
-      const dfl dd = df_add(df_mul(den.re, den.re), df_mul(den.im, den.im));
-      const dfl rd = df_rcp(dd);
-      scale.re = df_mul(den.re, rd);
-      scale.im = df_neg(df_mul(den.im, rd));
-    }
-    const bool active = !(tau.re.hi == 0.f && tau.im.hi == 0.f);
-    if (crank == 0 && tid == 0) {
-      a.d[k] = dpack(ld4(&x[0]).re);
-      a.e[k] = dpack(beta);
-      st4(&a.tau[k], tau);
-    }
-    // m <= TDC_MAX_N - 1 < TDC_THREADS: one entry per thread
-    if (tid < m) {
-      cdf vj;
-      if (tid == 0) vj = {{1.f, 0.f}, {0.f, 0.f}};
-      else vj = active ? c_mul(c_conj(ld4(&x[1 + tid])), scale) : c_zero();
-      st4(&v[tid], vj);
-      if (crank == 0) st4(&a.refl[(long long)k * n + tid], vj);
-    }
-    __syncthreads();
-    // --- w0 = tau A v for the own trailing rows: global g = k+1 .. n-1 with g % nct == crank
     const int lr0 = (k + 1 - crank + nct - 1) / nct;  // first own local row with g >= k+1
     const int nown = lr0 < R ? R - lr0 - ((R - 1) * nct + crank >= n ? 1 : 0) : 0;
-    if (active) {
-      for (int q = warp; q < nown; q += nw) {
-        const int lr = lr0 + q;
-        const float4* row = rows + (size_t)lr * n + (k + 1);
+    // --- 1. row sums against conj(x) (warps 0..nw-2) / Householder scalars (warp nw-1)
+    if (warp < nw - 1) {
+      for (int q = warp; q < nown; q += nw - 1) {
+        const float4* row = rows + (size_t)(lr0 + q) * n + (k + 1);
         cdf y = c_zero();
-        for (int j = lane; j < m; j += 32) c_acc_mul(y, ld4(&row[j]), ld4(&v[j]));
+        for (int j = 1 + lane; j < m; j += 32) c_acc_mul(y, ld4(&row[j]), c_conj(ld4(&x[1 + j])));
         y = c_warp_sum(y);
-        if (lane == 0) st4(&w0loc[par * R + lr], c_mul(tau, y));
+        if (lane == 0) {
+          st4(&srow[q], y);
+          srow[R + q] = row[0];
+        }
+      }
+    } else {
+      dfl t2 = df_f(0.f);
+      for (int j = 2 + lane; j <= m; j += 32) t2 = df_add(t2, dload(xsq[j]));
+      const dfl xn2 = df_warp_sum(t2);
+      const cdf x0 = c_conj(ld4(&x[1]));
+      cdf tau = c_zero(), scale = c_zero();
+      dfl beta = x0.re;
+      if (!(xn2.hi == 0.f && x0.im.hi == 0.f)) {
+        const dfl nrm = df_sqrt(df_add(df_add(df_mul(x0.re, x0.re), df_mul(x0.im, x0.im)), xn2));
+        beta = x0.re.hi >= 0.f ? df_neg(nrm) : nrm;
+        const dfl rb = df_rcp(beta);
+        tau.re = df_sub(df_f(1.f), df_mul(x0.re, rb));  // (beta - x0.re) / beta
+        tau.im = df_neg(df_mul(x0.im, rb));
+        const cdf den = {df_sub(x0.re, beta), x0.im};
+        const dfl dd = df_add(df_mul(den.re, den.re), df_mul(den.im, den.im));
+        const dfl rd = df_rcp(dd);
+        scale.re = df_mul(den.re, rd);
+        scale.im = df_neg(df_mul(den.im, rd));
+      }
+      if (lane == 0) {
+        st4(&hs[0], tau);
+        st4(&hs[1], scale);
+        hs[2] = make_float4(beta.hi, beta.lo, 0.f, 0.f);
+        if (crank == 0) {
+          a.d[k] = dpack(ld4(&x[0]).re);
+          a.e[k] = dpack(beta);
+          st4(&a.tau[k], tau);
+        }
       }
     }
+    __syncthreads();
+    // --- 2. v, w0 of the own rows and the CTA's partial sum
+    const cdf tau = ld4(&hs[0]), scale = ld4(&hs[1]);
+    const bool active = !(tau.re.hi == 0.f && tau.im.hi == 0.f);
+    cdf vt = c_zero();
+    if (tid < m) {
+      vt = tid == 0 ? cdf{{1.f, 0.f}, {0.f, 0.f}} : c_mul(c_conj(ld4(&x[1 + tid])), scale);
+      st4(&v[tid], vt);
+      if (crank == 0) st4(&a.refl[(long long)k * n + tid], vt);
+    }
+    if (warp == 0) {
+      cdf pc = c_zero();
+      if (lane < nown) {
+        const int lr = lr0 + lane, i = lr * nct + crank - (k + 1);
+        const cdf w0 = c_mul(tau, c_add(ld4(&srow[R + lane]), c_mul(scale, ld4(&srow[lane]))));
+        st4(&w0loc[par * R + lr], w0);
+        const cdf vi = i == 0 ? cdf{{1.f, 0.f}, {0.f, 0.f}} : c_mul(c_conj(ld4(&x[1 + i])), scale);
+        pc = c_mulc(w0, vi);
+      }
+      pc = c_warp_sum(pc);
+      if (lane == 0) st4(&partloc[par], pc);
+    }
     cl.sync();
-    // --- alpha = -tau/2 (w0^H v), w = w0 + alpha v (every CTA, w0 read from the row owners)
+    // --- 3. alpha = -tau/2 sum conj(w0) v, w = w0 + alpha v; the next pivot row's stored values
     const int owner1 = (k + 1) % nct;
     const float4* prow = cl.map_shared_rank(rows, owner1) + (size_t)((k + 1) / nct) * n + (k + 1);
+    cdf w0t = c_zero(), pv = c_zero(), pt = c_zero();
+    if (tid < m) {
+      const int g = k + 1 + tid;
+      w0t = ld4(cl.map_shared_rank(w0loc, g % nct) + par * R + g / nct);
+      pt = ld4(&prow[tid]);
+    }
+    if (lane < nct) pv = ld4(cl.map_shared_rank(partloc, lane) + par);
+    const cdf ssum = c_warp_sum(pv);
+    const cdf htau = {df_mul_f(tau.re, -0.5f), df_mul_f(tau.im, -0.5f)};
+    const cdf alpha = c_mul(htau, ssum);
+    if (tid < m) st4(&w[tid], c_add(w0t, c_mul(alpha, vt)));
+    __syncthreads();
+    // --- 4. rank-2 update of the own rows but row k+1: A_ij -= v_i conj(w_j) + w_i conj(v_j)
     if (active) {
-      cdf w0 = c_zero(), vj = c_zero();
-      if (tid < m) {
-        const int g = k + 1 + tid;
-        w0 = ld4(cl.map_shared_rank(w0loc, g % nct) + par * R + g / nct);
-        vj = ld4(&v[tid]);
-      }
-      const cdf ssum = block_sum_all(c_mulc(w0, vj), red_s);
-      const cdf htau = {df_mul_f(tau.re, -0.5f), df_mul_f(tau.im, -0.5f)};
-      const cdf alpha = c_mul(htau, ssum);
-      if (tid < m) st4(&w[tid], c_add(w0, c_mul(alpha, vj)));
-      __syncthreads();
-      // rank-2 update of the own rows but row k+1: A_ij -= v_i conj(w_j) + w_i conj(v_j)
       const int tot = nown * m;
       const float rm = 1.f / (float)m;
       for (int idx = tid; idx < tot; idx += TDC_THREADS) {
@@ -356,19 +391,14 @@ __global__ void __launch_bounds__(TDC_THREADS, 1) tridiag_cluster_kernel(const T
         st4(aij, c_renorm(acc));
       }
     }
-    // --- the next pivot row k+1 (relative row 0: v_0 = 1), formed by every CTA, and the squared
-    // norm of its entries 2.. for the next step
-    cdf s2n = c_zero();
+    // the next pivot row k+1 (relative row 0: v_0 = 1) and the squares of its entries
     if (tid < m) {
-      cdf aij = ld4(&prow[tid]);
-      if (active) {
-        const cdf w0c = ld4(&w[0]);
-        aij = c_sub(aij, c_add(c_conj(ld4(&w[tid])), c_mul(w0c, c_conj(ld4(&v[tid])))));
-      }
+      cdf aij = pt;
+      if (active) aij = c_sub(aij, c_add(c_conj(ld4(&w[tid])), c_mul(ld4(&w[0]), c_conj(vt))));
       st4(&x[tid], aij);
-      if (tid >= 2) s2n.re = df_add(df_mul(aij.re, aij.re), df_mul(aij.im, aij.im));
+      xsq[tid] = dpack(df_add(df_mul(aij.re, aij.re), df_mul(aij.im, aij.im)));
     }
-    xn2 = block_sum_all(s2n, red_n).re;
+    __syncthreads();
   }
   if (crank == 0 && tid == 0) a.d[n - 1] = dpack(ld4(&x[0]).re);
   cl.sync();  // no CTA leaves while others may still read its shared memory
@@ -376,7 +406,7 @@ __global__ void __launch_bounds__(TDC_THREADS, 1) tridiag_cluster_kernel(const T
 
 static size_t tdc_smem(int n) {
   const int R = (n + TDC_CTAS - 1) / TDC_CTAS;
-  return sizeof(float4) * ((size_t)R * n + 3 * (size_t)n + 2 * (size_t)R);
+  return sizeof(float4) * ((size_t)R * n + 3 * (size_t)n + 4 * (size_t)R) + sizeof(float2) * (size_t)n;
 }
 
 static cudaLaunchConfig_t tdc_cfg(size_t smem, cudaStream_t st, cudaLaunchAttribute* attr) {
@@ -686,7 +716,7 @@ __global__ void __launch_bounds__(256) td_wy_t_kernel(int n, const float4* __res
   __shared__ float4 S[WY_B][WY_B];  // S[i][j] = v_i^H v_j (i < j)
   __shared__ float4 T[WY_B][WY_B];
   const int blk = blockIdx.x, k0 = blk * WY_B, nb = min(WY_B, n - 1 - k0);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // row-major copy: Yt[blk][g][j] = v_{k0+j}[g], zero where g <= k0 + j
   float4* Y = Yt + (size_t)blk * n * WY_B;
   for (int idx = threadIdx.x; idx < n * WY_B; idx += blockDim.x) {
@@ -852,7 +882,8 @@ static hicu_status launch_tridiag_grid(hicu_handle* h, int n, float4* A, float2*
   int grid = h->num_sms;
   // own rows in shared memory when they fit next to the three vectors
   const int R = (n + grid - 1) / grid;
-  const size_t smem_vec = sizeof(float4) * 3 * (size_t)n;
+  // x, v, w, the row sums and the squares of x; the own rows on top when they fit
+  const size_t smem_vec = sizeof(float4) * (3 * (size_t)n + 2 * (size_t)R) + sizeof(float2) * (size_t)n;
   const size_t smem_rows = smem_vec + sizeof(float4) * (size_t)R * n;
   const bool in_smem = smem_rows <= 200 * 1024;
   const void* kern = in_smem ? (const void*)tridiag_kernel<true> : (const void*)tridiag_kernel<false>;
