@@ -674,8 +674,8 @@ def main():
         per_launch = flops_recon * args.steps / max(dom_launches, 1)
         achieved = per_launch / avg_launch_s / 1e12
         n_pb = pb.ncoil * pb.kernel[0] * pb.kernel[1] * pb.kernel[2]
-        # n <= 440 runs the one-cluster form of the tridiagonalisation, larger n the grid form
-        kname = (("tridiag_cluster_kernel" if n_pb <= 440 else "tridiag_kernel") if dominant == 8
+        # n <= 416 runs the one-cluster form of the tridiagonalisation, larger n the grid form
+        kname = (("tridiag_cluster_kernel" if n_pb <= 416 else "tridiag_kernel") if dominant == 8
                  else KERNEL_NAMES[dominant])
         roof = {"kernel": kname, "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",

@@ -220,28 +220,26 @@ __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
   if (c == 0 && tid == 0) a.d[n - 1] = dpack(ld4(&x[0]).re);
 }
 
-// ---------------------------------------------------------------- one-cluster form (n <= 440)
+// ---------------------------------------------------------------- one-cluster form (n <= 416)
 //
 // The same steps inside one thread-block cluster of TDC_CTAS CTAs: global row g lives in the
-// shared memory of CTA g mod TDC_CTAS (local row g / TDC_CTAS) for the whole run, w0 and the
-// partial sums stay in their producers' shared memory and are read through distributed shared
-// memory, and a step ends at the hardware cluster barrier instead of a grid barrier and L2
-// round trips.  As in the grid form, the pivot row k+1 is never written during step k: every CTA
-// forms it from the owner's stored row (read remotely) and v, w.
-//
-// Per step, with v = conj(x_{1..m}) / (x0 - beta) (x the pivot row, v_0 = 1):
-//   1. warps 0..nw-2: s_i = sum_{j>=1} A_ij conj(x_{1+j}) for the own rows; warp nw-1 in the
-//      meantime the norm of the pivot row's tail (squares left by the previous step) and the
-//      Householder scalars tau, beta, 1 / (x0 - beta).  CTA barrier.
-//   2. v; w0_i = tau (A_i0 + s_i / (x0 - beta)) and the CTA's partial sum of conj(w0_i) v_i
-//      (warp 0).  Cluster barrier.
-//   3. every warp: the 16 partial sums (remote) -> alpha; w = w0 + alpha v with w0 read from the
-//      row owners, the next pivot row's stored values fetched at the same time.  CTA barrier.
-//   4. rank-2 update of the own rows but row k+1; the next pivot row and its squares.  CTA
-//      barrier.
+// shared memory of CTA g mod TDC_CTAS (local row g / TDC_CTAS) for the whole run, and a step has
+// one hardware cluster barrier.  Whatever other CTAs need is pushed into their shared memory by
+// its producer before the barrier (remote stores, ordered by the barrier's release / acquire),
+// so that after it every CTA reads locally: w0_i from the owner of row i, the CTAs' partial sums
+// of conj(w0) v, and the stored row k+2 (the next step's pivot source) from its owner as it is
+// updated.  Per step k, with v = conj(x_{1..m}) / (x0 - beta) (x the pivot row, v_0 = 1):
+//   1. row sums s_i = sum_{j>=1} A_ij conj(x_{1+j}) of the own rows (a warp per row);
+//      w0_i = tau (A_i0 + s_i / (x0 - beta)) pushed to every CTA.  CTA barrier.
+//   2. v; the CTA's partial sum of conj(w0_i) v_i pushed to every CTA.  Cluster barrier.
+//   3. alpha = -tau/2 sum conj(w0) v; w = w0 + alpha v; the next pivot row
+//      x' = (stored row k+1) - conj(w) - w_0 conj(v) and the squares of its entries.  CTA barrier.
+//   4. warps 0..nw-2: rank-2 update of the own rows but row k+1 (row k+2 pushed as it is
+//      written); warp nw-1 meanwhile: the norm of x' and the Householder scalars of step k+1.
+//      CTA barrier.
 constexpr int TDC_CTAS = 16;
 constexpr int TDC_THREADS = 512;
-constexpr int TDC_MAX_N = 440;
+constexpr int TDC_MAX_N = 416;  // shared memory: R n + 7 n + R float4 and n float2 within 227 KB
 
 struct TdcArgs {
   int n;
@@ -252,88 +250,100 @@ struct TdcArgs {
   float4* tau;
 };
 
+// Householder scalars of the pivot row x (length m + 1; squares of x in xsq): tau, the inverse
+// 1 / (x0 - beta) of v's leading entry before normalisation, beta; one warp.
+__device__ __forceinline__ void tdc_scalars(int m, const float4* x, const float2* xsq, cdf& tau, cdf& scale,
+                                            dfl& beta) {
+  const int lane = threadIdx.x & 31;
+  dfl t2 = df_f(0.f);
+  for (int j = 2 + lane; j <= m; j += 32) t2 = df_add(t2, dload(xsq[j]));
+  const dfl xn2 = df_warp_sum(t2);
+  const cdf x0 = c_conj(ld4(&x[1]));
+  tau = c_zero();
+  scale = c_zero();
+  beta = x0.re;
+  if (!(xn2.hi == 0.f && x0.im.hi == 0.f)) {
+    const dfl nrm = df_sqrt(df_add(df_add(df_mul(x0.re, x0.re), df_mul(x0.im, x0.im)), xn2));
+    beta = x0.re.hi >= 0.f ? df_neg(nrm) : nrm;
+    const dfl rb = df_rcp(beta);
+    tau.re = df_sub(df_f(1.f), df_mul(x0.re, rb));  // (beta - x0.re) / beta
+    tau.im = df_neg(df_mul(x0.im, rb));
+    const cdf den = {df_sub(x0.re, beta), x0.im};
+    const dfl dd = df_add(df_mul(den.re, den.re), df_mul(den.im, den.im));
+    const dfl rd = df_rcp(dd);
+    scale.re = df_mul(den.re, rd);
+    scale.im = df_neg(df_mul(den.im, rd));
+  }
+}
+
 __global__ void __launch_bounds__(TDC_THREADS, 1) tridiag_cluster_kernel(const TdcArgs a) {
   cg::cluster_group cl = cg::this_cluster();
   const int crank = (int)cl.block_rank(), nct = (int)cl.num_blocks();
   const int n = a.n;
   const int R = (n + nct - 1) / nct;
   extern __shared__ float4 csm[];
-  float4* rows = csm;                // [R][n]
+  float4* rows = csm;                // [R][n] own rows
   float4* x = rows + (size_t)R * n;  // [n] pivot row
   float4* v = x + n;                 // [n]
   float4* w = v + n;                 // [n]
-  float4* w0loc = w + n;             // [2][R] w0 of own rows, by step parity
-  float4* srow = w0loc + 2 * R;      // [R] s_i of own rows, then A_i0 in [R..2R)
-  float2* xsq = (float2*)(srow + 2 * R);  // [n] squares of the pivot row's entries (double-float)
-  __shared__ float4 partloc[2];      // the CTA's partial sum of conj(w0_i) v_i, by step parity
-  __shared__ float4 hs[3];           // tau, 1 / (x0 - beta), (beta, active)
+  float4* w0all = w + n;             // [2][n] w0 of every trailing row (pushed by the owners), by step parity
+  float4* pub = w0all + 2 * n;       // [2][n] the next pivot row as stored (pushed by its owner), by step parity
+  float4* pcs = pub + 2 * n;         // [R] conj(w0_i) v_i of the own rows
+  float2* xsq = (float2*)(pcs + R);  // [n] squares of the pivot row's entries (double-float)
+  __shared__ float4 partall[2][TDC_CTAS];  // every CTA's partial sum of conj(w0) v, by step parity
+  __shared__ float4 hs[3];                 // tau, 1 / (x0 - beta), beta of the current step
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = TDC_THREADS / 32;
   for (int idx = tid; idx < R * n; idx += TDC_THREADS) {
     const int lr = idx / n, j = idx - lr * n;
     const int g = lr * nct + crank;
     if (g < n) rows[idx] = a.A[(size_t)g * n + j];
   }
-  cl.sync();
-  {
-    const float4* r0 = cl.map_shared_rank(rows, 0);
-    for (int j = tid; j < n; j += TDC_THREADS) {
-      const float4 xj = r0[j];
-      x[j] = xj;
-      xsq[j] = dpack(df_add(df_mul({xj.x, xj.y}, {xj.x, xj.y}), df_mul({xj.z, xj.w}, {xj.z, xj.w})));
-    }
+  for (int j = tid; j < n; j += TDC_THREADS) {
+    const float4 xj = a.A[j];
+    x[j] = xj;
+    xsq[j] = dpack(df_add(df_mul({xj.x, xj.y}, {xj.x, xj.y}), df_mul({xj.z, xj.w}, {xj.z, xj.w})));
+    if (j < n - 1) pub[j] = a.A[(size_t)n + 1 + j];  // row 1 from column 1: step 0's pivot source
   }
   __syncthreads();
+  if (warp == nw - 1) {
+    cdf tau, scale;
+    dfl beta;
+    tdc_scalars(n - 1, x, xsq, tau, scale, beta);
+    if (lane == 0) {
+      st4(&hs[0], tau);
+      st4(&hs[1], scale);
+      hs[2] = make_float4(beta.hi, beta.lo, 0.f, 0.f);
+    }
+  }
+  cl.sync();  // every CTA running (remote stores below) and the step-0 scalars in place
   for (int k = 0; k < n - 1; ++k) {
     const int m = n - k - 1;  // m <= TDC_MAX_N - 1 < TDC_THREADS: one entry per thread below
     const int par = k & 1;
     const int lr0 = (k + 1 - crank + nct - 1) / nct;  // first own local row with g >= k+1
     const int nown = lr0 < R ? R - lr0 - ((R - 1) * nct + crank >= n ? 1 : 0) : 0;
-    // --- 1. row sums against conj(x) (warps 0..nw-2) / Householder scalars (warp nw-1)
-    if (warp < nw - 1) {
-      for (int q = warp; q < nown; q += nw - 1) {
-        const float4* row = rows + (size_t)(lr0 + q) * n + (k + 1);
-        cdf y = c_zero();
-        for (int j = 1 + lane; j < m; j += 32) c_acc_mul(y, ld4(&row[j]), c_conj(ld4(&x[1 + j])));
-        y = c_warp_sum(y);
-        if (lane == 0) {
-          st4(&srow[q], y);
-          srow[R + q] = row[0];
-        }
-      }
-    } else {
-      dfl t2 = df_f(0.f);
-      for (int j = 2 + lane; j <= m; j += 32) t2 = df_add(t2, dload(xsq[j]));
-      const dfl xn2 = df_warp_sum(t2);
-      const cdf x0 = c_conj(ld4(&x[1]));
-      cdf tau = c_zero(), scale = c_zero();
-      dfl beta = x0.re;
-      if (!(xn2.hi == 0.f && x0.im.hi == 0.f)) {
-        const dfl nrm = df_sqrt(df_add(df_add(df_mul(x0.re, x0.re), df_mul(x0.im, x0.im)), xn2));
-        beta = x0.re.hi >= 0.f ? df_neg(nrm) : nrm;
-        const dfl rb = df_rcp(beta);
-        tau.re = df_sub(df_f(1.f), df_mul(x0.re, rb));  // (beta - x0.re) / beta
-        tau.im = df_neg(df_mul(x0.im, rb));
-        const cdf den = {df_sub(x0.re, beta), x0.im};
-        const dfl dd = df_add(df_mul(den.re, den.re), df_mul(den.im, den.im));
-        const dfl rd = df_rcp(dd);
-        scale.re = df_mul(den.re, rd);
-        scale.im = df_neg(df_mul(den.im, rd));
-      }
+    const cdf tau = ld4(&hs[0]), scale = ld4(&hs[1]);
+    const bool active = !(tau.re.hi == 0.f && tau.im.hi == 0.f);
+    if (crank == 0 && tid == 0) {
+      a.d[k] = dpack(ld4(&x[0]).re);
+      a.e[k] = dpack({hs[2].x, hs[2].y});
+      st4(&a.tau[k], tau);
+    }
+    // --- 1. row sums against conj(x); w0 of the own rows pushed to every CTA
+    for (int q = warp; q < nown; q += nw) {
+      const int lr = lr0 + q, i = lr * nct + crank - (k + 1);
+      const float4* row = rows + (size_t)lr * n + (k + 1);
+      cdf y = c_zero();
+      for (int j = 1 + lane; j < m; j += 32) c_acc_mul(y, ld4(&row[j]), c_conj(ld4(&x[1 + j])));
+      y = c_warp_sum(y);  // the same in every lane
+      const cdf w0 = c_mul(tau, c_add(ld4(&row[0]), c_mul(scale, y)));
+      if (lane < nct) st4(cl.map_shared_rank(w0all, lane) + par * n + i, w0);
       if (lane == 0) {
-        st4(&hs[0], tau);
-        st4(&hs[1], scale);
-        hs[2] = make_float4(beta.hi, beta.lo, 0.f, 0.f);
-        if (crank == 0) {
-          a.d[k] = dpack(ld4(&x[0]).re);
-          a.e[k] = dpack(beta);
-          st4(&a.tau[k], tau);
-        }
+        const cdf vi = i == 0 ? cdf{{1.f, 0.f}, {0.f, 0.f}} : c_mul(c_conj(ld4(&x[1 + i])), scale);
+        st4(&pcs[q], c_mulc(w0, vi));
       }
     }
     __syncthreads();
-    // --- 2. v, w0 of the own rows and the CTA's partial sum
-    const cdf tau = ld4(&hs[0]), scale = ld4(&hs[1]);
-    const bool active = !(tau.re.hi == 0.f && tau.im.hi == 0.f);
+    // --- 2. v; the CTA's partial sum pushed to every CTA
     cdf vt = c_zero();
     if (tid < m) {
       vt = tid == 0 ? cdf{{1.f, 0.f}, {0.f, 0.f}} : c_mul(c_conj(ld4(&x[1 + tid])), scale);
@@ -341,72 +351,82 @@ __global__ void __launch_bounds__(TDC_THREADS, 1) tridiag_cluster_kernel(const T
       if (crank == 0) st4(&a.refl[(long long)k * n + tid], vt);
     }
     if (warp == 0) {
-      cdf pc = c_zero();
-      if (lane < nown) {
-        const int lr = lr0 + lane, i = lr * nct + crank - (k + 1);
-        const cdf w0 = c_mul(tau, c_add(ld4(&srow[R + lane]), c_mul(scale, ld4(&srow[lane]))));
-        st4(&w0loc[par * R + lr], w0);
-        const cdf vi = i == 0 ? cdf{{1.f, 0.f}, {0.f, 0.f}} : c_mul(c_conj(ld4(&x[1 + i])), scale);
-        pc = c_mulc(w0, vi);
-      }
-      pc = c_warp_sum(pc);
-      if (lane == 0) st4(&partloc[par], pc);
+      const cdf pc = c_warp_sum(lane < nown ? ld4(&pcs[lane]) : c_zero());
+      if (lane < nct) st4(cl.map_shared_rank(&partall[0][0], lane) + par * TDC_CTAS + crank, pc);
     }
     cl.sync();
-    // --- 3. alpha = -tau/2 sum conj(w0) v, w = w0 + alpha v; the next pivot row's stored values
-    const int owner1 = (k + 1) % nct;
-    const float4* prow = cl.map_shared_rank(rows, owner1) + (size_t)((k + 1) / nct) * n + (k + 1);
-    cdf w0t = c_zero(), pv = c_zero(), pt = c_zero();
-    if (tid < m) {
-      const int g = k + 1 + tid;
-      w0t = ld4(cl.map_shared_rank(w0loc, g % nct) + par * R + g / nct);
-      pt = ld4(&prow[tid]);
-    }
-    if (lane < nct) pv = ld4(cl.map_shared_rank(partloc, lane) + par);
-    const cdf ssum = c_warp_sum(pv);
-    const cdf htau = {df_mul_f(tau.re, -0.5f), df_mul_f(tau.im, -0.5f)};
-    const cdf alpha = c_mul(htau, ssum);
-    if (tid < m) st4(&w[tid], c_add(w0t, c_mul(alpha, vt)));
-    __syncthreads();
-    // --- 4. rank-2 update of the own rows but row k+1: A_ij -= v_i conj(w_j) + w_i conj(v_j)
-    if (active) {
-      const int tot = nown * m;
-      const float rm = 1.f / (float)m;
-      for (int idx = tid; idx < tot; idx += TDC_THREADS) {
-        const int q = (int)__fmul_rn((float)idx + 0.5f, rm);  // idx / m (exact: idx < 2^14, m <= 439)
-        const int j = idx - q * m;
-        const int lr = lr0 + q, i = lr * nct + crank - (k + 1);
-        if (i == 0) continue;
-        float4* aij = rows + (size_t)lr * n + (k + 1) + j;
-        const cdf vi = ld4(&v[i]), wi = ld4(&w[i]), wj = ld4(&w[j]), vjj = ld4(&v[j]);
-        cdf acc = ld4(aij);
-        df_acc_mul(acc.re, df_neg(vi.re), wj.re);
-        df_acc_mul(acc.re, df_neg(vi.im), wj.im);
-        df_acc_mul(acc.re, df_neg(wi.re), vjj.re);
-        df_acc_mul(acc.re, df_neg(wi.im), vjj.im);
-        df_acc_mul(acc.im, df_neg(vi.im), wj.re);
-        df_acc_mul(acc.im, vi.re, wj.im);
-        df_acc_mul(acc.im, df_neg(wi.im), vjj.re);
-        df_acc_mul(acc.im, wi.re, vjj.im);
-        st4(aij, c_renorm(acc));
+    // --- 3. alpha, w, the next pivot row and its squares (all local reads)
+    {
+      const cdf ssum = c_warp_sum(lane < nct ? ld4(&partall[par][lane]) : c_zero());
+      const cdf htau = {df_mul_f(tau.re, -0.5f), df_mul_f(tau.im, -0.5f)};
+      const cdf alpha = c_mul(htau, ssum);
+      if (tid < m) {
+        const cdf wt = c_add(ld4(&w0all[par * n + tid]), c_mul(alpha, vt));
+        const cdf w0 = c_add(ld4(&w0all[par * n]), alpha);  // w_0 (v_0 = 1)
+        st4(&w[tid], wt);
+        const cdf xt = c_sub(ld4(&pub[par * n + tid]), c_add(c_conj(wt), c_mul(w0, c_conj(vt))));
+        st4(&x[tid], xt);
+        xsq[tid] = dpack(df_add(df_mul(xt.re, xt.re), df_mul(xt.im, xt.im)));
       }
     }
-    // the next pivot row k+1 (relative row 0: v_0 = 1) and the squares of its entries
-    if (tid < m) {
-      cdf aij = pt;
-      if (active) aij = c_sub(aij, c_add(c_conj(ld4(&w[tid])), c_mul(ld4(&w[0]), c_conj(vt))));
-      st4(&x[tid], aij);
-      xsq[tid] = dpack(df_add(df_mul(aij.re, aij.re), df_mul(aij.im, aij.im)));
+    __syncthreads();
+    // --- 4. rank-2 update (warps 0..nw-2) / Householder scalars of step k+1 (warp nw-1)
+    if (warp < nw - 1) {
+      if (active) {
+        const int tot = nown * m;
+        const float rm = 1.f / (float)m;
+        float4* nxt = pub + (par ^ 1) * n;  // row k+2 from column k+2, for step k+1
+        for (int idx = tid; idx < tot; idx += TDC_THREADS - 32) {
+          const int q = (int)__fmul_rn((float)idx + 0.5f, rm);  // idx / m (exact: idx < 2^14, m <= 415)
+          const int j = idx - q * m;
+          const int lr = lr0 + q, i = lr * nct + crank - (k + 1);
+          if (i == 0) continue;
+          float4* aij = rows + (size_t)lr * n + (k + 1) + j;
+          const cdf vi = ld4(&v[i]), wi = ld4(&w[i]), wj = ld4(&w[j]), vjj = ld4(&v[j]);
+          cdf acc = ld4(aij);
+          df_acc_mul(acc.re, df_neg(vi.re), wj.re);
+          df_acc_mul(acc.re, df_neg(vi.im), wj.im);
+          df_acc_mul(acc.re, df_neg(wi.re), vjj.re);
+          df_acc_mul(acc.re, df_neg(wi.im), vjj.im);
+          df_acc_mul(acc.im, df_neg(vi.im), wj.re);
+          df_acc_mul(acc.im, vi.re, wj.im);
+          df_acc_mul(acc.im, df_neg(wi.im), vjj.re);
+          df_acc_mul(acc.im, wi.re, vjj.im);
+          acc = c_renorm(acc);
+          st4(aij, acc);
+          if (i == 1 && j >= 1)
+            for (int r = 0; r < nct; ++r) st4(cl.map_shared_rank(nxt, r) + (j - 1), acc);
+        }
+      } else {
+        // no update: row k+2 as stored is the next pivot source
+        for (int idx = tid; idx < nown * m; idx += TDC_THREADS - 32) {
+          const int q = (int)__fmul_rn((float)idx + 0.5f, 1.f / (float)m);
+          const int j = idx - q * m;
+          const int lr = lr0 + q, i = lr * nct + crank - (k + 1);
+          if (i != 1 || j < 1) continue;
+          const float4 val = rows[(size_t)lr * n + (k + 1) + j];
+          for (int r = 0; r < nct; ++r) cl.map_shared_rank(pub + (par ^ 1) * n, r)[j - 1] = val;
+        }
+      }
+    } else if (k + 1 < n - 1) {
+      cdf tau1, scale1;
+      dfl beta1;
+      tdc_scalars(m - 1, x, xsq, tau1, scale1, beta1);
+      if (lane == 0) {
+        st4(&hs[0], tau1);
+        st4(&hs[1], scale1);
+        hs[2] = make_float4(beta1.hi, beta1.lo, 0.f, 0.f);
+      }
     }
     __syncthreads();
   }
   if (crank == 0 && tid == 0) a.d[n - 1] = dpack(ld4(&x[0]).re);
-  cl.sync();  // no CTA leaves while others may still read its shared memory
+  cl.sync();  // no CTA leaves while others may still read or write its shared memory
 }
 
 static size_t tdc_smem(int n) {
   const int R = (n + TDC_CTAS - 1) / TDC_CTAS;
-  return sizeof(float4) * ((size_t)R * n + 3 * (size_t)n + 4 * (size_t)R) + sizeof(float2) * (size_t)n;
+  return sizeof(float4) * ((size_t)R * n + 7 * (size_t)n + (size_t)R) + sizeof(float2) * (size_t)n;
 }
 
 static cudaLaunchConfig_t tdc_cfg(size_t smem, cudaStream_t st, cudaLaunchAttribute* attr) {
@@ -1017,7 +1037,7 @@ hicu_status run_principal(hicu_handle* h, int64_t n64, int64_t r64, const double
   HICU_LAUNCH(h, K_EIG, st, eig_absmax_kernel<<<eb, 256, 0, st>>>(nn, G, amax_bits));
   HICU_LAUNCH(h, K_EIG, st, td_prep_kernel<<<eb, 256, 0, st>>>(nn, G, amax_bits, scale, A));
 
-  // 1. tridiagonalisation: one cluster for n <= 440, else cooperative over all SMs
+  // 1. tridiagonalisation: one cluster for n <= 416, else cooperative over all SMs
   if (tdc_available(n)) {
     TdcArgs ca;
     ca.n = n;

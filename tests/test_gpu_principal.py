@@ -66,10 +66,12 @@ def test_principal_brain_centre_region(H):
     _check(H, G, pb.rank)
 
 
-@pytest.mark.parametrize("n,r", [(2, 1), (3, 2), (17, 5), (129, 40), (257, 100), (1000, 300)])
+@pytest.mark.parametrize("n,r", [(2, 1), (3, 2), (17, 5), (129, 40), (257, 100), (416, 150), (417, 150),
+                                 (1000, 300)])
 def test_principal_sizes(H, n, r):
     """Decaying spectra like a Gram of a low-rank Hankel matrix, from the smallest size to the
-    n = 1000 of the 5 x 5 x 5 x 8 kernels."""
+    n = 1000 of the 5 x 5 x 5 x 8 kernels; 416 and 417 are the largest one-cluster and the
+    smallest grid tridiagonalisation."""
     rng = np.random.default_rng(n)
     U, _ = np.linalg.qr(random_complex(rng, (n, n)))
     sv = np.exp(-np.arange(n) / (n / 12.0))
