@@ -44,6 +44,17 @@ hicu_status cuda_error(hicu_handle* h, cudaError_t e, const char* where) {
   return set_error(h, HICU_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+hicu_status ensure_side_stream(hicu_handle* h) {
+  if (h->side_st) return HICU_OK;
+  if (cudaStreamCreateWithFlags(&h->side_st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->side_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->side_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->draw_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->draw_join, cudaEventDisableTiming) != cudaSuccess)
+    return cuda_error(h, cudaGetLastError(), "side stream");
+  return HICU_OK;
+}
+
 void prof_begin(hicu_handle* h, int cls, cudaStream_t st) {
   ++h->launches_all;
   if (h->prof_class != cls) return;
@@ -209,6 +220,8 @@ extern "C" hicu_status hicu_destroy(hicu_handle* h) {
   if (h->side_st) cudaStreamDestroy(h->side_st);
   if (h->side_fork) cudaEventDestroy(h->side_fork);
   if (h->side_join) cudaEventDestroy(h->side_join);
+  if (h->draw_fork) cudaEventDestroy(h->draw_fork);
+  if (h->draw_join) cudaEventDestroy(h->draw_join);
   if (h->coop_in) cudaEventDestroy(h->coop_in);
   if (h->coop_out) cudaEventDestroy(h->coop_out);
   for (auto& w : h->ws)
@@ -415,7 +428,7 @@ extern "C" hicu_status hicu_conv_null(hicu_handle* h, const hicu_geom* geom, con
     if (s) return s;
     double* part = (double*)ws_get(h, WS_PART, sizeof(double) * nb, &s);
     if (s) return s;
-    s = tc_prepare_weights(h, g, (const float2*)filters, p, 0, bw, st);
+    s = tc_prepare_weights(h, g, (const float2*)filters, p, bw, nullptr, st);
     if (s) return s;
     s = tc_prepare_input(h, g, full_view(geom, region, const_cast<float*>(x)), xpl, st);
     if (s) return s;
@@ -467,7 +480,7 @@ extern "C" hicu_status hicu_conv_null_adjoint(hicu_handle* h, const hicu_geom* g
     if (s) return s;
     double* part = (double*)ws_get(h, WS_PART, sizeof(double) * nb, &s);
     if (s) return s;
-    s = tc_prepare_weights(h, g, (const float2*)filters, p, 1, bw, st);
+    s = tc_prepare_weights(h, g, (const float2*)filters, p, nullptr, bw, st);
     if (s) return s;
     s = tc_prepare_r(h, g, (const float2*)R, p, rpl, st);
     if (s) return s;
@@ -527,8 +540,7 @@ static hicu_status gd_step_filters_tc(hicu_handle* h, const hicu_geom* geom, con
   n3 = n1;
   double* part = (double*)ws_get(h, WS_PART, sizeof(double) * (n1 + n2 + n3), &s);
   if (s) return s;
-  if ((s = tc_prepare_weights(h, g, (const float2*)filters, p, 0, bwc, st))) return s;
-  if ((s = tc_prepare_weights(h, g, (const float2*)filters, p, 1, bwa, st))) return s;
+  if ((s = tc_prepare_weights(h, g, (const float2*)filters, p, bwc, bwa, st))) return s;
   if ((s = tc_prepare_input(h, g, yv, xpl, st))) return s;
   if ((s = launch_conv_tc(h, g, xpl, bwc, p, nullptr, rpl, part, &n1, st))) return s;
   if ((s = launch_adjoint_tc(h, g, rpl, bwa, p, mv, gview, part + n1, &n2, st))) return s;
@@ -746,12 +758,36 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
                     geom->ncoil, (int)geom->dim[0], (int)geom->dim[1], (int)geom->dim[2], (float2*)y, m,
                     geom->mask_per_coil ? geom->dim[0] * geom->dim[1] * geom->dim[2] : 0));
   }
+  // the JL basis (principal vectors, or the null basis) and its matrices' row count
+  const int64_t nq = principal ? r : nr;
+  const int jmode = principal ? HICU_JL_COMPLEMENT : prm->jl;
+  const int64_t prow = (jmode == HICU_JL_NULLSPACE) ? nq : n;
+  size_t pbatch = 0;
+  for (int i = 0; i < prm->nstages; ++i)
+    pbatch = std::max(pbatch, (size_t)prm->stages[i].gd_steps * (size_t)prow * (size_t)prm->stages[i].p);
+  float* Pall = nullptr;
+  if (pbatch > 0) {
+    Pall = (float*)ws_get(h, WS_REC_P, sizeof(float) * pbatch, &s);
+    if (s) return s;
+    if ((s = ensure_side_stream(h))) return s;
+  }
   uint64_t counter = 0;
   long long it = 0;
   hicu_region prev = prm->stages[0].region;
   for (int si = 0; si < prm->nstages; ++si) {
     const hicu_stage& stg = prm->stages[si];
     for (int i = 0; i < stg.iters; ++i) {
+      // the JL matrices of this outer iteration's descent steps depend on nothing but the seed and
+      // the step counter: drawn on the side stream beside the Gram and the eigen-solve (after the
+      // previous iteration's steps, the last readers of the buffer)
+      if (stg.gd_steps > 0) {
+        cudaError_t ce = cudaEventRecord(h->draw_fork, st);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(h->side_st, h->draw_fork, 0);
+        if (ce != cudaSuccess) return cuda_error(h, ce, "reconstruct: draw fork");
+        if ((s = jl_draw(h, prow, stg.p, stg.gd_steps, prm->seed, counter, Pall, h->side_st))) return s;
+        if ((ce = cudaEventRecord(h->draw_join, h->side_st)) != cudaSuccess)
+          return cuda_error(h, ce, "reconstruct: draw join");
+      }
       const hicu_region& greg = prm->gram_on_current ? stg.region : prev;
       s = run_gram(h, geom, &greg, y, G, st);
       if (s) return s;
@@ -768,12 +804,15 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
         HICU_LAUNCH(h, K_MISC, st, tail_sum_kernel<<<1, 256, 0, st>>>(eig, (int)nr, dlog + it));
       }
       // Algorithm 1 steps 6-8: the basis is converted to complex64 once per outer iteration
-      const int64_t nq = principal ? r : nr;
-      const int jmode = principal ? HICU_JL_COMPLEMENT : prm->jl;
       float2* Qf = nullptr;
-      if (stg.gd_steps > 0 && (s = jl_convert_q(h, n, nq, Q, &Qf, st))) return s;
+      if (stg.gd_steps > 0) {
+        if ((s = jl_convert_q(h, n, nq, Q, &Qf, st))) return s;
+        const cudaError_t ce = cudaStreamWaitEvent(st, h->draw_join, 0);
+        if (ce != cudaSuccess) return cuda_error(h, ce, "reconstruct: draw wait");
+      }
       for (int j = 0; j < stg.gd_steps; ++j) {
-        s = launch_jl_converted(h, n, nq, stg.p, Qf, jmode, nullptr, prm->seed, counter, bank, st);
+        s = launch_jl_converted(h, n, nq, stg.p, Qf, jmode, nullptr, Pall + (size_t)j * prow * stg.p, prm->seed,
+                                counter, bank, st);
         if (s) return s;
         s = gd_step_filters(h, geom, &stg.region, y, m, bank, stg.p, dstats + 4 * counter, prm->prec, st);
         if (s) return s;

@@ -450,39 +450,51 @@ __global__ void tc_split_r_kernel(long long npos, int p, int chunks_even, const 
 //                   [[f.re, -f.im], [f.im, f.re]].
 // The pseudo-3D offset index is (dz*ky + dy)*kx + dx, which is the bank's [kz][ky][kx] order in
 // 3D and its [ky][kx] order for a 2D problem run with rows as planes (ky = 1, kz = k_y).
-__global__ void tc_prep_b_kernel(int mode, int Cin, int Cout, int n, int kx, int ky, int kz, int kgroups, int ogs,
-                                 const float2* __restrict__ bank, __nv_bfloat16* __restrict__ out) {
-  const long long per_og = (long long)kgroups * ky * kx * 2 * kz * 32 * 8;
-  const long long tot = per_og * ogs;
+struct PrepB {
+  int mode, Cin, Cout, kgroups, ogs;
+  long long tot;
+  __nv_bfloat16* out;
+};
+
+// one element i of a B operand (see the layout above)
+__device__ __forceinline__ __nv_bfloat16 prep_b_elem(const PrepB& q, int n, int kx, int ky, int kz,
+                                                     const float2* __restrict__ bank, long long i) {
   const int K = kx * ky * kz;
+  long long t = i;
+  const int e = (int)(t % 8); t /= 8;
+  const int row = (int)(t % 32); t /= 32;
+  const int blk = (int)(t % kz); t /= kz;
+  const int cc = (int)(t % 2); t /= 2;
+  const int dx = (int)(t % kx); t /= kx;
+  const int dy = (int)(t % ky); t /= ky;
+  const int kg = (int)(t % q.kgroups); t /= q.kgroups;
+  const int og = (int)t;
+  const int dz = kz - 1 - blk;
+  const int ci = 8 * kg + 4 * cc + e / 2, tin = e & 1;
+  const int split = row >> 4, rr = row & 15;
+  const int co = 8 * og + rr / 2, uout = rr & 1;
+  float w = 0.f;
+  if (ci < q.Cin && co < q.Cout) {
+    if (q.mode == 0) {
+      const float2 f = bank[(long long)co * n + (long long)ci * K + (dz * ky + dy) * kx + dx];
+      w = (tin == 0) ? (uout == 0 ? f.x : f.y) : (uout == 0 ? -f.y : f.x);
+    } else {
+      const int d = ((kz - 1 - dz) * ky + (ky - 1 - dy)) * kx + (kx - 1 - dx);
+      const float2 f = bank[(long long)ci * n + (long long)co * K + d];
+      w = (tin == 0) ? (uout == 0 ? f.x : -f.y) : (uout == 0 ? f.y : f.x);
+    }
+  }
+  const float hi = __bfloat162float(__float2bfloat16_rn(w));
+  return __float2bfloat16_rn(split == 0 ? hi : w - hi);
+}
+
+// the B operands of the conv (q0) and of the adjoint (q1, tot = 0 when not wanted) in one launch
+__global__ void tc_prep_b_kernel(PrepB q0, PrepB q1, int n, int kx, int ky, int kz, const float2* __restrict__ bank) {
+  const long long tot = q0.tot + q1.tot;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
        i += (long long)gridDim.x * blockDim.x) {
-    long long t = i;
-    const int e = (int)(t % 8); t /= 8;
-    const int row = (int)(t % 32); t /= 32;
-    const int blk = (int)(t % kz); t /= kz;
-    const int cc = (int)(t % 2); t /= 2;
-    const int dx = (int)(t % kx); t /= kx;
-    const int dy = (int)(t % ky); t /= ky;
-    const int kg = (int)(t % kgroups); t /= kgroups;
-    const int og = (int)t;
-    const int dz = kz - 1 - blk;
-    const int ci = 8 * kg + 4 * cc + e / 2, tin = e & 1;
-    const int split = row >> 4, rr = row & 15;
-    const int co = 8 * og + rr / 2, uout = rr & 1;
-    float w = 0.f;
-    if (ci < Cin && co < Cout) {
-      if (mode == 0) {
-        const float2 f = bank[(long long)co * n + (long long)ci * K + (dz * ky + dy) * kx + dx];
-        w = (tin == 0) ? (uout == 0 ? f.x : f.y) : (uout == 0 ? -f.y : f.x);
-      } else {
-        const int d = ((kz - 1 - dz) * ky + (ky - 1 - dy)) * kx + (kx - 1 - dx);
-        const float2 f = bank[(long long)ci * n + (long long)co * K + d];
-        w = (tin == 0) ? (uout == 0 ? f.x : -f.y) : (uout == 0 ? f.y : f.x);
-      }
-    }
-    const float hi = __bfloat162float(__float2bfloat16_rn(w));
-    out[i] = __float2bfloat16_rn(split == 0 ? hi : w - hi);
+    if (i < q0.tot) q0.out[i] = prep_b_elem(q0, n, kx, ky, kz, bank, i);
+    else q1.out[i - q0.tot] = prep_b_elem(q1, n, kx, ky, kz, bank, i - q0.tot);
   }
 }
 
@@ -694,16 +706,25 @@ hicu_status tc_prepare_r(hicu_handle* h, const ConvGeom& g, const float2* R, int
   return cuda_error(h, cudaGetLastError(), "tc_split_r");
 }
 
-hicu_status tc_prepare_weights(hicu_handle* h, const ConvGeom& g, const float2* bank, int p, int mode,
-                               void* out, cudaStream_t st) {
+static PrepB prep_b_of(const ConvGeom& g, int p, int mode, void* out) {
+  PrepB q;
+  q.mode = mode;
+  q.Cin = mode == 0 ? g.C : p;
+  q.Cout = mode == 0 ? p : g.C;
+  q.kgroups = (q.Cin + 7) / 8;
+  q.ogs = (q.Cout + 7) / 8;
+  q.tot = out ? (long long)tc_b_bytes(g, p, mode) / 2 : 0;
+  q.out = (__nv_bfloat16*)out;
+  return q;
+}
+
+hicu_status tc_prepare_weights(hicu_handle* h, const ConvGeom& g, const float2* bank, int p, void* out_conv,
+                               void* out_adjoint, cudaStream_t st) {
   const Pseudo q = pseudo_of(g);
-  const int Cin = mode == 0 ? g.C : p, Cout = mode == 0 ? p : g.C;
-  const int kgroups = (Cin + 7) / 8, ogs = (Cout + 7) / 8;
-  const long long tot = (long long)tc_b_bytes(g, p, mode) / 2;
+  const PrepB q0 = prep_b_of(g, p, 0, out_conv), q1 = prep_b_of(g, p, 1, out_adjoint);
+  const long long tot = q0.tot + q1.tot;
   int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
-  HICU_LAUNCH(h, K_MISC, st,
-              tc_prep_b_kernel<<<blocks, 256, 0, st>>>(mode, Cin, Cout, g.n, q.kx, q.ky, q.kz, kgroups, ogs,
-                                                       bank, (__nv_bfloat16*)out));
+  HICU_LAUNCH(h, K_MISC, st, tc_prep_b_kernel<<<blocks, 256, 0, st>>>(q0, q1, g.n, q.kx, q.ky, q.kz, bank));
   return cuda_error(h, cudaGetLastError(), "tc_prep_b");
 }
 

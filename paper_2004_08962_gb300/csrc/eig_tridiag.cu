@@ -953,12 +953,7 @@ static hicu_status finish_principal(hicu_handle* h, int n, int r, const double2*
   float4* Tb = (float4*)ws_get(h, WS_EIG_WY, sizeof(float4) * (size_t)nblk * WY_B * (WY_B + (size_t)n), &sw);
   if (sw) return sw;
   float4* Yt = Tb + (size_t)nblk * WY_B * WY_B;
-  if (!h->side_st) {
-    if (cudaStreamCreateWithFlags(&h->side_st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->side_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->side_join, cudaEventDisableTiming) != cudaSuccess)
-      return cuda_error(h, cudaGetLastError(), "principal subspace: side stream");
-  }
+  if ((sw = ensure_side_stream(h))) return sw;
   {
     cudaError_t ce = cudaEventRecord(h->side_fork, st);
     if (ce == cudaSuccess) ce = cudaStreamWaitEvent(h->side_st, h->side_fork, 0);

@@ -183,6 +183,8 @@ struct hicu_handle {
   cudaStream_t side_st = nullptr;
   cudaEvent_t side_fork = nullptr;
   cudaEvent_t side_join = nullptr;
+  cudaEvent_t draw_fork = nullptr;  // JL draws of an outer iteration
+  cudaEvent_t draw_join = nullptr;
   // batch lanes (hicu_reconstruct_batched): one sub-handle and stream each, created on demand
   std::vector<hicu_handle*> lane_h;
   std::vector<cudaStream_t> lane_st;
@@ -223,6 +225,7 @@ enum Slot {
   WS_TC_BA,       // tensor-core B planes, adjoint
   WS_FGRAD,       // filter-gradient partials per CTA
   WS_EIG_WY,      // principal subspace: compact WY blocks of the back-transformation
+  WS_REC_P,       // reconstruct: JL matrices of one outer iteration's descent steps
   WS_COUNT
 };
 static_assert(WS_COUNT <= hicu_handle::kSlots, "workspace slots");
@@ -277,8 +280,9 @@ bool tc_supported(const ConvGeom& g);
 size_t tc_b_bytes(const ConvGeom& g, int p, int mode);
 size_t tc_x_bytes(const ConvGeom& g);          // split planes of a region input
 size_t tc_r_bytes(const ConvGeom& g, int p);   // split planes of R
-hicu_status tc_prepare_weights(hicu_handle* h, const ConvGeom& g, const float2* bank, int p, int mode,
-                               void* out, cudaStream_t st);
+// B operands of the conv and / or the adjoint (nullptr: not wanted) from one filter bank, one launch
+hicu_status tc_prepare_weights(hicu_handle* h, const ConvGeom& g, const float2* bank, int p, void* out_conv,
+                               void* out_adjoint, cudaStream_t st);
 hicu_status tc_prepare_input(hicu_handle* h, const ConvGeom& g, KView x, uint4* planar, cudaStream_t st);
 hicu_status tc_prepare_r(hicu_handle* h, const ConvGeom& g, const float2* R, int p, uint4* planar,
                          cudaStream_t st);
@@ -293,8 +297,17 @@ hicu_status launch_jl(hicu_handle* h, int64_t n, int64_t nr, int p, const double
 // the same in two parts: Q (complex128 [nr][n]) to complex64 in the handle's workspace, then the
 // compression from that copy (the reconstruction driver converts once per outer iteration)
 hicu_status jl_convert_q(hicu_handle* h, int64_t n, int64_t nr, const double* Q, float2** Qf, cudaStream_t st);
+// P: the caller's JL matrix (double, rows x p) or nullptr; Pdrawn: a float copy drawn beforehand
+// (jl_draw) or nullptr, else P is drawn here from (seed, counter)
 hicu_status launch_jl_converted(hicu_handle* h, int64_t n, int64_t nr, int p, const float2* Qf, int mode,
-                                const double* P, uint64_t seed, uint64_t counter, float* bank, cudaStream_t st);
+                                const double* P, const float* Pdrawn, uint64_t seed, uint64_t counter,
+                                float* bank, cudaStream_t st);
+// JL matrices of nsteps consecutive draws (counters counter .. counter + nsteps - 1), each
+// rows x p, into P (float, draw-major)
+hicu_status jl_draw(hicu_handle* h, int64_t rows, int p, int nsteps, uint64_t seed, uint64_t counter, float* P,
+                    cudaStream_t st);
+// the handle's side stream and its events, created on first use
+hicu_status ensure_side_stream(hicu_handle* h);
 hicu_status gd_step_filters(hicu_handle* h, const hicu_geom* geom, const hicu_region* region, float* y,
                             const uint8_t* mask, const float* filters, int32_t p, double* stats,
                             int32_t prec, cudaStream_t st);

@@ -28,14 +28,16 @@ __device__ __forceinline__ double jl_gauss(uint64_t seed, uint64_t counter, uint
   return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
 }
 
-// P (rows x p, row-major) in float; from the caller's double matrix or drawn here.
-__global__ void jl_make_p_kernel(int rows, int p, const double* __restrict__ Pin, uint64_t seed,
+// P (rows x p, row-major) in float, from the caller's double matrix or drawn here; nsteps
+// consecutive draws (counters counter, counter + 1, ...) one after another.
+__global__ void jl_make_p_kernel(int rows, int p, int nsteps, const double* __restrict__ Pin, uint64_t seed,
                                  uint64_t counter, float* __restrict__ Pout) {
-  const long long tot = (long long)rows * p;
+  const long long per = (long long)rows * p, tot = per * nsteps;
   const double scale = 1.0 / sqrt((double)p);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
        i += (long long)gridDim.x * blockDim.x) {
-    const double v = Pin ? Pin[i] : jl_gauss(seed, counter, (uint64_t)i) * scale;
+    const long long t = i / per, e = i - t * per;
+    const double v = Pin ? Pin[i] : jl_gauss(seed, counter + (uint64_t)t, (uint64_t)e) * scale;
     Pout[i] = (float)v;
   }
 }
@@ -119,6 +121,61 @@ __global__ void jl_combine_compl_kernel(int n, int m, int p, const float2* __res
   bank[(long long)k * n + a] = make_float2(P[(long long)a * p + k] - re, -im);
 }
 
+// Complement form in one launch, one CTA per column k of P, the principal vectors V (complex64
+// [m][n]) staged in shared memory: T_j = sum_a conj(V[j][a]) P[a][k] (a warp per j), then
+// bank[k][a] = P[a][k] - sum_j V[j][a] T_j.  The same sums in the same order as
+// jl_project_kernel + jl_combine_compl_kernel.  Dynamic shared memory: m n float2, n float, m float2.
+constexpr int JLF_THREADS = 512;
+
+__global__ void __launch_bounds__(JLF_THREADS) jl_compl_fused_kernel(int n, int m, int p, const float2* __restrict__ V,
+                                                                     const float* __restrict__ P,
+                                                                     float2* __restrict__ bank) {
+  extern __shared__ float2 jsm[];
+  float2* Vs = jsm;                     // [m][n]
+  float2* Ts = Vs + (size_t)m * n;      // [m]
+  float* Ps = (float*)(Ts + m);         // [n]
+  const int k = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (long long i = tid; i < (long long)m * n; i += JLF_THREADS) Vs[i] = V[i];
+  for (int a = tid; a < n; a += JLF_THREADS) Ps[a] = P[(long long)a * p + k];
+  __syncthreads();
+  for (int j = warp; j < m; j += JLF_THREADS / 32) {
+    float re = 0.f, im = 0.f;
+    for (int a = lane; a < n; a += 32) {
+      const float2 q = Vs[(size_t)j * n + a];
+      const float w = Ps[a];
+      re = fmaf(q.x, w, re);
+      im = fmaf(-q.y, w, im);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_down_sync(0xffffffffu, re, o);
+      im += __shfl_down_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) Ts[j] = make_float2(re, im);
+  }
+  __syncthreads();
+  for (int a = tid; a < n; a += JLF_THREADS) {
+    float re = 0.f, im = 0.f;
+    for (int j = 0; j < m; ++j) {
+      const float2 q = Vs[(size_t)j * n + a];
+      const float2 t = Ts[j];
+      re = fmaf(q.x, t.x, fmaf(-q.y, t.y, re));
+      im = fmaf(q.x, t.y, fmaf(q.y, t.x, im));
+    }
+    bank[(long long)k * n + a] = make_float2(Ps[a] - re, -im);
+  }
+}
+
+static size_t jl_fused_smem(int64_t n, int64_t m) { return sizeof(float2) * (size_t)(m * n + m) + sizeof(float) * (size_t)n; }
+
+hicu_status jl_draw(hicu_handle* h, int64_t rows, int p, int nsteps, uint64_t seed, uint64_t counter, float* P,
+                    cudaStream_t st) {
+  const long long tot = rows * p * (long long)nsteps;
+  int blocks = (int)((tot + 255) / 256);
+  if (blocks > 4 * h->num_sms) blocks = 4 * h->num_sms;
+  HICU_LAUNCH(h, K_JL, st, jl_make_p_kernel<<<blocks, 256, 0, st>>>((int)rows, p, nsteps, nullptr, seed, counter, P));
+  return cuda_error(h, cudaGetLastError(), "jl draw");
+}
+
 hicu_status jl_convert_q(hicu_handle* h, int64_t n, int64_t nr, const double* Q, float2** Qf, cudaStream_t st) {
   hicu_status s = HICU_OK;
   *Qf = (float2*)ws_get(h, WS_QF, sizeof(float2) * nr * n, &s);
@@ -131,16 +188,27 @@ hicu_status jl_convert_q(hicu_handle* h, int64_t n, int64_t nr, const double* Q,
 }
 
 hicu_status launch_jl_converted(hicu_handle* h, int64_t n, int64_t nr, int p, const float2* Qf, int mode,
-                                const double* P, uint64_t seed, uint64_t counter, float* bank, cudaStream_t st) {
+                                const double* P, const float* Pdrawn, uint64_t seed, uint64_t counter,
+                                float* bank, cudaStream_t st) {
   hicu_status s = HICU_OK;
   const int rows = (mode == HICU_JL_NULLSPACE) ? (int)nr : (int)n;
-  float* Pf = (float*)ws_get(h, WS_P, sizeof(float) * rows * p, &s);
-  if (s) return s;
-  {
+  const float* Pf = Pdrawn;
+  if (!Pf) {
+    float* Pw = (float*)ws_get(h, WS_P, sizeof(float) * rows * p, &s);
+    if (s) return s;
     const long long tot = (long long)rows * p;
     int blocks = (int)((tot + 255) / 256);
     if (blocks > 1024) blocks = 1024;
-    HICU_LAUNCH(h, K_JL, st, jl_make_p_kernel<<<blocks, 256, 0, st>>>(rows, p, P, seed, counter, Pf));
+    HICU_LAUNCH(h, K_JL, st, jl_make_p_kernel<<<blocks, 256, 0, st>>>(rows, p, 1, P, seed, counter, Pw));
+    Pf = Pw;
+  }
+  if (mode == HICU_JL_COMPLEMENT && nr > 0 && jl_fused_smem(n, nr) <= 200 * 1024) {
+    const cudaError_t e0 = allow_max_dynamic_smem((const void*)jl_compl_fused_kernel);
+    if (e0 != cudaSuccess) return cuda_error(h, e0, "jl smem");
+    HICU_LAUNCH(h, K_JL, st,
+                jl_compl_fused_kernel<<<p, JLF_THREADS, jl_fused_smem(n, nr), st>>>((int)n, (int)nr, p, Qf, Pf,
+                                                                                  (float2*)bank));
+    return cuda_error(h, cudaGetLastError(), "jl_compress");
   }
   dim3 grid((unsigned)((n + 127) / 128), (unsigned)p);
   if (mode == HICU_JL_NULLSPACE) {
@@ -168,7 +236,7 @@ hicu_status launch_jl(hicu_handle* h, int64_t n, int64_t nr, int p, const double
   float2* Qf = nullptr;
   hicu_status s = jl_convert_q(h, n, nr, Q, &Qf, st);
   if (s) return s;
-  return launch_jl_converted(h, n, nr, p, Qf, mode, P, seed, counter, bank, st);
+  return launch_jl_converted(h, n, nr, p, Qf, mode, P, nullptr, seed, counter, bank, st);
 }
 
 }  // namespace hicu
