@@ -151,7 +151,10 @@ hicu_status hicu_check(hicu_handle* h, void* stream);
 /*
  * Tracing: every kernel the library launches is counted; launches of one
  * selected class (hicu_kernel_class, -1 = none) are also bracketed by CUDA
- * events recorded on the launch stream.  hicu_profile_select() resets the
+ * events recorded on the launch stream, except launches on the handle's side
+ * stream (work that overlaps the caller's stream: the JL draws of an outer
+ * iteration, the compact-WY factors), which are counted but not timed, so that
+ * the class times add up the caller's stream.  hicu_profile_select() resets the
  * counters; hicu_profile_read() synchronises on the last event and returns the
  * summed device time (ms) of the timed launches, their number, and the number
  * of launches of every class since the last select/read, then resets.

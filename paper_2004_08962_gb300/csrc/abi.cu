@@ -55,6 +55,11 @@ hicu_status ensure_side_stream(hicu_handle* h) {
   return HICU_OK;
 }
 
+void prof_count(hicu_handle* h, int cls) {
+  ++h->launches_all;
+  if (h->prof_class == cls) ++h->launches_class;
+}
+
 void prof_begin(hicu_handle* h, int cls, cudaStream_t st) {
   ++h->launches_all;
   if (h->prof_class != cls) return;

@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(TDC_THREADS, 1) tridiag_cluster_kernel(const T
     }
     cl.sync();
     // --- 3. alpha, w, the next pivot row and its squares (all local reads)
-    {
+    if (warp * 32 < m) {  // only the warps that form entries need alpha
       const cdf ssum = c_warp_sum(lane < nct ? ld4(&partall[par][lane]) : c_zero());
       const cdf htau = {df_mul_f(tau.re, -0.5f), df_mul_f(tau.im, -0.5f)};
       const cdf alpha = c_mul(htau, ssum);
@@ -958,7 +958,7 @@ static hicu_status finish_principal(hicu_handle* h, int n, int r, const double2*
     cudaError_t ce = cudaEventRecord(h->side_fork, st);
     if (ce == cudaSuccess) ce = cudaStreamWaitEvent(h->side_st, h->side_fork, 0);
     if (ce != cudaSuccess) return cuda_error(h, ce, "principal subspace: fork");
-    HICU_LAUNCH(h, K_EIG, h->side_st, td_wy_t_kernel<<<nblk, 256, 0, h->side_st>>>(n, refl, tau, Tb, Yt));
+    HICU_LAUNCH_SIDE(h, K_EIG, td_wy_t_kernel<<<nblk, 256, 0, h->side_st>>>(n, refl, tau, Tb, Yt));
     ce = cudaEventRecord(h->side_join, h->side_st);
     if (ce != cudaSuccess) return cuda_error(h, ce, "principal subspace: join");
   }

@@ -146,6 +146,13 @@ struct Workspace {
     __VA_ARGS__;                       \
     hicu::prof_end((h), (cls), (st));   \
   } while (0)
+// A launch on the side stream, concurrent with the caller's stream: counted, not event-timed (the
+// class times add up the caller's stream; side work overlaps it).
+#define HICU_LAUNCH_SIDE(h, cls, ...) \
+  do {                                 \
+    hicu::prof_count((h), (cls));      \
+    __VA_ARGS__;                       \
+  } while (0)
 
 // The handle (opaque in the public header).
 struct hicu_handle {
@@ -234,6 +241,7 @@ static_assert(WS_COUNT <= hicu_handle::kSlots, "workspace slots");
 enum KClass { K_GRAM = 0, K_EIG = 1, K_CONV = 2, K_ADJOINT = 3, K_JL = 4, K_MISC = 5, K_CONV_TC = 6,
               K_ADJOINT_TC = 7, K_TRIDIAG = 8 };
 void prof_begin(hicu_handle* h, int cls, cudaStream_t st);
+void prof_count(hicu_handle* h, int cls);
 void prof_end(hicu_handle* h, int cls, cudaStream_t st);
 
 // Raise a kernel's dynamic shared-memory cap to the device's opt-in maximum, once per
@@ -335,11 +343,3 @@ __global__ void eig_scale_kernel(long long nn, double2* __restrict__ A, const un
                                  double* scale_out);
 
 }  // namespace hicu
-
-// Launch a kernel through the handle's accounting (and event timing when its class is selected).
-#define HICU_LAUNCH(h, cls, st, ...)  \
-  do {                                 \
-    hicu::prof_begin((h), (cls), (st)); \
-    __VA_ARGS__;                       \
-    hicu::prof_end((h), (cls), (st));   \
-  } while (0)

@@ -167,12 +167,13 @@ __global__ void __launch_bounds__(JLF_THREADS) jl_compl_fused_kernel(int n, int 
 
 static size_t jl_fused_smem(int64_t n, int64_t m) { return sizeof(float2) * (size_t)(m * n + m) + sizeof(float) * (size_t)n; }
 
+// on the side stream st (launch counted, not event-timed)
 hicu_status jl_draw(hicu_handle* h, int64_t rows, int p, int nsteps, uint64_t seed, uint64_t counter, float* P,
                     cudaStream_t st) {
   const long long tot = rows * p * (long long)nsteps;
   int blocks = (int)((tot + 255) / 256);
   if (blocks > 4 * h->num_sms) blocks = 4 * h->num_sms;
-  HICU_LAUNCH(h, K_JL, st, jl_make_p_kernel<<<blocks, 256, 0, st>>>((int)rows, p, nsteps, nullptr, seed, counter, P));
+  HICU_LAUNCH_SIDE(h, K_JL, jl_make_p_kernel<<<blocks, 256, 0, st>>>((int)rows, p, nsteps, nullptr, seed, counter, P));
   return cuda_error(h, cudaGetLastError(), "jl draw");
 }
 
