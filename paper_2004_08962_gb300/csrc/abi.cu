@@ -2,6 +2,7 @@
 // that chain the kernels into the steps of Algorithm 1.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -211,6 +212,8 @@ extern "C" hicu_status hicu_create(hicu_handle** out) {
     delete h;
     return HICU_ERR_ALLOC;
   }
+  const char* pdl_env = std::getenv("HICU_PDL");
+  h->pdl = !(pdl_env && pdl_env[0] == '0');
   *out = h;
   return HICU_OK;
 }
@@ -817,7 +820,7 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
       }
       for (int j = 0; j < stg.gd_steps; ++j) {
         s = launch_jl_converted(h, n, nq, stg.p, Qf, jmode, nullptr, Pall + (size_t)j * prow * stg.p, prm->seed,
-                                counter, bank, st);
+                                counter, bank, st, j > 0);
         if (s) return s;
         s = gd_step_filters(h, geom, &stg.region, y, m, bank, stg.p, dstats + 4 * counter, prm->prec, st);
         if (s) return s;

@@ -287,6 +287,8 @@ hicu_status launch_sum_partials(hicu_handle* h, const double* partial, int n, do
 // stats = {eta, objective, ||g||^2, D}
 __global__ void finalize_step_kernel(const double* __restrict__ part, int n_obj, int n_g, int n_d,
                                      double* stats) {
+  pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
+  pdl_trigger();
   __shared__ double sh[8];
   const double obj = fixed_order_sum(part, n_obj, sh);
   const double gn2 = fixed_order_sum(part + n_obj, n_g, sh);
@@ -303,12 +305,14 @@ __global__ void finalize_step_kernel(const double* __restrict__ part, int n_obj,
 
 hicu_status launch_finalize_step(hicu_handle* h, const double* part, int n_obj, int n_g, int n_d,
                                  double* stats, cudaStream_t st) {
-  HICU_LAUNCH(h, K_MISC, st, finalize_step_kernel<<<1, 256, 0, st>>>(part, n_obj, n_g, n_d, stats));
+  launch_pdl(h, K_MISC, st, dim3(1), dim3(256), 0, finalize_step_kernel, true, part, n_obj, n_g, n_d, stats);
   return cudaGetLastError() == cudaSuccess ? HICU_OK : HICU_ERR_CUDA;
 }
 
 // y <- y - eta g on unobserved entries of the region (observed entries are never written)
 __global__ void update_kernel(ConvGeom g, KView y, KView gb, MView m, const double* __restrict__ stats) {
+  pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
+  pdl_trigger();
   const double eta = stats[0];
   if (eta == 0.0) return;
   const float e = (float)eta;
@@ -342,7 +346,7 @@ hicu_status launch_update(hicu_handle* h, const ConvGeom& g, KView y, KView gb, 
   const long long total = (long long)g.C * g.ez * g.ey * g.ex;
   int blocks = (int)((total + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
-  HICU_LAUNCH(h, K_MISC, st, update_kernel<<<blocks, 256, 0, st>>>(g, y, gb, m, stats));
+  launch_pdl(h, K_MISC, st, dim3(blocks), dim3(256), 0, update_kernel, true, g, y, gb, m, stats);
   return cudaGetLastError() == cudaSuccess ? HICU_OK : HICU_ERR_CUDA;
 }
 

@@ -177,6 +177,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t taddr = *tslot;
+  // programmatic dependent launch: the set-up above overlaps the previous kernel's tail; its
+  // outputs (this kernel's inputs) are read only from here on
+  pdl_wait();
+  pdl_trigger();
   const int zspan = P.kz - 1;  // input planes beyond the last output plane of a run
 
   if (warp == 0) {
@@ -391,6 +395,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // chunk = 4 channels; channels >= C (padding) are zero.
 __global__ void tc_split_input_kernel(int C, int chunks_even, int ex, int ey, int ez, KView x,
                                       uint4* __restrict__ out) {
+  pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
+  pdl_trigger();
   const long long plane = (long long)ex * ey * ez;
   const long long tot = plane * chunks_even;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
@@ -490,6 +496,8 @@ __device__ __forceinline__ __nv_bfloat16 prep_b_elem(const PrepB& q, int n, int 
 
 // the B operands of the conv (q0) and of the adjoint (q1, tot = 0 when not wanted) in one launch
 __global__ void tc_prep_b_kernel(PrepB q0, PrepB q1, int n, int kx, int ky, int kz, const float2* __restrict__ bank) {
+  pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
+  pdl_trigger();
   const long long tot = q0.tot + q1.tot;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
        i += (long long)gridDim.x * blockDim.x) {
@@ -692,9 +700,9 @@ hicu_status tc_prepare_input(hicu_handle* h, const ConvGeom& g, KView x, uint4* 
   const int ce = chunks_even_of(g.C);
   const long long tot = (long long)g.ex * g.ey * g.ez * ce;
   int blocks = (int)std::min<long long>((tot + 255) / 256, 8192);
-  HICU_LAUNCH(h, K_MISC, st,
-              tc_split_input_kernel<<<blocks, 256, 0, st>>>(g.C, ce, g.ex, g.ey, g.ez, x, planar));
-  return cuda_error(h, cudaGetLastError(), "tc_split_input");
+  const cudaError_t e = launch_pdl(h, K_MISC, st, dim3(blocks), dim3(256), 0, tc_split_input_kernel, true, g.C, ce,
+                                   g.ex, g.ey, g.ez, x, planar);
+  return cuda_error(h, e != cudaSuccess ? e : cudaGetLastError(), "tc_split_input");
 }
 
 hicu_status tc_prepare_r(hicu_handle* h, const ConvGeom& g, const float2* R, int p, uint4* planar,
@@ -724,8 +732,9 @@ hicu_status tc_prepare_weights(hicu_handle* h, const ConvGeom& g, const float2* 
   const PrepB q0 = prep_b_of(g, p, 0, out_conv), q1 = prep_b_of(g, p, 1, out_adjoint);
   const long long tot = q0.tot + q1.tot;
   int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
-  HICU_LAUNCH(h, K_MISC, st, tc_prep_b_kernel<<<blocks, 256, 0, st>>>(q0, q1, g.n, q.kx, q.ky, q.kz, bank));
-  return cuda_error(h, cudaGetLastError(), "tc_prep_b");
+  const cudaError_t e = launch_pdl(h, K_MISC, st, dim3(blocks), dim3(256), 0, tc_prep_b_kernel, true, q0, q1, g.n,
+                                   q.kx, q.ky, q.kz, bank);
+  return cuda_error(h, e != cudaSuccess ? e : cudaGetLastError(), "tc_prep_b");
 }
 
 static hicu_status launch_plan(hicu_handle* h, TcPlan& pl, const void* in, int cls, cudaStream_t st) {
@@ -734,8 +743,9 @@ static hicu_status launch_plan(hicu_handle* h, TcPlan& pl, const void* in, int c
     return set_error(h, HICU_ERR_CUDA, "split-bf16: tensor map encoding failed");
   const cudaError_t e = allow_max_dynamic_smem((const void*)tc_corr_kernel);
   if (e != cudaSuccess) return cuda_error(h, e, "tc_corr smem");
-  HICU_LAUNCH(h, cls, st, tc_corr_kernel<<<pl.grid, TC_THREADS, pl.smem, st>>>(map, pl.P));
-  return cuda_error(h, cudaGetLastError(), "tc_corr");
+  const cudaError_t e2 = launch_pdl(h, cls, st, dim3(pl.grid), dim3(TC_THREADS), pl.smem, tc_corr_kernel, true, map,
+                                    pl.P);
+  return cuda_error(h, e2 != cudaSuccess ? e2 : cudaGetLastError(), "tc_corr");
 }
 
 // conv: x planar (region) -> R (complex64 and/or split planes), partial norms per CTA

@@ -472,6 +472,8 @@ static bool tdc_available(int n) {
 // A = 2^-e G in double-float (the largest |Re|, |Im| of G in [2^(e-1), 2^e)); scale = 2^-e
 __global__ void td_prep_kernel(long long nn, const double2* __restrict__ G, const unsigned long long* amax_bits,
                                double* scale_out, float4* __restrict__ A) {
+  pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
+  pdl_trigger();
   const double amax = __longlong_as_double((long long)*amax_bits);
   int ex2 = 0;
   if (amax > 0.0 && amax <= 1.7e308) frexp(amax, &ex2);
@@ -487,6 +489,8 @@ __global__ void td_prep_kernel(long long nn, const double2* __restrict__ G, cons
 // info: [0] lo, [1] hi (double-float), [2] tnorm, [3] pivmin (float in .x)
 __global__ void td_bounds_kernel(int n, const float2* __restrict__ d, const float2* __restrict__ e,
                                  float2* __restrict__ e2, float2* __restrict__ info) {
+  pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
+  pdl_trigger();
   __shared__ float s_lo[256], s_hi[256], s_e2[256];
   float lo = 3e38f, hi = -3e38f, e2m = 0.f;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -547,6 +551,8 @@ __global__ void __launch_bounds__(TB_THREADS) td_bisect_kernel(int n, int t0, co
                                                                const double* __restrict__ scale,
                                                                float2* __restrict__ lam_scaled,
                                                                double* __restrict__ lam_out) {
+  pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
+  pdl_trigger();
   extern __shared__ float2 bsm[];
   float2* sd = bsm;
   float2* se2 = bsm + n;
@@ -603,6 +609,8 @@ __global__ void __launch_bounds__(32) td_inviter_kernel(int n, int r, const floa
                                                         const float2* __restrict__ lam,
                                                         const float2* __restrict__ info, float2* __restrict__ Z,
                                                         int stage) {
+  pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
+  pdl_trigger();
   extern __shared__ float2 ism[];
   float2* u1i = ism;  // 1 / pivot
   float2* u2 = u1i + n;
@@ -796,6 +804,8 @@ __global__ void __launch_bounds__(BX_THREADS, 2) td_backxform_wy_kernel(int n, i
                                                                     const float4* __restrict__ Yt,
                                                                     const float2* __restrict__ Z,
                                                                     double2* __restrict__ V) {
+  pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
+  pdl_trigger();
   constexpr int NW = BX_THREADS / 32;
   extern __shared__ float4 usm2[];
   __shared__ float4 part[NW][WY_B];
@@ -874,6 +884,8 @@ __global__ void __launch_bounds__(BX_THREADS, 2) td_backxform_wy_kernel(int n, i
 // J = trace(G) - sum of the top r eigenvalues (the tail energy of Eq. 1); trace in FP64
 __global__ void td_tail_kernel(int n, int r, const double2* __restrict__ G, const double* __restrict__ lam_top,
                                double* __restrict__ J) {
+  pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
+  pdl_trigger();
   __shared__ double red[256];
   double s = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) s += G[(size_t)i * n + i].x;
@@ -963,13 +975,15 @@ static hicu_status finish_principal(hicu_handle* h, int n, int r, const double2*
     if (ce != cudaSuccess) return cuda_error(h, ce, "principal subspace: join");
   }
   // 2. eigenvalues (top r; all n when requested)
-  HICU_LAUNCH(h, K_EIG, st, td_bounds_kernel<<<1, 256, 0, st>>>(n, d, e, e2, info));
+  launch_pdl(h, K_EIG, st, dim3(1), dim3(256), 0, td_bounds_kernel, true, n, (const float2*)d, (const float2*)e, e2,
+             info);
   const size_t bsm_bytes = sizeof(float2) * 2 * (size_t)n;
   {
     cudaError_t e0 = allow_max_dynamic_smem((const void*)td_bisect_kernel);
     if (e0 != cudaSuccess) return cuda_error(h, e0, "bisection smem");
   }
-  HICU_LAUNCH(h, K_EIG, st, td_bisect_kernel<<<r, TB_THREADS, bsm_bytes, st>>>(n, n - r, d, e2, info, scale, lam, eig_top));
+  launch_pdl(h, K_EIG, st, dim3(r), dim3(TB_THREADS), bsm_bytes, td_bisect_kernel, true, n, n - r, (const float2*)d,
+             (const float2*)e2, (const float2*)info, (const double*)scale, lam, eig_top);
   if (eig_all)
     HICU_LAUNCH(h, K_EIG, st, td_bisect_kernel<<<n, TB_THREADS, bsm_bytes, st>>>(n, 0, d, e2, info, scale, nullptr, eig_all));
   // 3. eigenvectors of T, 4. back-transformation
@@ -978,7 +992,8 @@ static hicu_status finish_principal(hicu_handle* h, int n, int r, const double2*
     const size_t ism = sizeof(float2) * (stage ? 8 : 6) * (size_t)n;
     cudaError_t e0 = allow_max_dynamic_smem((const void*)td_inviter_kernel);
     if (e0 != cudaSuccess) return cuda_error(h, e0, "inverse iteration smem");
-    HICU_LAUNCH(h, K_EIG, st, td_inviter_kernel<<<r, 32, ism, st>>>(n, r, d, e, lam, info, Z, stage));
+    launch_pdl(h, K_EIG, st, dim3(r), dim3(32), ism, td_inviter_kernel, true, n, r, (const float2*)d, (const float2*)e,
+               (const float2*)lam, (const float2*)info, Z, stage);
   }
   {
     // apply the compact WY blocks, one CTA per eigenvector, once the factors are ready
@@ -990,7 +1005,9 @@ static hicu_status finish_principal(hicu_handle* h, int n, int r, const double2*
     HICU_LAUNCH(h, K_EIG, st,
                 td_backxform_wy_kernel<<<r, BX_THREADS, usm, st>>>(n, r, refl, Tb, Yt, Z, (double2*)Vout));
   }
-  if (J) HICU_LAUNCH(h, K_MISC, st, td_tail_kernel<<<1, 256, 0, st>>>(n, r, G, eig_top, J));
+  if (J)
+    launch_pdl(h, K_MISC, st, dim3(1), dim3(256), 0, td_tail_kernel, true, n, r, (const double2*)G,
+               (const double*)eig_top, J);
   return cuda_error(h, cudaGetLastError(), "principal subspace");
 }
 
@@ -1030,7 +1047,8 @@ hicu_status run_principal(hicu_handle* h, int64_t n64, int64_t r64, const double
   const int eb = (int)std::min<long long>((nn + 255) / 256, (long long)h->num_sms * 8);
   cudaMemsetAsync(amax_bits, 0, sizeof(unsigned long long), st);
   HICU_LAUNCH(h, K_EIG, st, eig_absmax_kernel<<<eb, 256, 0, st>>>(nn, G, amax_bits));
-  HICU_LAUNCH(h, K_EIG, st, td_prep_kernel<<<eb, 256, 0, st>>>(nn, G, amax_bits, scale, A));
+  launch_pdl(h, K_EIG, st, dim3(eb), dim3(256), 0, td_prep_kernel, true, nn, G, (const unsigned long long*)amax_bits,
+             scale, A);
 
   // 1. tridiagonalisation: one cluster for n <= 416, else cooperative over all SMs
   if (tdc_available(n)) {

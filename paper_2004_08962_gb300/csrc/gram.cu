@@ -82,6 +82,8 @@ __host__ __device__ inline long long task_index(int c1, int c2, int l, int C, in
 }
 
 __global__ void __launch_bounds__(256) gram_cells_kernel(GramParams P, float4* __restrict__ part) {
+  pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
+  pdl_trigger();
   __shared__ float4 vals[256 * GXSLOT];
   const ConvGeom& g = P.g;
   const long long task = blockIdx.x;
@@ -163,6 +165,8 @@ __device__ __forceinline__ int cut_index(const int* cuts, int ncut, int v) {
 
 __global__ void gram_assemble_kernel(GramParams P, const float4* __restrict__ part,
                                      double2* __restrict__ G) {
+  pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
+  pdl_trigger();
   const ConvGeom& g = P.g;
   const int n = g.n;
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -277,11 +281,12 @@ hicu_status run_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* r
   if (nt < 64) nt = 64;
   if (nt > 256) nt = 256;
   dim3 grid((unsigned)ntasks, (unsigned)npieces);
-  HICU_LAUNCH(h, K_GRAM, st, gram_cells_kernel<<<grid, nt, 0, st>>>(P, part));
+  launch_pdl(h, K_GRAM, st, dim3(grid), dim3(nt), 0, gram_cells_kernel, true, P, part);
   s = cuda_error(h, cudaGetLastError(), "gram_cells");
   if (s) return s;
   const long long nn = (long long)g.n * g.n;
-  HICU_LAUNCH(h, K_GRAM, st, gram_assemble_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(P, part, (double2*)G));
+  launch_pdl(h, K_GRAM, st, dim3((unsigned)((nn + 255) / 256)), dim3(256), 0, gram_assemble_kernel, true, P,
+             (const float4*)part, (double2*)G);
   return cuda_error(h, cudaGetLastError(), "gram_assemble");
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <mutex>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -130,6 +131,14 @@ __device__ inline bool grid_sync(const GridSync& gs, unsigned& epoch) {
   return s_ok != 0;
 }
 
+// Programmatic dependent launch: a kernel started with launch_pdl() may begin while the kernel
+// before it on the stream is still running.  Such a kernel calls pdl_wait() before its first
+// global-memory access (it returns once the preceding kernel has completed and its writes are
+// visible; without the launch attribute it returns at once) and pdl_trigger() to let its own
+// dependent start as early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ------------------------------------------------------------ host side
 
 struct Workspace {
@@ -158,6 +167,7 @@ struct Workspace {
 struct hicu_handle {
   int device = 0;
   int num_sms = 0;
+  bool pdl = true;  // programmatic dependent launches (HICU_PDL=0 turns them off)
   std::string last_error;
   static constexpr int kSlots = 32;
   hicu::Workspace ws[kSlots];
@@ -244,6 +254,28 @@ void prof_begin(hicu_handle* h, int cls, cudaStream_t st);
 void prof_count(hicu_handle* h, int cls);
 void prof_end(hicu_handle* h, int cls, cudaStream_t st);
 
+// Launch through the handle's accounting as a programmatic dependent of the previous kernel on
+// st (the kernel must call pdl_wait() before touching global memory).  allow = false, or the
+// handle's switch off: an ordinary stream-ordered launch.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(hicu_handle* h, int cls, cudaStream_t st, dim3 grid, dim3 block, size_t smem,
+                       void (*kernel)(KArgs...), bool allow, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = (allow && h->pdl) ? 1 : 0;
+  prof_begin(h, cls, st);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+  prof_end(h, cls, st);
+  return e;
+}
+
 // Raise a kernel's dynamic shared-memory cap to the device's opt-in maximum, once per
 // kernel and device (thread-safe).  Never set per launch: host threads launching the same
 // kernel with different sizes would race on the attribute.
@@ -307,9 +339,10 @@ hicu_status launch_jl(hicu_handle* h, int64_t n, int64_t nr, int p, const double
 hicu_status jl_convert_q(hicu_handle* h, int64_t n, int64_t nr, const double* Q, float2** Qf, cudaStream_t st);
 // P: the caller's JL matrix (double, rows x p) or nullptr; Pdrawn: a float copy drawn beforehand
 // (jl_draw) or nullptr, else P is drawn here from (seed, counter)
+// pdl: the launch may overlap the previous kernel on st (false after a cross-stream wait)
 hicu_status launch_jl_converted(hicu_handle* h, int64_t n, int64_t nr, int p, const float2* Qf, int mode,
                                 const double* P, const float* Pdrawn, uint64_t seed, uint64_t counter,
-                                float* bank, cudaStream_t st);
+                                float* bank, cudaStream_t st, bool pdl = false);
 // JL matrices of nsteps consecutive draws (counters counter .. counter + nsteps - 1), each
 // rows x p, into P (float, draw-major)
 hicu_status jl_draw(hicu_handle* h, int64_t rows, int p, int nsteps, uint64_t seed, uint64_t counter, float* P,

@@ -44,6 +44,8 @@ __global__ void jl_make_p_kernel(int rows, int p, int nsteps, const double* __re
 
 // complex128 -> complex64
 __global__ void to_c64_kernel(const double2* __restrict__ in, float2* __restrict__ out, long long n) {
+  pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
+  pdl_trigger();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const double2 v = in[i];
@@ -130,12 +132,29 @@ constexpr int JLF_THREADS = 512;
 __global__ void __launch_bounds__(JLF_THREADS) jl_compl_fused_kernel(int n, int m, int p, const float2* __restrict__ V,
                                                                      const float* __restrict__ P,
                                                                      float2* __restrict__ bank) {
-  extern __shared__ float2 jsm[];
+  pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
+  pdl_trigger();
+  extern __shared__ __align__(16) float2 jsm[];
   float2* Vs = jsm;                     // [m][n]
   float2* Ts = Vs + (size_t)m * n;      // [m]
   float* Ps = (float*)(Ts + m);         // [n]
   const int k = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (long long i = tid; i < (long long)m * n; i += JLF_THREADS) Vs[i] = V[i];
+  {
+    // 16-byte loads, eight in flight per thread (V is a workspace allocation: 256-byte aligned)
+    const long long nv = (long long)m * n, n4 = nv / 2;
+    const float4* V4 = reinterpret_cast<const float4*>(V);
+    float4* Vs4 = reinterpret_cast<float4*>(Vs);
+    long long i = tid;
+    for (; i + 7 * JLF_THREADS < n4; i += 8 * JLF_THREADS) {
+      float4 t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] = V4[i + u * JLF_THREADS];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) Vs4[i + u * JLF_THREADS] = t[u];
+    }
+    for (; i < n4; i += JLF_THREADS) Vs4[i] = V4[i];
+    if ((nv & 1) && tid == 0) Vs[nv - 1] = V[nv - 1];
+  }
   for (int a = tid; a < n; a += JLF_THREADS) Ps[a] = P[(long long)a * p + k];
   __syncthreads();
   for (int j = warp; j < m; j += JLF_THREADS / 32) {
@@ -184,13 +203,13 @@ hicu_status jl_convert_q(hicu_handle* h, int64_t n, int64_t nr, const double* Q,
   const long long tot = nr * n;
   int blocks = (int)((tot + 255) / 256);
   if (blocks > 2048) blocks = 2048;
-  HICU_LAUNCH(h, K_JL, st, to_c64_kernel<<<blocks, 256, 0, st>>>((const double2*)Q, *Qf, tot));
+  launch_pdl(h, K_JL, st, dim3(blocks), dim3(256), 0, to_c64_kernel, true, (const double2*)Q, *Qf, tot);
   return cuda_error(h, cudaGetLastError(), "jl convert");
 }
 
 hicu_status launch_jl_converted(hicu_handle* h, int64_t n, int64_t nr, int p, const float2* Qf, int mode,
                                 const double* P, const float* Pdrawn, uint64_t seed, uint64_t counter,
-                                float* bank, cudaStream_t st) {
+                                float* bank, cudaStream_t st, bool pdl) {
   hicu_status s = HICU_OK;
   const int rows = (mode == HICU_JL_NULLSPACE) ? (int)nr : (int)n;
   const float* Pf = Pdrawn;
@@ -206,9 +225,8 @@ hicu_status launch_jl_converted(hicu_handle* h, int64_t n, int64_t nr, int p, co
   if (mode == HICU_JL_COMPLEMENT && nr > 0 && jl_fused_smem(n, nr) <= 200 * 1024) {
     const cudaError_t e0 = allow_max_dynamic_smem((const void*)jl_compl_fused_kernel);
     if (e0 != cudaSuccess) return cuda_error(h, e0, "jl smem");
-    HICU_LAUNCH(h, K_JL, st,
-                jl_compl_fused_kernel<<<p, JLF_THREADS, jl_fused_smem(n, nr), st>>>((int)n, (int)nr, p, Qf, Pf,
-                                                                                  (float2*)bank));
+    launch_pdl(h, K_JL, st, dim3(p), dim3(JLF_THREADS), jl_fused_smem(n, nr), jl_compl_fused_kernel, pdl, (int)n,
+               (int)nr, p, (const float2*)Qf, (const float*)Pf, (float2*)bank);
     return cuda_error(h, cudaGetLastError(), "jl_compress");
   }
   dim3 grid((unsigned)((n + 127) / 128), (unsigned)p);
