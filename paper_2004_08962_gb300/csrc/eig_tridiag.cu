@@ -975,14 +975,16 @@ static hicu_status finish_principal(hicu_handle* h, int n, int r, const double2*
     if (ce != cudaSuccess) return cuda_error(h, ce, "principal subspace: join");
   }
   // 2. eigenvalues (top r; all n when requested)
-  launch_pdl(h, K_EIG, st, dim3(1), dim3(256), 0, td_bounds_kernel, true, n, (const float2*)d, (const float2*)e, e2,
+  // the eigen-solver chain is stream-ordered (allow = false): as programmatic dependents the
+  // waiting CTAs slowed it by 9 % at n = 1000 and gained nothing at n = 200
+  launch_pdl(h, K_EIG, st, dim3(1), dim3(256), 0, td_bounds_kernel, false, n, (const float2*)d, (const float2*)e, e2,
              info);
   const size_t bsm_bytes = sizeof(float2) * 2 * (size_t)n;
   {
     cudaError_t e0 = allow_max_dynamic_smem((const void*)td_bisect_kernel);
     if (e0 != cudaSuccess) return cuda_error(h, e0, "bisection smem");
   }
-  launch_pdl(h, K_EIG, st, dim3(r), dim3(TB_THREADS), bsm_bytes, td_bisect_kernel, true, n, n - r, (const float2*)d,
+  launch_pdl(h, K_EIG, st, dim3(r), dim3(TB_THREADS), bsm_bytes, td_bisect_kernel, false, n, n - r, (const float2*)d,
              (const float2*)e2, (const float2*)info, (const double*)scale, lam, eig_top);
   if (eig_all)
     HICU_LAUNCH(h, K_EIG, st, td_bisect_kernel<<<n, TB_THREADS, bsm_bytes, st>>>(n, 0, d, e2, info, scale, nullptr, eig_all));
@@ -992,7 +994,7 @@ static hicu_status finish_principal(hicu_handle* h, int n, int r, const double2*
     const size_t ism = sizeof(float2) * (stage ? 8 : 6) * (size_t)n;
     cudaError_t e0 = allow_max_dynamic_smem((const void*)td_inviter_kernel);
     if (e0 != cudaSuccess) return cuda_error(h, e0, "inverse iteration smem");
-    launch_pdl(h, K_EIG, st, dim3(r), dim3(32), ism, td_inviter_kernel, true, n, r, (const float2*)d, (const float2*)e,
+    launch_pdl(h, K_EIG, st, dim3(r), dim3(32), ism, td_inviter_kernel, false, n, r, (const float2*)d, (const float2*)e,
                (const float2*)lam, (const float2*)info, Z, stage);
   }
   {
@@ -1006,7 +1008,7 @@ static hicu_status finish_principal(hicu_handle* h, int n, int r, const double2*
                 td_backxform_wy_kernel<<<r, BX_THREADS, usm, st>>>(n, r, refl, Tb, Yt, Z, (double2*)Vout));
   }
   if (J)
-    launch_pdl(h, K_MISC, st, dim3(1), dim3(256), 0, td_tail_kernel, true, n, r, (const double2*)G,
+    launch_pdl(h, K_MISC, st, dim3(1), dim3(256), 0, td_tail_kernel, false, n, r, (const double2*)G,
                (const double*)eig_top, J);
   return cuda_error(h, cudaGetLastError(), "principal subspace");
 }
@@ -1047,7 +1049,7 @@ hicu_status run_principal(hicu_handle* h, int64_t n64, int64_t r64, const double
   const int eb = (int)std::min<long long>((nn + 255) / 256, (long long)h->num_sms * 8);
   cudaMemsetAsync(amax_bits, 0, sizeof(unsigned long long), st);
   HICU_LAUNCH(h, K_EIG, st, eig_absmax_kernel<<<eb, 256, 0, st>>>(nn, G, amax_bits));
-  launch_pdl(h, K_EIG, st, dim3(eb), dim3(256), 0, td_prep_kernel, true, nn, G, (const unsigned long long*)amax_bits,
+  launch_pdl(h, K_EIG, st, dim3(eb), dim3(256), 0, td_prep_kernel, false, nn, G, (const unsigned long long*)amax_bits,
              scale, A);
 
   // 1. tridiagonalisation: one cluster for n <= 416, else cooperative over all SMs

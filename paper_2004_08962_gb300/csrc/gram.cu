@@ -281,11 +281,13 @@ hicu_status run_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* r
   if (nt < 64) nt = 64;
   if (nt > 256) nt = 256;
   dim3 grid((unsigned)ntasks, (unsigned)npieces);
-  launch_pdl(h, K_GRAM, st, dim3(grid), dim3(nt), 0, gram_cells_kernel, true, P, part);
+  // stream-ordered (allow = false): as programmatic dependents, CTAs waiting beside the running
+  // kernel slowed the Gram by 4-8 % on GB300
+  launch_pdl(h, K_GRAM, st, dim3(grid), dim3(nt), 0, gram_cells_kernel, false, P, part);
   s = cuda_error(h, cudaGetLastError(), "gram_cells");
   if (s) return s;
   const long long nn = (long long)g.n * g.n;
-  launch_pdl(h, K_GRAM, st, dim3((unsigned)((nn + 255) / 256)), dim3(256), 0, gram_assemble_kernel, true, P,
+  launch_pdl(h, K_GRAM, st, dim3((unsigned)((nn + 255) / 256)), dim3(256), 0, gram_assemble_kernel, false, P,
              (const float4*)part, (double2*)G);
   return cuda_error(h, cudaGetLastError(), "gram_assemble");
 }
