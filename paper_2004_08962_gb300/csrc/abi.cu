@@ -23,12 +23,19 @@ hicu_status set_error(hicu_handle* h, hicu_status s, const std::string& msg) {
 cudaError_t allow_max_dynamic_smem(const void* kernel) {
   static std::mutex mu;
   static std::map<std::pair<const void*, int>, cudaError_t> done;
+  // per host thread: the (kernel, device) pairs already raised, checked without the lock
+  thread_local std::vector<std::pair<const void*, int>> seen;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  for (const auto& kd : seen)
+    if (kd.first == kernel && kd.second == dev) return cudaSuccess;
   std::lock_guard<std::mutex> lock(mu);
   auto it = done.find({kernel, dev});
-  if (it != done.end()) return it->second;
+  if (it != done.end()) {
+    if (it->second == cudaSuccess) seen.push_back({kernel, dev});
+    return it->second;
+  }
   int optin = 0;
   cudaFuncAttributes fa;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -37,6 +44,7 @@ cudaError_t allow_max_dynamic_smem(const void* kernel) {
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
   if (e != cudaSuccess) cudaGetLastError();
   done[{kernel, dev}] = e;
+  if (e == cudaSuccess) seen.push_back({kernel, dev});
   return e;
 }
 

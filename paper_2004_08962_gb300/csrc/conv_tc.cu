@@ -37,6 +37,8 @@
 #include <algorithm>
 #include <mutex>
 
+#include <map>
+#include <cstring>
 #include "hicu_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -672,16 +674,83 @@ bool encode_input_map(CUtensorMap* map, const void* base, int X, int Y, int Z, i
 
 int device_sms(hicu_handle* h) { return h->num_sms > 0 ? h->num_sms : 148; }
 
+// Plans and tensor maps are pure functions of their arguments; the descent loop asks for the same
+// few again and again, so both are kept (process-wide, under a mutex; host threads of a batch
+// share them).  A cached tensor map is keyed on its base address as well.
+struct PlanKey {
+  int v[16];
+  bool operator<(const PlanKey& o) const { return std::memcmp(v, o.v, sizeof v) < 0; }
+};
+struct PlanEntry {
+  bool ok;
+  TcPlan plan;
+};
+
+bool plan_tc_cached(TcPlan* pl, const ConvGeom& g, int mode, int p, int num_sms) {
+  static std::mutex mu;
+  static std::map<PlanKey, PlanEntry> cache;
+  PlanKey k;
+  std::memset(k.v, 0, sizeof k.v);
+  const int vals[16] = {g.C, g.kx, g.ky, g.kz, g.ex, g.ey, g.ez, g.sx, g.sy, g.sz, g.cx, g.cy, g.cz, mode, p, num_sms};
+  std::memcpy(k.v, vals, sizeof vals);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(k);
+    if (it != cache.end()) {
+      if (it->second.ok) *pl = it->second.plan;
+      return it->second.ok;
+    }
+  }
+  PlanEntry e;
+  e.ok = plan_tc(&e.plan, g, mode, p, num_sms);
+  std::lock_guard<std::mutex> lock(mu);
+  if (cache.size() > 4096) cache.clear();
+  cache[k] = e;
+  if (e.ok) *pl = e.plan;
+  return e.ok;
+}
+
+struct MapKey {
+  const void* base;
+  int v[6];
+  bool operator<(const MapKey& o) const {
+    if (base != o.base) return base < o.base;
+    return std::memcmp(v, o.v, sizeof v) < 0;
+  }
+};
+
+bool encode_input_map_cached(CUtensorMap* map, const void* base, int X, int Y, int Z, int planes, int W, int Ty) {
+  static std::mutex mu;
+  static std::map<MapKey, CUtensorMap> cache;
+  MapKey k;
+  k.base = base;
+  const int vals[6] = {X, Y, Z, planes, W, Ty};
+  std::memcpy(k.v, vals, sizeof vals);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(k);
+    if (it != cache.end()) {
+      *map = it->second;
+      return true;
+    }
+  }
+  if (!encode_input_map(map, base, X, Y, Z, planes, W, Ty)) return false;
+  std::lock_guard<std::mutex> lock(mu);
+  if (cache.size() > 1024) cache.clear();
+  cache[k] = *map;
+  return true;
+}
+
 }  // namespace
 
 bool tc_supported(const ConvGeom& g) {
   TcPlan a, b;
-  return plan_tc(&a, g, 0, 8, 152) && plan_tc(&b, g, 1, 8, 152) && encode_fn() != nullptr;
+  return plan_tc_cached(&a, g, 0, 8, 152) && plan_tc_cached(&b, g, 1, 8, 152) && encode_fn() != nullptr;
 }
 
 bool tc_supported_p(const ConvGeom& g, int p) {
   TcPlan a, b;
-  return plan_tc(&a, g, 0, p, 152) && plan_tc(&b, g, 1, p, 152) && encode_fn() != nullptr;
+  return plan_tc_cached(&a, g, 0, p, 152) && plan_tc_cached(&b, g, 1, p, 152) && encode_fn() != nullptr;
 }
 
 size_t tc_x_bytes(const ConvGeom& g) {
@@ -739,7 +808,7 @@ hicu_status tc_prepare_weights(hicu_handle* h, const ConvGeom& g, const float2* 
 
 static hicu_status launch_plan(hicu_handle* h, TcPlan& pl, const void* in, int cls, cudaStream_t st) {
   CUtensorMap map;
-  if (!encode_input_map(&map, in, pl.Xin, pl.Yin, pl.P.Zin, 2 * pl.P.chunks_even, pl.P.Wb, pl.P.Ty))
+  if (!encode_input_map_cached(&map, in, pl.Xin, pl.Yin, pl.P.Zin, 2 * pl.P.chunks_even, pl.P.Wb, pl.P.Ty))
     return set_error(h, HICU_ERR_CUDA, "split-bf16: tensor map encoding failed");
   const cudaError_t e = allow_max_dynamic_smem((const void*)tc_corr_kernel);
   if (e != cudaSuccess) return cuda_error(h, e, "tc_corr smem");
@@ -752,7 +821,7 @@ static hicu_status launch_plan(hicu_handle* h, TcPlan& pl, const void* in, int c
 hicu_status launch_conv_tc(hicu_handle* h, const ConvGeom& g, const uint4* xplanar, const void* bw, int p,
                            float2* R, uint4* Rs, double* partial, int* nblocks, cudaStream_t st) {
   TcPlan pl;
-  if (!plan_tc(&pl, g, 0, p, device_sms(h)))
+  if (!plan_tc_cached(&pl, g, 0, p, device_sms(h)))
     return set_error(h, HICU_ERR_UNSUPPORTED, "split-bf16 conv: geometry or filter bank does not fit the kernel");
   *nblocks = pl.grid;
   if (!partial) return HICU_OK;
@@ -772,7 +841,7 @@ hicu_status launch_conv_tc(hicu_handle* h, const ConvGeom& g, const uint4* xplan
 hicu_status launch_adjoint_tc(hicu_handle* h, const ConvGeom& g, const uint4* Rs, const void* bw, int p,
                               MView m, KView gout, double* partial, int* nblocks, cudaStream_t st) {
   TcPlan pl;
-  if (!plan_tc(&pl, g, 1, p, device_sms(h)))
+  if (!plan_tc_cached(&pl, g, 1, p, device_sms(h)))
     return set_error(h, HICU_ERR_UNSUPPORTED,
                      "split-bf16 adjoint: geometry or filter bank does not fit the kernel");
   *nblocks = pl.grid;
