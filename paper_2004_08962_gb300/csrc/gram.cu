@@ -157,6 +157,94 @@ __global__ void __launch_bounds__(256) gram_cells_kernel(GramParams P, float4* _
   }
 }
 
+// Row-streaming form for regions up to 256 positions wide: a CTA per (task, z piece), a thread
+// per x position.  The CTA walks every row of its planes in order; a thread keeps one
+// double-word accumulator for the y cell it is in and, when the row enters the next y cell,
+// adds it into that cell's slot of a shared [y cell][x] buffer (its own column: no other thread
+// writes it).  At the end the x cells of every y cell are summed (single-position x cells are
+// copied, the interior cell by a warp reduction) into the same partial layout as
+// gram_cells_kernel with one y piece per y cell.  The border rows, one-row cells, no longer cost a
+// CTA and an x reduction each.  Dynamic shared memory: ncy * ex float4.
+__global__ void gram_rows_kernel(GramParams P, float4* __restrict__ part) {
+  pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
+  pdl_trigger();
+  extern __shared__ float4 cellbuf[];  // [ncy][ex]
+  const ConvGeom& g = P.g;
+  const long long task = blockIdx.x;
+  const int pzi = blockIdx.y;
+  int c1, c2, l;
+  decode_task(task, g.C, P.nl, P.nlh, P.center, c1, c2, l);
+  const int ddx = l % P.lx - (g.kx - 1);
+  const int ddy = (l / P.lx) % P.ly - (g.ky - 1);
+  const int ddz = l / (P.lx * P.ly) - (g.kz - 1);
+  const float2* xa = P.x.p + (long long)c1 * P.x.sc;
+  const float2* xb = P.x.p + (long long)c2 * P.x.sc;
+  const int xx = threadIdx.x;
+  int vx = xx + ddx;
+  bool ok = xx < g.ex;
+  if (g.cx) vx = wrap(vx, g.ex);
+  else ok = ok && vx >= 0 && vx < g.ex;
+  if (xx < g.ex)
+    for (int c = 0; c < P.ncy; ++c) cellbuf[c * g.ex + xx] = make_float4(0.f, 0.f, 0.f, 0.f);
+  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+  int cell = -1;
+  auto flush = [&]() {
+    if (cell >= 0 && xx < g.ex) {
+      float4* slot = &cellbuf[cell * g.ex + xx];
+      const cdf sum = c_add(ld4(slot), cdf{{rh, rl}, {ih, il}});
+      st4(slot, sum);
+    }
+    rh = rl = ih = il = 0.f;
+  };
+  for (int z = P.pz0[pzi]; z < P.pz1[pzi]; ++z) {
+    int vz = z + ddz;
+    if (g.cz) vz = wrap(vz, g.ez);
+    else if (vz < 0 || vz >= g.ez) continue;
+    int cy = 0;
+    for (int y = 0; y < g.ey; ++y) {
+      while (P.cuty[cy + 1] <= y) ++cy;
+      if (cy != cell) {
+        flush();
+        cell = cy;
+      }
+      int vy = y + ddy;
+      if (g.cy) vy = wrap(vy, g.ey);
+      else if (vy < 0 || vy >= g.ey) continue;
+      if (ok) {
+        const float2 a = xa[(long long)(P.x.oz + z) * P.x.sz + (long long)(P.x.oy + y) * P.x.sy + P.x.ox + xx];
+        const float2 b = xb[(long long)(P.x.oz + vz) * P.x.sz + (long long)(P.x.oy + vy) * P.x.sy + P.x.ox + vx];
+        // conj(a) * b = (ar br + ai bi) + i (ar bi - ai br)
+        dd_acc(a.x, b.x, rh, rl);
+        dd_acc(a.y, b.y, rh, rl);
+        dd_acc(a.x, b.y, ih, il);
+        dd_acc(-a.y, b.x, ih, il);
+        dd_renorm(rh, rl);
+        dd_renorm(ih, il);
+      }
+    }
+  }
+  flush();
+  __syncthreads();
+  // x cells of every y cell
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const long long base = (task * (P.npy * P.npz) + (long long)pzi * P.npy) * P.ncx;
+  for (int cyi = warp; cyi < P.ncy; cyi += nw) {
+    const float4* row = cellbuf + cyi * g.ex;
+    float4* out = part + base + (long long)cyi * P.ncx;
+    for (int ci = 0; ci < P.ncx; ++ci) {
+      const int x0 = P.cutx[ci], x1 = P.cutx[ci + 1];
+      if (x1 - x0 == 1) {
+        if (lane == 0) out[ci] = row[x0];
+        continue;
+      }
+      cdf acc = c_zero();
+      for (int x = x0 + lane; x < x1; x += 32) acc = c_add(acc, ld4(&row[x]));
+      acc = c_warp_sum(acc);
+      if (lane == 0) st4(&out[ci], acc);
+    }
+  }
+}
+
 __device__ __forceinline__ int cut_index(const int* cuts, int ncut, int v) {
   for (int i = 0; i < ncut; ++i)
     if (cuts[i] == v) return i;
@@ -274,16 +362,36 @@ hicu_status run_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* r
   P.nlh = (P.nl + 1) / 2;
   P.center = (P.nl - 1) / 2;
   const long long ntasks = (long long)g.C * P.nlh + (long long)P.nl * ((long long)g.C * (g.C - 1) / 2);
+  // row-streaming kernel when a thread per x position fits one CTA and the [y cell][x] buffer
+  // fits shared memory; its y pieces are the y cells
+  const size_t rows_smem = sizeof(float4) * (size_t)P.ncy * g.ex;
+  const bool rows_form = g.ex <= 256 && rows_smem <= 96 * 1024;
+  if (rows_form) {
+    P.npy = P.ncy;
+    for (int c = 0; c < P.ncy; ++c) {
+      P.py0[c] = P.cuty[c];
+      P.py1[c] = P.cuty[c + 1];
+      P.pyc[c] = c;
+    }
+  }
   const int npieces = P.npy * P.npz;
   float4* part = (float4*)ws_get(h, WS_GRAM_PART, sizeof(float4) * ntasks * npieces * P.ncx, &s);
   if (s) return s;
-  int nt = ((g.ex + GXSLOT - 1) / GXSLOT + 31) / 32 * 32;
-  if (nt < 64) nt = 64;
-  if (nt > 256) nt = 256;
-  dim3 grid((unsigned)ntasks, (unsigned)npieces);
   // stream-ordered (allow = false): as programmatic dependents, CTAs waiting beside the running
   // kernel slowed the Gram by 4-8 % on GB300
-  launch_pdl(h, K_GRAM, st, dim3(grid), dim3(nt), 0, gram_cells_kernel, false, P, part);
+  if (rows_form) {
+    const int nt = (g.ex + 31) / 32 * 32;
+    const cudaError_t e0 = allow_max_dynamic_smem((const void*)gram_rows_kernel);
+    if (e0 != cudaSuccess) return cuda_error(h, e0, "gram smem");
+    launch_pdl(h, K_GRAM, st, dim3((unsigned)ntasks, (unsigned)P.npz), dim3(nt), rows_smem, gram_rows_kernel, false,
+               P, part);
+  } else {
+    int nt = ((g.ex + GXSLOT - 1) / GXSLOT + 31) / 32 * 32;
+    if (nt < 64) nt = 64;
+    if (nt > 256) nt = 256;
+    launch_pdl(h, K_GRAM, st, dim3((unsigned)ntasks, (unsigned)npieces), dim3(nt), 0, gram_cells_kernel, false, P,
+               part);
+  }
   s = cuda_error(h, cudaGetLastError(), "gram_cells");
   if (s) return s;
   const long long nn = (long long)g.n * g.n;

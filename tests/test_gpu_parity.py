@@ -122,8 +122,10 @@ def test_gd_step_filters_parity(H, name):
 
 
 @pytest.mark.parametrize("name", ["2d_64_c4_p4", "2d_odd_region", "3d_region", "cine_circular_t",
-                                  "2d_c16_p20", "tiny_one_output"])
+                                  "2d_c16_p20", "tiny_one_output", "2d_wide_two_x_tiles", "3d_c8_k5_region",
+                                  "cine_c8_k5_circular_t"])
 def test_gram_parity(H, name):
+    """Regions up to 256 positions wide run the row-streaming kernel, the 300-wide one the cell kernel."""
     from paper_2004_08962_gb300 import hicu
     og, oreg, hg, hr, x, f, mask, p, _ = setup(name, seed=3)
     G = hicu.hicu_gram(H, hg, hr, cuda(x)).cpu().numpy()
