@@ -562,8 +562,8 @@ static hicu_status gd_step_filters_tc(hicu_handle* h, const hicu_geom* geom, con
   if ((s = launch_adjoint_tc(h, g, rpl, bwa, p, mv, gview, part + n1, &n2, st))) return s;
   if ((s = tc_prepare_input(h, g, gview, gpl, st))) return s;
   if ((s = launch_conv_tc(h, g, gpl, bwc, p, nullptr, nullptr, part + n1 + n2, &n3, st))) return s;
-  if ((s = launch_finalize_step(h, part, n1, n2, n3, st4, st))) return cuda_error(h, cudaGetLastError(), "finalize");
-  if ((s = launch_update(h, g, yv, gview, mv, st4, st))) return cuda_error(h, cudaGetLastError(), "update");
+  if ((s = launch_update_step(h, g, yv, gview, mv, part, n1, n2, n3, st4, st)))
+    return cuda_error(h, cudaGetLastError(), "update");
   return HICU_OK;
 }
 
@@ -604,9 +604,7 @@ hicu_status gd_step_filters(hicu_handle* h, const hicu_geom* geom, const hicu_re
   if (s) return s;
   s = launch_conv_fp32(h, g, gview, b.fT, p, b.Ppad, nullptr, part + n1 + n2, &n3, st);
   if (s) return s;
-  s = launch_finalize_step(h, part, n1, n2, n3, st4, st);
-  if (s) return cuda_error(h, cudaGetLastError(), "finalize");
-  s = launch_update(h, g, yv, gview, mv, st4, st);
+  s = launch_update_step(h, g, yv, gview, mv, part, n1, n2, n3, st4, st);
   if (s) return cuda_error(h, cudaGetLastError(), "update");
   return HICU_OK;
 }

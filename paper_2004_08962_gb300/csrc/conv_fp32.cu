@@ -284,36 +284,31 @@ hicu_status launch_sum_partials(hicu_handle* h, const double* partial, int n, do
   return cudaGetLastError() == cudaSuccess ? HICU_OK : HICU_ERR_CUDA;
 }
 
-// stats = {eta, objective, ||g||^2, D}
-__global__ void finalize_step_kernel(const double* __restrict__ part, int n_obj, int n_g, int n_d,
-                                     double* stats) {
+// The descent step's finalisation and update in one launch: every CTA forms {eta, objective,
+// ||g||^2, D} from the partial sums in the same fixed order (so all agree bitwise), CTA 0 stores
+// them, and every CTA applies y <- y - eta g to its share of the unobserved entries.
+__global__ void update_step_kernel(ConvGeom g, KView y, KView gb, MView m, const double* __restrict__ part,
+                                   int n_obj, int n_g, int n_d, double* stats) {
   pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
   pdl_trigger();
   __shared__ double sh[8];
+  __shared__ double s_eta;
   const double obj = fixed_order_sum(part, n_obj, sh);
   const double gn2 = fixed_order_sum(part + n_obj, n_g, sh);
   const double D = fixed_order_sum(part + n_obj + n_g, n_d, sh);
   if (threadIdx.x == 0) {
     double eta = 0.0;
     if (D > 0.0 && gn2 > 0.0 && isfinite(D) && isfinite(gn2)) eta = gn2 / D;
-    stats[0] = eta;
-    stats[1] = obj;
-    stats[2] = gn2;
-    stats[3] = D;
+    if (blockIdx.x == 0) {
+      stats[0] = eta;
+      stats[1] = obj;
+      stats[2] = gn2;
+      stats[3] = D;
+    }
+    s_eta = eta;
   }
-}
-
-hicu_status launch_finalize_step(hicu_handle* h, const double* part, int n_obj, int n_g, int n_d,
-                                 double* stats, cudaStream_t st) {
-  launch_pdl(h, K_MISC, st, dim3(1), dim3(256), 0, finalize_step_kernel, true, part, n_obj, n_g, n_d, stats);
-  return cudaGetLastError() == cudaSuccess ? HICU_OK : HICU_ERR_CUDA;
-}
-
-// y <- y - eta g on unobserved entries of the region (observed entries are never written)
-__global__ void update_kernel(ConvGeom g, KView y, KView gb, MView m, const double* __restrict__ stats) {
-  pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
-  pdl_trigger();
-  const double eta = stats[0];
+  __syncthreads();
+  const double eta = s_eta;
   if (eta == 0.0) return;
   const float e = (float)eta;
   const long long total = (long long)g.C * g.ez * g.ey * g.ex;
@@ -341,13 +336,17 @@ __global__ void update_kernel(ConvGeom g, KView y, KView gb, MView m, const doub
   }
 }
 
-hicu_status launch_update(hicu_handle* h, const ConvGeom& g, KView y, KView gb, MView m,
-                          const double* stats, cudaStream_t st) {
+hicu_status launch_update_step(hicu_handle* h, const ConvGeom& g, KView y, KView gb, MView m, const double* part,
+                               int n_obj, int n_g, int n_d, double* stats, cudaStream_t st) {
   const long long total = (long long)g.C * g.ez * g.ey * g.ex;
+  // one wave of CTAs (each forms eta once, then strides over its share)
   int blocks = (int)((total + 255) / 256);
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  launch_pdl(h, K_MISC, st, dim3(blocks), dim3(256), 0, update_kernel, true, g, y, gb, m, stats);
+  const int cap = 4 * (h->num_sms > 0 ? h->num_sms : 152);
+  if (blocks > cap) blocks = cap;
+  launch_pdl(h, K_MISC, st, dim3(blocks), dim3(256), 0, update_step_kernel, true, g, y, gb, m, part, n_obj, n_g,
+             n_d, stats);
   return cudaGetLastError() == cudaSuccess ? HICU_OK : HICU_ERR_CUDA;
 }
+
 
 }  // namespace hicu

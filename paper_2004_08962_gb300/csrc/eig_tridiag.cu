@@ -55,16 +55,81 @@ struct TdArgs {
 __device__ __forceinline__ float2 dpack(dfl a) { return make_float2(a.hi, a.lo); }
 __device__ __forceinline__ dfl dload(float2 a) { return {a.x, a.y}; }
 
-// One barrier per reflector.  Global row g is owned by CTA g mod G for the whole run and, with
-// ROWS_IN_SMEM, held in that CTA's shared memory (local row g / G); it is updated in place by its
-// owner only, except row k+1, the next pivot row: nobody writes it during step k, its owner
+// Householder scalars of the pivot row x (length m + 1; squares of x in xsq): tau, the inverse
+// 1 / (x0 - beta) of v's leading entry before normalisation, beta; one warp.
+__device__ __forceinline__ void td_scalars(int m, const float4* x, const float2* xsq, cdf& tau, cdf& scale,
+                                            dfl& beta) {
+  const int lane = threadIdx.x & 31;
+  dfl t2 = df_f(0.f);
+  for (int j = 2 + lane; j <= m; j += 32) t2 = df_add(t2, dload(xsq[j]));
+  const dfl xn2 = df_warp_sum(t2);
+  const cdf x0 = c_conj(ld4(&x[1]));
+  tau = c_zero();
+  scale = c_zero();
+  beta = x0.re;
+  if (!(xn2.hi == 0.f && x0.im.hi == 0.f)) {
+    const dfl nrm = df_sqrt(df_add(df_add(df_mul(x0.re, x0.re), df_mul(x0.im, x0.im)), xn2));
+    beta = x0.re.hi >= 0.f ? df_neg(nrm) : nrm;
+    const dfl rb = df_rcp(beta);
+    tau.re = df_sub(df_f(1.f), df_mul(x0.re, rb));  // (beta - x0.re) / beta
+    tau.im = df_neg(df_mul(x0.im, rb));
+    const cdf den = {df_sub(x0.re, beta), x0.im};
+    const dfl dd = df_add(df_mul(den.re, den.re), df_mul(den.im, den.im));
+    const dfl rd = df_rcp(dd);
+    scale.re = df_mul(den.re, rd);
+    scale.im = df_neg(df_mul(den.im, rd));
+  }
+}
+
+// Grid barrier on a monotonic arrival counter: every CTA adds one (fire-and-forget, after a fence)
+// and polls until the count reaches (epoch + 1) * G, one L2 round trip after the last arrival.
+// Bounded like grid_sync: gives up after gs.timeout_ns (or another CTA's error), records
+// HICU_ERR_TIMEOUT and returns false in every thread of the CTA.  gs.count starts at zero.
+__device__ inline bool grid_sync_count(const GridSync& gs, unsigned& epoch) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned target = (epoch + 1u) * gs.nblocks;
+    __threadfence();
+    atomicAdd(gs.count, 1u);
+    unsigned long long t0 = 0;
+    for (unsigned it = 0; ld_acquire_u32(gs.count) < target; ++it) {
+      if ((it & 255u) == 255u) {
+        const unsigned long long t = global_ns();
+        if (t0 == 0) t0 = t;
+        if (t - t0 > gs.timeout_ns || *((volatile int*)gs.err) != 0) {
+          atomicExch(gs.err, (int)HICU_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  ++epoch;
+  return s_ok != 0;
+}
+
+// One grid barrier per reflector.  Global row g is owned by CTA g mod G for the whole run and,
+// with ROWS_IN_SMEM, held in that CTA's shared memory (local row g / G); it is updated in place by
+// its owner only, except row k+1, the next pivot row: nobody writes it during step k, its owner
 // publishes the stored values before the barrier, and every CTA forms its updated values from
 // them and v, w, so the next Householder vector needs no second barrier.  w0, the partial sums
 // and the published row alternate between two buffers: a CTA can start step k+1 while others
 // still read step k's, but cannot reach step k+2 before every CTA has passed step k+1's barrier.
-// Within a step (as in the one-cluster form below): the own rows' sums against conj(x) run on
-// warps 0..nw-2 while warp nw-1 forms the Householder scalars; v, w0 and the CTA's partial sum
-// follow; after the grid barrier every warp sums the G partials itself.
+// Per step k (as in the one-cluster form below):
+//   1. row sums s_i = sum_{j>=1} A_ij conj(x_{1+j}) of the own rows; w0_i = tau (A_i0 +
+//      s_i / (x0 - beta)) to global memory and conj(w0_i) v_i to shared memory.  CTA barrier.
+//   2. v; warp 0: the CTA's partial sum of conj(w0) v to global memory.  Grid barrier.
+//   3. w0 and the published row prefetched, the G partial sums (every warp) -> alpha;
+//      w = w0 + alpha v and the next pivot row x' = (stored row k+1) - conj(w) - w_0 conj(v)
+//      with the squares of its entries.  CTA barrier.
+//   4. warps 0..nw-2: rank-2 update of the own rows but row k+1; warp nw-1 meanwhile: the
+//      Householder scalars of step k+1 from x'.  CTA barrier.
+constexpr int TD_PF = 4;  // entries per thread prefetched after the barrier
+
 template <bool ROWS_IN_SMEM>
 __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
   extern __shared__ float4 tsm[];
@@ -74,10 +139,10 @@ __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
   float4* x = tsm;             // [n] current pivot row k: x[j] = A[k][k + j]
   float4* v = x + n;           // [n]
   float4* w = v + n;           // [n]
-  float4* srow = w + n;        // [2R] s_i of the own rows, then their entries A_i0
-  float4* rows = srow + 2 * R;  // [R][n] own rows (ROWS_IN_SMEM)
+  float4* pcs = w + n;         // [2R] conj(w0_i) v_i of the own rows (first R used)
+  float4* rows = pcs + 2 * R;  // [R][n] own rows (ROWS_IN_SMEM)
   float2* xsq = (float2*)(rows + (ROWS_IN_SMEM ? (size_t)R * n : 0));  // [n] squares of x
-  __shared__ float4 hs[2];     // tau, 1 / (x0 - beta)
+  __shared__ float4 hs[3];     // tau, 1 / (x0 - beta), beta of the current step
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = TD_THREADS / 32;
   auto row_of = [&](int g) -> float4* {
     return ROWS_IN_SMEM ? rows + (size_t)(g / G) * n : a.A + (size_t)g * n;
@@ -94,125 +159,133 @@ __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
     xsq[j] = dpack(df_add(df_mul({xj.x, xj.y}, {xj.x, xj.y}), df_mul({xj.z, xj.w}, {xj.z, xj.w})));
   }
   __syncthreads();
+  if (warp == nw - 1) {
+    cdf tau, scale;
+    dfl beta;
+    td_scalars(n - 1, x, xsq, tau, scale, beta);
+    if (lane == 0) {
+      st4(&hs[0], tau);
+      st4(&hs[1], scale);
+      hs[2] = make_float4(beta.hi, beta.lo, 0.f, 0.f);
+    }
+  }
+  __syncthreads();
   for (int k = 0; k < n - 1; ++k) {
     const int m = n - k - 1;
     const int par = k & 1;
+    const cdf tau = ld4(&hs[0]), scale = ld4(&hs[1]);
+    const bool active = !(tau.re.hi == 0.f && tau.im.hi == 0.f);
+    if (c == 0 && tid == 0) {
+      a.d[k] = dpack(ld4(&x[0]).re);
+      a.e[k] = dpack({hs[2].x, hs[2].y});
+      st4(&a.tau[k], tau);
+    }
     // --- the owner of row k+1 publishes it (stored values, columns k+1 ..)
     float4* pub = a.prow + par * n;
     if ((k + 1) % G == c) {
       const float4* src = row_of(k + 1) + (k + 1);
       for (int j = tid; j < m; j += TD_THREADS) pub[j] = src[j];
     }
+    float4* wg = a.w + par * n;
+    float4* pg = a.part + par * G;
     const int i0 = ((c - (k + 1)) % G + G) % G;  // first relative row owned by this CTA
     const int nown = i0 < m ? (m - 1 - i0) / G + 1 : 0;
-    // --- 1. row sums against conj(x) / Householder scalars
-    if (warp < nw - 1) {
-      for (int q = warp; q < nown; q += nw - 1) {
-        const float4* row = row_of(k + 1 + i0 + q * G) + (k + 1);
-        cdf y = c_zero();
-        for (int j = 1 + lane; j < m; j += 32) c_acc_mul(y, ld4(&row[j]), c_conj(ld4(&x[1 + j])));
-        y = c_warp_sum(y);
-        if (lane == 0) {
-          st4(&srow[q], y);
-          srow[R + q] = row[0];
-        }
-      }
-    } else {
-      dfl t2 = df_f(0.f);
-      for (int j = 2 + lane; j <= m; j += 32) t2 = df_add(t2, dload(xsq[j]));
-      const dfl xn2 = df_warp_sum(t2);
-      const cdf x0 = c_conj(ld4(&x[1]));
-      cdf tau = c_zero(), scale = c_zero();
-      dfl beta = x0.re;
-      if (!(xn2.hi == 0.f && x0.im.hi == 0.f)) {
-        const dfl nrm = df_sqrt(df_add(df_add(df_mul(x0.re, x0.re), df_mul(x0.im, x0.im)), xn2));
-        beta = x0.re.hi >= 0.f ? df_neg(nrm) : nrm;
-        const dfl rb = df_rcp(beta);
-        tau.re = df_sub(df_f(1.f), df_mul(x0.re, rb));  // (beta - x0.re) / beta
-        tau.im = df_neg(df_mul(x0.im, rb));
-        const cdf den = {df_sub(x0.re, beta), x0.im};  // v = x / (x0 - beta)
-        const dfl dd = df_add(df_mul(den.re, den.re), df_mul(den.im, den.im));
-        const dfl rd = df_rcp(dd);
-        scale.re = df_mul(den.re, rd);
-        scale.im = df_neg(df_mul(den.im, rd));
-      }
+    const int lrow0 = (k + 1 + i0) / G;           // its local row index
+    // --- 1. row sums against conj(x); w0 of the own rows
+    for (int q = warp; q < nown; q += nw) {
+      const int i = i0 + q * G;
+      const float4* row = row_of(k + 1 + i) + (k + 1);
+      cdf y = c_zero();
+      for (int j = 1 + lane; j < m; j += 32) c_acc_mul(y, ld4(&row[j]), c_conj(ld4(&x[1 + j])));
+      y = c_warp_sum(y);
       if (lane == 0) {
-        st4(&hs[0], tau);
-        st4(&hs[1], scale);
-        if (c == 0) {
-          a.d[k] = dpack(ld4(&x[0]).re);
-          a.e[k] = dpack(beta);
-          st4(&a.tau[k], tau);
-        }
+        const cdf w0 = c_mul(tau, c_add(ld4(&row[0]), c_mul(scale, y)));
+        st4(&wg[i], w0);
+        const cdf vi = i == 0 ? cdf{{1.f, 0.f}, {0.f, 0.f}} : c_mul(c_conj(ld4(&x[1 + i])), scale);
+        st4(&pcs[q], c_mulc(w0, vi));
       }
     }
     __syncthreads();
-    // --- 2. v; w0 = tau (A_i0 + s_i / (x0 - beta)) of the own rows and the CTA's partial sum
-    const cdf tau = ld4(&hs[0]), scale = ld4(&hs[1]);
-    const bool active = !(tau.re.hi == 0.f && tau.im.hi == 0.f);
+    // --- 2. v; the CTA's partial sum
     for (int j = tid; j < m; j += TD_THREADS) {
       const cdf vj = j == 0 ? cdf{{1.f, 0.f}, {0.f, 0.f}} : c_mul(c_conj(ld4(&x[1 + j])), scale);
       st4(&v[j], vj);
       if (c == 0) st4(&a.refl[(long long)k * n + j], vj);
     }
-    float4* wg = a.w + par * n;
-    float4* pg = a.part + par * G;
     if (warp == 0) {
       cdf pc = c_zero();
-      for (int q = lane; q < nown; q += 32) {
-        const int i = i0 + q * G;
-        const cdf w0 = c_mul(tau, c_add(ld4(&srow[R + q]), c_mul(scale, ld4(&srow[q]))));
-        st4(&wg[i], w0);
-        const cdf vi = i == 0 ? cdf{{1.f, 0.f}, {0.f, 0.f}} : c_mul(c_conj(ld4(&x[1 + i])), scale);
-        pc = c_add(pc, c_mulc(w0, vi));
-      }
+      for (int q = lane; q < nown; q += 32) pc = c_add(pc, ld4(&pcs[q]));
       pc = c_warp_sum(pc);
       if (lane == 0) st4(&pg[c], pc);
     }
-    if (!grid_sync(a.gs, epoch)) return;
-    // --- 3. alpha = -tau/2 sum conj(w0) v (every warp sums the G partials); w = w0 + alpha v
-    {
+    if (!grid_sync_count(a.gs, epoch)) return;
+    // --- 3. alpha, w, the next pivot row and its squares
+    if (warp * 32 < m) {
+      float4 wpf[TD_PF], ppf[TD_PF];
+#pragma unroll
+      for (int t = 0; t < TD_PF; ++t) {
+        const int j = tid + t * TD_THREADS;
+        if (j < m) {
+          wpf[t] = __ldcg(&wg[j]);
+          ppf[t] = __ldcg(&pub[j]);
+        }
+      }
+      const float4 w00 = __ldcg(&wg[0]);
       cdf sp = c_zero();
       for (int q = lane; q < G; q += 32) sp = c_add(sp, ld4(&pg[q]));
       const cdf ssum = c_warp_sum(sp);
       const cdf htau = {df_mul_f(tau.re, -0.5f), df_mul_f(tau.im, -0.5f)};
       const cdf alpha = c_mul(htau, ssum);
-      for (int j = tid; j < m; j += TD_THREADS) st4(&w[j], c_add(ld4(&wg[j]), c_mul(alpha, ld4(&v[j]))));
+      const cdf w0c = c_add({{w00.x, w00.y}, {w00.z, w00.w}}, alpha);  // w_0 (v_0 = 1)
+      auto form = [&](int j, const float4 wr, const float4 pr) {
+        const cdf vj = ld4(&v[j]);
+        const cdf wj = c_add({{wr.x, wr.y}, {wr.z, wr.w}}, c_mul(alpha, vj));
+        st4(&w[j], wj);
+        const cdf xj = c_sub({{pr.x, pr.y}, {pr.z, pr.w}}, c_add(c_conj(wj), c_mul(w0c, c_conj(vj))));
+        st4(&x[j], xj);
+        xsq[j] = dpack(df_add(df_mul(xj.re, xj.re), df_mul(xj.im, xj.im)));
+      };
+#pragma unroll
+      for (int t = 0; t < TD_PF; ++t)
+        if (tid + t * TD_THREADS < m) form(tid + t * TD_THREADS, wpf[t], ppf[t]);
+      for (int j = tid + TD_PF * TD_THREADS; j < m; j += TD_THREADS) form(j, __ldcg(&wg[j]), __ldcg(&pub[j]));
     }
     __syncthreads();
-    // --- 4. rank-2 update of the own rows but row k+1: A_ij -= v_i conj(w_j) + w_i conj(v_j)
-    if (active) {
-      const int tot = nown * m;
-      const float rm = 1.f / (float)m;
-      for (int idx = tid; idx < tot; idx += TD_THREADS) {
-        // idx / m: exact while nown m < 2^21 (the rounding error of the product stays below the
-        // distance 0.5 / m of (idx + 0.5) / m from an integer)
-        const int q = (int)__fmul_rn((float)idx + 0.5f, rm);
-        const int j = idx - q * m;
-        const int i = i0 + q * G;
-        if (i == 0) continue;
-        float4* aij = row_of(k + 1 + i) + (k + 1) + j;
-        const cdf vi = ld4(&v[i]), wi = ld4(&w[i]), wj = ld4(&w[j]), vjj = ld4(&v[j]);
-        cdf acc = ld4(aij);
-        df_acc_mul(acc.re, df_neg(vi.re), wj.re);
-        df_acc_mul(acc.re, df_neg(vi.im), wj.im);
-        df_acc_mul(acc.re, df_neg(wi.re), vjj.re);
-        df_acc_mul(acc.re, df_neg(wi.im), vjj.im);
-        df_acc_mul(acc.im, df_neg(vi.im), wj.re);
-        df_acc_mul(acc.im, vi.re, wj.im);
-        df_acc_mul(acc.im, df_neg(wi.im), vjj.re);
-        df_acc_mul(acc.im, wi.re, vjj.im);
-        st4(aij, c_renorm(acc));
+    // --- 4. rank-2 update (warps 0..nw-2) / Householder scalars of step k+1 (warp nw-1)
+    if (warp < nw - 1) {
+      if (active) {
+        const int tot = nown * m;
+        const float rm = 1.f / (float)m;
+        for (int idx = tid; idx < tot; idx += TD_THREADS - 32) {
+          // idx / m: exact while nown m < 2^21 (the rounding error of the product stays below the
+          // distance 0.5 / m of (idx + 0.5) / m from an integer)
+          const int q = (int)__fmul_rn((float)idx + 0.5f, rm);
+          const int j = idx - q * m;
+          const int i = i0 + q * G;
+          if (i == 0) continue;
+          // global row k+1+i = c + G (lrow0 + q): no division per entry
+          float4* aij = (ROWS_IN_SMEM ? rows + (size_t)(lrow0 + q) * n : a.A + (size_t)(k + 1 + i) * n) + (k + 1) + j;
+          const cdf vi = ld4(&v[i]), wi = ld4(&w[i]), wj = ld4(&w[j]), vjj = ld4(&v[j]);
+          cdf acc = ld4(aij);
+          df_acc_mul(acc.re, df_neg(vi.re), wj.re);
+          df_acc_mul(acc.re, df_neg(vi.im), wj.im);
+          df_acc_mul(acc.re, df_neg(wi.re), vjj.re);
+          df_acc_mul(acc.re, df_neg(wi.im), vjj.im);
+          df_acc_mul(acc.im, df_neg(vi.im), wj.re);
+          df_acc_mul(acc.im, vi.re, wj.im);
+          df_acc_mul(acc.im, df_neg(wi.im), vjj.re);
+          df_acc_mul(acc.im, wi.re, vjj.im);
+          st4(aij, c_renorm(acc));
+        }
       }
-    }
-    // the next pivot row k+1 (relative row 0: v_0 = 1), formed by every CTA, and its squares
-    {
-      const cdf w0c = ld4(&w[0]);
-      for (int j = tid; j < m; j += TD_THREADS) {
-        cdf aij = ld4(&pub[j]);
-        if (active) aij = c_sub(aij, c_add(c_conj(ld4(&w[j])), c_mul(w0c, c_conj(ld4(&v[j])))));
-        st4(&x[j], aij);
-        xsq[j] = dpack(df_add(df_mul(aij.re, aij.re), df_mul(aij.im, aij.im)));
+    } else if (k + 1 < n - 1) {
+      cdf tau1, scale1;
+      dfl beta1;
+      td_scalars(m - 1, x, xsq, tau1, scale1, beta1);
+      if (lane == 0) {
+        st4(&hs[0], tau1);
+        st4(&hs[1], scale1);
+        hs[2] = make_float4(beta1.hi, beta1.lo, 0.f, 0.f);
       }
     }
     __syncthreads();
@@ -250,32 +323,6 @@ struct TdcArgs {
   float4* tau;
 };
 
-// Householder scalars of the pivot row x (length m + 1; squares of x in xsq): tau, the inverse
-// 1 / (x0 - beta) of v's leading entry before normalisation, beta; one warp.
-__device__ __forceinline__ void tdc_scalars(int m, const float4* x, const float2* xsq, cdf& tau, cdf& scale,
-                                            dfl& beta) {
-  const int lane = threadIdx.x & 31;
-  dfl t2 = df_f(0.f);
-  for (int j = 2 + lane; j <= m; j += 32) t2 = df_add(t2, dload(xsq[j]));
-  const dfl xn2 = df_warp_sum(t2);
-  const cdf x0 = c_conj(ld4(&x[1]));
-  tau = c_zero();
-  scale = c_zero();
-  beta = x0.re;
-  if (!(xn2.hi == 0.f && x0.im.hi == 0.f)) {
-    const dfl nrm = df_sqrt(df_add(df_add(df_mul(x0.re, x0.re), df_mul(x0.im, x0.im)), xn2));
-    beta = x0.re.hi >= 0.f ? df_neg(nrm) : nrm;
-    const dfl rb = df_rcp(beta);
-    tau.re = df_sub(df_f(1.f), df_mul(x0.re, rb));  // (beta - x0.re) / beta
-    tau.im = df_neg(df_mul(x0.im, rb));
-    const cdf den = {df_sub(x0.re, beta), x0.im};
-    const dfl dd = df_add(df_mul(den.re, den.re), df_mul(den.im, den.im));
-    const dfl rd = df_rcp(dd);
-    scale.re = df_mul(den.re, rd);
-    scale.im = df_neg(df_mul(den.im, rd));
-  }
-}
-
 __global__ void __launch_bounds__(TDC_THREADS, 1) tridiag_cluster_kernel(const TdcArgs a) {
   cg::cluster_group cl = cg::this_cluster();
   const int crank = (int)cl.block_rank(), nct = (int)cl.num_blocks();
@@ -308,7 +355,7 @@ __global__ void __launch_bounds__(TDC_THREADS, 1) tridiag_cluster_kernel(const T
   if (warp == nw - 1) {
     cdf tau, scale;
     dfl beta;
-    tdc_scalars(n - 1, x, xsq, tau, scale, beta);
+    td_scalars(n - 1, x, xsq, tau, scale, beta);
     if (lane == 0) {
       st4(&hs[0], tau);
       st4(&hs[1], scale);
@@ -411,7 +458,7 @@ __global__ void __launch_bounds__(TDC_THREADS, 1) tridiag_cluster_kernel(const T
     } else if (k + 1 < n - 1) {
       cdf tau1, scale1;
       dfl beta1;
-      tdc_scalars(m - 1, x, xsq, tau1, scale1, beta1);
+      td_scalars(m - 1, x, xsq, tau1, scale1, beta1);
       if (lane == 0) {
         st4(&hs[0], tau1);
         st4(&hs[1], scale1);

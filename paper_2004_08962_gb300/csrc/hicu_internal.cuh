@@ -310,11 +310,9 @@ hicu_status launch_adjoint_fp32(hicu_handle* h, const ConvGeom& g, const float2*
                                 double* partial, int* nblocks, cudaStream_t st);
 hicu_status launch_sum_partials(hicu_handle* h, const double* partial, int n, double* out,
                                 cudaStream_t st);
-hicu_status launch_finalize_step(hicu_handle* h, const double* part, int n_obj, int n_g, int n_d,
-                                 double* stats, cudaStream_t st);
-hicu_status launch_update(hicu_handle* h, const ConvGeom& g, KView y, KView gbuf, MView m,
-                          const double* stats, cudaStream_t st);
-
+// finalisation (stats = {eta, objective, ||g||^2, D} from the partials) and update in one launch
+hicu_status launch_update_step(hicu_handle* h, const ConvGeom& g, KView y, KView gb, MView m, const double* part,
+                               int n_obj, int n_g, int n_d, double* stats, cudaStream_t st);
 // tensor-core (split-bf16) path: 2D and 3D, valid or circular along the outer axis
 bool tc_supported(const ConvGeom& g);
 size_t tc_b_bytes(const ConvGeom& g, int p, int mode);
