@@ -588,8 +588,8 @@ __device__ __forceinline__ int sturm_count(int n, const float2* d, const float2*
 }
 
 // Eigenvalue t0 + blockIdx.x (ascending order), one CTA of TB_THREADS each: multisection with
-// TB_THREADS points a round (8 bits) to an absolute width of 2^-46 ||T||, six rounds from the
-// Gershgorin interval.  Dynamic shared memory: d and e2 (2 n float2).
+// TB_THREADS points a round (8 bits) to an absolute width of 2^-46 ||T||: two FP32 rounds from the
+// Gershgorin interval, then four double-float rounds.  Dynamic shared memory: d and e2 (2 n float2).
 constexpr int TB_THREADS = 256;
 
 __global__ void __launch_bounds__(TB_THREADS) td_bisect_kernel(int n, int t0, const float2* __restrict__ d,
@@ -611,11 +611,39 @@ __global__ void __launch_bounds__(TB_THREADS) td_bisect_kernel(int n, int t0, co
     if (i < n - 1) se2[i] = e2[i];
   }
   __syncthreads();
-  dfl lo = dload(info[0]), hi = dload(info[1]);
   const float tol = 0x1.0p-46f * info[2].x + info[3].x;
   const float pivmin = info[3].x;
+  // Two rounds in FP32 first.  An FP32 Sturm count (reciprocal to ~2^-22) is exact for a matrix
+  // whose d and e^2 differ from T's by a few ulps relatively, so its bracket holds the eigenvalue
+  // of T within ~12 * 2^-24 ||T|| (Weyl); widened by 2^-16 ||T|| on each side it is handed to the
+  // double-float rounds, which then need 4 rounds instead of 6.
+  float lo32 = info[0].x, hi32 = info[1].x;
+  for (int it = 0; it < 2; ++it) {
+    const float step32 = (hi32 - lo32) * (1.f / (float)(TB_THREADS + 1));
+    const float x32 = lo32 + step32 * (float)(tid + 1);
+    float q = sd[0].x - x32;
+    if (fabsf(q) <= pivmin) q = -pivmin;
+    int cnt = q < 0.f;
+    for (int i = 1; i < n; ++i) {
+      q = (sd[i].x - x32) - se2[i - 1].x * rcp_approx(q);
+      if (fabsf(q) <= pivmin) q = -pivmin;
+      cnt += q < 0.f;
+    }
+    const unsigned above = __ballot_sync(0xffffffffu, cnt > t);
+    if (lane == 0) wfirst[it & 1][warp] = above ? warp * 32 + __ffs(above) - 1 : TB_THREADS;
+    __syncthreads();
+    int first = TB_THREADS;
+#pragma unroll
+    for (int w = 0; w < TB_THREADS / 32; ++w) first = min(first, wfirst[it & 1][w]);
+    const float nlo = first == 0 ? lo32 : lo32 + step32 * (float)first;
+    const float nhi = first == TB_THREADS ? hi32 : lo32 + step32 * (float)(first + 1);
+    lo32 = nlo;
+    hi32 = nhi;
+  }
+  const float pad = 0x1.0p-16f * info[2].x + pivmin;
+  dfl lo = df_sub(df_f(lo32), df_f(pad)), hi = df_add(df_f(hi32), df_f(pad));
   const dfl inv = df_div(df_f(1.f), df_f((float)(TB_THREADS + 1)));
-  for (int it = 0; it < 24 && df_sub(hi, lo).hi > tol; ++it) {
+  for (int it = 2; it < 24 && df_sub(hi, lo).hi > tol; ++it) {
     const dfl step = df_mul(df_sub(hi, lo), inv);
     const int cnt = sturm_count(n, sd, se2, df_add(lo, df_mul_f(step, (float)(tid + 1))), pivmin);
     // the first point whose count exceeds t bounds the eigenvalue from above
@@ -649,8 +677,11 @@ __device__ __forceinline__ float hash_unit(uint64_t t, uint64_t i) {
 // One warp per run of eigenvalues closer than 1e-10 ||T|| (the block of the run's first index
 // does the work; the others leave): lane 0 runs the serial pivoted LU and the triangular
 // solves in shared memory, the warp normalises and orthogonalises each new vector against the
-// run's earlier ones (modified Gram-Schmidt).  Shared memory: 6 n float2, plus 2 n for copies
-// of d and e when they fit (stage != 0).
+// run's earlier ones (modified Gram-Schmidt).  The factors are stored for short serial chains:
+// forward step (l_i, swap_i) in one float4; backward step x_i = z_i / u1_i - (u2_i / u1_i)
+// x_{i+1} - (u3_i / u1_i) x_{i+2} with the three quotients in one float4 and a float2; the next
+// step's factors are loaded one step ahead.  Shared memory: 6 n float2 (+ 2 n for copies of d and
+// e when they fit, stage != 0).
 __global__ void __launch_bounds__(32) td_inviter_kernel(int n, int r, const float2* __restrict__ d,
                                                         const float2* __restrict__ e,
                                                         const float2* __restrict__ lam,
@@ -658,13 +689,11 @@ __global__ void __launch_bounds__(32) td_inviter_kernel(int n, int r, const floa
                                                         int stage) {
   pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
   pdl_trigger();
-  extern __shared__ float2 ism[];
-  float2* u1i = ism;  // 1 / pivot
-  float2* u2 = u1i + n;
-  float2* u3 = u2 + n;
-  float2* lm = u3 + n;
-  float2* sw = lm + n;  // .x = 1: rows i, i+1 swapped at step i
-  float2* z = sw + n;
+  extern __shared__ __align__(16) float2 ism[];
+  float4* fw = reinterpret_cast<float4*>(ism);  // [n] forward: (l.hi, l.lo, swap, 0)
+  float4* bk = fw + n;                          // [n] backward: (u2/u1 .hi .lo, u3/u1 .hi .lo)
+  float2* bi = reinterpret_cast<float2*>(bk + n);  // [n] 1 / u1
+  float2* z = bi + n;                           // [n]
   float2* sd = stage ? z + n : nullptr;
   float2* se = stage ? sd + n : nullptr;
   const int j0 = blockIdx.x, lane = threadIdx.x;
@@ -695,55 +724,67 @@ __global__ void __launch_bounds__(32) td_inviter_kernel(int n, int r, const floa
           const dfl piv = fabsf(ca.hi) > tiny ? ca : df_f(ca.hi >= 0.f ? tiny : -tiny);
           const dfl pinv = df_rcp(piv);
           const dfl l = df_mul(b, pinv);
-          lm[i] = dpack(l);
-          sw[i] = make_float2(0.f, 0.f);
-          u1i[i] = dpack(pinv);
-          u2[i] = dpack(cc);
-          u3[i] = make_float2(0.f, 0.f);
+          const dfl q2 = df_mul(cc, pinv);
+          fw[i] = make_float4(l.hi, l.lo, 0.f, 0.f);
+          bk[i] = make_float4(q2.hi, q2.lo, 0.f, 0.f);
+          bi[i] = dpack(pinv);
           ca = df_sub(na, df_mul(l, cc));
           cc = nc;
         } else {
           const dfl binv = df_rcp(b);
           const dfl l = df_mul(ca, binv);
-          lm[i] = dpack(l);
-          sw[i] = make_float2(1.f, 0.f);
-          u1i[i] = dpack(binv);
-          u2[i] = dpack(na);
-          u3[i] = dpack(nc);
+          const dfl q2 = df_mul(na, binv), q3 = df_mul(nc, binv);
+          fw[i] = make_float4(l.hi, l.lo, 1.f, 0.f);
+          bk[i] = make_float4(q2.hi, q2.lo, q3.hi, q3.lo);
+          bi[i] = dpack(binv);
           ca = df_sub(cc, df_mul(l, na));
           cc = df_neg(df_mul(l, nc));
         }
       }
       const dfl last = fabsf(ca.hi) > tiny ? ca : df_f(ca.hi >= 0.f ? tiny : -tiny);
-      u1i[n - 1] = dpack(df_rcp(last));
+      bk[n - 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      bi[n - 1] = dpack(df_rcp(last));
     }
     for (int i = lane; i < n; i += 32) z[i] = make_float2(hash_unit((uint64_t)(j + 1), (uint64_t)i), 0.f);
     __syncwarp();
     for (int iter = 0; iter < 3; ++iter) {
       if (lane == 0) {
-        // forward: row swaps and L
+        // forward: row swaps and L (factors and the next entry loaded a step ahead)
         dfl zi = dload(z[0]);
+        float4 f = fw[0];
+        float2 znx = n > 1 ? z[1] : make_float2(0.f, 0.f);
         for (int i = 0; i < n - 1; ++i) {
-          dfl zn = dload(z[i + 1]);
-          if (sw[i].x != 0.f) {
+          const float4 fn = fw[i + 1 < n - 1 ? i + 1 : i];
+          const float2 zn2 = z[i + 2 < n ? i + 2 : i + 1];
+          dfl zn = dload(znx);
+          if (f.z != 0.f) {
             const dfl t = zi;
             zi = zn;
             zn = t;
           }
           z[i] = dpack(zi);
-          zi = df_sub(zn, df_mul(dload(lm[i]), zi));
+          zi = df_sub(zn, df_mul({f.x, f.y}, zi));
+          f = fn;
+          znx = zn2;
         }
         z[n - 1] = dpack(zi);
-        // back substitution with U (diagonals 1/u1, u2, u3)
+        // back substitution: x_i = z_i / u1_i - q2_i x_{i+1} - q3_i x_{i+2}
         dfl x1 = df_f(0.f), x2 = df_f(0.f);  // x[i+1], x[i+2]
+        float4 bq = bk[n - 1];
+        float2 bz = z[n - 1], bu = bi[n - 1];
         for (int i = n - 1; i >= 0; --i) {
-          dfl sacc = dload(z[i]);
-          if (i + 1 < n) sacc = df_sub(sacc, df_mul(dload(u2[i]), x1));
-          if (i + 2 < n) sacc = df_sub(sacc, df_mul(dload(u3[i]), x2));
-          const dfl xi = df_mul(sacc, dload(u1i[i]));
+          const int ip = i > 0 ? i - 1 : 0;
+          const float4 bqn = bk[ip];
+          const float2 bzn = z[ip], bun = bi[ip];
+          // off the chain: z_i / u1_i - q3_i x_{i+2}
+          const dfl t = df_sub(df_mul(dload(bz), dload(bu)), df_mul({bq.z, bq.w}, x2));
+          const dfl xi = df_sub(t, df_mul({bq.x, bq.y}, x1));
           z[i] = dpack(xi);
           x2 = x1;
           x1 = xi;
+          bq = bqn;
+          bz = bzn;
+          bu = bun;
         }
       }
       __syncwarp();
