@@ -829,8 +829,8 @@ constexpr int WY_B = 32;
 __global__ void __launch_bounds__(256) td_wy_t_kernel(int n, const float4* __restrict__ refl,
                                                       const float4* __restrict__ tau, float4* __restrict__ Tb,
                                                       float4* __restrict__ Yt) {
-  __shared__ float4 S[WY_B][WY_B];  // S[i][j] = v_i^H v_j (i < j)
-  __shared__ float4 T[WY_B][WY_B];
+  __shared__ float4 S[WY_B][WY_B + 1];  // S[i][j] = v_i^H v_j (i < j); rows padded against bank conflicts
+  __shared__ float4 T[WY_B][WY_B + 1];
   const int blk = blockIdx.x, k0 = blk * WY_B, nb = min(WY_B, n - 1 - k0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // row-major copy: Yt[blk][g][j] = v_{k0+j}[g], zero where g <= k0 + j
@@ -848,15 +848,18 @@ __global__ void __launch_bounds__(256) td_wy_t_kernel(int n, const float4* __res
   for (int pair = threadIdx.x; pair < WY_B * WY_B; pair += blockDim.x) {
     const int i = pair / WY_B, j = pair - i * WY_B;
     if (!(i < j && j < nb)) continue;
-    cdf a0 = c_zero(), a1 = c_zero();
+    // four lazily normalised chains (latency), combined at the end
+    cdf a0 = c_zero(), a1 = c_zero(), a2 = c_zero(), a3 = c_zero();
     int g = k0 + j + 1;
-    for (; g + 1 < n; g += 2) {
+    for (; g + 3 < n; g += 4) {
       const float4* y0 = Y + (size_t)g * WY_B;
-      a0 = c_add(a0, c_mulc(ld4(&y0[i]), ld4(&y0[j])));
-      a1 = c_add(a1, c_mulc(ld4(&y0[WY_B + i]), ld4(&y0[WY_B + j])));
+      c_acc_mulc(a0, ld4(&y0[i]), ld4(&y0[j]));
+      c_acc_mulc(a1, ld4(&y0[WY_B + i]), ld4(&y0[WY_B + j]));
+      c_acc_mulc(a2, ld4(&y0[2 * WY_B + i]), ld4(&y0[2 * WY_B + j]));
+      c_acc_mulc(a3, ld4(&y0[3 * WY_B + i]), ld4(&y0[3 * WY_B + j]));
     }
-    if (g < n) a0 = c_add(a0, c_mulc(ld4(&Y[(size_t)g * WY_B + i]), ld4(&Y[(size_t)g * WY_B + j])));
-    st4(&S[i][j], c_add(a0, a1));
+    for (; g < n; ++g) c_acc_mulc(a0, ld4(&Y[(size_t)g * WY_B + i]), ld4(&Y[(size_t)g * WY_B + j]));
+    st4(&S[i][j], c_add(c_add(a0, a1), c_add(a2, a3)));
   }
   for (int idx = threadIdx.x; idx < WY_B * WY_B; idx += blockDim.x) T[idx / WY_B][idx % WY_B] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
@@ -866,8 +869,16 @@ __global__ void __launch_bounds__(256) td_wy_t_kernel(int n, const float4* __res
       const cdf ti = ld4(&tau[k0 + i]);
       // lane a < i: T[a][i] = -tau_i sum_{c=a}^{i-1} T[a][c] S[c][i]
       if (lane < i) {
-        cdf acc = c_zero();
-        for (int c = lane; c < i; ++c) acc = c_add(acc, c_mul(ld4(&T[lane][c]), ld4(&S[c][i])));
+        cdf a0 = c_zero(), a1 = c_zero(), a2 = c_zero(), a3 = c_zero();
+        int c = lane;
+        for (; c + 3 < i; c += 4) {
+          c_acc_mul(a0, ld4(&T[lane][c]), ld4(&S[c][i]));
+          c_acc_mul(a1, ld4(&T[lane][c + 1]), ld4(&S[c + 1][i]));
+          c_acc_mul(a2, ld4(&T[lane][c + 2]), ld4(&S[c + 2][i]));
+          c_acc_mul(a3, ld4(&T[lane][c + 3]), ld4(&S[c + 3][i]));
+        }
+        for (; c < i; ++c) c_acc_mul(a0, ld4(&T[lane][c]), ld4(&S[c][i]));
+        const cdf acc = c_add(c_add(a0, a1), c_add(a2, a3));
         const cdf nt = {df_neg(ti.re), df_neg(ti.im)};
         st4(&T[lane][i], c_mul(nt, acc));
       }
