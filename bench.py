@@ -49,7 +49,7 @@ KERNEL_NAMES = {0: "gram", 1: "eig", 2: "conv_fp32", 3: "adjoint_fp32", 4: "jl",
 FP64_PEAK_TFLOPS = 1.25  # FP64 FMA-chain probe on this GB300, equal to the nominal rate
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of the same
 # kernel on the same workload (profiles/); a kernel changed since its capture has no entry.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {("2d_brain_256", "tridiag_cluster_kernel"): 704000}
 
 
 def load_peaks():
