@@ -559,8 +559,9 @@ static hicu_status gd_step_filters_tc(hicu_handle* h, const hicu_geom* geom, con
   if ((s = tc_prepare_weights(h, g, (const float2*)filters, p, bwc, bwa, st))) return s;
   if ((s = tc_prepare_input(h, g, yv, xpl, st))) return s;
   if ((s = launch_conv_tc(h, g, xpl, bwc, p, nullptr, rpl, part, &n1, st))) return s;
-  if ((s = launch_adjoint_tc(h, g, rpl, bwa, p, mv, gview, part + n1, &n2, st))) return s;
-  if ((s = tc_prepare_input(h, g, gview, gpl, st))) return s;
+  // the adjoint writes g both as complex64 (for the update) and as the split planes of the
+  // line-search convolution's input
+  if ((s = launch_adjoint_tc(h, g, rpl, bwa, p, mv, gview, part + n1, &n2, st, gpl))) return s;
   if ((s = launch_conv_tc(h, g, gpl, bwc, p, nullptr, nullptr, part + n1 + n2, &n3, st))) return s;
   if ((s = launch_update_step(h, g, yv, gview, mv, part, n1, n2, n3, st4, st)))
     return cuda_error(h, cudaGetLastError(), "update");

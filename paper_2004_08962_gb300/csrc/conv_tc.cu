@@ -76,6 +76,9 @@ struct TcParams {
   long long g_sc, g_sz, g_sy, g_base;
   const uint8_t* m;         // adjoint mask (nullable), same addressing with its strides
   long long m_sc, m_sz, m_sy, m_base;
+  uint4* gs;                // adjoint (nullable): g also as split input planes [split][gs_ce][o][8],
+  long long gs_plane;       //   the layout of tc_split_input_kernel over the region
+  int gs_ce;
   double* partial;
   int* err;
 };
@@ -367,14 +370,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           } else {
             const long long go = P.g_base + (long long)z * P.g_sz + (long long)oy * P.g_sy + ox;
             const long long mo = P.m_base + (long long)z * P.m_sz + (long long)oy * P.m_sy + ox;
+            float vm[16];
 #pragma unroll
             for (int q2 = 0; q2 < 8; ++q2) {
               const int c = U.og * 8 + q2;
+              float2 w = make_float2(0.f, 0.f);
               if (c < P.cout) {
-                float2 w = make_float2(v[2 * q2], v[2 * q2 + 1]);
+                w = make_float2(v[2 * q2], v[2 * q2 + 1]);
                 if (P.m && P.m[(long long)c * P.m_sc + mo]) w = make_float2(0.f, 0.f);
                 P.g[(long long)c * P.g_sc + go] = w;
                 nrm = fmaf(w.x, w.x, fmaf(w.y, w.y, nrm));
+              }
+              vm[2 * q2] = w.x;
+              vm[2 * q2 + 1] = w.y;
+            }
+            if (P.gs) {
+              // the masked g of this position as the next convolution's split input (4 channels
+              // per 16-byte word, hi and lo planes), in place of a separate split launch
+              const long long o = ((long long)z * P.oy_lim + oy) * P.ox_lim + ox;
+#pragma unroll
+              for (int hc = 0; hc < 2; ++hc) {
+                const int chunk = 2 * U.og + hc;
+                if (chunk < P.gs_ce) {
+                  float w8[8];
+#pragma unroll
+                  for (int e = 0; e < 8; ++e) w8[e] = vm[8 * hc + e];
+                  uint4 h4, l4;
+                  split8(w8, h4, l4);
+                  P.gs[(size_t)chunk * P.gs_plane + o] = h4;
+                  P.gs[(size_t)(P.gs_ce + chunk) * P.gs_plane + o] = l4;
+                }
               }
             }
           }
@@ -839,7 +864,8 @@ hicu_status launch_conv_tc(hicu_handle* h, const ConvGeom& g, const uint4* xplan
 
 // adjoint: split planes of R -> masked g (region view), partial norms per CTA
 hicu_status launch_adjoint_tc(hicu_handle* h, const ConvGeom& g, const uint4* Rs, const void* bw, int p,
-                              MView m, KView gout, double* partial, int* nblocks, cudaStream_t st) {
+                              MView m, KView gout, double* partial, int* nblocks, cudaStream_t st,
+                              uint4* gsplit) {
   TcPlan pl;
   if (!plan_tc_cached(&pl, g, 1, p, device_sms(h)))
     return set_error(h, HICU_ERR_UNSUPPORTED,
@@ -862,6 +888,9 @@ hicu_status launch_adjoint_tc(hicu_handle* h, const ConvGeom& g, const uint4* Rs
   P.m_sz = as2d ? m.sy : m.sz;
   P.m_sy = as2d ? 0 : m.sy;
   P.m_base = (long long)m.oz * m.sz + (long long)m.oy * m.sy + m.ox;
+  P.gs = gsplit;
+  P.gs_plane = (long long)g.ex * g.ey * g.ez;
+  P.gs_ce = chunks_even_of(g.C);
   P.partial = partial;
   P.err = h->dev_err;
   return launch_plan(h, pl, Rs, K_ADJOINT_TC, st);

@@ -326,8 +326,10 @@ hicu_status tc_prepare_r(hicu_handle* h, const ConvGeom& g, const float2* R, int
                          cudaStream_t st);
 hicu_status launch_conv_tc(hicu_handle* h, const ConvGeom& g, const uint4* xplanar, const void* bw, int p,
                            float2* R, uint4* Rs, double* partial, int* nblocks, cudaStream_t st);
+// gsplit (nullable): also write the masked g as split input planes for the next convolution
 hicu_status launch_adjoint_tc(hicu_handle* h, const ConvGeom& g, const uint4* Rs, const void* bw, int p,
-                              MView m, KView gout, double* partial, int* nblocks, cudaStream_t st);
+                              MView m, KView gout, double* partial, int* nblocks, cudaStream_t st,
+                              uint4* gsplit = nullptr);
 
 hicu_status launch_jl(hicu_handle* h, int64_t n, int64_t nr, int p, const double* Q, int mode,
                       const double* P, uint64_t seed, uint64_t counter, float* bank,
