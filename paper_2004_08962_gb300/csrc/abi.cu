@@ -524,7 +524,7 @@ namespace hicu {
 // conv of g reduced to D, then the same line search and update as the FP32 form.
 static hicu_status gd_step_filters_tc(hicu_handle* h, const hicu_geom* geom, const hicu_region* region,
                                       const ConvGeom& g, float* y, const uint8_t* mask, const float* filters,
-                                      int p, double* stats, cudaStream_t st) {
+                                      int p, double* stats, cudaStream_t st, bool planes_valid, bool keep_planes) {
   hicu_status s = check_tc(h, g);
   if (s) return s;
   const size_t xbytes = tc_x_bytes(g);
@@ -557,12 +557,14 @@ static hicu_status gd_step_filters_tc(hicu_handle* h, const hicu_geom* geom, con
   double* part = (double*)ws_get(h, WS_PART, sizeof(double) * (n1 + n2 + n3), &s);
   if (s) return s;
   if ((s = tc_prepare_weights(h, g, (const float2*)filters, p, bwc, bwa, st))) return s;
-  if ((s = tc_prepare_input(h, g, yv, xpl, st))) return s;
+  // the split planes of y: left by the previous step's update when the caller says so
+  if (!planes_valid && (s = tc_prepare_input(h, g, yv, xpl, st))) return s;
   if ((s = launch_conv_tc(h, g, xpl, bwc, p, nullptr, rpl, part, &n1, st))) return s;
   // the adjoint writes g both as complex64 (for the update) and as the split planes of the
   // line-search convolution's input
   if ((s = launch_adjoint_tc(h, g, rpl, bwa, p, mv, gview, part + n1, &n2, st, gpl))) return s;
   if ((s = launch_conv_tc(h, g, gpl, bwc, p, nullptr, nullptr, part + n1 + n2, &n3, st))) return s;
+  if (keep_planes) return launch_update_step_planes(h, g, yv, gview, mv, part, n1, n2, n3, st4, xpl, st);
   if ((s = launch_update_step(h, g, yv, gview, mv, part, n1, n2, n3, st4, st)))
     return cuda_error(h, cudaGetLastError(), "update");
   return HICU_OK;
@@ -571,13 +573,15 @@ static hicu_status gd_step_filters_tc(hicu_handle* h, const hicu_geom* geom, con
 // One descent step for a fixed bank (Algorithm 1 steps 7-8).
 hicu_status gd_step_filters(hicu_handle* h, const hicu_geom* geom, const hicu_region* region, float* y,
                             const uint8_t* mask, const float* filters, int32_t p, double* stats,
-                            int32_t prec, cudaStream_t st) {
+                            int32_t prec, cudaStream_t st, bool planes_valid,
+                            bool keep_planes) {
   hicu_status s = check_prec(h, prec);
   if (s) return s;
   ConvGeom g;
   s = make_conv_geom(h, geom, region, &g);
   if (s) return s;
-  if (prec == HICU_SPLIT_BF16) return gd_step_filters_tc(h, geom, region, g, y, mask, filters, p, stats, st);
+  if (prec == HICU_SPLIT_BF16)
+    return gd_step_filters_tc(h, geom, region, g, y, mask, filters, p, stats, st, planes_valid, keep_planes);
   StepBuffers b;
   s = prep_filters(h, g, filters, p, true, true, &b, st);
   if (s) return s;
@@ -791,6 +795,9 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
   hicu_region prev = prm->stages[0].region;
   for (int si = 0; si < prm->nstages; ++si) {
     const hicu_stage& stg = prm->stages[si];
+    // split planes of y on this stage's region: made by the stage's first step, then kept current
+    // by each step's update (the Gram and eigen-solve leave y alone)
+    bool planes_valid = false;
     for (int i = 0; i < stg.iters; ++i) {
       // the JL matrices of this outer iteration's descent steps depend on nothing but the seed and
       // the step counter: drawn on the side stream beside the Gram and the eigen-solve (after the
@@ -829,7 +836,10 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
         s = launch_jl_converted(h, n, nq, stg.p, Qf, jmode, nullptr, Pall + (size_t)j * prow * stg.p, prm->seed,
                                 counter, bank, st, j > 0);
         if (s) return s;
-        s = gd_step_filters(h, geom, &stg.region, y, m, bank, stg.p, dstats + 4 * counter, prm->prec, st);
+        // the update leaves the split planes of y for the next step of the same region
+        s = gd_step_filters(h, geom, &stg.region, y, m, bank, stg.p, dstats + 4 * counter, prm->prec, st,
+                            planes_valid, true);
+        planes_valid = true;
         if (s) return s;
         ++counter;
       }

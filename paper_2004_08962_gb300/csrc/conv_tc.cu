@@ -533,6 +533,73 @@ __global__ void tc_prep_b_kernel(PrepB q0, PrepB q1, int n, int kx, int ky, int 
   }
 }
 
+// The descent step's finalisation and update (as update_step_kernel) for the tensor-core path,
+// a thread per (4-channel chunk, region position): y <- y - eta g on the unobserved entries (the
+// observed ones are never written), and the updated y of the region written as the split input
+// planes of the next step's convolution (the layout of tc_split_input_kernel), so that the next
+// step needs no split launch of its own.
+__global__ void update_step_planes_kernel(ConvGeom g, KView y, KView gb, MView m, const double* __restrict__ part,
+                                          int n_obj, int n_g, int n_d, double* stats, uint4* __restrict__ planes,
+                                          int chunks_even) {
+  pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
+  pdl_trigger();
+  __shared__ double sh[8];
+  __shared__ double s_eta;
+  const double obj = block_fixed_sum(part, n_obj, sh);
+  const double gn2 = block_fixed_sum(part + n_obj, n_g, sh);
+  const double D = block_fixed_sum(part + n_obj + n_g, n_d, sh);
+  if (threadIdx.x == 0) {
+    double eta = 0.0;
+    if (D > 0.0 && gn2 > 0.0 && isfinite(D) && isfinite(gn2)) eta = gn2 / D;
+    if (blockIdx.x == 0) {
+      stats[0] = eta;
+      stats[1] = obj;
+      stats[2] = gn2;
+      stats[3] = D;
+    }
+    s_eta = eta;
+  }
+  __syncthreads();
+  const double eta = s_eta;
+  const float e = (float)eta;
+  const long long plane = (long long)g.ex * g.ey * g.ez;
+  const long long tot = plane * chunks_even;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(i / plane);
+    const long long pos = i - (long long)j * plane;
+    const int ux = (int)(pos % g.ex);
+    const long long r = pos / g.ex;
+    const int uy = (int)(r % g.ey), uz = (int)(r / g.ey);
+    float v[8];
+#pragma unroll
+    for (int e4 = 0; e4 < 4; ++e4) {
+      const int c = 4 * j + e4;
+      float2 a = make_float2(0.f, 0.f);
+      if (c < g.C) {
+        float2* yp = y.p + (long long)c * y.sc + (long long)(y.oz + uz) * y.sz + (long long)(y.oy + uy) * y.sy +
+                     (y.ox + ux);
+        a = *yp;
+        const bool observed = m.p && m.p[(long long)c * m.sc + (long long)(m.oz + uz) * m.sz +
+                                         (long long)(m.oy + uy) * m.sy + (m.ox + ux)];
+        if (!observed && eta != 0.0) {
+          const float2 gv = gb.p[(long long)c * gb.sc + (long long)(gb.oz + uz) * gb.sz +
+                                 (long long)(gb.oy + uy) * gb.sy + (gb.ox + ux)];
+          a.x = fmaf(-e, gv.x, a.x);
+          a.y = fmaf(-e, gv.y, a.y);
+          *yp = a;
+        }
+      }
+      v[2 * e4] = a.x;
+      v[2 * e4 + 1] = a.y;
+    }
+    uint4 hi, lo;
+    split8(v, hi, lo);
+    planes[(long long)j * plane + pos] = hi;
+    planes[(long long)(chunks_even + j) * plane + pos] = lo;
+  }
+}
+
 // ---------------------------------------------------------------- host side
 
 namespace {
@@ -797,6 +864,19 @@ hicu_status tc_prepare_input(hicu_handle* h, const ConvGeom& g, KView x, uint4* 
   const cudaError_t e = launch_pdl(h, K_MISC, st, dim3(blocks), dim3(256), 0, tc_split_input_kernel, true, g.C, ce,
                                    g.ex, g.ey, g.ez, x, planar);
   return cuda_error(h, e != cudaSuccess ? e : cudaGetLastError(), "tc_split_input");
+}
+
+hicu_status launch_update_step_planes(hicu_handle* h, const ConvGeom& g, KView y, KView gb, MView m,
+                                     const double* part, int n_obj, int n_g, int n_d, double* stats, uint4* planar,
+                                     cudaStream_t st) {
+  const int ce = chunks_even_of(g.C);
+  const long long tot = (long long)g.ex * g.ey * g.ez * ce;
+  int blocks = (int)((tot + 255) / 256);
+  const int cap = 4 * (h->num_sms > 0 ? h->num_sms : 152);
+  if (blocks > cap) blocks = cap;
+  const cudaError_t e = launch_pdl(h, K_MISC, st, dim3(blocks), dim3(256), 0, update_step_planes_kernel, true, g,
+                                   y, gb, m, part, n_obj, n_g, n_d, stats, planar, ce);
+  return cuda_error(h, e != cudaSuccess ? e : cudaGetLastError(), "update");
 }
 
 hicu_status tc_prepare_r(hicu_handle* h, const ConvGeom& g, const float2* R, int p, uint4* planar,

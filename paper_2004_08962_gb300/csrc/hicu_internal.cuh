@@ -63,6 +63,13 @@ __device__ inline double block_sum(double v, double* sh) {
   return t;  // valid in thread 0
 }
 
+// Sum of v[0..n) by a CTA of 256 threads in a fixed order (the same in every CTA); thread 0 holds it.
+__device__ inline double block_fixed_sum(const double* v, int n, double* sh) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) s += v[i];
+  return block_sum<256>(s, sh);
+}
+
 // ----------------------------------------------------- bounded grid barrier
 // Used only inside cooperative launches (all CTAs co-resident).  Each wait
 // gives up after `timeout_ns` and records HICU_ERR_TIMEOUT in *err.
@@ -322,6 +329,11 @@ size_t tc_r_bytes(const ConvGeom& g, int p);   // split planes of R
 hicu_status tc_prepare_weights(hicu_handle* h, const ConvGeom& g, const float2* bank, int p, void* out_conv,
                                void* out_adjoint, cudaStream_t st);
 hicu_status tc_prepare_input(hicu_handle* h, const ConvGeom& g, KView x, uint4* planar, cudaStream_t st);
+// finalisation and update of a descent step that also writes the updated region of y as split
+// input planes (the layout of tc_prepare_input)
+hicu_status launch_update_step_planes(hicu_handle* h, const ConvGeom& g, KView y, KView gb, MView m,
+                                     const double* part, int n_obj, int n_g, int n_d, double* stats, uint4* planar,
+                                     cudaStream_t st);
 hicu_status tc_prepare_r(hicu_handle* h, const ConvGeom& g, const float2* R, int p, uint4* planar,
                          cudaStream_t st);
 hicu_status launch_conv_tc(hicu_handle* h, const ConvGeom& g, const uint4* xplanar, const void* bw, int p,
@@ -349,9 +361,12 @@ hicu_status jl_draw(hicu_handle* h, int64_t rows, int p, int nsteps, uint64_t se
                     cudaStream_t st);
 // the handle's side stream and its events, created on first use
 hicu_status ensure_side_stream(hicu_handle* h);
+// planes_valid: the split planes of y on this region are current (TC path); keep_planes: the update
+// leaves them current for the next step
 hicu_status gd_step_filters(hicu_handle* h, const hicu_geom* geom, const hicu_region* region, float* y,
                             const uint8_t* mask, const float* filters, int32_t p, double* stats,
-                            int32_t prec, cudaStream_t st);
+                            int32_t prec, cudaStream_t st,
+                            bool planes_valid = false, bool keep_planes = false);
 
 hicu_status run_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* reg, const float* x,
                      double* G, cudaStream_t st);
