@@ -6,18 +6,21 @@
 // Method (Golub & Van Loan, 4th ed., sections 8.3.1, 8.4.1 and 8.4.2):
 //  1. G = Q_H T Q_H^H with T real symmetric tridiagonal: n - 1 Householder steps
 //     H_k = I - tau_k v_k v_k^H, each making the part of column k below the
-//     subdiagonal vanish with a real subdiagonal entry.  One cooperative kernel over
-//     all SMs: every CTA forms v_k itself from the pivot row k (G is Hermitian and kept
-//     in full), w = tau A v on its own rows, one grid barrier, then the symmetric
-//     rank-2 update A <- A - v w^H - w v^H (w corrected by -tau/2 (w^H v) v) of its own
-//     rows and, in every CTA, of the next pivot row.
-//  2. Eigenvalues of T by bisection on Sturm counts (the LDL^T pivot recurrence,
-//     Kahan's form, which is backward stable): one warp per eigenvalue, 32 points a round.
+//     subdiagonal vanish with a real subdiagonal entry.  Every CTA forms v_k itself from its
+//     copy of the pivot row k (G is Hermitian and kept in full), w = tau A v on its own rows,
+//     one barrier, then the symmetric rank-2 update A <- A - v w^H - w v^H (w corrected by
+//     -tau/2 (w^H v) v) of its own rows and, in every CTA, of the next pivot row.  n <= 416:
+//     one 16-CTA cluster with the rows in shared memory (hardware cluster barrier); larger n:
+//     a cooperative grid over all SMs (grid barrier on an arrival counter).
+//  2. Eigenvalues of T by multisection on Sturm counts (the LDL^T pivot recurrence,
+//     Kahan's form, which is backward stable): a CTA of 256 threads per eigenvalue, 256
+//     points a round, two FP32 rounds then four double-float rounds.
 //  3. Eigenvectors of T for the r largest eigenvalues by inverse iteration with a
 //     pivoted tridiagonal LU; eigenvalues closer than 1e-10 ||T|| are solved one after
 //     the other and orthogonalised against each other (modified Gram-Schmidt).
 //  4. V = Q_H Z: the reflectors applied to each eigenvector in compact WY blocks of 32
-//     (I - Y T Y^H per block, Schreiber & Van Loan), last block first.
+//     (I - Y T Y^H per block, Schreiber & Van Loan), last block first; the WY factors are
+//     built on a side stream during steps 2-3.
 // Arithmetic: double-float (df.cuh, ~2^-48), because FP64 on this GPU is both slow and of
 // long latency, and every stage here is a chain of dependent operations.  The input is
 // pre-scaled by an exact power of two (largest entry O(1)); inputs and outputs are FP64.
