@@ -238,13 +238,16 @@ hicu_status hicu_nullspace(hicu_handle* h, int64_t n, int64_t r, const double* G
  * vectors of H are the eigenvectors of G = H^H H for its r largest
  * eigenvalues; the null space of step 3 is their orthogonal complement, which
  * HICU_JL_COMPLEMENT uses without forming it).
- * Householder tridiagonalisation G = Q_H T Q_H^H (one cooperative FP64 kernel,
- * two bounded grid barriers per reflector), bisection on Sturm counts for the
- * eigenvalues of T, inverse iteration for its r top eigenvectors (eigenvalues
- * closer than 1e-10 ||G|| are orthogonalised against each other) and the
- * reflectors applied to them.  FP64 throughout; the input is pre-scaled by a
- * power of two.  Eigenvalues are accurate to ~1e-16 ||G|| (absolute) and
- * span(V) to ~1e-16 ||G|| / (lambda_r - lambda_{r+1}).
+ * Householder tridiagonalisation G = Q_H T Q_H^H (one barrier per reflector: a
+ * 16-CTA cluster with the matrix in shared memory for n <= 416, else a
+ * cooperative kernel over all SMs with a bounded grid barrier), multisection on
+ * Sturm counts for the eigenvalues of T, inverse iteration for its r top
+ * eigenvectors (eigenvalues closer than 1e-10 ||G|| are orthogonalised against
+ * each other) and the reflectors applied to them in compact-WY blocks.
+ * Double-float arithmetic (an unevaluated sum of two FP32 numbers, unit roundoff
+ * 2^-48) on the FP32 pipes; the input is pre-scaled by a power of two; inputs and
+ * outputs FP64.  Eigenvalues are accurate to ~1e-14 ||G|| (absolute) and span(V)
+ * to ~1e-14 ||G|| / (lambda_r - lambda_{r+1}).
  *   n       : 2 .. 4096;  r : 1 .. n-1  (else HICU_ERR_SHAPE / HICU_ERR_RANK)
  *   G       : complex128 n x n row-major, Hermitian (only read)
  *   V       : complex128 [r][n]: row j is the eigenvector of eig_top[j]
