@@ -196,7 +196,7 @@ def _slab(reg, geom, kernel, circular, max_out):
     return sub, O.num_outputs(geom, sub) / full
 
 
-def oracle_sample(pb, seed=11, max_outputs=40000):
+def oracle_sample(pb, seed=11, max_outputs=40000, target_s=10.0):
     """Time the FP64 oracle on a bounded sample of one reconstruction and extrapolate.
 
     Units timed: the Gram matrix of each stage's null-space region (Algorithm 1 step 2 reads
@@ -204,55 +204,63 @@ def oracle_sample(pb, seed=11, max_outputs=40000):
     one descent step on each stage's region.  A Gram or a step whose valid outputs exceed
     max_outputs runs on a slab of the region and its time is scaled by the ratio of outputs
     (both costs are linear in them).  The reconstruction is the sum over stages of iters x
-    (Gram + eigh + gd_steps x step).  Returns (GD-iters/s, CPU seconds of the sample,
-    description).
+    (Gram + eigh + gd_steps x step).  The sample is repeated until it has taken target_s of CPU
+    time (at most 50 times) and the median extrapolation is kept.  Returns (GD-iters/s, CPU
+    seconds of the sample, description).
     """
     from oracle import hicu_oracle as O
     og = O.Geom(pb.dims, pb.ncoil, pb.kernel, pb.circular)
     x = O.initial_estimate(pb.x0.astype(np.complex128), pb.mask,
                            "time_average" if pb.init == "time_average" else "zero_filled")
-    sample_s, scaled = 0.0, False
-    cache = {}
+    total_s, recons, scaled = 0.0, [], False
+    while True:
+        sample_s = 0.0
+        cache = {}
 
-    def timed(kind, reg):
-        nonlocal sample_s, scaled
-        key = (kind, tuple(reg.off), tuple(reg.ext))
-        if key in cache:
+        def timed(kind, reg):
+            nonlocal sample_s, scaled
+            key = (kind, tuple(reg.off), tuple(reg.ext))
+            if key in cache:
+                return cache[key]
+            sub, frac = _slab(reg, og, pb.kernel, pb.circular, max_outputs)
+            scaled = scaled or frac < 1.0
+            t0 = time.perf_counter()
+            if kind == "gram":
+                cache["G"] = O.gram(x, og, sub)
+            else:
+                f = O.as_filters(O.jl_compress(Q, O.jl_matrix(seed, 0, og.n, 8), "projector"), og)
+                O.gd_step(x, pb.mask, og, sub, f)
+            dt = time.perf_counter() - t0
+            sample_s += dt
+            cache[key] = dt / frac
             return cache[key]
-        sub, frac = _slab(reg, og, pb.kernel, pb.circular, max_outputs)
-        scaled = scaled or frac < 1.0
-        t0 = time.perf_counter()
-        if kind == "gram":
-            cache["G"] = O.gram(x, og, sub)
-        else:
-            f = O.as_filters(O.jl_compress(Q, O.jl_matrix(seed, 0, og.n, 8), "projector"), og)
-            O.gd_step(x, pb.mask, og, sub, f)
-        dt = time.perf_counter() - t0
-        sample_s += dt
-        cache[key] = dt / frac
-        return cache[key]
 
-    t_gram = timed("gram", O.Region(pb.stages[0].off, pb.stages[0].ext))
-    t0 = time.perf_counter()
-    Q, _ = O.nullspace(cache["G"], pb.rank)
-    t_eigh = time.perf_counter() - t0
-    sample_s += t_eigh
-    t_recon = 0.0
-    prev = pb.stages[0]
-    for st in pb.stages:
-        rst = O.Region(st.off, st.ext)
-        t_first = timed("gram", O.Region(prev.off, prev.ext))
-        t_rest = timed("gram", rst) if st.iters > 1 else 0.0
-        t_step = timed("step", rst)
-        # the step above uses p = 8 filters; the step's cost is linear in p
-        t_step *= st.p / 8.0
-        t_recon += t_first + (st.iters - 1) * t_rest + st.iters * (t_eigh + st.gd_steps * t_step)
-        prev = st
-    del t_gram
+        timed("gram", O.Region(pb.stages[0].off, pb.stages[0].ext))
+        t0 = time.perf_counter()
+        Q, _ = O.nullspace(cache["G"], pb.rank)
+        t_eigh = time.perf_counter() - t0
+        sample_s += t_eigh
+        t_recon = 0.0
+        prev = pb.stages[0]
+        for st in pb.stages:
+            rst = O.Region(st.off, st.ext)
+            t_first = timed("gram", O.Region(prev.off, prev.ext))
+            t_rest = timed("gram", rst) if st.iters > 1 else 0.0
+            t_step = timed("step", rst)
+            # the step above uses p = 8 filters; the step's cost is linear in p
+            t_step *= st.p / 8.0
+            t_recon += t_first + (st.iters - 1) * t_rest + st.iters * (t_eigh + st.gd_steps * t_step)
+            prev = st
+        recons.append(t_recon)
+        total_s += sample_s
+        if total_s >= target_s or len(recons) >= 50:
+            break
+    t_recon = statistics.median(recons)
     slab = " (large regions on slabs, times scaled by their share of outputs)" if scaled else ""
     desc = (f"per-stage Gram, one eigh (n={og.n}) and one descent step per stage{slab}, "
-            f"{sample_s:.1f} s of CPU, extrapolated to the {gd_steps_per_recon(pb)}-step schedule")
-    return gd_steps_per_recon(pb) / t_recon, sample_s, desc
+            f"{len(recons)} repetitions, {total_s:.1f} s of CPU, median extrapolated to the "
+            f"{gd_steps_per_recon(pb)}-step schedule")
+    return gd_steps_per_recon(pb) / t_recon, total_s, desc
 
 
 def schedule_text(pb):
