@@ -146,7 +146,7 @@ def conv_null(x: np.ndarray, geom: Geom, reg: Region, filters: np.ndarray) -> np
     R = np.zeros(out_shape(geom, reg) + (f.shape[0],), dtype=np.complex128)
     for dz, dy, dx in _offsets(geom):
         blk = _shifted_block(x, geom, reg, dz, dy, dx)            # (C, sz, sy, sx)
-        R += np.einsum("czyx,kc->zyxk", blk, f[:, :, dz, dy, dx])
+        R += np.einsum("czyx,kc->zyxk", blk, f[:, :, dz, dy, dx], optimize=True)
     return R
 
 
@@ -167,7 +167,7 @@ def conv_null_adjoint(R: np.ndarray, geom: Geom, reg: Region, filters: np.ndarra
         iz = _axis_index(geom, reg, 2, dz)
         iy = _axis_index(geom, reg, 1, dy)
         ix = _axis_index(geom, reg, 0, dx)
-        contrib = np.einsum("zyxk,kc->czyx", R, np.conj(f[:, :, dz, dy, dx]))
+        contrib = np.einsum("zyxk,kc->czyx", R, np.conj(f[:, :, dz, dy, dx]), optimize=True)
         # for a fixed offset d the map p -> p + d is injective, so plain fancy-index add is exact
         g[:, iz[:, None, None], iy[None, :, None], ix[None, None, :]] += contrib
     if mask is not None:
@@ -190,7 +190,7 @@ def filter_gradient(x: np.ndarray, geom: Geom, reg: Region, Rbar: np.ndarray) ->
     F = np.zeros((Rb.shape[-1], geom.ncoil, kz, ky, kx), dtype=np.complex128)
     for dz, dy, dx in _offsets(geom):
         blk = _shifted_block(x, geom, reg, dz, dy, dx)            # (C, sz, sy, sx)
-        F[:, :, dz, dy, dx] = np.einsum("czyx,zyxk->kc", np.conj(blk), Rb)
+        F[:, :, dz, dy, dx] = np.einsum("czyx,zyxk->kc", np.conj(blk), Rb, optimize=True)
     return F
 
 
@@ -214,7 +214,7 @@ def conv_null_at(x: np.ndarray, geom: Geom, reg: Region, filters: np.ndarray, ou
         idx.append(reg.off[a] + rel)                               # (m, k_a)
     ix, iy, iz = idx
     patch = x[:, iz[:, :, None, None], iy[:, None, :, None], ix[:, None, None, :]]   # (C, m, kz, ky, kx)
-    return np.einsum("cmzyx,kczyx->mk", patch, f)
+    return np.einsum("cmzyx,kczyx->mk", patch, f, optimize=True)
 
 
 def gradient_at(x: np.ndarray, geom: Geom, reg: Region, filters: np.ndarray, us: np.ndarray,
@@ -243,7 +243,7 @@ def gradient_at(x: np.ndarray, geom: Geom, reg: Region, filters: np.ndarray, us:
         if not ok.any():
             continue
         R = conv_null_at(x, geom, reg, f, o[ok])                   # (m_ok, p)
-        g[:, ok] += np.einsum("mk,kc->cm", R, np.conj(f[:, :, dz, dy, dx]))
+        g[:, ok] += np.einsum("mk,kc->cm", R, np.conj(f[:, :, dz, dy, dx]), optimize=True)
     if mask is not None:
         m = np.asarray(mask)
         m4 = m if m.ndim == 4 else m[None]
