@@ -5,6 +5,7 @@ The checked losses are linear (Re<W, output>) or quadratic (||H(x) f||^2) in eac
 central difference equals the directional derivative exactly and the comparison only sees FP32
 rounding."""
 import numpy as np
+from closeness import assert_close
 import pytest
 import torch
 
@@ -31,8 +32,6 @@ def H():
     return hicu.Handle()
 
 
-def rel(a, b):
-    return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
 
 
 def setup(H, name, seed=0):
@@ -59,7 +58,7 @@ def test_filter_gradient_parity(H, name):
     F = hicu.hicu_conv_null_filter_grad(H, op.geom, op.region, torch.from_numpy(x).cuda(),
                                         torch.from_numpy(Rb).cuda()).cpu().numpy()
     ref = O.filter_gradient(x, og, oreg, Rb).reshape(p, -1)
-    assert rel(F, ref) < 5e-6
+    assert_close(F, ref, 5e-6)
     # deterministic: a second call is bit-identical
     F2 = hicu.hicu_conv_null_filter_grad(H, op.geom, op.region, torch.from_numpy(x).cuda(),
                                          torch.from_numpy(Rb).cuda()).cpu().numpy()
@@ -98,8 +97,8 @@ def test_conv_null_autograd(H, name):
     loss.backward()
     Wn = W.cpu().numpy().astype(np.complex128)
     # conjugate-Wirtinger convention: the gradient of Re<W, A z> is A^H W
-    assert rel(xt.grad.cpu().numpy(), O.conv_null_adjoint(Wn, og, oreg, filt(f, og))) < 5e-6
-    assert rel(ft.grad.cpu().numpy(), O.filter_gradient(x, og, oreg, Wn).reshape(p, -1)) < 5e-6
+    assert_close(xt.grad.cpu().numpy(), O.conv_null_adjoint(Wn, og, oreg, filt(f, og)), 5e-6)
+    assert_close(ft.grad.cpu().numpy(), O.filter_gradient(x, og, oreg, Wn).reshape(p, -1), 5e-6)
     vx = torch.from_numpy(random_complex(rng, x.shape).astype(np.complex64)).cuda()
     vf = torch.from_numpy(random_complex(rng, f.shape).astype(np.complex64)).cuda()
     lx = lambda t: torch.real(torch.vdot(W.reshape(-1), op.conv_null(t, ft.detach()).reshape(-1)))
@@ -123,8 +122,8 @@ def test_conv_null_adjoint_autograd(H, name):
     loss = torch.real(torch.vdot(W.reshape(-1), g.reshape(-1)))
     loss.backward()
     PW = O.project_unobserved(W.cpu().numpy(), og, oreg, mask)
-    assert rel(Rt.grad.cpu().numpy(), O.conv_null(PW, og, oreg, filt(f, og))) < 5e-6
-    assert rel(ft.grad.cpu().numpy(), O.filter_gradient(PW, og, oreg, R).reshape(p, -1)) < 5e-6
+    assert_close(Rt.grad.cpu().numpy(), O.conv_null(PW, og, oreg, filt(f, og)), 5e-6)
+    assert_close(ft.grad.cpu().numpy(), O.filter_gradient(PW, og, oreg, R).reshape(p, -1), 5e-6)
     vR = torch.from_numpy(random_complex(rng, R.shape).astype(np.complex64)).cuda()
     vf = torch.from_numpy(random_complex(rng, f.shape).astype(np.complex64)).cuda()
     lR = lambda t: torch.real(torch.vdot(W.reshape(-1), op.conv_null_adjoint(t, ft.detach(), mt).reshape(-1)))
@@ -147,8 +146,8 @@ def test_null_objective_recomputes_and_matches(H, name):
     (F * 0.75).backward()
     gx_ref = 1.5 * O.conv_null_adjoint(Rref, og, oreg, filt(f, og))
     gf_ref = 1.5 * O.filter_gradient(x, og, oreg, Rref).reshape(p, -1)
-    assert rel(xt.grad.cpu().numpy(), gx_ref) < 1e-5
-    assert rel(ft.grad.cpu().numpy(), gf_ref) < 1e-5
+    assert_close(xt.grad.cpu().numpy(), gx_ref, 1e-5)
+    assert_close(ft.grad.cpu().numpy(), gf_ref, 1e-5)
     scale = 0.05
     vx = torch.from_numpy(random_complex(rng, x.shape).astype(np.complex64) * scale).cuda()
     vf = torch.from_numpy(random_complex(rng, f.shape).astype(np.complex64) * scale).cuda()
@@ -198,8 +197,8 @@ def test_autograd_full_size_brain_slice(H, prec):
     R = O.conv_null(x, og, reg, filt(f, og))
     tol = 1e-5 if prec == "fp32" else 1e-3
     assert abs(F.item() - np.sum(np.abs(R) ** 2)) < tol * F.item()
-    assert rel(xt.grad.cpu().numpy(), 2 * O.conv_null_adjoint(R, og, reg, filt(f, og))) < tol
-    assert rel(ft.grad.cpu().numpy(), 2 * O.filter_gradient(x, og, reg, R).reshape(p, -1)) < tol
+    assert_close(xt.grad.cpu().numpy(), 2 * O.conv_null_adjoint(R, og, reg, filt(f, og)), tol)
+    assert_close(ft.grad.cpu().numpy(), 2 * O.filter_gradient(x, og, reg, R).reshape(p, -1), tol)
     vx = torch.from_numpy((random_complex(rng, x.shape) * 0.02 * np.abs(x).max()).astype(np.complex64)).cuda()
     vf = torch.from_numpy((random_complex(rng, f.shape) * 0.002).astype(np.complex64)).cuda()
     lx = lambda t: op.null_objective(t, ft.detach())

@@ -13,6 +13,7 @@ Scaled down (cine 96 x 72 x 24, knee 64 x 64 x 40), a short centre-out reconstru
 oracle's: NRMSE <= 1e-3 and SER within 0.05 dB.
 """
 import numpy as np
+from closeness import assert_close
 import pytest
 import torch
 
@@ -38,8 +39,6 @@ def problems():
     return {name: make_problem(name) for name in WORKLOADS}
 
 
-def rel(a, b):
-    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
 
 
 def _setup(pb, seed, p=8):
@@ -73,7 +72,7 @@ def test_full_size_step_sampled(H, problems, name, prec):
            torch.from_numpy(outs[:, 2]).cuda()].cpu().numpy()
     fo = O.as_filters(f.astype(np.complex128), og)
     Ro = O.conv_null_at(y, og, reg, fo, outs)
-    assert rel(Rg, Ro) < 2e-5
+    assert_close(Rg, Ro, 2e-5)
     # masked gradient at sampled positions (including the region's borders)
     g = hicu.hicu_conv_null_adjoint(H, hg, hr, R, fb, mask=md, prec=pr)
     nx, ny, nz = pb.dims
@@ -82,7 +81,7 @@ def test_full_size_step_sampled(H, problems, name, prec):
     gg = g[:, torch.from_numpy(us[:, 0]).cuda(), torch.from_numpy(us[:, 1]).cuda(),
            torch.from_numpy(us[:, 2]).cuda()].cpu().numpy()
     go = O.gradient_at(y, og, reg, fo, us, pb.mask)
-    assert rel(gg, go) < 1e-4
+    assert_close(gg, go, 1e-4)
     # one descent step: eta = ||g||^2 / D and the closed-form decrease of the objective
     stats = hicu.hicu_gd_step_filters(H, hg, hr, yd, md, fb, prec=pr).cpu().numpy()
     eta, obj0, gn2, D = stats
@@ -118,5 +117,5 @@ def test_scaled_reconstruction_matches_oracle(H, name):
     og = O.Geom(pb.dims, pb.ncoil, pb.kernel, pb.circular)
     ost = [O.StageSpec(O.Region(off, ext), it, gd, p) for off, ext, it, gd, p in stages]
     x_ref = O.reconstruct(pb.x0, pb.mask, og, ost, pb.rank, seed=5, jl_mode="projector", init=pb.init)
-    assert rel(x_gpu, x_ref) <= 1e-3
+    assert_close(x_gpu, x_ref, 1e-3)
     assert abs(O.ser_db(pb.x_full, x_gpu) - O.ser_db(pb.x_full, x_ref)) <= 0.05

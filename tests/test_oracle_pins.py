@@ -481,3 +481,55 @@ def test_reconstruct_recovers_exactly_low_rank_data():
 def test_ser_definition():
     a = np.ones(4, dtype=np.complex128)
     assert abs(O.ser_db(a, a * 1.1) - 20.0) < 1e-12              # ||X||/||0.1 X|| = 10
+
+
+def test_reconstruct_stage_transition_uses_previous_region():
+    """Algorithm 1 step 2 takes the null space of H^(i-1)(x^(i-1)), on the region of the
+    previous outer iteration; step 4 then picks S^(i) for the descent steps.  At the first
+    iteration of a new centre-out stage the Gram is therefore formed on the previous stage's
+    region, while the steps already move entries of the new, larger region.
+
+    Pinned through Eq. 1: the logged J of every outer iteration must equal the tail energy
+    sum_{k>r} sigma_k^2 of the explicitly built Hankel matrix (loops of brute_hankel, SVD) of the
+    iterate entering that iteration, on the region the algorithm names.  The outer iterates come
+    from truncated schedules (the JL counter is the global step index, so a prefix of the schedule
+    reproduces the first iterates exactly)."""
+    rng = np.random.default_rng(17)
+    L = 5
+    x_true = lowrank_exponential_kspace(rng, (1, 14, 15), 2, L) + 0.02 * random_complex(rng, (2, 1, 14, 15))
+    mask = (rng.random((1, 14, 15)) < 0.5).astype(np.uint8)
+    x0 = x_true * mask[None]
+    geom = O.Geom((15, 14, 1), 2, (3, 3, 1))
+    S1 = O.Region((4, 3, 0), (8, 7, 1))
+    S2 = O.full_region(geom)
+    st1 = O.StageSpec(S1, iters=2, gd_steps=2, p=4)
+    st2 = O.StageSpec(S2, iters=2, gd_steps=2, p=4)
+    r = L
+
+    def J_eq1(x, reg):
+        sv = np.linalg.svd(brute_hankel(x, geom, reg), compute_uv=False)
+        return float(np.sum(sv[r:] ** 2))
+
+    log = O.ReconLog([], [], [])
+    O.reconstruct(x0, mask, geom, [st1, st2], r, seed=3, log=log)
+    assert len(log.J) == 4 and len(log.eta) == 8
+    # x^(0) .. x^(3): prefixes of the schedule
+    prefixes = [[], [O.StageSpec(S1, 1, 2, 4)], [st1], [st1, O.StageSpec(S2, 1, 2, 4)]]
+    xs = [x0 if not pre else O.reconstruct(x0, mask, geom, pre, r, seed=3) for pre in prefixes]
+    gram_regions = [S1, S1, S1, S2]          # S^(0) := S^(1); iteration 3 uses S^(2) = previous
+    scale = float(np.sum(np.abs(x_true) ** 2))
+    for i, (x, reg) in enumerate(zip(xs, gram_regions)):
+        assert abs(log.J[i] - J_eq1(x, reg)) <= 1e-9 * scale, i
+    # the pin separates the two regions at the transition (a swapped region fails it) ...
+    assert abs(J_eq1(xs[2], S1) - J_eq1(xs[2], S2)) > 1e-3 * scale
+    # ... and the transition iteration's descent steps already act outside S^(1)
+    outside = np.ones(x0.shape, dtype=bool)
+    outside[:, :, 3:10, 4:12] = False
+    unobs = np.broadcast_to(mask[None] == 0, x0.shape)
+    np.testing.assert_array_equal(xs[2][outside], x0[outside])
+    assert np.abs(xs[3] - xs[2])[outside & unobs].max() > 0.0
+    # gram_on="current" takes S^(2) at the transition and gives a different J there
+    log_c = O.ReconLog([], [], [])
+    O.reconstruct(x0, mask, geom, [st1, st2], r, seed=3, gram_on="current", log=log_c)
+    assert abs(log_c.J[2] - J_eq1(xs[2], S2)) <= 1e-9 * scale
+    assert abs(log_c.J[2] - log.J[2]) > 1e-3 * scale
