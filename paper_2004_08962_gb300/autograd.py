@@ -121,8 +121,9 @@ class NullObjective(torch.autograd.Function):
         op = ctx.op
         R = op._conv(x, f)
         # both maps are real-linear in R and g is real-linear in f, so the real factor 2 go
-        # is applied to the small p x n banks instead of the large arrays
-        s = 2.0 * float(go)
+        # is applied to the small p x n banks instead of the large arrays; it stays a device
+        # scalar (no host read, so the backward pass never waits for the stream)
+        s = (2.0 * go.detach()).to(f.dtype)
         gx = op._adjoint(R, f * s) if ctx.needs_input_grad[0] else None
         gf = op._fgrad(x, R) * s if ctx.needs_input_grad[1] else None
         return gx, gf, None

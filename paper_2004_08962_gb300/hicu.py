@@ -154,12 +154,70 @@ def _stream(stream=None):
     return c_void_p(s.cuda_stream)
 
 
+
+# ------------------------------------------------------------ argument checks
+#
+# The C ABI sees only pointers, so a tensor of the wrong dtype, shape, layout or device would be
+# read out of bounds by the kernels.  Every wrapper checks its tensors here and raises ValueError
+# before anything is launched; calls then run with the tensors' device current.
+
+def _dev(*ts):
+    devs = {t.device for t in ts if t is not None}
+    if len(devs) != 1:
+        raise ValueError(f"tensors must all live on one CUDA device, got {sorted(map(str, devs))}")
+    d = devs.pop()
+    if d.type != "cuda":
+        raise ValueError(f"expected CUDA tensors, got {d}")
+    return d
+
+
+def _need(t, name, dtype, shape=None):
+    """dtype, layout and shape of one tensor (its device is checked by _dev)."""
+    if t is None:
+        return
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name} must be a torch.Tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(int(v) for v in shape):
+        raise ValueError(f"{name} must have shape {tuple(int(v) for v in shape)}, got {tuple(t.shape)}")
+
+
+def _kshape(geom):
+    return (geom.ncoil, geom.dim[2], geom.dim[1], geom.dim[0])
+
+
+def _mshape(geom):
+    return _kshape(geom) if geom.mask_per_coil else _kshape(geom)[1:]
+
+
+def _filter_len(geom):
+    return geom.ncoil * geom.k[0] * geom.k[1] * geom.k[2]
+
+
+def _bank(f, geom, name="filters"):
+    if f is None or f.dim() != 2:
+        raise ValueError(f"{name} must be a (p, n) complex64 tensor")
+    _need(f, name, torch.complex64, (f.shape[0], _filter_len(geom)))
+    return f.shape[0]
+
+
 class Handle:
     """Owns a hicu_handle (workspace, warm-start state) on the current device."""
 
     def __init__(self):
         self.ptr = c_void_p()
+        self.device = torch.device("cuda", torch.cuda.current_device())
         self._check(lib().hicu_create(ctypes.byref(self.ptr)))
+
+    def _dev(self, *ts):
+        """The one CUDA device of the tensors, which must be the handle's own."""
+        d = _dev(*ts)
+        if d != self.device:
+            raise ValueError(f"tensors on {d}, but the handle belongs to {self.device}")
+        return d
 
     def _check(self, status: int):
         if status != 0:
@@ -217,10 +275,13 @@ def hicu_profile_eig_sweeps(h: Handle) -> int:
 
 def hicu_gram(h: Handle, geom, region, x: torch.Tensor, G: Optional[torch.Tensor] = None, stream=None):
     n = hicu_filter_length(geom)
+    _need(x, "x", torch.complex64, _kshape(geom))
     if G is None:
         G = torch.empty((n, n), dtype=torch.complex128, device=x.device)
-    h._check(lib().hicu_gram(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(x), _ptr(G),
-                             _stream(stream)))
+    _need(G, "G", torch.complex128, (n, n))
+    with torch.cuda.device(h._dev(x, G)):
+        h._check(lib().hicu_gram(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(x), _ptr(G),
+                                 _stream(stream)))
     return G
 
 
@@ -232,14 +293,16 @@ def hicu_nullspace(h: Handle, G: torch.Tensor, r: int, warm: bool = False, split
                    solver: Optional[str] = None, stream=None):
     """solver: None (by size), "grid" or "cluster"."""
     n = G.shape[0]
-    Q = torch.empty((n - r, n), dtype=torch.complex128, device=G.device)
+    _need(G, "G", torch.complex128, (n, n))
+    Q = torch.empty((max(n - r, 0), n), dtype=torch.complex128, device=G.device)  # r is checked by the library
     eig = torch.empty((n,), dtype=torch.float64, device=G.device)
     if solver not in (None, "grid", "cluster"):
         raise ValueError(f"unknown solver {solver!r}")
     flags = ((HICU_NULLSPACE_WARM if warm else 0) | (HICU_NULLSPACE_SPLIT if split else 0)
              | (HICU_NULLSPACE_GRID if solver == "grid" else 0)
              | (HICU_NULLSPACE_CLUSTER if solver == "cluster" else 0))
-    h._check(lib().hicu_nullspace(h.ptr, n, r, _ptr(G), _ptr(Q), _ptr(eig), flags, _stream(stream)))
+    with torch.cuda.device(h._dev(G)):
+        h._check(lib().hicu_nullspace(h.ptr, n, r, _ptr(G), _ptr(Q), _ptr(eig), flags, _stream(stream)))
     return Q, eig
 
 
@@ -247,12 +310,14 @@ def hicu_principal_subspace(h: Handle, G: torch.Tensor, r: int, want_all: bool =
                             want_tail: bool = False, stream=None):
     """-> (V [r][n] complex128 rows, eig_top [r] ascending[, eig_all [n]][, tail J])."""
     n = G.shape[0]
-    V = torch.empty((r, n), dtype=torch.complex128, device=G.device)
-    top = torch.empty((r,), dtype=torch.float64, device=G.device)
+    _need(G, "G", torch.complex128, (n, n))
+    V = torch.empty((max(r, 0), n), dtype=torch.complex128, device=G.device)  # r is checked by the library
+    top = torch.empty((max(r, 0),), dtype=torch.float64, device=G.device)
     allv = torch.empty((n,), dtype=torch.float64, device=G.device) if want_all else None
     tail = torch.zeros((1,), dtype=torch.float64, device=G.device) if want_tail else None
-    h._check(lib().hicu_principal_subspace(h.ptr, n, r, _ptr(G), _ptr(V), _ptr(top), _ptr(allv), _ptr(tail),
-                                           _stream(stream)))
+    with torch.cuda.device(h._dev(G)):
+        h._check(lib().hicu_principal_subspace(h.ptr, n, r, _ptr(G), _ptr(V), _ptr(top), _ptr(allv),
+                                               _ptr(tail), _stream(stream)))
     out = (V, top)
     if want_all:
         out += (allv,)
@@ -270,55 +335,74 @@ def hicu_nullspace_info(h: Handle):
 
 def hicu_jl_compress(h: Handle, Q: torch.Tensor, p: int, mode: int = HICU_JL_NULLSPACE,
                      P: Optional[torch.Tensor] = None, seed: int = 0, counter: int = 0, stream=None):
+    if Q.dim() != 2:
+        raise ValueError("Q must be a (rows, n) complex128 tensor")
     nr, n = Q.shape
+    _need(Q, "Q", torch.complex128, (nr, n))
+    _need(P, "P", torch.float64, ((nr if mode == HICU_JL_NULLSPACE else n), p))
     bank = torch.empty((p, n), dtype=torch.complex64, device=Q.device)
-    h._check(lib().hicu_jl_compress(h.ptr, n, nr, p, _ptr(Q), mode, _ptr(P), seed, counter,
-                                    _ptr(bank), _stream(stream)))
+    with torch.cuda.device(h._dev(Q, P)):
+        h._check(lib().hicu_jl_compress(h.ptr, n, nr, p, _ptr(Q), mode, _ptr(P), seed, counter,
+                                        _ptr(bank), _stream(stream)))
     return bank
 
 
 def hicu_conv_null_filter_grad(h: Handle, geom, region, x: torch.Tensor, Rbar: torch.Tensor, stream=None):
     """F = H(x)^H Rbar as a (p, n) complex64 filter bank."""
     p = Rbar.shape[-1]
-    n = geom.ncoil * geom.k[0] * geom.k[1] * geom.k[2]
+    n = _filter_len(geom)
+    _need(x, "x", torch.complex64, _kshape(geom))
+    _need(Rbar, "Rbar", torch.complex64, out_shape(geom, region) + (p,))
     F = torch.empty((p, n), dtype=torch.complex64, device=x.device)
-    h._check(lib().hicu_conv_null_filter_grad(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(x),
-                                              _ptr(Rbar), p, _ptr(F), _stream(stream)))
+    with torch.cuda.device(h._dev(x, Rbar)):
+        h._check(lib().hicu_conv_null_filter_grad(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(x),
+                                                  _ptr(Rbar), p, _ptr(F), _stream(stream)))
     return F
 
 
 def hicu_project_unobserved(h: Handle, geom, region, x: torch.Tensor, mask: Optional[torch.Tensor],
                             out: Optional[torch.Tensor] = None, stream=None):
     """(1 - M) o x on the region, 0 elsewhere."""
+    _need(x, "x", torch.complex64, _kshape(geom))
+    _need(mask, "mask", torch.uint8, _mshape(geom))
     if out is None:
         out = torch.empty_like(x)
-    h._check(lib().hicu_project_unobserved(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(mask),
-                                           _ptr(x), _ptr(out), _stream(stream)))
+    _need(out, "out", torch.complex64, _kshape(geom))
+    with torch.cuda.device(h._dev(x, mask, out)):
+        h._check(lib().hicu_project_unobserved(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(mask),
+                                               _ptr(x), _ptr(out), _stream(stream)))
     return out
 
 
 def hicu_conv_null(h: Handle, geom, region, x: torch.Tensor, filters: torch.Tensor,
                    prec: int = HICU_FP32, want_objective: bool = False, stream=None, store_R: bool = True):
     """store_R=False (with want_objective) only reduces ||R||^2 and returns (None, objective)."""
-    p = filters.shape[0]
+    _need(x, "x", torch.complex64, _kshape(geom))
+    p = _bank(filters, geom)
     if not store_R and not want_objective:
         raise ValueError("store_R=False needs want_objective=True")
     R = (torch.empty(out_shape(geom, region) + (p,), dtype=torch.complex64, device=x.device)
          if store_R else None)
     obj = torch.zeros((1,), dtype=torch.float64, device=x.device) if want_objective else None
-    h._check(lib().hicu_conv_null(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(x),
-                                  _ptr(filters), p, _ptr(R), _ptr(obj), prec, _stream(stream)))
+    with torch.cuda.device(h._dev(x, filters)):
+        h._check(lib().hicu_conv_null(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(x),
+                                      _ptr(filters), p, _ptr(R), _ptr(obj), prec, _stream(stream)))
     return (R, obj) if want_objective else R
 
 
 def hicu_conv_null_noalloc(geom, region, x: torch.Tensor, filters: torch.Tensor,
-                           want_objective: bool = False, stream=None):
+                           want_objective: bool = False, stream=None, store_R: bool = True):
     """hicu_conv_null without a handle or any device allocation (static scratch)."""
-    p = filters.shape[0]
-    R = torch.empty(out_shape(geom, region) + (p,), dtype=torch.complex64, device=x.device)
+    _need(x, "x", torch.complex64, _kshape(geom))
+    p = _bank(filters, geom)
+    R = (torch.empty(out_shape(geom, region) + (p,), dtype=torch.complex64, device=x.device)
+         if store_R else None)
+    if R is None and not want_objective:
+        raise ValueError("store_R=False needs want_objective=True")
     obj = torch.zeros((1,), dtype=torch.float64, device=x.device) if want_objective else None
-    st = lib().hicu_conv_null_noalloc(ctypes.byref(geom), ctypes.byref(region), _ptr(x),
-                                      _ptr(filters), p, _ptr(R), _ptr(obj), _stream(stream))
+    with torch.cuda.device(_dev(x, filters)):
+        st = lib().hicu_conv_null_noalloc(ctypes.byref(geom), ctypes.byref(region), _ptr(x),
+                                          _ptr(filters), p, _ptr(R), _ptr(obj), _stream(stream))
     if st != 0:
         raise HicuError(st, lib().hicu_status_string(st).decode())
     return (R, obj) if want_objective else R
@@ -327,25 +411,32 @@ def hicu_conv_null_noalloc(geom, region, x: torch.Tensor, filters: torch.Tensor,
 def hicu_conv_null_adjoint(h: Handle, geom, region, R: torch.Tensor, filters: torch.Tensor,
                            mask: Optional[torch.Tensor] = None, g: Optional[torch.Tensor] = None,
                            prec: int = HICU_FP32, want_gnorm2: bool = False, stream=None):
-    p = filters.shape[0]
+    p = _bank(filters, geom)
+    _need(R, "R", torch.complex64, out_shape(geom, region) + (p,))
+    _need(mask, "mask", torch.uint8, _mshape(geom))
     if g is None:
-        g = torch.zeros((geom.ncoil, geom.dim[2], geom.dim[1], geom.dim[0]), dtype=torch.complex64,
-                        device=R.device)
+        g = torch.zeros(_kshape(geom), dtype=torch.complex64, device=R.device)
+    _need(g, "g", torch.complex64, _kshape(geom))
     gn = torch.zeros((1,), dtype=torch.float64, device=R.device) if want_gnorm2 else None
-    h._check(lib().hicu_conv_null_adjoint(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(R),
-                                          _ptr(filters), p, _ptr(mask), _ptr(g), _ptr(gn), prec,
-                                          _stream(stream)))
+    with torch.cuda.device(h._dev(R, filters, mask, g)):
+        h._check(lib().hicu_conv_null_adjoint(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(R),
+                                              _ptr(filters), p, _ptr(mask), _ptr(g), _ptr(gn), prec,
+                                              _stream(stream)))
     return (g, gn) if want_gnorm2 else g
 
 
 def hicu_gd_step_filters(h: Handle, geom, region, y: torch.Tensor, mask: Optional[torch.Tensor],
                          filters: torch.Tensor, prec: int = HICU_FP32, stats=None, stream=None):
-    p = filters.shape[0]
+    _need(y, "y", torch.complex64, _kshape(geom))
+    _need(mask, "mask", torch.uint8, _mshape(geom))
+    p = _bank(filters, geom)
     if stats is None:
         stats = torch.zeros((4,), dtype=torch.float64, device=y.device)
-    h._check(lib().hicu_gd_step_filters(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(y),
-                                        _ptr(mask), _ptr(filters), p, _ptr(stats), prec,
-                                        _stream(stream)))
+    _need(stats, "stats", torch.float64, (4,))
+    with torch.cuda.device(h._dev(y, mask, filters, stats)):
+        h._check(lib().hicu_gd_step_filters(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(y),
+                                            _ptr(mask), _ptr(filters), p, _ptr(stats), prec,
+                                            _stream(stream)))
     return stats
 
 
@@ -353,12 +444,20 @@ def hicu_gd_step(h: Handle, geom, region, y: torch.Tensor, mask: Optional[torch.
                  Q: torch.Tensor, p: int, jl_mode: int = HICU_JL_NULLSPACE, seed: int = 0,
                  counter: int = 0, P: Optional[torch.Tensor] = None, prec: int = HICU_FP32,
                  stats=None, stream=None):
+    _need(y, "y", torch.complex64, _kshape(geom))
+    _need(mask, "mask", torch.uint8, _mshape(geom))
+    if Q.dim() != 2:
+        raise ValueError("Q must be a (rows, n) complex128 tensor")
     nr = Q.shape[0]
+    _need(Q, "Q", torch.complex128, (nr, _filter_len(geom)))
+    _need(P, "P", torch.float64, ((nr if jl_mode == HICU_JL_NULLSPACE else _filter_len(geom)), p))
     if stats is None:
         stats = torch.zeros((4,), dtype=torch.float64, device=y.device)
-    h._check(lib().hicu_gd_step(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(y), _ptr(mask),
-                                _ptr(Q), nr, p, jl_mode, seed, counter, _ptr(P), _ptr(stats), prec,
-                                _stream(stream)))
+    _need(stats, "stats", torch.float64, (4,))
+    with torch.cuda.device(h._dev(y, mask, Q, P, stats)):
+        h._check(lib().hicu_gd_step(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(y), _ptr(mask),
+                                    _ptr(Q), nr, p, jl_mode, seed, counter, _ptr(P), _ptr(stats), prec,
+                                    _stream(stream)))
     return stats
 
 
@@ -391,8 +490,14 @@ def make_params(rank: int, stages, seed: int = 0, jl: int = HICU_JL_PROJECTOR, p
 def hicu_reconstruct(h: Handle, geom, x0: torch.Tensor, mask: torch.Tensor, params: hicu_params,
                      x_out: Optional[torch.Tensor] = None, want_log: bool = False, stream=None):
     """x0 / mask / x_out may live on the GPU or (pinned) on the host."""
+    _need(x0, "x0", torch.complex64, _kshape(geom))
+    _need(mask, "mask", torch.uint8, _mshape(geom))
     if x_out is None:
         x_out = torch.empty_like(x0)
+    _need(x_out, "x_out", torch.complex64, _kshape(geom))
+    on_gpu = [t for t in (x0, mask, x_out) if t.device.type == "cuda"]
+    if on_gpu:
+        h._dev(*on_gpu)
     log_struct, logs = None, None
     if want_log:
         iters = sum(params.stages[i].iters for i in range(params.nstages))
@@ -418,6 +523,9 @@ def hicu_reconstruct(h: Handle, geom, x0: torch.Tensor, mask: torch.Tensor, para
 
 def make_problem_struct(geom, x0: torch.Tensor, mask: torch.Tensor, params: hicu_params,
                         x_out: torch.Tensor) -> hicu_problem:
+    _need(x0, "x0", torch.complex64, _kshape(geom))
+    _need(mask, "mask", torch.uint8, _mshape(geom))
+    _need(x_out, "x_out", torch.complex64, _kshape(geom))
     pr = hicu_problem()
     pr.geom = geom
     pr.x0 = x0.data_ptr()
