@@ -449,12 +449,15 @@ hicu_status hicu_reconstruct_batched(hicu_handle* h, int32_t nslices, const hicu
  *   No handle, no cudaMalloc/cudaFree, no allocating library call.  Scratch is
  *   one static device array of HICU_NOALLOC_SCRATCH_BYTES that every GPU
  *   loading the library keeps until the process exits.
- *   Limits: n * roundup(p, 16) <= HICU_NOALLOC_MAX_FILTER_WORDS and
- *   ceil(sx/32) * ceil(sy/4) * sz <= HICU_NOALLOC_MAX_PARTIALS; larger requests
- *   return HICU_ERR_UNSUPPORTED (use hicu_conv_null).  Other errors: HICU_ERR_ARG,
- *   HICU_ERR_RANK, HICU_ERR_SHAPE, HICU_ERR_CUDA (no error text without a handle).
+ *   Limits: n * roundup(p, 16) <= HICU_NOALLOC_MAX_FILTER_WORDS,
+ *   ceil(sx/32) * ceil(sy/4) * sz <= HICU_NOALLOC_MAX_PARTIALS, and the halo tile
+ *   of 8*kz*(ky+3)*(kx+31) bytes within the device's per-block shared-memory
+ *   opt-in maximum (227 KB on GB300); larger requests return HICU_ERR_UNSUPPORTED
+ *   (use hicu_conv_null).  Other errors: HICU_ERR_ARG, HICU_ERR_RANK,
+ *   HICU_ERR_SHAPE, HICU_ERR_CUDA (no error text without a handle).
  *   The first call on each device (with that device current) looks up the
- *   array's device address; make that first call before any stream capture.
+ *   array's device address and keeps it; make that first call before any stream
+ *   capture, and do not reset the device (cudaDeviceReset) between calls.
  *   All calls share the array and it keeps the previous call's contents; each
  *   call writes every word it reads, so nothing needs clearing.  Calls that
  *   overlap on the GPU (other streams or host threads) race on the array.

@@ -21,7 +21,14 @@
 // Device address: host code cannot pass the array's name to a kernel (on the host
 // it is only a stand-in symbol), so the first call on each device, with that
 // device current, looks the address up with cudaGetSymbolAddress and caches it;
-// that first call should come before any stream capture.
+// that first call should come before any stream capture.  The cached address
+// belongs to the device's context: a cudaDeviceReset between calls would leave
+// it stale, so callers must not reset the device while they use this entry point.
+//
+// Shared memory: the convolution's halo tile takes 8*kz*(ky+3)*(kx+31) bytes;
+// above 48 KB the call raises the kernel's dynamic shared-memory limit (a
+// function attribute, no allocation), and a tile above the device's per-block
+// opt-in maximum (227 KB on GB300) is refused with HICU_ERR_UNSUPPORTED.
 #include <mutex>
 
 #include "hicu_internal.cuh"
@@ -74,12 +81,24 @@ extern "C" hicu_status hicu_conv_null_noalloc(const hicu_geom* geom, const hicu_
   size_t smem = 0;
   conv_fp32_launch_shape(g, &grid, &block, &smem);
   const long long nblocks = (long long)grid.x * grid.y * grid.z;
-  if ((long long)g.n * Ppad > HICU_NOALLOC_MAX_FILTER_WORDS || nblocks > HICU_NOALLOC_MAX_PARTIALS ||
-      smem > 48 * 1024)
+  if ((long long)g.n * Ppad > HICU_NOALLOC_MAX_FILTER_WORDS || nblocks > HICU_NOALLOC_MAX_PARTIALS)
     return HICU_ERR_UNSUPPORTED;  // beyond the static scratch: use hicu_conv_null
   void* base = nullptr;
   s = scratch_for_current_device(&base);
   if (s) return s;
+  if (smem > 48 * 1024) {
+    // the halo tile needs the opt-in shared-memory size (a function attribute, no allocation)
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, (const void*)conv_fp32_kernel) != cudaSuccess) {
+      cudaGetLastError();
+      return HICU_ERR_CUDA;
+    }
+    if (smem + fa.sharedSizeBytes > (size_t)optin) return HICU_ERR_UNSUPPORTED;
+    if (allow_max_dynamic_smem((const void*)conv_fp32_kernel) != cudaSuccess) return HICU_ERR_CUDA;
+  }
   float2* fT = reinterpret_cast<float2*>(base);
   double* part = reinterpret_cast<double*>(static_cast<unsigned char*>(base) + kFilterBytes);
   cudaStream_t st = (cudaStream_t)stream;
