@@ -1,22 +1,30 @@
 #!/usr/bin/env python3
 """Benchmark of the HICU hot path on GB300.
 
-One step = one call of hicu_reconstruct on the 2D brain-slice workload
-(256 x 256 k-space, 8 coils, 5 x 5 kernel, n = 200, rank 75; centre-out stage
-on the central 64 x 64 region: 50 outer iterations x 5 descent steps, p = 8;
-then full k-space: 10 outer iterations x 10 descent steps, p = 32), i.e. 60
-Gram + null-space updates and 350 JL-compressed descent steps with exact line
-search.  The metric is descent steps (GD iterations) per second.
+One step = one call of hicu_reconstruct (Algorithm 1 with centre-out stages: Gram,
+principal subspace, JL-compressed descent steps with exact line search) on the
+chosen workload.  The default line is the 3D knee-shaped volume (256 x 256 x 160,
+8 coils, 5 x 5 x 5 kernel, n = 1000, rank 400; centre-out stage on the central
+64 x 64 x 40 region: 10 outer iterations x 5 descent steps, p = 8; then full
+k-space: 1 outer iteration x 20 descent steps, p = 8), i.e. 11 Gram + null-space
+updates and 70 descent steps.  --workload brain / cine / batch give the other
+configurations.  The metric is descent steps (GD iterations) per second.
 
   value   device time of K steps (CUDA events on the launch stream), inputs
-          resident in HBM, L2 flushed between steps, max over ranks
+          resident in HBM, L2 flushed between steps, max over ranks; no per-launch
+          events inside this timed region (launches are only counted)
   e2e     the same call with pinned HOST input/output buffers: the library
           copies x0 and the mask in and the result out inside the timed call
-  roofline  the kernel class with the largest live device time, timed with CUDA
-          events around each of its launches during the timed region
-  cpu_baseline  the FP64 oracle on a bounded sample of the same workload
+  roofline  the kernel class with the largest device time: one reconstruction per
+          class finds it, then a second pass of K steps brackets each of its
+          launches with CUDA events on its launch stream
+  accuracy  the timed split-BF16 reconstruction against the plain-FP32 GPU
+          reconstruction of the same schedule, and both GPU forms against the FP64
+          oracle on the workload scaled down with a shortened schedule
+  cpu_baseline  the FP64 oracle on a bounded sample of the same workload,
+          extrapolated to the schedule
 
-Multi-GPU: replicas only (each rank reconstructs its own slice), no collective
+Multi-GPU: replicas only (each rank reconstructs its own problem), no collective
 on the data path; launched by torchrun with one process per GPU.
 """
 from __future__ import annotations
@@ -36,20 +44,34 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "2d_brain_256"
-METRIC = "HICU GD-iters/s (full hicu_reconstruct of one 256x256x8-coil slice)"
-# --workload name -> (synthetic problem, metric text); the brain slice is the default line
+# --workload name -> (synthetic problem, metric text); the knee volume is the default line
 WORKLOADS = {
-    "brain": ("2d_brain_256", METRIC),
-    "cine": ("cine_192x144x24", "HICU GD-iters/s (full hicu_reconstruct of one 192x144x24-frame 8-coil cine)"),
     "knee": ("knee3d_256x256x160", "HICU GD-iters/s (full hicu_reconstruct of one 256x256x160 8-coil volume)"),
+    "brain": ("2d_brain_256", "HICU GD-iters/s (full hicu_reconstruct of one 256x256x8-coil slice)"),
+    "cine": ("cine_192x144x24", "HICU GD-iters/s (full hicu_reconstruct of one 192x144x24-frame 8-coil cine)"),
 }
+# accuracy block: (scale-down factor per spatial axis, (iters, gd_steps, p) per stage) of the
+# reconstruction compared with the FP64 oracle
+ORACLE_CHECK = {"knee": (4, [(2, 2, 8), (1, 2, 8)]), "cine": (2, [(2, 2, 8), (1, 2, 8)]),
+                "brain": (2, [(10, 5, 8), (2, 5, 32)])}
 UNIT = "GD-iters/s"
 KERNEL_NAMES = {0: "gram", 1: "eig", 2: "conv_fp32", 3: "adjoint_fp32", 4: "jl", 5: "misc",
                 6: "conv_tc", 7: "adjoint_tc", 8: "tridiag"}
-FP64_PEAK_TFLOPS = 1.25  # FP64 FMA-chain probe on this GB300, equal to the nominal rate
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of the same
-# kernel on the same workload (profiles/); a kernel changed since its capture has no entry.
-NCU_TRAFFIC = {("2d_brain_256", "tridiag_cluster_kernel"): 704000}
+# FP32 pipe: 152 SMs x 128 lanes, one FMA (2 flops) or one add/multiply per lane per clock
+SMS, FP32_LANES = 152, 128
+# Gram: each complex product conj(a) b is 4 real products, each formed exactly and accumulated in
+# double-word arithmetic (1 multiply, 1 FMA for the error term, 8 adds of the two-sum): 40 FP32
+# instructions for the 8 algorithmic flops of one complex multiply-add
+GRAM_INSTR_PER_CMAC = 40
+# DRAM bytes (read + write) per launch from one ncu capture of the same kernel on the same
+# workload (profiles/); a kernel changed since its capture has no entry.
+NCU_TRAFFIC = {}
+
+
+def problem_seed(workload: str, rank: int) -> int:
+    """Seed of the synthetic problem of a workload on a rank (replicas reconstruct different data)."""
+    order = {"brain": 0, "cine": 1, "knee": 2}
+    return 1000 * (1 + order[workload]) + rank
 
 
 def load_peaks():
@@ -94,6 +116,75 @@ def algorithmic_flops(pb, cls):
             tot += st.iters * 8.0 * n * n * pb.rank
         prev = st
     return tot
+
+
+def _filter_len(pb):
+    return pb.ncoil * pb.kernel[0] * pb.kernel[1] * pb.kernel[2]
+
+
+def class_roofline(pb, wname, cls, ms, launches, recons, peaks):
+    """Roofline of one kernel class from its summed event time `ms` over `launches` launches made by
+    `recons` reconstructions: algorithmic work of those reconstructions / device time, against the
+    peak of the pipe the kernel runs on."""
+    fp32_instr = SMS * FP32_LANES * peaks.get("sm_max_mhz", 2070.0) * 1e6   # FP32 instructions / s
+    avg_s = ms / 1e3 / max(launches, 1)
+    flops = algorithmic_flops(pb, cls) * recons
+    ach = flops / max(ms / 1e3, 1e-12) / 1e12
+    base = {"kernel": KERNEL_NAMES[cls], "avg_launch_us": avg_s * 1e6, "launches": launches}
+    if cls in (6, 7):
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        base.update({"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                     "peak_source": "measured bf16 cuBLAS GEMM, sustained (the kernel is timed inside a "
+                                    "long reconstruction)",
+                     "work": "8 n p s algorithmic flops per convolution (n p s complex MACs); the split-bf16 "
+                             "form issues 4 tensor products per algorithmic one (hi and lo of the input "
+                             "against [B_hi | B_lo])"})
+    elif cls == 0:
+        peak = fp32_instr * 8.0 / GRAM_INSTR_PER_CMAC / 1e12
+        base.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                     "peak_source": f"FP32 pipe {SMS} SMs x {FP32_LANES} lanes x max SM clock, "
+                                    f"{GRAM_INSTR_PER_CMAC} FP32 instructions per double-word complex "
+                                    "multiply-add (8 algorithmic flops)",
+                     "work": "lag-form cross-correlation: C^2 (2k-1)^d / 2 complex MACs per region point "
+                             "(8 flops each)"})
+    elif cls in (2, 3):
+        peak = 2.0 * fp32_instr / 1e12
+        base.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                     "peak_source": "FP32 pipe, FMA = 2 flops, max SM clock",
+                     "work": "8 n p s flops per convolution"})
+    elif cls == 8:
+        n = _filter_len(pb)
+        per_step_us = avg_s * 1e6 / max(n - 2, 1)
+        base.update({"bound": "latency", "achieved": per_step_us, "unit": "us per Householder step",
+                     "peak": None, "frac": None, "n": n,
+                     "algorithmic_tflops": ach,
+                     "work": "16 n^3 / 3 flops per tridiagonalisation in n - 2 dependent Householder steps, "
+                             "one barrier each, double-float arithmetic on the FP32 pipe"})
+    else:
+        base.update({"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None})
+    tr = NCU_TRAFFIC.get((wname, base["kernel"]))
+    base["traffic"] = tr
+    if tr is not None:
+        base["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
+    return base
+
+
+def roofline_block(pb, wname, cls, ms, launches, eig_sweeps, recons, peaks, peak_src):
+    r = class_roofline(pb, wname, cls, ms, launches, recons, peaks)
+    r["peaks_source"] = peak_src
+    r["timing"] = f"CUDA events around each launch of the class on its launch stream, {recons} reconstructions"
+    if cls == 1 and eig_sweeps:
+        r["jacobi_sweeps"] = eig_sweeps
+    return r
+
+
+def kernel_rooflines(pb, wname, per_class, peaks):
+    out = {}
+    for c in (6, 7, 0, 8, 2, 3):
+        ms, nl = per_class.get(c, (0.0, 0))
+        if nl:
+            out[KERNEL_NAMES[c]] = class_roofline(pb, wname, c, ms, nl, 1, peaks)
+    return out
 
 
 class ClockSampler:
@@ -289,27 +380,39 @@ def blas_threads():
 
 
 def run_reference(args, rank, world):
+    """The oracle arm: every step is one bounded sample of the workload (per stage the Gram of its
+    null-space region, one eigh and one descent step, regions above 10 000 valid outputs cut to a
+    slab), timed on the host cores; `value` is the GD-iters/s of the whole schedule extrapolated
+    from the sample (median over the timed steps), `ms_per_step` the measured time of one sample."""
     if rank != 0:
         return 0
     from synth.phantoms import make_problem
     wname, metric = WORKLOADS[args.workload]
-    pb = make_problem(wname)
-    vals, descs = [], []
+    pb = make_problem(wname, seed=problem_seed(args.workload, 0))
+    vals, descs, step_s = [], [], []
     for i in range(args.warmup + args.steps):
-        v, _, desc = oracle_sample(pb)
+        t0 = time.perf_counter()
+        v, _, desc = oracle_sample(pb, max_outputs=10000, target_s=0.0)
+        dt = time.perf_counter() - t0
         if i >= args.warmup:
             vals.append(v)
             descs.append(desc)
+            step_s.append(dt)
     value = statistics.median(vals)
     cores = blas_threads()
     sample = "per step: " + descs[-1]
+    config = workload_config(wname, pb)
+    config.update({"l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"})
     line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * gd_steps_per_recon(pb) / value,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(step_s) / len(step_s),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "impl": "reference",
-            "config": workload_config(wname, pb),
+            "data": "synthetic", "impl": "reference", "extrapolated": True,
+            "extrapolated_ms_per_reconstruction": 1e3 * gd_steps_per_recon(pb) / value,
+            "note": "ms_per_step is the measured time of one bounded oracle sample; value is the "
+                    "schedule's GD-iters/s extrapolated from it",
+            "config": config,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "extrapolated": True},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -331,6 +434,8 @@ def run_profile_case(kind: str, size: int) -> int:
         Gram (n = 200, r = 75) and of the cine workload's centre-region Gram (n = 1000, r = 300),
         twice each
     recon: one full reconstruction of the brain slice (for the launch list)
+    recon_knee: one full reconstruction of the knee volume (for the launch list)
+    gram_knee: the Gram of the knee volume's centre region (n = 1000), twice
     """
     import torch
     from paper_2004_08962_gb300 import build, hicu
@@ -388,6 +493,18 @@ def run_profile_case(kind: str, size: int) -> int:
                                   prec=hicu.HICU_SPLIT_BF16)
         hicu.hicu_reconstruct(h, geom, torch.from_numpy(pb.x0).cuda(), torch.from_numpy(pb.mask).cuda(),
                               params)
+    elif kind in ("recon_knee", "gram_knee"):
+        pk = make_problem("knee3d_256x256x160", seed=problem_seed("knee", 0))
+        gk = hicu.make_geom(pk.dims, pk.ncoil, pk.kernel, pk.circular)
+        xk = torch.from_numpy(pk.x0).cuda()
+        if kind == "recon_knee":
+            params = hicu.make_params(pk.rank, schedule(pk), seed=11, jl=hicu.HICU_JL_PROJECTOR,
+                                      prec=hicu.HICU_SPLIT_BF16)
+            hicu.hicu_reconstruct(h, gk, xk, torch.from_numpy(pk.mask).cuda(), params)
+        else:
+            st = pk.stages[0]
+            for _ in range(2):
+                hicu.hicu_gram(h, gk, hicu.make_region(st.off, st.ext), xk)
     else:
         raise SystemExit(f"unknown profile case {kind}")
     torch.cuda.synchronize()
@@ -506,6 +623,68 @@ def run_batch(args, rank, world):
 
 # -------------------------------------------------------------------- GPU arm
 
+def timed_recons(one, steps, flush, stream):
+    """Device time (ms) of `steps` reconstructions: CUDA events on the launch stream around each
+    call, L2 flushed before each (outside the events), synchronised on both sides."""
+    import torch
+    total = 0.0
+    torch.cuda.synchronize()
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one()
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    return total
+
+
+def accuracy_block(args, pb, hicu, h, geom, x_bf16, x_fp32):
+    """NRMSE / SER of the timed split-BF16 reconstruction against the plain-FP32 GPU reconstruction
+    of the same schedule, and (the full-size oracle reconstruction would take hours) both GPU
+    forms against the FP64 oracle on the workload scaled down with a shortened schedule."""
+    import torch
+    from oracle import hicu_oracle as O
+    from synth.phantoms import make_problem
+    out = {}
+    if x_bf16 is not None and x_fp32 is not None:
+        out["split_bf16_vs_plain_fp32"] = {
+            "nrmse": float(np.linalg.norm(x_bf16 - x_fp32) / np.linalg.norm(x_fp32)),
+            "ser_db_split_bf16": O.ser_db(pb.x_full, x_bf16), "ser_db_plain_fp32": O.ser_db(pb.x_full, x_fp32),
+            "ser_db_zero_filled": O.ser_db(pb.x_full, pb.x0)}
+    if args.no_oracle_check:
+        return out
+    name = WORKLOADS[args.workload][0]
+    scale, sched = ORACLE_CHECK[args.workload]
+    ps = make_problem(name, scale=scale)
+    stages = [(st.off, st.ext, it, gd, p) for st, (it, gd, p) in zip(ps.stages, sched)]
+    init = 1 if ps.init == "time_average" else 0
+    og = O.Geom(ps.dims, ps.ncoil, ps.kernel, ps.circular)
+    ost = [O.StageSpec(O.Region(off, ext), it, gd, p) for off, ext, it, gd, p in stages]
+    t0 = time.perf_counter()
+    ref = O.reconstruct(ps.x0, ps.mask, og, ost, ps.rank, seed=5, jl_mode="projector", init=ps.init)
+    t_or = time.perf_counter() - t0
+    gs = hicu.make_geom(ps.dims, ps.ncoil, ps.kernel, ps.circular)
+    res = {"workload": f"{name} scaled 1/{scale} per spatial axis ({'x'.join(str(d) for d in ps.dims if d > 1)})",
+           "schedule": " + ".join(f"{it}x{gd} p={p}" for it, gd, p in sched), "oracle_s": t_or,
+           "ser_db_oracle": O.ser_db(ps.x_full, ref)}
+    for tag, prec in (("split_bf16", hicu.HICU_SPLIT_BF16), ("plain_fp32", hicu.HICU_FP32)):
+        prm = hicu.make_params(ps.rank, stages, seed=5, jl=hicu.HICU_JL_PROJECTOR, prec=prec, init=init)
+        x = hicu.hicu_reconstruct(h, gs, torch.from_numpy(ps.x0).cuda(), torch.from_numpy(ps.mask).cuda(),
+                                  prm).cpu().numpy()
+        res[tag] = {"nrmse": float(np.linalg.norm(x - ref) / np.linalg.norm(ref)),
+                    "max_abs_err_rel": float(np.max(np.abs(x - ref)) / np.max(np.abs(ref))),
+                    "ser_db": O.ser_db(ps.x_full, x)}
+    res["bounds"] = "NRMSE <= 1e-3 and SER within 0.05 dB of the oracle's"
+    res["pass"] = all(res[t]["nrmse"] <= 1e-3 and abs(res[t]["ser_db"] - res["ser_db_oracle"]) <= 0.05
+                      for t in ("split_bf16", "plain_fp32"))
+    out["oracle_check"] = res
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -514,12 +693,15 @@ def main():
     ap.add_argument("--impl", default="hicu", choices=["hicu", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", default=None, choices=["eig", "eig_cluster", "tc_step", "tc_step3d", "principal", "fgrad", "recon"],
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the scaled-down oracle reconstruction of the accuracy block")
+    ap.add_argument("--profile", default=None, choices=["eig", "eig_cluster", "tc_step", "tc_step3d", "principal",
+                                                        "fgrad", "recon", "recon_knee", "gram_knee"],
                     help="run one small fixed case for an ncu capture and exit")
     ap.add_argument("--size", type=int, default=2048, help="image size of the tc_step profile case")
-    ap.add_argument("--workload", default="brain", choices=["brain", "cine", "knee", "batch"],
-                    help="brain: the 256x256x8 slice (default line); cine: 192x144x24 frames x 8 coils, "
-                         "5x5x5 kernel, circular time; knee: 256x256x160 x 8 coils, 5x5x5 kernel; "
+    ap.add_argument("--workload", default="knee", choices=["knee", "brain", "cine", "batch"],
+                    help="knee: 256x256x160 x 8 coils, 5x5x5 kernel (default line); brain: the 256x256x8 "
+                         "slice; cine: 192x144x24 frames x 8 coils, 5x5x5 kernel, circular time; "
                          "batch: the uneven 52-slice batch")
     ap.add_argument("--lanes", type=int, default=8, help="worker lanes of the batched workload")
     args = ap.parse_args()
@@ -554,7 +736,7 @@ def main():
         build.build()
     if world > 1:
         dist.barrier()
-    pb = make_problem(wname, seed=1000 * (1 + list(WORKLOADS).index(args.workload)) + rank)
+    pb = make_problem(wname, seed=problem_seed(args.workload, rank))
     prec = hicu.HICU_FP32 if args.prec == "fp32" else hicu.HICU_SPLIT_BF16
     h = hicu.Handle()
     geom = hicu.make_geom(pb.dims, pb.ncoil, pb.kernel, pb.circular)
@@ -570,71 +752,56 @@ def main():
     def one():
         hicu.hicu_reconstruct(h, geom, x0, mask, params, x_out=xout)
 
-    # warm-up; the last warm-up steps find the kernel class with the most device time
-    classes = [0, 1, 2, 3, 4, 5, 6, 7, 8]
-    per_class = {}
-    for i in range(args.warmup):
+    for _ in range(args.warmup):
         one()
-    for c in classes:
-        hicu.hicu_profile_select(h, c)
-        one()
-        ms, nl, _ = hicu.hicu_profile_read(h)
-        per_class[c] = ms
-    dominant = max(per_class, key=per_class.get)
-    launches_per_class = {}
-    for c in classes:
-        hicu.hicu_profile_select(h, c)
-        one()
-        ms, nl, _ = hicu.hicu_profile_read(h)
-        launches_per_class[c] = (ms, nl)
-    hicu.hicu_profile_select(h, -1)
 
-    # timed region
+    # timed region: no per-launch events (profiling off); launches are only counted
+    hicu.hicu_profile_select(h, -1)
+    hicu.hicu_profile_read(h)
     sampler = ClockSampler(local)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     sampler.start()
-    hicu.hicu_profile_select(h, dominant)
-    hicu.hicu_profile_eig_sweeps(h)  # reset the sweep counter
-    total_ms = 0.0
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        one()
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
-    torch.cuda.synchronize()
-    dom_ms, dom_launches, all_launches = hicu.hicu_profile_read(h)
-    eig_sweeps = hicu.hicu_profile_eig_sweeps(h)
-    hicu.hicu_profile_select(h, -1)
+    total_ms = timed_recons(one, args.steps, flush, stream)
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
+    _, _, all_launches = hicu.hicu_profile_read(h)
     tmax_s = max_over_ranks(total_ms, "cuda") / 1e3
     value = job_rate(steps_per, args.steps, world, tmax_s)
+    x_main = xout.cpu().numpy() if rank == 0 else None
+
+    # class times, one reconstruction per kernel class with events around that class's launches
+    classes = [0, 1, 2, 3, 4, 5, 6, 7, 8]
+    per_class = {}
+    for c in classes:
+        hicu.hicu_profile_select(h, c)
+        one()
+        ms, nl, _ = hicu.hicu_profile_read(h)
+        per_class[c] = (ms, nl)
+    hicu.hicu_profile_select(h, -1)
+    dominant = max(per_class, key=lambda c: per_class[c][0])
+    # roofline pass: the same K reconstructions with events around every launch of the dominant class
+    hicu.hicu_profile_select(h, dominant)
+    hicu.hicu_profile_eig_sweeps(h)
+    roof_total_ms = timed_recons(one, args.steps, flush, stream)
+    dom_ms, dom_launches, _ = hicu.hicu_profile_read(h)
+    eig_sweeps = hicu.hicu_profile_eig_sweeps(h)
+    hicu.hicu_profile_select(h, -1)
 
     # the plain complex-FP32 form of the same reconstruction, same timing rules
-    fp32_ms = None
+    fp32_ms, fp32_steps, x_fp32 = None, 0, None
     if args.prec == "bf16":
         params32 = hicu.make_params(pb.rank, schedule(pb), seed=11, jl=hicu.HICU_JL_PROJECTOR,
                                     prec=hicu.HICU_FP32, init=init)
-        hicu.hicu_reconstruct(h, geom, x0, mask, params32, x_out=xout)
-        fp32_ms = 0.0
-        for _ in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            hicu.hicu_reconstruct(h, geom, x0, mask, params32, x_out=xout)
-            e1.record(stream)
-            e1.synchronize()
-            fp32_ms += e0.elapsed_time(e1)
-
-    fp32_value = None if fp32_ms is None else job_rate(steps_per, args.steps, world,
+        out32 = torch.empty_like(x0)
+        one32 = lambda: hicu.hicu_reconstruct(h, geom, x0, mask, params32, x_out=out32)
+        one32()
+        fp32_steps = min(args.steps, 5)
+        fp32_ms = timed_recons(one32, fp32_steps, flush, stream)
+        x_fp32 = out32.cpu().numpy() if rank == 0 else None
+    fp32_value = None if fp32_ms is None else job_rate(steps_per, fp32_steps, world,
                                                         max_over_ranks(fp32_ms, "cuda") / 1e3)
 
     # end-to-end through the C ABI with pinned host buffers (copies inside the call)
@@ -663,70 +830,9 @@ def main():
         return 0
 
     peaks, peak_src = load_peaks()
-    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # TFLOP/s
-    avg_launch_s = dom_ms / 1e3 / max(dom_launches, 1)
-    flops_recon = algorithmic_flops(pb, dominant)
-    if dominant in (1, 8) and eig_sweeps > 0:
-        # Jacobi: per round the n x n Hermitian matrix is rotated from both sides (4 complex MACs
-        # per entry) and V from one side (2 per entry): 48 n^2 real FP64 flops; n-1 rounds a sweep
-        n = pb.ncoil * pb.kernel[0] * pb.kernel[1] * pb.kernel[2]
-        per_launch = eig_sweeps * (n - 1) * 48.0 * n * n / max(dom_launches, 1)
-        achieved = per_launch / avg_launch_s / 1e12
-        roof = {"kernel": KERNEL_NAMES[dominant], "bound": "alu", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": None,
-                "peak_source": "FP64 FMA-chain probe on this GB300 (1.25 TFLOP/s, equal to the nominal rate)",
-                "avg_launch_us": avg_launch_s * 1e6, "launches": dom_launches,
-                "sweeps_per_launch": eig_sweeps / max(dom_launches, 1)}
-    elif dominant in (1, 8) and flops_recon > 0:
-        per_launch = flops_recon * args.steps / max(dom_launches, 1)
-        achieved = per_launch / avg_launch_s / 1e12
-        n_pb = pb.ncoil * pb.kernel[0] * pb.kernel[1] * pb.kernel[2]
-        # n <= 416 runs the one-cluster form of the tridiagonalisation, larger n the grid form
-        kname = (("tridiag_cluster_kernel" if n_pb <= 416 else "tridiag_kernel") if dominant == 8
-                 else KERNEL_NAMES[dominant])
-        roof = {"kernel": kname, "bound": "alu",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get((wname, kname)),
-                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-                "work": "16 n^3 / 3 real FP64 flops per n x n Hermitian tridiagonalisation" if dominant == 8
-                        else "8 n^2 r FP64 flops per back-transformation",
-                "peak_source": "FP64 FMA-chain probe on this GB300 (1.25 TFLOP/s, equal to the nominal rate)",
-                "avg_launch_us": avg_launch_s * 1e6, "launches": dom_launches}
-    elif flops_recon > 0:
-        per_launch = flops_recon * args.steps / max(dom_launches, 1)
-        achieved = per_launch / avg_launch_s / 1e12
-        roof = {"kernel": KERNEL_NAMES[dominant], "bound": "alu", "achieved": achieved,
-                "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
-                "peak_source": "FP32 CUDA-core peak derived from 152 SMs x 128 lanes x 2 x max SM clock",
-                "avg_launch_us": avg_launch_s * 1e6, "launches": dom_launches}
-    else:
-        fp64_peak = FP64_PEAK_TFLOPS
-        roof = {"kernel": KERNEL_NAMES[dominant], "bound": "alu", "achieved": None, "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": None, "traffic": None,
-                "peak_source": "nominal FP64 rate of GB300",
-                "avg_launch_us": avg_launch_s * 1e6, "launches": dom_launches}
-    bf16_peak = peaks.get("bf16_tflops", 1855.5)
-    extra_roofs = {}
-    for c in (6, 7, 2, 3):
-        ms_c, nl_c = launches_per_class.get(c, (0.0, 0))
-        if nl_c == 0:
-            continue
-        fl = algorithmic_flops(pb, c)
-        ach = fl / (ms_c / 1e3) / 1e12
-        if c in (6, 7):
-            extra_roofs[KERNEL_NAMES[c]] = {
-                "bound": "tensor", "achieved": ach, "peak": bf16_peak, "unit": "TFLOP/s",
-                "frac": ach / bf16_peak, "traffic": None,
-                "note": "algorithmic 8 n p s flops; the split-bf16 form issues 4x that on the tensor "
-                        "pipe (hi and lo of the input against [B_hi | B_lo]); timed with events over one "
-                        "warm-up reconstruction",
-                "avg_launch_us": ms_c * 1e3 / nl_c, "launches": nl_c}
-        else:
-            extra_roofs[KERNEL_NAMES[c]] = {
-                "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": None, "avg_launch_us": ms_c * 1e3 / nl_c,
-                "launches": nl_c}
+    roof = roofline_block(pb, wname, dominant, dom_ms, dom_launches, eig_sweeps, args.steps, peaks, peak_src)
+    roof["timed_pass_ms_per_step"] = roof_total_ms / args.steps
+    extra_roofs = kernel_rooflines(pb, wname, per_class, peaks)
     config = workload_config(wname, pb)
     config.update({"l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"})
     line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -738,17 +844,21 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": all_launches,
             "roofline": roof,
-            "class_ms_per_step": {KERNEL_NAMES[c]: round(v, 3) for c, v in per_class.items()},
+            "class_ms_per_step": {KERNEL_NAMES[c]: round(v[0], 3) for c, v in per_class.items()},
+            "class_launches_per_step": {KERNEL_NAMES[c]: v[1] for c, v in per_class.items()},
             "kernel_rooflines": extra_roofs,
             "plain_fp32": None if fp32_ms is None else {
-                "value": fp32_value, "unit": UNIT,
-                "ms_per_step": fp32_ms / args.steps},
+                "value": fp32_value, "unit": UNIT, "ms_per_step": fp32_ms / fp32_steps, "steps": fp32_steps,
+                "speedup_of_split_bf16": value / fp32_value},
             "clocks": clocks,
             "peaks_source": peak_src}
+    if world == 1:
+        line["accuracy"] = accuracy_block(args, pb, hicu, h, geom, x_main if args.prec == "bf16" else None,
+                                          x_fp32)
     if world == 1 and not args.no_cpu_baseline:
         v, _, desc = oracle_sample(pb)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-                                "sample": desc}
+                                "sample": desc, "extrapolated": True}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
