@@ -245,6 +245,166 @@ __global__ void gram_rows_kernel(GramParams P, float4* __restrict__ part) {
   }
 }
 
+// Lag-row form for regions up to 128 positions wide and kernels up to 5 wide in x and y: a CTA per
+// (coil pair, y lag, z lag, z piece) and a thread per x position forms the products of one sample
+// of coil c1 with the 2 kx - 1 samples of coil c2 at all x lags, so every loaded sample feeds
+// 2 kx - 1 products and the row and index arithmetic is shared by them.  The y cells are split
+// between two kinds of CTA (blockIdx.z): kind 0 sums the interior y cell, its rows spread over the
+// CTA's row groups; kind 1 sums the single-row border cells, one row at a time per row group.  So
+// every accumulator lives in registers for the whole CTA; the cells of x and the row groups are
+// summed once at the end through shared memory.  The partial sums go to the same layout as
+// gram_rows_kernel (y pieces = y cells), read by gram_assemble_kernel.
+struct LagRowParams {
+  int xw, rgroups;       // threads per row (= ex), row groups (blockDim = xw * rgroups rounded up to 32)
+  int ly, nyz, cyz;      // y lags, y-z lags, centre y-z lag
+  int y_lo, y_hi;        // interior y cell [y_lo, y_hi) (all rows for a circular y axis)
+  int cy_int;            // its y cell index
+  int nb;                // border rows (single-row y cells)
+  int brow[2 * GMAXCUT]; // their rows
+  int bcell[2 * GMAXCUT];// and y cell indices
+};
+
+__host__ __device__ inline void decode_task9(long long t, int C, int nyz, int cyz, int& c1, int& c2, int& lyz) {
+  for (c1 = 0; c1 < C; ++c1) {
+    const long long sz = (nyz - cyz) + (long long)(C - 1 - c1) * nyz;
+    if (t < sz) break;
+    t -= sz;
+  }
+  if (t < nyz - cyz) {
+    c2 = c1;
+    lyz = cyz + (int)t;
+  } else {
+    t -= nyz - cyz;
+    c2 = c1 + 1 + (int)(t / nyz);
+    lyz = (int)(t % nyz);
+  }
+}
+
+template <int LX>
+__global__ void __launch_bounds__(256) gram_lagrow_kernel(GramParams P, LagRowParams Q, float4* __restrict__ part) {
+  pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
+  pdl_trigger();
+  extern __shared__ float4 red[];  // kind 0: [rgroups][LX][xw]; kind 1: [nb][LX][xw]
+  const ConvGeom& g = P.g;
+  const int kind = blockIdx.z;
+  if (kind == 1 && Q.nb == 0) return;
+  int c1, c2, lyz;
+  decode_task9(blockIdx.x, g.C, Q.nyz, Q.cyz, c1, c2, lyz);
+  const int pzi = blockIdx.y;
+  const int ddy = lyz % Q.ly - (g.ky - 1);
+  const int ddz = lyz / Q.ly - (g.kz - 1);
+  const int x = threadIdx.x % Q.xw, rg = threadIdx.x / Q.xw;
+  const bool active = rg < Q.rgroups;   // the block is rounded up to whole warps
+  const float2* xa = P.x.p + (long long)c1 * P.x.sc + P.x.ox;
+  const float2* xb = P.x.p + (long long)c2 * P.x.sc + P.x.ox;
+  // x lags: the sample of coil c2 at x + j - (kx - 1).  A lag that leaves a non-circular region
+  // reads a clamped sample instead: every cell that ends up in a Gram entry for lag j has all its
+  // x + j - (kx - 1) inside the region, so those products only reach cells no entry reads.
+  int bx[LX];
+#pragma unroll
+  for (int j = 0; j < LX; ++j) {
+    int vx = x + j - (g.kx - 1);
+    if (g.cx) vx = wrap(vx, g.ex);
+    else vx = min(max(vx, 0), g.ex - 1);
+    bx[j] = vx;
+  }
+  float rh[LX], rl[LX], ih[LX], il[LX];
+  auto zero = [&]() {
+#pragma unroll
+    for (int j = 0; j < LX; ++j) rh[j] = rl[j] = ih[j] = il[j] = 0.f;
+  };
+  // one row pair: a = x_c1[z][y][x], b_j = x_c2[z + ddz][vy][x + j - (kx - 1)]
+  auto row = [&](int z, int vz, int y, int vy) {
+    const float2* ar = xa + (long long)(P.x.oz + z) * P.x.sz + (long long)(P.x.oy + y) * P.x.sy;
+    const float2* br = xb + (long long)(P.x.oz + vz) * P.x.sz + (long long)(P.x.oy + vy) * P.x.sy;
+    const float2 a = __ldg(ar + x);
+    float2 b[LX];
+#pragma unroll
+    for (int j = 0; j < LX; ++j) b[j] = __ldg(br + bx[j]);
+#pragma unroll
+    for (int j = 0; j < LX; ++j) {
+      // conj(a) * b = (ar br + ai bi) + i (ar bi - ai br)
+      dd_acc(a.x, b[j].x, rh[j], rl[j]);
+      dd_acc(a.y, b[j].y, rh[j], rl[j]);
+      dd_acc(a.x, b[j].y, ih[j], il[j]);
+      dd_acc(-a.y, b[j].x, ih[j], il[j]);
+      dd_renorm(rh[j], rl[j]);
+      dd_renorm(ih[j], il[j]);
+    }
+  };
+  auto shifted = [&](int v, int e, bool circ, int& out) -> bool {
+    if (circ) { out = wrap(v, e); return true; }
+    out = v;
+    return v >= 0 && v < e;
+  };
+  const int z0 = P.pz0[pzi], z1 = P.pz1[pzi];
+  if (!active) {
+    // idle tail of the last warp: nothing to sum
+  } else if (kind == 0) {
+    zero();
+    for (int z = z0; z < z1; ++z) {
+      int vz;
+      if (!shifted(z + ddz, g.ez, g.cz, vz)) continue;
+      for (int y = Q.y_lo + rg; y < Q.y_hi; y += Q.rgroups) {
+        int vy;
+        if (!shifted(y + ddy, g.ey, g.cy, vy)) continue;
+        row(z, vz, y, vy);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < LX; ++j) red[(rg * LX + j) * Q.xw + x] = make_float4(rh[j], rl[j], ih[j], il[j]);
+  } else {
+    for (int b = rg; b < Q.nb; b += Q.rgroups) {
+      zero();
+      const int y = Q.brow[b];
+      int vy;
+      if (shifted(y + ddy, g.ey, g.cy, vy)) {
+        for (int z = z0; z < z1; ++z) {
+          int vz;
+          if (!shifted(z + ddz, g.ez, g.cz, vz)) continue;
+          row(z, vz, y, vy);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < LX; ++j) red[(b * LX + j) * Q.xw + x] = make_float4(rh[j], rl[j], ih[j], il[j]);
+    }
+  }
+  __syncthreads();
+  // cells of x (and the row groups of kind 0): one warp per (set, lag).  Single-position cells
+  // (the border columns) are copied lane by lane; only the wide cells take a warp reduction.
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nsets = kind == 0 ? 1 : Q.nb;
+  const int npieces = P.npy * P.npz;
+  const bool diag_centre = (c1 == c2) && (lyz == Q.cyz);
+  const int nsum = kind == 0 ? Q.rgroups : 1;
+  for (int item = warp; item < nsets * LX; item += nw) {
+    const int set = item / LX, j = item % LX;
+    if (diag_centre && j < g.kx - 1) continue;   // lag with delta x < 0: its conjugate is stored
+    const int l = j + (2 * g.kx - 1) * lyz;
+    const long long task = task_index(c1, c2, l, g.C, P.nl, P.nlh, P.center);
+    const int cy = kind == 0 ? Q.cy_int : Q.bcell[set];
+    float4* out = part + (task * npieces + (long long)pzi * P.npy + cy) * P.ncx;
+    const float4* src = red + (size_t)((kind == 0 ? 0 : set) * LX + j) * Q.xw;
+    const size_t gstride = (size_t)LX * Q.xw;   // between row groups (kind 0)
+    for (int ci = lane; ci < P.ncx; ci += 32) {
+      const int x0 = P.cutx[ci];
+      if (P.cutx[ci + 1] - x0 != 1) continue;
+      cdf acc = ld4(&src[x0]);
+      for (int r = 1; r < nsum; ++r) acc = c_add(acc, ld4(&src[r * gstride + x0]));
+      st4(&out[ci], acc);
+    }
+    for (int ci = 0; ci < P.ncx; ++ci) {
+      const int x0 = P.cutx[ci], x1 = P.cutx[ci + 1];
+      if (x1 - x0 == 1) continue;
+      cdf acc = c_zero();
+      for (int xx = x0 + lane; xx < x1; xx += 32)
+        for (int r = 0; r < nsum; ++r) acc = c_add(acc, ld4(&src[r * gstride + xx]));
+      acc = c_warp_sum(acc);
+      if (lane == 0) st4(&out[ci], acc);
+    }
+  }
+}
+
 __device__ __forceinline__ int cut_index(const int* cuts, int ncut, int v) {
   for (int i = 0; i < ncut; ++i)
     if (cuts[i] == v) return i;
@@ -374,9 +534,63 @@ hicu_status run_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* r
       P.pyc[c] = c;
     }
   }
+  // lag-row form: every x lag of a (coil pair, y lag, z lag) task in one thread (kx, ky <= 5,
+  // ex <= 128); the interior y cell and the single-row border cells of y go to two kinds of CTA
+  LagRowParams Q;
+  bool lagrow = rows_form && g.kx <= 5 && g.ky <= 5 && g.ex <= 128;
+  if (lagrow) {
+    Q.xw = g.ex;
+    Q.rgroups = std::max(1, 256 / g.ex);
+    Q.ly = P.ly;
+    Q.nyz = P.ly * P.lz;
+    Q.cyz = (Q.nyz - 1) / 2;
+    int big = 0;
+    for (int c = 0; c < P.ncy; ++c)
+      if (P.cuty[c + 1] - P.cuty[c] > P.cuty[big + 1] - P.cuty[big]) big = c;
+    Q.y_lo = P.cuty[big];
+    Q.y_hi = P.cuty[big + 1];
+    Q.cy_int = big;
+    Q.nb = 0;
+    for (int c = 0; c < P.ncy && lagrow; ++c) {
+      if (c == big) continue;
+      if (P.cuty[c + 1] - P.cuty[c] != 1 || Q.nb >= 2 * GMAXCUT) {
+        lagrow = false;  // more than one multi-row y cell: the row-streaming form
+        break;
+      }
+      Q.brow[Q.nb] = P.cuty[c];
+      Q.bcell[Q.nb] = c;
+      ++Q.nb;
+    }
+    if (sizeof(float4) * (size_t)std::max(Q.nb, Q.rgroups) * (2 * g.kx - 1) * Q.xw > 200 * 1024) lagrow = false;
+  }
   const int npieces = P.npy * P.npz;
   float4* part = (float4*)ws_get(h, WS_GRAM_PART, sizeof(float4) * ntasks * npieces * P.ncx, &s);
   if (s) return s;
+  if (lagrow) {
+    const int LX = 2 * g.kx - 1;
+    const long long ntask9 = (long long)g.C * (Q.nyz - Q.cyz) + (long long)Q.nyz * ((long long)g.C * (g.C - 1) / 2);
+    const size_t smem = sizeof(float4) * (size_t)std::max(Q.nb, Q.rgroups) * LX * Q.xw;
+    const int nt = (Q.xw * Q.rgroups + 31) / 32 * 32;
+    const dim3 grid((unsigned)ntask9, (unsigned)P.npz, Q.nb > 0 ? 2u : 1u);
+    const void* fn = LX == 9 ? (const void*)gram_lagrow_kernel<9> : LX == 7 ? (const void*)gram_lagrow_kernel<7>
+                   : LX == 5 ? (const void*)gram_lagrow_kernel<5> : LX == 3 ? (const void*)gram_lagrow_kernel<3>
+                   : (const void*)gram_lagrow_kernel<1>;
+    const cudaError_t e0 = allow_max_dynamic_smem(fn);
+    if (e0 != cudaSuccess) return cuda_error(h, e0, "gram smem");
+    switch (LX) {
+      case 9: launch_pdl(h, K_GRAM, st, grid, dim3(nt), smem, gram_lagrow_kernel<9>, false, P, Q, part); break;
+      case 7: launch_pdl(h, K_GRAM, st, grid, dim3(nt), smem, gram_lagrow_kernel<7>, false, P, Q, part); break;
+      case 5: launch_pdl(h, K_GRAM, st, grid, dim3(nt), smem, gram_lagrow_kernel<5>, false, P, Q, part); break;
+      case 3: launch_pdl(h, K_GRAM, st, grid, dim3(nt), smem, gram_lagrow_kernel<3>, false, P, Q, part); break;
+      default: launch_pdl(h, K_GRAM, st, grid, dim3(nt), smem, gram_lagrow_kernel<1>, false, P, Q, part); break;
+    }
+    s = cuda_error(h, cudaGetLastError(), "gram_lagrow");
+    if (s) return s;
+    const long long nn = (long long)g.n * g.n;
+    launch_pdl(h, K_GRAM, st, dim3((unsigned)((nn + 255) / 256)), dim3(256), 0, gram_assemble_kernel, false, P,
+               (const float4*)part, (double2*)G);
+    return cuda_error(h, cudaGetLastError(), "gram_assemble");
+  }
   // stream-ordered (allow = false): as programmatic dependents, CTAs waiting beside the running
   // kernel slowed the Gram by 4-8 % on GB300
   if (rows_form) {

@@ -118,11 +118,23 @@ def test_gd_step_filters_parity(H, name):
     np.testing.assert_array_equal(y1[:, ~inside], x[:, ~inside])         # outside S untouched
 
 
+# Gram cases for each form: lag-row (every x lag in one thread; kx, ky <= 5 and regions up to 128
+# wide, x-lag counts 1, 5, 7, 9, a circular y axis with one y cell), row-streaming (129 .. 256
+# wide) and cells (wider)
+CASES["gram_w128_k5x3"] = ((128, 20, 1), 3, (5, 3, 1), (0, 0, 0), ((0, 2, 0), (128, 17, 1)), 2)
+CASES["gram_w200_rows"] = ((200, 12, 1), 2, (3, 3, 1), (0, 0, 0), ((0, 0, 0), (200, 12, 1)), 2)
+CASES["gram_k1x_3d"] = ((10, 12, 9), 2, (1, 3, 3), (0, 0, 0), ((1, 1, 1), (8, 11, 8)), 2)
+CASES["gram_k4x_2d"] = ((30, 20, 1), 3, (4, 2, 1), (0, 0, 0), ((1, 0, 0), (29, 20, 1)), 2)
+CASES["gram_circ_y_3d"] = ((20, 16, 6), 2, (3, 3, 3), (0, 1, 0), ((0, 0, 0), (20, 16, 6)), 2)
+
+
 @pytest.mark.parametrize("name", ["2d_64_c4_p4", "2d_odd_region", "3d_region", "cine_circular_t",
                                   "2d_c16_p20", "tiny_one_output", "2d_wide_two_x_tiles", "3d_c8_k5_region",
-                                  "cine_c8_k5_circular_t"])
+                                  "cine_c8_k5_circular_t", "gram_w128_k5x3", "gram_w200_rows", "gram_k1x_3d",
+                                  "gram_k4x_2d", "gram_circ_y_3d"])
 def test_gram_parity(H, name):
-    """Regions up to 256 positions wide run the row-streaming kernel, the 300-wide one the cell kernel."""
+    """Regions up to 128 positions wide with kx, ky <= 5 run the lag-row kernel, up to 256 the
+    row-streaming kernel, wider ones the cell kernel."""
     from paper_2004_08962_gb300 import hicu
     og, oreg, hg, hr, x, f, mask, p, _ = setup(name, seed=3)
     G = hicu.hicu_gram(H, hg, hr, cuda(x)).cpu().numpy()
