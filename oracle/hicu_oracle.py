@@ -42,13 +42,46 @@ import numpy as np
 class Geom:
     dims: Tuple[int, int, int]          # (Nx, Ny, Nz)
     ncoil: int
-    kernel: Tuple[int, int, int]        # (kx, ky, kz)
+    kernel: Tuple[int, int, int]        # (kx, ky, kz): the box that holds the kernel mask
     circular: Tuple[int, int, int] = (0, 0, 0)
+    # kernel mask K (Algorithm 1 input; Theory: v lists the kernel values on the support of K):
+    # the offsets (dz, dy, dx) of the support in scan order, or None for the whole box
+    support: Optional[Tuple[Tuple[int, int, int], ...]] = None
+
+    @property
+    def nk(self) -> int:
+        """|K|, the number of kernel offsets per coil."""
+        kx, ky, kz = self.kernel
+        return len(self.support) if self.support is not None else kx * ky * kz
 
     @property
     def n(self) -> int:
-        kx, ky, kz = self.kernel
-        return self.ncoil * kx * ky * kz
+        return self.ncoil * self.nk
+
+
+def ellipsoid_support(kernel: Tuple[int, int, int], radius: float) -> Tuple[Tuple[int, int, int], ...]:
+    """Circular (2D) or spherical (3D) kernel mask inside the box `kernel` (Discussion: circumscribing
+    circular or spherical kernel masks): the offsets d with sum_a (d_a - c_a)^2 <= radius^2 over the
+    axes with k_a > 1, c_a = (k_a - 1) / 2 the box centre.  Offsets in (dz, dy, dx) scan order."""
+    kx, ky, kz = kernel
+    cx, cy, cz = (kx - 1) / 2.0, (ky - 1) / 2.0, (kz - 1) / 2.0
+    out = []
+    for dz in range(kz):
+        for dy in range(ky):
+            for dx in range(kx):
+                r2 = (dx - cx) ** 2 + (dy - cy) ** 2 + (dz - cz) ** 2
+                if r2 <= radius * radius + 1e-9:
+                    out.append((dz, dy, dx))
+    return tuple(out)
+
+
+def support_mask(geom: Geom) -> np.ndarray:
+    """The kernel mask K as a {0,1} array [kz][ky][kx]."""
+    kx, ky, kz = geom.kernel
+    m = np.zeros((kz, ky, kx), dtype=np.uint8)
+    for dz, dy, dx in _offsets(geom):
+        m[dz, dy, dx] = 1
+    return m
 
 
 @dataclass(frozen=True)
@@ -100,6 +133,10 @@ def _shifted_block(x: np.ndarray, geom: Geom, reg: Region, dz: int, dy: int, dx:
 
 
 def _offsets(geom: Geom):
+    """The kernel offsets (dz, dy, dx) on the support of K, in scan order (dx fastest)."""
+    if geom.support is not None:
+        yield from geom.support
+        return
     kx, ky, kz = geom.kernel
     for dz in range(kz):
         for dy in range(ky):
@@ -122,15 +159,15 @@ def _check(x: np.ndarray, geom: Geom, reg: Region):
 def hankel_matrix(x: np.ndarray, geom: Geom, reg: Region) -> np.ndarray:
     """Explicit m-by-n multi-level Hankel matrix H(x) on region S (Theory section).
 
-    Row order: valid outputs (z, y, x) with x fastest.  Column order: (c, dz, dy, dx).
-    Only for small inputs (it is the object HICU never forms).
+    Row order: valid outputs (z, y, x) with x fastest.  Column order: (c, kernel offset) with the
+    offsets of the support of K in scan order (dz, dy, dx).  Only for small inputs (it is the object
+    HICU never forms).
     """
     _check(x, geom, reg)
     s = num_outputs(geom, reg)
-    kx, ky, kz = geom.kernel
-    cols = np.empty((geom.ncoil, kz, ky, kx, s), dtype=np.complex128)
-    for dz, dy, dx in _offsets(geom):
-        cols[:, dz, dy, dx, :] = _shifted_block(x, geom, reg, dz, dy, dx).reshape(geom.ncoil, s)
+    cols = np.empty((geom.ncoil, geom.nk, s), dtype=np.complex128)
+    for j, (dz, dy, dx) in enumerate(_offsets(geom)):
+        cols[:, j, :] = _shifted_block(x, geom, reg, dz, dy, dx).reshape(geom.ncoil, s)
     return cols.reshape(geom.n, s).T.copy()
 
 
@@ -204,6 +241,8 @@ def conv_null_at(x: np.ndarray, geom: Geom, reg: Region, filters: np.ndarray, ou
     _check(x, geom, reg)
     x = np.asarray(x, dtype=np.complex128)
     f = np.asarray(filters, dtype=np.complex128)
+    if geom.support is not None:
+        f = f * support_mask(geom)[None, None]   # the kernel lives on the support of K
     outs = np.asarray(outs, dtype=np.int64).reshape(-1, 3)
     kx, ky, kz = geom.kernel
     idx = []
@@ -297,12 +336,11 @@ def gram(x: np.ndarray, geom: Geom, reg: Region, chunk: int = 1 << 15) -> np.nda
 
 def _hankel_rows(x, geom, reg, z0, z1):
     sz, sy, sx = out_shape(geom, reg)
-    kx, ky, kz = geom.kernel
     rows = (z1 - z0) * sy * sx
-    cols = np.empty((geom.ncoil, kz, ky, kx, rows), dtype=np.complex128)
-    for dz, dy, dx in _offsets(geom):
+    cols = np.empty((geom.ncoil, geom.nk, rows), dtype=np.complex128)
+    for j, (dz, dy, dx) in enumerate(_offsets(geom)):
         blk = _shifted_block(x, geom, reg, dz, dy, dx)[:, z0:z1]
-        cols[:, dz, dy, dx, :] = blk.reshape(geom.ncoil, rows)
+        cols[:, j, :] = blk.reshape(geom.ncoil, rows)
     return cols.reshape(geom.n, rows).T
 
 
@@ -390,8 +428,17 @@ def jl_compress(Q: np.ndarray, P: np.ndarray, mode: str = "nullspace") -> np.nda
 
 
 def as_filters(Qt_pn: np.ndarray, geom: Geom) -> np.ndarray:
+    """p filters of length n (coil, then the support offsets) as arrays (p, C, kz, ky, kx) over the
+    kernel's box, zero outside the support of K."""
     kx, ky, kz = geom.kernel
-    return Qt_pn.reshape(Qt_pn.shape[0], geom.ncoil, kz, ky, kx)
+    p = Qt_pn.shape[0]
+    if geom.support is None:
+        return Qt_pn.reshape(p, geom.ncoil, kz, ky, kx)
+    out = np.zeros((p, geom.ncoil, kz, ky, kx), dtype=Qt_pn.dtype)
+    v = Qt_pn.reshape(p, geom.ncoil, geom.nk)
+    for j, (dz, dy, dx) in enumerate(geom.support):
+        out[:, :, dz, dy, dx] = v[:, :, j]
+    return out
 
 
 # ------------------------------------------------------------ gradient step + ELS

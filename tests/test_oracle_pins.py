@@ -533,3 +533,103 @@ def test_reconstruct_stage_transition_uses_previous_region():
     O.reconstruct(x0, mask, geom, [st1, st2], r, seed=3, gram_on="current", log=log_c)
     assert abs(log_c.J[2] - J_eq1(xs[2], S2)) <= 1e-9 * scale
     assert abs(log_c.J[2] - log.J[2]) > 1e-3 * scale
+
+
+# ------------------------------------------------------------ kernel masks (Discussion)
+
+
+def brute_hankel_support(x, geom, reg, kmask):
+    """Row-by-row H_K(x) for a {0,1} kernel mask kmask [kz][ky][kx]: only the columns (c, d) with
+    d on the support, by explicit loops (independent of the oracle)."""
+    full = brute_hankel(x, O.Geom(geom.dims, geom.ncoil, geom.kernel, geom.circular), reg)
+    kx, ky, kz = geom.kernel
+    keep = [c * kx * ky * kz + (dz * ky + dy) * kx + dx
+            for c in range(geom.ncoil) for dz in range(kz) for dy in range(ky) for dx in range(kx)
+            if kmask[dz, dy, dx]]
+    return full[:, keep]
+
+
+MASK_CASES = [
+    # dims, C, kernel, circular, region, radius
+    ((9, 8, 1), 2, (5, 5, 1), (0, 0, 0), ((0, 0, 0), (9, 8, 1)), 2.0),     # 13-point disc
+    ((9, 9, 1), 2, (5, 5, 1), (0, 0, 0), ((1, 0, 0), (8, 9, 1)), 2.5),     # 21 points (corners cut)
+    ((7, 6, 6), 2, (3, 3, 3), (0, 0, 1), ((0, 0, 0), (7, 6, 6)), 1.0),     # 7-point 3D cross, circular z
+]
+
+
+def test_ellipsoid_support_counts():
+    assert len(O.ellipsoid_support((5, 5, 1), 2.0)) == 13
+    assert len(O.ellipsoid_support((5, 5, 1), 2.5)) == 21
+    assert len(O.ellipsoid_support((3, 3, 3), 1.0)) == 7
+    assert len(O.ellipsoid_support((5, 5, 5), 2.0)) == 33
+    # a radius reaching the corners gives the whole box, in scan order
+    box = O.ellipsoid_support((3, 4, 2), 10.0)
+    assert box == tuple((z, y, x) for z in range(2) for y in range(4) for x in range(3))
+
+
+@pytest.mark.parametrize("i", range(len(MASK_CASES)))
+def test_masked_hankel_gram_and_conv_match_brute_force(i):
+    dims, C, ker, circ, (off, ext), rad = MASK_CASES[i]
+    sup = O.ellipsoid_support(ker, rad)
+    geom = O.Geom(dims, C, ker, circ, sup)
+    reg = O.Region(off, ext)
+    rng = np.random.default_rng(40 + i)
+    x = random_complex(rng, (C, dims[2], dims[1], dims[0]))
+    kmask = O.support_mask(geom)
+    assert kmask.sum() == len(sup) and geom.n == C * len(sup)
+    Hb = brute_hankel_support(x, geom, reg, kmask)
+    np.testing.assert_allclose(O.hankel_matrix(x, geom, reg), Hb, atol=0)
+    np.testing.assert_allclose(O.gram(x, geom, reg), Hb.conj().T @ Hb, rtol=1e-13, atol=1e-12)
+    # H_K(x) v = valid convolution with the kernel that is v on the support and zero elsewhere
+    v = random_complex(rng, (3, geom.n))
+    R = O.conv_null(x, geom, reg, O.as_filters(v, geom))
+    np.testing.assert_allclose(R.reshape(-1, 3), Hb @ v.T, rtol=1e-12, atol=1e-12)
+    outs = np.array([[0, 0, 0], [O.out_shape(geom, reg)[0] - 1, 1, 2]])
+    sz, sy, sx = O.out_shape(geom, reg)
+    rows = outs[:, 0] * sy * sx + outs[:, 1] * sx + outs[:, 2]
+    np.testing.assert_allclose(O.conv_null_at(x, geom, reg, O.as_filters(v, geom), outs), (Hb @ v.T)[rows],
+                               rtol=1e-12, atol=1e-12)
+    # adjoint identity in x and in the filters, with masked filters
+    Rr = random_complex(rng, R.shape)
+    g = O.conv_null_adjoint(Rr, geom, reg, O.as_filters(v, geom))
+    assert abs(np.vdot(R, Rr) - np.vdot(x, g)) < 1e-10 * np.abs(R).sum()
+    F = O.filter_gradient(x, geom, reg, Rr)
+    off_support = np.broadcast_to(kmask == 0, F.shape[2:])
+    assert np.all(F[:, :, off_support] == 0)
+    # Eq. 1 on the masked Hankel matrix: the tail energy of the masked Gram's eigenvalues
+    r = geom.n // 3
+    Q, w = O.nullspace(O.gram(x, geom, reg), r)
+    sv = np.linalg.svd(Hb, compute_uv=False)
+    assert abs(O.tail_energy(w, r) - np.sum(sv[r:] ** 2)) < 1e-10 * sv[0] ** 2
+
+
+def test_full_box_support_equals_rectangular_kernel():
+    geom_box = O.Geom((8, 7, 1), 2, (3, 3, 1))
+    geom_sup = O.Geom((8, 7, 1), 2, (3, 3, 1), (0, 0, 0), O.ellipsoid_support((3, 3, 1), 5.0))
+    rng = np.random.default_rng(3)
+    x = random_complex(rng, (2, 1, 7, 8))
+    reg = O.full_region(geom_box)
+    np.testing.assert_array_equal(O.gram(x, geom_sup, reg), O.gram(x, geom_box, reg))
+
+
+def test_masked_kernel_annihilates_exactly_low_rank_kspace_and_reconstructs():
+    """Sums of L exponentials have rank <= L Hankel matrices for any kernel support, so a disc mask
+    also annihilates them exactly.  The iteration drives J (Eq. 1) on the masked Hankel matrix to
+    zero with the observed samples untouched, and where the masked completion is determined by the
+    samples (80 % here; a smaller support needs more of them than the full box) it recovers the
+    unobserved ones."""
+    rng = np.random.default_rng(8)
+    L = 3
+    x_true = lowrank_exponential_kspace(rng, (1, 14, 15), 2, L)
+    geom = O.Geom((15, 14, 1), 2, (5, 5, 1), (0, 0, 0), O.ellipsoid_support((5, 5, 1), 2.0))
+    reg = O.full_region(geom)
+    w = np.linalg.eigvalsh(O.gram(x_true, geom, reg))
+    assert w[: geom.n - L].max() < 1e-11 * w[-1]
+    mask = (rng.random((1, 14, 15)) < 0.8).astype(np.uint8)
+    x0 = x_true * mask[None]
+    log = O.ReconLog([], [], [])
+    xr = O.reconstruct(x0, mask, geom, [O.StageSpec(reg, iters=30, gd_steps=5, p=6)], r=L, seed=2, log=log)
+    assert abs(log.J[-1]) < 1e-9 * log.J[0]
+    m4 = np.broadcast_to(mask[None], x0.shape).astype(bool)
+    np.testing.assert_array_equal(xr[m4], x0[m4])
+    assert O.ser_db(x_true, xr) > O.ser_db(x_true, x0) + 60.0
