@@ -126,6 +126,11 @@ typedef struct {
                                 HICU_NULLSPACE_GRID or HICU_NULLSPACE_CLUSTER force
                                 Jacobi (see hicu_nullspace); HICU_NULLSPACE_TRIDIAG
                                 needs jl = HICU_JL_PROJECTOR */
+  const uint8_t* kernel_mask;/* kernel mask K: HOST array [kz][ky][kx] of the box geom.k,
+                                nonzero = in the support (Algorithm 1 input; Discussion:
+                                circular or spherical masks); NULL = the whole box.  The
+                                null space then has n = C |K| coefficients (see
+                                hicu_gram_support) */
 } hicu_params;
 
 /* Optional per-iteration log, HOST arrays (any may be NULL). */
@@ -194,6 +199,40 @@ hicu_status hicu_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* 
 #define HICU_NULLSPACE_CLUSTER_AUTO_MAX 128
 /* hicu_params.eig_solver only: principal subspace by tridiagonalisation (hicu_principal_subspace) */
 #define HICU_NULLSPACE_TRIDIAG 16
+
+/*
+ * Kernel masks.  Algorithm 1 takes a {0,1} kernel mask K; a filter v lists the kernel values on
+ * its support (Theory section), so n = C |K| coefficients ordered [c][support offset], the
+ * offsets of the support in scan order of the box [kz][ky][kx] (dx fastest).  The Gram matrix,
+ * null space and JL filters of a masked problem are of that length; the convolution calls take
+ * filters in the box layout, zero off the support (hicu_expand_filters).  A mask is a HOST array
+ * [kz][ky][kx] of uint8 (nonzero = in the support) over the box geom.k; the handle keeps its index
+ * maps and uploads them again only when the mask changes.
+ */
+
+/* C |K| for the kernel mask, or -1 for an invalid geometry or an empty mask (host only). */
+int64_t hicu_support_length(const hicu_geom* geom, const uint8_t* kmask);
+
+/*
+ * hicu_gram_support - G = H_K(x)^H H_K(x) for the masked Hankel matrix (columns (c, d) with d on
+ * the support of K; Eq. 1 then holds for H_K).  The same cross-correlation sums as hicu_gram;
+ * only the support's rows and columns are assembled.
+ *   kmask : HOST [kz][ky][kx] kernel mask;  x : complex64 k-space (device)
+ *   G     : complex128 (C |K|) x (C |K|) row-major (device)
+ * HICU_ERR_SHAPE for an empty mask.
+ */
+hicu_status hicu_gram_support(hicu_handle* h, const hicu_geom* geom, const hicu_region* region,
+                              const uint8_t* kmask, const float* x, double* G, void* stream);
+
+/*
+ * hicu_expand_filters - bank_box[k][c][kz][ky][kx] = the coefficient of offset (kz, ky, kx) of
+ * bank_sup[k][c][.] on the support of K, zero off the support: filters on a kernel mask in the
+ * layout of the convolution calls.
+ *   kmask    : HOST [kz][ky][kx] kernel mask
+ *   bank_sup : complex64 [p][C |K|] (device);  bank_box : complex64 [p][C kz ky kx] (device)
+ */
+hicu_status hicu_expand_filters(hicu_handle* h, const hicu_geom* geom, const uint8_t* kmask,
+                                const float* bank_sup, int32_t p, float* bank_box, void* stream);
 
 /*
  * hicu_nullspace - eigen-decomposition of the Hermitian n x n matrix G and the
@@ -368,7 +407,10 @@ hicu_status hicu_gd_step(hicu_handle* h, const hicu_geom* geom, const hicu_regio
  * hicu_reconstruct - Algorithm 1 with centre-out stages: for every outer
  * iteration the Gram matrix and null space (hicu_gram, hicu_nullspace; region
  * chosen by params->gram_on_current), then G^(i) calls of hicu_gd_step with
- * JL counter = global step index (0, 1, 2, ...).
+ * JL counter = global step index (0, 1, 2, ...).  With params->kernel_mask the
+ * Gram, null space and JL draws are over the C |K| coefficients of the mask's
+ * support (hicu_gram_support) and each filter bank is placed in the box
+ * (hicu_expand_filters) for the convolutions.
  *   x0, mask, x_out may be HOST or DEVICE pointers (detected per pointer);
  *   host buffers are staged through the handle's workspace with copies on
  *   `stream`, and the call then returns after x_out is written.

@@ -706,7 +706,18 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
   if (!geom || !x0 || !mask || !prm || !x_out) return set_error(h, HICU_ERR_ARG, "reconstruct: null pointer");
   if (!geom_ok(geom)) return set_error(h, HICU_ERR_SHAPE, "reconstruct: invalid geometry");
   if (prm->nstages < 1 || !prm->stages) return set_error(h, HICU_ERR_ARG, "reconstruct: no stages");
-  const int64_t n = hicu_filter_length(geom);
+  cudaStream_t st = (cudaStream_t)stream;
+  // kernel mask: the null space lives on the C |K| coefficients of the support, the convolutions
+  // on the box (n_box) with the bank scattered into it
+  const int64_t n_box = hicu_filter_length(geom);
+  const int* sup = nullptr;
+  const int* inv = nullptr;
+  int nk = 0;
+  if (prm->kernel_mask) {
+    hicu_status sm = support_maps(h, geom, prm->kernel_mask, &sup, &inv, &nk, st);
+    if (sm) return sm;
+  }
+  const int64_t n = prm->kernel_mask ? (int64_t)geom->ncoil * nk : n_box;
   const int64_t r = prm->rank;
   if (r < 1 || r >= n) return set_error(h, HICU_ERR_RANK, "reconstruct: rank must satisfy 0 < r < n");
   const int64_t nr = n - r;
@@ -735,7 +746,6 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
     total_iters += stg.iters;
     total_steps += (long long)stg.iters * stg.gd_steps;
   }
-  cudaStream_t st = (cudaStream_t)stream;
   const long long N = geom->dim[0] * geom->dim[1] * geom->dim[2] * (long long)geom->ncoil;
   const long long NM = geom->dim[0] * geom->dim[1] * geom->dim[2] * (geom->mask_per_coil ? geom->ncoil : 1);
   const bool out_dev = is_device_ptr(x_out);
@@ -769,8 +779,13 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
   if (s) return s;
   int pmax = 1;
   for (int i = 0; i < prm->nstages; ++i) pmax = std::max(pmax, (int)prm->stages[i].p);
-  float* bank = (float*)ws_get(h, WS_BANK, sizeof(float2) * (size_t)pmax * n, &s);
+  float* bank = (float*)ws_get(h, WS_BANK, sizeof(float2) * (size_t)pmax * n_box, &s);
   if (s) return s;
+  float* bank_sup = nullptr;   // JL filters on the support of the kernel mask, before the scatter
+  if (prm->kernel_mask) {
+    bank_sup = (float*)ws_get(h, WS_BANK_SUP, sizeof(float2) * (size_t)pmax * n, &s);
+    if (s) return s;
+  }
   if (prm->init == 1) {
     HICU_LAUNCH(h, K_MISC, st,
                 time_average_kernel<<<1024, 256, 0, st>>>(
@@ -811,7 +826,7 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
           return cuda_error(h, ce, "reconstruct: draw join");
       }
       const hicu_region& greg = prm->gram_on_current ? stg.region : prev;
-      s = run_gram(h, geom, &greg, y, G, st);
+      s = run_gram(h, geom, &greg, y, G, st, sup, nk);
       if (s) return s;
       // after the first outer iteration: warm start, and stop at the top-r / rest split (step 3
       // needs an orthonormal basis of the complement of the r principal vectors, nothing more)
@@ -834,8 +849,12 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
       }
       for (int j = 0; j < stg.gd_steps; ++j) {
         s = launch_jl_converted(h, n, nq, stg.p, Qf, jmode, nullptr, Pall + (size_t)j * prow * stg.p, prm->seed,
-                                counter, bank, st, j > 0);
+                                counter, prm->kernel_mask ? bank_sup : bank, st, j > 0);
         if (s) return s;
+        if (prm->kernel_mask &&
+            (s = launch_support_scatter(h, stg.p, geom->ncoil, geom->k[0] * geom->k[1] * geom->k[2], nk, inv,
+                                        (const float2*)bank_sup, (float2*)bank, st)))
+          return s;
         // the update leaves the split planes of y for the next step of the same region
         s = gd_step_filters(h, geom, &stg.region, y, m, bank, stg.p, dstats + 4 * counter, prm->prec, st,
                             planes_valid, true);

@@ -38,6 +38,8 @@ struct GramParams {
   int py0[GMAXPIECE], py1[GMAXPIECE], pyc[GMAXPIECE];
   int pz0[GMAXPIECE], pz1[GMAXPIECE], pzc[GMAXPIECE];
   int lx, ly, lz, nl, nlh, center;
+  const int* sup;  // kernel mask: box offset of support offset j (nullptr: the whole box)
+  int nk;          // offsets per coil in G's index (|K|, or kx ky kz)
 };
 
 __device__ __forceinline__ void dd_acc(float a, float b, float& hi, float& lo) {
@@ -416,12 +418,12 @@ __global__ void gram_assemble_kernel(GramParams P, const float4* __restrict__ pa
   pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
   pdl_trigger();
   const ConvGeom& g = P.g;
-  const int n = g.n;
+  const int n = g.C * P.nk;   // G over the coefficients of the kernel mask's support
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)n * n) return;
   const int a = (int)(idx / n), b = (int)(idx % n);
-  const int K = g.K;
-  const int c1 = a / K, k1 = a % K, c2 = b / K, k2 = b % K;
+  const int c1 = a / P.nk, c2 = b / P.nk;
+  const int k1 = P.sup ? P.sup[a % P.nk] : a % P.nk, k2 = P.sup ? P.sup[b % P.nk] : b % P.nk;
   const int d1x = k1 % g.kx, d1y = (k1 / g.kx) % g.ky, d1z = k1 / (g.kx * g.ky);
   const int d2x = k2 % g.kx, d2y = (k2 / g.kx) % g.ky, d2z = k2 / (g.kx * g.ky);
   const int l = ((d2z - d1z + g.kz - 1) * P.ly + (d2y - d1y + g.ky - 1)) * P.lx + (d2x - d1x + g.kx - 1);
@@ -500,7 +502,7 @@ static int build_pieces(const int* cuts, int ncell, int* p0, int* p1, int* pc) {
 }
 
 hicu_status run_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* reg, const float* x,
-                     double* G, cudaStream_t st) {
+                     double* G, cudaStream_t st, const int* sup, int nk) {
   ConvGeom g;
   hicu_status s = make_conv_geom(h, geom, reg, &g);
   if (s) return s;
@@ -509,6 +511,8 @@ hicu_status run_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* r
   if (g.ex > 256 * GXSLOT) return set_error(h, HICU_ERR_UNSUPPORTED, "gram: region x extent above 1024");
   GramParams P;
   P.g = g;
+  P.sup = sup;
+  P.nk = sup ? nk : g.K;
   P.x = full_view(geom, reg, const_cast<float*>(x));
   P.ncx = build_cuts(g.ex, g.kx, g.cx, P.cutx);
   P.ncy = build_cuts(g.ey, g.ky, g.cy, P.cuty);
@@ -586,7 +590,7 @@ hicu_status run_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* r
     }
     s = cuda_error(h, cudaGetLastError(), "gram_lagrow");
     if (s) return s;
-    const long long nn = (long long)g.n * g.n;
+    const long long nn = (long long)g.C * P.nk * g.C * P.nk;
     launch_pdl(h, K_GRAM, st, dim3((unsigned)((nn + 255) / 256)), dim3(256), 0, gram_assemble_kernel, false, P,
                (const float4*)part, (double2*)G);
     return cuda_error(h, cudaGetLastError(), "gram_assemble");
@@ -608,7 +612,7 @@ hicu_status run_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* r
   }
   s = cuda_error(h, cudaGetLastError(), "gram_cells");
   if (s) return s;
-  const long long nn = (long long)g.n * g.n;
+  const long long nn = (long long)g.C * P.nk * g.C * P.nk;
   launch_pdl(h, K_GRAM, st, dim3((unsigned)((nn + 255) / 256)), dim3(256), 0, gram_assemble_kernel, false, P,
              (const float4*)part, (double2*)G);
   return cuda_error(h, cudaGetLastError(), "gram_assemble");

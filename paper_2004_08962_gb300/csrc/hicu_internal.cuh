@@ -176,7 +176,7 @@ struct hicu_handle {
   int num_sms = 0;
   bool pdl = true;  // programmatic dependent launches (HICU_PDL=0 turns them off)
   std::string last_error;
-  static constexpr int kSlots = 32;
+  static constexpr int kSlots = 40;
   hicu::Workspace ws[kSlots];
   int* dev_err = nullptr;          // device error word
   unsigned* dev_sync = nullptr;    // grid-barrier words (count, gen)
@@ -209,6 +209,9 @@ struct hicu_handle {
   cudaEvent_t side_join = nullptr;
   cudaEvent_t draw_fork = nullptr;  // JL draws of an outer iteration
   cudaEvent_t draw_join = nullptr;
+  // kernel mask K (support.cu): host copy of the last mask whose maps sit in WS_SUP
+  std::vector<uint8_t> sup_mask;
+  int sup_nk = 0;
   // batch lanes (hicu_reconstruct_batched): one sub-handle and stream each, created on demand
   std::vector<hicu_handle*> lane_h;
   std::vector<cudaStream_t> lane_st;
@@ -250,6 +253,8 @@ enum Slot {
   WS_FGRAD,       // filter-gradient partials per CTA
   WS_EIG_WY,      // principal subspace: compact WY blocks of the back-transformation
   WS_REC_P,       // reconstruct: JL matrices of one outer iteration's descent steps
+  WS_SUP,         // kernel mask maps: support offset -> box offset, box offset -> support offset or -1
+  WS_BANK_SUP,    // reconstruct: filter bank on the support of K [p][C][|K|]
   WS_COUNT
 };
 static_assert(WS_COUNT <= hicu_handle::kSlots, "workspace slots");
@@ -368,8 +373,18 @@ hicu_status gd_step_filters(hicu_handle* h, const hicu_geom* geom, const hicu_re
                             int32_t prec, cudaStream_t st,
                             bool planes_valid = false, bool keep_planes = false);
 
+// sup (device, nk entries): the box offsets of a kernel mask's support; G is then (C nk) x (C nk)
+// over the support's coefficients (nullptr: the whole box)
 hicu_status run_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* reg, const float* x,
-                     double* G, cudaStream_t st);
+                     double* G, cudaStream_t st, const int* sup = nullptr, int nk = 0);
+// kernel mask maps in the handle's workspace for a HOST mask [kz][ky][kx] (support.cu): *sup[nk]
+// box offsets of the support, *inv[K] support index of each box offset or -1; re-uploaded only
+// when the mask differs from the previous one
+hicu_status support_maps(hicu_handle* h, const hicu_geom* geom, const uint8_t* kmask, const int** sup,
+                         const int** inv, int* nk, cudaStream_t st);
+// bank_box[k][c][kbox] = bank_sup[k][c][inv[kbox]] (zero off the support)
+hicu_status launch_support_scatter(hicu_handle* h, int p, int C, int K, int nk, const int* inv,
+                                   const float2* bank_sup, float2* bank_box, cudaStream_t st);
 // cluster Jacobi (eig_cluster.cu): cluster size for an n x n solve (0: use the grid solver),
 // its padded size, and the solve itself on a prepared A0 / V0
 int cluster_eig_ctas(int64_t n);

@@ -28,6 +28,7 @@ EXPORTED = (
     "hicu_reconstruct", "hicu_profile_select", "hicu_profile_read", "hicu_conv_null_noalloc",
     "hicu_profile_eig_sweeps", "hicu_batch_order", "hicu_reconstruct_batched",
     "hicu_conv_null_filter_grad", "hicu_project_unobserved",
+    "hicu_support_length", "hicu_gram_support", "hicu_expand_filters",
 )
 
 HICU_K_GRAM, HICU_K_EIG, HICU_K_CONV, HICU_K_ADJOINT, HICU_K_JL, HICU_K_MISC = 0, 1, 2, 3, 4, 5
@@ -50,7 +51,8 @@ class hicu_stage(ctypes.Structure):
 class hicu_params(ctypes.Structure):
     _fields_ = [("rank", c_int64), ("nstages", c_int32), ("stages", POINTER(hicu_stage)),
                 ("seed", c_uint64), ("jl", c_int32), ("prec", c_int32),
-                ("gram_on_current", c_int32), ("init", c_int32), ("eig_solver", c_int32)]
+                ("gram_on_current", c_int32), ("init", c_int32), ("eig_solver", c_int32),
+                ("kernel_mask", c_void_p)]
 
 
 class hicu_log(ctypes.Structure):
@@ -114,6 +116,9 @@ def lib() -> ctypes.CDLL:
             "hicu_conv_null_filter_grad": ([P, G, R, P, P, c_int32, P, P], c_int32),
             "hicu_project_unobserved": ([P, G, R, P, P, P, P], c_int32),
             "hicu_reconstruct_batched": ([P, c_int32, P, c_int32, P, P], c_int32),
+            "hicu_support_length": ([G, P], c_int64),
+            "hicu_gram_support": ([P, G, R, P, P, P, P], c_int32),
+            "hicu_expand_filters": ([P, G, P, P, c_int32, P, P], c_int32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -283,6 +288,55 @@ def hicu_gram(h: Handle, geom, region, x: torch.Tensor, G: Optional[torch.Tensor
         h._check(lib().hicu_gram(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(x), _ptr(G),
                                  _stream(stream)))
     return G
+
+
+def _kmask(geom, kmask):
+    """A kernel mask as a contiguous HOST uint8 array [kz][ky][kx] over the box geom.k."""
+    import numpy as np
+    m = np.ascontiguousarray(np.asarray(kmask.cpu() if isinstance(kmask, torch.Tensor) else kmask),
+                             dtype=np.uint8)
+    if m.shape != (geom.k[2], geom.k[1], geom.k[0]):
+        raise ValueError(f"kernel mask must have shape (kz, ky, kx) = {(geom.k[2], geom.k[1], geom.k[0])}, "
+                         f"got {m.shape}")
+    if not m.any():
+        raise ValueError("kernel mask has an empty support")
+    return m
+
+
+def hicu_support_length(geom, kmask) -> int:
+    """C |K| for a kernel mask (the length of a filter on the mask's support)."""
+    m = _kmask(geom, kmask)
+    return int(lib().hicu_support_length(ctypes.byref(geom), m.ctypes.data_as(c_void_p)))
+
+
+def hicu_gram_support(h: Handle, geom, region, kmask, x: torch.Tensor, G: Optional[torch.Tensor] = None,
+                      stream=None):
+    """G = H_K(x)^H H_K(x) over the C |K| coefficients of the kernel mask's support."""
+    m = _kmask(geom, kmask)
+    n = hicu_support_length(geom, m)
+    _need(x, "x", torch.complex64, _kshape(geom))
+    if G is None:
+        G = torch.empty((n, n), dtype=torch.complex128, device=x.device)
+    _need(G, "G", torch.complex128, (n, n))
+    with torch.cuda.device(h._dev(x, G)):
+        h._check(lib().hicu_gram_support(h.ptr, ctypes.byref(geom), ctypes.byref(region),
+                                         m.ctypes.data_as(c_void_p), _ptr(x), _ptr(G), _stream(stream)))
+    return G
+
+
+def hicu_expand_filters(h: Handle, geom, kmask, bank_sup: torch.Tensor, stream=None):
+    """(p, C |K|) filters on the mask's support -> (p, C kz ky kx) box-layout filters, zero off it."""
+    m = _kmask(geom, kmask)
+    n = hicu_support_length(geom, m)
+    if bank_sup.dim() != 2:
+        raise ValueError("bank_sup must be a (p, C |K|) complex64 tensor")
+    p = bank_sup.shape[0]
+    _need(bank_sup, "bank_sup", torch.complex64, (p, n))
+    out = torch.empty((p, _filter_len(geom)), dtype=torch.complex64, device=bank_sup.device)
+    with torch.cuda.device(h._dev(bank_sup)):
+        h._check(lib().hicu_expand_filters(h.ptr, ctypes.byref(geom), m.ctypes.data_as(c_void_p), _ptr(bank_sup),
+                                           p, _ptr(out), _stream(stream)))
+    return out
 
 
 HICU_NULLSPACE_WARM, HICU_NULLSPACE_SPLIT, HICU_NULLSPACE_GRID, HICU_NULLSPACE_CLUSTER = 1, 2, 4, 8
@@ -462,10 +516,12 @@ def hicu_gd_step(h: Handle, geom, region, y: torch.Tensor, mask: Optional[torch.
 
 
 def make_params(rank: int, stages, seed: int = 0, jl: int = HICU_JL_PROJECTOR, prec: int = HICU_FP32,
-                gram_on_current: bool = False, init: int = 0, eig_solver: Optional[str] = None):
+                gram_on_current: bool = False, init: int = 0, eig_solver: Optional[str] = None,
+                kernel_mask=None):
     """stages: sequence of (off, ext, iters, gd_steps, p).  eig_solver: None (the library's
     default: tridiagonal principal subspace in projector mode, else Jacobi by size), "grid",
-    "cluster" (Jacobi) or "tridiag"."""
+    "cluster" (Jacobi) or "tridiag".  kernel_mask: optional (kz, ky, kx) {0,1} array over the
+    kernel's box (the shape is checked by hicu_reconstruct's binding)."""
     arr = (hicu_stage * len(stages))()
     for i, (off, ext, iters, gd, p) in enumerate(stages):
         arr[i].region = make_region(off, ext)
@@ -484,12 +540,19 @@ def make_params(rank: int, stages, seed: int = 0, jl: int = HICU_JL_PROJECTOR, p
     prm.eig_solver = {None: 0, "grid": HICU_NULLSPACE_GRID, "cluster": HICU_NULLSPACE_CLUSTER,
                       "tridiag": HICU_NULLSPACE_TRIDIAG}[eig_solver]
     prm._keep = arr  # keep the stage array alive with the struct
+    if kernel_mask is not None:
+        import numpy as np
+        km = np.ascontiguousarray(np.asarray(kernel_mask), dtype=np.uint8)
+        prm.kernel_mask = km.ctypes.data_as(c_void_p)
+        prm._keep_mask = km
     return prm
 
 
 def hicu_reconstruct(h: Handle, geom, x0: torch.Tensor, mask: torch.Tensor, params: hicu_params,
                      x_out: Optional[torch.Tensor] = None, want_log: bool = False, stream=None):
     """x0 / mask / x_out may live on the GPU or (pinned) on the host."""
+    if getattr(params, "_keep_mask", None) is not None:
+        _kmask(geom, params._keep_mask)
     _need(x0, "x0", torch.complex64, _kshape(geom))
     _need(mask, "mask", torch.uint8, _mshape(geom))
     if x_out is None:
