@@ -481,6 +481,72 @@ def gd_step(y: np.ndarray, mask: np.ndarray, geom: Geom, reg: Region, filters: n
     return y - eta * g, StepInfo(eta, obj, gn2, D)
 
 
+def region_indicator(geom: Geom, reg: Region) -> np.ndarray:
+    """1 on the entries of region S, 0 elsewhere, shape (1, Nz, Ny, Nx)."""
+    nx, ny, nz = geom.dims
+    ind = np.zeros((1, nz, ny, nx))
+    ind[:, reg.off[2]:reg.off[2] + reg.ext[2], reg.off[1]:reg.off[1] + reg.ext[1],
+        reg.off[0]:reg.off[0] + reg.ext[0]] = 1.0
+    return ind
+
+
+def gd_step_soft(y: np.ndarray, x0: np.ndarray, mask: np.ndarray, geom: Geom, reg: Region, filters: np.ndarray,
+                 lam: float) -> Tuple[np.ndarray, StepInfo]:
+    """One descent step on ||H(y) Q~||^2 + lam ||M o y - X0||^2 with exact line search: the soft
+    data-consistency cost f_1 of the problem statement with multiplier lam (Theory, Eq. 3), in
+    Algorithm 1 steps 7-8.
+
+    Only the entries of region S move (the others are constants of this step), so the data term
+    is taken over S.  With X0 zero off the samples, M o y - X0 = M o (y - X0) and
+      g   = sum_k H^H(H(y) q~_k) + lam M o (y - X0)            (on S; the factor 2 dropped)
+      phi(eta) = ||H(y - eta g) Q~||^2 + lam ||M o (y - eta g - X0)||^2,
+    a quadratic in eta whose minimiser is Re<H(y)Q~, H(g)Q~> + lam Re<M(y - X0), M g> over
+    ||H(g)Q~||^2 + lam ||M g||^2, and the numerator equals ||g||^2.  StepInfo.objective is
+    phi(0), StepInfo.denom the denominator.
+    """
+    y = np.asarray(y, dtype=np.complex128)
+    x0 = np.asarray(x0, dtype=np.complex128)
+    ind = region_indicator(geom, reg)
+    m = _mask4(mask, y.shape)
+    R = conv_null(y, geom, reg, filters)
+    dc = ind * m * (y - x0)
+    g = conv_null_adjoint(R, geom, reg, filters) + lam * dc
+    obj = float(np.vdot(R, R).real + lam * np.vdot(dc, dc).real)
+    gn2 = float(np.vdot(g, g).real)
+    Rg = conv_null(g, geom, reg, filters)
+    mg = ind * m * g
+    D = float(np.vdot(Rg, Rg).real + lam * np.vdot(mg, mg).real)
+    eta = gn2 / D if (D > 0.0 and gn2 > 0.0) else 0.0
+    return y - eta * g, StepInfo(eta, obj, gn2, D)
+
+
+def image_axes(geom: Geom) -> Tuple[int, ...]:
+    """Array axes of the sparsifying transform: x, y and z, except a circular z (the time axis of
+    2D+t) and axes of length 1."""
+    nx, ny, nz = geom.dims
+    axes = []
+    if nz > 1 and not geom.circular[2]:
+        axes.append(1)
+    if ny > 1:
+        axes.append(2)
+    if nx > 1:
+        axes.append(3)
+    return tuple(axes)
+
+
+def soft_threshold(x: np.ndarray, geom: Geom, tau: float) -> np.ndarray:
+    """The proximal step of tau ||T x||_1 for T the centred orthonormal inverse DFT of every coil
+    over the image axes (the coil images): x <- T^H S_tau(T x), with the complex soft threshold
+    S_tau(w) = w max(0, 1 - tau / |w|) (Discussion: an l1 norm of a linear sparsifying transform of
+    X is a soft-thresholding after Algorithm 1 step 8)."""
+    axes = image_axes(geom)
+    x = np.asarray(x, dtype=np.complex128)
+    w = np.fft.fftshift(np.fft.ifftn(np.fft.ifftshift(x, axes=axes), axes=axes, norm="ortho"), axes=axes)
+    mag = np.abs(w)
+    w = w * np.maximum(0.0, 1.0 - tau / np.maximum(mag, 1e-300))
+    return np.fft.fftshift(np.fft.fftn(np.fft.ifftshift(w, axes=axes), axes=axes, norm="ortho"), axes=axes)
+
+
 # ----------------------------------------------------------- the HICU iteration
 
 
@@ -516,12 +582,17 @@ def initial_estimate(x0: np.ndarray, mask: np.ndarray, mode: str = "zero_filled"
 
 def reconstruct(x0: np.ndarray, mask: np.ndarray, geom: Geom, stages: Sequence[StageSpec], r: int,
                 seed: int, jl_mode: str = "projector", gram_on: str = "previous",
-                init: str = "zero_filled", log: Optional[ReconLog] = None) -> np.ndarray:
+                init: str = "zero_filled", log: Optional[ReconLog] = None, lam: float = 0.0,
+                tau: float = 0.0) -> np.ndarray:
     """Algorithm 1 (HICU) with the Gram route for steps 2-3 and centre-out stages.
 
     For i = 1..I: null space of H^(i-1)(x^(i-1)) (step 2 names the previous region;
     ``gram_on="current"`` uses S^(i) instead), then G^(i) descent steps on S^(i), each with a
     fresh JL draw (counter = global step index, starting at 0).
+    lam > 0: soft data consistency with that multiplier (gd_step_soft) instead of hard data
+    consistency.  tau > 0: after every descent step of a stage whose region is the whole array,
+    the l1 proximal step soft_threshold (Discussion), followed under hard data consistency by
+    restoring the observed samples.
     """
     x = initial_estimate(x0, mask, init)
     counter = 0
@@ -535,11 +606,20 @@ def reconstruct(x0: np.ndarray, mask: np.ndarray, geom: Geom, stages: Sequence[S
                 log.J.append(tail_energy(w, r))
             y = x
             rows = Q.shape[0] if jl_mode == "projector" else Q.shape[1]
+            whole = tuple(st.region.off) == (0, 0, 0) and tuple(st.region.ext) == tuple(geom.dims)
             for _ in range(st.gd_steps):
                 P = jl_matrix(seed, counter, rows, st.p)
                 counter += 1
                 f = as_filters(jl_compress(Q, P, jl_mode), geom)
-                y, info = gd_step(y, mask, geom, st.region, f)
+                if lam > 0.0:
+                    y, info = gd_step_soft(y, x0, mask, geom, st.region, f, lam)
+                else:
+                    y, info = gd_step(y, mask, geom, st.region, f)
+                if tau > 0.0 and whole:
+                    y = soft_threshold(y, geom, tau)
+                    if lam <= 0.0:
+                        obs = _mask4(mask, y.shape) > 0
+                        y = np.where(obs, np.asarray(x0, dtype=np.complex128), y)
                 if log is not None:
                     log.objective.append(info.objective)
                     log.eta.append(info.eta)

@@ -633,3 +633,98 @@ def test_masked_kernel_annihilates_exactly_low_rank_kspace_and_reconstructs():
     m4 = np.broadcast_to(mask[None], x0.shape).astype(bool)
     np.testing.assert_array_equal(xr[m4], x0[m4])
     assert O.ser_db(x_true, xr) > O.ser_db(x_true, x0) + 60.0
+
+
+# ------------------------------------------- soft data consistency and l1 (Theory; Discussion)
+
+
+def _soft_case(seed=11):
+    geom, reg, x, rng = make_case(0, seed)
+    f = rand_filters(rng, geom, 3)
+    mask = (rng.random((geom.dims[2], geom.dims[1], geom.dims[0])) < 0.4).astype(np.uint8)
+    x0 = random_complex(rng, x.shape) * mask[None]
+    return geom, reg, x, f, mask, x0, rng
+
+
+def _soft_objective(y, x0, mask, geom, reg, f, lam):
+    R = O.conv_null(y, geom, reg, f)
+    ind = O.region_indicator(geom, reg)
+    dc = ind * mask[None] * (y - x0)
+    return float(np.vdot(R, R).real + lam * np.vdot(dc, dc).real)
+
+
+def test_soft_dc_gradient_matches_finite_differences():
+    geom, reg, y, f, mask, x0, rng = _soft_case()
+    lam = 0.7
+    _, info = O.gd_step_soft(y, x0, mask, geom, reg, f, lam)
+    # g from the step: y_new = y - eta g
+    y1, info = O.gd_step_soft(y, x0, mask, geom, reg, f, lam)
+    g = (y - y1) / info.eta
+    ind = O.region_indicator(geom, reg)
+    np.testing.assert_array_equal(g * (1 - ind), 0)                # nothing outside S moves
+    eps = 1e-6
+    for t in range(4):
+        d = random_complex(rng, y.shape) * ind
+        fd = (_soft_objective(y + eps * d, x0, mask, geom, reg, f, lam)
+              - _soft_objective(y - eps * d, x0, mask, geom, reg, f, lam)) / (2 * eps)
+        assert abs(fd - 2 * np.vdot(g, d).real) < 1e-6 * abs(fd) + 1e-8
+
+
+def test_soft_dc_exact_line_search_and_special_case():
+    geom, reg, y, f, mask, x0, rng = _soft_case(12)
+    lam = 2.5
+    y1, info = O.gd_step_soft(y, x0, mask, geom, reg, f, lam)
+    g = (y - y1) / info.eta
+    phi = lambda e: _soft_objective(y - e * g, x0, mask, geom, reg, f, lam)
+    assert abs(phi(0.0) - info.objective) < 1e-10 * info.objective
+    for de in (1e-3, -1e-3):
+        assert phi(info.eta) <= phi(info.eta * (1 + de))
+    assert abs((phi(0.0) - phi(info.eta)) - info.gnorm2 ** 2 / info.denom) < 1e-9 * phi(0.0)
+    # lam = 0: the unconstrained step (no data term, every entry of S free)
+    y0s, i0 = O.gd_step_soft(y, x0, mask, geom, reg, f, 0.0)
+    y0h, ih = O.gd_step(y, None, geom, reg, f)
+    np.testing.assert_allclose(y0s, y0h, rtol=1e-13, atol=1e-13)
+
+
+def test_soft_threshold_is_the_l1_prox():
+    rng = np.random.default_rng(4)
+    for dims, circ in (((8, 6, 1), (0, 0, 0)), ((7, 5, 4), (0, 0, 0)), ((6, 5, 4), (0, 0, 1))):
+        geom = O.Geom(dims, 2, (3, 3, 1), circ)
+        v = random_complex(rng, (2, dims[2], dims[1], dims[0]))
+        np.testing.assert_allclose(O.soft_threshold(v, geom, 0.0), v, rtol=1e-13, atol=1e-13)
+        tau = 0.8
+        u = O.soft_threshold(v, geom, tau)
+        axes = O.image_axes(geom)
+        T = lambda z: np.fft.fftshift(np.fft.ifftn(np.fft.ifftshift(z, axes=axes), axes=axes, norm="ortho"),
+                                      axes=axes)
+        Tu, Tr = T(u), T(v - u)
+        on = np.abs(Tu) > 1e-12
+        # optimality: T(v - u) = tau Tu / |Tu| on the support, |T(v - u)| <= tau off it
+        np.testing.assert_allclose(Tr[on], tau * Tu[on] / np.abs(Tu[on]), rtol=1e-10, atol=1e-10)
+        assert np.all(np.abs(Tr[~on]) <= tau + 1e-10)
+        # the centring shifts are permutations and unit-modulus modulations: they drop out
+        w = np.fft.ifftn(v, axes=axes, norm="ortho")
+        w = w * np.maximum(0.0, 1.0 - tau / np.maximum(np.abs(w), 1e-300))
+        np.testing.assert_allclose(np.fft.fftn(w, axes=axes, norm="ortho"), u, rtol=1e-12, atol=1e-12)
+        if circ[2]:
+            assert axes == (2, 3)
+
+
+def test_soft_dc_and_l1_reconstructions():
+    rng = np.random.default_rng(3)
+    L = 4
+    x_true = lowrank_exponential_kspace(rng, (1, 16, 16), 2, L)
+    mask = (rng.random((1, 16, 16)) < 0.55).astype(np.uint8)
+    x0 = x_true * mask[None]
+    geom = O.Geom((16, 16, 1), 2, (3, 3, 1))
+    st = [O.StageSpec(O.full_region(geom), iters=40, gd_steps=5, p=6)]
+    # soft data consistency: noise-free exactly low-rank data are still recovered, and the
+    # observed samples move only by what the data term allows
+    xs = O.reconstruct(x0, mask, geom, st, r=L, seed=1, lam=10.0)
+    assert O.ser_db(x_true, xs) > O.ser_db(x_true, x0) + 25.0
+    m4 = np.broadcast_to(mask[None], x0.shape).astype(bool)
+    assert not np.array_equal(xs[m4], x0[m4])
+    # l1 step under hard data consistency: observed samples bit-identical
+    xl = O.reconstruct(x0, mask, geom, st[:1], r=L, seed=1, tau=1e-4)
+    np.testing.assert_array_equal(xl[m4], x0[m4])
+    assert O.ser_db(x_true, xl) > O.ser_db(x_true, x0) + 10.0
