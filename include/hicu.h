@@ -131,6 +131,13 @@ typedef struct {
                                 circular or spherical masks); NULL = the whole box.  The
                                 null space then has n = C |K| coefficients (see
                                 hicu_gram_support) */
+  double dc_weight;          /* lambda of the soft data-consistency cost lambda ||M o X - X0||^2
+                                (Theory, Eq. 3); 0 = hard data consistency (observed samples
+                                never move).  Steps as hicu_gd_step_soft */
+  double l1_threshold;       /* tau of the l1 step hicu_soft_threshold after every descent step of
+                                a stage whose region is the whole array (Discussion); 0 = off.
+                                Under hard data consistency the observed samples are restored
+                                after it */
 } hicu_params;
 
 /* Optional per-iteration log, HOST arrays (any may be NULL). */
@@ -393,6 +400,33 @@ hicu_status hicu_gd_step_filters(hicu_handle* h, const hicu_geom* geom,
                                  const hicu_region* region, float* y, const uint8_t* mask,
                                  const float* filters, int32_t p, double* stats, int32_t prec,
                                  void* stream);
+
+/*
+ * hicu_gd_step_soft - one descent step on ||H(y) Q~||^2 + lambda ||M o y - X0||^2 with exact line
+ * search: the soft data-consistency cost, f_1 with multiplier lambda (Theory, Eq. 3; Algorithm 1
+ * steps 7-8).  Only entries of S move; observed ones move too.  On S:
+ *   g   = sum_k H^H(H(y) q~_k) + lambda M o (y - X0)
+ *   eta = ||g||^2 / (||H(g) Q~||^2 + lambda ||M o g||^2),   y <- y - eta g
+ *   x0    : complex64 observed data X0, zero off the samples (device)
+ *   lambda: >= 0 (0 gives the unconstrained step: no data term, every entry of S free)
+ *   stats : optional device double[4] = {eta, objective before the step (both terms), ||g||^2,
+ *           the denominator}
+ * Other arguments as hicu_gd_step_filters.
+ */
+hicu_status hicu_gd_step_soft(hicu_handle* h, const hicu_geom* geom, const hicu_region* region, float* y,
+                              const uint8_t* mask, const float* x0, double lambda, const float* filters,
+                              int32_t p, double* stats, int32_t prec, void* stream);
+
+/*
+ * hicu_soft_threshold - the proximal step of tau ||T x||_1, x <- T^H S_tau(T x), in place on the
+ * whole array (Discussion: an l1 norm of a linear sparsifying transform adds a soft-thresholding
+ * after Algorithm 1 step 8).  T is the centred orthonormal inverse DFT of every coil over the image
+ * axes (x, y, and z unless z is flagged circular: the time axis of 2D+t), i.e. the coil images;
+ * S_tau(w) = w max(0, 1 - tau / |w|).  The two transforms are cuFFT's; the handle keeps the plan.
+ *   x   : complex64 [C][Nz][Ny][Nx] (device), overwritten
+ *   tau : >= 0 (0: no change)
+ */
+hicu_status hicu_soft_threshold(hicu_handle* h, const hicu_geom* geom, float* x, double tau, void* stream);
 
 /*
  * hicu_gd_step - JL compression (hicu_jl_compress) followed by

@@ -68,7 +68,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < _newest(objs):
         libdir = _cuda_lib_dir(nvcc)
         cmd = [nvcc] + ARCH + ["-shared", "-o", LIB] + objs + [
-            "-cudart", "shared", f"-L{libdir}", "-Xlinker", f"-rpath,{libdir}", "-lpthread"]
+            "-cudart", "shared", f"-L{libdir}", "-Xlinker", f"-rpath,{libdir}", "-lcufft", "-lpthread"]
         if verbose:
             print(" ".join(cmd), flush=True)
         res = subprocess.run(cmd, capture_output=True, text=True)

@@ -1,5 +1,6 @@
 // C ABI of libhicu: handle, argument validation, workspace, and the drivers
 // that chain the kernels into the steps of Algorithm 1.
+#include <cmath>
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -243,6 +244,7 @@ extern "C" hicu_status hicu_destroy(hicu_handle* h) {
   for (auto& w : h->ws)
     if (w.ptr) cudaFree(w.ptr);
   for (auto e : h->prof_events) cudaEventDestroy(e);
+  release_fft(h);
   cudaFree(h->dev_err);
   cudaFree(h->dev_sync);
   delete h;
@@ -614,7 +616,104 @@ hicu_status gd_step_filters(hicu_handle* h, const hicu_geom* geom, const hicu_re
   return HICU_OK;
 }
 
+// One descent step with soft data consistency (softdc.cu describes the cost and the step): the
+// convolution of y, the unmasked adjoint, the data term added to g on the region, the convolution of
+// g, then the update over the whole region.  Partial-sum layout for the update kernel:
+// [conv: ||H(y)Q~||^2 | lambda ||M(y - X0)||^2 | ||g||^2 | conv: ||H(g)Q~||^2 | lambda ||M g||^2],
+// so its objective, numerator and denominator sums take the data term along.
+hicu_status gd_step_filters_soft(hicu_handle* h, const hicu_geom* geom, const hicu_region* region, float* y,
+                                 const uint8_t* mask, const float* x0, double lam, const float* filters, int32_t p,
+                                 double* stats, int32_t prec, cudaStream_t st) {
+  hicu_status s = check_prec(h, prec);
+  if (s) return s;
+  ConvGeom g;
+  s = make_conv_geom(h, geom, region, &g);
+  if (s) return s;
+  const bool tc = prec == HICU_SPLIT_BF16;
+  if (tc && (s = check_tc(h, g))) return s;
+  float2* gb = (float2*)ws_get(h, WS_G, sizeof(float2) * (size_t)g.C * g.ex * g.ey * g.ez, &s);
+  if (s) return s;
+  double* st4 = stats;
+  if (!st4) {
+    st4 = (double*)ws_get(h, WS_STATS, sizeof(double) * 8, &s);
+    if (s) return s;
+  }
+  const KView yv = full_view(geom, region, y);
+  const KView xv = full_view(geom, region, const_cast<float*>(x0));
+  const KView gview = region_view(g, gb);
+  const MView mv = mask_view(geom, region, mask);
+  MView none = mv;
+  none.p = nullptr;
+  int n1 = 0, n2 = 0, n3 = 0, nb = 0;
+  launch_soft_dc(h, g, gview, yv, xv, mv, lam, nullptr, nullptr, nullptr, &nb, st);
+  if (tc) {
+    const size_t xbytes = tc_x_bytes(g);
+    uint4* xpl = (uint4*)ws_get(h, WS_TC_X, xbytes, &s);
+    if (s) return s;
+    uint4* gpl = (uint4*)ws_get(h, WS_TC_G, xbytes, &s);
+    if (s) return s;
+    uint4* rpl = (uint4*)ws_get(h, WS_TC_R, tc_r_bytes(g, p), &s);
+    if (s) return s;
+    void* bwc = ws_get(h, WS_TC_BC, tc_b_bytes(g, p, 0), &s);
+    if (s) return s;
+    void* bwa = ws_get(h, WS_TC_BA, tc_b_bytes(g, p, 1), &s);
+    if (s) return s;
+    if ((s = launch_conv_tc(h, g, nullptr, nullptr, p, nullptr, nullptr, nullptr, &n1, st))) return s;
+    if ((s = launch_adjoint_tc(h, g, nullptr, nullptr, p, none, gview, nullptr, &n2, st))) return s;
+    n3 = n1;
+    double* part = (double*)ws_get(h, WS_PART, sizeof(double) * (n1 + n3 + 3 * (size_t)nb + n2), &s);
+    if (s) return s;
+    double* p_dc = part + n1;
+    double* p_g = p_dc + nb;
+    double* p_d = p_g + nb;
+    double* p_mg = p_d + n3;
+    double* p_adj = p_mg + nb;   // the adjoint's own norm partials (not used)
+    if ((s = tc_prepare_weights(h, g, (const float2*)filters, p, bwc, bwa, st))) return s;
+    if ((s = tc_prepare_input(h, g, yv, xpl, st))) return s;
+    if ((s = launch_conv_tc(h, g, xpl, bwc, p, nullptr, rpl, part, &n1, st))) return s;
+    if ((s = launch_adjoint_tc(h, g, rpl, bwa, p, none, gview, p_adj, &n2, st))) return s;
+    if ((s = launch_soft_dc(h, g, gview, yv, xv, mv, lam, p_dc, p_g, p_mg, &nb, st))) return s;
+    if ((s = tc_prepare_input(h, g, gview, gpl, st))) return s;
+    if ((s = launch_conv_tc(h, g, gpl, bwc, p, nullptr, nullptr, p_d, &n3, st))) return s;
+    if ((s = launch_update_step(h, g, yv, gview, none, part, n1 + nb, nb, n3 + nb, st4, st)))
+      return cuda_error(h, cudaGetLastError(), "update");
+    return HICU_OK;
+  }
+  StepBuffers b;
+  s = prep_filters(h, g, filters, p, true, true, &b, st);
+  if (s) return s;
+  float2* R = (float2*)ws_get(h, WS_R, sizeof(float2) * (size_t)g.s * p, &s);
+  if (s) return s;
+  launch_conv_fp32(h, g, yv, b.fT, p, b.Ppad, nullptr, nullptr, &n1, st);
+  launch_adjoint_fp32(h, g, R, b.fA, p, b.Ppad, b.Cpad, none, gview, nullptr, &n2, st);
+  n3 = n1;
+  double* part = (double*)ws_get(h, WS_PART, sizeof(double) * (n1 + n3 + 3 * (size_t)nb + n2), &s);
+  if (s) return s;
+  double* p_dc = part + n1;
+  double* p_g = p_dc + nb;
+  double* p_d = p_g + nb;
+  double* p_mg = p_d + n3;
+  double* p_adj = p_mg + nb;
+  if ((s = launch_conv_fp32(h, g, yv, b.fT, p, b.Ppad, R, part, &n1, st))) return s;
+  if ((s = launch_adjoint_fp32(h, g, R, b.fA, p, b.Ppad, b.Cpad, none, gview, p_adj, &n2, st))) return s;
+  if ((s = launch_soft_dc(h, g, gview, yv, xv, mv, lam, p_dc, p_g, p_mg, &nb, st))) return s;
+  if ((s = launch_conv_fp32(h, g, gview, b.fT, p, b.Ppad, nullptr, p_d, &n3, st))) return s;
+  if ((s = launch_update_step(h, g, yv, gview, none, part, n1 + nb, nb, n3 + nb, st4, st)))
+    return cuda_error(h, cudaGetLastError(), "update");
+  return HICU_OK;
+}
+
 }  // namespace hicu
+
+extern "C" hicu_status hicu_gd_step_soft(hicu_handle* h, const hicu_geom* geom, const hicu_region* region,
+                                         float* y, const uint8_t* mask, const float* x0, double lambda,
+                                         const float* filters, int32_t p, double* stats, int32_t prec, void* stream) {
+  if (!h) return HICU_ERR_ARG;
+  if (!y || !mask || !x0 || !filters) return set_error(h, HICU_ERR_ARG, "gd_step_soft: null pointer");
+  if (p < 1 || p > 4096) return set_error(h, HICU_ERR_RANK, "gd_step_soft: p out of range");
+  if (!(lambda >= 0.0) || !std::isfinite(lambda)) return set_error(h, HICU_ERR_ARG, "gd_step_soft: lambda must be >= 0");
+  return gd_step_filters_soft(h, geom, region, y, mask, x0, lambda, filters, p, stats, prec, (cudaStream_t)stream);
+}
 
 extern "C" hicu_status hicu_gd_step_filters(hicu_handle* h, const hicu_geom* geom,
                                             const hicu_region* region, float* y, const uint8_t* mask,
@@ -724,6 +823,9 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
   if (prm->jl != HICU_JL_NULLSPACE && prm->jl != HICU_JL_PROJECTOR)
     return set_error(h, HICU_ERR_ARG, "reconstruct: unknown JL mode");
   if (prm->init != 0 && prm->init != 1) return set_error(h, HICU_ERR_ARG, "reconstruct: unknown init");
+  if (!(prm->dc_weight >= 0.0) || !std::isfinite(prm->dc_weight) || !(prm->l1_threshold >= 0.0) ||
+      !std::isfinite(prm->l1_threshold))
+    return set_error(h, HICU_ERR_ARG, "reconstruct: dc_weight and l1_threshold must be finite and >= 0");
   if (prm->eig_solver != 0 && prm->eig_solver != HICU_NULLSPACE_GRID && prm->eig_solver != HICU_NULLSPACE_CLUSTER &&
       prm->eig_solver != HICU_NULLSPACE_TRIDIAG)
     return set_error(h, HICU_ERR_ARG, "reconstruct: unknown eig_solver");
@@ -767,6 +869,16 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
   if (cudaMemcpyAsync(y, x0, sizeof(float2) * N, in_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                       st) != cudaSuccess)
     return cuda_error(h, cudaGetLastError(), "reconstruct: input copy");
+  // the observed data X0, kept for the soft data-consistency term and for restoring the samples after
+  // the l1 step (the start estimate in y may differ from it: time-averaged initialisation)
+  const bool soft = prm->dc_weight > 0.0, l1 = prm->l1_threshold > 0.0;
+  float* x0c = nullptr;
+  if (soft || l1) {
+    x0c = (float*)ws_get(h, WS_REC_X0, sizeof(float2) * N, &s);
+    if (s) return s;
+    if (cudaMemcpyAsync(x0c, y, sizeof(float2) * N, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return cuda_error(h, cudaGetLastError(), "reconstruct: X0 copy");
+  }
   double* G = (double*)ws_get(h, WS_REC_G, sizeof(double2) * n * n, &s);
   if (s) return s;
   double* Q = (double*)ws_get(h, WS_REC_Q, sizeof(double2) * n * (principal ? r : nr), &s);
@@ -813,6 +925,8 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
     // split planes of y on this stage's region: made by the stage's first step, then kept current
     // by each step's update (the Gram and eigen-solve leave y alone)
     bool planes_valid = false;
+    bool whole = true;
+    for (int a = 0; a < 3; ++a) whole = whole && stg.region.off[a] == 0 && stg.region.ext[a] == geom->dim[a];
     for (int i = 0; i < stg.iters; ++i) {
       // the JL matrices of this outer iteration's descent steps depend on nothing but the seed and
       // the step counter: drawn on the side stream beside the Gram and the eigen-solve (after the
@@ -855,11 +969,23 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
             (s = launch_support_scatter(h, stg.p, geom->ncoil, geom->k[0] * geom->k[1] * geom->k[2], nk, inv,
                                         (const float2*)bank_sup, (float2*)bank, st)))
           return s;
-        // the update leaves the split planes of y for the next step of the same region
-        s = gd_step_filters(h, geom, &stg.region, y, m, bank, stg.p, dstats + 4 * counter, prm->prec, st,
-                            planes_valid, true);
-        planes_valid = true;
+        if (soft) {
+          s = gd_step_filters_soft(h, geom, &stg.region, y, m, x0c, prm->dc_weight, bank, stg.p,
+                                   dstats + 4 * counter, prm->prec, st);
+        } else {
+          // the update leaves the split planes of y for the next step of the same region
+          s = gd_step_filters(h, geom, &stg.region, y, m, bank, stg.p, dstats + 4 * counter, prm->prec, st,
+                              planes_valid, true);
+          planes_valid = true;
+        }
         if (s) return s;
+        // the l1 step after Algorithm 1 step 8, on stages over the whole array; under hard data
+        // consistency the observed samples are restored after it
+        if (l1 && whole) {
+          if ((s = run_soft_threshold(h, geom, y, prm->l1_threshold, st))) return s;
+          if (!soft && (s = launch_restore_observed(h, geom, y, x0c, m, st))) return s;
+          planes_valid = false;
+        }
         ++counter;
       }
       ++it;

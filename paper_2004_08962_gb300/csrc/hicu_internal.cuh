@@ -209,6 +209,10 @@ struct hicu_handle {
   cudaEvent_t side_join = nullptr;
   cudaEvent_t draw_fork = nullptr;  // JL draws of an outer iteration
   cudaEvent_t draw_join = nullptr;
+  // l1 step (softdc.cu): the FFT plan (a cufftHandle) and the geometry key it was made for
+  int fft_plan = 0;
+  bool fft_have = false;
+  long long fft_key[5] = {0, 0, 0, 0, 0};
   // kernel mask K (support.cu): host copy of the last mask whose maps sit in WS_SUP
   std::vector<uint8_t> sup_mask;
   int sup_nk = 0;
@@ -255,6 +259,7 @@ enum Slot {
   WS_REC_P,       // reconstruct: JL matrices of one outer iteration's descent steps
   WS_SUP,         // kernel mask maps: support offset -> box offset, box offset -> support offset or -1
   WS_BANK_SUP,    // reconstruct: filter bank on the support of K [p][C][|K|]
+  WS_REC_X0,      // reconstruct: the observed data X0, kept for soft data consistency / the l1 step
   WS_COUNT
 };
 static_assert(WS_COUNT <= hicu_handle::kSlots, "workspace slots");
@@ -382,6 +387,19 @@ hicu_status run_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* r
 // when the mask differs from the previous one
 hicu_status support_maps(hicu_handle* h, const hicu_geom* geom, const uint8_t* kmask, const int** sup,
                          const int** inv, int* nk, cudaStream_t st);
+// soft data consistency (softdc.cu): g += lambda M o (y - X0) on the region (gb), per-CTA partials of
+// lambda ||M o (y - X0)||^2, ||g||^2 and lambda ||M o g||^2; part_dc == nullptr: sizing only
+hicu_status launch_soft_dc(hicu_handle* h, const ConvGeom& g, KView gb, KView y, KView x0, MView m, double lam,
+                           double* part_dc, double* part_g, double* part_mg, int* nblocks, cudaStream_t st);
+// the l1 proximal step on the whole array (in place), and the restore of the observed samples
+hicu_status run_soft_threshold(hicu_handle* h, const hicu_geom* geom, float* x, double tau, cudaStream_t st);
+hicu_status launch_restore_observed(hicu_handle* h, const hicu_geom* geom, float* y, const float* x0,
+                                    const uint8_t* mask, cudaStream_t st);
+void release_fft(hicu_handle* h);
+// one descent step with soft data consistency (abi.cu)
+hicu_status gd_step_filters_soft(hicu_handle* h, const hicu_geom* geom, const hicu_region* region, float* y,
+                                 const uint8_t* mask, const float* x0, double lam, const float* filters, int32_t p,
+                                 double* stats, int32_t prec, cudaStream_t st);
 // bank_box[k][c][kbox] = bank_sup[k][c][inv[kbox]] (zero off the support)
 hicu_status launch_support_scatter(hicu_handle* h, int p, int C, int K, int nk, const int* inv,
                                    const float2* bank_sup, float2* bank_box, cudaStream_t st);

@@ -29,6 +29,7 @@ EXPORTED = (
     "hicu_profile_eig_sweeps", "hicu_batch_order", "hicu_reconstruct_batched",
     "hicu_conv_null_filter_grad", "hicu_project_unobserved",
     "hicu_support_length", "hicu_gram_support", "hicu_expand_filters",
+    "hicu_gd_step_soft", "hicu_soft_threshold",
 )
 
 HICU_K_GRAM, HICU_K_EIG, HICU_K_CONV, HICU_K_ADJOINT, HICU_K_JL, HICU_K_MISC = 0, 1, 2, 3, 4, 5
@@ -52,7 +53,7 @@ class hicu_params(ctypes.Structure):
     _fields_ = [("rank", c_int64), ("nstages", c_int32), ("stages", POINTER(hicu_stage)),
                 ("seed", c_uint64), ("jl", c_int32), ("prec", c_int32),
                 ("gram_on_current", c_int32), ("init", c_int32), ("eig_solver", c_int32),
-                ("kernel_mask", c_void_p)]
+                ("kernel_mask", c_void_p), ("dc_weight", c_double), ("l1_threshold", c_double)]
 
 
 class hicu_log(ctypes.Structure):
@@ -119,6 +120,8 @@ def lib() -> ctypes.CDLL:
             "hicu_support_length": ([G, P], c_int64),
             "hicu_gram_support": ([P, G, R, P, P, P, P], c_int32),
             "hicu_expand_filters": ([P, G, P, P, c_int32, P, P], c_int32),
+            "hicu_gd_step_soft": ([P, G, R, P, P, P, c_double, P, c_int32, P, c_int32, P], c_int32),
+            "hicu_soft_threshold": ([P, G, P, c_double, P], c_int32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -494,6 +497,33 @@ def hicu_gd_step_filters(h: Handle, geom, region, y: torch.Tensor, mask: Optiona
     return stats
 
 
+def hicu_gd_step_soft(h: Handle, geom, region, y: torch.Tensor, mask: torch.Tensor, x0: torch.Tensor,
+                      lam: float, filters: torch.Tensor, prec: int = HICU_FP32, stats=None, stream=None):
+    """One descent step with soft data consistency lam ||M o y - X0||^2 (y updated in place)."""
+    _need(y, "y", torch.complex64, _kshape(geom))
+    _need(x0, "x0", torch.complex64, _kshape(geom))
+    if mask is None:
+        raise ValueError("the soft data-consistency step needs the sampling mask")
+    _need(mask, "mask", torch.uint8, _mshape(geom))
+    p = _bank(filters, geom)
+    if stats is None:
+        stats = torch.zeros((4,), dtype=torch.float64, device=y.device)
+    _need(stats, "stats", torch.float64, (4,))
+    with torch.cuda.device(h._dev(y, mask, x0, filters, stats)):
+        h._check(lib().hicu_gd_step_soft(h.ptr, ctypes.byref(geom), ctypes.byref(region), _ptr(y), _ptr(mask),
+                                         _ptr(x0), float(lam), _ptr(filters), p, _ptr(stats), prec,
+                                         _stream(stream)))
+    return stats
+
+
+def hicu_soft_threshold(h: Handle, geom, x: torch.Tensor, tau: float, stream=None):
+    """The l1 proximal step on the coil images, in place on x; returns x."""
+    _need(x, "x", torch.complex64, _kshape(geom))
+    with torch.cuda.device(h._dev(x)):
+        h._check(lib().hicu_soft_threshold(h.ptr, ctypes.byref(geom), _ptr(x), float(tau), _stream(stream)))
+    return x
+
+
 def hicu_gd_step(h: Handle, geom, region, y: torch.Tensor, mask: Optional[torch.Tensor],
                  Q: torch.Tensor, p: int, jl_mode: int = HICU_JL_NULLSPACE, seed: int = 0,
                  counter: int = 0, P: Optional[torch.Tensor] = None, prec: int = HICU_FP32,
@@ -517,11 +547,12 @@ def hicu_gd_step(h: Handle, geom, region, y: torch.Tensor, mask: Optional[torch.
 
 def make_params(rank: int, stages, seed: int = 0, jl: int = HICU_JL_PROJECTOR, prec: int = HICU_FP32,
                 gram_on_current: bool = False, init: int = 0, eig_solver: Optional[str] = None,
-                kernel_mask=None):
+                kernel_mask=None, dc_weight: float = 0.0, l1_threshold: float = 0.0):
     """stages: sequence of (off, ext, iters, gd_steps, p).  eig_solver: None (the library's
     default: tridiagonal principal subspace in projector mode, else Jacobi by size), "grid",
     "cluster" (Jacobi) or "tridiag".  kernel_mask: optional (kz, ky, kx) {0,1} array over the
-    kernel's box (the shape is checked by hicu_reconstruct's binding)."""
+    kernel's box (the shape is checked by hicu_reconstruct's binding).  dc_weight: lambda of soft
+    data consistency (0 = hard); l1_threshold: tau of the l1 step (0 = off)."""
     arr = (hicu_stage * len(stages))()
     for i, (off, ext, iters, gd, p) in enumerate(stages):
         arr[i].region = make_region(off, ext)
@@ -539,6 +570,8 @@ def make_params(rank: int, stages, seed: int = 0, jl: int = HICU_JL_PROJECTOR, p
     prm.init = int(init)
     prm.eig_solver = {None: 0, "grid": HICU_NULLSPACE_GRID, "cluster": HICU_NULLSPACE_CLUSTER,
                       "tridiag": HICU_NULLSPACE_TRIDIAG}[eig_solver]
+    prm.dc_weight = float(dc_weight)
+    prm.l1_threshold = float(l1_threshold)
     prm._keep = arr  # keep the stage array alive with the struct
     if kernel_mask is not None:
         import numpy as np
