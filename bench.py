@@ -621,6 +621,76 @@ def run_batch(args, rank, world):
     return 0
 
 
+# ------------------------------------------------------------------- ablations
+
+def run_ablation(args):
+    """The JL p-sweep and the CO x JL ablation of the paper's Study I (Results, the JL / CO figure),
+    re-run on the synthetic 2D brain slice.  For every variant the schedule is cut after a growing
+    number of outer iterations; each cut reconstruction is timed with CUDA events (L2 flushed before
+    it) and scored by its SER against the fully sampled k-space, giving SER against time.
+      p sweep : p in {1, 2, 4, 8, 32, n - r} in both stages, and no compression (exact gradient)
+      CO x JL : centre-out schedule or full k-space from the first iteration, JL (p = 8 / 32) or
+                exact gradient
+    Every variant runs the plain complex-FP32 convolutions: without compression (n filters) and at
+    p = n - r the filter bank is larger than the split-BF16 adjoint keeps in shared memory, and one
+    form for all keeps the times comparable.  Prints one JSON object."""
+    import torch
+    from oracle import hicu_oracle as O
+    from paper_2004_08962_gb300 import build, hicu
+    from synth.phantoms import make_problem
+    build.build()
+    pb = make_problem("2d_brain_256", seed=problem_seed("brain", 0))
+    n = pb.ncoil * pb.kernel[0] * pb.kernel[1] * pb.kernel[2]
+    h = hicu.Handle()
+    geom = hicu.make_geom(pb.dims, pb.ncoil, pb.kernel, pb.circular)
+    x0 = torch.from_numpy(pb.x0).cuda()
+    mask = torch.from_numpy(pb.mask).cuda()
+    out = torch.empty_like(x0)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    prec = hicu.HICU_FP32
+    co, full = pb.stages[0], pb.stages[1]
+    cuts = [1, 5, 10, 20, 30, 40, 50, 52, 55, 60]
+
+    def stages_for(co_on, p1, p2, upto):
+        st = [((co.off, co.ext) if co_on else ((0, 0, 0), pb.dims)) + (co.iters, co.gd_steps, p1),
+              ((0, 0, 0), pb.dims, full.iters, full.gd_steps, p2)]
+        outp, left = [], upto
+        for off, ext, it, gd, p in st:
+            k = min(it, left)
+            if k > 0:
+                outp.append((off, ext, k, gd, p))
+            left -= k
+        return outp
+
+    def curve(co_on, p1, p2, exact):
+        pts = []
+        for c in cuts:
+            prm = hicu.make_params(pb.rank, stages_for(co_on, p1, p2, c), seed=11, jl=hicu.HICU_JL_PROJECTOR,
+                                   prec=prec, jl_exact=exact)
+            hicu.hicu_reconstruct(h, geom, x0, mask, prm, x_out=out)   # warm
+            ms = timed_recons(lambda: hicu.hicu_reconstruct(h, geom, x0, mask, prm, x_out=out), 1, flush, stream)
+            steps = sum(it * gd for _, _, it, gd, _ in stages_for(co_on, p1, p2, c))
+            pts.append({"outer_iters": c, "gd_steps": steps, "ms": round(ms, 3),
+                        "ser_db": round(O.ser_db(pb.x_full, out.cpu().numpy()), 4)})
+        return pts
+
+    res = {"ablation": "JL p-sweep and CO x JL on the synthetic 2D brain slice (256x256, 8 coils, 5x5, r = 75)",
+           "prec": "fp32", "ser_db_zero_filled": round(O.ser_db(pb.x_full, pb.x0), 4),
+           "schedule": "CO 64x64 50x5, then full 10x10; p applied to both stages", "p_sweep": [], "co_jl": []}
+    for p in (1, 2, 4, 8, 32, n - pb.rank):
+        res["p_sweep"].append({"p": p, "curve": curve(True, p, p, False)})
+    res["p_sweep"].append({"p": "exact (no JL)", "curve": curve(True, 1, 1, True)})
+    for co_on in (True, False):
+        for jl_on in (True, False):
+            res["co_jl"].append({"co": co_on, "jl": jl_on, "curve": curve(co_on, 8, 32, not jl_on)})
+    torch.cuda.synchronize()
+    hicu.hicu_check(h)
+    h.close()
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 # -------------------------------------------------------------------- GPU arm
 
 def timed_recons(one, steps, flush, stream):
@@ -704,9 +774,13 @@ def main():
                          "slice; cine: 192x144x24 frames x 8 coils, 5x5x5 kernel, circular time; "
                          "batch: the uneven 52-slice batch")
     ap.add_argument("--lanes", type=int, default=8, help="worker lanes of the batched workload")
+    ap.add_argument("--ablation", action="store_true",
+                    help="the JL p-sweep and CO x JL ablation on the brain slice (one JSON object, no bench line)")
     args = ap.parse_args()
     if args.profile:
         return run_profile_case(args.profile, args.size)
+    if args.ablation:
+        return run_ablation(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -138,6 +138,14 @@ typedef struct {
                                 a stage whose region is the whole array (Discussion); 0 = off.
                                 Under hard data consistency the observed samples are restored
                                 after it */
+  int32_t jl_exact;          /* 1: no JL compression (the stages' p are ignored): every descent step
+                                uses the whole null space, Q~ = Q (HICU_JL_NULLSPACE, n - r
+                                filters) or Q~ = I - V V^H (the principal-subspace route, n
+                                filters; the same Q~ Q~^H = Q Q^H), i.e. the exact gradient of
+                                ||H(y) Q||^2; 0: JL draws (Algorithm 1 step 6).  A bank
+                                that large exceeds the split-BF16 adjoint's shared memory
+                                (at most 64 filters of a 5 x 5 kernel, 8 of a 5 x 5 x 5):
+                                HICU_ERR_UNSUPPORTED there, use HICU_FP32 */
 } hicu_params;
 
 /* Optional per-iteration log, HOST arrays (any may be NULL). */

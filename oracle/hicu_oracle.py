@@ -589,6 +589,7 @@ def reconstruct(x0: np.ndarray, mask: np.ndarray, geom: Geom, stages: Sequence[S
     For i = 1..I: null space of H^(i-1)(x^(i-1)) (step 2 names the previous region;
     ``gram_on="current"`` uses S^(i) instead), then G^(i) descent steps on S^(i), each with a
     fresh JL draw (counter = global step index, starting at 0).
+    jl_mode "exact": no JL compression, every step uses the whole null basis Q as its filters.
     lam > 0: soft data consistency with that multiplier (gd_step_soft) instead of hard data
     consistency.  tau > 0: after every descent step of a stage whose region is the whole array,
     the l1 proximal step soft_threshold (Discussion), followed under hard data consistency by
@@ -608,9 +609,13 @@ def reconstruct(x0: np.ndarray, mask: np.ndarray, geom: Geom, stages: Sequence[S
             rows = Q.shape[0] if jl_mode == "projector" else Q.shape[1]
             whole = tuple(st.region.off) == (0, 0, 0) and tuple(st.region.ext) == tuple(geom.dims)
             for _ in range(st.gd_steps):
-                P = jl_matrix(seed, counter, rows, st.p)
+                if jl_mode == "exact":
+                    # no JL compression: the n - r columns of Q are the filters (exact gradient)
+                    f = as_filters(Q.T.copy(), geom)
+                else:
+                    P = jl_matrix(seed, counter, rows, st.p)
+                    f = as_filters(jl_compress(Q, P, jl_mode), geom)
                 counter += 1
-                f = as_filters(jl_compress(Q, P, jl_mode), geom)
                 if lam > 0.0:
                     y, info = gd_step_soft(y, x0, mask, geom, st.region, f, lam)
                 else:

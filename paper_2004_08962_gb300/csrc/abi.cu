@@ -843,7 +843,7 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
     s = make_conv_geom(h, geom, &stg.region, &g);
     if (s) return s;
     if (stg.iters < 0 || stg.gd_steps < 0) return set_error(h, HICU_ERR_ARG, "reconstruct: negative count");
-    if (stg.p < 1 || (prm->jl == HICU_JL_NULLSPACE && stg.p > nr))
+    if (!prm->jl_exact && (stg.p < 1 || (prm->jl == HICU_JL_NULLSPACE && stg.p > nr)))
       return set_error(h, HICU_ERR_RANK, "reconstruct: p must be in [1, n-r]");
     total_iters += stg.iters;
     total_steps += (long long)stg.iters * stg.gd_steps;
@@ -889,8 +889,15 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
   if (s) return s;
   double* dstats = (double*)ws_get(h, WS_REC_STATS, sizeof(double) * 4 * (total_steps + 1), &s);
   if (s) return s;
+  if (prm->jl_exact != 0 && prm->jl_exact != 1) return set_error(h, HICU_ERR_ARG, "reconstruct: jl_exact is 0 or 1");
+  // the JL basis (principal vectors, or the null basis), its matrices' row count, and with jl_exact
+  // the filter count of the uncompressed gradient (identity P: Q~ = I - V V^H, or Q~ = Q)
+  const int64_t nq = principal ? r : nr;
+  const int jmode = principal ? HICU_JL_COMPLEMENT : prm->jl;
+  const int64_t prow = (jmode == HICU_JL_NULLSPACE) ? nq : n;
+  const int p_exact = (int)prow;
   int pmax = 1;
-  for (int i = 0; i < prm->nstages; ++i) pmax = std::max(pmax, (int)prm->stages[i].p);
+  for (int i = 0; i < prm->nstages; ++i) pmax = std::max(pmax, prm->jl_exact ? p_exact : (int)prm->stages[i].p);
   float* bank = (float*)ws_get(h, WS_BANK, sizeof(float2) * (size_t)pmax * n_box, &s);
   if (s) return s;
   float* bank_sup = nullptr;   // JL filters on the support of the kernel mask, before the scatter
@@ -904,18 +911,16 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
                     geom->ncoil, (int)geom->dim[0], (int)geom->dim[1], (int)geom->dim[2], (float2*)y, m,
                     geom->mask_per_coil ? geom->dim[0] * geom->dim[1] * geom->dim[2] : 0));
   }
-  // the JL basis (principal vectors, or the null basis) and its matrices' row count
-  const int64_t nq = principal ? r : nr;
-  const int jmode = principal ? HICU_JL_COMPLEMENT : prm->jl;
-  const int64_t prow = (jmode == HICU_JL_NULLSPACE) ? nq : n;
   size_t pbatch = 0;
   for (int i = 0; i < prm->nstages; ++i)
     pbatch = std::max(pbatch, (size_t)prm->stages[i].gd_steps * (size_t)prow * (size_t)prm->stages[i].p);
+  if (prm->jl_exact) pbatch = (size_t)prow * prow;
   float* Pall = nullptr;
   if (pbatch > 0) {
     Pall = (float*)ws_get(h, WS_REC_P, sizeof(float) * pbatch, &s);
     if (s) return s;
     if ((s = ensure_side_stream(h))) return s;
+    if (prm->jl_exact && (s = jl_identity(h, prow, Pall, st))) return s;
   }
   uint64_t counter = 0;
   long long it = 0;
@@ -931,7 +936,8 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
       // the JL matrices of this outer iteration's descent steps depend on nothing but the seed and
       // the step counter: drawn on the side stream beside the Gram and the eigen-solve (after the
       // previous iteration's steps, the last readers of the buffer)
-      if (stg.gd_steps > 0) {
+      const int pst = prm->jl_exact ? p_exact : stg.p;   // filters per descent step
+      if (stg.gd_steps > 0 && !prm->jl_exact) {
         cudaError_t ce = cudaEventRecord(h->draw_fork, st);
         if (ce == cudaSuccess) ce = cudaStreamWaitEvent(h->side_st, h->draw_fork, 0);
         if (ce != cudaSuccess) return cuda_error(h, ce, "reconstruct: draw fork");
@@ -958,23 +964,26 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
       float2* Qf = nullptr;
       if (stg.gd_steps > 0) {
         if ((s = jl_convert_q(h, n, nq, Q, &Qf, st))) return s;
-        const cudaError_t ce = cudaStreamWaitEvent(st, h->draw_join, 0);
-        if (ce != cudaSuccess) return cuda_error(h, ce, "reconstruct: draw wait");
+        if (!prm->jl_exact) {
+          const cudaError_t ce = cudaStreamWaitEvent(st, h->draw_join, 0);
+          if (ce != cudaSuccess) return cuda_error(h, ce, "reconstruct: draw wait");
+        }
       }
       for (int j = 0; j < stg.gd_steps; ++j) {
-        s = launch_jl_converted(h, n, nq, stg.p, Qf, jmode, nullptr, Pall + (size_t)j * prow * stg.p, prm->seed,
-                                counter, prm->kernel_mask ? bank_sup : bank, st, j > 0);
+        const float* Pj = prm->jl_exact ? Pall : Pall + (size_t)j * prow * stg.p;
+        s = launch_jl_converted(h, n, nq, pst, Qf, jmode, nullptr, Pj, prm->seed, counter,
+                                prm->kernel_mask ? bank_sup : bank, st, j > 0);
         if (s) return s;
         if (prm->kernel_mask &&
-            (s = launch_support_scatter(h, stg.p, geom->ncoil, geom->k[0] * geom->k[1] * geom->k[2], nk, inv,
+            (s = launch_support_scatter(h, pst, geom->ncoil, geom->k[0] * geom->k[1] * geom->k[2], nk, inv,
                                         (const float2*)bank_sup, (float2*)bank, st)))
           return s;
         if (soft) {
-          s = gd_step_filters_soft(h, geom, &stg.region, y, m, x0c, prm->dc_weight, bank, stg.p,
+          s = gd_step_filters_soft(h, geom, &stg.region, y, m, x0c, prm->dc_weight, bank, pst,
                                    dstats + 4 * counter, prm->prec, st);
         } else {
           // the update leaves the split planes of y for the next step of the same region
-          s = gd_step_filters(h, geom, &stg.region, y, m, bank, stg.p, dstats + 4 * counter, prm->prec, st,
+          s = gd_step_filters(h, geom, &stg.region, y, m, bank, pst, dstats + 4 * counter, prm->prec, st,
                               planes_valid, true);
           planes_valid = true;
         }

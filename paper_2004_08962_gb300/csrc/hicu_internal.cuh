@@ -369,6 +369,8 @@ hicu_status launch_jl_converted(hicu_handle* h, int64_t n, int64_t nr, int p, co
 // rows x p, into P (float, draw-major)
 hicu_status jl_draw(hicu_handle* h, int64_t rows, int p, int nsteps, uint64_t seed, uint64_t counter, float* P,
                     cudaStream_t st);
+// the rows x rows identity as a JL matrix (no compression: the exact gradient)
+hicu_status jl_identity(hicu_handle* h, int64_t rows, float* P, cudaStream_t st);
 // the handle's side stream and its events, created on first use
 hicu_status ensure_side_stream(hicu_handle* h);
 // planes_valid: the split planes of y on this region are current (TC path); keep_planes: the update

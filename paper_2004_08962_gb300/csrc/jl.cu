@@ -196,6 +196,22 @@ hicu_status jl_draw(hicu_handle* h, int64_t rows, int p, int nsteps, uint64_t se
   return cuda_error(h, cudaGetLastError(), "jl draw");
 }
 
+namespace {
+__global__ void jl_identity_kernel(int rows, float* __restrict__ P) {
+  const long long tot = (long long)rows * rows;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x)
+    P[i] = (i / rows == i % rows) ? 1.f : 0.f;
+}
+}  // namespace
+
+hicu_status jl_identity(hicu_handle* h, int64_t rows, float* P, cudaStream_t st) {
+  const long long tot = rows * rows;
+  int blocks = (int)((tot + 255) / 256);
+  if (blocks > 4 * h->num_sms) blocks = 4 * h->num_sms;
+  HICU_LAUNCH(h, K_JL, st, jl_identity_kernel<<<blocks, 256, 0, st>>>((int)rows, P));
+  return cuda_error(h, cudaGetLastError(), "jl identity");
+}
+
 hicu_status jl_convert_q(hicu_handle* h, int64_t n, int64_t nr, const double* Q, float2** Qf, cudaStream_t st) {
   hicu_status s = HICU_OK;
   *Qf = (float2*)ws_get(h, WS_QF, sizeof(float2) * nr * n, &s);

@@ -53,7 +53,8 @@ class hicu_params(ctypes.Structure):
     _fields_ = [("rank", c_int64), ("nstages", c_int32), ("stages", POINTER(hicu_stage)),
                 ("seed", c_uint64), ("jl", c_int32), ("prec", c_int32),
                 ("gram_on_current", c_int32), ("init", c_int32), ("eig_solver", c_int32),
-                ("kernel_mask", c_void_p), ("dc_weight", c_double), ("l1_threshold", c_double)]
+                ("kernel_mask", c_void_p), ("dc_weight", c_double), ("l1_threshold", c_double),
+                ("jl_exact", c_int32)]
 
 
 class hicu_log(ctypes.Structure):
@@ -547,12 +548,13 @@ def hicu_gd_step(h: Handle, geom, region, y: torch.Tensor, mask: Optional[torch.
 
 def make_params(rank: int, stages, seed: int = 0, jl: int = HICU_JL_PROJECTOR, prec: int = HICU_FP32,
                 gram_on_current: bool = False, init: int = 0, eig_solver: Optional[str] = None,
-                kernel_mask=None, dc_weight: float = 0.0, l1_threshold: float = 0.0):
+                kernel_mask=None, dc_weight: float = 0.0, l1_threshold: float = 0.0, jl_exact: bool = False):
     """stages: sequence of (off, ext, iters, gd_steps, p).  eig_solver: None (the library's
     default: tridiagonal principal subspace in projector mode, else Jacobi by size), "grid",
     "cluster" (Jacobi) or "tridiag".  kernel_mask: optional (kz, ky, kx) {0,1} array over the
     kernel's box (the shape is checked by hicu_reconstruct's binding).  dc_weight: lambda of soft
-    data consistency (0 = hard); l1_threshold: tau of the l1 step (0 = off)."""
+    data consistency (0 = hard); l1_threshold: tau of the l1 step (0 = off); jl_exact: no JL
+    compression (every step uses the whole null space: the exact gradient)."""
     arr = (hicu_stage * len(stages))()
     for i, (off, ext, iters, gd, p) in enumerate(stages):
         arr[i].region = make_region(off, ext)
@@ -570,6 +572,7 @@ def make_params(rank: int, stages, seed: int = 0, jl: int = HICU_JL_PROJECTOR, p
     prm.init = int(init)
     prm.eig_solver = {None: 0, "grid": HICU_NULLSPACE_GRID, "cluster": HICU_NULLSPACE_CLUSTER,
                       "tridiag": HICU_NULLSPACE_TRIDIAG}[eig_solver]
+    prm.jl_exact = 1 if jl_exact else 0
     prm.dc_weight = float(dc_weight)
     prm.l1_threshold = float(l1_threshold)
     prm._keep = arr  # keep the stage array alive with the struct

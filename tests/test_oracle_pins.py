@@ -728,3 +728,21 @@ def test_soft_dc_and_l1_reconstructions():
     xl = O.reconstruct(x0, mask, geom, st[:1], r=L, seed=1, tau=1e-4)
     np.testing.assert_array_equal(xl[m4], x0[m4])
     assert O.ser_db(x_true, xl) > O.ser_db(x_true, x0) + 10.0
+
+
+def test_exact_gradient_mode_is_the_full_null_space_objective():
+    """jl_mode "exact" (no JL compression, the whole null basis as filters): every descent step
+    lowers ||H(y) Q||_F^2 = J for the outer iteration's Q, and its objective before the first step
+    equals J of Eq. 1 (the tail of the Gram's spectrum)."""
+    rng = np.random.default_rng(6)
+    x_true = lowrank_exponential_kspace(rng, (1, 14, 13), 2, 4) + 0.05 * random_complex(rng, (2, 1, 14, 13))
+    mask = (rng.random((1, 14, 13)) < 0.5).astype(np.uint8)
+    x0 = x_true * mask[None]
+    geom = O.Geom((13, 14, 1), 2, (3, 3, 1))
+    st = [O.StageSpec(O.full_region(geom), iters=3, gd_steps=4, p=1)]
+    log = O.ReconLog([], [], [])
+    O.reconstruct(x0, mask, geom, st, r=5, seed=1, jl_mode="exact", log=log)
+    for i in range(3):
+        objs = log.objective[4 * i:4 * i + 4]
+        assert abs(objs[0] - log.J[i]) < 1e-9 * log.J[0]
+        assert all(b <= a * (1 + 1e-12) for a, b in zip(objs, objs[1:]))
