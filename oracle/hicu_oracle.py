@@ -427,6 +427,28 @@ def jl_compress(Q: np.ndarray, P: np.ndarray, mode: str = "nullspace") -> np.nda
     return Qt.T.copy()
 
 
+def qplus_matrix(Q0: np.ndarray, blocks: int) -> np.ndarray:
+    """Q+ = blockdiag(Q0, ..., Q0) with `blocks` repetitions (Methods, Study IV: the null space is
+    augmented to [Q | Q+] with the null vectors Q0 of the non-diffusion (b0) data, one block per
+    shot).  Q0 is n0 x m0 over one shot's channels (coil, then kernel offset); the shots' channels
+    are consecutive in the filter order [channel][offset], so block s covers filter indices
+    [s n0, (s + 1) n0)."""
+    n0, m0 = Q0.shape
+    out = np.zeros((blocks * n0, blocks * m0), dtype=np.complex128)
+    for b in range(blocks):
+        out[b * n0:(b + 1) * n0, b * m0:(b + 1) * m0] = Q0
+    return out
+
+
+def jl_compress_augmented(Q: np.ndarray, Qplus: np.ndarray, P: np.ndarray, mode: str = "projector") -> np.ndarray:
+    """Q~ = [Q | Q+] P for the augmented null space (Algorithm 1 step 6 with step 3's basis
+    [Q | Q+]): the first rows of P compress Q as jl_compress does, the last Q+.shape[1] rows
+    multiply Q+.  E[Q~ Q~^H] = Q Q^H + Q+ Q+^H.  Returns (p, n)."""
+    m = Qplus.shape[1]
+    head, tail = P[:P.shape[0] - m], P[P.shape[0] - m:]
+    return jl_compress(Q, head, mode) + (Qplus @ tail).T
+
+
 def as_filters(Qt_pn: np.ndarray, geom: Geom) -> np.ndarray:
     """p filters of length n (coil, then the support offsets) as arrays (p, C, kz, ky, kx) over the
     kernel's box, zero outside the support of K."""
@@ -583,13 +605,16 @@ def initial_estimate(x0: np.ndarray, mask: np.ndarray, mode: str = "zero_filled"
 def reconstruct(x0: np.ndarray, mask: np.ndarray, geom: Geom, stages: Sequence[StageSpec], r: int,
                 seed: int, jl_mode: str = "projector", gram_on: str = "previous",
                 init: str = "zero_filled", log: Optional[ReconLog] = None, lam: float = 0.0,
-                tau: float = 0.0) -> np.ndarray:
+                tau: float = 0.0, qplus: Optional[Tuple[np.ndarray, int]] = None) -> np.ndarray:
     """Algorithm 1 (HICU) with the Gram route for steps 2-3 and centre-out stages.
 
     For i = 1..I: null space of H^(i-1)(x^(i-1)) (step 2 names the previous region;
     ``gram_on="current"`` uses S^(i) instead), then G^(i) descent steps on S^(i), each with a
     fresh JL draw (counter = global step index, starting at 0).
     jl_mode "exact": no JL compression, every step uses the whole null basis Q as its filters.
+    qplus = (Q0, blocks): the augmented null space [Q | Q+] of the multi-shot study (qplus_matrix);
+    each step's JL matrix has Q+.shape[1] more rows (jl_compress_augmented), or without
+    compression the filters are the columns of [Q | Q+].
     lam > 0: soft data consistency with that multiplier (gd_step_soft) instead of hard data
     consistency.  tau > 0: after every descent step of a stage whose region is the whole array,
     the l1 proximal step soft_threshold (Discussion), followed under hard data consistency by
@@ -608,13 +633,19 @@ def reconstruct(x0: np.ndarray, mask: np.ndarray, geom: Geom, stages: Sequence[S
             y = x
             rows = Q.shape[0] if jl_mode == "projector" else Q.shape[1]
             whole = tuple(st.region.off) == (0, 0, 0) and tuple(st.region.ext) == tuple(geom.dims)
+            Qp = None if qplus is None else qplus_matrix(qplus[0], qplus[1])
+            mplus = 0 if Qp is None else Qp.shape[1]
             for _ in range(st.gd_steps):
                 if jl_mode == "exact":
-                    # no JL compression: the n - r columns of Q are the filters (exact gradient)
-                    f = as_filters(Q.T.copy(), geom)
-                else:
+                    # no JL compression: the n - r columns of Q (and of Q+) are the filters
+                    basis = Q if Qp is None else np.concatenate([Q, Qp], axis=1)
+                    f = as_filters(basis.T.copy(), geom)
+                elif Qp is None:
                     P = jl_matrix(seed, counter, rows, st.p)
                     f = as_filters(jl_compress(Q, P, jl_mode), geom)
+                else:
+                    P = jl_matrix(seed, counter, rows + mplus, st.p)
+                    f = as_filters(jl_compress_augmented(Q, Qp, P, jl_mode), geom)
                 counter += 1
                 if lam > 0.0:
                     y, info = gd_step_soft(y, x0, mask, geom, st.region, f, lam)

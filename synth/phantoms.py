@@ -322,6 +322,49 @@ def make_batch(seed: int = 4000, n_plain: int = 48, n_dwi: int = 4, sizes=(128, 
     return out
 
 
+def make_msdwi(seed: int = 5000, n: int = 256, C: int = 8, S: int = 4, pf: float = 0.59,
+               co_iters: int = 50, co_steps: int = 5, pf_steps: int = 100, rank: int = 45):
+    """Multi-shot diffusion slice shaped like the paper's Study IV, and its non-diffusion (b0) data.
+
+    Diffusion-weighted data: one image (ellipses), C coil maps, S interleaved EPI shots each with its
+    own smooth random phase (the shot-to-shot motion phase), stacked as S*C channels [shot][coil].
+    Shot s samples the phase-encode lines s, s + S, ... (uniform downsampling) inside the
+    partial-Fourier extent: lines [round((1 - pf) n), n) (the first (1 - pf) n lines are never
+    sampled).  The b0 data: a second image (the same ellipses, other intensities) with one smooth
+    phase, fully sampled, C coils (the four shots of the non-diffusion scan summed).
+    Schedule (Methods, Study IV): centre-out on the central n/4 x n/4 region for co_iters
+    iterations of co_steps descent steps (p = C), then the partial-Fourier sampled region with
+    pf_steps steps.  Returns (Problem, x_b0)."""
+    rng = np.random.default_rng(seed)
+    base = np.random.default_rng(int(rng.integers(0, 2 ** 63)))
+    img = ellipse_image_2d(np.random.default_rng(int(base.integers(0, 2 ** 63))), n, n, 12)
+    maps = coil_maps(rng, (n, n), C)
+    yy, xx = _grid((n, n))
+    y0 = int(round((1.0 - pf) * n))
+    chans, masks = [], []
+    for s in range(S):
+        ph = np.exp(1j * _smooth_phase(rng, (yy, xx), order=1, amp=np.pi))
+        k = centered_fft(maps * (img * ph)[None], axes=(-2, -1))
+        chans.append(_noisy(rng, k, 1e-3))
+        m = np.zeros((n, n), dtype=np.uint8)
+        lines = np.arange(n)
+        m[(lines % S == s) & (lines >= y0), :] = 1
+        masks.append(np.repeat(m[None], C, axis=0))
+    k = np.concatenate(chans)[:, None].astype(np.complex64)     # (S*C, 1, n, n)
+    mask = np.concatenate(masks)[:, None]                       # per-channel mask
+    # b0: same anatomy, different contrast, one phase, fully sampled
+    rb = np.random.default_rng(int(rng.integers(0, 2 ** 63)))
+    img0 = ellipse_image_2d(np.random.default_rng(int(base.integers(0, 2 ** 63))), n, n, 12) * 0.5 + img
+    ph0 = np.exp(1j * _smooth_phase(rb, (yy, xx), order=1, amp=np.pi / 2))
+    x_b0 = _noisy(rb, centered_fft(maps * (img0 * ph0)[None], axes=(-2, -1)), 1e-3)[:, None].astype(np.complex64)
+    co_off, co_ext = _co_region((n, n, 1), ())
+    stages = [Stage(co_off, co_ext, iters=co_iters, gd_steps=co_steps, p=C),
+              Stage((0, y0, 0), (n, n - y0, 1), iters=1, gd_steps=pf_steps, p=C)]
+    pb = Problem(f"msdwi_{n}_c{S * C}", k, mask, (k * mask).astype(np.complex64), (5, 5, 1), (0, 0, 0), rank,
+                 stages, seed)
+    return pb, x_b0
+
+
 def lowrank_exponential_kspace(rng, shape, ncoil, n_terms):
     """Exactly low-rank multi-coil k-space: every coil is a sum of the same n_terms complex
     exponentials with coil-specific amplitudes, so any block-Hankel matrix built from it

@@ -746,3 +746,65 @@ def test_exact_gradient_mode_is_the_full_null_space_objective():
         objs = log.objective[4 * i:4 * i + 4]
         assert abs(objs[0] - log.J[i]) < 1e-9 * log.J[0]
         assert all(b <= a * (1 + 1e-12) for a, b in zip(objs, objs[1:]))
+
+
+# ------------------------------------------- augmented null space (Methods, Study IV)
+
+
+def test_qplus_is_block_diagonal():
+    import scipy.linalg
+    rng = np.random.default_rng(1)
+    Q0 = random_complex(rng, (6, 3))
+    np.testing.assert_array_equal(O.qplus_matrix(Q0, 4), scipy.linalg.block_diag(Q0, Q0, Q0, Q0))
+
+
+def test_augmented_jl_mean_and_exact_objective():
+    """E[Q~ Q~^H] = Q Q^H + Q+ Q+^H for Q~ = [Q | Q+] P (Monte Carlo over the generator's draws),
+    and without compression the first step's objective is ||H Q||^2 + ||H Q+||^2."""
+    rng = np.random.default_rng(2)
+    C, S = 2, 2
+    geom = O.Geom((9, 8, 1), C * S, (3, 2, 1))
+    n0 = C * 3 * 2
+    x = random_complex(rng, (C * S, 1, 8, 9))
+    reg = O.full_region(geom)
+    G = O.gram(x, geom, reg)
+    r = 10
+    Q, _ = O.nullspace(G, r)
+    Q0, _ = np.linalg.qr(random_complex(rng, (n0, 3)))
+    Qp = O.qplus_matrix(Q0, S)
+    acc = np.zeros((geom.n, geom.n), dtype=np.complex128)
+    draws = 3000
+    for t in range(draws):
+        P = O.jl_matrix(9, t, geom.n + Qp.shape[1], 4)
+        Qt = O.jl_compress_augmented(Q, Qp, P, "projector").T
+        acc += Qt @ Qt.conj().T
+    want = Q @ Q.conj().T + Qp @ Qp.conj().T
+    assert np.linalg.norm(acc / draws - want) < 0.06 * np.linalg.norm(want)
+    # exact mode: objective of the first step = ||H Q||^2 + ||H Q+||^2
+    Hx = brute_hankel(x, geom, reg)
+    mask = np.ones((1, 8, 9), dtype=np.uint8)
+    mask[0, 3, 4] = 0
+    log = O.ReconLog([], [], [])
+    O.reconstruct(x * mask[None], mask, geom, [O.StageSpec(reg, 1, 1, 1)], r, seed=0, jl_mode="exact",
+                  qplus=(Q0, S), log=log)
+    H0 = brute_hankel(x * mask[None], geom, reg)
+    Qm, _ = O.nullspace(O.gram(x * mask[None], geom, reg), r)
+    want_obj = np.linalg.norm(H0 @ Qm) ** 2 + np.linalg.norm(H0 @ Qp) ** 2
+    assert abs(log.objective[0] - want_obj) < 1e-9 * want_obj
+
+
+def test_qplus_from_b0_annihilates_shots_that_share_its_structure():
+    """Shots whose k-space is the b0 k-space times a per-shot unit scalar (the same sums of
+    exponentials per coil) are annihilated by the b0 null vectors: ||H(x) Q+|| ~ 0 in closed form."""
+    rng = np.random.default_rng(7)
+    C, S, L = 2, 3, 4
+    xb0 = lowrank_exponential_kspace(rng, (1, 14, 15), C, L)
+    g0 = O.Geom((15, 14, 1), C, (3, 3, 1))
+    G0 = O.gram(xb0, g0, O.full_region(g0))
+    Q0, w0 = O.nullspace(G0, L)                      # n0 - L null vectors
+    phases = np.exp(2j * np.pi * rng.random(S))
+    x = np.concatenate([xb0 * ph for ph in phases])  # (S*C, 1, 14, 15)
+    geom = O.Geom((15, 14, 1), C * S, (3, 3, 1))
+    Hx = brute_hankel(x, geom, O.full_region(geom))
+    Qp = O.qplus_matrix(Q0, S)
+    assert np.linalg.norm(Hx @ Qp) < 1e-6 * np.linalg.norm(Hx)
