@@ -146,6 +146,16 @@ typedef struct {
                                 that large exceeds the split-BF16 adjoint's shared memory
                                 (at most 64 filters of a 5 x 5 kernel, 8 of a 5 x 5 x 5):
                                 HICU_ERR_UNSUPPORTED there, use HICU_FP32 */
+  const double* qplus;       /* augmented null space [Q | Q+] of Algorithm 1 step 3 (Methods,
+                                Study IV): Q0, complex128 [qplus_cols][n / qplus_blocks]
+                                (DEVICE; row j a null vector of one channel group's Hankel
+                                matrix, e.g. of the b0 scan: hicu_gram + hicu_nullspace), and
+                                Q+ = blockdiag(Q0, ..., Q0) over qplus_blocks consecutive equal
+                                groups of channels (the shots).  Each JL matrix gets
+                                qplus_blocks * qplus_cols more rows, which multiply Q+
+                                (Q~ = [Q | Q+] P).  NULL = no augmentation */
+  int32_t qplus_cols;        /* columns of Q0 */
+  int32_t qplus_blocks;      /* diagonal blocks of Q+ (must divide the channel count) */
 } hicu_params;
 
 /* Optional per-iteration log, HOST arrays (any may be NULL). */

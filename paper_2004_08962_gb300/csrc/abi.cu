@@ -890,12 +890,36 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
   double* dstats = (double*)ws_get(h, WS_REC_STATS, sizeof(double) * 4 * (total_steps + 1), &s);
   if (s) return s;
   if (prm->jl_exact != 0 && prm->jl_exact != 1) return set_error(h, HICU_ERR_ARG, "reconstruct: jl_exact is 0 or 1");
-  // the JL basis (principal vectors, or the null basis), its matrices' row count, and with jl_exact
-  // the filter count of the uncompressed gradient (identity P: Q~ = I - V V^H, or Q~ = Q)
+  // augmented null space [Q | Q+], Q+ = blockdiag(Q0, ...) over qplus_blocks groups of channels
+  const bool aug = prm->qplus != nullptr;
+  int n0 = 0, m0 = 0;
+  if (aug) {
+    const int nb = prm->qplus_blocks;
+    m0 = prm->qplus_cols;
+    if (nb < 1 || m0 < 1 || geom->ncoil % nb != 0)
+      return set_error(h, HICU_ERR_SHAPE, "reconstruct: qplus_blocks must divide the channels, qplus_cols >= 1");
+    n0 = (int)(n / nb);
+    if ((int64_t)n0 * nb != n || m0 > n0)
+      return set_error(h, HICU_ERR_SHAPE, "reconstruct: Q0 must have n / qplus_blocks rows and at most as many columns");
+  }
+  const int64_t mplus = aug ? (int64_t)prm->qplus_blocks * m0 : 0;
+  // the JL basis (principal vectors, or the null basis), its matrices' row count (with the rows
+  // that multiply Q+), and with jl_exact the filter count of the uncompressed gradient (identity
+  // P: Q~ = [I - V V^H | Q+], or [Q | Q+])
   const int64_t nq = principal ? r : nr;
   const int jmode = principal ? HICU_JL_COMPLEMENT : prm->jl;
-  const int64_t prow = (jmode == HICU_JL_NULLSPACE) ? nq : n;
+  const int64_t prow0 = (jmode == HICU_JL_NULLSPACE) ? nq : n;
+  const int64_t prow = prow0 + mplus;
   const int p_exact = (int)prow;
+  float2* q0f = nullptr;
+  if (aug) {
+    q0f = (float2*)ws_get(h, WS_QPLUS, sizeof(float2) * (size_t)n0 * m0, &s);
+    if (s) return s;
+    float2* tmp = nullptr;
+    if ((s = jl_convert_q(h, n0, m0, prm->qplus, &tmp, st))) return s;
+    if (cudaMemcpyAsync(q0f, tmp, sizeof(float2) * (size_t)n0 * m0, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return cuda_error(h, cudaGetLastError(), "reconstruct: Q0 copy");
+  }
   int pmax = 1;
   for (int i = 0; i < prm->nstages; ++i) pmax = std::max(pmax, prm->jl_exact ? p_exact : (int)prm->stages[i].p);
   float* bank = (float*)ws_get(h, WS_BANK, sizeof(float2) * (size_t)pmax * n_box, &s);
@@ -971,9 +995,11 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
       }
       for (int j = 0; j < stg.gd_steps; ++j) {
         const float* Pj = prm->jl_exact ? Pall : Pall + (size_t)j * prow * stg.p;
-        s = launch_jl_converted(h, n, nq, pst, Qf, jmode, nullptr, Pj, prm->seed, counter,
-                                prm->kernel_mask ? bank_sup : bank, st, j > 0);
+        float* bank_j = prm->kernel_mask ? bank_sup : bank;
+        s = launch_jl_converted(h, n, nq, pst, Qf, jmode, nullptr, Pj, prm->seed, counter, bank_j, st, j > 0);
         if (s) return s;
+        // rows prow0 .. prow-1 of the step's JL matrix multiply Q+
+        if (aug && (s = launch_jl_qplus(h, pst, n, n0, m0, q0f, Pj + (size_t)prow0 * pst, bank_j, st))) return s;
         if (prm->kernel_mask &&
             (s = launch_support_scatter(h, pst, geom->ncoil, geom->k[0] * geom->k[1] * geom->k[2], nk, inv,
                                         (const float2*)bank_sup, (float2*)bank, st)))

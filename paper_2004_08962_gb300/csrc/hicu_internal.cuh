@@ -260,6 +260,7 @@ enum Slot {
   WS_SUP,         // kernel mask maps: support offset -> box offset, box offset -> support offset or -1
   WS_BANK_SUP,    // reconstruct: filter bank on the support of K [p][C][|K|]
   WS_REC_X0,      // reconstruct: the observed data X0, kept for soft data consistency / the l1 step
+  WS_QPLUS,       // reconstruct: the augmenting null vectors Q0 in complex64
   WS_COUNT
 };
 static_assert(WS_COUNT <= hicu_handle::kSlots, "workspace slots");
@@ -371,6 +372,9 @@ hicu_status jl_draw(hicu_handle* h, int64_t rows, int p, int nsteps, uint64_t se
                     cudaStream_t st);
 // the rows x rows identity as a JL matrix (no compression: the exact gradient)
 hicu_status jl_identity(hicu_handle* h, int64_t rows, float* P, cudaStream_t st);
+// bank [p][n] += Q+ P2 for Q+ = blockdiag(Q0, ...): Q0f complex64 [m0][n0], P2 float [blocks m0][p]
+hicu_status launch_jl_qplus(hicu_handle* h, int p, int64_t n, int n0, int m0, const float2* Q0f, const float* P2,
+                            float* bank, cudaStream_t st);
 // the handle's side stream and its events, created on first use
 hicu_status ensure_side_stream(hicu_handle* h);
 // planes_valid: the split planes of y on this region are current (TC path); keep_planes: the update

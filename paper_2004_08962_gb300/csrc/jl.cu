@@ -204,6 +204,43 @@ __global__ void jl_identity_kernel(int rows, float* __restrict__ P) {
 }
 }  // namespace
 
+namespace {
+// bank[k][s n0 + i] += sum_j Q0[j][i] P2[s m0 + j][k]: the Q+ P2 part of [Q | Q+] P for the
+// block-diagonal Q+ = blockdiag(Q0, ..., Q0)
+__global__ void jl_qplus_add_kernel(int p, int n, int n0, int m0, const float2* __restrict__ Q0,
+                                    const float* __restrict__ P2, float2* __restrict__ bank) {
+  pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
+  pdl_trigger();
+  const long long tot = (long long)p * n;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(idx / n), i = (int)(idx % n);
+    const int s = i / n0, li = i % n0;
+    float ar = 0.f, ai = 0.f;
+    for (int j = 0; j < m0; ++j) {
+      const float2 q = Q0[(long long)j * n0 + li];
+      const float w = P2[(long long)(s * m0 + j) * p + k];
+      ar = fmaf(q.x, w, ar);
+      ai = fmaf(q.y, w, ai);
+    }
+    float2 b = bank[idx];
+    b.x += ar;
+    b.y += ai;
+    bank[idx] = b;
+  }
+}
+}  // namespace
+
+hicu_status launch_jl_qplus(hicu_handle* h, int p, int64_t n, int n0, int m0, const float2* Q0f, const float* P2,
+                            float* bank, cudaStream_t st) {
+  const long long tot = (long long)p * n;
+  int blocks = (int)((tot + 255) / 256);
+  if (blocks > 4 * h->num_sms) blocks = 4 * h->num_sms;
+  launch_pdl(h, K_JL, st, dim3(blocks), dim3(256), 0, jl_qplus_add_kernel, true, p, (int)n, n0, m0, Q0f, P2,
+             reinterpret_cast<float2*>(bank));
+  return cuda_error(h, cudaGetLastError(), "jl qplus");
+}
+
 hicu_status jl_identity(hicu_handle* h, int64_t rows, float* P, cudaStream_t st) {
   const long long tot = rows * rows;
   int blocks = (int)((tot + 255) / 256);

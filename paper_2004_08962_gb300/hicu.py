@@ -54,7 +54,7 @@ class hicu_params(ctypes.Structure):
                 ("seed", c_uint64), ("jl", c_int32), ("prec", c_int32),
                 ("gram_on_current", c_int32), ("init", c_int32), ("eig_solver", c_int32),
                 ("kernel_mask", c_void_p), ("dc_weight", c_double), ("l1_threshold", c_double),
-                ("jl_exact", c_int32)]
+                ("jl_exact", c_int32), ("qplus", c_void_p), ("qplus_cols", c_int32), ("qplus_blocks", c_int32)]
 
 
 class hicu_log(ctypes.Structure):
@@ -548,13 +548,16 @@ def hicu_gd_step(h: Handle, geom, region, y: torch.Tensor, mask: Optional[torch.
 
 def make_params(rank: int, stages, seed: int = 0, jl: int = HICU_JL_PROJECTOR, prec: int = HICU_FP32,
                 gram_on_current: bool = False, init: int = 0, eig_solver: Optional[str] = None,
-                kernel_mask=None, dc_weight: float = 0.0, l1_threshold: float = 0.0, jl_exact: bool = False):
+                kernel_mask=None, dc_weight: float = 0.0, l1_threshold: float = 0.0, jl_exact: bool = False,
+                qplus: Optional[torch.Tensor] = None, qplus_blocks: int = 0):
     """stages: sequence of (off, ext, iters, gd_steps, p).  eig_solver: None (the library's
     default: tridiagonal principal subspace in projector mode, else Jacobi by size), "grid",
     "cluster" (Jacobi) or "tridiag".  kernel_mask: optional (kz, ky, kx) {0,1} array over the
     kernel's box (the shape is checked by hicu_reconstruct's binding).  dc_weight: lambda of soft
     data consistency (0 = hard); l1_threshold: tau of the l1 step (0 = off); jl_exact: no JL
-    compression (every step uses the whole null space: the exact gradient)."""
+    compression (every step uses the whole null space: the exact gradient).  qplus: Q0 as a
+    complex128 CUDA tensor (m0, n / qplus_blocks) of null vectors (rows), augmenting the null space
+    with blockdiag(Q0, ..., Q0) over qplus_blocks channel groups."""
     arr = (hicu_stage * len(stages))()
     for i, (off, ext, iters, gd, p) in enumerate(stages):
         arr[i].region = make_region(off, ext)
@@ -573,6 +576,14 @@ def make_params(rank: int, stages, seed: int = 0, jl: int = HICU_JL_PROJECTOR, p
     prm.eig_solver = {None: 0, "grid": HICU_NULLSPACE_GRID, "cluster": HICU_NULLSPACE_CLUSTER,
                       "tridiag": HICU_NULLSPACE_TRIDIAG}[eig_solver]
     prm.jl_exact = 1 if jl_exact else 0
+    if qplus is not None:
+        if not (isinstance(qplus, torch.Tensor) and qplus.dtype == torch.complex128 and qplus.dim() == 2
+                and qplus.is_contiguous() and qplus.device.type == "cuda"):
+            raise ValueError("qplus must be a contiguous complex128 CUDA tensor (m0, n0)")
+        prm.qplus = qplus.data_ptr()
+        prm.qplus_cols = int(qplus.shape[0])
+        prm.qplus_blocks = int(qplus_blocks)
+        prm._keep_qplus = qplus
     prm.dc_weight = float(dc_weight)
     prm.l1_threshold = float(l1_threshold)
     prm._keep = arr  # keep the stage array alive with the struct
@@ -589,6 +600,13 @@ def hicu_reconstruct(h: Handle, geom, x0: torch.Tensor, mask: torch.Tensor, para
     """x0 / mask / x_out may live on the GPU or (pinned) on the host."""
     if getattr(params, "_keep_mask", None) is not None:
         _kmask(geom, params._keep_mask)
+    if getattr(params, "_keep_qplus", None) is not None:
+        q = params._keep_qplus
+        nb = params.qplus_blocks
+        n = hicu_filter_length(geom) if getattr(params, "_keep_mask", None) is None else \
+            hicu_support_length(geom, params._keep_mask)
+        if nb < 1 or n % nb or q.shape[1] != n // nb:
+            raise ValueError(f"qplus must have n / qplus_blocks = {n // max(nb, 1)} columns per row")
     _need(x0, "x0", torch.complex64, _kshape(geom))
     _need(mask, "mask", torch.uint8, _mshape(geom))
     if x_out is None:
