@@ -49,11 +49,15 @@ WORKLOADS = {
     "knee": ("knee3d_256x256x160", "HICU GD-iters/s (full hicu_reconstruct of one 256x256x160 8-coil volume)"),
     "brain": ("2d_brain_256", "HICU GD-iters/s (full hicu_reconstruct of one 256x256x8-coil slice)"),
     "cine": ("cine_192x144x24", "HICU GD-iters/s (full hicu_reconstruct of one 192x144x24-frame 8-coil cine)"),
+    "dwi": ("msdwi_256_c32", "HICU GD-iters/s (full hicu_reconstruct of one 256x256 multi-shot diffusion slice, "
+                             "4 shots x 8 coils, null space augmented with b0 null vectors)"),
 }
+# multi-shot diffusion slice: shots, coils per shot, b0 null vectors (Methods, Study IV)
+DWI_SHOTS, DWI_COILS, DWI_Q0 = 4, 8, 40
 # accuracy block: (scale-down factor per spatial axis, (iters, gd_steps, p) per stage) of the
 # reconstruction compared with the FP64 oracle
 ORACLE_CHECK = {"knee": (4, [(2, 2, 8), (1, 2, 8)]), "cine": (2, [(2, 2, 8), (1, 2, 8)]),
-                "brain": (2, [(10, 5, 8), (2, 5, 32)])}
+                "brain": (2, [(10, 5, 8), (2, 5, 32)]), "dwi": (4, [(3, 2, 8), (1, 4, 8)])}
 UNIT = "GD-iters/s"
 KERNEL_NAMES = {0: "gram", 1: "eig", 2: "conv_fp32", 3: "adjoint_fp32", 4: "jl", 5: "misc",
                 6: "conv_tc", 7: "adjoint_tc", 8: "tridiag"}
@@ -70,8 +74,33 @@ NCU_TRAFFIC = {}
 
 def problem_seed(workload: str, rank: int) -> int:
     """Seed of the synthetic problem of a workload on a rank (replicas reconstruct different data)."""
-    order = {"brain": 0, "cine": 1, "knee": 2}
+    order = {"brain": 0, "cine": 1, "knee": 2, "dwi": 4}
     return 1000 * (1 + order[workload]) + rank
+
+
+def workload_problem(workload: str, seed: int, scale: int = 1, sched=None):
+    """(problem, b0 k-space or None) of a workload; `scale` shrinks the spatial axes and `sched`
+    replaces the (iters, gd_steps, p) of its stages."""
+    from synth.phantoms import make_msdwi, make_problem
+    if workload == "dwi":
+        n = 256 // scale
+        pb, xb0 = make_msdwi(seed=seed, n=n, C=DWI_COILS, S=DWI_SHOTS)
+    else:
+        pb, xb0 = make_problem(WORKLOADS[workload][0], seed=seed, scale=scale), None
+    if sched is not None:
+        for st, (it, gd, p) in zip(pb.stages, sched):
+            st.iters, st.gd_steps, st.p = it, gd, p
+    return pb, xb0
+
+
+def dwi_q0_oracle(xb0):
+    """The b0 null vectors Q0 (columns) by the oracle: the DWI_Q0 smallest eigenvectors of the b0
+    Gram over the whole b0 k-space, kernel 5 x 5 over the coils."""
+    from oracle import hicu_oracle as O
+    C, nz, ny, nx = xb0.shape
+    g0 = O.Geom((nx, ny, nz), C, (5, 5, 1))
+    Q0, _ = O.nullspace(O.gram(xb0.astype(np.complex128), g0, O.full_region(g0)), g0.n - DWI_Q0)
+    return Q0
 
 
 def load_peaks():
@@ -355,8 +384,12 @@ def oracle_sample(pb, seed=11, max_outputs=40000, target_s=10.0):
 
 
 def schedule_text(pb):
-    return " + ".join(f"{'CO ' + 'x'.join(str(e) for e in st.ext if e > 1) if i == 0 else 'full'} "
-                      f"{st.iters}x{st.gd_steps} p={st.p}" for i, st in enumerate(pb.stages))
+    def reg(st):
+        if tuple(st.off) == (0, 0, 0) and tuple(st.ext) == tuple(pb.dims):
+            return "full"
+        return ("CO " if tuple(st.off) != (0,) * 3 and st.ext[1] < pb.dims[1] // 2 else "region ") + \
+            "x".join(str(e) for e in st.ext if e > 1)
+    return " + ".join(f"{reg(st)} {st.iters}x{st.gd_steps} p={st.p}" for st in pb.stages)
 
 
 def workload_config(name, pb):
@@ -388,7 +421,7 @@ def run_reference(args, rank, world):
         return 0
     from synth.phantoms import make_problem
     wname, metric = WORKLOADS[args.workload]
-    pb = make_problem(wname, seed=problem_seed(args.workload, 0))
+    pb, _ = workload_problem(args.workload, problem_seed(args.workload, 0))
     vals, descs, step_s = [], [], []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -729,20 +762,24 @@ def accuracy_block(args, pb, hicu, h, geom, x_bf16, x_fp32):
         return out
     name = WORKLOADS[args.workload][0]
     scale, sched = ORACLE_CHECK[args.workload]
-    ps = make_problem(name, scale=scale)
-    stages = [(st.off, st.ext, it, gd, p) for st, (it, gd, p) in zip(ps.stages, sched)]
+    ps, xb0 = workload_problem(args.workload, problem_seed(args.workload, 0), scale=scale, sched=sched)
+    stages = [(st.off, st.ext, st.iters, st.gd_steps, st.p) for st in ps.stages]
     init = 1 if ps.init == "time_average" else 0
     og = O.Geom(ps.dims, ps.ncoil, ps.kernel, ps.circular)
     ost = [O.StageSpec(O.Region(off, ext), it, gd, p) for off, ext, it, gd, p in stages]
+    Q0 = dwi_q0_oracle(xb0) if xb0 is not None else None
     t0 = time.perf_counter()
-    ref = O.reconstruct(ps.x0, ps.mask, og, ost, ps.rank, seed=5, jl_mode="projector", init=ps.init)
+    ref = O.reconstruct(ps.x0, ps.mask, og, ost, ps.rank, seed=5, jl_mode="projector", init=ps.init,
+                        qplus=None if Q0 is None else (Q0, DWI_SHOTS))
     t_or = time.perf_counter() - t0
-    gs = hicu.make_geom(ps.dims, ps.ncoil, ps.kernel, ps.circular)
+    gs = hicu.make_geom(ps.dims, ps.ncoil, ps.kernel, ps.circular, mask_per_coil=ps.mask.ndim == 4)
+    q0t = None if Q0 is None else torch.from_numpy(np.ascontiguousarray(Q0.T)).cuda()
     res = {"workload": f"{name} scaled 1/{scale} per spatial axis ({'x'.join(str(d) for d in ps.dims if d > 1)})",
            "schedule": " + ".join(f"{it}x{gd} p={p}" for it, gd, p in sched), "oracle_s": t_or,
            "ser_db_oracle": O.ser_db(ps.x_full, ref)}
     for tag, prec in (("split_bf16", hicu.HICU_SPLIT_BF16), ("plain_fp32", hicu.HICU_FP32)):
-        prm = hicu.make_params(ps.rank, stages, seed=5, jl=hicu.HICU_JL_PROJECTOR, prec=prec, init=init)
+        prm = hicu.make_params(ps.rank, stages, seed=5, jl=hicu.HICU_JL_PROJECTOR, prec=prec, init=init,
+                               qplus=q0t, qplus_blocks=DWI_SHOTS if q0t is not None else 0)
         x = hicu.hicu_reconstruct(h, gs, torch.from_numpy(ps.x0).cuda(), torch.from_numpy(ps.mask).cuda(),
                                   prm).cpu().numpy()
         res[tag] = {"nrmse": float(np.linalg.norm(x - ref) / np.linalg.norm(ref)),
@@ -769,10 +806,11 @@ def main():
                                                         "fgrad", "recon", "recon_knee", "gram_knee"],
                     help="run one small fixed case for an ncu capture and exit")
     ap.add_argument("--size", type=int, default=2048, help="image size of the tc_step profile case")
-    ap.add_argument("--workload", default="knee", choices=["knee", "brain", "cine", "batch"],
+    ap.add_argument("--workload", default="knee", choices=["knee", "brain", "cine", "dwi", "batch"],
                     help="knee: 256x256x160 x 8 coils, 5x5x5 kernel (default line); brain: the 256x256x8 "
-                         "slice; cine: 192x144x24 frames x 8 coils, 5x5x5 kernel, circular time; "
-                         "batch: the uneven 52-slice batch")
+                         "slice; cine: 192x144x24 frames x 8 coils, 5x5x5 kernel, circular time; dwi: a "
+                         "256x256 multi-shot diffusion slice (4 shots x 8 coils, augmented null space, "
+                         "partial-Fourier final region); batch: the uneven 52-slice batch")
     ap.add_argument("--lanes", type=int, default=8, help="worker lanes of the batched workload")
     ap.add_argument("--ablation", action="store_true",
                     help="the JL p-sweep and CO x JL ablation on the brain slice (one JSON object, no bench line)")
@@ -810,12 +848,28 @@ def main():
         build.build()
     if world > 1:
         dist.barrier()
-    pb = make_problem(wname, seed=problem_seed(args.workload, rank))
+    pb, xb0 = workload_problem(args.workload, problem_seed(args.workload, rank))
     prec = hicu.HICU_FP32 if args.prec == "fp32" else hicu.HICU_SPLIT_BF16
     h = hicu.Handle()
-    geom = hicu.make_geom(pb.dims, pb.ncoil, pb.kernel, pb.circular)
+    geom = hicu.make_geom(pb.dims, pb.ncoil, pb.kernel, pb.circular, mask_per_coil=pb.mask.ndim == 4)
     init = 1 if pb.init == "time_average" else 0
-    params = hicu.make_params(pb.rank, schedule(pb), seed=11, jl=hicu.HICU_JL_PROJECTOR, prec=prec, init=init)
+    q0, q0_ms = None, None
+    if xb0 is not None:
+        # the b0 null vectors: Gram and null space of the b0 k-space on the GPU (once per slice,
+        # before the reconstruction; timed separately)
+        c0 = xb0.shape[0]
+        g0 = hicu.make_geom(pb.dims, c0, (5, 5, 1))
+        xb0_t = torch.from_numpy(xb0).cuda()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        G0 = hicu.hicu_gram(h, g0, hicu.make_region((0, 0, 0), pb.dims), xb0_t)
+        n0 = c0 * 25
+        q0, _ = hicu.hicu_nullspace(h, G0, n0 - DWI_Q0)
+        e1.record()
+        e1.synchronize()
+        q0_ms = e0.elapsed_time(e1)
+    params = hicu.make_params(pb.rank, schedule(pb), seed=11, jl=hicu.HICU_JL_PROJECTOR, prec=prec, init=init,
+                              qplus=q0, qplus_blocks=DWI_SHOTS if q0 is not None else 0)
     x0 = torch.from_numpy(pb.x0).cuda()
     mask = torch.from_numpy(pb.mask).cuda()
     xout = torch.empty_like(x0)
@@ -868,7 +922,8 @@ def main():
     fp32_ms, fp32_steps, x_fp32 = None, 0, None
     if args.prec == "bf16":
         params32 = hicu.make_params(pb.rank, schedule(pb), seed=11, jl=hicu.HICU_JL_PROJECTOR,
-                                    prec=hicu.HICU_FP32, init=init)
+                                    prec=hicu.HICU_FP32, init=init, qplus=q0,
+                                    qplus_blocks=DWI_SHOTS if q0 is not None else 0)
         out32 = torch.empty_like(x0)
         one32 = lambda: hicu.hicu_reconstruct(h, geom, x0, mask, params32, x_out=out32)
         one32()
@@ -926,6 +981,8 @@ def main():
                 "speedup_of_split_bf16": value / fp32_value},
             "clocks": clocks,
             "peaks_source": peak_src}
+    if q0_ms is not None:
+        line["b0_null_space_ms"] = q0_ms
     if world == 1:
         line["accuracy"] = accuracy_block(args, pb, hicu, h, geom, x_main if args.prec == "bf16" else None,
                                           x_fp32)
