@@ -364,6 +364,66 @@ def tail_energy(eigvals: np.ndarray, r: int) -> float:
     return float(np.sum(eigvals[: n - r]))
 
 
+# ------------------------------------------------------- randomized SVD (Theory: rSVD)
+
+
+def complex_gaussian(seed: int, counter: int, rows: int, cols: int) -> np.ndarray:
+    """rows x cols complex Gaussian matrix of unit variance: entry (a, b) has real part
+    gaussian(seed, counter, 2 e) / sqrt(2) and imaginary part gaussian(seed, counter, 2 e + 1) / sqrt(2),
+    e = a cols + b (the same counter-based generator as the JL draws)."""
+    out = np.empty((rows, cols), dtype=np.complex128)
+    for a in range(rows):
+        for b in range(cols):
+            e = a * cols + b
+            out[a, b] = complex(gaussian(seed, counter, 2 * e), gaussian(seed, counter, 2 * e + 1)) / math.sqrt(2.0)
+    return out
+
+
+RSVD_SHIFT = 1e-11   # the stabilising shift nu of rsvd_principal, relative to ||Z||_F / sqrt(l)
+
+
+def rsvd_principal(x: np.ndarray, geom: Geom, reg: Region, r: int, l: int, seed: int, counter: int,
+                   V_prev: Optional[np.ndarray] = None) -> Tuple[np.ndarray, np.ndarray]:
+    """The r principal right singular vectors of H(x) on S by randomized SVD (Theory: rSVD, Algorithm
+    1 step 2), with a warm start.
+
+    Test matrix Omega (n x l): the previous outer iteration's principal vectors V_prev (when given),
+    then complex Gaussian columns complex_gaussian(seed, counter, n, l - r0).  One application of the
+    valid convolution and one of its conjugate transpose per column give Z = H^H (H Omega) =
+    (H^H H) Omega.  The randomized SVD of H through its Gram H^H H (the single-pass form for a
+    positive semidefinite matrix, with a small shift nu for stability):
+        Y = Z + nu Omega,   T = Omega^H Y = R^H R (Cholesky),   K = Y R^{-1},
+    so K K^H = (H^H H + nu I) Omega (Omega^H (H^H H + nu I) Omega)^{-1} Omega^H (H^H H + nu I) is the
+    rank-l approximation of H^H H + nu I from range(H^H H Omega); the top r left singular vectors of
+    K are V and their squared singular values minus nu the eigenvalue estimates.  Exact when
+    rank(H) <= l.  nu = RSVD_SHIFT ||Z||_F / sqrt(l).  Returns (V n x r, estimates ascending)."""
+    n = geom.n
+    r0 = 0 if V_prev is None else V_prev.shape[1]
+    gauss = complex_gaussian(seed, counter, n, l - r0)
+    Omega = gauss if V_prev is None else np.concatenate([V_prev, gauss], axis=1)
+    R = conv_null(x, geom, reg, as_filters(Omega.T.copy(), geom))          # H Omega, (sz, sy, sx, l)
+    Z = _support_coeffs(filter_gradient(x, geom, reg, R).reshape(l, geom.ncoil, -1), geom).T   # n x l
+    nu = RSVD_SHIFT * np.linalg.norm(Z) / math.sqrt(l)
+    Y = Z + nu * Omega
+    T = Omega.conj().T @ Y
+    T = 0.5 * (T + T.conj().T)
+    Rc = np.linalg.cholesky(T).conj().T                                   # T = Rc^H Rc, Rc upper
+    K = np.linalg.solve(Rc.T, Y.T).T                                      # K Rc = Y
+    W, sig, _ = np.linalg.svd(K, full_matrices=False)
+    lam = np.maximum(sig[:r] ** 2 - nu, 0.0)
+    return W[:, :r][:, ::-1].copy(), lam[::-1].copy()
+
+
+def _support_coeffs(F: np.ndarray, geom: Geom) -> np.ndarray:
+    """Box-layout coefficients (p, C, kz ky kx) -> the n coefficients on the support of K (p, n)."""
+    p = F.shape[0]
+    if geom.support is None:
+        return F.reshape(p, -1)
+    kx, ky, kz = geom.kernel
+    idx = [(dz * ky + dy) * kx + dx for dz, dy, dx in geom.support]
+    return F[:, :, idx].reshape(p, -1)
+
+
 # --------------------------------------------------------------- JL compression
 
 _GAMMA = 0x9E3779B97F4A7C15
@@ -605,12 +665,16 @@ def initial_estimate(x0: np.ndarray, mask: np.ndarray, mode: str = "zero_filled"
 def reconstruct(x0: np.ndarray, mask: np.ndarray, geom: Geom, stages: Sequence[StageSpec], r: int,
                 seed: int, jl_mode: str = "projector", gram_on: str = "previous",
                 init: str = "zero_filled", log: Optional[ReconLog] = None, lam: float = 0.0,
-                tau: float = 0.0, qplus: Optional[Tuple[np.ndarray, int]] = None) -> np.ndarray:
+                tau: float = 0.0, qplus: Optional[Tuple[np.ndarray, int]] = None,
+                rsvd: Optional[Tuple[int, int]] = None) -> np.ndarray:
     """Algorithm 1 (HICU) with the Gram route for steps 2-3 and centre-out stages.
 
     For i = 1..I: null space of H^(i-1)(x^(i-1)) (step 2 names the previous region;
     ``gram_on="current"`` uses S^(i) instead), then G^(i) descent steps on S^(i), each with a
     fresh JL draw (counter = global step index, starting at 0).
+    rsvd = (l, seed): the principal vectors by rsvd_principal with l test vectors, warm-started from
+    the previous outer iteration's (counter = outer iteration index), then the projector-form filters
+    (I - V V^H) P; J is logged as trace(G) - sum of the Ritz values.
     jl_mode "exact": no JL compression, every step uses the whole null basis Q as its filters.
     qplus = (Q0, blocks): the augmented null space [Q | Q+] of the multi-shot study (qplus_matrix);
     each step's JL matrix has Q+.shape[1] more rows (jl_compress_augmented), or without
@@ -623,13 +687,24 @@ def reconstruct(x0: np.ndarray, mask: np.ndarray, geom: Geom, stages: Sequence[S
     x = initial_estimate(x0, mask, init)
     counter = 0
     prev = stages[0].region
+    V = None
+    it = 0
     for st in stages:
         for _ in range(st.iters):
             greg = prev if gram_on == "previous" else st.region
-            G = gram(x, geom, greg)
-            Q, w = nullspace(G, r)
-            if log is not None:
-                log.J.append(tail_energy(w, r))
+            if rsvd is not None:
+                V, lam_r = rsvd_principal(x, geom, greg, r, rsvd[0], rsvd[1], it, V)
+                # the null space's projector I - V V^H through an orthonormal completion of V
+                Q = np.linalg.svd(np.eye(geom.n) - V @ V.conj().T)[0][:, :geom.n - r]
+                if log is not None:
+                    tr = float(np.sum(np.abs(_hankel_rows(x, geom, greg, 0, out_shape(geom, greg)[0])) ** 2))
+                    log.J.append(tr - float(np.sum(lam_r)))
+            else:
+                G = gram(x, geom, greg)
+                Q, w = nullspace(G, r)
+                if log is not None:
+                    log.J.append(tail_energy(w, r))
+            it += 1
             y = x
             rows = Q.shape[0] if jl_mode == "projector" else Q.shape[1]
             whole = tuple(st.region.off) == (0, 0, 0) and tuple(st.region.ext) == tuple(geom.dims)

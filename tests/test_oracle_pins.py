@@ -808,3 +808,76 @@ def test_qplus_from_b0_annihilates_shots_that_share_its_structure():
     Hx = brute_hankel(x, geom, O.full_region(geom))
     Qp = O.qplus_matrix(Q0, S)
     assert np.linalg.norm(Hx @ Qp) < 1e-6 * np.linalg.norm(Hx)
+
+
+# ------------------------------------------------------------ randomized SVD (Theory: rSVD)
+
+
+def _proj_dist(A, B):
+    return float(np.linalg.norm(A @ A.conj().T - B @ B.conj().T, 2))
+
+
+def test_rsvd_is_exact_up_to_its_rank_and_its_estimates_stay_below():
+    """With l >= rank of H the randomized SVD reproduces the principal subspace (exact in exact
+    arithmetic; here up to the stabilising shift), and its eigenvalue estimates never exceed the
+    true ones (the approximation K K^H - nu I is below H^H H in the Loewner order)."""
+    geom, reg, x, rng = make_case(0, 21)
+    G = O.gram(x, geom, reg)
+    w, U = np.linalg.eigh(G)
+    r = 4
+    V, lam = O.rsvd_principal(x, geom, reg, r, geom.n, seed=3, counter=0)
+    assert _proj_dist(V, U[:, -r:]) < 1e-8 * w[-1] / (w[-r] - w[-r - 1])
+    np.testing.assert_allclose(lam, w[-r:], rtol=1e-8)
+    np.testing.assert_allclose(V.conj().T @ V, np.eye(r), atol=1e-12)
+    V, lam = O.rsvd_principal(x, geom, reg, r, r + 3, seed=3, counter=1)
+    assert np.all(lam <= w[-r:] * (1 + 1e-9))
+    np.testing.assert_allclose(V.conj().T @ V, np.eye(r), atol=1e-12)
+
+
+def test_rsvd_test_matrix_products_are_the_gram_products():
+    """Z = H^H (H Omega) from one convolution and one filter gradient equals G Omega (H^H H = G),
+    including on a kernel mask's support."""
+    for geom, reg, x, rng in (make_case(1, 4), make_case(2, 5)):
+        for sup in (None, O.ellipsoid_support(geom.kernel, 1.0)):
+            g2 = O.Geom(geom.dims, geom.ncoil, geom.kernel, geom.circular, sup)
+            Om = random_complex(rng, (g2.n, 3))
+            R = O.conv_null(x, g2, reg, O.as_filters(Om.T.copy(), g2))
+            Z = O._support_coeffs(O.filter_gradient(x, g2, reg, R).reshape(3, g2.ncoil, -1), g2).T
+            np.testing.assert_allclose(Z, O.gram(x, g2, reg) @ Om, rtol=1e-11, atol=1e-11)
+
+
+def test_rsvd_recovers_exactly_low_rank_subspace_and_warm_start_converges():
+    rng = np.random.default_rng(13)
+    L = 5
+    x = lowrank_exponential_kspace(rng, (1, 12, 13), 2, L)
+    geom = O.Geom((13, 12, 1), 2, (3, 3, 1))
+    reg = O.full_region(geom)
+    w, U = np.linalg.eigh(O.gram(x, geom, reg))
+    V, lam = O.rsvd_principal(x, geom, reg, L, L + 2, seed=1, counter=0)
+    assert _proj_dist(V, U[:, -L:]) < 1e-8
+    # general data: repeated warm starts (subspace iteration) approach the principal subspace
+    geom, reg, x, rng = make_case(0, 8)
+    G = O.gram(x, geom, reg)
+    w, U = np.linalg.eigh(G)
+    r = 3
+    V, _ = O.rsvd_principal(x, geom, reg, r, r + 2, seed=2, counter=0)
+    d0 = _proj_dist(V, U[:, -r:])
+    for k in range(1, 40):
+        V, _ = O.rsvd_principal(x, geom, reg, r, r + 2, seed=2, counter=k, V_prev=V)
+    assert _proj_dist(V, U[:, -r:]) < 1e-3 * max(d0, 1e-3)
+
+
+def test_rsvd_reconstruction_recovers_exactly_low_rank_data():
+    rng = np.random.default_rng(3)
+    L = 4
+    x_true = lowrank_exponential_kspace(rng, (1, 16, 16), 2, L)
+    mask = (rng.random((1, 16, 16)) < 0.55).astype(np.uint8)
+    x0 = x_true * mask[None]
+    geom = O.Geom((16, 16, 1), 2, (3, 3, 1))
+    st = [O.StageSpec(O.full_region(geom), iters=40, gd_steps=5, p=6)]
+    log = O.ReconLog([], [], [])
+    xr = O.reconstruct(x0, mask, geom, st, r=L, seed=1, rsvd=(L + 4, 7), log=log)
+    assert O.ser_db(x_true, xr) > O.ser_db(x_true, x0) + 30.0
+    assert log.J[-1] < 1e-4 * log.J[0]
+    m4 = np.broadcast_to(mask[None], x0.shape).astype(bool)
+    np.testing.assert_array_equal(xr[m4], x0[m4])
