@@ -156,6 +156,10 @@ typedef struct {
                                 (Q~ = [Q | Q+] P).  NULL = no augmentation */
   int32_t qplus_cols;        /* columns of Q0 */
   int32_t qplus_blocks;      /* diagonal blocks of Q+ (must divide the channel count) */
+  int32_t rsvd_cols;         /* eig_solver HICU_NULLSPACE_RSVD: test vectors l (0: min(n, r +
+                                max(r/2, 8))); the previous iteration's r principal vectors are
+                                the first r of them after the first outer iteration */
+  uint64_t rsvd_seed;        /* its Gaussian test vectors: draw counter = outer iteration index */
 } hicu_params;
 
 /* Optional per-iteration log, HOST arrays (any may be NULL). */
@@ -224,6 +228,9 @@ hicu_status hicu_gram(hicu_handle* h, const hicu_geom* geom, const hicu_region* 
 #define HICU_NULLSPACE_CLUSTER_AUTO_MAX 128
 /* hicu_params.eig_solver only: principal subspace by tridiagonalisation (hicu_principal_subspace) */
 #define HICU_NULLSPACE_TRIDIAG 16
+/* hicu_params.eig_solver only: principal vectors by randomized SVD with a warm start
+   (hicu_principal_rsvd; no Gram matrix), needs jl = HICU_JL_PROJECTOR */
+#define HICU_NULLSPACE_RSVD 32
 
 /*
  * Kernel masks.  Algorithm 1 takes a {0,1} kernel mask K; a filter v lists the kernel values on
@@ -326,6 +333,30 @@ hicu_status hicu_nullspace(hicu_handle* h, int64_t n, int64_t r, const double* G
  */
 hicu_status hicu_principal_subspace(hicu_handle* h, int64_t n, int64_t r, const double* G, double* V,
                                     double* eig_top, double* eig_all, double* tail, void* stream);
+
+/*
+ * hicu_principal_rsvd - the r principal right singular vectors of H(x) on S by randomized SVD
+ * (Theory: rSVD; Algorithm 1 step 2), without the Gram matrix.  l test vectors Omega: the r0 rows
+ * of V_prev (a warm start, e.g. the previous outer iteration's V), then complex Gaussian vectors,
+ * entry a of vector r0 + b being (z(2e) + i z(2e + 1)) / sqrt(2), e = a (l - r0) + b, z the
+ * counter-based generator of hicu_jl_compress with (seed, counter).  One convolution with the l
+ * vectors as filters and one filter gradient give Z = H^H H Omega (2 l applications of H and H^H,
+ * both in complex FP32); then in FP64 the single-pass randomized SVD of H through H^H H with a
+ * stabilising shift nu = 2^-17 ||Z||_F / sqrt(l), above the rounding level of the FP32 Z:
+ *   Y = Z + nu Omega, Omega^H Y = R^H R (Cholesky), K = Y R^-1, V = the top r left singular
+ *   vectors of K, eig_top = their squared singular values - nu.
+ * Exact when rank(H) <= l.  The Cholesky factor is formed by one CTA (about l^3 / 3 FP64
+ * operations: milliseconds for l in the hundreds).
+ *   kmask   : optional HOST kernel mask (NULL = the whole box); n = C |K| or C kx ky kz
+ *   r, l    : 1 <= r < l <= min(n, 4096);  V_prev : complex128 [r0][n] (device), r0 <= l
+ *   V       : complex128 [r][n] (device) row j the vector of eig_top[j] (ascending); may be V_prev
+ *   tail    : optional device double, J = trace(H^H H) - sum(eig_top) (Eq. 1)
+ * HICU_ERR_NUMERIC (via hicu_check) if the Cholesky factorisation meets a non-positive pivot.
+ */
+hicu_status hicu_principal_rsvd(hicu_handle* h, const hicu_geom* geom, const hicu_region* region,
+                                const uint8_t* kmask, const float* x, int64_t r, int64_t l, const double* V_prev,
+                                int64_t r0, uint64_t seed, uint64_t counter, double* V, double* eig_top,
+                                double* tail, void* stream);
 
 /*
  * hicu_nullspace_info - sweeps used by the last hicu_nullspace call on this

@@ -379,7 +379,10 @@ def complex_gaussian(seed: int, counter: int, rows: int, cols: int) -> np.ndarra
     return out
 
 
-RSVD_SHIFT = 1e-11   # the stabilising shift nu of rsvd_principal, relative to ||Z||_F / sqrt(l)
+# the stabilising shift nu of rsvd_principal, relative to ||Z||_F / sqrt(l): above the rounding level
+# of an FP32 evaluation of Z = H^H H Omega (a smaller shift lets that rounding into Omega^H Y's
+# smallest directions), 2^-17
+RSVD_SHIFT = 2.0 ** -17
 
 
 def rsvd_principal(x: np.ndarray, geom: Geom, reg: Region, r: int, l: int, seed: int, counter: int,

@@ -827,13 +827,15 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
       !std::isfinite(prm->l1_threshold))
     return set_error(h, HICU_ERR_ARG, "reconstruct: dc_weight and l1_threshold must be finite and >= 0");
   if (prm->eig_solver != 0 && prm->eig_solver != HICU_NULLSPACE_GRID && prm->eig_solver != HICU_NULLSPACE_CLUSTER &&
-      prm->eig_solver != HICU_NULLSPACE_TRIDIAG)
+      prm->eig_solver != HICU_NULLSPACE_TRIDIAG && prm->eig_solver != HICU_NULLSPACE_RSVD)
     return set_error(h, HICU_ERR_ARG, "reconstruct: unknown eig_solver");
-  if (prm->eig_solver == HICU_NULLSPACE_TRIDIAG && prm->jl != HICU_JL_PROJECTOR)
-    return set_error(h, HICU_ERR_ARG, "reconstruct: the tridiagonal solver needs jl = HICU_JL_PROJECTOR");
+  if ((prm->eig_solver == HICU_NULLSPACE_TRIDIAG || prm->eig_solver == HICU_NULLSPACE_RSVD) &&
+      prm->jl != HICU_JL_PROJECTOR)
+    return set_error(h, HICU_ERR_ARG, "reconstruct: the principal-vector solvers need jl = HICU_JL_PROJECTOR");
   // principal vectors V and complement filters (I - V V^H) P: the projector-mode filters
-  const bool principal = prm->jl == HICU_JL_PROJECTOR &&
-                         (prm->eig_solver == 0 || prm->eig_solver == HICU_NULLSPACE_TRIDIAG);
+  const bool principal = prm->jl == HICU_JL_PROJECTOR && (prm->eig_solver == 0 || prm->eig_solver == HICU_NULLSPACE_TRIDIAG ||
+                                                          prm->eig_solver == HICU_NULLSPACE_RSVD);
+  const bool rsvd = prm->eig_solver == HICU_NULLSPACE_RSVD;
   hicu_status s = check_prec(h, prm->prec);
   if (s) return s;
   long long total_iters = 0, total_steps = 0;
@@ -970,11 +972,21 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
           return cuda_error(h, ce, "reconstruct: draw join");
       }
       const hicu_region& greg = prm->gram_on_current ? stg.region : prev;
-      s = run_gram(h, geom, &greg, y, G, st, sup, nk);
-      if (s) return s;
+      if (rsvd) {
+        // randomized SVD of H on the previous region, warm-started from the last principal vectors
+        const int64_t l = prm->rsvd_cols > 0 ? prm->rsvd_cols : std::min<int64_t>(n, r + std::max<int64_t>(r / 2, 8));
+        s = run_rsvd(h, geom, &greg, prm->kernel_mask, y, r, l, it > 0 ? Q : nullptr, it > 0 ? r : 0, prm->rsvd_seed,
+                     (uint64_t)it, Q, eig, dlog + it, st);
+        if (s) return s;
+      } else {
+        s = run_gram(h, geom, &greg, y, G, st, sup, nk);
+        if (s) return s;
+      }
       // after the first outer iteration: warm start, and stop at the top-r / rest split (step 3
       // needs an orthonormal basis of the complement of the r principal vectors, nothing more)
-      if (principal) {
+      if (rsvd) {
+        // V and J came from the randomized SVD
+      } else if (principal) {
         // Q (here: the r principal vectors) and J of Eq. 1 directly
         s = run_principal(h, n, r, G, Q, eig, nullptr, dlog + it, st);
         if (s) return s;

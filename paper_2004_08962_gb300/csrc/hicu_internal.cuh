@@ -176,7 +176,7 @@ struct hicu_handle {
   int num_sms = 0;
   bool pdl = true;  // programmatic dependent launches (HICU_PDL=0 turns them off)
   std::string last_error;
-  static constexpr int kSlots = 40;
+  static constexpr int kSlots = 48;
   hicu::Workspace ws[kSlots];
   int* dev_err = nullptr;          // device error word
   unsigned* dev_sync = nullptr;    // grid-barrier words (count, gen)
@@ -261,6 +261,15 @@ enum Slot {
   WS_BANK_SUP,    // reconstruct: filter bank on the support of K [p][C][|K|]
   WS_REC_X0,      // reconstruct: the observed data X0, kept for soft data consistency / the l1 step
   WS_QPLUS,       // reconstruct: the augmenting null vectors Q0 in complex64
+  WS_RS_OMEGA,    // randomized SVD: test vectors [l][n] (complex128)
+  WS_RS_BANK,     // randomized SVD: test vectors as complex64 filters / the support's coefficients of Z
+  WS_RS_BOX,      // randomized SVD: box-layout filters (kernel mask)
+  WS_RS_R,        // randomized SVD: H Omega [s][l]
+  WS_RS_Y,        // randomized SVD: Y = Z + nu Omega
+  WS_RS_K,        // randomized SVD: K = Y R^-1
+  WS_RS_T,        // randomized SVD: l x l matrices
+  WS_RS_U,        // randomized SVD: top eigenvectors of K^H K
+  WS_RS_SCAL,     // randomized SVD: eigenvalues and scalars
   WS_COUNT
 };
 static_assert(WS_COUNT <= hicu_handle::kSlots, "workspace slots");
@@ -406,6 +415,16 @@ void release_fft(hicu_handle* h);
 hicu_status gd_step_filters_soft(hicu_handle* h, const hicu_geom* geom, const hicu_region* region, float* y,
                                  const uint8_t* mask, const float* x0, double lam, const float* filters, int32_t p,
                                  double* stats, int32_t prec, cudaStream_t st);
+// randomized SVD (rsvd.cu) and its helpers: test vectors (jl.cu), complex128 -> complex64 (jl.cu),
+// box -> support coefficients (support.cu)
+hicu_status run_rsvd(hicu_handle* h, const hicu_geom* geom, const hicu_region* region, const uint8_t* kmask,
+                     const float* x, int64_t r, int64_t l, const double* V_prev, int64_t r0, uint64_t seed,
+                     uint64_t counter, double* V, double* eig_top, double* tail, cudaStream_t st);
+hicu_status launch_rsvd_omega(hicu_handle* h, int64_t n, int64_t l, int64_t r0, const double* V_prev, uint64_t seed,
+                              uint64_t counter, double2* Om, cudaStream_t st);
+hicu_status launch_to_c64(hicu_handle* h, const double* in, float2* out, long long tot, cudaStream_t st);
+hicu_status launch_support_gather(hicu_handle* h, int p, int C, int K, int nk, const int* sup,
+                                  const float2* bank_box, float2* bank_sup, cudaStream_t st);
 // bank_box[k][c][kbox] = bank_sup[k][c][inv[kbox]] (zero off the support)
 hicu_status launch_support_scatter(hicu_handle* h, int p, int C, int K, int nk, const int* inv,
                                    const float2* bank_sup, float2* bank_box, cudaStream_t st);

@@ -241,6 +241,42 @@ hicu_status launch_jl_qplus(hicu_handle* h, int p, int64_t n, int n0, int m0, co
   return cuda_error(h, cudaGetLastError(), "jl qplus");
 }
 
+namespace {
+// randomized-SVD test vectors Omega [l][n]: rows 0..r0-1 copied from V_prev, row r0 + b, entry a the
+// complex Gaussian (z(2e) + i z(2e + 1)) / sqrt(2) of draw `counter`, e = a (l - r0) + b
+__global__ void rsvd_omega_kernel(int n, int l, int r0, const double2* __restrict__ Vp, uint64_t seed,
+                                  uint64_t counter, double2* __restrict__ Om) {
+  const long long tot = (long long)l * n;
+  const double s = 0.70710678118654752440;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int row = (int)(t / n), a = (int)(t % n);
+    if (row < r0) {
+      Om[t] = Vp[t];
+    } else {
+      const uint64_t e = (uint64_t)a * (uint64_t)(l - r0) + (uint64_t)(row - r0);
+      Om[t] = make_double2(jl_gauss(seed, counter, 2ull * e) * s, jl_gauss(seed, counter, 2ull * e + 1ull) * s);
+    }
+  }
+}
+}  // namespace
+
+hicu_status launch_rsvd_omega(hicu_handle* h, int64_t n, int64_t l, int64_t r0, const double* V_prev, uint64_t seed,
+                              uint64_t counter, double2* Om, cudaStream_t st) {
+  const long long tot = l * n;
+  int blocks = (int)((tot + 255) / 256);
+  if (blocks > 8 * h->num_sms) blocks = 8 * h->num_sms;
+  HICU_LAUNCH(h, K_EIG, st, rsvd_omega_kernel<<<blocks, 256, 0, st>>>((int)n, (int)l, (int)r0,
+                                                                      (const double2*)V_prev, seed, counter, Om));
+  return cuda_error(h, cudaGetLastError(), "rsvd omega");
+}
+
+hicu_status launch_to_c64(hicu_handle* h, const double* in, float2* out, long long tot, cudaStream_t st) {
+  int blocks = (int)((tot + 255) / 256);
+  if (blocks > 2048) blocks = 2048;
+  launch_pdl(h, K_MISC, st, dim3(blocks), dim3(256), 0, to_c64_kernel, true, (const double2*)in, out, tot);
+  return cuda_error(h, cudaGetLastError(), "to complex64");
+}
+
 hicu_status jl_identity(hicu_handle* h, int64_t rows, float* P, cudaStream_t st) {
   const long long tot = rows * rows;
   int blocks = (int)((tot + 255) / 256);

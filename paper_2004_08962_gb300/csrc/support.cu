@@ -34,7 +34,30 @@ __global__ void support_scatter_kernel(int p, int C, int K, int nk, const int* _
   }
 }
 
+// bank_sup[k][c][j] = bank_box[k][c][sup[j]]: the support's coefficients of box-layout filters
+__global__ void support_gather_kernel(int p, int C, int K, int nk, const int* __restrict__ sup,
+                                      const float2* __restrict__ bank_box, float2* __restrict__ bank_sup) {
+  pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
+  pdl_trigger();
+  const long long tot = (long long)p * C * nk;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(i % nk);
+    const long long fc = i / nk;
+    bank_sup[i] = bank_box[fc * K + sup[j]];
+  }
+}
+
 }  // namespace
+
+hicu_status launch_support_gather(hicu_handle* h, int p, int C, int K, int nk, const int* sup,
+                                  const float2* bank_box, float2* bank_sup, cudaStream_t st) {
+  const long long tot = (long long)p * C * nk;
+  const int blocks = (int)std::min<long long>((tot + 255) / 256, 1024);
+  launch_pdl(h, K_MISC, st, dim3(blocks), dim3(256), 0, support_gather_kernel, true, p, C, K, nk, sup, bank_box,
+             bank_sup);
+  return cuda_error(h, cudaGetLastError(), "support gather");
+}
 
 hicu_status support_maps(hicu_handle* h, const hicu_geom* geom, const uint8_t* kmask, const int** sup,
                          const int** inv, int* nk, cudaStream_t st) {

@@ -29,7 +29,7 @@ EXPORTED = (
     "hicu_profile_eig_sweeps", "hicu_batch_order", "hicu_reconstruct_batched",
     "hicu_conv_null_filter_grad", "hicu_project_unobserved",
     "hicu_support_length", "hicu_gram_support", "hicu_expand_filters",
-    "hicu_gd_step_soft", "hicu_soft_threshold",
+    "hicu_gd_step_soft", "hicu_soft_threshold", "hicu_principal_rsvd",
 )
 
 HICU_K_GRAM, HICU_K_EIG, HICU_K_CONV, HICU_K_ADJOINT, HICU_K_JL, HICU_K_MISC = 0, 1, 2, 3, 4, 5
@@ -54,7 +54,8 @@ class hicu_params(ctypes.Structure):
                 ("seed", c_uint64), ("jl", c_int32), ("prec", c_int32),
                 ("gram_on_current", c_int32), ("init", c_int32), ("eig_solver", c_int32),
                 ("kernel_mask", c_void_p), ("dc_weight", c_double), ("l1_threshold", c_double),
-                ("jl_exact", c_int32), ("qplus", c_void_p), ("qplus_cols", c_int32), ("qplus_blocks", c_int32)]
+                ("jl_exact", c_int32), ("qplus", c_void_p), ("qplus_cols", c_int32), ("qplus_blocks", c_int32),
+                ("rsvd_cols", c_int32), ("rsvd_seed", c_uint64)]
 
 
 class hicu_log(ctypes.Structure):
@@ -123,6 +124,8 @@ def lib() -> ctypes.CDLL:
             "hicu_expand_filters": ([P, G, P, P, c_int32, P, P], c_int32),
             "hicu_gd_step_soft": ([P, G, R, P, P, P, c_double, P, c_int32, P, c_int32, P], c_int32),
             "hicu_soft_threshold": ([P, G, P, c_double, P], c_int32),
+            "hicu_principal_rsvd": ([P, G, R, P, P, c_int64, c_int64, P, c_int64, c_uint64, c_uint64, P, P, P, P],
+                                    c_int32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -345,6 +348,30 @@ def hicu_expand_filters(h: Handle, geom, kmask, bank_sup: torch.Tensor, stream=N
 
 HICU_NULLSPACE_WARM, HICU_NULLSPACE_SPLIT, HICU_NULLSPACE_GRID, HICU_NULLSPACE_CLUSTER = 1, 2, 4, 8
 HICU_NULLSPACE_TRIDIAG = 16
+HICU_NULLSPACE_RSVD = 32
+
+
+def hicu_principal_rsvd(h: Handle, geom, region, x: torch.Tensor, r: int, l: int, V_prev=None, seed: int = 0,
+                        counter: int = 0, kmask=None, want_tail: bool = False, stream=None):
+    """-> (V [r][n] complex128 rows, eig_top [r] ascending[, tail J]) by randomized SVD."""
+    m = None if kmask is None else _kmask(geom, kmask)
+    n = _filter_len(geom) if m is None else hicu_support_length(geom, m)
+    _need(x, "x", torch.complex64, _kshape(geom))
+    r0 = 0
+    if V_prev is not None:
+        if V_prev.dim() != 2:
+            raise ValueError("V_prev must be a (r0, n) complex128 tensor")
+        r0 = V_prev.shape[0]
+        _need(V_prev, "V_prev", torch.complex128, (r0, n))
+    V = torch.empty((max(r, 0), n), dtype=torch.complex128, device=x.device)
+    top = torch.empty((max(r, 0),), dtype=torch.float64, device=x.device)
+    tail = torch.zeros((1,), dtype=torch.float64, device=x.device) if want_tail else None
+    with torch.cuda.device(h._dev(x, V_prev)):
+        h._check(lib().hicu_principal_rsvd(h.ptr, ctypes.byref(geom), ctypes.byref(region),
+                                           None if m is None else m.ctypes.data_as(c_void_p), _ptr(x), r, l,
+                                           _ptr(V_prev), r0, seed, counter, _ptr(V), _ptr(top), _ptr(tail),
+                                           _stream(stream)))
+    return (V, top, tail) if want_tail else (V, top)
 
 
 def hicu_nullspace(h: Handle, G: torch.Tensor, r: int, warm: bool = False, split: bool = False,
@@ -549,10 +576,12 @@ def hicu_gd_step(h: Handle, geom, region, y: torch.Tensor, mask: Optional[torch.
 def make_params(rank: int, stages, seed: int = 0, jl: int = HICU_JL_PROJECTOR, prec: int = HICU_FP32,
                 gram_on_current: bool = False, init: int = 0, eig_solver: Optional[str] = None,
                 kernel_mask=None, dc_weight: float = 0.0, l1_threshold: float = 0.0, jl_exact: bool = False,
-                qplus: Optional[torch.Tensor] = None, qplus_blocks: int = 0):
+                qplus: Optional[torch.Tensor] = None, qplus_blocks: int = 0, rsvd_cols: int = 0,
+                rsvd_seed: int = 0):
     """stages: sequence of (off, ext, iters, gd_steps, p).  eig_solver: None (the library's
     default: tridiagonal principal subspace in projector mode, else Jacobi by size), "grid",
-    "cluster" (Jacobi) or "tridiag".  kernel_mask: optional (kz, ky, kx) {0,1} array over the
+    "cluster" (Jacobi), "tridiag" or "rsvd" (randomized SVD with rsvd_cols test vectors, 0 = the
+    library's default, Gaussian draws from rsvd_seed).  kernel_mask: optional (kz, ky, kx) {0,1} array over the
     kernel's box (the shape is checked by hicu_reconstruct's binding).  dc_weight: lambda of soft
     data consistency (0 = hard); l1_threshold: tau of the l1 step (0 = off); jl_exact: no JL
     compression (every step uses the whole null space: the exact gradient).  qplus: Q0 as a
@@ -574,7 +603,9 @@ def make_params(rank: int, stages, seed: int = 0, jl: int = HICU_JL_PROJECTOR, p
     prm.gram_on_current = 1 if gram_on_current else 0
     prm.init = int(init)
     prm.eig_solver = {None: 0, "grid": HICU_NULLSPACE_GRID, "cluster": HICU_NULLSPACE_CLUSTER,
-                      "tridiag": HICU_NULLSPACE_TRIDIAG}[eig_solver]
+                      "tridiag": HICU_NULLSPACE_TRIDIAG, "rsvd": HICU_NULLSPACE_RSVD}[eig_solver]
+    prm.rsvd_cols = int(rsvd_cols)
+    prm.rsvd_seed = int(rsvd_seed)
     prm.jl_exact = 1 if jl_exact else 0
     if qplus is not None:
         if not (isinstance(qplus, torch.Tensor) and qplus.dtype == torch.complex128 and qplus.dim() == 2
