@@ -724,6 +724,69 @@ def run_ablation(args):
     return 0
 
 
+def run_nullspace_compare(args):
+    """Time one null-space update (Algorithm 1 steps 2-3) by the two routes on the centre-out
+    regions of the brain slice (n = 200, r = 75) and the knee volume (n = 1000, r = 400):
+      gram   : the lag-form Gram (hicu_gram) and the principal subspace by Householder
+               tridiagonalisation (hicu_principal_subspace)
+      rsvd   : the randomized SVD (hicu_principal_rsvd) with l = r + max(r/2, 8) test vectors, warm
+               started from the previous call's vectors (the reconstruction's steady state)
+    CUDA events around each call, median of 5 after a warm-up; the distance between the two
+    subspaces (spectral norm of the projector difference) and each route's J.  One JSON object."""
+    import torch
+    from paper_2004_08962_gb300 import build, hicu
+    build.build()
+    h = hicu.Handle()
+    out = {"nullspace_compare": "one null-space update by the Gram route and by the randomized SVD", "cases": []}
+    for wl in ("brain", "knee"):
+        pb, _ = workload_problem(wl, problem_seed(wl, 0))
+        st = pb.stages[0]
+        geom = hicu.make_geom(pb.dims, pb.ncoil, pb.kernel, pb.circular)
+        reg = hicu.make_region(st.off, st.ext)
+        x = torch.from_numpy(pb.x0).cuda()
+        r = pb.rank
+        n = pb.ncoil * pb.kernel[0] * pb.kernel[1] * pb.kernel[2]
+        l = min(n, r + max(r // 2, 8))
+
+        def timed(fn, reps=5):
+            fn()
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                res = fn()
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return statistics.median(ts), res
+
+        def gram_route():
+            G = hicu.hicu_gram(h, geom, reg, x)
+            return hicu.hicu_principal_subspace(h, G, r, want_tail=True)
+
+        t_gram, (Vg, eg, Jg) = timed(gram_route)
+        Vr, er, Jr = hicu.hicu_principal_rsvd(h, geom, reg, x, r, l, seed=7, counter=0, want_tail=True)
+        state = {"V": Vr, "k": 1}
+
+        def rsvd_route():
+            V, e, J = hicu.hicu_principal_rsvd(h, geom, reg, x, r, l, V_prev=state["V"], seed=7, counter=state["k"],
+                                               want_tail=True)
+            state["V"], state["k"] = V, state["k"] + 1
+            return V, e, J
+
+        t_rsvd, (Vr, er, Jr) = timed(rsvd_route)
+        A, B = Vg.cpu().numpy().T, Vr.cpu().numpy().T
+        dist = float(np.linalg.norm(A @ A.conj().T - B @ B.conj().T, 2))
+        out["cases"].append({"workload": WORKLOADS[wl][0], "n": n, "r": r, "l": l,
+                             "region": "x".join(str(e) for e in st.ext if e > 1),
+                             "gram_route_ms": round(t_gram, 3), "rsvd_ms": round(t_rsvd, 3),
+                             "subspace_distance": dist, "J_gram": float(Jg.item()), "J_rsvd": float(Jr.item())})
+    hicu.hicu_check(h)
+    h.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 # -------------------------------------------------------------------- GPU arm
 
 def timed_recons(one, steps, flush, stream):
@@ -814,11 +877,15 @@ def main():
     ap.add_argument("--lanes", type=int, default=8, help="worker lanes of the batched workload")
     ap.add_argument("--ablation", action="store_true",
                     help="the JL p-sweep and CO x JL ablation on the brain slice (one JSON object, no bench line)")
+    ap.add_argument("--nullspace-compare", action="store_true",
+                    help="time one null-space update by the Gram route and by the randomized SVD (brain, knee)")
     args = ap.parse_args()
     if args.profile:
         return run_profile_case(args.profile, args.size)
     if args.ablation:
         return run_ablation(args)
+    if args.nullspace_compare:
+        return run_nullspace_compare(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

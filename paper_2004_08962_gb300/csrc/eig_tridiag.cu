@@ -39,7 +39,7 @@ namespace cg = cooperative_groups;
 
 namespace hicu {
 
-constexpr int TD_THREADS = 256;
+constexpr int TD_THREADS = 512;
 
 struct TdArgs {
   int n;
