@@ -68,8 +68,10 @@ SMS, FP32_LANES = 152, 128
 # instructions for the 8 algorithmic flops of one complex multiply-add
 GRAM_INSTR_PER_CMAC = 40
 # DRAM bytes (read + write) per launch from one ncu capture of the same kernel on the same
-# workload (profiles/); a kernel changed since its capture has no entry.
-NCU_TRAFFIC = {}
+# workload (profiles/), averaged over the class's launches in one reconstruction (centre-region
+# and full-size launches together, as the event timing averages them); a kernel changed since its
+# capture has no entry.
+NCU_TRAFFIC = {("knee3d_256x256x160", "conv_tc"): 293316615, ("knee3d_256x256x160", "adjoint_tc"): 570953051}
 
 
 def problem_seed(workload: str, rank: int) -> int:
