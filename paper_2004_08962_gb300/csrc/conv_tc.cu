@@ -144,6 +144,85 @@ __device__ __forceinline__ void mma_window(uint32_t dcol0, int slot, int cnt, in
                  tc::idesc_bf16_f32(128, TC_SLOT_COLS * (cnt - first)), acc);
 }
 
+// The MMAs of one stage: for each of the NM M tiles, the kx offsets, each with the hi and the lo
+// input planes, into the window of accumulator slots [d0, d0 + 32 n0) (and [0, 32 n1) where the
+// ring wraps).  The single issuing thread is the kernel's critical path, so descriptors are formed
+// once and advanced by adding to their address field (16-byte units; shared-memory addresses stay
+// below 2^18, so the field never carries), and the loops are unrolled at compile time: in
+// straight-line code an MMA of N = 160 issues about as fast as the tensor core completes it
+// (about 80 cycles), while a loop with a branch per offset halves the issue rate.
+struct StageWin {
+  uint32_t d0, id0, id1, dstride;   // dstride: TMEM columns between the M tiles' rings
+  uint64_t bw0, bw1, lo16, boff16;
+};
+
+template <int KX, int NM, bool WRAP, int DX0>
+__device__ __forceinline__ void stage_mmas(uint32_t taddr, uint64_t a_st, uint64_t b_st, const StageWin& w) {
+#pragma unroll
+  for (int mt = 0; mt < NM; ++mt) {
+    const uint32_t dm = taddr + (uint32_t)mt * w.dstride;
+    const uint64_t a_mt = a_st + (uint64_t)(mt * 128);
+#pragma unroll
+    for (int dx = DX0; dx < KX; ++dx) {
+      const uint64_t ah = a_mt + (uint64_t)dx, al = ah + w.lo16;
+      const uint64_t bb = b_st + (uint64_t)dx * w.boff16;
+      tc::mma_bf16_acc(dm + w.d0, ah, bb + w.bw0, w.id0);
+      if (WRAP) tc::mma_bf16_acc(dm, ah, bb + w.bw1, w.id1);
+      tc::mma_bf16_acc(dm + w.d0, al, bb + w.bw0, w.id0);
+      if (WRAP) tc::mma_bf16_acc(dm, al, bb + w.bw1, w.id1);
+    }
+  }
+}
+
+template <int KX, int NM>
+__device__ __forceinline__ void stage_mmas_sel(bool wrap, bool skip0, uint32_t taddr, uint64_t a_st, uint64_t b_st,
+                                               const StageWin& w) {
+  if (wrap) {
+    if (skip0) stage_mmas<KX, NM, true, 1>(taddr, a_st, b_st, w);
+    else stage_mmas<KX, NM, true, 0>(taddr, a_st, b_st, w);
+  } else {
+    if (skip0) stage_mmas<KX, NM, false, 1>(taddr, a_st, b_st, w);
+    else stage_mmas<KX, NM, false, 0>(taddr, a_st, b_st, w);
+  }
+}
+
+template <int KX>
+__device__ __forceinline__ void stage_mmas_kx(int nM, bool wrap, bool skip0, uint32_t taddr, uint64_t a_st,
+                                              uint64_t b_st, const StageWin& w) {
+  if (nM == 2) stage_mmas_sel<KX, 2>(wrap, skip0, taddr, a_st, b_st, w);
+  else stage_mmas_sel<KX, 1>(wrap, skip0, taddr, a_st, b_st, w);
+}
+
+// offsets dx0 .. kx - 1 of every M tile (dx0 is 1 where offset 0 was issued with the accumulator
+// start); kernel widths without an unrolled form take a loop
+__device__ __forceinline__ void stage_mmas_any(int kx, int nM, bool wrap, int dx0, uint32_t taddr, uint64_t a_st,
+                                               uint64_t b_st, const StageWin& w) {
+  const bool skip0 = dx0 > 0;
+  switch (kx) {
+    case 1:
+      if (!skip0) stage_mmas_kx<1>(nM, wrap, false, taddr, a_st, b_st, w);
+      return;
+    case 2: stage_mmas_kx<2>(nM, wrap, skip0, taddr, a_st, b_st, w); return;
+    case 3: stage_mmas_kx<3>(nM, wrap, skip0, taddr, a_st, b_st, w); return;
+    case 4: stage_mmas_kx<4>(nM, wrap, skip0, taddr, a_st, b_st, w); return;
+    case 5: stage_mmas_kx<5>(nM, wrap, skip0, taddr, a_st, b_st, w); return;
+    case 7: stage_mmas_kx<7>(nM, wrap, skip0, taddr, a_st, b_st, w); return;
+    default: break;
+  }
+  for (int mt = 0; mt < nM; ++mt) {
+    const uint32_t dm = taddr + (uint32_t)mt * w.dstride;
+    const uint64_t a_mt = a_st + (uint64_t)(mt * 128);
+    for (int dx = dx0; dx < kx; ++dx) {
+      const uint64_t ah = a_mt + (uint64_t)dx, al = ah + w.lo16;
+      const uint64_t bb = b_st + (uint64_t)dx * w.boff16;
+      tc::mma_bf16_acc(dm + w.d0, ah, bb + w.bw0, w.id0);
+      if (wrap) tc::mma_bf16_acc(dm, ah, bb + w.bw1, w.id1);
+      tc::mma_bf16_acc(dm + w.d0, al, bb + w.bw0, w.id0);
+      if (wrap) tc::mma_bf16_acc(dm, al, bb + w.bw1, w.id1);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_corr_kernel(const __grid_constant__ CUtensorMap amap, const TcParams P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -192,7 +271,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ------------------------------------------------------------- TMA producer
     if (lane == 0) {
       bool ok = true;
-      long long it = 0;
+      // stage ring position and completed rounds (counters, not divisions: the roles' loops are on
+      // the critical path and a 64-bit division costs about a hundred instructions)
+      int s = 0;
+      uint32_t round = 0;
       int prev_og = -1, j = 0;
       const uint32_t plane_b = (uint32_t)P.PA * 16u;
       const uint32_t a_tx = 4u * (uint32_t)P.nbx * (uint32_t)P.Ty * (uint32_t)P.Wb * 16u;
@@ -212,10 +294,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (P.circ_z) zin = wrap(zin, P.Zin);
           for (int dy = 0; dy < P.ky && ok; ++dy) {
             const int yin = U.ty * P.Ty + dy + P.org_y;
-            for (int kg = 0; kg < P.kgroups; ++kg, ++it) {
-              const int s = (int)(it % P.stages);
-              const long long round = it / P.stages;
-              if (round > 0) ok = tc::mbar_wait(&empty[s], (uint32_t)((round - 1) & 1), P.err);
+            for (int kg = 0; kg < P.kgroups; ++kg) {
+              if (round > 0) ok = tc::mbar_wait(&empty[s], (round - 1) & 1u, P.err);
               if (!ok) break;
               unsigned char* st = sA + (size_t)s * P.stage_bytes;
               tc::mbar_arrive_expect_tx(&full[s], a_tx);
@@ -226,6 +306,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                   for (int bx = 0; bx < P.nbx; ++bx)  // nbx > 1 only with one row per tile
                     tma_load_5d(st + (sp * 2 + cc) * plane_b + bx * P.Wb * 16, &amap, 0, xin + bx * P.Wb, yin,
                                 zin, sp * P.chunks_even + 2 * kg + cc, &full[s]);
+              if (++s == P.stages) {
+                s = 0;
+                ++round;
+              }
             }
           }
         }
@@ -235,12 +319,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ------------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       bool ok = true;
-      long long it = 0, q0 = 0;
+      int s = 0, q0 = 0;
+      uint32_t round = 0;
       int prev_og = -1, nb = 0;
       const uint32_t plane_b = (uint32_t)P.PA * 16u;
       const uint32_t lbo_b = 512u * (uint32_t)P.kz;   // cc0 -> cc1 core matrices of B
       const uint32_t boff = 1024u * (uint32_t)P.kz;   // B bytes per (kg, dy, dx)
       const uint32_t b_base = tc::smem_u32(sB);
+      const uint64_t a_desc0 = tc::smem_desc(tc::smem_u32(sA), plane_b, 128);
+      const uint64_t b_desc0 = tc::smem_desc(b_base, lbo_b, 128);
+      const uint64_t stage16 = P.stage_bytes >> 4;
+      StageWin w;
+      w.lo16 = (2u * plane_b) >> 4;
+      w.boff16 = boff >> 4;
+      w.dstride = (uint32_t)(P.rs * TC_SLOT_COLS);
       for (long long u = blockIdx.x; u < P.units && ok; u += gridDim.x) {
         const Unit U = unit_of(P, u);
         if (U.og != prev_og) {
@@ -254,43 +346,50 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const int za = max(zo_lo, v - zspan), zb = min(zo_hi - 1, v);
           const int cnt = zb - za + 1;
           const bool fresh = v <= zo_hi - 1;  // output plane v starts here
-          const long long qa = q0 + (za - zo_lo);
-          const int sa = (int)(qa % P.rs);
+          const int sa = (q0 + (za - zo_lo)) % P.rs;
           if (fresh) {
-            const long long qn = q0 + (v - zo_lo);
+            const int qn = q0 + (v - zo_lo);
             if (qn >= P.rs) ok = tc::mbar_wait(&acc_empty[qn % P.rs], (uint32_t)(((qn / P.rs) - 1) & 1), P.err);
             if (!ok) break;
           }
           const int ba = P.kz - 1 - (v - za);  // B block of output plane za (blocks hold dz = kz-1-b)
           const int sb = (sa + cnt - 1) % P.rs;
+          // the window's slots [sa, sa + cnt) as one MMA, or two where the ring wraps at rs
+          const int n0 = min(cnt, P.rs - sa), n1 = cnt - n0;
+          w.d0 = (uint32_t)(sa * TC_SLOT_COLS);
+          w.id0 = tc::idesc_bf16_f32(128, TC_SLOT_COLS * n0);
+          w.id1 = tc::idesc_bf16_f32(128, TC_SLOT_COLS * (n1 > 0 ? n1 : 1));
+          w.bw0 = (uint64_t)ba * 32u;
+          w.bw1 = (uint64_t)(ba + n0) * 32u;
           for (int dy = 0; dy < P.ky && ok; ++dy) {
-            for (int kg = 0; kg < P.kgroups; ++kg, ++it) {
-              const int s = (int)(it % P.stages);
-              ok = tc::mbar_wait(&full[s], (uint32_t)((it / P.stages) & 1), P.err);
+            for (int kg = 0; kg < P.kgroups; ++kg) {
+              ok = tc::mbar_wait(&full[s], round & 1u, P.err);
               if (!ok) break;
               tc::tc_fence_after();
-              const uint32_t a_st = tc::smem_u32(sA) + (uint32_t)s * P.stage_bytes;
-              for (int mt = 0; mt < P.nM; ++mt) {
-                const uint32_t dcol0 = taddr + (uint32_t)(mt * P.rs * TC_SLOT_COLS);
-                for (int dx = 0; dx < P.kx; ++dx) {
-                  const uint32_t apos = (uint32_t)(mt * 128 + dx) * 16u;
-                  const uint64_t a_hi = tc::smem_desc(a_st + apos, plane_b, 128);
-                  const uint64_t a_lo = tc::smem_desc(a_st + 2u * plane_b + apos, plane_b, 128);
-                  const uint32_t baddr = b_base + (uint32_t)((kg * P.ky + dy) * P.kx + dx) * boff + (uint32_t)ba * 512u;
-                  if (fresh && dy == 0 && kg == 0 && dx == 0) {
-                    if (cnt > 1) mma_window(dcol0, sa, cnt - 1, P.rs, a_hi, baddr, lbo_b, 1u);
-                    mma_window(dcol0, sb, 1, P.rs, a_hi, baddr + (uint32_t)(cnt - 1) * 512u, lbo_b, 0u);
-                  } else {
-                    mma_window(dcol0, sa, cnt, P.rs, a_hi, baddr, lbo_b, 1u);
-                  }
-                  mma_window(dcol0, sa, cnt, P.rs, a_lo, baddr, lbo_b, 1u);
+              const uint64_t a_st = a_desc0 + (uint64_t)s * stage16;
+              const uint64_t b_st = b_desc0 + (uint64_t)((kg * P.ky + dy) * P.kx) * w.boff16;
+              const bool first = fresh && dy == 0 && kg == 0;
+              if (first) {
+                // the first product into output plane v starts its accumulator
+                const uint32_t baddr = b_base + (uint32_t)((kg * P.ky + dy) * P.kx) * boff + (uint32_t)ba * 512u;
+                for (int mt = 0; mt < P.nM; ++mt) {
+                  const uint32_t dm = taddr + (uint32_t)mt * w.dstride;
+                  const uint64_t a_mt = a_st + (uint64_t)(mt * 128);
+                  if (cnt > 1) mma_window(dm, sa, cnt - 1, P.rs, a_mt, baddr, lbo_b, 1u);
+                  mma_window(dm, sb, 1, P.rs, a_mt, baddr + (uint32_t)(cnt - 1) * 512u, lbo_b, 0u);
+                  mma_window(dm, sa, cnt, P.rs, a_mt + w.lo16, baddr, lbo_b, 1u);
                 }
               }
+              stage_mmas_any(P.kx, P.nM, n1 > 0, first ? 1 : 0, taddr, a_st, b_st, w);
               tc::mma_commit(&empty[s]);
+              if (++s == P.stages) {
+                s = 0;
+                ++round;
+              }
             }
           }
           if (ok && v - zspan >= zo_lo) {
-            const long long qc = q0 + (v - zspan - zo_lo);  // output plane complete
+            const int qc = q0 + (v - zspan - zo_lo);  // output plane complete
             tc::mma_commit(&acc_full[qc % P.rs]);
           }
         }
@@ -306,12 +405,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
     double nrm_d = 0.0;
     bool ok = true;
-    long long q = 0;
+    int q = 0;
     for (long long u = blockIdx.x; u < P.units && ok; u += gridDim.x) {
       const Unit U = unit_of(P, u);
       const int zo_lo = U.zr * P.L, zo_hi = min(zo_lo + P.L, P.oz_lim);
       for (int z = zo_lo; z < zo_hi; ++z, ++q) {
-        const int slot = (int)(q % P.rs);
+        const int slot = q % P.rs;
         ok = tc::mbar_wait(&acc_full[slot], (uint32_t)((q / P.rs) & 1), P.err);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
@@ -725,7 +824,8 @@ bool plan_tc(TcPlan* pl, const ConvGeom& g, int mode, int p, int num_sms) {
   const size_t fixed = TC_BAR_BYTES + P.b_bytes + 128;
   if (fixed + 2 * (size_t)P.stage_bytes > TC_SMEM_LIMIT) return false;
   P.stages = (int)std::min<size_t>(TC_MAX_STAGES, (TC_SMEM_LIMIT - fixed) / P.stage_bytes);
-  P.rs = std::min(P.kz + 1, 512 / (TC_SLOT_COLS * P.nM));
+  // the whole TMEM (one CTA per SM): a longer ring wraps fewer MMA windows
+  P.rs = std::min(16, 512 / (TC_SLOT_COLS * P.nM));
   if (P.rs < P.kz || P.rs > 16) return false;
   int cols = 32;
   while (cols < P.nM * P.rs * TC_SLOT_COLS) cols <<= 1;
