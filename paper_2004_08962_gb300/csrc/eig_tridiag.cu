@@ -94,8 +94,9 @@ __device__ inline bool grid_sync_count(const GridSync& gs, unsigned& epoch) {
   if (threadIdx.x == 0) {
     int ok = 1;
     const unsigned target = (epoch + 1u) * gs.nblocks;
-    __threadfence();
-    atomicAdd(gs.count, 1u);
+    // arrival with release semantics at GPU scope (cumulative over the CTA's writes, which the
+    // __syncthreads above made visible to this thread): one reduction, no separate fence
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(gs.count) : "memory");
     unsigned long long t0 = 0;
     for (unsigned it = 0; ld_acquire_u32(gs.count) < target; ++it) {
       if ((it & 255u) == 255u) {
@@ -209,12 +210,7 @@ __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
       }
     }
     __syncthreads();
-    // --- 2. v; the CTA's partial sum
-    for (int j = tid; j < m; j += TD_THREADS) {
-      const cdf vj = j == 0 ? cdf{{1.f, 0.f}, {0.f, 0.f}} : c_mul(c_conj(ld4(&x[1 + j])), scale);
-      st4(&v[j], vj);
-      if (c == 0) st4(&a.refl[(long long)k * n + j], vj);
-    }
+    // --- 2. the CTA's partial sum (v itself is formed after the barrier, under its loads)
     if (warp == 0) {
       cdf pc = c_zero();
       for (int q = lane; q < nown; q += 32) pc = c_add(pc, ld4(&pcs[q]));
@@ -222,9 +218,11 @@ __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
       if (lane == 0) st4(&pg[c], pc);
     }
     if (!grid_sync_count(a.gs, epoch)) return;
-    // --- 3. alpha, w, the next pivot row and its squares
+    // --- 3. v (from the pivot row, before it is overwritten) while the other CTAs' w0, the
+    // published row and the partial sums are loaded; then alpha, w, the next pivot row and its
+    // squares
+    float4 wpf[TD_PF], ppf[TD_PF], w00;
     if (warp * 32 < m) {
-      float4 wpf[TD_PF], ppf[TD_PF];
 #pragma unroll
       for (int t = 0; t < TD_PF; ++t) {
         const int j = tid + t * TD_THREADS;
@@ -233,7 +231,15 @@ __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
           ppf[t] = __ldcg(&pub[j]);
         }
       }
-      const float4 w00 = __ldcg(&wg[0]);
+      w00 = __ldcg(&wg[0]);
+    }
+    for (int j = tid; j < m; j += TD_THREADS) {
+      const cdf vj = j == 0 ? cdf{{1.f, 0.f}, {0.f, 0.f}} : c_mul(c_conj(ld4(&x[1 + j])), scale);
+      st4(&v[j], vj);
+      if (c == 0) st4(&a.refl[(long long)k * n + j], vj);
+    }
+    __syncthreads();
+    if (warp * 32 < m) {
       cdf sp = c_zero();
       for (int q = lane; q < G; q += 32) sp = c_add(sp, ld4(&pg[q]));
       const cdf ssum = c_warp_sum(sp);
