@@ -596,9 +596,13 @@ __device__ __forceinline__ int sturm_count(int n, const float2* d, const float2*
   return cnt;
 }
 
-// Eigenvalue t0 + blockIdx.x (ascending order), one CTA of TB_THREADS each: multisection with
-// TB_THREADS points a round (8 bits) to an absolute width of 2^-46 ||T||: two FP32 rounds from the
-// Gershgorin interval, then four double-float rounds.  Dynamic shared memory: d and e2 (2 n float2).
+// Eigenvalue t0 + blockIdx.x (ascending order), one CTA each: multisection with P = blockDim.x
+// points a round (a multiple of 32, at most TB_THREADS) to an absolute width of 2^-46 ||T||:
+// FP32 rounds from the Gershgorin interval while the bracket is wider than 2^-14 ||T||, then
+// double-float rounds.  P follows the number of eigenvalues (bisection_points): the Sturm counts
+// are long dependent chains, so a few eigenvalues want many points (fewer rounds) and many
+// eigenvalues want few (the sweeps of all CTAs are issue-bound beyond ~8 warps per SM).
+// Dynamic shared memory: d and e2 (2 n float2).
 constexpr int TB_THREADS = 256;
 
 __global__ void __launch_bounds__(TB_THREADS) td_bisect_kernel(int n, int t0, const float2* __restrict__ d,
@@ -614,21 +618,35 @@ __global__ void __launch_bounds__(TB_THREADS) td_bisect_kernel(int n, int t0, co
   float2* se2 = bsm + n;
   __shared__ int wfirst[2][TB_THREADS / 32];
   const int g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int P = blockDim.x, nw = P >> 5;
   const int t = t0 + g;
-  for (int i = tid; i < n; i += TB_THREADS) {
+  for (int i = tid; i < n; i += P) {
     sd[i] = d[i];
     if (i < n - 1) se2[i] = e2[i];
   }
   __syncthreads();
   const float tol = 0x1.0p-46f * info[2].x + info[3].x;
   const float pivmin = info[3].x;
-  // Two rounds in FP32 first.  An FP32 Sturm count (reciprocal to ~2^-22) is exact for a matrix
-  // whose d and e^2 differ from T's by a few ulps relatively, so its bracket holds the eigenvalue
-  // of T within ~12 * 2^-24 ||T|| (Weyl); widened by 2^-16 ||T|| on each side it is handed to the
-  // double-float rounds, which then need 4 rounds instead of 6.
+  // the index of the first of the P points whose count exceeds t (P when none), from the warps'
+  // ballots; the two buffers alternate by round, so one CTA barrier a round suffices
+  int rnd = 0;
+  auto first_above = [&](bool above_t) -> int {
+    const unsigned above = __ballot_sync(0xffffffffu, above_t);
+    if (lane == 0) wfirst[rnd & 1][warp] = above ? warp * 32 + __ffs(above) - 1 : P;
+    __syncthreads();
+    int first = P;
+    for (int w = 0; w < nw; ++w) first = min(first, wfirst[rnd & 1][w]);
+    ++rnd;
+    return first;
+  };
+  // FP32 rounds first.  An FP32 Sturm count (reciprocal to ~2^-22) is exact for a matrix whose d
+  // and e^2 differ from T's by a few ulps relatively, so its bracket holds the eigenvalue of T
+  // within ~12 * 2^-24 ||T|| (Weyl); widened by 2^-16 ||T|| on each side it is handed to the
+  // double-float rounds.
   float lo32 = info[0].x, hi32 = info[1].x;
-  for (int it = 0; it < 2; ++it) {
-    const float step32 = (hi32 - lo32) * (1.f / (float)(TB_THREADS + 1));
+  const float inv32 = 1.f / (float)(P + 1);
+  for (int it = 0; it < 8 && hi32 - lo32 > 0x1.0p-14f * info[2].x; ++it) {
+    const float step32 = (hi32 - lo32) * inv32;
     const float x32 = lo32 + step32 * (float)(tid + 1);
     float q = sd[0].x - x32;
     if (fabsf(q) <= pivmin) q = -pivmin;
@@ -638,32 +656,22 @@ __global__ void __launch_bounds__(TB_THREADS) td_bisect_kernel(int n, int t0, co
       if (fabsf(q) <= pivmin) q = -pivmin;
       cnt += q < 0.f;
     }
-    const unsigned above = __ballot_sync(0xffffffffu, cnt > t);
-    if (lane == 0) wfirst[it & 1][warp] = above ? warp * 32 + __ffs(above) - 1 : TB_THREADS;
-    __syncthreads();
-    int first = TB_THREADS;
-#pragma unroll
-    for (int w = 0; w < TB_THREADS / 32; ++w) first = min(first, wfirst[it & 1][w]);
+    const int first = first_above(cnt > t);
     const float nlo = first == 0 ? lo32 : lo32 + step32 * (float)first;
-    const float nhi = first == TB_THREADS ? hi32 : lo32 + step32 * (float)(first + 1);
+    const float nhi = first == P ? hi32 : lo32 + step32 * (float)(first + 1);
     lo32 = nlo;
     hi32 = nhi;
   }
   const float pad = 0x1.0p-16f * info[2].x + pivmin;
   dfl lo = df_sub(df_f(lo32), df_f(pad)), hi = df_add(df_f(hi32), df_f(pad));
-  const dfl inv = df_div(df_f(1.f), df_f((float)(TB_THREADS + 1)));
-  for (int it = 2; it < 24 && df_sub(hi, lo).hi > tol; ++it) {
+  const dfl inv = df_div(df_f(1.f), df_f((float)(P + 1)));
+  for (int it = 0; it < 24 && df_sub(hi, lo).hi > tol; ++it) {
     const dfl step = df_mul(df_sub(hi, lo), inv);
     const int cnt = sturm_count(n, sd, se2, df_add(lo, df_mul_f(step, (float)(tid + 1))), pivmin);
     // the first point whose count exceeds t bounds the eigenvalue from above
-    const unsigned above = __ballot_sync(0xffffffffu, cnt > t);
-    if (lane == 0) wfirst[it & 1][warp] = above ? warp * 32 + __ffs(above) - 1 : TB_THREADS;
-    __syncthreads();
-    int first = TB_THREADS;
-#pragma unroll
-    for (int w = 0; w < TB_THREADS / 32; ++w) first = min(first, wfirst[it & 1][w]);
+    const int first = first_above(cnt > t);
     const dfl nlo = first == 0 ? lo : df_add(lo, df_mul_f(step, (float)first));
-    const dfl nhi = first == TB_THREADS ? hi : df_add(lo, df_mul_f(step, (float)(first + 1)));
+    const dfl nhi = first == P ? hi : df_add(lo, df_mul_f(step, (float)(first + 1)));
     lo = nlo;
     hi = nhi;
   }
@@ -672,6 +680,14 @@ __global__ void __launch_bounds__(TB_THREADS) td_bisect_kernel(int n, int t0, co
     if (lam_scaled) lam_scaled[g] = dpack(l);
     if (lam_out) lam_out[g] = df_to(l) / *scale;
   }
+}
+
+// points a round for `count` eigenvalues: about 8 warps of Sturm chains per SM in all
+static int bisection_points(int count, int num_sms) {
+  const long long target = (long long)num_sms * 8 * 32;
+  int P = TB_THREADS;
+  while (P > 32 && (long long)count * P > target) P >>= 1;
+  return P;
 }
 
 __device__ __forceinline__ float hash_unit(uint64_t t, uint64_t i) {
@@ -1092,10 +1108,13 @@ static hicu_status finish_principal(hicu_handle* h, int n, int r, const double2*
     cudaError_t e0 = allow_max_dynamic_smem((const void*)td_bisect_kernel);
     if (e0 != cudaSuccess) return cuda_error(h, e0, "bisection smem");
   }
-  launch_pdl(h, K_EIG, st, dim3(r), dim3(TB_THREADS), bsm_bytes, td_bisect_kernel, false, n, n - r, (const float2*)d,
-             (const float2*)e2, (const float2*)info, (const double*)scale, lam, eig_top);
+  const int nsm = h->num_sms > 0 ? h->num_sms : 148;
+  launch_pdl(h, K_EIG, st, dim3(r), dim3(bisection_points(r, nsm)), bsm_bytes, td_bisect_kernel, false, n, n - r,
+             (const float2*)d, (const float2*)e2, (const float2*)info, (const double*)scale, lam, eig_top);
   if (eig_all)
-    HICU_LAUNCH(h, K_EIG, st, td_bisect_kernel<<<n, TB_THREADS, bsm_bytes, st>>>(n, 0, d, e2, info, scale, nullptr, eig_all));
+    HICU_LAUNCH(h, K_EIG, st,
+                td_bisect_kernel<<<n, bisection_points(n, nsm), bsm_bytes, st>>>(n, 0, d, e2, info, scale, nullptr,
+                                                                                 eig_all));
   // 3. eigenvectors of T, 4. back-transformation
   {
     const int stage = 8 * (size_t)n * sizeof(float2) <= 200 * 1024;
