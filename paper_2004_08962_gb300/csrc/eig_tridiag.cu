@@ -399,18 +399,20 @@ __global__ void __launch_bounds__(TDC_THREADS, 1) tridiag_cluster_kernel(const T
       }
     }
     __syncthreads();
-    // --- 2. v; the CTA's partial sum pushed to every CTA
+    // --- 2. the CTA's partial sum pushed to every CTA; v after the cluster barrier is arrived at
+    // (its entries are this thread's alone until step 3's CTA barrier)
+    if (warp == 0) {
+      const cdf pc = c_warp_sum(lane < nown ? ld4(&pcs[lane]) : c_zero());
+      if (lane < nct) st4(cl.map_shared_rank(&partall[0][0], lane) + par * TDC_CTAS + crank, pc);
+    }
+    cl.barrier_arrive();
     cdf vt = c_zero();
     if (tid < m) {
       vt = tid == 0 ? cdf{{1.f, 0.f}, {0.f, 0.f}} : c_mul(c_conj(ld4(&x[1 + tid])), scale);
       st4(&v[tid], vt);
       if (crank == 0) st4(&a.refl[(long long)k * n + tid], vt);
     }
-    if (warp == 0) {
-      const cdf pc = c_warp_sum(lane < nown ? ld4(&pcs[lane]) : c_zero());
-      if (lane < nct) st4(cl.map_shared_rank(&partall[0][0], lane) + par * TDC_CTAS + crank, pc);
-    }
-    cl.sync();
+    cl.barrier_wait();
     // --- 3. alpha, w, the next pivot row and its squares (all local reads)
     if (warp * 32 < m) {  // only the warps that form entries need alpha
       const cdf ssum = c_warp_sum(lane < nct ? ld4(&partall[par][lane]) : c_zero());
