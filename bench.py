@@ -95,6 +95,16 @@ def workload_problem(workload: str, seed: int, scale: int = 1, sched=None):
     return pb, xb0
 
 
+def eig_kwargs(args, pb):
+    """make_params keywords of the null-space route: the Gram and the principal subspace by
+    tridiagonalisation (default), or the randomized SVD (Theory: rSVD) with l = r + max(r/2, 8)
+    test vectors (at most n), warm started by the reconstruction."""
+    if getattr(args, "eig_solver", "tridiag") != "rsvd":
+        return {}
+    n = pb.ncoil * pb.kernel[0] * pb.kernel[1] * pb.kernel[2]
+    return {"eig_solver": "rsvd", "rsvd_cols": min(n, pb.rank + max(pb.rank // 2, 8)), "rsvd_seed": 23}
+
+
 def dwi_q0_oracle(xb0):
     """The b0 null vectors Q0 (columns) by the oracle: the DWI_Q0 smallest eigenvectors of the b0
     Gram over the whole b0 k-space, kernel 5 x 5 over the coils."""
@@ -438,6 +448,9 @@ def run_reference(args, rank, world):
     sample = "per step: " + descs[-1]
     config = workload_config(wname, pb)
     config.update({"l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"})
+    ekw = eig_kwargs(args, pb)
+    config["null_space"] = (f"randomized SVD, l = {ekw['rsvd_cols']} (warm started)" if ekw
+                            else "Gram + principal subspace by tridiagonalisation")
     line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(step_s) / len(step_s),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -728,7 +741,8 @@ def run_ablation(args):
 
 def run_nullspace_compare(args):
     """Time one null-space update (Algorithm 1 steps 2-3) by the two routes on the centre-out
-    regions of the brain slice (n = 200, r = 75) and the knee volume (n = 1000, r = 400):
+    regions of the brain slice (n = 200, r = 75), the multi-shot diffusion slice (n = 800, r = 45)
+    and the knee volume (n = 1000, r = 400):
       gram   : the lag-form Gram (hicu_gram) and the principal subspace by Householder
                tridiagonalisation (hicu_principal_subspace)
       rsvd   : the randomized SVD (hicu_principal_rsvd) with l = r + max(r/2, 8) test vectors, warm
@@ -740,7 +754,7 @@ def run_nullspace_compare(args):
     build.build()
     h = hicu.Handle()
     out = {"nullspace_compare": "one null-space update by the Gram route and by the randomized SVD", "cases": []}
-    for wl in ("brain", "knee"):
+    for wl in ("brain", "dwi", "knee"):
         pb, _ = workload_problem(wl, problem_seed(wl, 0))
         st = pb.stages[0]
         geom = hicu.make_geom(pb.dims, pb.ncoil, pb.kernel, pb.circular)
@@ -833,9 +847,11 @@ def accuracy_block(args, pb, hicu, h, geom, x_bf16, x_fp32):
     og = O.Geom(ps.dims, ps.ncoil, ps.kernel, ps.circular)
     ost = [O.StageSpec(O.Region(off, ext), it, gd, p) for off, ext, it, gd, p in stages]
     Q0 = dwi_q0_oracle(xb0) if xb0 is not None else None
+    ekw = eig_kwargs(args, ps)
     t0 = time.perf_counter()
     ref = O.reconstruct(ps.x0, ps.mask, og, ost, ps.rank, seed=5, jl_mode="projector", init=ps.init,
-                        qplus=None if Q0 is None else (Q0, DWI_SHOTS))
+                        qplus=None if Q0 is None else (Q0, DWI_SHOTS),
+                        rsvd=(ekw["rsvd_cols"], ekw["rsvd_seed"]) if ekw else None)
     t_or = time.perf_counter() - t0
     gs = hicu.make_geom(ps.dims, ps.ncoil, ps.kernel, ps.circular, mask_per_coil=ps.mask.ndim == 4)
     q0t = None if Q0 is None else torch.from_numpy(np.ascontiguousarray(Q0.T)).cuda()
@@ -844,7 +860,7 @@ def accuracy_block(args, pb, hicu, h, geom, x_bf16, x_fp32):
            "ser_db_oracle": O.ser_db(ps.x_full, ref)}
     for tag, prec in (("split_bf16", hicu.HICU_SPLIT_BF16), ("plain_fp32", hicu.HICU_FP32)):
         prm = hicu.make_params(ps.rank, stages, seed=5, jl=hicu.HICU_JL_PROJECTOR, prec=prec, init=init,
-                               qplus=q0t, qplus_blocks=DWI_SHOTS if q0t is not None else 0)
+                               qplus=q0t, qplus_blocks=DWI_SHOTS if q0t is not None else 0, **ekw)
         x = hicu.hicu_reconstruct(h, gs, torch.from_numpy(ps.x0).cuda(), torch.from_numpy(ps.mask).cuda(),
                                   prm).cpu().numpy()
         res[tag] = {"nrmse": float(np.linalg.norm(x - ref) / np.linalg.norm(ref)),
@@ -880,8 +896,15 @@ def main():
     ap.add_argument("--ablation", action="store_true",
                     help="the JL p-sweep and CO x JL ablation on the brain slice (one JSON object, no bench line)")
     ap.add_argument("--nullspace-compare", action="store_true",
-                    help="time one null-space update by the Gram route and by the randomized SVD (brain, knee)")
+                    help="time one null-space update by the Gram route and by the randomized SVD "
+                         "(brain, diffusion, knee)")
+    ap.add_argument("--eig-solver", default="tridiag", choices=["tridiag", "rsvd"],
+                    help="null-space route of the timed reconstruction: the Gram and the principal subspace "
+                         "by tridiagonalisation, or the randomized SVD (its oracle check uses the oracle's "
+                         "randomized SVD)")
     args = ap.parse_args()
+    if args.eig_solver != "tridiag" and args.impl == "reference":
+        ap.error("--eig-solver rsvd times the library's route; the reference arm samples the oracle's Gram route")
     if args.profile:
         return run_profile_case(args.profile, args.size)
     if args.ablation:
@@ -938,7 +961,7 @@ def main():
         e1.synchronize()
         q0_ms = e0.elapsed_time(e1)
     params = hicu.make_params(pb.rank, schedule(pb), seed=11, jl=hicu.HICU_JL_PROJECTOR, prec=prec, init=init,
-                              qplus=q0, qplus_blocks=DWI_SHOTS if q0 is not None else 0)
+                              qplus=q0, qplus_blocks=DWI_SHOTS if q0 is not None else 0, **eig_kwargs(args, pb))
     x0 = torch.from_numpy(pb.x0).cuda()
     mask = torch.from_numpy(pb.mask).cuda()
     xout = torch.empty_like(x0)
@@ -992,7 +1015,7 @@ def main():
     if args.prec == "bf16":
         params32 = hicu.make_params(pb.rank, schedule(pb), seed=11, jl=hicu.HICU_JL_PROJECTOR,
                                     prec=hicu.HICU_FP32, init=init, qplus=q0,
-                                    qplus_blocks=DWI_SHOTS if q0 is not None else 0)
+                                    qplus_blocks=DWI_SHOTS if q0 is not None else 0, **eig_kwargs(args, pb))
         out32 = torch.empty_like(x0)
         one32 = lambda: hicu.hicu_reconstruct(h, geom, x0, mask, params32, x_out=out32)
         one32()
@@ -1033,6 +1056,9 @@ def main():
     extra_roofs = kernel_rooflines(pb, wname, per_class, peaks)
     config = workload_config(wname, pb)
     config.update({"l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"})
+    ekw = eig_kwargs(args, pb)
+    config["null_space"] = (f"randomized SVD, l = {ekw['rsvd_cols']} (warm started)" if ekw
+                            else "Gram + principal subspace by tridiagonalisation")
     line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tmax_s * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "bf16x2",
