@@ -336,17 +336,18 @@ hicu_status hicu_principal_subspace(hicu_handle* h, int64_t n, int64_t r, const 
 
 /*
  * hicu_principal_rsvd - the r principal right singular vectors of H(x) on S by randomized SVD
- * (Theory: rSVD; Algorithm 1 step 2), without the Gram matrix.  l test vectors Omega: the r0 rows
- * of V_prev (a warm start, e.g. the previous outer iteration's V), then complex Gaussian vectors,
- * entry a of vector r0 + b being (z(2e) + i z(2e + 1)) / sqrt(2), e = a (l - r0) + b, z the
- * counter-based generator of hicu_jl_compress with (seed, counter).  One convolution with the l
- * vectors as filters and one filter gradient give Z = H^H H Omega (2 l applications of H and H^H,
- * both in complex FP32); then in FP64 the single-pass randomized SVD of H through H^H H with a
- * stabilising shift nu = 2^-17 ||Z||_F / sqrt(l), above the rounding level of the FP32 Z:
+ * (Theory: rSVD; Algorithm 1 step 2), without an n x n eigendecomposition.  l test vectors Omega:
+ * the r0 rows of V_prev (a warm start, e.g. the previous outer iteration's V), then complex
+ * Gaussian vectors, entry a of vector r0 + b being (z(2e) + i z(2e + 1)) / sqrt(2),
+ * e = a (l - r0) + b, z the counter-based generator of hicu_jl_compress with (seed, counter).
+ * Z = H^H H Omega is formed as G Omega from the region's Gram G = H^H H (as hicu_gram, double-word
+ * sums) in double-float arithmetic; then the single-pass randomized SVD of H through H^H H with a
+ * stabilising shift nu = 2^-17 ||Z||_F / sqrt(l):
  *   Y = Z + nu Omega, Omega^H Y = R^H R (Cholesky), K = Y R^-1, V = the top r left singular
  *   vectors of K, eig_top = their squared singular values - nu.
- * Exact when rank(H) <= l.  The Cholesky factor is formed by one CTA (about l^3 / 3 FP64
- * operations: milliseconds for l in the hundreds).
+ * Exact when rank(H) <= l.  The Cholesky factor is formed by one CTA in double-float (about
+ * l^3 / 6 complex multiply-adds: tens of microseconds at l ~ 100, milliseconds at l in the
+ * hundreds).  Workspace: n x n complex128 for G plus O(l n).
  *   kmask   : optional HOST kernel mask (NULL = the whole box); n = C |K| or C kx ky kz
  *   r, l    : 1 <= r < l <= min(n, 4096);  V_prev : complex128 [r0][n] (device), r0 <= l
  *   V       : complex128 [r][n] (device) row j the vector of eig_top[j] (ascending); may be V_prev

@@ -262,9 +262,7 @@ enum Slot {
   WS_REC_X0,      // reconstruct: the observed data X0, kept for soft data consistency / the l1 step
   WS_QPLUS,       // reconstruct: the augmenting null vectors Q0 in complex64
   WS_RS_OMEGA,    // randomized SVD: test vectors [l][n] (complex128)
-  WS_RS_BANK,     // randomized SVD: test vectors as complex64 filters / the support's coefficients of Z
-  WS_RS_BOX,      // randomized SVD: box-layout filters (kernel mask)
-  WS_RS_R,        // randomized SVD: H Omega [s][l]
+  WS_RS_G,        // randomized SVD: the Gram G of the region (n x n complex128)
   WS_RS_Y,        // randomized SVD: Y = Z + nu Omega
   WS_RS_K,        // randomized SVD: K = Y R^-1
   WS_RS_T,        // randomized SVD: l x l matrices
@@ -422,7 +420,6 @@ hicu_status run_rsvd(hicu_handle* h, const hicu_geom* geom, const hicu_region* r
                      uint64_t counter, double* V, double* eig_top, double* tail, cudaStream_t st);
 hicu_status launch_rsvd_omega(hicu_handle* h, int64_t n, int64_t l, int64_t r0, const double* V_prev, uint64_t seed,
                               uint64_t counter, double2* Om, cudaStream_t st);
-hicu_status launch_to_c64(hicu_handle* h, const double* in, float2* out, long long tot, cudaStream_t st);
 hicu_status launch_support_gather(hicu_handle* h, int p, int C, int K, int nk, const int* sup,
                                   const float2* bank_box, float2* bank_sup, cudaStream_t st);
 // bank_box[k][c][kbox] = bank_sup[k][c][inv[kbox]] (zero off the support)

@@ -270,13 +270,6 @@ hicu_status launch_rsvd_omega(hicu_handle* h, int64_t n, int64_t l, int64_t r0, 
   return cuda_error(h, cudaGetLastError(), "rsvd omega");
 }
 
-hicu_status launch_to_c64(hicu_handle* h, const double* in, float2* out, long long tot, cudaStream_t st) {
-  int blocks = (int)((tot + 255) / 256);
-  if (blocks > 2048) blocks = 2048;
-  launch_pdl(h, K_MISC, st, dim3(blocks), dim3(256), 0, to_c64_kernel, true, (const double2*)in, out, tot);
-  return cuda_error(h, cudaGetLastError(), "to complex64");
-}
-
 hicu_status jl_identity(hicu_handle* h, int64_t rows, float* P, cudaStream_t st) {
   const long long tot = rows * rows;
   int blocks = (int)((tot + 255) / 256);
