@@ -2,8 +2,8 @@
 
 hicu_principal_rsvd against the oracle's rsvd_principal with the same test vectors (the same
 counter-based draws, the same warm start): the principal subspace to 1e-4 lambda_max / gap and the
-eigenvalue estimates to 1e-4 lambda_max (Z = H^H H Omega comes from FP32 kernels), on
-2D, 3D and kernel-mask cases; on exactly low-rank data the subspace of eigh.  Reconstructions with
+eigenvalue estimates to 1e-4 lambda_max, on 2D, 3D and kernel-mask cases and with l = 130 (the
+Cholesky factorisation outside shared memory); on exactly low-rank data the subspace of eigh.  Reconstructions with
 eig_solver "rsvd" against the oracle's: NRMSE <= 1e-3, SER within 0.05 dB, J per outer iteration
 to 1e-3.
 """
@@ -38,6 +38,9 @@ CASES = {
     "3d": ((20, 18, 12), 3, (3, 3, 3), (0, 0, 0), ((1, 1, 1), (18, 16, 10)), 10, 24, None),
     "2d_disc": ((40, 36, 1), 4, (5, 5, 1), (0, 0, 0), ((0, 0, 0), (40, 36, 1)), 10, 20, 2.0),
     "cine_circular_t": ((24, 20, 8), 2, (3, 3, 3), (0, 0, 1), ((0, 0, 0), (24, 20, 8)), 10, 20, None),
+    # l = 130: the Cholesky factorisation's working copy (l^2 double-float entries) exceeds shared
+    # memory and lives in the workspace
+    "2d_c8_l130": ((48, 44, 1), 8, (5, 5, 1), (0, 0, 0), ((0, 0, 0), (48, 44, 1)), 10, 130, None),
 }
 
 
