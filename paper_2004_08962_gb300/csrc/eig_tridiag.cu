@@ -132,7 +132,8 @@ __device__ inline bool grid_sync_count(const GridSync& gs, unsigned& epoch) {
 //      with the squares of its entries.  CTA barrier.
 //   4. warps 0..nw-2: rank-2 update of the own rows but row k+1; warp nw-1 meanwhile: the
 //      Householder scalars of step k+1 from x'.  CTA barrier.
-constexpr int TD_PF = 4;  // entries per thread prefetched after the barrier
+constexpr int TD_PF = 4;   // entries per thread prefetched after the barrier
+constexpr int TD_SEG = 4;  // at most this many warps (segments) per row in the update
 
 template <bool ROWS_IN_SMEM>
 __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
@@ -143,8 +144,8 @@ __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
   float4* x = tsm;             // [n] current pivot row k: x[j] = A[k][k + j]
   float4* v = x + n;           // [n]
   float4* w = v + n;           // [n]
-  float4* pcs = w + n;         // [2R] conj(w0_i) v_i of the own rows (first R used)
-  float4* rows = pcs + 2 * R;  // [R][n] own rows (ROWS_IN_SMEM)
+  float4* segp = w + n;        // [R][TD_SEG] partial row sums of the own rows (by local row, segment)
+  float4* rows = segp + TD_SEG * R;  // [R][n] own rows (ROWS_IN_SMEM)
   float2* xsq = (float2*)(rows + (ROWS_IN_SMEM ? (size_t)R * n : 0));  // [n] squares of x
   __shared__ float4 hs[3];     // tau, 1 / (x0 - beta), beta of the current step
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = TD_THREADS / 32;
@@ -174,6 +175,21 @@ __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
     }
   }
   __syncthreads();
+  // row sums of step 0 (later steps' sums are formed with the rank-2 update, phase 4)
+  int S_prev = 1;
+  {
+    const int g0 = c >= 1 ? c : G;                          // the first own row with g >= 1
+    const int nown0 = g0 <= n - 1 ? (n - 1 - g0) / G + 1 : 0;
+    for (int q = warp; q < nown0; q += nw) {
+      const int g = g0 + q * G;
+      const float4* row = row_of(g) + 1;
+      cdf y = c_zero();
+      for (int j = 1 + lane; j < n - 1; j += 32) c_acc_mul(y, ld4(&row[j]), c_conj(ld4(&x[1 + j])));
+      y = c_warp_sum(y);
+      if (lane == 0) st4(&segp[(g / G) * TD_SEG], y);
+    }
+  }
+  __syncthreads();
   for (int k = 0; k < n - 1; ++k) {
     const int m = n - k - 1;
     const int par = k & 1;
@@ -195,25 +211,21 @@ __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
     const int i0 = ((c - (k + 1)) % G + G) % G;  // first relative row owned by this CTA
     const int nown = i0 < m ? (m - 1 - i0) / G + 1 : 0;
     const int lrow0 = (k + 1 + i0) / G;           // its local row index
-    // --- 1. row sums against conj(x); w0 of the own rows
-    for (int q = warp; q < nown; q += nw) {
-      const int i = i0 + q * G;
-      const float4* row = row_of(k + 1 + i) + (k + 1);
-      cdf y = c_zero();
-      for (int j = 1 + lane; j < m; j += 32) c_acc_mul(y, ld4(&row[j]), c_conj(ld4(&x[1 + j])));
-      y = c_warp_sum(y);
-      if (lane == 0) {
+    // --- 1-2. warp 0: w0_i = tau (A_i0 + s_i / (x0 - beta)) of the own rows from their row sums
+    // s_i (formed with the previous step's update) to global memory, and the CTA's partial sum of
+    // conj(w0_i) v_i (v itself is formed after the barrier, under its loads)
+    if (warp == 0) {
+      cdf pc = c_zero();
+      for (int q = lane; q < nown; q += 32) {
+        const int i = i0 + q * G, lr = lrow0 + q;
+        cdf y = ld4(&segp[lr * TD_SEG]);
+        for (int sg = 1; sg < S_prev; ++sg) y = c_add(y, ld4(&segp[lr * TD_SEG + sg]));
+        const float4* row = row_of(k + 1 + i) + (k + 1);
         const cdf w0 = c_mul(tau, c_add(ld4(&row[0]), c_mul(scale, y)));
         st4(&wg[i], w0);
         const cdf vi = i == 0 ? cdf{{1.f, 0.f}, {0.f, 0.f}} : c_mul(c_conj(ld4(&x[1 + i])), scale);
-        st4(&pcs[q], c_mulc(w0, vi));
+        pc = c_add(pc, c_mulc(w0, vi));
       }
-    }
-    __syncthreads();
-    // --- 2. the CTA's partial sum (v itself is formed after the barrier, under its loads)
-    if (warp == 0) {
-      cdf pc = c_zero();
-      for (int q = lane; q < nown; q += 32) pc = c_add(pc, ld4(&pcs[q]));
       pc = c_warp_sum(pc);
       if (lane == 0) st4(&pg[c], pc);
     }
@@ -260,32 +272,39 @@ __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
       for (int j = tid + TD_PF * TD_THREADS; j < m; j += TD_THREADS) form(j, __ldcg(&wg[j]), __ldcg(&pub[j]));
     }
     __syncthreads();
-    // --- 4. rank-2 update (warps 0..nw-2) / Householder scalars of step k+1 (warp nw-1)
+    // --- 4. warps 0..nw-2: rank-2 update of the own rows but row k+1, each updated entry
+    // (columns j >= 2) summed at once against conj(x') for the next step's row sums: S warps per
+    // row, each over every S-th 32-column chunk; warp nw-1 meanwhile: the Householder scalars of
+    // step k+1
+    const int S = (nown > 0 && 2 * nown <= nw - 1) ? min(TD_SEG, (nw - 1) / nown) : 1;
     if (warp < nw - 1) {
-      if (active) {
-        const int tot = nown * m;
-        const float rm = 1.f / (float)m;
-        for (int idx = tid; idx < tot; idx += TD_THREADS - 32) {
-          // idx / m: exact while nown m < 2^21 (the rounding error of the product stays below the
-          // distance 0.5 / m of (idx + 0.5) / m from an integer)
-          const int q = (int)__fmul_rn((float)idx + 0.5f, rm);
-          const int j = idx - q * m;
-          const int i = i0 + q * G;
-          if (i == 0) continue;
-          // global row k+1+i = c + G (lrow0 + q): no division per entry
-          float4* aij = (ROWS_IN_SMEM ? rows + (size_t)(lrow0 + q) * n : a.A + (size_t)(k + 1 + i) * n) + (k + 1) + j;
-          const cdf vi = ld4(&v[i]), wi = ld4(&w[i]), wj = ld4(&w[j]), vjj = ld4(&v[j]);
-          cdf acc = ld4(aij);
-          df_acc_mul(acc.re, df_neg(vi.re), wj.re);
-          df_acc_mul(acc.re, df_neg(vi.im), wj.im);
-          df_acc_mul(acc.re, df_neg(wi.re), vjj.re);
-          df_acc_mul(acc.re, df_neg(wi.im), vjj.im);
-          df_acc_mul(acc.im, df_neg(vi.im), wj.re);
-          df_acc_mul(acc.im, vi.re, wj.im);
-          df_acc_mul(acc.im, df_neg(wi.im), vjj.re);
-          df_acc_mul(acc.im, wi.re, vjj.im);
-          st4(aij, c_renorm(acc));
+      for (int t = warp; t < nown * S; t += nw - 1) {
+        const int q = t / S, sg = t - q * S;
+        const int i = i0 + q * G;
+        if (i == 0) continue;
+        // global row k+1+i = c + G (lrow0 + q): no division per entry
+        float4* arow = (ROWS_IN_SMEM ? rows + (size_t)(lrow0 + q) * n : a.A + (size_t)(k + 1 + i) * n) + (k + 1);
+        const cdf vi = ld4(&v[i]), wi = ld4(&w[i]);
+        cdf y = c_zero();
+        for (int j = 32 * sg + lane; j < m; j += 32 * S) {
+          cdf acc = ld4(&arow[j]);
+          if (active) {
+            const cdf wj = ld4(&w[j]), vjj = ld4(&v[j]);
+            df_acc_mul(acc.re, df_neg(vi.re), wj.re);
+            df_acc_mul(acc.re, df_neg(vi.im), wj.im);
+            df_acc_mul(acc.re, df_neg(wi.re), vjj.re);
+            df_acc_mul(acc.re, df_neg(wi.im), vjj.im);
+            df_acc_mul(acc.im, df_neg(vi.im), wj.re);
+            df_acc_mul(acc.im, vi.re, wj.im);
+            df_acc_mul(acc.im, df_neg(wi.im), vjj.re);
+            df_acc_mul(acc.im, wi.re, vjj.im);
+            acc = c_renorm(acc);
+            st4(&arow[j], acc);
+          }
+          if (j >= 2) c_acc_mul(y, acc, c_conj(ld4(&x[j])));
         }
+        y = c_warp_sum(y);
+        if (lane == 0) st4(&segp[(lrow0 + q) * TD_SEG + sg], y);
       }
     } else if (k + 1 < n - 1) {
       cdf tau1, scale1;
@@ -297,6 +316,7 @@ __global__ void __launch_bounds__(TD_THREADS) tridiag_kernel(const TdArgs a) {
         hs[2] = make_float4(beta1.hi, beta1.lo, 0.f, 0.f);
       }
     }
+    S_prev = S;
     __syncthreads();
   }
   if (c == 0 && tid == 0) a.d[n - 1] = dpack(ld4(&x[0]).re);
@@ -1041,7 +1061,7 @@ static hicu_status launch_tridiag_grid(hicu_handle* h, int n, float4* A, float2*
   // own rows in shared memory when they fit next to the three vectors
   const int R = (n + grid - 1) / grid;
   // x, v, w, the row sums and the squares of x; the own rows on top when they fit
-  const size_t smem_vec = sizeof(float4) * (3 * (size_t)n + 2 * (size_t)R) + sizeof(float2) * (size_t)n;
+  const size_t smem_vec = sizeof(float4) * (3 * (size_t)n + TD_SEG * (size_t)R) + sizeof(float2) * (size_t)n;
   const size_t smem_rows = smem_vec + sizeof(float4) * (size_t)R * n;
   const bool in_smem = smem_rows <= 200 * 1024;
   const void* kern = in_smem ? (const void*)tridiag_kernel<true> : (const void*)tridiag_kernel<false>;
