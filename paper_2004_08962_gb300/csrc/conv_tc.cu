@@ -26,8 +26,9 @@
 // out-of-range boxes are zero-filled, which supplies the adjoint's halo) into a
 // ring of shared-memory stages; warp 1 lane 0 issues the MMAs and commits each
 // stage back to the producer and each finished output plane to the epilogue;
-// warps 2-5 drain finished planes from TMEM (tcgen05.ld), write R / the masked
-// gradient and accumulate squared norms, then free the slot.  The filter bank of
+// warps 2-5 drain finished planes from TMEM (tcgen05.ld), zero the slot again
+// (tcgen05.st; the whole ring is zeroed at the start, so every MMA accumulates),
+// write R / the masked gradient and accumulate squared norms.  The filter bank of
 // the unit's output-channel group stays resident in shared memory.  The grid is
 // persistent (one CTA per SM, static unit schedule), so results are
 // deterministic.  Every mbarrier wait is bounded (tc_ptx.cuh): on a timeout the
@@ -131,19 +132,6 @@ __device__ __forceinline__ Unit unit_of(const TcParams& P, long long u) {
   return U;
 }
 
-// MMAs of one A tile into the accumulators of `cnt` consecutive output planes whose slots
-// start at `slot` (wrapping around the ring of rs slots); B block j of the window sits
-// 512 bytes after block j - 1.
-__device__ __forceinline__ void mma_window(uint32_t dcol0, int slot, int cnt, int rs, uint64_t adesc,
-                                           uint32_t baddr, uint32_t lbo_b, uint32_t acc) {
-  const int first = min(cnt, rs - slot);
-  tc::mma_bf16(dcol0 + (uint32_t)(slot * TC_SLOT_COLS), adesc, tc::smem_desc(baddr, lbo_b, 128),
-               tc::idesc_bf16_f32(128, TC_SLOT_COLS * first), acc);
-  if (cnt > first)
-    tc::mma_bf16(dcol0, adesc, tc::smem_desc(baddr + (uint32_t)first * 512u, lbo_b, 128),
-                 tc::idesc_bf16_f32(128, TC_SLOT_COLS * (cnt - first)), acc);
-}
-
 // The MMAs of one stage: for each of the NM M tiles, the kx offsets, each with the hi and the lo
 // input planes, into the window of accumulator slots [d0, d0 + 32 n0) (and [0, 32 n1) where the
 // ring wraps).  The single issuing thread is the kernel's critical path, so descriptors are formed
@@ -156,14 +144,14 @@ struct StageWin {
   uint64_t bw0, bw1, lo16, boff16;
 };
 
-template <int KX, int NM, bool WRAP, int DX0>
+template <int KX, int NM, bool WRAP>
 __device__ __forceinline__ void stage_mmas(uint32_t taddr, uint64_t a_st, uint64_t b_st, const StageWin& w) {
 #pragma unroll
   for (int mt = 0; mt < NM; ++mt) {
     const uint32_t dm = taddr + (uint32_t)mt * w.dstride;
     const uint64_t a_mt = a_st + (uint64_t)(mt * 128);
 #pragma unroll
-    for (int dx = DX0; dx < KX; ++dx) {
+    for (int dx = 0; dx < KX; ++dx) {
       const uint64_t ah = a_mt + (uint64_t)dx, al = ah + w.lo16;
       const uint64_t bb = b_st + (uint64_t)dx * w.boff16;
       tc::mma_bf16_acc(dm + w.d0, ah, bb + w.bw0, w.id0);
@@ -174,45 +162,34 @@ __device__ __forceinline__ void stage_mmas(uint32_t taddr, uint64_t a_st, uint64
   }
 }
 
-template <int KX, int NM>
-__device__ __forceinline__ void stage_mmas_sel(bool wrap, bool skip0, uint32_t taddr, uint64_t a_st, uint64_t b_st,
-                                               const StageWin& w) {
-  if (wrap) {
-    if (skip0) stage_mmas<KX, NM, true, 1>(taddr, a_st, b_st, w);
-    else stage_mmas<KX, NM, true, 0>(taddr, a_st, b_st, w);
+template <int KX>
+__device__ __forceinline__ void stage_mmas_kx(int nM, bool wrap, uint32_t taddr, uint64_t a_st, uint64_t b_st,
+                                              const StageWin& w) {
+  if (nM == 2) {
+    if (wrap) stage_mmas<KX, 2, true>(taddr, a_st, b_st, w);
+    else stage_mmas<KX, 2, false>(taddr, a_st, b_st, w);
   } else {
-    if (skip0) stage_mmas<KX, NM, false, 1>(taddr, a_st, b_st, w);
-    else stage_mmas<KX, NM, false, 0>(taddr, a_st, b_st, w);
+    if (wrap) stage_mmas<KX, 1, true>(taddr, a_st, b_st, w);
+    else stage_mmas<KX, 1, false>(taddr, a_st, b_st, w);
   }
 }
 
-template <int KX>
-__device__ __forceinline__ void stage_mmas_kx(int nM, bool wrap, bool skip0, uint32_t taddr, uint64_t a_st,
-                                              uint64_t b_st, const StageWin& w) {
-  if (nM == 2) stage_mmas_sel<KX, 2>(wrap, skip0, taddr, a_st, b_st, w);
-  else stage_mmas_sel<KX, 1>(wrap, skip0, taddr, a_st, b_st, w);
-}
-
-// offsets dx0 .. kx - 1 of every M tile (dx0 is 1 where offset 0 was issued with the accumulator
-// start); kernel widths without an unrolled form take a loop
-__device__ __forceinline__ void stage_mmas_any(int kx, int nM, bool wrap, int dx0, uint32_t taddr, uint64_t a_st,
+// the offsets of every M tile; kernel widths without an unrolled form take a loop
+__device__ __forceinline__ void stage_mmas_any(int kx, int nM, bool wrap, uint32_t taddr, uint64_t a_st,
                                                uint64_t b_st, const StageWin& w) {
-  const bool skip0 = dx0 > 0;
   switch (kx) {
-    case 1:
-      if (!skip0) stage_mmas_kx<1>(nM, wrap, false, taddr, a_st, b_st, w);
-      return;
-    case 2: stage_mmas_kx<2>(nM, wrap, skip0, taddr, a_st, b_st, w); return;
-    case 3: stage_mmas_kx<3>(nM, wrap, skip0, taddr, a_st, b_st, w); return;
-    case 4: stage_mmas_kx<4>(nM, wrap, skip0, taddr, a_st, b_st, w); return;
-    case 5: stage_mmas_kx<5>(nM, wrap, skip0, taddr, a_st, b_st, w); return;
-    case 7: stage_mmas_kx<7>(nM, wrap, skip0, taddr, a_st, b_st, w); return;
+    case 1: stage_mmas_kx<1>(nM, wrap, taddr, a_st, b_st, w); return;
+    case 2: stage_mmas_kx<2>(nM, wrap, taddr, a_st, b_st, w); return;
+    case 3: stage_mmas_kx<3>(nM, wrap, taddr, a_st, b_st, w); return;
+    case 4: stage_mmas_kx<4>(nM, wrap, taddr, a_st, b_st, w); return;
+    case 5: stage_mmas_kx<5>(nM, wrap, taddr, a_st, b_st, w); return;
+    case 7: stage_mmas_kx<7>(nM, wrap, taddr, a_st, b_st, w); return;
     default: break;
   }
   for (int mt = 0; mt < nM; ++mt) {
     const uint32_t dm = taddr + (uint32_t)mt * w.dstride;
     const uint64_t a_mt = a_st + (uint64_t)(mt * 128);
-    for (int dx = dx0; dx < kx; ++dx) {
+    for (int dx = 0; dx < kx; ++dx) {
       const uint64_t ah = a_mt + (uint64_t)dx, al = ah + w.lo16;
       const uint64_t bb = b_st + (uint64_t)dx * w.boff16;
       tc::mma_bf16_acc(dm + w.d0, ah, bb + w.bw0, w.id0);
@@ -261,6 +238,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t taddr = *tslot;
+  // every accumulator slot starts at zero (and the epilogue zeroes each slot it drains), so that
+  // every MMA accumulates: the epilogue warps clear their lane quarter of the allocation
+  if (warp >= 2) {
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    for (int col = 0; col < P.tmem_cols; col += 16) tc::tmem_st16_zero(taddr + lane_base + (uint32_t)col);
+    tc::tmem_st_wait();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
   // programmatic dependent launch: the set-up above overlaps the previous kernel's tail; its
   // outputs (this kernel's inputs) are read only from here on
   pdl_wait();
@@ -353,7 +340,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (!ok) break;
           }
           const int ba = P.kz - 1 - (v - za);  // B block of output plane za (blocks hold dz = kz-1-b)
-          const int sb = (sa + cnt - 1) % P.rs;
           // the window's slots [sa, sa + cnt) as one MMA, or two where the ring wraps at rs
           const int n0 = min(cnt, P.rs - sa), n1 = cnt - n0;
           w.d0 = (uint32_t)(sa * TC_SLOT_COLS);
@@ -368,19 +354,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               tc::tc_fence_after();
               const uint64_t a_st = a_desc0 + (uint64_t)s * stage16;
               const uint64_t b_st = b_desc0 + (uint64_t)((kg * P.ky + dy) * P.kx) * w.boff16;
-              const bool first = fresh && dy == 0 && kg == 0;
-              if (first) {
-                // the first product into output plane v starts its accumulator
-                const uint32_t baddr = b_base + (uint32_t)((kg * P.ky + dy) * P.kx) * boff + (uint32_t)ba * 512u;
-                for (int mt = 0; mt < P.nM; ++mt) {
-                  const uint32_t dm = taddr + (uint32_t)mt * w.dstride;
-                  const uint64_t a_mt = a_st + (uint64_t)(mt * 128);
-                  if (cnt > 1) mma_window(dm, sa, cnt - 1, P.rs, a_mt, baddr, lbo_b, 1u);
-                  mma_window(dm, sb, 1, P.rs, a_mt, baddr + (uint32_t)(cnt - 1) * 512u, lbo_b, 0u);
-                  mma_window(dm, sa, cnt, P.rs, a_mt + w.lo16, baddr, lbo_b, 1u);
-                }
-              }
-              stage_mmas_any(P.kx, P.nM, n1 > 0, first ? 1 : 0, taddr, a_st, b_st, w);
+              stage_mmas_any(P.kx, P.nM, n1 > 0, taddr, a_st, b_st, w);
               tc::mma_commit(&empty[s]);
               if (++s == P.stages) {
                 s = 0;
@@ -425,6 +399,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
         tc::tmem_ld_wait();
+        // the slot back to zero for the next output plane that takes it
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          if (mt < P.nM) {
+            const uint32_t col = taddr + lane_base + (uint32_t)((mt * P.rs + slot) * TC_SLOT_COLS);
+            tc::tmem_st16_zero(col);
+            tc::tmem_st16_zero(col + 16u);
+          }
+        }
+        tc::tmem_st_wait();
         tc::tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&acc_empty[slot]);
