@@ -332,7 +332,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int v = zo_lo; v <= zo_hi - 1 + zspan && ok; ++v) {
           const int za = max(zo_lo, v - zspan), zb = min(zo_hi - 1, v);
           const int cnt = zb - za + 1;
-          const bool fresh = v <= zo_hi - 1;  // output plane v starts here
+          // output plane v starts here: its slot's previous plane must have been drained (and the
+          // slot zeroed) by the epilogue before the first MMA accumulates into it
+          const bool fresh = v <= zo_hi - 1;
           const int sa = (q0 + (za - zo_lo)) % P.rs;
           if (fresh) {
             const int qn = q0 + (v - zo_lo);
