@@ -42,20 +42,38 @@ struct GramParams {
   int nk;          // offsets per coil in G's index (|K|, or kx ky kz)
 };
 
-__device__ __forceinline__ void dd_acc(float a, float b, float& hi, float& lo) {
-  const float p = __fmul_rn(a, b);
-  const float e = __fmaf_rn(a, b, -p);  // exact: a*b = p + e
-  const float s = __fadd_rn(hi, p);     // two-sum(hi, p) = s + err
-  const float bb = __fadd_rn(s, -hi);
-  const float err = __fadd_rn(__fadd_rn(hi, -__fadd_rn(s, -bb)), __fadd_rn(p, -bb));
+// conj(a) b added to the double-word sums of its real and imaginary parts: per component the
+// value is hi + lo.  Each real product is formed exactly (p plus its fma error term e), p enters
+// the sum through a two-sum and the rounding errors of both go to lo; the sums are renormalised
+// after every complex product.  The paired FP32 instructions of sm_100 and later (__fmul2_rn,
+// __fadd2_rn, __ffma2_rn, two independent IEEE round-to-nearest operations each) carry the real and
+// the imaginary sum together, which halves the instructions the kernels issue: the first pair of
+// products is (ar br, ar bi), the second (ai bi, -ai br).  A difference x - y is formed as
+// fma(y, -1, x), which rounds the same exact value once, and the error term as RN(p - a b) from the
+// negated factor, which is -e exactly; so each component goes through the same rounded operations,
+// in the same order, as a scalar two-sum accumulation, and the pairing does not change the sums.
+__device__ __forceinline__ void dd_acc2(float2 a, float2 na, float2 b, float2& hi, float2& lo) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 p = __fmul2_rn(a, b);
+  const float2 ne = __ffma2_rn(na, b, p);            // p - a b = -e, exact
+  const float2 s = __fadd2_rn(hi, p);                // two-sum(hi, p) = s + err
+  const float2 bb = __ffma2_rn(hi, m1, s);           // s - hi
+  const float2 err = __fadd2_rn(__ffma2_rn(__ffma2_rn(bb, m1, s), m1, hi), __ffma2_rn(bb, m1, p));
   hi = s;
-  lo = __fadd_rn(lo, __fadd_rn(err, e));
+  lo = __fadd2_rn(lo, __ffma2_rn(ne, m1, err));      // lo + (err + e)
 }
 
-__device__ __forceinline__ void dd_renorm(float& hi, float& lo) {
-  const float s = __fadd_rn(hi, lo);
-  lo = __fadd_rn(lo, -__fadd_rn(s, -hi));
+__device__ __forceinline__ void dd_renorm2(float2& hi, float2& lo) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 s = __fadd2_rn(hi, lo);
+  lo = __ffma2_rn(__ffma2_rn(hi, m1, s), m1, lo);    // lo - (s - hi)
   hi = s;
+}
+
+__device__ __forceinline__ void cmac_dd2(float2 a, float2 b, float2& hi, float2& lo) {
+  dd_acc2(make_float2(a.x, a.x), make_float2(-a.x, -a.x), b, hi, lo);
+  dd_acc2(make_float2(a.y, -a.y), make_float2(-a.y, a.y), make_float2(b.y, b.x), hi, lo);
+  dd_renorm2(hi, lo);
 }
 
 __host__ __device__ inline void decode_task(long long t, int C, int nl, int nlh, int center, int& c1,
@@ -100,12 +118,12 @@ __global__ void __launch_bounds__(256) gram_cells_kernel(GramParams P, float4* _
   const float2* xb = P.x.p + (long long)c2 * P.x.sc;
   const int nt = blockDim.x;
 
-  float rh[GXSLOT], rl[GXSLOT], ih[GXSLOT], il[GXSLOT];
+  float2 sh[GXSLOT], sl[GXSLOT];   // (re, im) double-word sums: hi, lo
   int bx[GXSLOT];
   bool bok[GXSLOT];
 #pragma unroll
   for (int j = 0; j < GXSLOT; ++j) {
-    rh[j] = rl[j] = ih[j] = il[j] = 0.f;
+    sh[j] = sl[j] = make_float2(0.f, 0.f);
     const int xx = threadIdx.x + j * nt;
     int vx = xx + ddx;
     bool ok = xx < g.ex;
@@ -128,13 +146,7 @@ __global__ void __launch_bounds__(256) gram_cells_kernel(GramParams P, float4* _
         if (bok[j]) {
           const float2 a = arow[threadIdx.x + j * nt];
           const float2 b = brow[bx[j]];
-          // conj(a) * b = (ar br + ai bi) + i (ar bi - ai br)
-          dd_acc(a.x, b.x, rh[j], rl[j]);
-          dd_acc(a.y, b.y, rh[j], rl[j]);
-          dd_acc(a.x, b.y, ih[j], il[j]);
-          dd_acc(-a.y, b.x, ih[j], il[j]);
-          dd_renorm(rh[j], rl[j]);
-          dd_renorm(ih[j], il[j]);
+          cmac_dd2(a, b, sh[j], sl[j]);   // conj(a) * b = (ar br + ai bi) + i (ar bi - ai br)
         }
       }
     }
@@ -142,7 +154,7 @@ __global__ void __launch_bounds__(256) gram_cells_kernel(GramParams P, float4* _
 #pragma unroll
   for (int j = 0; j < GXSLOT; ++j) {
     const int xx = threadIdx.x + j * nt;
-    if (xx < g.ex) vals[xx] = make_float4(rh[j], rl[j], ih[j], il[j]);
+    if (xx < g.ex) vals[xx] = make_float4(sh[j].x, sl[j].x, sh[j].y, sl[j].y);
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = nt >> 5;
@@ -188,15 +200,15 @@ __global__ void gram_rows_kernel(GramParams P, float4* __restrict__ part) {
   else ok = ok && vx >= 0 && vx < g.ex;
   if (xx < g.ex)
     for (int c = 0; c < P.ncy; ++c) cellbuf[c * g.ex + xx] = make_float4(0.f, 0.f, 0.f, 0.f);
-  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+  float2 sh = make_float2(0.f, 0.f), sl = sh;   // (re, im) double-word sums: hi, lo
   int cell = -1;
   auto flush = [&]() {
     if (cell >= 0 && xx < g.ex) {
       float4* slot = &cellbuf[cell * g.ex + xx];
-      const cdf sum = c_add(ld4(slot), cdf{{rh, rl}, {ih, il}});
+      const cdf sum = c_add(ld4(slot), cdf{{sh.x, sl.x}, {sh.y, sl.y}});
       st4(slot, sum);
     }
-    rh = rl = ih = il = 0.f;
+    sh = sl = make_float2(0.f, 0.f);
   };
   for (int z = P.pz0[pzi]; z < P.pz1[pzi]; ++z) {
     int vz = z + ddz;
@@ -215,13 +227,7 @@ __global__ void gram_rows_kernel(GramParams P, float4* __restrict__ part) {
       if (ok) {
         const float2 a = xa[(long long)(P.x.oz + z) * P.x.sz + (long long)(P.x.oy + y) * P.x.sy + P.x.ox + xx];
         const float2 b = xb[(long long)(P.x.oz + vz) * P.x.sz + (long long)(P.x.oy + vy) * P.x.sy + P.x.ox + vx];
-        // conj(a) * b = (ar br + ai bi) + i (ar bi - ai br)
-        dd_acc(a.x, b.x, rh, rl);
-        dd_acc(a.y, b.y, rh, rl);
-        dd_acc(a.x, b.y, ih, il);
-        dd_acc(-a.y, b.x, ih, il);
-        dd_renorm(rh, rl);
-        dd_renorm(ih, il);
+        cmac_dd2(a, b, sh, sl);   // conj(a) * b = (ar br + ai bi) + i (ar bi - ai br)
       }
     }
   }
@@ -283,7 +289,7 @@ __host__ __device__ inline void decode_task9(long long t, int C, int nyz, int cy
 }
 
 template <int LX>
-__global__ void __launch_bounds__(256) gram_lagrow_kernel(GramParams P, LagRowParams Q, float4* __restrict__ part) {
+__global__ void __launch_bounds__(256, 3) gram_lagrow_kernel(GramParams P, LagRowParams Q, float4* __restrict__ part) {
   pdl_wait();  // programmatic dependent launch: inputs of the previous kernel
   pdl_trigger();
   extern __shared__ float4 red[];  // kind 0: [rgroups][LX][xw]; kind 1: [nb][LX][xw]
@@ -310,10 +316,10 @@ __global__ void __launch_bounds__(256) gram_lagrow_kernel(GramParams P, LagRowPa
     else vx = min(max(vx, 0), g.ex - 1);
     bx[j] = vx;
   }
-  float rh[LX], rl[LX], ih[LX], il[LX];
+  float2 sh[LX], sl[LX];   // (re, im) double-word sums of x lag j: hi, lo
   auto zero = [&]() {
 #pragma unroll
-    for (int j = 0; j < LX; ++j) rh[j] = rl[j] = ih[j] = il[j] = 0.f;
+    for (int j = 0; j < LX; ++j) sh[j] = sl[j] = make_float2(0.f, 0.f);
   };
   // one row pair: a = x_c1[z][y][x], b_j = x_c2[z + ddz][vy][x + j - (kx - 1)]
   auto row = [&](int z, int vz, int y, int vy) {
@@ -324,15 +330,7 @@ __global__ void __launch_bounds__(256) gram_lagrow_kernel(GramParams P, LagRowPa
 #pragma unroll
     for (int j = 0; j < LX; ++j) b[j] = __ldg(br + bx[j]);
 #pragma unroll
-    for (int j = 0; j < LX; ++j) {
-      // conj(a) * b = (ar br + ai bi) + i (ar bi - ai br)
-      dd_acc(a.x, b[j].x, rh[j], rl[j]);
-      dd_acc(a.y, b[j].y, rh[j], rl[j]);
-      dd_acc(a.x, b[j].y, ih[j], il[j]);
-      dd_acc(-a.y, b[j].x, ih[j], il[j]);
-      dd_renorm(rh[j], rl[j]);
-      dd_renorm(ih[j], il[j]);
-    }
+    for (int j = 0; j < LX; ++j) cmac_dd2(a, b[j], sh[j], sl[j]);   // conj(a) * b_j
   };
   auto shifted = [&](int v, int e, bool circ, int& out) -> bool {
     if (circ) { out = wrap(v, e); return true; }
@@ -354,7 +352,7 @@ __global__ void __launch_bounds__(256) gram_lagrow_kernel(GramParams P, LagRowPa
       }
     }
 #pragma unroll
-    for (int j = 0; j < LX; ++j) red[(rg * LX + j) * Q.xw + x] = make_float4(rh[j], rl[j], ih[j], il[j]);
+    for (int j = 0; j < LX; ++j) red[(rg * LX + j) * Q.xw + x] = make_float4(sh[j].x, sl[j].x, sh[j].y, sl[j].y);
   } else {
     for (int b = rg; b < Q.nb; b += Q.rgroups) {
       zero();
@@ -368,7 +366,7 @@ __global__ void __launch_bounds__(256) gram_lagrow_kernel(GramParams P, LagRowPa
         }
       }
 #pragma unroll
-      for (int j = 0; j < LX; ++j) red[(b * LX + j) * Q.xw + x] = make_float4(rh[j], rl[j], ih[j], il[j]);
+      for (int j = 0; j < LX; ++j) red[(b * LX + j) * Q.xw + x] = make_float4(sh[j].x, sl[j].x, sh[j].y, sl[j].y);
     }
   }
   __syncthreads();
