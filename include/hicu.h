@@ -497,7 +497,15 @@ hicu_status hicu_gd_step(hicu_handle* h, const hicu_geom* geom, const hicu_regio
  * (hicu_expand_filters) for the convolutions.
  *   x0, mask, x_out may be HOST or DEVICE pointers (detected per pointer);
  *   host buffers are staged through the handle's workspace with copies on
- *   `stream`, and the call then returns after x_out is written.
+ *   `stream`, and the call then returns after x_out is written.  A host x0
+ *   whose first stage covers only some z planes is uploaded in two parts:
+ *   those planes on `stream`, the others on a copy stream of the handle
+ *   while the first stages run; `stream` waits for that copy (an event)
+ *   before any stage that reaches beyond the planes, before the output copy
+ *   and before an error return, so synchronising `stream` covers it.  A
+ *   circular z axis, params->init = 1, dc_weight > 0 and l1_threshold > 0
+ *   upload x0 in one copy.  Host buffers must stay valid until `stream` has
+ *   been synchronised.
  *   log: optional host log; when given, the call synchronises the stream.
  */
 hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, const float* x0,

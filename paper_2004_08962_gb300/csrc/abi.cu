@@ -65,6 +65,15 @@ hicu_status ensure_side_stream(hicu_handle* h) {
   return HICU_OK;
 }
 
+static hicu_status ensure_copy_stream(hicu_handle* h) {
+  if (h->copy_st) return HICU_OK;
+  if (cudaStreamCreateWithFlags(&h->copy_st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->copy_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->copy_join, cudaEventDisableTiming) != cudaSuccess)
+    return cuda_error(h, cudaGetLastError(), "copy stream");
+  return HICU_OK;
+}
+
 void prof_count(hicu_handle* h, int cls) {
   ++h->launches_all;
   if (h->prof_class == cls) ++h->launches_class;
@@ -239,6 +248,9 @@ extern "C" hicu_status hicu_destroy(hicu_handle* h) {
   if (h->side_join) cudaEventDestroy(h->side_join);
   if (h->draw_fork) cudaEventDestroy(h->draw_fork);
   if (h->draw_join) cudaEventDestroy(h->draw_join);
+  if (h->copy_st) cudaStreamDestroy(h->copy_st);
+  if (h->copy_fork) cudaEventDestroy(h->copy_fork);
+  if (h->copy_join) cudaEventDestroy(h->copy_join);
   if (h->coop_in) cudaEventDestroy(h->coop_in);
   if (h->coop_out) cudaEventDestroy(h->coop_out);
   for (auto& w : h->ws)
@@ -798,6 +810,27 @@ __global__ void tail_sum_kernel(const double* eig, int nr, double* out) {
 
 }  // namespace
 
+// A host input goes up in two parts: the z planes of the first stage's region (every channel) on
+// the call's stream, then the other planes on the handle's copy stream while the first stages run,
+// which read and write y only inside their regions.  The call's stream waits for the second part
+// before the first stage that reaches beyond those planes and before the output copy, and on an
+// early return, so that synchronising the call's stream always covers the copy.
+struct StagedUpload {
+  hicu_handle* h;
+  cudaStream_t st;
+  long long z0, z1;   // planes uploaded on the call's stream
+  bool pending = false;
+  bool covers(const hicu_region& r) const { return r.off[2] >= z0 && r.off[2] + r.ext[2] <= z1; }
+  hicu_status join() {
+    if (!pending) return HICU_OK;
+    pending = false;
+    return cuda_error(h, cudaStreamWaitEvent(st, h->copy_join, 0), "reconstruct: upload join");
+  }
+  ~StagedUpload() {
+    if (pending) cudaStreamWaitEvent(st, h->copy_join, 0);
+  }
+};
+
 extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, const float* x0,
                                         const uint8_t* mask, const hicu_params* prm, float* x_out,
                                         hicu_log* log, void* stream) {
@@ -868,12 +901,49 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
       return cuda_error(h, cudaGetLastError(), "reconstruct: mask upload");
     m = mm;
   }
-  if (cudaMemcpyAsync(y, x0, sizeof(float2) * N, in_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                      st) != cudaSuccess)
-    return cuda_error(h, cudaGetLastError(), "reconstruct: input copy");
+  const bool soft = prm->dc_weight > 0.0, l1 = prm->l1_threshold > 0.0;
+  // a host input is uploaded in two parts where the first stage covers only some z planes and
+  // nothing reads the whole array first (time-averaged start, a copy of X0); a circular z axis
+  // goes up whole
+  const long long Z = geom->dim[2];
+  StagedUpload up{h, st, 0, Z};
+  if (!in_dev && !geom->circular[2] && prm->init == 0 && !soft && !l1) {
+    up.z0 = prm->stages[0].region.off[2];
+    up.z1 = up.z0 + prm->stages[0].region.ext[2];
+  }
+  if (up.z0 == 0 && up.z1 == Z) {
+    if (cudaMemcpyAsync(y, x0, sizeof(float2) * N, in_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        st) != cudaSuccess)
+      return cuda_error(h, cudaGetLastError(), "reconstruct: input copy");
+  } else {
+    if ((s = ensure_copy_stream(h))) return s;
+    const size_t pbytes = sizeof(float2) * (size_t)(geom->dim[0] * geom->dim[1]);   // one z plane
+    char* yd = reinterpret_cast<char*>(y);
+    const char* xs = reinterpret_cast<const char*>(x0);
+    auto part = [&](long long c, long long za, long long zb, cudaStream_t cs) {
+      const size_t off = (size_t)(c * Z + za) * pbytes;
+      return za < zb ? cudaMemcpyAsync(yd + off, xs + off, (size_t)(zb - za) * pbytes, cudaMemcpyHostToDevice, cs)
+                     : cudaSuccess;
+    };
+    cudaError_t ce = cudaSuccess;
+    for (long long c = 0; c < geom->ncoil && ce == cudaSuccess; ++c) ce = part(c, up.z0, up.z1, st);
+    if (ce == cudaSuccess) ce = cudaEventRecord(h->copy_fork, st);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(h->copy_st, h->copy_fork, 0);
+    if (ce != cudaSuccess) return cuda_error(h, ce, "reconstruct: input copy");
+    for (long long c = 0; c < geom->ncoil && ce == cudaSuccess; ++c) {
+      ce = part(c, 0, up.z0, h->copy_st);
+      if (ce == cudaSuccess) ce = part(c, up.z1, Z, h->copy_st);
+    }
+    const cudaError_t cj = cudaEventRecord(h->copy_join, h->copy_st);
+    if (cj != cudaSuccess) {
+      cudaStreamSynchronize(h->copy_st);   // nothing to join: the copies end before the return
+      return cuda_error(h, cj, "reconstruct: input copy");
+    }
+    up.pending = true;
+    if (ce != cudaSuccess) return cuda_error(h, ce, "reconstruct: input copy");
+  }
   // the observed data X0, kept for the soft data-consistency term and for restoring the samples after
   // the l1 step (the start estimate in y may differ from it: time-averaged initialisation)
-  const bool soft = prm->dc_weight > 0.0, l1 = prm->l1_threshold > 0.0;
   float* x0c = nullptr;
   if (soft || l1) {
     x0c = (float*)ws_get(h, WS_REC_X0, sizeof(float2) * N, &s);
@@ -953,6 +1023,7 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
   hicu_region prev = prm->stages[0].region;
   for (int si = 0; si < prm->nstages; ++si) {
     const hicu_stage& stg = prm->stages[si];
+    if (!up.covers(stg.region) && (s = up.join())) return s;
     // split planes of y on this stage's region: made by the stage's first step, then kept current
     // by each step's update (the Gram and eigen-solve leave y alone)
     bool planes_valid = false;
@@ -1039,6 +1110,7 @@ extern "C" hicu_status hicu_reconstruct(hicu_handle* h, const hicu_geom* geom, c
       prev = stg.region;
     }
   }
+  if ((s = up.join())) return s;
   if (!out_dev) {
     if (cudaMemcpyAsync(x_out, y, sizeof(float2) * N, cudaMemcpyDeviceToHost, st) != cudaSuccess)
       return cuda_error(h, cudaGetLastError(), "reconstruct: output copy");

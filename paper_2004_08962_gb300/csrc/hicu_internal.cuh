@@ -209,6 +209,11 @@ struct hicu_handle {
   cudaEvent_t side_join = nullptr;
   cudaEvent_t draw_fork = nullptr;  // JL draws of an outer iteration
   cudaEvent_t draw_join = nullptr;
+  // upload stream of hicu_reconstruct (created on demand): the part of a host input that the first
+  // stages do not read, copied while they run
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t copy_fork = nullptr;
+  cudaEvent_t copy_join = nullptr;
   // l1 step (softdc.cu): the FFT plan (a cufftHandle) and the geometry key it was made for
   int fft_plan = 0;
   bool fft_have = false;
