@@ -71,7 +71,8 @@ GRAM_INSTR_PER_CMAC = 40
 # workload (profiles/), averaged over the class's launches in one reconstruction (centre-region
 # and full-size launches together, as the event timing averages them); a kernel changed since its
 # capture has no entry.
-NCU_TRAFFIC = {("knee3d_256x256x160", "conv_tc"): 293246606, ("knee3d_256x256x160", "adjoint_tc"): 570873406}
+NCU_TRAFFIC = {("knee3d_256x256x160", "conv_tc"): 293246606, ("knee3d_256x256x160", "adjoint_tc"): 570873406,
+               ("knee3d_256x256x160", "gram"): 395651072}
 
 
 def problem_seed(workload: str, rank: int) -> int:
