@@ -65,8 +65,9 @@ KERNEL_NAMES = {0: "gram", 1: "eig", 2: "conv_fp32", 3: "adjoint_fp32", 4: "jl",
 SMS, FP32_LANES = 152, 128
 # Gram: each complex product conj(a) b is 4 real products, each formed exactly and accumulated in
 # double-word arithmetic (1 multiply, 1 FMA for the error term, 8 adds of the two-sum): 40 FP32
-# instructions for the 8 algorithmic flops of one complex multiply-add
-GRAM_INSTR_PER_CMAC = 40
+# operations for the 8 algorithmic flops of one complex multiply-add (issued two per paired
+# instruction; the FP32 pipe's operation rate is the bound)
+GRAM_OPS_PER_CMAC = 40
 # DRAM bytes (read + write) per launch from one ncu capture of the same kernel on the same
 # workload (profiles/), averaged over the class's launches in one reconstruction (centre-region
 # and full-size launches together, as the event timing averages them); a kernel changed since its
@@ -148,15 +149,18 @@ def algorithmic_flops(pb, cls):
             tot += st.iters * st.gd_steps * 2 * 8.0 * n * st.p * s
         elif cls in (3, 7):  # one adjoint per step, same count
             tot += st.iters * st.gd_steps * 8.0 * n * st.p * s
-        elif cls == 0:  # lag-form correlation: C^2 (2k-1)^d / 2 complex MACs per region point
-            region = prev.ext[0] * prev.ext[1] * prev.ext[2]
+        elif cls == 0 and st.iters > 0:
+            # lag-form correlation: C^2 (2k-1)^d / 2 complex MACs per point of the previous outer
+            # iteration's region: the previous stage's for a stage's first iteration, its own after
+            points = prev.ext[0] * prev.ext[1] * prev.ext[2] + (st.iters - 1) * st.ext[0] * st.ext[1] * st.ext[2]
             lags = (2 * kx - 1) * (2 * ky - 1) * (2 * kz - 1)
-            tot += st.iters * 8.0 * (C * C * lags / 2.0) * region
+            tot += 8.0 * (C * C * lags / 2.0) * points
         elif cls == 8:  # Householder tridiagonalisation of the n x n Hermitian Gram: 16 n^3 / 3
             tot += st.iters * 16.0 * n ** 3 / 3.0
         elif cls == 1:  # back-transformation of the r principal vectors: 8 n^2 r
             tot += st.iters * 8.0 * n * n * pb.rank
-        prev = st
+        if st.iters > 0:
+            prev = st
     return tot
 
 
@@ -168,7 +172,7 @@ def class_roofline(pb, wname, cls, ms, launches, recons, peaks):
     """Roofline of one kernel class from its summed event time `ms` over `launches` launches made by
     `recons` reconstructions: algorithmic work of those reconstructions / device time, against the
     peak of the pipe the kernel runs on."""
-    fp32_instr = SMS * FP32_LANES * peaks.get("sm_max_mhz", 2070.0) * 1e6   # FP32 instructions / s
+    fp32_ops = SMS * FP32_LANES * peaks.get("sm_max_mhz", 2070.0) * 1e6   # FP32 lane operations / s
     avg_s = ms / 1e3 / max(launches, 1)
     flops = algorithmic_flops(pb, cls) * recons
     ach = flops / max(ms / 1e3, 1e-12) / 1e12
@@ -182,15 +186,15 @@ def class_roofline(pb, wname, cls, ms, launches, recons, peaks):
                              "form issues 4 tensor products per algorithmic one (hi and lo of the input "
                              "against [B_hi | B_lo])"})
     elif cls == 0:
-        peak = fp32_instr * 8.0 / GRAM_INSTR_PER_CMAC / 1e12
+        peak = fp32_ops * 8.0 / GRAM_OPS_PER_CMAC / 1e12
         base.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                      "peak_source": f"FP32 pipe {SMS} SMs x {FP32_LANES} lanes x max SM clock, "
-                                    f"{GRAM_INSTR_PER_CMAC} FP32 instructions per double-word complex "
+                                    f"{GRAM_OPS_PER_CMAC} FP32 operations per double-word complex "
                                     "multiply-add (8 algorithmic flops)",
                      "work": "lag-form cross-correlation: C^2 (2k-1)^d / 2 complex MACs per region point "
                              "(8 flops each)"})
     elif cls in (2, 3):
-        peak = 2.0 * fp32_instr / 1e12
+        peak = 2.0 * fp32_ops / 1e12
         base.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                      "peak_source": "FP32 pipe, FMA = 2 flops, max SM clock",
                      "work": "8 n p s flops per convolution"})
